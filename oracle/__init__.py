@@ -1,0 +1,221 @@
+"""CPU oracle for the barrier-repair loop (TEST INFRASTRUCTURE ONLY).
+
+Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline leg may import this package.  The product path never does.  It
+shares no code with the CUDA engine: it compiles ``oracle.c`` (plain C) with
+gcc on first use and calls it through ctypes.
+
+Functions take duck-typed programs (any object with the attributes of
+``paper_2011_08373_gb300.synth.Program``) and return plain Python values.
+
+Parity status: every C function is pinned by ``tests/test_oracle_pins.py``
+(paper listings, the Section 2.4 mhs counterexample, an independent flag-reset
+race detector, a closed form for affine maps, interval-stabbing DP, scipy
+MILP, invariants, the path-independence lemma).  The synthetic workload
+distributions themselves are free choices and carry no pin.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAX_TRAJ = 64
+MAX_CLAUSES = 656
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, plain -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Prog(C.Structure):
+    _fields_ = [
+        ("n_stmts", C.c_uint32),
+        ("op", C.c_void_p), ("space", C.c_void_p), ("kind", C.c_void_p),
+        ("a", C.c_void_p), ("b", C.c_void_p), ("c", C.c_void_p), ("perm_off", C.c_void_p),
+        ("guard_k", C.c_void_p), ("guard_r", C.c_void_p),
+        ("slot_level", C.c_void_p),
+        ("slot_guard_k", C.c_void_p), ("slot_guard_r", C.c_void_p),
+        ("slot_weight", C.c_void_p),
+        ("m_shared", C.c_uint32), ("m_global", C.c_uint32),
+        ("perm", C.c_void_p), ("perm_len", C.c_uint32),
+        ("existing_mask", C.c_uint32),
+        ("blocks", C.c_uint32), ("threads", C.c_uint32),
+    ]
+
+
+class _Witness(C.Structure):
+    _fields_ = [("intra", C.c_uint32 * 32), ("inter", C.c_uint32 * 32),
+                ("diverge", C.c_uint32), ("access_pairs", C.c_uint64)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("mask", C.c_uint32), ("weight", C.c_uint32),
+                ("added", C.c_uint32), ("removed", C.c_uint32), ("iters", C.c_uint32),
+                ("traj", C.c_uint32 * MAX_TRAJ), ("n_clauses", C.c_uint32),
+                ("clauses", C.c_uint32 * MAX_CLAUSES), ("forbidden", C.c_uint32),
+                ("access_pairs", C.c_uint64)]
+
+
+def _configure(path):
+    lib = C.CDLL(path)
+    lib.orc_check.argtypes = [C.POINTER(_Prog), C.c_uint32, C.POINTER(_Witness)]
+    lib.orc_check.restype = None
+    lib.orc_clauses.argtypes = [C.POINTER(_Prog), C.POINTER(_Witness),
+                                C.POINTER(C.c_uint32), C.c_uint32]
+    lib.orc_clauses.restype = C.c_uint32
+    lib.orc_solve.argtypes = [C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                              C.c_uint32, C.POINTER(C.c_uint32), C.c_uint32, C.c_uint32,
+                              C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]
+    lib.orc_solve.restype = C.c_int
+    lib.orc_repair.argtypes = [C.POINTER(_Prog), C.c_int, C.c_int, C.c_uint32,
+                               C.POINTER(_Result)]
+    lib.orc_repair.restype = None
+    lib.orc_repair_batch.argtypes = [C.POINTER(_Prog), C.POINTER(C.c_int32), C.c_uint32,
+                                     C.c_int, C.c_uint32, C.POINTER(_Result), C.c_uint32]
+    lib.orc_repair_batch.restype = None
+    assert lib.orc_sizeof_result() == C.sizeof(_Result)
+    assert lib.orc_sizeof_prog() == C.sizeof(_Prog)
+    assert lib.orc_sizeof_witness() == C.sizeof(_Witness)
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _configure(build())
+    return _lib
+
+
+class using_library:
+    """Temporarily route every call through another build of oracle.c (the
+    mutation tests use it to show that the pins reject planted mistakes)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _load()
+        _lib = _configure(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _u32(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.uint32))
+
+
+def _u8(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.uint8))
+
+
+class _Marshalled:
+    """Keeps the numpy buffers of one program alive while C reads them."""
+
+    def __init__(self, p):
+        n = p.op.shape[0] - 1
+        self.keep = [
+            _u8(p.op), _u8(p.space), _u8(p.kind), _u32(p.a), _u32(p.b), _u32(p.c),
+            _u32(p.perm_off), _u32(p.guard_k), _u32(p.guard_r), _u8(p.slot_level),
+            _u32(p.slot_guard_k), _u32(p.slot_guard_r), _u32(p.slot_weight),
+            _u32(p.perm) if len(p.perm) else np.zeros(1, np.uint32),
+        ]
+        assert len(p.slot_level) == n
+        k = self.keep
+        ptr = lambda arr: arr.ctypes.data
+        self.s = _Prog(p.op.shape[0], ptr(k[0]), ptr(k[1]), ptr(k[2]), ptr(k[3]), ptr(k[4]),
+                       ptr(k[5]), ptr(k[6]), ptr(k[7]), ptr(k[8]), ptr(k[9]), ptr(k[10]),
+                       ptr(k[11]), ptr(k[12]), int(p.m_shared), int(p.m_global), ptr(k[13]),
+                       len(p.perm), int(p.existing_mask), int(p.blocks), int(p.threads))
+
+
+def check(p, mask: int) -> dict:
+    """Witnesses of program ``p`` under barrier mask ``mask``."""
+    lib = _load()
+    m = _Marshalled(p)
+    w = _Witness()
+    lib.orc_check(C.byref(m.s), mask, C.byref(w))
+    S = p.op.shape[0]
+    return {"intra": [w.intra[i] for i in range(S)], "inter": [w.inter[i] for i in range(S)],
+            "diverge": w.diverge, "access_pairs": w.access_pairs}
+
+
+def clauses(p, witness: dict) -> list:
+    """Sorted unique clause masks generated by one check's witnesses."""
+    lib = _load()
+    m = _Marshalled(p)
+    w = _Witness()
+    for i, v in enumerate(witness["intra"]):
+        w.intra[i] = v
+    for i, v in enumerate(witness["inter"]):
+        w.inter[i] = v
+    w.diverge = witness["diverge"]
+    buf = (C.c_uint32 * (2 * 32 * 32))()
+    n = lib.orc_clauses(C.byref(m.s), C.byref(w), buf, 0)
+    return [buf[i] for i in range(n)]
+
+
+def solve(n_vars: int, weights, pos, neg=(), forced: int = 0, forbidden: int = 0):
+    """Lowest (weight, mask) hitting set, or None if unsatisfiable."""
+    lib = _load()
+    w = (C.c_uint32 * max(1, n_vars))(*[int(x) for x in weights])
+    pa = (C.c_uint32 * max(1, len(pos)))(*[int(x) for x in pos])
+    na = (C.c_uint32 * max(1, len(neg)))(*[int(x) for x in neg])
+    mask = C.c_uint32()
+    wt = C.c_uint64()
+    rc = lib.orc_solve(n_vars, w, pa, len(pos), na, len(neg), forced, forbidden,
+                       C.byref(mask), C.byref(wt))
+    if rc:
+        return None
+    return mask.value, wt.value
+
+
+def _result_dict(r: _Result) -> dict:
+    return {"status": r.status, "mask": r.mask, "weight": r.weight, "added": r.added,
+            "removed": r.removed, "iters": r.iters,
+            "traj": [r.traj[i] for i in range(min(r.iters, MAX_TRAJ))],
+            "clauses": [r.clauses[i] for i in range(r.n_clauses)], "forbidden": r.forbidden,
+            "access_pairs": r.access_pairs}
+
+
+def repair(p, mode=None, grid_enabled: bool = True, max_iters: int = 64) -> dict:
+    """Algorithm 1 on one program (mode defaults to ``p.mode``)."""
+    lib = _load()
+    m = _Marshalled(p)
+    r = _Result()
+    lib.orc_repair(C.byref(m.s), int(p.mode if mode is None else mode), int(grid_enabled),
+                   max_iters, C.byref(r))
+    return _result_dict(r)
+
+
+def repair_batch(progs, grid_enabled: bool = True, max_iters: int = 64,
+                 n_threads: int = 1) -> list:
+    """Algorithm 1 on many programs, spread over ``n_threads`` CPU threads."""
+    lib = _load()
+    ms = [_Marshalled(p) for p in progs]
+    arr = (_Prog * len(progs))(*[m.s for m in ms])
+    modes = (C.c_int32 * len(progs))(*[int(p.mode) for p in progs])
+    out = (_Result * len(progs))()
+    lib.orc_repair_batch(arr, modes, len(progs), int(grid_enabled), max_iters, out, n_threads)
+    return [_result_dict(out[i]) for i in range(len(progs))]

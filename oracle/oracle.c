@@ -1,0 +1,338 @@
+/*
+ * CPU oracle for the barrier-repair loop of GPURepair (arXiv 2011.08373).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow, literal C: every function below
+ * writes out a definition or the steps of Algorithm 1 with no blocking,
+ * fusion or reordering.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library; the product path never
+ * does.  It shares no code, header or table with the CUDA engine.
+ *
+ * Model (the paper's instrumented kernel, Section 2.2, restated over a
+ * concrete launch of B blocks x T threads):
+ *   statement s: op (0 read / 1 write), space (0 shared: one private array per
+ *   block / 1 global: one array for the grid), address map
+ *     affine, strided : (a*tid + c*blk + b) mod M
+ *     permutation     : perm[perm_off + ((tid + c*blk + b) mod M)]
+ *   and guard (k, r): statement s runs for thread tid iff k == 0 or tid%k == r.
+ *   slot k (between statements k and k+1): level (0 block / 1 grid),
+ *   guard (k, r) with the same meaning, weight w_k.
+ *
+ * Parity-pinned functions (see tests/test_oracle_pins.py):
+ *   orc_check  -- pinned by the paper's listings (Section 1, Appendix A.4),
+ *                 an independent flag-reset race detector (Section 2.2),
+ *                 a number-theoretic closed form for affine maps, invariants.
+ *   orc_clauses-- pinned by the exact-filter invariant against orc_check.
+ *   orc_solve  -- pinned by the mhs counterexample of Section 2.4, interval
+ *                 stabbing by dynamic programming, and scipy's MILP solver.
+ *   orc_repair -- pinned by the listings and by the path-independence lemma
+ *                 (final mask = lowest-key witness-free mask over all masks).
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_STMTS 25
+#define ORC_MAX_CLAUSES 656
+#define ORC_MAX_TRAJ 64
+
+typedef struct {
+    uint32_t n_stmts;
+    const uint8_t *op, *space, *kind;
+    const uint32_t *a, *b, *c, *perm_off;
+    const uint32_t *guard_k, *guard_r;         /* per statement */
+    const uint8_t *slot_level;                 /* per slot */
+    const uint32_t *slot_guard_k, *slot_guard_r;
+    const uint32_t *slot_weight;
+    uint32_t m_shared, m_global;
+    const uint32_t *perm;
+    uint32_t perm_len;
+    uint32_t existing_mask;
+    uint32_t blocks, threads;
+} orc_prog;
+
+typedef struct {
+    uint32_t intra[32]; /* row i: bit j set <=> same-block witness (i, j), j >= i */
+    uint32_t inter[32]; /* row i: bit j set <=> cross-block witness (i, j)        */
+    uint32_t diverge;   /* bit k set <=> enabled slot k is divergent               */
+    uint64_t access_pairs;
+} orc_witness;
+
+typedef struct {
+    int32_t status; /* 0 repaired, 1 unrepairable, 2 iteration cap reached */
+    uint32_t mask, weight, added, removed, iters;
+    uint32_t traj[ORC_MAX_TRAJ];
+    uint32_t n_clauses;
+    uint32_t clauses[ORC_MAX_CLAUSES];
+    uint32_t forbidden;
+    uint64_t access_pairs;
+} orc_result;
+
+/* --- the model's primitive definitions ----------------------------------- */
+
+static int orc_active(uint32_t k, uint32_t r, uint32_t tid) {
+    return k == 0 || tid % k == r;
+}
+
+static uint32_t orc_addr(const orc_prog *p, uint32_t s, uint32_t blk, uint32_t tid) {
+    uint64_t M = p->space[s] == 0 ? p->m_shared : p->m_global;
+    if (p->kind[s] == 2) {
+        uint64_t idx = ((uint64_t)tid + (uint64_t)p->c[s] * blk + p->b[s]) % M;
+        return p->perm[p->perm_off[s] + idx];
+    }
+    return (uint32_t)(((uint64_t)p->a[s] * tid + (uint64_t)p->c[s] * blk + p->b[s]) % M);
+}
+
+/* Is there an enabled slot (any level / grid level) among slots i .. j-1?
+ * A block barrier orders the accesses of threads in the same block, a grid
+ * barrier those of every pair of threads (Section 2.2, flag reset). */
+static int orc_separated(const orc_prog *p, uint32_t mask, uint32_t i, uint32_t j, int grid_only) {
+    for (uint32_t k = i; k < j; k++)
+        if ((mask >> k) & 1u)
+            if (!grid_only || p->slot_level[k] == 1) return 1;
+    return 0;
+}
+
+/* Check P under barrier mask m: every race witness (i, j) and every
+ * divergent enabled slot.  Definition by enumeration of all thread pairs.
+ *   (i, j), i <= j, same space, at least one write: a witness exists iff there
+ *   are distinct threads g1 (running i) and g2 (running j) with the same
+ *   address in the same array instance (same block for shared arrays), and no
+ *   enabled barrier separating them.  Same-block pairs go to intra[i], cross
+ *   block pairs to inter[i].  Values are not modelled: equal-value writes race
+ *   (Appendix A.4, write-write race).
+ *   Slot k diverges iff it is enabled and its guard is true for some thread
+ *   of a block and false for another (Section 1, barrier divergence).
+ * access_pairs counts the thread pairs examined: for i < j ordered pairs
+ * (g1 at i, g2 at j), for i == j unordered pairs, each only while its scope
+ * (same block / cross block) is not separated under m. */
+void orc_check(const orc_prog *p, uint32_t mask, orc_witness *out) {
+    memset(out, 0, sizeof(*out));
+    const uint32_t S = p->n_stmts, B = p->blocks, T = p->threads;
+    const uint64_t G = (uint64_t)B * T;
+    /* each statement's address and guard, evaluated once per thread */
+    uint32_t *addr = (uint32_t *)malloc(sizeof(uint32_t) * S * G);
+    uint8_t *act = (uint8_t *)malloc(S * (size_t)T);
+    for (uint32_t s = 0; s < S; s++) {
+        for (uint32_t t = 0; t < T; t++) act[(size_t)s * T + t] = (uint8_t)orc_active(p->guard_k[s], p->guard_r[s], t);
+        for (uint32_t b = 0; b < B; b++)
+            for (uint32_t t = 0; t < T; t++) addr[s * G + (uint64_t)b * T + t] = orc_addr(p, s, b, t);
+    }
+    for (uint32_t i = 0; i < S; i++) {
+        for (uint32_t j = i; j < S; j++) {
+            if (p->space[i] != p->space[j]) continue;
+            if (p->op[i] != 1 && p->op[j] != 1) continue;
+            const int shared = p->space[i] == 0;
+            const int open_same = !orc_separated(p, mask, i, j, 0);
+            const int open_cross = !shared && !orc_separated(p, mask, i, j, 1);
+            if (!open_same && !open_cross) continue;
+            for (uint32_t b1 = 0; b1 < B; b1++) {
+                for (uint32_t t1 = 0; t1 < T; t1++) {
+                    if (!act[(size_t)i * T + t1]) continue;
+                    const uint32_t a1 = addr[i * G + (uint64_t)b1 * T + t1];
+                    for (uint32_t b2 = 0; b2 < B; b2++) {
+                        const int same = b1 == b2;
+                        if (same && !open_same) continue;
+                        if (!same && !open_cross) continue;
+                        for (uint32_t t2 = 0; t2 < T; t2++) {
+                            if (same && t1 == t2) continue;
+                            /* statement i == j: count each unordered pair once */
+                            if (i == j && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;
+                            if (!act[(size_t)j * T + t2]) continue;
+                            out->access_pairs++;
+                            if (addr[j * G + (uint64_t)b2 * T + t2] != a1) continue;
+                            if (same) out->intra[i] |= 1u << j;
+                            else out->inter[i] |= 1u << j;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    free(addr);
+    free(act);
+    for (uint32_t k = 0; k + 1 < S; k++) {
+        if (!((mask >> k) & 1u) || p->slot_guard_k[k] == 0) continue;
+        int seen_true = 0, seen_false = 0;
+        for (uint32_t t = 0; t < T; t++) {
+            if (orc_active(p->slot_guard_k[k], p->slot_guard_r[k], t)) seen_true = 1;
+            else seen_false = 1;
+        }
+        if (seen_true && seen_false) out->diverge |= 1u << k;
+    }
+}
+
+/* GenerateClause (Section 2.4): a race witness (i, j) is avoided exactly when
+ * some barrier able to order it is on: any slot in i .. j-1 for a same-block
+ * witness, a grid slot in i .. j-1 for a cross-block one.  (i, i) gives the
+ * empty clause.  Result: the set of clauses as sorted unique masks. */
+static int orc_cmp_u32(const void *x, const void *y) {
+    uint32_t a = *(const uint32_t *)x, b = *(const uint32_t *)y;
+    return a < b ? -1 : a > b;
+}
+
+static uint32_t orc_slot_range(uint32_t i, uint32_t j) {
+    uint32_t m = 0;
+    for (uint32_t k = i; k < j; k++) m |= 1u << k;
+    return m;
+}
+
+uint32_t orc_clauses(const orc_prog *p, const orc_witness *w, uint32_t *clauses, uint32_t n_in) {
+    uint32_t grid = 0, n = n_in;
+    for (uint32_t k = 0; k + 1 < p->n_stmts; k++)
+        if (p->slot_level[k] == 1) grid |= 1u << k;
+    for (uint32_t i = 0; i < p->n_stmts; i++) {
+        for (uint32_t j = i; j < p->n_stmts; j++) {
+            if ((w->intra[i] >> j) & 1u) clauses[n++] = orc_slot_range(i, j);
+            if ((w->inter[i] >> j) & 1u) clauses[n++] = orc_slot_range(i, j) & grid;
+        }
+    }
+    qsort(clauses, n, sizeof(uint32_t), orc_cmp_u32);
+    uint32_t u = 0;
+    for (uint32_t t = 0; t < n; t++)
+        if (u == 0 || clauses[u - 1] != clauses[t]) clauses[u++] = clauses[t];
+    return u;
+}
+
+/* Minimum-weight hitting set (Section 2.3 definitions; weighted form of
+ * Section 2.4): among masks x with forced <= x, x & forbidden == 0, x hitting
+ * every positive clause and not containing any negative clause, the least
+ * (weight(x), x) in lexicographic order.  Brute force over all 2^n masks.
+ * Returns 0 and fills mask/weight, or 1 if no such mask exists. */
+int orc_solve(uint32_t n, const uint32_t *w, const uint32_t *pos, uint32_t n_pos,
+              const uint32_t *neg, uint32_t n_neg, uint32_t forced, uint32_t forbidden,
+              uint32_t *mask_out, uint64_t *weight_out) {
+    int found = 0;
+    uint64_t best_w = 0;
+    uint32_t best_x = 0;
+    const uint64_t total = 1ull << n;
+    for (uint64_t xx = 0; xx < total; xx++) {
+        const uint32_t x = (uint32_t)xx;
+        if ((x & forced) != forced) continue;
+        if (x & forbidden) continue;
+        int ok = 1;
+        for (uint32_t c = 0; c < n_pos && ok; c++)
+            if ((x & pos[c]) == 0) ok = 0;
+        for (uint32_t c = 0; c < n_neg && ok; c++)
+            if ((x & neg[c]) == neg[c]) ok = 0;
+        if (!ok) continue;
+        uint64_t wt = 0;
+        for (uint32_t k = 0; k < n; k++)
+            if ((x >> k) & 1u) wt += w[k];
+        if (!found || wt < best_w || (wt == best_w && x < best_x)) {
+            found = 1;
+            best_w = wt;
+            best_x = x;
+        }
+    }
+    if (!found) return 1;
+    *mask_out = best_x;
+    *weight_out = best_w;
+    return 0;
+}
+
+/* Algorithm 1, with the exact clause of each witness.
+ *   mode 0 (repair, inspection off): existing barriers are forced on.
+ *   mode 1 (remove, inspection on): no slot is forced; the existing mask is
+ *     checked first as a probe whose witnesses seed the clause set, and is not
+ *     itself returned.
+ *   grid_enabled == 0 forbids every grid slot.
+ * Loop: propose the minimum hitting set of the clauses so far; stop when a
+ * proposed mask has no witness (repaired) or the clauses are unsatisfiable
+ * (unrepairable); each race witness adds its clause, each divergent slot a
+ * negative unit clause.  More than max_iters checks ends with status 2. */
+void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iters, orc_result *r) {
+    memset(r, 0, sizeof(*r));
+    const uint32_t n = p->n_stmts - 1;
+    uint32_t grid = 0;
+    for (uint32_t k = 0; k < n; k++)
+        if (p->slot_level[k] == 1) grid |= 1u << k;
+    const uint32_t forced = mode == 0 ? p->existing_mask : 0;
+    uint32_t forbidden = grid_enabled ? 0 : grid;
+    uint32_t clauses[ORC_MAX_CLAUSES + 2 * ORC_MAX_STMTS * ORC_MAX_STMTS];
+    uint32_t n_cl = 0;
+    uint32_t m = 0;
+    int probe = 0;
+    int status = 0;
+    if (mode == 1) {
+        m = p->existing_mask;
+        probe = 1;
+    } else {
+        uint64_t wt;
+        if (orc_solve(n, p->slot_weight, NULL, 0, NULL, 0, forced, forbidden, &m, &wt)) {
+            status = 1;
+            goto done;
+        }
+    }
+    for (;;) {
+        if (r->iters == max_iters) {
+            status = 2;
+            break;
+        }
+        orc_witness w;
+        orc_check(p, m, &w);
+        if (r->iters < ORC_MAX_TRAJ) r->traj[r->iters] = m;
+        r->iters++;
+        r->access_pairs += w.access_pairs;
+        int any = w.diverge != 0;
+        for (uint32_t i = 0; i < p->n_stmts; i++)
+            if (w.intra[i] | w.inter[i]) any = 1;
+        if (!any && !probe) {
+            status = 0;
+            r->mask = m;
+            break;
+        }
+        probe = 0;
+        n_cl = orc_clauses(p, &w, clauses, n_cl);
+        forbidden |= w.diverge;
+        uint64_t wt;
+        if (orc_solve(n, p->slot_weight, clauses, n_cl, NULL, 0, forced, forbidden, &m, &wt)) {
+            status = 1;
+            break;
+        }
+    }
+done:
+    r->status = status;
+    if (status != 0) r->mask = 0;
+    for (uint32_t k = 0; k < n; k++)
+        if ((r->mask >> k) & 1u) r->weight += p->slot_weight[k];
+    r->added = r->mask & ~p->existing_mask;
+    r->removed = status == 0 ? (p->existing_mask & ~r->mask) : 0;
+    r->n_clauses = n_cl;
+    memcpy(r->clauses, clauses, n_cl * sizeof(uint32_t));
+    r->forbidden = forbidden;
+}
+
+/* Many independent programs on worker threads (programs are independent). */
+typedef struct {
+    const orc_prog *progs;
+    const int32_t *modes;
+    int grid_enabled;
+    uint32_t max_iters;
+    orc_result *out;
+    uint32_t n, stride, first;
+} orc_job;
+
+static void *orc_worker(void *arg) {
+    orc_job *j = (orc_job *)arg;
+    for (uint32_t i = j->first; i < j->n; i += j->stride)
+        orc_repair(&j->progs[i], j->modes[i], j->grid_enabled, j->max_iters, &j->out[i]);
+    return NULL;
+}
+
+void orc_repair_batch(const orc_prog *progs, const int32_t *modes, uint32_t n, int grid_enabled,
+                      uint32_t max_iters, orc_result *out, uint32_t n_threads) {
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    pthread_t th[256];
+    orc_job jobs[256];
+    for (uint32_t t = 0; t < n_threads; t++) {
+        jobs[t] = (orc_job){progs, modes, grid_enabled, max_iters, out, n, n_threads, t};
+        pthread_create(&th[t], NULL, orc_worker, &jobs[t]);
+    }
+    for (uint32_t t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+}
+
+uint32_t orc_sizeof_result(void) { return (uint32_t)sizeof(orc_result); }
+uint32_t orc_sizeof_prog(void) { return (uint32_t)sizeof(orc_prog); }
+uint32_t orc_sizeof_witness(void) { return (uint32_t)sizeof(orc_witness); }

@@ -1,0 +1,78 @@
+"""The oracle's pins must reject plausible mistakes.  Each case plants one
+mistake in a temporary copy of oracle.c (a dropped term, a wrong bound, a
+reversed comparison ...), builds it, routes the oracle through it and checks
+that some pin of tests/test_oracle_pins.py fails.  CPU only."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+MUTANTS = [
+    ("separation_off_by_one", "for (uint32_t k = i; k < j; k++)\n        if ((mask >> k) & 1u)",
+     "for (uint32_t k = i; k <= j; k++)\n        if ((mask >> k) & 1u)"),
+    ("block_barrier_orders_blocks", "if (!grid_only || p->slot_level[k] == 1) return 1;", "return 1;"),
+    ("shared_arrays_cross_blocks", "const int open_cross = !shared && ", "const int open_cross = "),
+    ("same_thread_races", "if (same && t1 == t2) continue;", ""),
+    ("clause_range_inclusive", "for (uint32_t k = i; k < j; k++) m |= 1u << k;",
+     "for (uint32_t k = i; k <= j; k++) m |= 1u << k;"),
+    ("inter_clause_not_grid_only", "clauses[n++] = orc_slot_range(i, j) & grid;",
+     "clauses[n++] = orc_slot_range(i, j);"),
+    ("tie_break_reversed", "(wt == best_w && x < best_x)", "(wt == best_w && x > best_x)"),
+    ("forbidden_ignored", "if (x & forbidden) continue;", ""),
+    ("negative_clause_wrong", "if ((x & neg[c]) == neg[c]) ok = 0;", "if ((x & neg[c]) != 0) ok = 0;"),
+    ("divergence_ignores_mask", "if (!((mask >> k) & 1u) || p->slot_guard_k[k] == 0) continue;",
+     "if (p->slot_guard_k[k] == 0) continue;"),
+    ("probe_returned", "if (!any && !probe) {", "if (!any) {"),
+    ("existing_not_forced", "const uint32_t forced = mode == 0 ? p->existing_mask : 0;",
+     "const uint32_t forced = 0;"),
+    ("divergence_not_forbidden", "forbidden |= w.diverge;", ""),
+    ("perm_offset_dropped", "((uint64_t)tid + (uint64_t)p->c[s] * blk + p->b[s]) % M;",
+     "((uint64_t)tid + (uint64_t)p->c[s] * blk) % M;"),
+    ("block_term_dropped", "(((uint64_t)p->a[s] * tid + (uint64_t)p->c[s] * blk + p->b[s]) % M)",
+     "(((uint64_t)p->a[s] * tid + p->b[s]) % M)"),
+    ("read_read_pairs", "if (p->op[i] != 1 && p->op[j] != 1) continue;", ""),
+    ("guard_negated", "return k == 0 || tid % k == r;", "return k == 0 || tid % k != r;"),
+    ("weight_of_all_slots", "if ((x >> k) & 1u) wt += w[k];", "wt += w[k];"),
+    ("pairs_double_counted",
+     "if (i == j && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;", ""),
+]
+
+
+def _all_pins():
+    for case in pins.GOLD["cases"]:
+        yield lambda c=case: pins.test_listing_checks(c)
+        yield lambda c=case: pins.test_listing_repairs(c)
+    for case in pins.GOLD["solver_cases"]:
+        yield lambda c=case: pins.test_solver_paper_example(c)
+    for s in range(16):
+        yield lambda s=s: pins.test_check_matches_flag_reset_detector(s)
+        yield lambda s=s: pins.test_check_matches_affine_closed_form(s)
+        yield lambda s=s: pins.test_access_pairs_closed_form(s)
+        yield lambda s=s: pins.test_solve_matches_interval_dp(s)
+        yield lambda s=s: pins.test_solve_matches_milp(s)
+        yield lambda s=s: pins.test_check_antitone_in_mask(s)
+        yield lambda s=s: pins.test_clause_is_exact_filter(s)
+        yield lambda s=s: pins.test_repair_path_independence(s)
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_mutant(name, old, new, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    assert src.count(old) == 1, "mutation site must be unique"
+    mutated = tmp_path / "oracle_mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o",
+                           str(lib), str(mutated)])
+    killed = False
+    with oracle.using_library(str(lib)):
+        for pin in _all_pins():
+            try:
+                pin()
+            except AssertionError:
+                killed = True
+                break
+    assert killed, f"no pin rejects the planted mistake '{name}'"
