@@ -1,0 +1,288 @@
+"""Benchmark: repairs/s of the batched, device-resident repair loop.
+
+One step = the whole hot path over one batch of synthetic programs already
+resident in device memory: address-trace expansion, then the persistent
+repair launch (check -> clauses -> exact hitting set, to the fixed point for
+every program).  Default workload: 1,024 programs, 4 blocks x 256 threads,
+24 statements, 23 block slots, 1,024-word shared array.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank repairs its own batch (programs offset by rank:
+weak scaling, no collective on the data path); rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle (the slow plain-C definition) on a
+bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2011_08373_gb300 import synth  # noqa: E402
+
+WORKLOAD = "batch1024_4x256_s24"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._thr.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    wl = synth.WORKLOADS[args.workload]
+    sample_n = args.ref_sample
+    progs = synth.generate(args.workload, sample_n)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = oracle.repair_batch(progs, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = sample_n * len(times) / total
+    checks = sum(r["iters"] for r in res)
+    line = {
+        "impl": "reference", "metric": "repairs/s", "value": value, "unit": "repairs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "programs_per_step": sample_n,
+                   "blocks": wl.blocks, "threads": wl.threads, "stmts": wl.n_stmts},
+        "cpu_baseline": {"value": value, "unit": "repairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample_n} programs of {args.workload}, all-thread-pair "
+                                   f"enumeration + brute-force hitting set, {cores} threads"},
+        "e2e": {"value": value, "unit": "repairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "checks_per_step": checks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_leg(workload, n_sample):
+    import oracle
+
+    cores = os.cpu_count() or 1
+    progs = synth.generate(workload, n_sample)
+    oracle.repair_batch(progs[:2], n_threads=cores)  # build + warm
+    t0 = time.perf_counter()
+    oracle.repair_batch(progs, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": "repairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sample} programs of {workload}, all-thread-pair enumeration + "
+                      f"brute-force hitting set, {cores} threads, {dt:.1f} s"}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2011_08373_gb300 import binding
+    from paper_2011_08373_gb300.build import build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    build()
+    wl = synth.WORKLOADS[args.workload]
+    n = args.programs or wl.n_programs
+    progs = synth.generate(args.workload, n, start=rank * n)
+    batch = binding.DeviceBatch(progs)
+    stream = torch.cuda.current_stream()
+    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        batch.run()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            l2_flush.zero_()  # inputs fit in L2: flush it between steps (outside the events)
+            e0, e1, e2 = ev[i]
+            e0.record(stream)
+            batch.expand()
+            e1.record(stream)
+            batch.repair_expanded()
+            e2.record(stream)
+        barrier()
+        wall = time.perf_counter() - wall0
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    repair_ms = [b.elapsed_time(c) for a, b, c in ev]
+    expand_ms = [a.elapsed_time(b) for a, b, c in ev]
+    t_step = sum(step_ms) / len(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    res = batch.results_raw()
+    checks = int(res["iters"].sum())
+    pairs = int(res["access_pairs"].sum())
+    status = np.bincount(res["status"].astype(np.int64), minlength=3)[:3].tolist()
+    lat = (res["t_end_ns"].astype(np.int64) - int(res["t_start_ns"].min())) / 1e3
+    value = n * world / t_step
+
+    # algorithmic bytes of the repair kernel: each check reads the program's
+    # trace once (S x B x T u16 addresses); the arena and results once per launch
+    trace_bytes = sum(int(p.n_stmts) * p.blocks * p.threads * 2 * int(r["iters"]) for p, r in zip(progs, res))
+    launch_bytes = trace_bytes + batch.arena_bytes + n * binding.RESULT_DTYPE.itemsize
+    t_rep = statistics.mean(repair_ms) / 1000.0
+    peak, peak_kind = _peaks()
+    achieved = launch_bytes / t_rep / 1e9
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        binding.repair_batch_raw(progs)  # warm the host-pointer path
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            binding.repair_batch_raw(progs)
+        e2e_t = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": n / e2e_t, "unit": "repairs/s", "h2d_bytes_per_step": int(batch.arena_bytes),
+               "d2h_bytes_per_step": int(n * binding.RESULT_DTYPE.itemsize),
+               "note": "gr_repair_batch with host program structs: validate + pack + H2D + kernels + D2H"}
+    plain = None
+    if rank == 0 and args.plain_programs > 0:
+        sub = progs[:args.plain_programs]
+        binding.repair_plain(sub[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in sub:
+            binding.repair_plain(p)
+        plain = len(sub) / (time.perf_counter() - t0)
+    cpu = None
+    if rank == 0 and args.cpu_sample > 0:
+        cpu = cpu_baseline_leg(args.workload, args.cpu_sample)
+    if rank == 0:
+        line = {
+            "metric": "repairs/s", "value": value, "unit": "repairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1000,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "programs": n, "blocks": wl.blocks, "threads": wl.threads,
+                       "stmts": wl.n_stmts, "m_words": wl.m_words, "seed": wl.seed,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_repair",
+                         "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "checks_per_s": checks * world / t_step,
+            "access_pair_checks_per_s": pairs * world / t_step,
+            "plain_repairs_per_s": plain,
+            "expand_ms": statistics.mean(expand_ms), "repair_kernel_ms": statistics.mean(repair_ms),
+            "latency_in_batch_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "status_counts": {"repaired": status[0], "unrepairable": status[1], "iter_cap": status[2]},
+            "checks_per_repair": checks / n, "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--programs", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--plain-programs", type=int, default=64)
+    ap.add_argument("--cpu-sample", type=int, default=32)
+    ap.add_argument("--ref-sample", type=int, default=32)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * gpurepair.h — C ABI of the GB300 engine for GPURepair's repair loop
+ * (Joshi and Muduganti, "GPURepair: Automated Repair of GPU Kernels",
+ * arXiv 2011.08373).
+ *
+ * The engine restates the paper's instrumented kernel (Section 2.2) over a
+ * concrete launch and runs Algorithm 1 (Section 2.4) on the GPU:
+ *   check  — every race witness (i, j) and every divergent enabled barrier of
+ *            a program under a barrier mask (the paper's Verify);
+ *   clause — each race witness becomes "some slot that can order it is on",
+ *            each divergent slot a negative unit clause (GenerateClause);
+ *   solve  — the exact minimum-weight hitting set of the clauses, ties broken
+ *            by the lowest mask (Solve, in its weighted MaxSAT form);
+ *   repair — the loop of the three to a fixed point.
+ *
+ * Model.  A program has S (1..25) straight-line statements.  Statement s is a
+ * read (GR_R) or write (GR_W) of one 32-bit word of the SHARED array (one
+ * private copy per block, m_shared words) or of the GLOBAL array (one copy
+ * for the grid, m_global words) at an address given by a per-thread map:
+ *   GR_AFFINE, GR_STRIDED: (a*tid + c*blk + b) mod M
+ *   GR_PERM:               perm[perm_off + ((tid + c*blk + b) mod M)]
+ * (64-bit intermediates; tid = threadIdx.x, blk = blockIdx.x).  Statement s
+ * runs for thread tid iff guard_k == 0 or tid % guard_k == guard_r.
+ * Slot k (0..S-2) is a candidate barrier between statements k and k+1 with a
+ * level (GR_BLOCK orders threads of one block, GR_GRID orders all threads;
+ * Section 2.2), a guard (same meaning; the barrier is executed by the threads
+ * whose guard holds) and a weight (Section 2.4: (gw*gb) + lw^ld).  A mask has
+ * bit k set when slot k is enabled.
+ *
+ * Ownership and errors (every entry point).  The caller owns every input and
+ * output buffer.  Host-pointer entry points copy their inputs during the call
+ * and return after the result is in the caller's memory.  Inputs are
+ * validated before any device work; a rejected call returns GR_EINVAL and
+ * leaves the outputs untouched (gr_last_error() says why).  CUDA failures
+ * return GR_ECUDA; a failed allocation returns GR_ENOMEM.  The library keeps
+ * one device workspace per device, grown on demand and guarded by a mutex:
+ * host-pointer calls from several threads are serialised.
+ */
+#ifndef GPUREPAIR_H
+#define GPUREPAIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GR_MAX_STMTS 25
+#define GR_MAX_SLOTS 24
+#define GR_MAX_THREADS 1024
+#define GR_MAX_BLOCKS 65533
+#define GR_MAX_WORDS 65536
+#define GR_MAX_WEIGHT (1u << 24)
+#define GR_MAX_CLAUSES 656
+#define GR_MAX_ITERS 64
+
+typedef int32_t gr_status;
+enum {
+    GR_OK = 0,
+    GR_UNSAT = 1,      /* gr_solve only: no mask satisfies the clauses */
+    GR_EINVAL = -1,    /* invalid argument; outputs untouched */
+    GR_ENOMEM = -2,    /* device or host allocation failed */
+    GR_ECUDA = -4,     /* a CUDA call failed (gr_last_error has the text) */
+    GR_ECAPACITY = -6  /* a buffer the caller passed is too small */
+};
+
+enum { GR_R = 0, GR_W = 1 };
+enum { GR_SHARED = 0, GR_GLOBAL = 1 };
+enum { GR_AFFINE = 0, GR_STRIDED = 1, GR_PERM = 2 };
+enum { GR_BLOCK = 0, GR_GRID = 1 };
+
+/* Repair modes (Section 5, Table 3 configurations).
+ * GR_MODE_REPAIR  (--disable-inspect): existing barriers stay on; only new
+ *                 ones are added.
+ * GR_MODE_REMOVE  (default inspection): existing barriers are variables too;
+ *                 the existing mask is checked first as a probe and the loop
+ *                 may drop barriers that no witness needs. */
+enum { GR_MODE_REPAIR = 0, GR_MODE_REMOVE = 1 };
+
+/* Per-program outcome (Algorithm 1's exits). */
+enum { GR_REPAIRED = 0, GR_UNREPAIRABLE = 1, GR_ITER_CAP = 2 };
+
+typedef struct {
+    uint8_t op;        /* GR_R / GR_W */
+    uint8_t space;     /* GR_SHARED / GR_GLOBAL */
+    uint8_t kind;      /* GR_AFFINE / GR_STRIDED / GR_PERM */
+    uint8_t _pad;
+    uint32_t a, b, c;  /* map coefficients (a unused for GR_PERM) */
+    uint32_t perm_off; /* GR_PERM: offset of this statement's table in perm */
+    uint16_t guard_k;  /* 0: unguarded; else tid % guard_k == guard_r */
+    uint16_t guard_r;
+} gr_stmt;
+
+typedef struct {
+    uint32_t n_stmts;             /* 1..GR_MAX_STMTS */
+    const gr_stmt *stmts;         /* n_stmts entries */
+    const uint8_t *slot_level;    /* n_stmts-1 entries: GR_BLOCK / GR_GRID */
+    const uint16_t *slot_guard;   /* 2*(n_stmts-1) entries: (k, r) per slot; NULL = unguarded */
+    const uint32_t *slot_weight;  /* n_stmts-1 entries in 1..GR_MAX_WEIGHT; NULL = paper
+                                     defaults gw=12, ld=0: block 1, grid 13 */
+    uint32_t m_shared, m_global;  /* words (1..GR_MAX_WORDS) of each array a statement uses */
+    const uint32_t *perm;         /* concatenated permutation tables (may be NULL if unused) */
+    uint32_t perm_len;
+    uint32_t existing_mask;       /* barriers the programmer wrote (E) */
+} gr_program;
+
+typedef struct {
+    uint32_t blocks;   /* 1..GR_MAX_BLOCKS */
+    uint32_t threads;  /* 1..GR_MAX_THREADS */
+} gr_launch;
+
+typedef struct {
+    uint32_t race_intra[32]; /* row i, bit j (j >= i): same-block race witness (i, j) */
+    uint32_t race_inter[32]; /* row i, bit j (j >= i): cross-block race witness (i, j) */
+    uint32_t diverge;        /* bit k: enabled slot k is divergent */
+    uint32_t n_stmts;
+    uint64_t access_pairs;   /* thread pairs a pairwise checker would examine under the
+                                mask: statement pairs (i <= j) of one space with a write;
+                                ordered pairs for i < j, unordered for i == j; same-block
+                                pairs unless an enabled slot lies in [i, j-1], cross-block
+                                pairs (global only) unless an enabled grid slot does */
+} gr_witnesses;
+
+typedef struct {
+    uint8_t grid_enabled; /* 0 = --disable-grid: every grid slot is forbidden */
+    uint8_t _pad[3];
+    uint32_t max_iters;   /* checks allowed per program, 1..GR_MAX_ITERS; 0 = 64 */
+} gr_options;
+
+typedef struct {
+    int32_t status;               /* GR_REPAIRED / GR_UNREPAIRABLE / GR_ITER_CAP */
+    uint32_t mask;                /* final mask (0 unless repaired) */
+    uint32_t weight;              /* sum of the weights of mask's slots */
+    uint32_t added, removed;      /* mask & ~E, E & ~mask (removed is 0 unless repaired) */
+    uint32_t iters;               /* checks performed (the paper's verifier calls) */
+    uint32_t traj[GR_MAX_ITERS];  /* the masks checked, in order */
+    uint32_t n_clauses;
+    uint32_t clauses[GR_MAX_CLAUSES]; /* final positive clauses, sorted, unique */
+    uint32_t forbidden;           /* final negative unit clauses (divergent or disabled slots) */
+    uint32_t _pad;
+    uint64_t access_pairs;        /* summed over this program's checks */
+    uint64_t t_start_ns, t_end_ns;/* device clock when the program's loop began / ended */
+} gr_repair_result;
+
+/* ---------------------------------------------------------------------- */
+/* Library                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Version string of the engine. */
+const char *gr_version(void);
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *gr_last_error(void);
+/* Validate one program and launch without touching the device. */
+gr_status gr_validate(const gr_program *prog, gr_launch launch);
+
+/* ---------------------------------------------------------------------- */
+/* Host-pointer entry points (synchronous; library-owned device workspace) */
+/* ---------------------------------------------------------------------- */
+
+/* Verify(P_sol) of Algorithm 1 (Section 2.4) as an exact concrete check:
+ * every race witness and divergent slot of prog under mask.  mask must only
+ * use bits < n_stmts-1. */
+gr_status gr_check(const gr_program *prog, gr_launch launch, uint32_t mask, gr_witnesses *out);
+
+/* Algorithm 1 (Section 2.4) on one program, in one persistent launch.
+ * mode: GR_MODE_REPAIR / GR_MODE_REMOVE.  opts may be NULL (grid enabled,
+ * 64 iterations). */
+gr_status gr_repair(const gr_program *prog, gr_launch launch, int32_t mode,
+                    const gr_options *opts, gr_repair_result *out);
+
+/* The same loop driven from the host with one check launch and one solve
+ * launch per iteration (the plain comparison path). Same result as gr_repair. */
+gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode,
+                          const gr_options *opts, gr_repair_result *out);
+
+/* Minimum-weight hitting set (Section 2.3 definitions, Section 2.4 weighted
+ * MaxSAT form) on the GPU: the least (weight, mask) over masks x of n_vars
+ * (1..24) bits with forced <= x, x & forbidden == 0, x & pos[i] != 0 for
+ * every positive clause and (x & neg[i]) != neg[i] for every negative clause.
+ * w: n_vars weights in 1..GR_MAX_WEIGHT.  n_pos + n_neg <= GR_MAX_CLAUSES.
+ * Returns GR_OK (outputs set) or GR_UNSAT (outputs set to 0). */
+gr_status gr_solve(uint32_t n_vars, const uint32_t *w, const uint32_t *pos, uint32_t n_pos,
+                   const uint32_t *neg, uint32_t n_neg, uint32_t forced, uint32_t forbidden,
+                   uint32_t *mask_out, uint32_t *weight_out);
+
+/* Many independent programs (uneven sizes) in one persistent launch on
+ * `stream` (a cudaStream_t, NULL = legacy default stream); returns once out
+ * holds every result.  modes: one GR_MODE_* per program. */
+gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches,
+                          const int32_t *modes, uint32_t n, const gr_options *opts,
+                          gr_repair_result *out, void *stream);
+
+/* One check per (program, mask) in one persistent launch. */
+gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches,
+                         const uint32_t *masks, uint32_t n, gr_witnesses *out, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Device-resident entry points (asynchronous on `stream`, no allocation)  */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of the packed program arena and of the device scratch (address
+ * traces and tile masks) that n programs need. */
+gr_status gr_pack_size(const gr_program *progs, const gr_launch *launches, uint32_t n,
+                       uint64_t *arena_bytes, uint64_t *scratch_bytes);
+
+/* Validate and pack n programs into a host buffer of arena_bytes (16-byte
+ * aligned).  The caller copies it to device memory; it stays valid for any
+ * number of launches. */
+gr_status gr_pack(const gr_program *progs, const gr_launch *launches, const int32_t *modes,
+                  uint32_t n, void *host_arena, uint64_t arena_bytes);
+
+/* Algorithm 1 on every program of a packed arena already in device memory:
+ * expands the address traces into d_scratch, then runs the persistent repair
+ * launch.  d_out: n results in device memory.  Enqueued on stream; nothing is
+ * allocated and nothing synchronises.  d_arena and d_scratch must be 256-byte
+ * aligned; scratch_bytes must be at least gr_pack_size's figure. */
+gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *opts,
+                           void *d_scratch, uint64_t scratch_bytes, gr_repair_result *d_out,
+                           void *stream);
+
+/* The two halves of gr_repair_packed, for callers that time or overlap them:
+ * gr_expand_packed writes the address traces and chunk masks of every
+ * program into d_scratch; gr_repair_expanded runs the persistent repair
+ * launch on traces a previous gr_expand_packed of the same arena wrote. */
+gr_status gr_expand_packed(const void *d_arena, void *d_scratch, uint64_t scratch_bytes, void *stream);
+gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                             uint64_t scratch_bytes, gr_repair_result *d_out, void *stream);
+
+/* One check per program of a device-resident packed arena under d_masks[p]. */
+gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_masks,
+                          void *d_scratch, uint64_t scratch_bytes, gr_witnesses *d_out,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPUREPAIR_H */

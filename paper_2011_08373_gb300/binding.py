@@ -1,0 +1,370 @@
+"""ctypes binding of libgpurepair.so (include/gpurepair.h).
+
+Argument marshalling only: every step of the repair path runs in the
+library's CUDA kernels.  The library must have been built (``build()`` in
+``paper_2011_08373_gb300.build``); loading raises if it is missing.  Names
+follow the C entry points without the ``gr_`` prefix.  Device memory and
+streams for the device-resident calls come from PyTorch.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgpurepair.so")
+
+MAX_STMTS, MAX_SLOTS, MAX_ITERS, MAX_CLAUSES = 25, 24, 64, 656
+OK, UNSAT, EINVAL, ENOMEM, ECUDA, ECAPACITY = 0, 1, -1, -2, -4, -6
+REPAIRED, UNREPAIRABLE, ITER_CAP = 0, 1, 2
+
+
+class GrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gpurepair error {code}: {msg}")
+        self.code = code
+
+
+class gr_stmt(C.Structure):
+    _fields_ = [("op", C.c_uint8), ("space", C.c_uint8), ("kind", C.c_uint8), ("_pad", C.c_uint8),
+                ("a", C.c_uint32), ("b", C.c_uint32), ("c", C.c_uint32), ("perm_off", C.c_uint32),
+                ("guard_k", C.c_uint16), ("guard_r", C.c_uint16)]
+
+
+class gr_program(C.Structure):
+    _fields_ = [("n_stmts", C.c_uint32), ("stmts", C.POINTER(gr_stmt)),
+                ("slot_level", C.POINTER(C.c_uint8)), ("slot_guard", C.POINTER(C.c_uint16)),
+                ("slot_weight", C.POINTER(C.c_uint32)), ("m_shared", C.c_uint32),
+                ("m_global", C.c_uint32), ("perm", C.POINTER(C.c_uint32)), ("perm_len", C.c_uint32),
+                ("existing_mask", C.c_uint32)]
+
+
+class gr_launch(C.Structure):
+    _fields_ = [("blocks", C.c_uint32), ("threads", C.c_uint32)]
+
+
+class gr_witnesses(C.Structure):
+    _fields_ = [("race_intra", C.c_uint32 * 32), ("race_inter", C.c_uint32 * 32),
+                ("diverge", C.c_uint32), ("n_stmts", C.c_uint32), ("access_pairs", C.c_uint64)]
+
+
+class gr_options(C.Structure):
+    _fields_ = [("grid_enabled", C.c_uint8), ("_pad", C.c_uint8 * 3), ("max_iters", C.c_uint32)]
+
+
+class gr_repair_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("mask", C.c_uint32), ("weight", C.c_uint32),
+                ("added", C.c_uint32), ("removed", C.c_uint32), ("iters", C.c_uint32),
+                ("traj", C.c_uint32 * MAX_ITERS), ("n_clauses", C.c_uint32),
+                ("clauses", C.c_uint32 * MAX_CLAUSES), ("forbidden", C.c_uint32), ("_pad", C.c_uint32),
+                ("access_pairs", C.c_uint64), ("t_start_ns", C.c_uint64), ("t_end_ns", C.c_uint64)]
+
+
+RESULT_DTYPE = np.dtype(gr_repair_result)
+WITNESS_DTYPE = np.dtype(gr_witnesses)
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair", "gr_repair_plain",
+           "gr_solve", "gr_repair_batch", "gr_check_batch", "gr_pack_size", "gr_pack",
+           "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded"]
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2011_08373_gb300.build` (nvcc, sm_103a)")
+            L = C.CDLL(LIB_PATH)
+            P = C.POINTER
+            L.gr_version.restype = C.c_char_p
+            L.gr_last_error.restype = C.c_char_p
+            L.gr_validate.argtypes = [P(gr_program), gr_launch]
+            L.gr_check.argtypes = [P(gr_program), gr_launch, C.c_uint32, P(gr_witnesses)]
+            L.gr_repair.argtypes = [P(gr_program), gr_launch, C.c_int32, P(gr_options),
+                                    P(gr_repair_result)]
+            L.gr_repair_plain.argtypes = L.gr_repair.argtypes
+            L.gr_solve.argtypes = [C.c_uint32, P(C.c_uint32), P(C.c_uint32), C.c_uint32, P(C.c_uint32),
+                                   C.c_uint32, C.c_uint32, C.c_uint32, P(C.c_uint32), P(C.c_uint32)]
+            L.gr_repair_batch.argtypes = [P(gr_program), P(gr_launch), P(C.c_int32), C.c_uint32,
+                                          P(gr_options), C.c_void_p, C.c_void_p]
+            L.gr_check_batch.argtypes = [P(gr_program), P(gr_launch), P(C.c_uint32), C.c_uint32,
+                                         C.c_void_p, C.c_void_p]
+            L.gr_pack_size.argtypes = [P(gr_program), P(gr_launch), C.c_uint32, P(C.c_uint64),
+                                       P(C.c_uint64)]
+            L.gr_pack.argtypes = [P(gr_program), P(gr_launch), P(C.c_int32), C.c_uint32, C.c_void_p,
+                                  C.c_uint64]
+            L.gr_repair_packed.argtypes = [C.c_void_p, C.c_uint32, P(gr_options), C.c_void_p,
+                                           C.c_uint64, C.c_void_p, C.c_void_p]
+            L.gr_expand_packed.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]
+            L.gr_repair_expanded.argtypes = L.gr_repair_packed.argtypes
+            L.gr_check_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint64,
+                                          C.c_void_p, C.c_void_p]
+            for name in EXPORTS[2:]:
+                getattr(L, name).restype = C.c_int32
+            _lib = L
+    return _lib
+
+
+def version() -> str:
+    return lib().gr_version().decode()
+
+
+def last_error() -> str:
+    return lib().gr_last_error().decode()
+
+
+def _check(code: int, allowed=(OK,)) -> int:
+    if code not in allowed:
+        raise GrError(code, last_error())
+    return code
+
+
+# ---------------------------------------------------------------------------
+# Program marshalling
+# ---------------------------------------------------------------------------
+
+class CProgram:
+    """A Program marshalled into C structs (keeps its buffers alive)."""
+
+    def __init__(self, p):
+        S = int(p.op.shape[0])
+        n = S - 1
+        st = (gr_stmt * S)()
+        for s in range(S):
+            st[s].op, st[s].space, st[s].kind = int(p.op[s]), int(p.space[s]), int(p.kind[s])
+            st[s].a, st[s].b, st[s].c = int(p.a[s]), int(p.b[s]), int(p.c[s])
+            st[s].perm_off = int(p.perm_off[s])
+            st[s].guard_k, st[s].guard_r = int(p.guard_k[s]), int(p.guard_r[s])
+        self.stmts = st
+        self.level = np.ascontiguousarray(p.slot_level, dtype=np.uint8)
+        sg = np.zeros(2 * max(n, 1), np.uint16)
+        sg[0:2 * n:2] = p.slot_guard_k
+        sg[1:2 * n:2] = p.slot_guard_r
+        self.guard = sg
+        self.weight = np.ascontiguousarray(p.slot_weight, dtype=np.uint32)
+        self.perm = np.ascontiguousarray(p.perm, dtype=np.uint32) if len(p.perm) else None
+        self.s = gr_program()
+        self.s.n_stmts = S
+        self.s.stmts = C.cast(st, C.POINTER(gr_stmt))
+        self.s.slot_level = self.level.ctypes.data_as(C.POINTER(C.c_uint8)) if n else None
+        self.s.slot_guard = self.guard.ctypes.data_as(C.POINTER(C.c_uint16))
+        self.s.slot_weight = self.weight.ctypes.data_as(C.POINTER(C.c_uint32)) if n else None
+        self.s.m_shared, self.s.m_global = int(p.m_shared), int(p.m_global)
+        if self.perm is not None:
+            self.s.perm = self.perm.ctypes.data_as(C.POINTER(C.c_uint32))
+            self.s.perm_len = len(self.perm)
+        self.s.existing_mask = int(p.existing_mask)
+        self.launch = gr_launch(int(p.blocks), int(p.threads))
+        self.mode = int(p.mode)
+
+
+def _options(grid_enabled: bool = True, max_iters: int = 64) -> gr_options:
+    o = gr_options()
+    o.grid_enabled = 1 if grid_enabled else 0
+    o.max_iters = max_iters
+    return o
+
+
+def _program_array(progs: Sequence) -> tuple:
+    cps = [CProgram(p) for p in progs]
+    arr = (gr_program * len(cps))(*[c.s for c in cps])
+    la = (gr_launch * len(cps))(*[c.launch for c in cps])
+    return cps, arr, la
+
+
+def witness_dict(w, S: int) -> dict:
+    return {"intra": [int(w["race_intra"][i]) for i in range(S)],
+            "inter": [int(w["race_inter"][i]) for i in range(S)],
+            "diverge": int(w["diverge"]), "access_pairs": int(w["access_pairs"])}
+
+
+def result_dict(r) -> dict:
+    it = int(r["iters"])
+    nc = int(r["n_clauses"])
+    return {"status": int(r["status"]), "mask": int(r["mask"]), "weight": int(r["weight"]),
+            "added": int(r["added"]), "removed": int(r["removed"]), "iters": it,
+            "traj": [int(x) for x in r["traj"][:min(it, MAX_ITERS)]],
+            "clauses": [int(x) for x in r["clauses"][:nc]], "forbidden": int(r["forbidden"]),
+            "access_pairs": int(r["access_pairs"]), "t_start_ns": int(r["t_start_ns"]),
+            "t_end_ns": int(r["t_end_ns"])}
+
+
+# ---------------------------------------------------------------------------
+# Host-pointer entry points
+# ---------------------------------------------------------------------------
+
+def validate(p) -> None:
+    c = CProgram(p)
+    _check(lib().gr_validate(C.byref(c.s), c.launch))
+
+
+def check(p, mask: int) -> dict:
+    c = CProgram(p)
+    w = gr_witnesses()
+    _check(lib().gr_check(C.byref(c.s), c.launch, mask, C.byref(w)))
+    arr = np.frombuffer(bytes(w), dtype=WITNESS_DTYPE)[0]
+    return witness_dict(arr, p.n_stmts)
+
+
+def repair(p, mode: Optional[int] = None, grid_enabled: bool = True, max_iters: int = 64) -> dict:
+    c = CProgram(p)
+    r = gr_repair_result()
+    o = _options(grid_enabled, max_iters)
+    _check(lib().gr_repair(C.byref(c.s), c.launch, c.mode if mode is None else mode, C.byref(o),
+                           C.byref(r)))
+    return result_dict(np.frombuffer(bytes(r), dtype=RESULT_DTYPE)[0])
+
+
+def repair_plain(p, mode: Optional[int] = None, grid_enabled: bool = True,
+                 max_iters: int = 64) -> dict:
+    c = CProgram(p)
+    r = gr_repair_result()
+    o = _options(grid_enabled, max_iters)
+    _check(lib().gr_repair_plain(C.byref(c.s), c.launch, c.mode if mode is None else mode,
+                                 C.byref(o), C.byref(r)))
+    return result_dict(np.frombuffer(bytes(r), dtype=RESULT_DTYPE)[0])
+
+
+def solve(n_vars: int, weights, pos, neg=(), forced: int = 0, forbidden: int = 0):
+    """Lowest (mask, weight) hitting set, or None when unsatisfiable."""
+    w = (C.c_uint32 * max(1, n_vars))(*[int(x) for x in weights])
+    pa = (C.c_uint32 * max(1, len(pos)))(*[int(x) for x in pos])
+    na = (C.c_uint32 * max(1, len(neg)))(*[int(x) for x in neg])
+    m, wt = C.c_uint32(), C.c_uint32()
+    rc = _check(lib().gr_solve(n_vars, w, pa, len(pos), na, len(neg), forced, forbidden,
+                               C.byref(m), C.byref(wt)), allowed=(OK, UNSAT))
+    return None if rc == UNSAT else (m.value, wt.value)
+
+
+def repair_batch_raw(progs: Sequence, grid_enabled: bool = True, max_iters: int = 64,
+                     stream: int = 0) -> np.ndarray:
+    cps, arr, la = _program_array(progs)
+    modes = (C.c_int32 * len(cps))(*[c.mode for c in cps])
+    out = np.zeros(len(cps), dtype=RESULT_DTYPE)
+    o = _options(grid_enabled, max_iters)
+    _check(lib().gr_repair_batch(arr, la, modes, len(cps), C.byref(o), out.ctypes.data,
+                                 C.c_void_p(stream)))
+    return out
+
+
+def repair_batch(progs: Sequence, grid_enabled: bool = True, max_iters: int = 64,
+                 stream: int = 0) -> List[dict]:
+    return [result_dict(r) for r in repair_batch_raw(progs, grid_enabled, max_iters, stream)]
+
+
+def check_batch(progs: Sequence, masks: Sequence[int], stream: int = 0) -> List[dict]:
+    cps, arr, la = _program_array(progs)
+    m = (C.c_uint32 * len(cps))(*[int(x) for x in masks])
+    out = np.zeros(len(cps), dtype=WITNESS_DTYPE)
+    _check(lib().gr_check_batch(arr, la, m, len(cps), out.ctypes.data, C.c_void_p(stream)))
+    return [witness_dict(out[i], progs[i].n_stmts) for i in range(len(progs))]
+
+
+# ---------------------------------------------------------------------------
+# Device-resident entry points (torch supplies device memory and streams)
+# ---------------------------------------------------------------------------
+
+def pack(progs: Sequence) -> tuple:
+    """(host arena as a 256-byte-aligned uint8 array, scratch bytes needed)."""
+    cps, arr, la = _program_array(progs)
+    ab, sb = C.c_uint64(), C.c_uint64()
+    _check(lib().gr_pack_size(arr, la, len(cps), C.byref(ab), C.byref(sb)))
+    raw = np.zeros(ab.value + 256, np.uint8)
+    off = (-raw.ctypes.data) % 256
+    host = raw[off:off + ab.value]
+    modes = (C.c_int32 * len(cps))(*[c.mode for c in cps])
+    _check(lib().gr_pack(arr, la, modes, len(cps), host.ctypes.data, ab.value))
+    return host, sb.value
+
+
+class DeviceBatch:
+    """A packed batch resident in device memory with its scratch and results.
+
+    ``run()`` enqueues the whole repair (trace expansion + persistent repair
+    launch) on the current torch stream; nothing is allocated per call.
+    """
+
+    def __init__(self, progs: Sequence, device: str = "cuda", grid_enabled: bool = True,
+                 max_iters: int = 64):
+        import torch
+
+        self.n = len(progs)
+        host, scratch_bytes = pack(progs)
+        self.arena_bytes = host.nbytes
+        self.scratch_bytes = scratch_bytes
+        self.arena = torch.empty(self.arena_bytes + 256, dtype=torch.uint8, device=device)
+        self.scratch = torch.empty(scratch_bytes + 256, dtype=torch.uint8, device=device)
+        self.out = torch.empty(self.n * RESULT_DTYPE.itemsize + 256, dtype=torch.uint8, device=device)
+        self.wit = None
+        self._arena_ptr = _aligned(self.arena.data_ptr())
+        self._scratch_ptr = _aligned(self.scratch.data_ptr())
+        self._out_ptr = _aligned(self.out.data_ptr())
+        a_off = self._arena_ptr - self.arena.data_ptr()
+        self.arena[a_off:a_off + self.arena_bytes].copy_(torch.from_numpy(host))
+        self.opts = _options(grid_enabled, max_iters)
+        self.host_arena = host
+
+    def run(self, stream: Optional[int] = None) -> None:
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_repair_packed(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
+                                      C.c_void_p(self._scratch_ptr), self.scratch_bytes,
+                                      C.c_void_p(self._out_ptr), C.c_void_p(st)))
+
+    def expand(self, stream: Optional[int] = None) -> None:
+        """Only the trace expansion (first half of run())."""
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_expand_packed(C.c_void_p(self._arena_ptr), C.c_void_p(self._scratch_ptr),
+                                      self.scratch_bytes, C.c_void_p(st)))
+
+    def repair_expanded(self, stream: Optional[int] = None) -> None:
+        """Only the persistent repair launch (second half of run())."""
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_repair_expanded(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
+                                        C.c_void_p(self._scratch_ptr), self.scratch_bytes,
+                                        C.c_void_p(self._out_ptr), C.c_void_p(st)))
+
+    def check(self, masks, stream: Optional[int] = None):
+        import torch
+
+        if self.wit is None:
+            self.wit = torch.empty(self.n * WITNESS_DTYPE.itemsize + 256, dtype=torch.uint8,
+                                   device=self.arena.device)
+            self.masks = torch.empty(self.n, dtype=torch.int32, device=self.arena.device)
+        self.masks.copy_(torch.as_tensor(np.asarray(masks, np.uint32).view(np.int32)))
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_check_packed(C.c_void_p(self._arena_ptr), self.n,
+                                     C.c_void_p(self.masks.data_ptr()), C.c_void_p(self._scratch_ptr),
+                                     self.scratch_bytes, C.c_void_p(_aligned(self.wit.data_ptr())),
+                                     C.c_void_p(st)))
+
+    def results_raw(self) -> np.ndarray:
+        off = self._out_ptr - self.out.data_ptr()
+        b = self.out[off:off + self.n * RESULT_DTYPE.itemsize].cpu().numpy()
+        return b.view(RESULT_DTYPE)
+
+    def results(self) -> List[dict]:
+        return [result_dict(r) for r in self.results_raw()]
+
+    def witnesses(self, progs) -> List[dict]:
+        off = _aligned(self.wit.data_ptr()) - self.wit.data_ptr()
+        b = self.wit[off:off + self.n * WITNESS_DTYPE.itemsize].cpu().numpy().view(WITNESS_DTYPE)
+        return [witness_dict(b[i], progs[i].n_stmts) for i in range(self.n)]
+
+
+def _aligned(ptr: int) -> int:
+    return (ptr + 255) // 256 * 256

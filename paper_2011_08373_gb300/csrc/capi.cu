@@ -1,0 +1,574 @@
+// capi.cu — host side of the C ABI (include/gpurepair.h): validation, packing
+// of programs into the device arena, the per-device workspace, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+
+using namespace gr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gr_status fail(gr_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+gr_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? GR_ENOMEM : GR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GR_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+uint32_t slot_weight_of(const gr_program &p, uint32_t k) {
+    if (p.slot_weight) return p.slot_weight[k];
+    return p.slot_level[k] == GR_GRID ? 13u : 1u;  // (gw*gb) + lw^0 with gw = 12
+}
+
+gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
+    if (!p) return fail(GR_EINVAL, "program %u: NULL", idx);
+    if (p->n_stmts < 1 || p->n_stmts > GR_MAX_STMTS)
+        return fail(GR_EINVAL, "program %u: n_stmts %u outside 1..%d", idx, p->n_stmts, GR_MAX_STMTS);
+    if (!p->stmts) return fail(GR_EINVAL, "program %u: stmts is NULL", idx);
+    if (l.blocks < 1 || l.blocks > GR_MAX_BLOCKS)
+        return fail(GR_EINVAL, "program %u: blocks %u outside 1..%d", idx, l.blocks, GR_MAX_BLOCKS);
+    if (l.threads < 1 || l.threads > GR_MAX_THREADS)
+        return fail(GR_EINVAL, "program %u: threads %u outside 1..%d", idx, l.threads, GR_MAX_THREADS);
+    if (p->m_shared > GR_MAX_WORDS || p->m_global > GR_MAX_WORDS)
+        return fail(GR_EINVAL, "program %u: array size above %d words", idx, GR_MAX_WORDS);
+    const uint32_t n = p->n_stmts - 1;
+    for (uint32_t s = 0; s < p->n_stmts; ++s) {
+        const gr_stmt &st = p->stmts[s];
+        if (st.op > GR_W || st.space > GR_GLOBAL || st.kind > GR_PERM)
+            return fail(GR_EINVAL, "program %u stmt %u: bad op/space/kind", idx, s);
+        const uint32_t M = st.space == GR_SHARED ? p->m_shared : p->m_global;
+        if (M == 0) return fail(GR_EINVAL, "program %u stmt %u: its array has 0 words", idx, s);
+        if (st.guard_k == 0 ? st.guard_r != 0 : st.guard_r >= st.guard_k)
+            return fail(GR_EINVAL, "program %u stmt %u: guard (%u, %u) needs r < k", idx, s, st.guard_k, st.guard_r);
+        if (st.kind == GR_PERM) {
+            if (!p->perm) return fail(GR_EINVAL, "program %u stmt %u: permutation map without perm", idx, s);
+            if ((uint64_t)st.perm_off + M > p->perm_len)
+                return fail(GR_EINVAL, "program %u stmt %u: perm_off + M beyond perm_len", idx, s);
+            std::vector<uint8_t> seen(M, 0);
+            for (uint32_t i = 0; i < M; ++i) {
+                const uint32_t v = p->perm[st.perm_off + i];
+                if (v >= M || seen[v]) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
+                seen[v] = 1;
+            }
+        }
+    }
+    if (n > 0 && !p->slot_level) return fail(GR_EINVAL, "program %u: slot_level is NULL", idx);
+    for (uint32_t k = 0; k < n; ++k) {
+        if (p->slot_level[k] > GR_GRID) return fail(GR_EINVAL, "program %u slot %u: bad level", idx, k);
+        if (p->slot_guard) {
+            const uint32_t gk = p->slot_guard[2 * k], gr_ = p->slot_guard[2 * k + 1];
+            if (gk == 0 ? gr_ != 0 : gr_ >= gk)
+                return fail(GR_EINVAL, "program %u slot %u: guard (%u, %u) needs r < k", idx, k, gk, gr_);
+        }
+        if (p->slot_weight && (p->slot_weight[k] < 1 || p->slot_weight[k] > GR_MAX_WEIGHT))
+            return fail(GR_EINVAL, "program %u slot %u: weight outside 1..2^24", idx, k);
+    }
+    if (n < 32 && (p->existing_mask >> n) != 0)
+        return fail(GR_EINVAL, "program %u: existing_mask has bits beyond slot %u", idx, n);
+    return GR_OK;
+}
+
+gr_status validate_opts(const gr_options *o) {
+    if (o && o->max_iters > GR_MAX_ITERS) return fail(GR_EINVAL, "max_iters above %d", GR_MAX_ITERS);
+    return GR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Packing
+// ---------------------------------------------------------------------------
+
+size_t align_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t progs_off, order_off, segbase_off, perm_off, arena_bytes;
+    size_t segmask_off, trace_off, scratch_bytes;
+    uint64_t n_segments;
+    std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
+};
+
+uint32_t t_pad_of(uint32_t T) { return (T + 7u) & ~7u; }
+
+Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
+    Layout L;
+    L.progs_off = sizeof(ArenaHeader);
+    L.order_off = align_to(L.progs_off + (size_t)n * sizeof(DevProg), 16);
+    L.segbase_off = align_to(L.order_off + (size_t)n * 4, 16);
+    L.perm_off = align_to(L.segbase_off + (size_t)(n + 1) * 8, 16);
+    L.trace_elem.resize(n);
+    L.segmask_elem.resize(n);
+    L.perm_base.resize(n);
+    uint64_t perm_total = 0, seg_total = 0, trace_total = 0;
+    for (uint32_t p = 0; p < n; ++p) {
+        L.perm_base[p] = perm_total;
+        perm_total += progs[p].perm ? progs[p].perm_len : 0;
+        L.segmask_elem[p] = seg_total;
+        const uint64_t segs = (uint64_t)progs[p].n_stmts * ls[p].blocks;
+        seg_total += segs;
+        L.trace_elem[p] = trace_total;
+        trace_total += align_to(segs * t_pad_of(ls[p].threads), 128);
+    }
+    L.n_segments = seg_total;
+    L.arena_bytes = align_to(L.perm_off + perm_total * 4, 256);
+    L.segmask_off = 256;
+    L.trace_off = align_to(L.segmask_off + seg_total * 8, 256);
+    L.scratch_bytes = align_to(L.trace_off + trace_total * 2, 256);
+    return L;
+}
+
+gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n) {
+    if (n == 0) return fail(GR_EINVAL, "no programs");
+    if (!progs || !ls) return fail(GR_EINVAL, "progs or launches is NULL");
+    for (uint32_t p = 0; p < n; ++p) {
+        gr_status s = validate_one(&progs[p], ls[p], p);
+        if (s != GR_OK) return s;
+    }
+    return GR_OK;
+}
+
+void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
+               uint8_t *arena) {
+    memset(arena, 0, L.arena_bytes);
+    ArenaHeader *H = reinterpret_cast<ArenaHeader *>(arena);
+    H->magic = kArenaMagic;
+    H->n_progs = n;
+    H->progs_off = L.progs_off;
+    H->order_off = L.order_off;
+    H->segbase_off = L.segbase_off;
+    H->perm_off = L.perm_off;
+    H->n_segments = L.n_segments;
+    H->scratch_segmask_off = L.segmask_off;
+    H->scratch_trace_off = L.trace_off;
+    H->scratch_bytes = L.scratch_bytes;
+    DevProg *dp = reinterpret_cast<DevProg *>(arena + L.progs_off);
+    uint32_t *order = reinterpret_cast<uint32_t *>(arena + L.order_off);
+    uint64_t *segbase = reinterpret_cast<uint64_t *>(arena + L.segbase_off);
+    uint32_t *perm = reinterpret_cast<uint32_t *>(arena + L.perm_off);
+    std::vector<uint64_t> cost(n);
+    for (uint32_t p = 0; p < n; ++p) {
+        const gr_program &P = progs[p];
+        DevProg &D = dp[p];
+        const uint32_t S = P.n_stmts, nsl = S - 1;
+        D.n_stmts = S;
+        D.n_slots = nsl;
+        D.blocks = ls[p].blocks;
+        D.threads = ls[p].threads;
+        D.t_pad = t_pad_of(ls[p].threads);
+        D.m_shared = P.m_shared;
+        D.m_global = P.m_global;
+        D.mode = modes ? modes[p] : GR_MODE_REPAIR;
+        D.existing = P.existing_mask;
+        D.trace_off = L.trace_elem[p];
+        D.segmask_off = L.segmask_elem[p];
+        for (uint32_t k = 0; k < nsl; ++k) {
+            if (P.slot_level[k] == GR_GRID) D.grid_mask |= 1u << k;
+            D.weights[k] = slot_weight_of(P, k);
+            D.slot_gk[k] = P.slot_guard ? P.slot_guard[2 * k] : 0;
+            D.slot_gr[k] = P.slot_guard ? P.slot_guard[2 * k + 1] : 0;
+            if (D.slot_gk[k]) D.guarded_slots |= 1u << k;
+        }
+        for (uint32_t s = 0; s < S; ++s) {
+            const gr_stmt &st = P.stmts[s];
+            DevStmt &ds = D.stmts[s];
+            const uint32_t M = st.space == GR_SHARED ? P.m_shared : P.m_global;
+            ds.op = st.op;
+            ds.space = st.space;
+            ds.kind = st.kind;
+            ds.am = st.a % M;
+            ds.bm = st.b % M;
+            ds.cm = st.c % M;
+            ds.perm_off = st.kind == GR_PERM ? (uint32_t)(L.perm_base[p] + st.perm_off) : 0u;
+            ds.gk = st.guard_k;
+            ds.gr = st.guard_r;
+            ds.m = M;
+            if (st.op == GR_W) D.write_mask |= 1u << s;
+            if (st.space == GR_SHARED) D.shared_rows |= 1u << s;
+            else D.global_rows |= 1u << s;
+        }
+        if (P.perm && P.perm_len) memcpy(perm + L.perm_base[p], P.perm, (size_t)P.perm_len * 4);
+        segbase[p] = L.segmask_elem[p];
+        cost[p] = (uint64_t)S * ls[p].blocks * t_pad_of(ls[p].threads);
+    }
+    segbase[n] = L.n_segments;
+    std::iota(order, order + n, 0u);
+    std::stable_sort(order, order + n, [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+}
+
+// ---------------------------------------------------------------------------
+// Per-device workspace
+// ---------------------------------------------------------------------------
+
+struct DeviceBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    gr_status ensure(size_t bytes) {
+        if (bytes <= cap) return GR_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, (size_t)1 << 20);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+        cap = want;
+        return GR_OK;
+    }
+};
+
+struct Workspace {
+    std::mutex mu;
+    bool configured = false;
+    int sms = 0;
+    uint32_t max_dyn = 0;
+    DeviceBuf arena, scratch, out, aux;
+    std::vector<uint8_t> host_arena;
+};
+
+constexpr int kMaxDevices = 64;
+Workspace g_ws[kMaxDevices];
+
+gr_status current_ws(Workspace **ws) {
+    int dev = 0;
+    GR_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(GR_ECUDA, "device index %d unsupported", dev);
+    *ws = &g_ws[dev];
+    return GR_OK;
+}
+
+constexpr uint32_t kDefaultTableBytes = 96u * 1024u;
+
+gr_status ensure_configured(Workspace &ws) {
+    if (ws.configured) return GR_OK;
+    int dev = 0;
+    GR_CUDA(cudaGetDevice(&dev));
+    GR_CUDA(cudaDeviceGetAttribute(&ws.sms, cudaDevAttrMultiProcessorCount, dev));
+    int optin = 0;
+    GR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    ws.max_dyn = (uint32_t)optin;
+    GR_CUDA(configure_kernels(ws.max_dyn));
+    ws.configured = true;
+    return GR_OK;
+}
+
+uint32_t dyn_bytes_for(uint32_t table_bytes) {
+    return (uint32_t)(fixed_smem_bytes() + align_to(std::max<size_t>(table_bytes, 48 * 1024), 16));
+}
+
+LaunchCfg choose_cfg(const Workspace &ws, uint32_t n) {
+    LaunchCfg c;
+    c.table_bytes = kDefaultTableBytes;
+    if (dyn_bytes_for(c.table_bytes) > ws.max_dyn) c.table_bytes = kMinTableBytes;
+    const uint32_t per_sm = std::max<uint32_t>(1u, (228u * 1024u) / (dyn_bytes_for(c.table_bytes) + 1024u));
+    c.grid = std::min<uint32_t>(n, (uint32_t)ws.sms * std::min<uint32_t>(per_sm, 2u));
+    if (c.grid == 0) c.grid = 1;
+    return c;
+}
+
+uint32_t expand_grid(const Workspace &ws) { return (uint32_t)ws.sms * 8u; }
+
+gr_status upload_batch(Workspace &ws, const gr_program *progs, const gr_launch *ls, const int32_t *modes,
+                       uint32_t n, cudaStream_t st, Layout *Lout) {
+    Layout L = layout_of(progs, ls, n);
+    ws.host_arena.resize(L.arena_bytes);
+    pack_into(progs, ls, modes, n, L, ws.host_arena.data());
+    gr_status s;
+    if ((s = ws.arena.ensure(L.arena_bytes)) != GR_OK) return s;
+    if ((s = ws.scratch.ensure(L.scratch_bytes)) != GR_OK) return s;
+    GR_CUDA(cudaMemcpyAsync(ws.arena.p, ws.host_arena.data(), L.arena_bytes, cudaMemcpyHostToDevice, st));
+    *Lout = L;
+    return GR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *gr_version(void) { return "gpurepair-gb300 0.1 (sm_103a)"; }
+
+const char *gr_last_error(void) { return g_last_error.c_str(); }
+
+gr_status gr_validate(const gr_program *prog, gr_launch launch) { return validate_one(prog, launch, 0); }
+
+gr_status gr_pack_size(const gr_program *progs, const gr_launch *launches, uint32_t n, uint64_t *arena_bytes,
+                       uint64_t *scratch_bytes) {
+    if (!arena_bytes || !scratch_bytes) return fail(GR_EINVAL, "NULL output");
+    gr_status s = validate_all(progs, launches, n);
+    if (s != GR_OK) return s;
+    Layout L = layout_of(progs, launches, n);
+    *arena_bytes = L.arena_bytes;
+    *scratch_bytes = L.scratch_bytes;
+    return GR_OK;
+}
+
+gr_status gr_pack(const gr_program *progs, const gr_launch *launches, const int32_t *modes, uint32_t n,
+                  void *host_arena, uint64_t arena_bytes) {
+    if (!host_arena) return fail(GR_EINVAL, "host_arena is NULL");
+    if (reinterpret_cast<uintptr_t>(host_arena) % 16) return fail(GR_EINVAL, "host_arena not 16-byte aligned");
+    gr_status s = validate_all(progs, launches, n);
+    if (s != GR_OK) return s;
+    if (modes)
+        for (uint32_t p = 0; p < n; ++p)
+            if (modes[p] != GR_MODE_REPAIR && modes[p] != GR_MODE_REMOVE)
+                return fail(GR_EINVAL, "program %u: bad mode %d", p, modes[p]);
+    Layout L = layout_of(progs, launches, n);
+    if (arena_bytes < L.arena_bytes)
+        return fail(GR_ECAPACITY, "arena needs %llu bytes", (unsigned long long)L.arena_bytes);
+    pack_into(progs, launches, modes, n, L, static_cast<uint8_t *>(host_arena));
+    return GR_OK;
+}
+
+static gr_options opts_or_default(const gr_options *o) {
+    gr_options d;
+    memset(&d, 0, sizeof(d));
+    d.grid_enabled = 1;
+    d.max_iters = GR_MAX_ITERS;
+    if (o) {
+        d.grid_enabled = o->grid_enabled;
+        d.max_iters = o->max_iters ? o->max_iters : GR_MAX_ITERS;
+    }
+    return d;
+}
+
+gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                           uint64_t scratch_bytes, gr_repair_result *d_out, void *stream) {
+    if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    if (scratch_bytes < 256) return fail(GR_ECAPACITY, "scratch too small");
+    gr_status s = validate_opts(opts);
+    if (s != GR_OK) return s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
+    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
+    GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, choose_cfg(*ws, n), st));
+    return GR_OK;
+}
+
+gr_status gr_expand_packed(const void *d_arena, void *d_scratch, uint64_t scratch_bytes, void *stream) {
+    if (!d_arena || !d_scratch) return fail(GR_EINVAL, "NULL buffer");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    if (scratch_bytes < 256) return fail(GR_ECAPACITY, "scratch too small");
+    gr_status s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), static_cast<cudaStream_t>(stream)));
+    return GR_OK;
+}
+
+gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                             uint64_t scratch_bytes, gr_repair_result *d_out, void *stream) {
+    if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    if (scratch_bytes < 256) return fail(GR_ECAPACITY, "scratch too small");
+    gr_status s = validate_opts(opts);
+    if (s != GR_OK) return s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
+    GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, choose_cfg(*ws, n), st));
+    return GR_OK;
+}
+
+gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
+                          uint64_t scratch_bytes, gr_witnesses *d_out, void *stream) {
+    if (!d_arena || !d_scratch || !d_out || !d_masks || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    if (scratch_bytes < 256) return fail(GR_ECAPACITY, "scratch too small");
+    gr_status s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
+    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
+    GR_CUDA(launch_check(d_arena, n, d_masks, d_scratch, d_out, choose_cfg(*ws, n), st));
+    return GR_OK;
+}
+
+gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, const int32_t *modes, uint32_t n,
+                          const gr_options *opts, gr_repair_result *out, void *stream) {
+    if (!out) return fail(GR_EINVAL, "out is NULL");
+    gr_status s = validate_all(progs, launches, n);
+    if (s != GR_OK) return s;
+    if ((s = validate_opts(opts)) != GR_OK) return s;
+    if (modes)
+        for (uint32_t p = 0; p < n; ++p)
+            if (modes[p] != GR_MODE_REPAIR && modes[p] != GR_MODE_REMOVE)
+                return fail(GR_EINVAL, "program %u: bad mode %d", p, modes[p]);
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Layout L;
+    if ((s = upload_batch(*ws, progs, launches, modes, n, st, &L)) != GR_OK) return s;
+    if ((s = ws->out.ensure((size_t)n * sizeof(gr_repair_result))) != GR_OK) return s;
+    GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
+    GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
+    GR_CUDA(launch_repair(ws->arena.p, n, opts_or_default(opts), ws->scratch.p,
+                          static_cast<gr_repair_result *>(ws->out.p), choose_cfg(*ws, n), st));
+    GR_CUDA(cudaMemcpyAsync(out, ws->out.p, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    return GR_OK;
+}
+
+gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches, const uint32_t *masks, uint32_t n,
+                         gr_witnesses *out, void *stream) {
+    if (!out || !masks) return fail(GR_EINVAL, "out or masks is NULL");
+    gr_status s = validate_all(progs, launches, n);
+    if (s != GR_OK) return s;
+    for (uint32_t p = 0; p < n; ++p) {
+        const uint32_t nsl = progs[p].n_stmts - 1;
+        if (nsl < 32 && (masks[p] >> nsl)) return fail(GR_EINVAL, "program %u: mask has bits beyond slot %u", p, nsl);
+    }
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Layout L;
+    if ((s = upload_batch(*ws, progs, launches, nullptr, n, st, &L)) != GR_OK) return s;
+    const size_t mask_bytes = align_to((size_t)n * 4, 256);
+    if ((s = ws->out.ensure((size_t)n * sizeof(gr_witnesses))) != GR_OK) return s;
+    if ((s = ws->aux.ensure(mask_bytes)) != GR_OK) return s;
+    GR_CUDA(cudaMemcpyAsync(ws->aux.p, masks, (size_t)n * 4, cudaMemcpyHostToDevice, st));
+    GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
+    GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
+    GR_CUDA(launch_check(ws->arena.p, n, static_cast<const uint32_t *>(ws->aux.p), ws->scratch.p,
+                         static_cast<gr_witnesses *>(ws->out.p), choose_cfg(*ws, n), st));
+    GR_CUDA(cudaMemcpyAsync(out, ws->out.p, (size_t)n * sizeof(gr_witnesses), cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    return GR_OK;
+}
+
+gr_status gr_check(const gr_program *prog, gr_launch launch, uint32_t mask, gr_witnesses *out) {
+    return gr_check_batch(prog, &launch, &mask, 1, out, nullptr);
+}
+
+gr_status gr_repair(const gr_program *prog, gr_launch launch, int32_t mode, const gr_options *opts,
+                    gr_repair_result *out) {
+    return gr_repair_batch(prog, &launch, &mode, 1, opts, out, nullptr);
+}
+
+gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode, const gr_options *opts,
+                          gr_repair_result *out) {
+    if (!out) return fail(GR_EINVAL, "out is NULL");
+    gr_status s = validate_all(prog, &launch, 1);
+    if (s != GR_OK) return s;
+    if ((s = validate_opts(opts)) != GR_OK) return s;
+    if (mode != GR_MODE_REPAIR && mode != GR_MODE_REMOVE) return fail(GR_EINVAL, "bad mode %d", mode);
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = nullptr;
+    Layout L;
+    if ((s = upload_batch(*ws, prog, &launch, &mode, 1, st, &L)) != GR_OK) return s;
+    const size_t state_bytes = align_to(sizeof(LoopState), 256);
+    const size_t wit_bytes = align_to(sizeof(gr_witnesses), 256);
+    if ((s = ws->aux.ensure(state_bytes + wit_bytes + sizeof(gr_repair_result))) != GR_OK) return s;
+    LoopState *d_state = static_cast<LoopState *>(ws->aux.p);
+    gr_witnesses *d_wit = reinterpret_cast<gr_witnesses *>(static_cast<uint8_t *>(ws->aux.p) + state_bytes);
+    gr_repair_result *d_out =
+        reinterpret_cast<gr_repair_result *>(static_cast<uint8_t *>(ws->aux.p) + state_bytes + wit_bytes);
+    GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
+    const gr_options o = opts_or_default(opts);
+    GR_CUDA(launch_plain_init(ws->arena.p, 0, o, d_state, st));
+    const LaunchCfg cfg = choose_cfg(*ws, 1);
+    uint32_t done = 0;
+    GR_CUDA(cudaMemcpy(&done, &d_state->done, 4, cudaMemcpyDeviceToHost));
+    for (uint32_t guard = 0; !done && guard <= GR_MAX_ITERS; ++guard) {
+        GR_CUDA(cudaMemsetAsync(d_wit, 0, sizeof(gr_witnesses), st));
+        GR_CUDA(launch_plain_check(ws->arena.p, 0, ws->scratch.p, d_state, d_wit, launch.blocks, cfg.table_bytes, st));
+        GR_CUDA(launch_plain_solve(ws->arena.p, 0, d_state, d_wit, d_out, st));
+        GR_CUDA(cudaMemcpy(&done, &d_state->done, 4, cudaMemcpyDeviceToHost));
+    }
+    if (!done) return fail(GR_ECUDA, "plain loop did not terminate");
+    if (L.n_segments == 0) return fail(GR_ECUDA, "empty layout");
+    // a program that ended in the initial solve still needs its result written
+    GR_CUDA(launch_plain_solve(ws->arena.p, 0, d_state, d_wit, d_out, st));
+    GR_CUDA(cudaMemcpy(out, d_out, sizeof(gr_repair_result), cudaMemcpyDeviceToHost));
+    return GR_OK;
+}
+
+gr_status gr_solve(uint32_t n_vars, const uint32_t *w, const uint32_t *pos, uint32_t n_pos, const uint32_t *neg,
+                   uint32_t n_neg, uint32_t forced, uint32_t forbidden, uint32_t *mask_out, uint32_t *weight_out) {
+    if (!mask_out || !weight_out || !w) return fail(GR_EINVAL, "NULL argument");
+    if (n_vars < 1 || n_vars > GR_MAX_SLOTS) return fail(GR_EINVAL, "n_vars %u outside 1..%d", n_vars, GR_MAX_SLOTS);
+    if (n_pos + n_neg > GR_MAX_CLAUSES) return fail(GR_EINVAL, "more than %d clauses", GR_MAX_CLAUSES);
+    if ((n_pos && !pos) || (n_neg && !neg)) return fail(GR_EINVAL, "NULL clause array");
+    const uint32_t full = n_vars == 32 ? 0xFFFFFFFFu : ((1u << n_vars) - 1u);
+    for (uint32_t k = 0; k < n_vars; ++k)
+        if (w[k] < 1 || w[k] > GR_MAX_WEIGHT) return fail(GR_EINVAL, "weight %u outside 1..2^24", k);
+    for (uint32_t i = 0; i < n_pos; ++i)
+        if (pos[i] & ~full) return fail(GR_EINVAL, "positive clause %u uses a variable >= n_vars", i);
+    for (uint32_t i = 0; i < n_neg; ++i)
+        if ((neg[i] & ~full) || neg[i] == 0) return fail(GR_EINVAL, "negative clause %u empty or out of range", i);
+    if ((forced | forbidden) & ~full) return fail(GR_EINVAL, "forced/forbidden use a variable >= n_vars");
+    std::vector<uint32_t> in(5 + GR_MAX_SLOTS + n_pos + n_neg, 0);
+    in[0] = n_vars;
+    in[1] = n_pos;
+    in[2] = n_neg;
+    in[3] = forced;
+    in[4] = forbidden;
+    for (uint32_t k = 0; k < n_vars; ++k) in[5 + k] = w[k];
+    for (uint32_t i = 0; i < n_pos; ++i) in[5 + GR_MAX_SLOTS + i] = pos[i];
+    for (uint32_t i = 0; i < n_neg; ++i) in[5 + GR_MAX_SLOTS + n_pos + i] = neg[i];
+    gr_status s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    const size_t in_bytes = align_to(in.size() * 4, 256);
+    if ((s = ws->aux.ensure(in_bytes + 256)) != GR_OK) return s;
+    uint32_t *d_in = static_cast<uint32_t *>(ws->aux.p);
+    uint32_t *d_out = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(ws->aux.p) + in_bytes);
+    GR_CUDA(cudaMemcpy(d_in, in.data(), in.size() * 4, cudaMemcpyHostToDevice));
+    GR_CUDA(launch_solve(d_in, d_out, nullptr));
+    uint32_t res[3];
+    GR_CUDA(cudaMemcpy(res, d_out, sizeof(res), cudaMemcpyDeviceToHost));
+    *mask_out = res[1];
+    *weight_out = res[2];
+    return res[0] ? GR_OK : GR_UNSAT;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// engine.cuh — packed device layout shared by the host packer (capi.cu) and
+// the kernels (kernels.cu).  Internal to libgpurepair; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gpurepair.h"
+
+namespace gr {
+
+constexpr uint32_t kArenaMagic = 0x47525031u;  // "GRP1"
+constexpr uint32_t kThreads = 512;             // threads per CTA of the repair kernels
+constexpr uint32_t kChunkShift = 10;           // address chunk = 1,024 words
+constexpr uint32_t kChunkWords = 1u << kChunkShift;
+constexpr uint16_t kEmpty = 0xFFFFu;           // owner-table sentinels
+constexpr uint16_t kMulti = 0xFFFEu;
+constexpr uint32_t kClauseCap = 1024;          // clause buffer (>= 2 * 25 * 26 / 2)
+constexpr uint32_t kMinTableBytes = 25u * 2u * kChunkWords;  // one chunk for 25 rows
+
+// One statement, with map coefficients reduced modulo its array's size.
+struct DevStmt {
+    uint8_t op, space, kind, _pad;
+    uint32_t am, bm, cm;   // a, b, c mod M
+    uint32_t perm_off;     // absolute index into the arena's permutation area
+    uint16_t gk, gr;       // guard: active iff gk == 0 || tid % gk == gr
+    uint32_t m;            // words of its array
+    uint32_t _pad2;
+};
+static_assert(sizeof(DevStmt) == 32, "DevStmt layout");
+
+// One program: header + statements + slots.  16-byte aligned, fixed size.
+struct DevProg {
+    uint32_t n_stmts, n_slots, blocks, threads;
+    uint32_t t_pad;        // threads rounded up to a multiple of 8
+    uint32_t m_shared, m_global;
+    int32_t mode;          // GR_MODE_*
+    uint32_t existing, grid_mask, write_mask, shared_rows;
+    uint32_t global_rows, guarded_slots, _r1, _r2;
+    uint64_t trace_off;    // u16 elements from the scratch trace base; layout [S][B][t_pad]
+    uint64_t segmask_off;  // u64 elements from the scratch segment-mask base; layout [S][B]
+    uint32_t weights[GR_MAX_SLOTS];
+    uint16_t slot_gk[GR_MAX_SLOTS];
+    uint16_t slot_gr[GR_MAX_SLOTS];
+    DevStmt stmts[GR_MAX_STMTS];
+};
+static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");
+
+// Arena = ArenaHeader | DevProg[n] | order[n] | seg_base[n+1] | perm[]
+// Scratch = ctrl (256 B) | segmask u64[] | trace u16[]
+struct ArenaHeader {
+    uint32_t magic, n_progs, _r0, _r1;
+    uint64_t progs_off, order_off, segbase_off, perm_off;  // bytes from the arena start
+    uint64_t n_segments;                                   // sum over programs of S*B
+    uint64_t scratch_segmask_off, scratch_trace_off;       // bytes from the scratch start
+    uint64_t scratch_bytes;
+    uint64_t _r2[6];
+};
+static_assert(sizeof(ArenaHeader) == 128, "ArenaHeader layout");
+
+// Loop state of one program between iterations (plain path keeps it in
+// device memory between launches).
+struct LoopState {
+    uint32_t mask, probe, done, status, iters, forced, forbidden, max_iters;
+    uint64_t access_pairs, t_start;
+    uint32_t traj[GR_MAX_ITERS];
+    uint32_t acc_intra[32], acc_inter[32];
+};
+
+struct LaunchCfg {
+    uint32_t grid;         // CTAs of the persistent kernels
+    uint32_t table_bytes;  // shared-memory owner-table budget per CTA
+};
+
+// Host-callable launchers (kernels.cu).
+cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint32_t grid, cudaStream_t st);
+cudaError_t launch_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
+                          gr_repair_result *d_out, LaunchCfg cfg, cudaStream_t st);
+cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
+                         gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st);
+cudaError_t launch_plain_init(const void *d_arena, uint32_t p, const gr_options &opts,
+                              LoopState *d_state, cudaStream_t st);
+cudaError_t launch_plain_check(const void *d_arena, uint32_t p, void *d_scratch, LoopState *d_state,
+                               gr_witnesses *d_wit, uint32_t n_blocks, uint32_t table_bytes,
+                               cudaStream_t st);
+cudaError_t launch_plain_solve(const void *d_arena, uint32_t p, LoopState *d_state,
+                               const gr_witnesses *d_wit, gr_repair_result *d_out, cudaStream_t st);
+cudaError_t launch_solve(const uint32_t *d_in, uint32_t *d_out, cudaStream_t st);
+size_t fixed_smem_bytes();
+cudaError_t configure_kernels(uint32_t max_dynamic_smem);
+
+}  // namespace gr

@@ -1,0 +1,1135 @@
+// kernels.cu — sm_103a kernels of the repair loop (Algorithm 1 of GPURepair,
+// Section 2.4) over concrete access programs.
+//
+//   k_expand        : address traces, one u16 word address per (statement,
+//                     thread), layout [S][B][t_pad], plus per-(statement, block)
+//                     masks of the 1,024-word chunks touched.
+//   owner tables    : the check (Verify).  For each address of a chunk tile, a
+//                     shared-memory table holds per statement the one thread
+//                     (same-block pass) or block (cross-block pass) that touched
+//                     it, or MULTI.  Two plain-store passes build it without
+//                     atomics; a scan of the table emits the witness bitmaps.
+//   mhs_solve       : exact minimum-weight hitting set (Solve), bit-sliced: the
+//                     low 5 compact variables ride in the bits of a 32-bit word,
+//                     the rest are enumerated by popcount level (Gosper order)
+//                     with a weight bound; ties go to the lowest mask.
+//   k_repair        : persistent work-queue kernel, one CTA per program, that
+//                     runs check -> clauses -> solve to the fixed point.
+//   k_plain_*       : the same stages as separate launches, one check launch
+//                     per iteration (host-driven loop).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "engine.cuh"
+
+namespace gr {
+
+// ---------------------------------------------------------------------------
+// Shared memory
+// ---------------------------------------------------------------------------
+
+struct MhsSmem {
+    uint32_t pc[kClauseCap];   // preprocessed positive clauses (0 = dropped)
+    uint32_t khi[kClauseCap];  // kept clauses: compact high part
+    uint32_t klo[kClauseCap];  // kept clauses: low-part hit pattern over 32 low assignments
+    uint32_t nraw[kClauseCap]; // negative clauses after preprocessing (0 = dropped)
+    uint32_t nhi[kClauseCap];
+    uint32_t nlo[kClauseCap];
+    uint32_t binom[25][25];
+    uint32_t w8[3][256];       // weight of each byte of the high part
+    uint32_t wlo[32];          // weight of each low assignment
+    uint32_t lb[26];           // sum of the k smallest high weights
+    uint32_t wc[GR_MAX_SLOTS]; // compact weights
+    uint32_t n_kept, n_negk, R, unsat;
+};
+
+struct Smem {
+    DevProg prog;
+    uint32_t act[GR_MAX_STMTS][32];  // active-thread bitmaps per statement
+    uint32_t rows_intra[32], rows_inter[32];
+    uint32_t acc_intra[32], acc_inter[32];
+    uint32_t ph_intra[32], ph_inter[32];
+    uint32_t traj[GR_MAX_ITERS];
+    uint32_t cl[kClauseCap];
+    uint32_t row_list[32];
+    uint32_t scan[32];
+    uint8_t chunk_slot[64];
+    unsigned long long best;
+    unsigned long long pairs;
+    unsigned long long access_pairs;
+    unsigned long long t_start;
+    unsigned long long chunk_acc;
+    // loop state
+    uint32_t mask, probe, done, status, iters, forced, forbidden, max_iters;
+    uint32_t diverge, n_cl, n_rows, item;
+    uint32_t rel_sh, rel_gi, rel_gx, sol_found, sol_mask, sol_weight;
+};
+
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+constexpr size_t kFixedSmem = align_up(sizeof(Smem), 16);
+
+size_t fixed_smem_bytes() { return kFixedSmem; }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t range_mask(uint32_t i, uint32_t j) {  // bits [i, j)
+    const uint32_t hi = j >= 32 ? 0xFFFFFFFFu : ((1u << j) - 1u);
+    return hi & ~((1u << i) - 1u);
+}
+
+// Statements in the same phase as s when the slots in `cut` are enabled:
+// slot k separates statements k and k+1.
+__device__ __forceinline__ uint32_t phase_of(uint32_t s, uint32_t cut, uint32_t S) {
+    const uint32_t below = cut & ((1u << s) - 1u);
+    const uint32_t start = below ? 32u - __clz(below) : 0u;
+    const uint32_t above = cut >> s;
+    const uint32_t end = above ? s + __ffs(above) - 1u : S - 1u;
+    return range_mask(start, end + 1u);
+}
+
+__device__ __forceinline__ uint32_t pext32(uint32_t x, uint32_t m) {
+    uint32_t out = 0, j = 0;
+    for (uint32_t t = m; t; t &= t - 1u, ++j)
+        if (x & (t & (0u - t))) out |= 1u << j;
+    return out;
+}
+
+__device__ __forceinline__ uint32_t pdep32(uint32_t x, uint32_t m) {
+    uint32_t out = 0, j = 0;
+    for (uint32_t t = m; t; t &= t - 1u, ++j)
+        if ((x >> j) & 1u) out |= t & (0u - t);
+    return out;
+}
+
+// Low assignments l in [0,32) with bit k set, k < 5.
+__device__ __forceinline__ uint32_t low_pattern(uint32_t k) {
+    const uint32_t p[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+    return p[k];
+}
+
+__device__ __forceinline__ void or_row(uint32_t *rows, uint32_t i, uint32_t bits) {
+    volatile uint32_t *vr = rows;
+    if (bits & ~vr[i]) atomicOr(&rows[i], bits);
+}
+
+// ---------------------------------------------------------------------------
+// Program load
+// ---------------------------------------------------------------------------
+
+__device__ void load_program(Smem &sm, const DevProg *gp) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(gp);
+    uint4 *dst = reinterpret_cast<uint4 *>(&sm.prog);
+    for (uint32_t i = threadIdx.x; i < sizeof(DevProg) / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    // active-thread bitmaps: one ballot per 32 threads of a statement
+    const uint32_t S = sm.prog.n_stmts, T = sm.prog.threads;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t w = warp; w < S * 32u; w += nwarps) {
+        const uint32_t s = w >> 5, word = w & 31u;
+        const uint32_t tid = word * 32u + lane;
+        const uint32_t k = sm.prog.stmts[s].gk, r = sm.prog.stmts[s].gr;
+        const bool on = tid < T && (k == 0 || tid % k == r);
+        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, on);
+        if (lane == 0) sm.act[s][word] = bits;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Check: owner tables
+// ---------------------------------------------------------------------------
+
+// One owner pass over the statements in `rows` (bit s = statement s), the
+// accesses of blocks [blk_lo, blk_lo+nb) and the address chunks in `chunks`.
+// The owner of an access is its tid (same-block pass, nb == 1) or its block
+// (cross-block pass).  Witness bits go to rows_out (row i, bit j >= i) for
+// pairs in one phase (ph) with at least one write.
+template <bool kInter>
+__device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const uint16_t *trace,
+                           uint32_t rows, uint32_t blk_lo, uint32_t nb, uint64_t chunks,
+                           const uint32_t *ph, uint32_t *rows_out) {
+    const DevProg &P = sm.prog;
+    const uint32_t S = P.n_stmts, B = P.blocks, tpad = P.t_pad, nv = tpad >> 3;
+    const uint32_t n_rows = __popc(rows);
+    if (n_rows == 0 || chunks == 0) return;  // uniform
+    __syncthreads();                          // row_list / chunk_slot reuse
+    if (threadIdx.x == 0) {
+        uint32_t n = 0;
+        for (uint32_t t = rows; t; t &= t - 1u) sm.row_list[n++] = __ffs(t) - 1u;
+    }
+    const uint32_t cap = table_bytes / (2u * S * kChunkWords);
+    const uint32_t wmask = P.write_mask;
+    uint64_t pending = chunks;
+    while (pending) {
+        uint64_t sel = 0;
+        uint32_t k = 0;
+        while (pending && k < cap) {
+            const uint64_t low = pending & (~pending + 1ull);
+            sel |= low;
+            pending ^= low;
+            ++k;
+        }
+        const uint32_t cols = k * kChunkWords;
+        if (threadIdx.x < 64) {
+            const uint32_t c = threadIdx.x;
+            sm.chunk_slot[c] = ((sel >> c) & 1ull) ? (uint8_t)__popcll(sel & ((1ull << c) - 1ull)) : 0xFF;
+        }
+        __syncthreads();
+        // clear the rows in use
+        const uint32_t vpr = cols >> 3;
+        for (uint32_t u = threadIdx.x; u < n_rows * vpr; u += blockDim.x) {
+            const uint32_t r = u / vpr, v = u - r * vpr;
+            reinterpret_cast<uint4 *>(tab + (size_t)sm.row_list[r] * cols)[v] =
+                make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        }
+        __syncthreads();
+        // pass 0: every access stores its owner (one of them wins);
+        // pass 1: an access that finds another owner stores MULTI.
+        const uint32_t units = n_rows * nb * nv;
+        for (uint32_t pass = 0; pass < 2; ++pass) {
+            for (uint32_t u = threadIdx.x; u < units; u += blockDim.x) {
+                const uint32_t v = u % nv;
+                const uint32_t rest = u / nv;
+                const uint32_t bi = rest % nb;
+                const uint32_t s = sm.row_list[rest / nb];
+                const uint32_t act8 = (sm.act[s][v >> 2] >> ((v & 3u) * 8u)) & 0xFFu;
+                if (!act8) continue;
+                const uint32_t blk = blk_lo + bi;
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(trace + ((size_t)s * B + blk) * tpad) + v);
+                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+                uint16_t *row = tab + (size_t)s * cols;
+#pragma unroll
+                for (uint32_t e = 0; e < 8; ++e) {
+                    if (!((act8 >> e) & 1u)) continue;
+                    const uint32_t a = (w4[e >> 1] >> ((e & 1u) * 16u)) & 0xFFFFu;
+                    const uint32_t slot = sm.chunk_slot[a >> kChunkShift];
+                    if (slot == 0xFFu) continue;
+                    const uint32_t idx = slot * kChunkWords + (a & (kChunkWords - 1u));
+                    const uint16_t owner = kInter ? (uint16_t)blk : (uint16_t)(v * 8u + e);
+                    if (pass == 0) {
+                        row[idx] = owner;
+                    } else if (row[idx] != owner) {
+                        row[idx] = kMulti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // scan: per address, the statements touching it and their owners
+        for (uint32_t col = threadIdx.x; col < cols; col += blockDim.x) {
+            uint32_t tm = 0;
+            for (uint32_t r = 0; r < n_rows; ++r) {
+                const uint32_t s = sm.row_list[r];
+                if (tab[(size_t)s * cols + col] != kEmpty) tm |= 1u << s;
+            }
+            if (!tm) continue;
+            if ((tm & (tm - 1u)) == 0) {  // one statement: only a self race is possible
+                const uint32_t s = __ffs(tm) - 1u;
+                if (((wmask >> s) & 1u) && tab[(size_t)s * cols + col] == kMulti) or_row(rows_out, s, 1u << s);
+                continue;
+            }
+            const uint16_t first = tab[(size_t)(__ffs(tm) - 1u) * cols + col];
+            bool uniform = first != kMulti;
+            for (uint32_t t = tm & (tm - 1u); t && uniform; t &= t - 1u)
+                if (tab[(size_t)(__ffs(t) - 1u) * cols + col] != first) uniform = false;
+            if (uniform) continue;  // one owner for every access: no race here
+            for (uint32_t it = tm; it; it &= it - 1u) {
+                const uint32_t i = __ffs(it) - 1u;
+                const uint16_t oi = tab[(size_t)i * cols + col];
+                uint32_t conf;
+                if (oi == kMulti) {
+                    conf = tm;
+                } else {
+                    uint32_t same = 0;
+                    for (uint32_t jt = tm; jt; jt &= jt - 1u) {
+                        const uint32_t j = __ffs(jt) - 1u;
+                        if (tab[(size_t)j * cols + col] == oi) same |= 1u << j;
+                    }
+                    conf = tm & ~same;
+                }
+                conf &= ph[i] & ~((1u << i) - 1u);
+                if (!((wmask >> i) & 1u)) conf &= wmask;
+                if (conf) or_row(rows_out, i, conf);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ uint64_t block_chunks(const uint64_t *segmask, uint32_t B, uint32_t rows, uint32_t blk) {
+    uint64_t m = 0;
+    for (uint32_t t = rows; t; t &= t - 1u) m |= segmask[(size_t)(__ffs(t) - 1u) * B + blk];
+    return m;
+}
+
+// Phase masks and the statements that share a phase with a write of their space.
+__device__ void prepare_check(Smem &sm, uint32_t mask) {
+    const DevProg &P = sm.prog;
+    const uint32_t S = P.n_stmts;
+    if (threadIdx.x < 32) {
+        const uint32_t s = threadIdx.x;
+        sm.rows_intra[s] = 0;
+        sm.rows_inter[s] = 0;
+        if (s < S) {
+            sm.ph_intra[s] = phase_of(s, mask, S);
+            sm.ph_inter[s] = phase_of(s, mask & P.grid_mask, S);
+        } else {
+            sm.ph_intra[s] = sm.ph_inter[s] = 0;
+        }
+        __syncwarp();
+        if (s == 0) {
+            uint32_t sh = 0, gi = 0, gx = 0;
+            for (uint32_t t = 0; t < S; ++t) {
+                const uint32_t bit = 1u << t;
+                if ((P.shared_rows & bit) && (sm.ph_intra[t] & P.shared_rows & P.write_mask)) sh |= bit;
+                if ((P.global_rows & bit) && (sm.ph_intra[t] & P.global_rows & P.write_mask)) gi |= bit;
+                if ((P.global_rows & bit) && (sm.ph_inter[t] & P.global_rows & P.write_mask)) gx |= bit;
+            }
+            sm.rel_sh = sh;
+            sm.rel_gi = gi;
+            sm.rel_gx = (P.blocks > 1) ? gx : 0u;
+            sm.pairs = 0;
+            sm.chunk_acc = 0;
+            sm.diverge = 0;
+        }
+    }
+    __syncthreads();
+}
+
+// Divergence (closed form over tid in [0, T)) and the access-pair count.
+__device__ void check_misc(Smem &sm, uint32_t mask) {
+    const DevProg &P = sm.prog;
+    const uint32_t S = P.n_stmts, T = P.threads;
+    const uint64_t B = P.blocks;
+    if (threadIdx.x == 0) {
+        uint32_t dv = 0;
+        for (uint32_t t = mask & P.guarded_slots; t; t &= t - 1u) {
+            const uint32_t k = __ffs(t) - 1u;
+            const uint32_t gk = P.slot_gk[k], gr = P.slot_gr[k];
+            const uint32_t cnt = T > gr ? (T - 1u - gr) / gk + 1u : 0u;
+            if (cnt > 0 && cnt < T) dv |= 1u << k;
+        }
+        sm.diverge = dv;
+    }
+    unsigned long long local = 0;
+    for (uint32_t idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+        const uint32_t i = idx / S, j = idx - i * S;
+        if (j < i) continue;
+        const DevStmt &a = P.stmts[i], &b = P.stmts[j];
+        if (a.space != b.space || (a.op != GR_W && b.op != GR_W)) continue;
+        uint64_t ni = 0, nj = 0, nij = 0;
+        for (uint32_t w = 0; w < 32; ++w) {
+            ni += __popc(sm.act[i][w]);
+            nj += __popc(sm.act[j][w]);
+            nij += __popc(sm.act[i][w] & sm.act[j][w]);
+        }
+        const uint32_t rg = range_mask(i, j);
+        const bool open_same = (mask & rg) == 0;
+        const bool open_cross = a.space == GR_GLOBAL && (mask & P.grid_mask & rg) == 0;
+        if (i < j) {
+            if (open_same) local += B * (ni * nj - nij);
+            if (open_cross) local += B * (B - 1) * ni * nj;
+        } else {
+            local += B * (ni * (ni - 1) / 2);
+            if (a.space == GR_GLOBAL) local += (B * (B - 1) / 2) * ni * ni;
+        }
+    }
+    if (local) atomicAdd(&sm.pairs, local);
+}
+
+// Same-block passes for blocks [b0, b1) and, if requested, the cross-block pass.
+__device__ void check_blocks(Smem &sm, uint16_t *tab, uint32_t table_bytes, const uint16_t *trace,
+                             const uint64_t *segmask, uint32_t b0, uint32_t b1, bool inter) {
+    const DevProg &P = sm.prog;
+    const uint32_t B = P.blocks;
+    for (uint32_t blk = b0; blk < b1; ++blk) {
+        if (sm.rel_sh) {
+            const uint64_t ch = block_chunks(segmask, B, sm.rel_sh, blk);
+            owner_pass<false>(sm, tab, table_bytes, trace, sm.rel_sh, blk, 1, ch, sm.ph_intra, sm.rows_intra);
+        }
+        if (sm.rel_gi) {
+            const uint64_t ch = block_chunks(segmask, B, sm.rel_gi, blk);
+            owner_pass<false>(sm, tab, table_bytes, trace, sm.rel_gi, blk, 1, ch, sm.ph_intra, sm.rows_intra);
+        }
+    }
+    if (inter && sm.rel_gx) {
+        __syncthreads();
+        unsigned long long m = 0;
+        const uint32_t nr = __popc(sm.rel_gx);
+        for (uint32_t u = threadIdx.x; u < nr * B; u += blockDim.x) {
+            const uint32_t r = u / B, blk = u - r * B;
+            uint32_t t = sm.rel_gx;
+            for (uint32_t q = 0; q < r; ++q) t &= t - 1u;
+            m |= segmask[(size_t)(__ffs(t) - 1u) * B + blk];
+        }
+        if (m) atomicOr(&sm.chunk_acc, m);
+        __syncthreads();
+        owner_pass<true>(sm, tab, table_bytes, trace, sm.rel_gx, 0, B, sm.chunk_acc, sm.ph_inter, sm.rows_inter);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Exact minimum-weight hitting set
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t unrank_colex(uint32_t rank, uint32_t k, uint32_t n, const MhsSmem &mh) {
+    uint32_t h = 0;
+    int c = (int)n - 1;
+    for (uint32_t i = k; i >= 1; --i) {
+        while (c >= 0 && mh.binom[c][i] > rank) --c;
+        h |= 1u << c;
+        rank -= mh.binom[c][i];
+        --c;
+    }
+    return h;
+}
+
+__device__ __forceinline__ uint32_t gosper_next(uint32_t h) {
+    const uint32_t c = h & (0u - h);
+    const uint32_t r = h + c;
+    return (((r ^ h) >> 2) >> (__ffs(c) - 1u)) | r;
+}
+
+// Least (weight, mask) with forced <= mask, mask & forbidden == 0, hitting
+// every clause of sm.cl[0..n_cl) and containing no negative clause neg[0..n_neg).
+// Result in sm.sol_found / sol_mask / sol_weight.  All threads must call.
+__device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t *w, uint32_t n_cl,
+                          const uint32_t *neg, uint32_t n_neg, uint32_t forced, uint32_t forbidden) {
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    __syncthreads();
+    if (tid == 0) {
+        mh.n_kept = 0;
+        mh.n_negk = 0;
+        mh.R = 0;
+        mh.unsat = (forced & forbidden) ? 1u : 0u;
+        sm.best = ~0ull;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < n_cl; i += nt) {
+        const uint32_t c = sm.cl[i];
+        uint32_t pc = 0;
+        if (!(c & forced)) {
+            pc = c & ~forbidden;
+            if (!pc) mh.unsat = 1;
+        }
+        mh.pc[i] = pc;
+    }
+    for (uint32_t i = tid; i < n_neg; i += nt) {
+        const uint32_t N = neg[i];
+        uint32_t v = 0;
+        if (!(N & forbidden)) {
+            v = N & ~forced;
+            if (!v) mh.unsat = 1;
+        }
+        mh.nraw[i] = v;
+    }
+    __syncthreads();
+    if (mh.unsat) {
+        if (tid == 0) sm.sol_found = 0;
+        __syncthreads();
+        return;
+    }
+    // drop every clause that contains another one (equal clauses: keep the first)
+    for (uint32_t i = tid; i < n_cl; i += nt) {
+        const uint32_t c = mh.pc[i];
+        if (!c) continue;
+        bool keep = true;
+        for (uint32_t j = 0; j < n_cl && keep; ++j) {
+            const uint32_t d = mh.pc[j];
+            if (d && j != i && (d & ~c) == 0 && (d != c || j < i)) keep = false;
+        }
+        if (keep) {
+            const uint32_t k = atomicAdd(&mh.n_kept, 1u);
+            mh.khi[k] = c;
+            atomicOr(&mh.R, c);
+        }
+    }
+    __syncthreads();
+    const uint32_t R = mh.R;
+    // variables outside every clause stay off; a negative clause with such a
+    // variable can never be violated
+    for (uint32_t i = tid; i < n_neg; i += nt) {
+        const uint32_t N = mh.nraw[i];
+        if (N && (N & ~R) == 0) {
+            const uint32_t k = atomicAdd(&mh.n_negk, 1u);
+            mh.nhi[k] = N;
+        }
+    }
+    const uint32_t r = __popc(R);
+    const uint32_t L = r < 5 ? r : 5;
+    const uint32_t rh = r - L;
+    const uint32_t lomask = (1u << L) - 1u;
+    for (uint32_t i = tid; i < 25 * 25; i += nt) {
+        const uint32_t n = i / 25, k = i - n * 25;
+        uint64_t c = 0;
+        if (k <= n) {
+            c = 1;
+            for (uint32_t q = 1; q <= k; ++q) c = c * (n - k + q) / q;
+        }
+        mh.binom[n][k] = (uint32_t)c;
+    }
+    if (tid < GR_MAX_SLOTS) {
+        uint32_t v = 0;
+        if (tid < r) {
+            uint32_t t = R;
+            for (uint32_t q = 0; q < tid; ++q) t &= t - 1u;
+            v = w[__ffs(t) - 1u];
+        }
+        mh.wc[tid] = v;
+    }
+    __syncthreads();
+    const uint32_t n_kept = mh.n_kept, n_negk = mh.n_negk;
+    for (uint32_t k = tid; k < n_kept; k += nt) {
+        const uint32_t c = pext32(mh.khi[k], R);
+        uint32_t lo = 0;
+        for (uint32_t b = 0; b < L; ++b)
+            if ((c >> b) & 1u) lo |= low_pattern(b);
+        mh.khi[k] = c >> L;
+        mh.klo[k] = lo;
+    }
+    for (uint32_t k = tid; k < n_negk; k += nt) {
+        const uint32_t c = pext32(mh.nhi[k], R);
+        uint32_t lo = 0xFFFFFFFFu;
+        for (uint32_t b = 0; b < L; ++b)
+            if ((c >> b) & 1u) lo &= low_pattern(b);
+        mh.nhi[k] = c >> L;
+        mh.nlo[k] = lo;
+    }
+    if (tid < 32) {
+        uint32_t v = 0;
+        for (uint32_t b = 0; b < L; ++b)
+            if ((tid >> b) & 1u) v += mh.wc[b];
+        mh.wlo[tid] = v;
+    }
+    for (uint32_t e = tid; e < 3 * 256; e += nt) {
+        const uint32_t q = e >> 8, byte = e & 255u;
+        uint32_t v = 0;
+        for (uint32_t b = 0; b < 8; ++b) {
+            const uint32_t hb = q * 8u + b;
+            if (((byte >> b) & 1u) && hb < rh) v += mh.wc[L + hb];
+        }
+        mh.w8[q][byte] = v;
+    }
+    if (tid == 0) {
+        uint32_t hw[GR_MAX_SLOTS];
+        for (uint32_t i = 0; i < rh; ++i) hw[i] = mh.wc[L + i];
+        for (uint32_t i = 1; i < rh; ++i) {
+            const uint32_t x = hw[i];
+            uint32_t j = i;
+            while (j > 0 && hw[j - 1] > x) {
+                hw[j] = hw[j - 1];
+                --j;
+            }
+            hw[j] = x;
+        }
+        uint32_t acc = 0;
+        mh.lb[0] = 0;
+        for (uint32_t i = 0; i < rh; ++i) {
+            acc += hw[i];
+            mh.lb[i + 1] = acc;
+        }
+    }
+    __syncthreads();
+    const uint32_t VL = L == 5 ? 0xFFFFFFFFu : ((1u << (1u << L)) - 1u);
+    (void)lomask;
+    for (uint32_t kh = 0; kh <= rh; ++kh) {
+        const unsigned long long cur = *(volatile unsigned long long *)&sm.best;
+        if (cur != ~0ull && (unsigned long long)mh.lb[kh] > (cur >> 32)) break;  // uniform
+        const uint32_t total = mh.binom[rh][kh];
+        const uint32_t per = (total + nt - 1u) / nt;
+        const uint32_t start = tid * per;
+        const uint32_t end = min(total, start + per);
+        unsigned long long local = cur;
+        if (start < end) {
+            uint32_t h = unrank_colex(start, kh, rh, mh);
+            for (uint32_t idx = start; idx < end; ++idx) {
+                const uint32_t wh = mh.w8[0][h & 255u] + mh.w8[1][(h >> 8) & 255u] + mh.w8[2][(h >> 16) & 255u];
+                const uint64_t lw = local >> 32;
+                bool skip = (uint64_t)wh > lw || ((uint64_t)wh == lw && (h << L) > (uint32_t)local);
+                if (!skip) {
+                    uint32_t F = VL;
+                    for (uint32_t c = 0; c < n_kept; ++c) {
+                        if ((mh.khi[c] & h) == 0) {
+                            F &= mh.klo[c];
+                            if (!F) break;
+                        }
+                    }
+                    if (F)
+                        for (uint32_t c = 0; c < n_negk; ++c)
+                            if ((mh.nhi[c] & ~h) == 0) F &= ~mh.nlo[c];
+                    while (F) {
+                        const uint32_t l = __ffs(F) - 1u;
+                        F &= F - 1u;
+                        const unsigned long long key =
+                            ((unsigned long long)(wh + mh.wlo[l]) << 32) | (unsigned long long)((h << L) | l);
+                        if (key < local) local = key;
+                    }
+                }
+                if (idx + 1u < end) h = gosper_next(h);
+            }
+        }
+        if (local < cur) atomicMin(&sm.best, local);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const unsigned long long b = sm.best;
+        if (b == ~0ull) {
+            sm.sol_found = 0;
+        } else {
+            const uint32_t x = pdep32((uint32_t)b, R) | forced;
+            uint32_t wt = (uint32_t)(b >> 32);
+            for (uint32_t t = forced; t; t &= t - 1u) wt += w[__ffs(t) - 1u];
+            (void)n_vars;
+            sm.sol_found = 1;
+            sm.sol_mask = x;
+            sm.sol_weight = wt;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Loop steps (Algorithm 1)
+// ---------------------------------------------------------------------------
+
+// Clause list from the accumulated witnesses: same-block (i, j) -> slots in
+// [i, j-1]; cross-block (i, j) -> grid slots in [i, j-1] (GenerateClause).
+__device__ void build_clauses(Smem &sm) {
+    const DevProg &P = sm.prog;
+    const uint32_t S = P.n_stmts;
+    __syncthreads();
+    if (threadIdx.x == 0) sm.n_cl = 0;
+    __syncthreads();
+    for (uint32_t idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+        const uint32_t i = idx / S, j = idx - i * S;
+        if (j < i) continue;
+        const uint32_t rg = range_mask(i, j);
+        if ((sm.acc_intra[i] >> j) & 1u) sm.cl[atomicAdd(&sm.n_cl, 1u)] = rg;
+        if ((sm.acc_inter[i] >> j) & 1u) sm.cl[atomicAdd(&sm.n_cl, 1u)] = rg & P.grid_mask;
+    }
+    __syncthreads();
+}
+
+// Initial state: remove mode probes E; repair mode starts at MHS(empty) = E.
+__device__ void loop_init(Smem &sm, MhsSmem &mh, const gr_options &opts) {
+    const DevProg &P = sm.prog;
+    if (threadIdx.x == 0) {
+        sm.forced = P.mode == GR_MODE_REPAIR ? P.existing : 0u;
+        sm.forbidden = opts.grid_enabled ? 0u : P.grid_mask;
+        sm.max_iters = opts.max_iters == 0 ? GR_MAX_ITERS : min(opts.max_iters, (uint32_t)GR_MAX_ITERS);
+        sm.iters = 0;
+        sm.done = 0;
+        sm.status = GR_REPAIRED;
+        sm.access_pairs = 0;
+        sm.n_cl = 0;
+        sm.t_start = globaltimer();
+        sm.probe = P.mode == GR_MODE_REMOVE ? 1u : 0u;
+        sm.mask = P.existing;
+    }
+    if (threadIdx.x < 32) {
+        sm.acc_intra[threadIdx.x] = 0;
+        sm.acc_inter[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    if (P.mode != GR_MODE_REMOVE) {
+        mhs_solve(sm, mh, P.n_slots, P.weights, 0, nullptr, 0, sm.forced, sm.forbidden);
+        if (threadIdx.x == 0) {
+            if (sm.sol_found) {
+                sm.mask = sm.sol_mask;
+            } else {
+                sm.status = GR_UNREPAIRABLE;
+                sm.done = 1;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && !sm.done && sm.iters >= sm.max_iters) {
+        sm.status = GR_ITER_CAP;
+        sm.done = 1;
+    }
+    __syncthreads();
+}
+
+// After a check (witnesses in rows_*, diverge, pairs): record it, stop if the
+// proposed mask is clean, else add the clauses and solve for the next mask.
+__device__ void loop_step(Smem &sm, MhsSmem &mh) {
+    const DevProg &P = sm.prog;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sm.traj[sm.iters] = sm.mask;
+        sm.iters += 1;
+        sm.access_pairs += sm.pairs;
+        uint32_t any = sm.diverge;
+        for (uint32_t i = 0; i < P.n_stmts; ++i) any |= sm.rows_intra[i] | sm.rows_inter[i];
+        if (!any && !sm.probe) {
+            sm.status = GR_REPAIRED;
+            sm.done = 1;
+        } else {
+            sm.probe = 0;
+            for (uint32_t i = 0; i < P.n_stmts; ++i) {
+                sm.acc_intra[i] |= sm.rows_intra[i];
+                sm.acc_inter[i] |= sm.rows_inter[i];
+            }
+            sm.forbidden |= sm.diverge;
+        }
+    }
+    __syncthreads();
+    if (sm.done) return;
+    build_clauses(sm);
+    mhs_solve(sm, mh, P.n_slots, P.weights, sm.n_cl, nullptr, 0, sm.forced, sm.forbidden);
+    if (threadIdx.x == 0) {
+        if (!sm.sol_found) {
+            sm.status = GR_UNREPAIRABLE;
+            sm.done = 1;
+        } else {
+            sm.mask = sm.sol_mask;
+            if (sm.iters >= sm.max_iters) {
+                sm.status = GR_ITER_CAP;
+                sm.done = 1;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Bitonic sort of sm.cl padded to kClauseCap entries, then unique compaction
+// into out->clauses.
+__device__ void write_result(Smem &sm, gr_repair_result *out) {
+    const DevProg &P = sm.prog;
+    build_clauses(sm);
+    const uint32_t n = sm.n_cl;
+    for (uint32_t i = threadIdx.x + n; i < kClauseCap; i += blockDim.x) sm.cl[i] = 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t k = 2; k <= kClauseCap; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < kClauseCap; i += blockDim.x) {
+                const uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const uint32_t a = sm.cl[i], b = sm.cl[ixj];
+                    if ((a > b) == up) {
+                        sm.cl[i] = b;
+                        sm.cl[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // unique: position of element i = number of first occurrences before it
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t groups = kClauseCap / 32u;
+    for (uint32_t g = warp; g < groups; g += nw) {
+        const uint32_t i = g * 32u + lane;
+        const bool first = sm.cl[i] != 0xFFFFFFFFu && (i == 0 || sm.cl[i] != sm.cl[i - 1]);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
+        if (lane == 0) sm.scan[g] = __popc(bal);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = lane < groups ? sm.scan[lane] : 0u;
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane < groups) sm.scan[lane] = v;  // inclusive
+    }
+    __syncthreads();
+    const uint32_t n_unique = sm.scan[groups - 1];
+    for (uint32_t g = warp; g < groups; g += nw) {
+        const uint32_t i = g * 32u + lane;
+        const bool first = sm.cl[i] != 0xFFFFFFFFu && (i == 0 || sm.cl[i] != sm.cl[i - 1]);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
+        const uint32_t base = g ? sm.scan[g - 1] : 0u;
+        if (first) out->clauses[base + __popc(bal & ((1u << lane) - 1u))] = sm.cl[i];
+    }
+    for (uint32_t i = threadIdx.x + n_unique; i < GR_MAX_CLAUSES; i += blockDim.x) out->clauses[i] = 0;
+    for (uint32_t i = threadIdx.x; i < GR_MAX_ITERS; i += blockDim.x) out->traj[i] = i < sm.iters ? sm.traj[i] : 0u;
+    if (threadIdx.x == 0) {
+        const bool ok = sm.status == GR_REPAIRED;
+        const uint32_t m = ok ? sm.mask : 0u;
+        uint32_t wt = 0;
+        for (uint32_t t = m; t; t &= t - 1u) wt += P.weights[__ffs(t) - 1u];
+        out->status = (int32_t)sm.status;
+        out->mask = m;
+        out->weight = wt;
+        out->added = m & ~P.existing;
+        out->removed = ok ? (P.existing & ~m) : 0u;
+        out->iters = sm.iters;
+        out->n_clauses = n_unique;
+        out->forbidden = sm.forbidden;
+        out->_pad = 0;
+        out->access_pairs = sm.access_pairs;
+        out->t_start_ns = sm.t_start;
+        out->t_end_ns = globaltimer();
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+struct ArenaView {
+    const ArenaHeader *h;
+    const DevProg *progs;
+    const uint32_t *order;
+    const uint64_t *segbase;
+    const uint32_t *perm;
+};
+
+__device__ __forceinline__ ArenaView view(const uint8_t *arena) {
+    ArenaView v;
+    v.h = reinterpret_cast<const ArenaHeader *>(arena);
+    v.progs = reinterpret_cast<const DevProg *>(arena + v.h->progs_off);
+    v.order = reinterpret_cast<const uint32_t *>(arena + v.h->order_off);
+    v.segbase = reinterpret_cast<const uint64_t *>(arena + v.h->segbase_off);
+    v.perm = reinterpret_cast<const uint32_t *>(arena + v.h->perm_off);
+    return v;
+}
+
+// K0: one warp per (program, statement, block) segment of t_pad threads.
+__global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ arena, uint8_t *__restrict__ scratch) {
+    const ArenaView V = view(arena);
+    const uint32_t n = V.h->n_progs;
+    const uint64_t nseg = V.h->n_segments;
+    uint16_t *traces = reinterpret_cast<uint16_t *>(scratch + V.h->scratch_trace_off);
+    uint64_t *segmask = reinterpret_cast<uint64_t *>(scratch + V.h->scratch_segmask_off);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t seg = warp0; seg < nseg; seg += nwarps) {
+        uint32_t lo = 0, hi = n;  // last p with segbase[p] <= seg
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (V.segbase[mid] <= seg) lo = mid; else hi = mid;
+        }
+        const uint32_t p = lo;
+        const DevProg &P = V.progs[p];
+        const uint32_t local = (uint32_t)(seg - V.segbase[p]);
+        const uint32_t B = P.blocks, T = P.threads, tpad = P.t_pad;
+        const uint32_t s = local / B, blk = local - s * B;
+        const DevStmt st = P.stmts[s];
+        const uint32_t M = st.m;
+        const uint32_t base = (uint32_t)(((uint64_t)st.cm * blk + st.bm) % M);
+        const bool perm = st.kind == GR_PERM;
+        const uint32_t step = perm ? 1u : st.am;
+        uint16_t *out = traces + P.trace_off + ((size_t)s * B + blk) * tpad;
+        uint64_t chunks = 0;
+        for (uint32_t v = lane; v < (tpad >> 3); v += 32) {
+            const uint32_t t0 = v * 8u;
+            // x = (step * t + base) mod M, advanced by one thread at a time
+            uint32_t x = (uint32_t)(((uint64_t)step * t0 + base) % M);
+            uint32_t w4[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (uint32_t e = 0; e < 8; ++e) {
+                const uint32_t t = t0 + e;
+                uint32_t a = 0;
+                if (t < T) {
+                    a = perm ? V.perm[st.perm_off + x] : x;
+                    if (st.gk == 0 || t % st.gk == st.gr) chunks |= 1ull << (a >> kChunkShift);
+                }
+                w4[e >> 1] |= (a & 0xFFFFu) << ((e & 1u) * 16u);
+                x += step;
+                if (x >= M) x -= M;
+            }
+            reinterpret_cast<uint4 *>(out)[v] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        const uint32_t lo32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)chunks);
+        const uint32_t hi32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(chunks >> 32));
+        if (lane == 0) segmask[P.segmask_off + (size_t)s * B + blk] = ((uint64_t)hi32 << 32) | lo32;
+    }
+}
+
+struct Dyn {
+    Smem *sm;
+    uint16_t *tab;
+    MhsSmem *mh;
+};
+
+__device__ __forceinline__ Dyn dyn_smem() {
+    extern __shared__ uint4 dyn_raw[];
+    Dyn d;
+    d.sm = reinterpret_cast<Smem *>(dyn_raw);
+    d.tab = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(dyn_raw) + kFixedSmem);
+    d.mh = reinterpret_cast<MhsSmem *>(d.tab);
+    return d;
+}
+
+// K4: persistent repair.  CTAs take programs from a queue in the host's order
+// (largest first) and run Algorithm 1 on each.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_repair(const uint8_t *__restrict__ arena, uint32_t n, gr_options opts, uint8_t *__restrict__ scratch,
+             gr_repair_result *__restrict__ out, uint32_t table_bytes) {
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    const ArenaView V = view(arena);
+    const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
+    const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
+    uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
+    for (;;) {
+        if (threadIdx.x == 0) sm.item = atomicAdd(&ctrl[0], 1u);
+        __syncthreads();
+        const uint32_t item = sm.item;
+        if (item >= n) break;
+        const uint32_t p = V.order[item];
+        load_program(sm, &V.progs[p]);
+        const uint16_t *trace = traces + sm.prog.trace_off;
+        const uint64_t *sgm = segmask + sm.prog.segmask_off;
+        loop_init(sm, *d.mh, opts);
+        while (!sm.done) {
+            const uint32_t mask = sm.mask;
+            prepare_check(sm, mask);
+            check_misc(sm, mask);
+            check_blocks(sm, d.tab, table_bytes, trace, sgm, 0, sm.prog.blocks, true);
+            loop_step(sm, *d.mh);
+        }
+        write_result(sm, &out[p]);
+    }
+}
+
+// One check per program under masks[p] (persistent, same queue).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_check(const uint8_t *__restrict__ arena, uint32_t n, const uint32_t *__restrict__ masks,
+            uint8_t *__restrict__ scratch, gr_witnesses *__restrict__ out, uint32_t table_bytes) {
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    const ArenaView V = view(arena);
+    const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
+    const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
+    uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
+    for (;;) {
+        if (threadIdx.x == 0) sm.item = atomicAdd(&ctrl[0], 1u);
+        __syncthreads();
+        const uint32_t item = sm.item;
+        if (item >= n) break;
+        const uint32_t p = V.order[item];
+        load_program(sm, &V.progs[p]);
+        const uint32_t mask = masks[p];
+        prepare_check(sm, mask);
+        check_misc(sm, mask);
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off, 0,
+                     sm.prog.blocks, true);
+        if (threadIdx.x < 32) {
+            out[p].race_intra[threadIdx.x] = sm.rows_intra[threadIdx.x];
+            out[p].race_inter[threadIdx.x] = sm.rows_inter[threadIdx.x];
+        }
+        if (threadIdx.x == 0) {
+            out[p].diverge = sm.diverge;
+            out[p].n_stmts = sm.prog.n_stmts;
+            out[p].access_pairs = sm.pairs;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- plain path: one launch per stage ------------------------------------
+
+__device__ void state_to_smem(Smem &sm, const LoopState *st) {
+    if (threadIdx.x == 0) {
+        sm.mask = st->mask;
+        sm.probe = st->probe;
+        sm.done = st->done;
+        sm.status = st->status;
+        sm.iters = st->iters;
+        sm.forced = st->forced;
+        sm.forbidden = st->forbidden;
+        sm.max_iters = st->max_iters;
+        sm.access_pairs = st->access_pairs;
+        sm.t_start = st->t_start;
+    }
+    if (threadIdx.x < 32) {
+        sm.acc_intra[threadIdx.x] = st->acc_intra[threadIdx.x];
+        sm.acc_inter[threadIdx.x] = st->acc_inter[threadIdx.x];
+    }
+    for (uint32_t i = threadIdx.x; i < GR_MAX_ITERS; i += blockDim.x) sm.traj[i] = st->traj[i];
+    __syncthreads();
+}
+
+__device__ void state_from_smem(const Smem &sm, LoopState *st) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->mask = sm.mask;
+        st->probe = sm.probe;
+        st->done = sm.done;
+        st->status = sm.status;
+        st->iters = sm.iters;
+        st->forced = sm.forced;
+        st->forbidden = sm.forbidden;
+        st->max_iters = sm.max_iters;
+        st->access_pairs = sm.access_pairs;
+        st->t_start = sm.t_start;
+    }
+    if (threadIdx.x < 32) {
+        st->acc_intra[threadIdx.x] = sm.acc_intra[threadIdx.x];
+        st->acc_inter[threadIdx.x] = sm.acc_inter[threadIdx.x];
+    }
+    for (uint32_t i = threadIdx.x; i < GR_MAX_ITERS; i += blockDim.x) st->traj[i] = sm.traj[i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_plain_init(const uint8_t *__restrict__ arena, uint32_t p, gr_options opts, LoopState *st) {
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    const ArenaView V = view(arena);
+    load_program(sm, &V.progs[p]);
+    loop_init(sm, *d.mh, opts);
+    state_from_smem(sm, st);
+}
+
+// CTA b < B: same-block passes of block b; CTA B: cross-block pass, divergence
+// and the pair count.  Witness bits are OR-ed into wit (zeroed by the host).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_plain_check(const uint8_t *__restrict__ arena, uint32_t p, const uint8_t *__restrict__ scratch,
+                  const LoopState *__restrict__ st, gr_witnesses *wit, uint32_t table_bytes) {
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    const ArenaView V = view(arena);
+    const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
+    const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
+    load_program(sm, &V.progs[p]);
+    const uint32_t mask = st->mask;
+    prepare_check(sm, mask);
+    const uint32_t B = sm.prog.blocks;
+    const uint32_t b = blockIdx.x;
+    if (b < B) {
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off, b, b + 1,
+                     false);
+    } else {
+        check_misc(sm, mask);
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off, 0, 0,
+                     true);
+        if (threadIdx.x == 0) {
+            wit->diverge = sm.diverge;
+            wit->access_pairs = sm.pairs;
+            wit->n_stmts = sm.prog.n_stmts;
+        }
+    }
+    if (threadIdx.x < 32) {
+        if (sm.rows_intra[threadIdx.x]) atomicOr(&wit->race_intra[threadIdx.x], sm.rows_intra[threadIdx.x]);
+        if (sm.rows_inter[threadIdx.x]) atomicOr(&wit->race_inter[threadIdx.x], sm.rows_inter[threadIdx.x]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_plain_solve(const uint8_t *__restrict__ arena, uint32_t p, LoopState *st, const gr_witnesses *__restrict__ wit,
+                  gr_repair_result *out) {
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    const ArenaView V = view(arena);
+    load_program(sm, &V.progs[p]);
+    state_to_smem(sm, st);
+    if (!sm.done) {
+        if (threadIdx.x < 32) {
+            sm.rows_intra[threadIdx.x] = wit->race_intra[threadIdx.x];
+            sm.rows_inter[threadIdx.x] = wit->race_inter[threadIdx.x];
+        }
+        if (threadIdx.x == 0) {
+            sm.diverge = wit->diverge;
+            sm.pairs = wit->access_pairs;
+        }
+        __syncthreads();
+        loop_step(sm, *d.mh);
+    }
+    state_from_smem(sm, st);
+    if (sm.done) write_result(sm, out);
+}
+
+// gr_solve: in = [n_vars, n_pos, n_neg, forced, forbidden, w[24], pos..., neg...];
+// out = [found, mask, weight].
+__global__ void __launch_bounds__(kThreads, 1) k_solve(const uint32_t *__restrict__ in, uint32_t *__restrict__ out) {
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    MhsSmem &mh = *d.mh;
+    const uint32_t n_vars = in[0], n_pos = in[1], n_neg = in[2], forced = in[3], forbidden = in[4];
+    const uint32_t *w = in + 5;
+    for (uint32_t i = threadIdx.x; i < n_pos; i += blockDim.x) sm.cl[i] = in[5 + GR_MAX_SLOTS + i];
+    // negative clauses live after the positive ones in the mhs scratch
+    uint32_t *neg = mh.nlo;  // staging; mhs_solve reads neg[] before it writes nlo
+    for (uint32_t i = threadIdx.x; i < n_neg; i += blockDim.x) neg[i] = in[5 + GR_MAX_SLOTS + n_pos + i];
+    __shared__ uint32_t wsh[GR_MAX_SLOTS];
+    if (threadIdx.x < GR_MAX_SLOTS) wsh[threadIdx.x] = threadIdx.x < n_vars ? w[threadIdx.x] : 0u;
+    __syncthreads();
+    mhs_solve(sm, mh, n_vars, wsh, n_pos, neg, n_neg, forced, forbidden);
+    if (threadIdx.x == 0) {
+        out[0] = sm.sol_found;
+        out[1] = sm.sol_found ? sm.sol_mask : 0u;
+        out[2] = sm.sol_found ? sm.sol_weight : 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+
+static size_t dyn_bytes(uint32_t table_bytes) {
+    const size_t region = table_bytes > sizeof(MhsSmem) ? table_bytes : sizeof(MhsSmem);
+    return kFixedSmem + align_up(region, 16);
+}
+
+cudaError_t configure_kernels(uint32_t max_dynamic_smem) {
+    cudaError_t e;
+    const void *fns[] = {(const void *)k_repair, (const void *)k_check, (const void *)k_plain_init,
+                         (const void *)k_plain_check, (const void *)k_plain_solve, (const void *)k_solve};
+    for (const void *f : fns) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic_smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint32_t grid, cudaStream_t st) {
+    k_expand<<<grid, 256, 0, st>>>(static_cast<const uint8_t *>(d_arena), static_cast<uint8_t *>(d_scratch));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
+                          gr_repair_result *d_out, LaunchCfg cfg, cudaStream_t st) {
+    k_repair<<<cfg.grid, kThreads, dyn_bytes(cfg.table_bytes), st>>>(
+        static_cast<const uint8_t *>(d_arena), n, opts, static_cast<uint8_t *>(d_scratch), d_out, cfg.table_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
+                         gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st) {
+    k_check<<<cfg.grid, kThreads, dyn_bytes(cfg.table_bytes), st>>>(
+        static_cast<const uint8_t *>(d_arena), n, d_masks, static_cast<uint8_t *>(d_scratch), d_out,
+        cfg.table_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_init(const void *d_arena, uint32_t p, const gr_options &opts, LoopState *d_state,
+                              cudaStream_t st) {
+    k_plain_init<<<1, kThreads, dyn_bytes(kMinTableBytes), st>>>(static_cast<const uint8_t *>(d_arena), p, opts,
+                                                                  d_state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_check(const void *d_arena, uint32_t p, void *d_scratch, LoopState *d_state,
+                               gr_witnesses *d_wit, uint32_t n_blocks, uint32_t table_bytes, cudaStream_t st) {
+    k_plain_check<<<n_blocks + 1, kThreads, dyn_bytes(table_bytes), st>>>(
+        static_cast<const uint8_t *>(d_arena), p, static_cast<const uint8_t *>(d_scratch), d_state, d_wit,
+        table_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_solve(const void *d_arena, uint32_t p, LoopState *d_state, const gr_witnesses *d_wit,
+                               gr_repair_result *out, cudaStream_t st) {
+    k_plain_solve<<<1, kThreads, dyn_bytes(kMinTableBytes), st>>>(static_cast<const uint8_t *>(d_arena), p,
+                                                                   d_state, d_wit, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(const uint32_t *d_in, uint32_t *d_out, cudaStream_t st) {
+    k_solve<<<1, kThreads, dyn_bytes(kMinTableBytes), st>>>(d_in, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace gr

@@ -1,0 +1,167 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything here is integer and exact, so every comparison is bit-exact:
+witness bitmaps, divergence masks, access-pair counts, clause lists, masks,
+weights, trajectories and statuses."""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import load_golden, program_from_spec
+from _tiny import random_program
+from paper_2011_08373_gb300 import synth
+from paper_2011_08373_gb300.synth import MAP_AFFINE, MAP_STRIDED, SPACE_SHARED
+
+pytestmark = pytest.mark.gpu
+
+GOLD = load_golden("listings.json")
+RESULT_KEYS = ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses",
+               "forbidden", "access_pairs")
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_08373_gb300.build import build
+    from paper_2011_08373_gb300 import binding
+
+    build()
+    binding.lib()
+    return binding
+
+
+def _same_result(got, want, ctx=""):
+    for k in RESULT_KEYS:
+        assert got[k] == want[k], (ctx, k, got[k], want[k])
+
+
+@pytest.mark.parametrize("case", GOLD["cases"], ids=[c["name"] for c in GOLD["cases"]])
+def test_listings(gb, case):
+    p = program_from_spec(case["program"])
+    for chk in case["checks"]:
+        got = gb.check(p, chk["mask"])
+        assert got["intra"] == chk["intra"] and got["inter"] == chk["inter"]
+        assert got["diverge"] == chk["diverge"]
+        if "access_pairs" in chk:
+            assert got["access_pairs"] == chk["access_pairs"]
+    for exp in case["repairs"]:
+        for fn in (gb.repair, gb.repair_plain):
+            got = fn(p, mode=exp["mode"])
+            for key in ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses",
+                        "forbidden"):
+                assert got[key] == exp[key], (fn.__name__, key)
+
+
+def test_solver_paper_example(gb):
+    for case in GOLD["solver_cases"]:
+        got = gb.solve(case["n_vars"], case["weights"], case["pos"], case["neg"], case["forced"],
+                       case["forbidden"])
+        assert got == (case["expect"]["mask"], case["expect"]["weight"])
+
+
+def test_solver_random_vs_oracle(gb):
+    for seed in range(120):
+        rng = synth.SplitMix64(synth.program_seed(99, seed))
+        n = rng.randint(1, 24 if seed % 10 == 0 else 14)
+        full = (1 << n) - 1
+        w = [rng.randint(1, 1 << rng.randint(0, 12)) for _ in range(n)]
+        pos = [(rng.randint(1, full) & rng.randint(1, full)) or 1 for _ in range(rng.randint(0, 40))]
+        neg = [rng.randint(1, full) | rng.randint(1, full) for _ in range(rng.randint(0, 4))]
+        forced = rng.randint(0, full) & rng.randint(0, full) & rng.randint(0, full)
+        forbidden = rng.randint(0, full) & rng.randint(0, full) & rng.randint(0, full) & ~forced
+        got = gb.solve(n, w, pos, neg, forced, forbidden)
+        want = oracle.solve(n, w, pos, neg, forced, forbidden)
+        assert got == want, (seed, n)
+
+
+def test_tiny_checks_all_masks(gb):
+    progs, masks, refs = [], [], []
+    for seed in range(150):
+        p = random_program(10000 + seed, s_max=5, b_max=3, t_max=9, m_max=16)
+        for m in range(1 << p.n_slots):
+            progs.append(p)
+            masks.append(m)
+    got = gb.check_batch(progs, masks)
+    for p, m, g in zip(progs, masks, got):
+        assert g == oracle.check(p, m), m
+
+
+def test_tiny_repairs(gb):
+    progs = [random_program(20000 + seed, s_max=6, b_max=3, t_max=12, m_max=24) for seed in range(200)]
+    for grid_enabled in (True, False):
+        got = gb.repair_batch(progs, grid_enabled=grid_enabled)
+        for p, g in zip(progs, got):
+            _same_result(g, oracle.repair(p, grid_enabled=grid_enabled), p.mode)
+
+
+def test_iteration_cap(gb):
+    progs = [random_program(30000 + seed, s_min=4, s_max=8, b_max=2, t_max=16, m_max=24)
+             for seed in range(60)]
+    for cap in (1, 2):
+        got = gb.repair_batch(progs, max_iters=cap)
+        for p, g in zip(progs, got):
+            _same_result(g, oracle.repair(p, max_iters=cap))
+
+
+def test_medium_programs_all_paths(gb):
+    """Several chunks, ragged thread counts, guards and both array kinds."""
+    progs = [random_program(40000 + seed, s_min=6, s_max=14, b_min=1, b_max=4, t_min=20, t_max=200,
+                            m_max=3000, a_max=9, c_max=700) for seed in range(24)]
+    got = gb.repair_batch(progs)
+    for p, g in zip(progs, got):
+        want = oracle.repair(p)
+        _same_result(g, want)
+    for p in progs[:6]:
+        _same_result(gb.repair(p), oracle.repair(p))
+        _same_result(gb.repair_plain(p), oracle.repair(p))
+
+
+def test_single_workload(gb):
+    p = synth.generate("single_1x64_s8", 1)[0]
+    want = oracle.repair(p)
+    for fn in (gb.repair, gb.repair_plain):
+        _same_result(fn(p), want, fn.__name__)
+
+
+def test_batch_workload_sample_full_size(gb):
+    progs = synth.generate("batch1024_4x256_s24", 12)
+    want = oracle.repair_batch(progs, n_threads=12)
+    got = gb.repair_batch(progs)
+    for g, w in zip(got, want):
+        _same_result(g, w)
+
+
+def test_interblock_workload_reduced(gb):
+    progs = synth.generate("interblock256_64x256_s16", 8, blocks=6, threads=32, m_words=4096)
+    want = oracle.repair_batch(progs, n_threads=8)
+    got = gb.repair_batch(progs)
+    for g, w in zip(got, want):
+        _same_result(g, w)
+
+
+def test_uneven_workload_sample(gb):
+    progs = [p for p in synth.generate("uneven4096_mixed", 200) if p.blocks * p.threads <= 1200][:40]
+    want = oracle.repair_batch(progs, n_threads=16)
+    got = gb.repair_batch(progs)
+    for g, w in zip(got, want):
+        _same_result(g, w)
+
+
+def test_device_resident_matches_host_path(gb):
+    import torch
+
+    progs = synth.generate("uneven4096_mixed", 64)
+    host = gb.repair_batch(progs)
+    db = gb.DeviceBatch(progs)
+    db.run()
+    torch.cuda.synchronize()
+    dev = db.results()
+    for a, b in zip(host, dev):
+        _same_result(a, b)
+    db.run()  # a second launch on the same buffers gives the same results
+    torch.cuda.synchronize()
+    for a, b in zip(host, db.results()):
+        _same_result(a, b)
