@@ -105,7 +105,7 @@ size_t align_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
     size_t progs_off, order_off, segbase_off, perm_off, arena_bytes;
-    size_t segmask_off, trace_off, scratch_bytes;
+    size_t segmask_off, segrange_off, trace_off, scratch_bytes;
     uint64_t n_segments;
     std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
 };
@@ -134,7 +134,8 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     L.n_segments = seg_total;
     L.arena_bytes = align_to(L.perm_off + perm_total * 4, 256);
     L.segmask_off = 256;
-    L.trace_off = align_to(L.segmask_off + seg_total * 8, 256);
+    L.segrange_off = align_to(L.segmask_off + seg_total * 8, 256);
+    L.trace_off = align_to(L.segrange_off + seg_total * 4, 256);
     L.scratch_bytes = align_to(L.trace_off + trace_total * 2, 256);
     return L;
 }
@@ -162,6 +163,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     H->n_segments = L.n_segments;
     H->scratch_segmask_off = L.segmask_off;
     H->scratch_trace_off = L.trace_off;
+    H->scratch_segrange_off = L.segrange_off;
     H->scratch_bytes = L.scratch_bytes;
     DevProg *dp = reinterpret_cast<DevProg *>(arena + L.progs_off);
     uint32_t *order = reinterpret_cast<uint32_t *>(arena + L.order_off);
@@ -241,6 +243,7 @@ struct Workspace {
     std::mutex mu;
     bool configured = false;
     int sms = 0;
+    int smem_per_sm = 0;
     uint32_t max_dyn = 0;
     DeviceBuf arena, scratch, out, aux;
     std::vector<uint8_t> host_arena;
@@ -257,13 +260,13 @@ gr_status current_ws(Workspace **ws) {
     return GR_OK;
 }
 
-constexpr uint32_t kDefaultTableBytes = 96u * 1024u;
 
 gr_status ensure_configured(Workspace &ws) {
     if (ws.configured) return GR_OK;
     int dev = 0;
     GR_CUDA(cudaGetDevice(&dev));
     GR_CUDA(cudaDeviceGetAttribute(&ws.sms, cudaDevAttrMultiProcessorCount, dev));
+    GR_CUDA(cudaDeviceGetAttribute(&ws.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     int optin = 0;
     GR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     ws.max_dyn = (uint32_t)optin;
@@ -272,16 +275,22 @@ gr_status ensure_configured(Workspace &ws) {
     return GR_OK;
 }
 
-uint32_t dyn_bytes_for(uint32_t table_bytes) {
-    return (uint32_t)(fixed_smem_bytes() + align_to(std::max<size_t>(table_bytes, 48 * 1024), 16));
-}
-
 LaunchCfg choose_cfg(const Workspace &ws, uint32_t n) {
+    // Two CTAs per SM: the owner table takes what is left of half the SM's
+    // shared memory after the fixed part (1 KB per CTA is reserved).
     LaunchCfg c;
-    c.table_bytes = kDefaultTableBytes;
-    if (dyn_bytes_for(c.table_bytes) > ws.max_dyn) c.table_bytes = kMinTableBytes;
-    const uint32_t per_sm = std::max<uint32_t>(1u, (228u * 1024u) / (dyn_bytes_for(c.table_bytes) + 1024u));
-    c.grid = std::min<uint32_t>(n, (uint32_t)ws.sms * std::min<uint32_t>(per_sm, 2u));
+    const size_t half = (size_t)ws.smem_per_sm / 2;
+    const size_t fixed = fixed_smem_bytes() + 1024;
+    size_t table = half > fixed ? (half - fixed) / 2048 * 2048 : 0;
+    static_assert(kMinTableBytes >= 25u * 2u * kChunkWords, "one chunk for 25 rows");
+    if (table > 96u * 1024u) table = 96u * 1024u;
+    uint32_t per_sm = 2;
+    if (table < kMinTableBytes) {
+        table = kMinTableBytes;
+        per_sm = 1;
+    }
+    c.table_bytes = (uint32_t)table;
+    c.grid = std::min<uint32_t>(n, (uint32_t)ws.sms * per_sm);
     if (c.grid == 0) c.grid = 1;
     return c;
 }
@@ -298,6 +307,15 @@ gr_status upload_batch(Workspace &ws, const gr_program *progs, const gr_launch *
     if ((s = ws.scratch.ensure(L.scratch_bytes)) != GR_OK) return s;
     GR_CUDA(cudaMemcpyAsync(ws.arena.p, ws.host_arena.data(), L.arena_bytes, cudaMemcpyHostToDevice, st));
     *Lout = L;
+    return GR_OK;
+}
+
+// Wait for the stream, then report the kernels' device error word.
+gr_status finish_sync(void *d_scratch, cudaStream_t st) {
+    uint32_t err = 0;
+    GR_CUDA(cudaMemcpyAsync(&err, static_cast<uint32_t *>(d_scratch) + 1, 4, cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    if (err) return fail(GR_ECUDA, "device error word 0x%x (owner table too small)", err);
     return GR_OK;
 }
 
@@ -447,8 +465,7 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     GR_CUDA(launch_repair(ws->arena.p, n, opts_or_default(opts), ws->scratch.p,
                           static_cast<gr_repair_result *>(ws->out.p), choose_cfg(*ws, n), st));
     GR_CUDA(cudaMemcpyAsync(out, ws->out.p, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost, st));
-    GR_CUDA(cudaStreamSynchronize(st));
-    return GR_OK;
+    return finish_sync(ws->scratch.p, st);
 }
 
 gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches, const uint32_t *masks, uint32_t n,
@@ -476,8 +493,7 @@ gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches, con
     GR_CUDA(launch_check(ws->arena.p, n, static_cast<const uint32_t *>(ws->aux.p), ws->scratch.p,
                          static_cast<gr_witnesses *>(ws->out.p), choose_cfg(*ws, n), st));
     GR_CUDA(cudaMemcpyAsync(out, ws->out.p, (size_t)n * sizeof(gr_witnesses), cudaMemcpyDeviceToHost, st));
-    GR_CUDA(cudaStreamSynchronize(st));
-    return GR_OK;
+    return finish_sync(ws->scratch.p, st);
 }
 
 gr_status gr_check(const gr_program *prog, gr_launch launch, uint32_t mask, gr_witnesses *out) {

@@ -14,10 +14,13 @@ constexpr uint32_t kArenaMagic = 0x47525031u;  // "GRP1"
 constexpr uint32_t kThreads = 512;             // threads per CTA of the repair kernels
 constexpr uint32_t kChunkShift = 10;           // address chunk = 1,024 words
 constexpr uint32_t kChunkWords = 1u << kChunkShift;
+constexpr uint32_t kMaxTileChunks = 8;           // address chunks per owner-table tile
+constexpr uint32_t kSegCap = 512;                // (statement, block) segments listed per batch
 constexpr uint16_t kEmpty = 0xFFFFu;           // owner-table sentinels
 constexpr uint16_t kMulti = 0xFFFEu;
 constexpr uint32_t kClauseCap = 1024;          // clause buffer (>= 2 * 25 * 26 / 2)
 constexpr uint32_t kMinTableBytes = 25u * 2u * kChunkWords;  // one chunk for 25 rows
+constexpr uint32_t kErrTableTooSmall = 1u;  // bits of the device error word (scratch control word 1)
 
 // One statement, with map coefficients reduced modulo its array's size.
 struct DevStmt {
@@ -39,7 +42,7 @@ struct DevProg {
     uint32_t existing, grid_mask, write_mask, shared_rows;
     uint32_t global_rows, guarded_slots, _r1, _r2;
     uint64_t trace_off;    // u16 elements from the scratch trace base; layout [S][B][t_pad]
-    uint64_t segmask_off;  // u64 elements from the scratch segment-mask base; layout [S][B]
+    uint64_t segmask_off;  // element index of the program's [S][B] segment masks and ranges
     uint32_t weights[GR_MAX_SLOTS];
     uint16_t slot_gk[GR_MAX_SLOTS];
     uint16_t slot_gr[GR_MAX_SLOTS];
@@ -48,14 +51,15 @@ struct DevProg {
 static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");
 
 // Arena = ArenaHeader | DevProg[n] | order[n] | seg_base[n+1] | perm[]
-// Scratch = ctrl (256 B) | segmask u64[] | trace u16[]
+// Scratch = ctrl (256 B) | segmask u64[] | segrange u32[] | trace u16[]
 struct ArenaHeader {
     uint32_t magic, n_progs, _r0, _r1;
     uint64_t progs_off, order_off, segbase_off, perm_off;  // bytes from the arena start
     uint64_t n_segments;                                   // sum over programs of S*B
     uint64_t scratch_segmask_off, scratch_trace_off;       // bytes from the scratch start
     uint64_t scratch_bytes;
-    uint64_t _r2[6];
+    uint64_t scratch_segrange_off;
+    uint64_t _r2[5];
 };
 static_assert(sizeof(ArenaHeader) == 128, "ArenaHeader layout");
 

@@ -30,18 +30,18 @@ namespace gr {
 // ---------------------------------------------------------------------------
 
 struct MhsSmem {
+    uint32_t cl[kClauseCap];   // raw clause list (shares the table region: never live during a check)
     uint32_t pc[kClauseCap];   // preprocessed positive clauses (0 = dropped)
     uint32_t khi[kClauseCap];  // kept clauses: compact high part
     uint32_t klo[kClauseCap];  // kept clauses: low-part hit pattern over 32 low assignments
     uint32_t nraw[kClauseCap]; // negative clauses after preprocessing (0 = dropped)
     uint32_t nhi[kClauseCap];
     uint32_t nlo[kClauseCap];
-    uint32_t binom[25][25];
     uint32_t w8[3][256];       // weight of each byte of the high part
     uint32_t wlo[32];          // weight of each low assignment
     uint32_t lb[26];           // sum of the k smallest high weights
     uint32_t wc[GR_MAX_SLOTS]; // compact weights
-    uint32_t n_kept, n_negk, R, unsat;
+    uint32_t n_kept, n_negk, R, U, unsat;
 };
 
 struct Smem {
@@ -51,8 +51,13 @@ struct Smem {
     uint32_t acc_intra[32], acc_inter[32];
     uint32_t ph_intra[32], ph_inter[32];
     uint32_t traj[GR_MAX_ITERS];
-    uint32_t cl[kClauseCap];
     uint32_t row_list[32];
+    uint32_t pend_row[32];  // pending partners of each statement in the current pass
+    uint32_t n_seg_list, pass_rows;
+    uint32_t rlo[32], rhi[32], clo[32], chi[32];
+    uint32_t seg_list[kSegCap];
+    unsigned long long bchunk[2][64];
+    unsigned long long npair[2][325];  // per statement pair: same-block / cross-block thread pairs
     uint32_t scan[32];
     uint8_t chunk_slot[64];
     unsigned long long best;
@@ -64,10 +69,16 @@ struct Smem {
     uint32_t mask, probe, done, status, iters, forced, forbidden, max_iters;
     uint32_t diverge, n_cl, n_rows, item;
     uint32_t rel_sh, rel_gi, rel_gx, sol_found, sol_mask, sol_weight;
+    uint32_t *err;  // device error word (scratch control area)
 };
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 constexpr size_t kFixedSmem = align_up(sizeof(Smem), 16);
+
+// The clause list lives in the region the owner table uses during a check.
+__device__ __forceinline__ uint32_t *mh_cl(Smem &sm) {
+    return reinterpret_cast<MhsSmem *>(reinterpret_cast<uint8_t *>(&sm) + kFixedSmem)->cl;
+}
 
 size_t fixed_smem_bytes() { return kFixedSmem; }
 
@@ -121,6 +132,8 @@ __device__ __forceinline__ void or_row(uint32_t *rows, uint32_t i, uint32_t bits
 // Program load
 // ---------------------------------------------------------------------------
 
+__device__ void pair_counts(Smem &sm);
+
 __device__ void load_program(Smem &sm, const DevProg *gp) {
     const uint4 *src = reinterpret_cast<const uint4 *>(gp);
     uint4 *dst = reinterpret_cast<uint4 *>(&sm.prog);
@@ -138,6 +151,7 @@ __device__ void load_program(Smem &sm, const DevProg *gp) {
         if (lane == 0) sm.act[s][word] = bits;
     }
     __syncthreads();
+    pair_counts(sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -149,21 +163,70 @@ __device__ void load_program(Smem &sm, const DevProg *gp) {
 // The owner of an access is its tid (same-block pass, nb == 1) or its block
 // (cross-block pass).  Witness bits go to rows_out (row i, bit j >= i) for
 // pairs in one phase (ph) with at least one write.
+//
+// Only candidate pairs not yet in rows_out are pending, and only their
+// statements get a table row.  Chunks are processed in tiles of up to `cap`
+// chunks.  Per tile:
+//   clear — each row's owner entries over its own address range;
+//   build — pass 0 stores every access's owner, pass 1 turns an entry that sees
+//           another owner into MULTI (plain stores); only (statement, block)
+//           segments whose chunk mask meets the tile are read;
+//   probe — pass 2: an access (owner o, address a) of statement i and a pending
+//           partner j form a witness iff j's entry at a is neither empty nor
+//           o (a MULTI entry always differs; j == i is the self race).  Each
+//           thread probes its eight addresses per partner and skips partners
+//           already witnessed.
 template <bool kInter>
 __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const uint16_t *trace,
-                           uint32_t rows, uint32_t blk_lo, uint32_t nb, uint64_t chunks,
-                           const uint32_t *ph, uint32_t *rows_out) {
+                           const uint64_t *segmask, const uint32_t *segrange, uint32_t rows,
+                           uint32_t blk_lo, uint32_t nb, uint64_t chunks, const uint32_t *ph,
+                           uint32_t *rows_out) {
     const DevProg &P = sm.prog;
     const uint32_t S = P.n_stmts, B = P.blocks, tpad = P.t_pad, nv = tpad >> 3;
-    const uint32_t n_rows = __popc(rows);
-    if (n_rows == 0 || chunks == 0) return;  // uniform
-    __syncthreads();                          // row_list / chunk_slot reuse
-    if (threadIdx.x == 0) {
-        uint32_t n = 0;
-        for (uint32_t t = rows; t; t &= t - 1u) sm.row_list[n++] = __ffs(t) - 1u;
-    }
-    const uint32_t cap = table_bytes / (2u * S * kChunkWords);
+    if (rows == 0 || chunks == 0) return;  // uniform
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t wmask = P.write_mask;
+    __syncthreads();  // row_list / pending / ranges are reused across passes
+    if (warp == 0) {
+        const uint32_t i = lane;
+        const bool in = i < S && ((rows >> i) & 1u);
+        // pending candidate partners: j >= i in i's phase (a read only with a
+        // write), not yet witnessed
+        uint32_t pend = 0;
+        if (in) pend = rows & ph[i] & ~((1u << i) - 1u) & (((wmask >> i) & 1u) ? 0xFFFFFFFFu : wmask) & ~rows_out[i];
+        sm.pend_row[i] = pend;
+        // statements of pending pairs
+        uint32_t involved = pend | (pend ? (1u << i) : 0u);
+        for (uint32_t o = 16; o > 0; o >>= 1) involved |= __shfl_xor_sync(0xFFFFFFFFu, involved, o);
+        const bool keep = (involved >> i) & 1u;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if (keep) sm.row_list[__popc(bal & ((1u << lane) - 1u))] = i;
+        if (lane == 0) sm.pass_rows = involved;
+        sm.rlo[lane] = 0xFFFFu;
+        sm.rhi[lane] = 0u;
+    }
+    __syncthreads();
+    rows = sm.pass_rows;
+    const uint32_t n_rows = __popc(rows);
+    if (n_rows == 0) return;  // every candidate pair already witnessed
+    // address range of each row over the blocks of the pass
+    for (uint32_t u = threadIdx.x; u < S * nb; u += blockDim.x) {
+        const uint32_t st = u / nb, bi = u - st * nb;
+        if (!((rows >> st) & 1u)) continue;
+        const uint32_t r = segrange[(size_t)st * B + blk_lo + bi];
+        const uint32_t lo = r & 0xFFFFu, hi = r >> 16;
+        if (lo <= hi) {
+            atomicMin(&sm.rlo[st], lo);
+            atomicMax(&sm.rhi[st], hi);
+        }
+    }
+    const uint32_t cap = min(table_bytes / (2u * S * kChunkWords), kMaxTileChunks);
+    if (cap == 0) {  // the host sizes the table for at least one chunk; never loop without progress
+        if (threadIdx.x == 0) atomicOr(sm.err, kErrTableTooSmall);
+        return;
+    }
+    const uint32_t n_segs = n_rows * nb;
+    const bool one_batch = n_segs <= kSegCap;
     uint64_t pending = chunks;
     while (pending) {
         uint64_t sel = 0;
@@ -180,84 +243,143 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
             sm.chunk_slot[c] = ((sel >> c) & 1ull) ? (uint8_t)__popcll(sel & ((1ull << c) - 1ull)) : 0xFF;
         }
         __syncthreads();
-        // clear the rows in use
-        const uint32_t vpr = cols >> 3;
-        for (uint32_t u = threadIdx.x; u < n_rows * vpr; u += blockDim.x) {
-            const uint32_t r = u / vpr, v = u - r * vpr;
-            reinterpret_cast<uint4 *>(tab + (size_t)sm.row_list[r] * cols)[v] =
-                make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        // column range of each row within this tile (the tile keeps address order)
+        if (threadIdx.x < 32) {
+            const uint32_t st = threadIdx.x;
+            uint32_t c0 = 1, c1 = 0;
+            const uint32_t lo = sm.rlo[st], hi = sm.rhi[st];
+            if (st < S && ((rows >> st) & 1u) && lo <= hi) {
+                const uint32_t k0 = lo >> kChunkShift, k1 = hi >> kChunkShift;
+                for (uint32_t ch = k0; ch <= k1; ++ch) {
+                    if (sm.chunk_slot[ch] != 0xFF) {
+                        c0 = sm.chunk_slot[ch] * kChunkWords + (ch == k0 ? (lo & (kChunkWords - 1u)) : 0u);
+                        break;
+                    }
+                }
+                for (uint32_t ch = k1 + 1; ch-- > k0;) {
+                    if (sm.chunk_slot[ch] != 0xFF) {
+                        c1 = sm.chunk_slot[ch] * kChunkWords + (ch == k1 ? (hi & (kChunkWords - 1u)) : kChunkWords - 1u);
+                        break;
+                    }
+                }
+                if (c0 > c1) {
+                    c0 = 1;
+                    c1 = 0;
+                }
+            }
+            sm.clo[st] = c0;
+            sm.chi[st] = c1;
         }
         __syncthreads();
+        // clear each row over the word-aligned span of its column range
+        {
+            const uint32_t wpr = cols >> 1;  // words per row
+            for (uint32_t u = threadIdx.x; u < n_rows * wpr; u += blockDim.x) {
+                const uint32_t r = u / wpr, w = u - r * wpr;
+                const uint32_t st = sm.row_list[r];
+                if (sm.clo[st] <= sm.chi[st] && w >= (sm.clo[st] >> 1) && w <= (sm.chi[st] >> 1))
+                    reinterpret_cast<uint32_t *>(tab + (size_t)st * cols)[w] = 0xFFFFFFFFu;
+            }
+        }
         // pass 0: every access stores its owner (one of them wins);
-        // pass 1: an access that finds another owner stores MULTI.
-        const uint32_t units = n_rows * nb * nv;
-        for (uint32_t pass = 0; pass < 2; ++pass) {
-            for (uint32_t u = threadIdx.x; u < units; u += blockDim.x) {
-                const uint32_t v = u % nv;
-                const uint32_t rest = u / nv;
-                const uint32_t bi = rest % nb;
-                const uint32_t s = sm.row_list[rest / nb];
-                const uint32_t act8 = (sm.act[s][v >> 2] >> ((v & 3u) * 8u)) & 0xFFu;
-                if (!act8) continue;
-                const uint32_t blk = blk_lo + bi;
-                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(trace + ((size_t)s * B + blk) * tpad) + v);
-                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-                uint16_t *row = tab + (size_t)s * cols;
+        // pass 1: an access that finds another owner stores MULTI;
+        // pass 2: probe the pending partners.
+        uint4 held0 = make_uint4(0, 0, 0, 0), held1 = held0;
+        for (uint32_t pass = 0; pass < 3; ++pass) {
+            for (uint32_t base = 0; base < n_segs; base += kSegCap) {
+                if (pass == 0 || !one_batch) {
+                    // segments of this batch whose chunks meet the tile
+                    __syncthreads();
+                    if (threadIdx.x == 0) sm.n_seg_list = 0;
+                    __syncthreads();
+                    const uint32_t end = min(n_segs, base + kSegCap);
+                    for (uint32_t g = base + warp * 32u; g < end; g += nwarps * 32u) {
+                        const uint32_t u = g + lane;
+                        bool keep = false;
+                        uint32_t code = 0;
+                        if (u < end) {
+                            const uint32_t r = u / nb, bi = u - r * nb;
+                            const uint32_t st = sm.row_list[r];
+                            keep = (segmask[(size_t)st * B + blk_lo + bi] & sel) != 0;
+                            code = (st << 16) | bi;
+                        }
+                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+                        uint32_t at = 0;
+                        if (lane == 0 && bal) at = atomicAdd(&sm.n_seg_list, __popc(bal));
+                        at = __shfl_sync(0xFFFFFFFFu, at, 0);
+                        if (keep) sm.seg_list[at + __popc(bal & ((1u << lane) - 1u))] = code;
+                    }
+                }
+                __syncthreads();
+                const uint32_t units = sm.n_seg_list * nv;
+                const bool hold = one_batch && units <= 2u * blockDim.x;
+                uint32_t slot_i = 0;
+                for (uint32_t u = threadIdx.x; u < units; u += blockDim.x, ++slot_i) {
+                    const uint32_t code = sm.seg_list[u / nv];
+                    const uint32_t v = u % nv;
+                    const uint32_t st = code >> 16, blk = blk_lo + (code & 0xFFFFu);
+                    const uint32_t act8 = (sm.act[st][v >> 2] >> ((v & 3u) * 8u)) & 0xFFu;
+                    if (!act8) continue;
+                    uint32_t pend = 0;
+                    if (pass == 2) {
+                        pend = sm.pend_row[st] & ~*(volatile uint32_t *)&rows_out[st];
+                        if (!pend) continue;
+                    }
+                    uint4 q;
+                    if (pass > 0 && hold) {
+                        q = slot_i ? held1 : held0;
+                    } else {
+                        q = __ldg(reinterpret_cast<const uint4 *>(trace + ((size_t)st * B + blk) * tpad) + v);
+                        if (slot_i) held1 = q; else held0 = q;
+                    }
+                    const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+                    if (pass < 2) {
+                        uint16_t *row = tab + (size_t)st * cols;
 #pragma unroll
-                for (uint32_t e = 0; e < 8; ++e) {
-                    if (!((act8 >> e) & 1u)) continue;
-                    const uint32_t a = (w4[e >> 1] >> ((e & 1u) * 16u)) & 0xFFFFu;
-                    const uint32_t slot = sm.chunk_slot[a >> kChunkShift];
-                    if (slot == 0xFFu) continue;
-                    const uint32_t idx = slot * kChunkWords + (a & (kChunkWords - 1u));
-                    const uint16_t owner = kInter ? (uint16_t)blk : (uint16_t)(v * 8u + e);
-                    if (pass == 0) {
-                        row[idx] = owner;
-                    } else if (row[idx] != owner) {
-                        row[idx] = kMulti;
+                        for (uint32_t e = 0; e < 8; ++e) {
+                            if (!((act8 >> e) & 1u)) continue;
+                            const uint32_t a = (w4[e >> 1] >> ((e & 1u) * 16u)) & 0xFFFFu;
+                            const uint32_t slot = sm.chunk_slot[a >> kChunkShift];
+                            if (slot == 0xFFu) continue;
+                            const uint32_t idx = slot * kChunkWords + (a & (kChunkWords - 1u));
+                            const uint16_t owner = kInter ? (uint16_t)blk : (uint16_t)(v * 8u + e);
+                            if (pass == 0) {
+                                row[idx] = owner;
+                            } else if (row[idx] != owner) {
+                                row[idx] = kMulti;
+                            }
+                        }
+                    } else {
+                        uint32_t col[8];
+#pragma unroll
+                        for (uint32_t e = 0; e < 8; ++e) {
+                            const uint32_t a = (w4[e >> 1] >> ((e & 1u) * 16u)) & 0xFFFFu;
+                            const uint32_t slot = sm.chunk_slot[a >> kChunkShift];
+                            col[e] = (((act8 >> e) & 1u) && slot != 0xFFu)
+                                         ? slot * kChunkWords + (a & (kChunkWords - 1u)) : 0xFFFFFFFFu;
+                        }
+                        for (uint32_t jt = pend; jt; jt &= jt - 1u) {
+                            const uint32_t j = __ffs(jt) - 1u;
+                            if ((*(volatile uint32_t *)&rows_out[st] >> j) & 1u) continue;
+                            const uint32_t c0 = sm.clo[j], c1 = sm.chi[j];
+                            const uint16_t *rj = tab + (size_t)j * cols;
+                            bool hit = false;
+#pragma unroll
+                            for (uint32_t e = 0; e < 8; ++e) {
+                                const uint32_t c = col[e];
+                                if (c >= c0 && c <= c1) {  // j's entries outside its range are stale
+                                    const uint32_t o = rj[c];
+                                    const uint32_t mine = kInter ? blk : (v * 8u + e);
+                                    hit |= o != kEmpty && o != mine;
+                                }
+                            }
+                            if (hit) atomicOr(&rows_out[st], 1u << j);
+                        }
                     }
                 }
             }
             __syncthreads();
         }
-        // scan: per address, the statements touching it and their owners
-        for (uint32_t col = threadIdx.x; col < cols; col += blockDim.x) {
-            uint32_t tm = 0;
-            for (uint32_t r = 0; r < n_rows; ++r) {
-                const uint32_t s = sm.row_list[r];
-                if (tab[(size_t)s * cols + col] != kEmpty) tm |= 1u << s;
-            }
-            if (!tm) continue;
-            if ((tm & (tm - 1u)) == 0) {  // one statement: only a self race is possible
-                const uint32_t s = __ffs(tm) - 1u;
-                if (((wmask >> s) & 1u) && tab[(size_t)s * cols + col] == kMulti) or_row(rows_out, s, 1u << s);
-                continue;
-            }
-            const uint16_t first = tab[(size_t)(__ffs(tm) - 1u) * cols + col];
-            bool uniform = first != kMulti;
-            for (uint32_t t = tm & (tm - 1u); t && uniform; t &= t - 1u)
-                if (tab[(size_t)(__ffs(t) - 1u) * cols + col] != first) uniform = false;
-            if (uniform) continue;  // one owner for every access: no race here
-            for (uint32_t it = tm; it; it &= it - 1u) {
-                const uint32_t i = __ffs(it) - 1u;
-                const uint16_t oi = tab[(size_t)i * cols + col];
-                uint32_t conf;
-                if (oi == kMulti) {
-                    conf = tm;
-                } else {
-                    uint32_t same = 0;
-                    for (uint32_t jt = tm; jt; jt &= jt - 1u) {
-                        const uint32_t j = __ffs(jt) - 1u;
-                        if (tab[(size_t)j * cols + col] == oi) same |= 1u << j;
-                    }
-                    conf = tm & ~same;
-                }
-                conf &= ph[i] & ~((1u << i) - 1u);
-                if (!((wmask >> i) & 1u)) conf &= wmask;
-                if (conf) or_row(rows_out, i, conf);
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -301,11 +423,48 @@ __device__ void prepare_check(Smem &sm, uint32_t mask) {
     __syncthreads();
 }
 
+__device__ __forceinline__ uint32_t tri_index(uint32_t i, uint32_t j, uint32_t S) {  // i <= j < S
+    return i * S - (i * (i - 1u)) / 2u + (j - i);
+}
+
+// Thread pairs of each statement pair (i <= j, one space, a write): same-block
+// and cross-block, independent of the mask; computed once per program.
+__device__ void pair_counts(Smem &sm) {
+    const DevProg &P = sm.prog;
+    const uint32_t S = P.n_stmts;
+    const uint64_t B = P.blocks;
+    for (uint32_t idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
+        const uint32_t i = idx / S, j = idx - i * S;
+        if (j < i) continue;
+        const DevStmt &a = P.stmts[i], &b = P.stmts[j];
+        uint64_t same = 0, cross = 0;
+        if (a.space == b.space && (a.op == GR_W || b.op == GR_W)) {
+            uint64_t ni = 0, nj = 0, nij = 0;
+            for (uint32_t w = 0; w < 32; ++w) {
+                ni += __popc(sm.act[i][w]);
+                nj += __popc(sm.act[j][w]);
+                nij += __popc(sm.act[i][w] & sm.act[j][w]);
+            }
+            const bool global = a.space == GR_GLOBAL;
+            if (i < j) {
+                same = B * (ni * nj - nij);
+                cross = global ? B * (B - 1) * ni * nj : 0;
+            } else {
+                same = B * (ni * (ni - 1) / 2);
+                cross = global ? (B * (B - 1) / 2) * ni * ni : 0;
+            }
+        }
+        const uint32_t t = tri_index(i, j, S);
+        sm.npair[0][t] = same;
+        sm.npair[1][t] = cross;
+    }
+    __syncthreads();
+}
+
 // Divergence (closed form over tid in [0, T)) and the access-pair count.
 __device__ void check_misc(Smem &sm, uint32_t mask) {
     const DevProg &P = sm.prog;
     const uint32_t S = P.n_stmts, T = P.threads;
-    const uint64_t B = P.blocks;
     if (threadIdx.x == 0) {
         uint32_t dv = 0;
         for (uint32_t t = mask & P.guarded_slots; t; t &= t - 1u) {
@@ -320,56 +479,59 @@ __device__ void check_misc(Smem &sm, uint32_t mask) {
     for (uint32_t idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
         const uint32_t i = idx / S, j = idx - i * S;
         if (j < i) continue;
-        const DevStmt &a = P.stmts[i], &b = P.stmts[j];
-        if (a.space != b.space || (a.op != GR_W && b.op != GR_W)) continue;
-        uint64_t ni = 0, nj = 0, nij = 0;
-        for (uint32_t w = 0; w < 32; ++w) {
-            ni += __popc(sm.act[i][w]);
-            nj += __popc(sm.act[j][w]);
-            nij += __popc(sm.act[i][w] & sm.act[j][w]);
-        }
         const uint32_t rg = range_mask(i, j);
-        const bool open_same = (mask & rg) == 0;
-        const bool open_cross = a.space == GR_GLOBAL && (mask & P.grid_mask & rg) == 0;
-        if (i < j) {
-            if (open_same) local += B * (ni * nj - nij);
-            if (open_cross) local += B * (B - 1) * ni * nj;
-        } else {
-            local += B * (ni * (ni - 1) / 2);
-            if (a.space == GR_GLOBAL) local += (B * (B - 1) / 2) * ni * ni;
-        }
+        const uint32_t t = tri_index(i, j, S);
+        if ((mask & rg) == 0) local += sm.npair[0][t];
+        if ((mask & P.grid_mask & rg) == 0) local += sm.npair[1][t];
     }
-    if (local) atomicAdd(&sm.pairs, local);
+    for (uint32_t o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xFFFFFFFFu, local, o);
+    if ((threadIdx.x & 31u) == 0 && local) atomicAdd(&sm.pairs, local);
 }
 
 // Same-block passes for blocks [b0, b1) and, if requested, the cross-block pass.
 __device__ void check_blocks(Smem &sm, uint16_t *tab, uint32_t table_bytes, const uint16_t *trace,
-                             const uint64_t *segmask, uint32_t b0, uint32_t b1, bool inter) {
+                             const uint64_t *segmask, const uint32_t *segrange, uint32_t b0, uint32_t b1,
+                             bool inter) {
     const DevProg &P = sm.prog;
-    const uint32_t B = P.blocks;
+    const uint32_t B = P.blocks, S = P.n_stmts;
+    const bool cached = b1 - b0 <= 64;
+    if (cached) {  // chunk masks of every block of the range, OR-reduced in parallel
+        __syncthreads();
+        for (uint32_t u = threadIdx.x; u < 128; u += blockDim.x) (&sm.bchunk[0][0])[u] = 0;
+        __syncthreads();
+        const uint32_t nb = b1 - b0;
+        for (uint32_t u = threadIdx.x; u < S * nb; u += blockDim.x) {
+            const uint32_t s = u / nb, bi = u - s * nb;
+            const uint32_t bit = 1u << s;
+            if (!((sm.rel_sh | sm.rel_gi) & bit)) continue;
+            const uint64_t m = segmask[(size_t)s * B + b0 + bi];
+            if (m) atomicOr(&sm.bchunk[(sm.rel_sh & bit) ? 0 : 1][bi], m);
+        }
+        __syncthreads();
+    }
     for (uint32_t blk = b0; blk < b1; ++blk) {
         if (sm.rel_sh) {
-            const uint64_t ch = block_chunks(segmask, B, sm.rel_sh, blk);
-            owner_pass<false>(sm, tab, table_bytes, trace, sm.rel_sh, blk, 1, ch, sm.ph_intra, sm.rows_intra);
+            const uint64_t ch = cached ? sm.bchunk[0][blk - b0] : block_chunks(segmask, B, sm.rel_sh, blk);
+            owner_pass<false>(sm, tab, table_bytes, trace, segmask, segrange, sm.rel_sh, blk, 1, ch, sm.ph_intra,
+                              sm.rows_intra);
         }
         if (sm.rel_gi) {
-            const uint64_t ch = block_chunks(segmask, B, sm.rel_gi, blk);
-            owner_pass<false>(sm, tab, table_bytes, trace, sm.rel_gi, blk, 1, ch, sm.ph_intra, sm.rows_intra);
+            const uint64_t ch = cached ? sm.bchunk[1][blk - b0] : block_chunks(segmask, B, sm.rel_gi, blk);
+            owner_pass<false>(sm, tab, table_bytes, trace, segmask, segrange, sm.rel_gi, blk, 1, ch, sm.ph_intra,
+                              sm.rows_intra);
         }
     }
     if (inter && sm.rel_gx) {
         __syncthreads();
         unsigned long long m = 0;
-        const uint32_t nr = __popc(sm.rel_gx);
-        for (uint32_t u = threadIdx.x; u < nr * B; u += blockDim.x) {
-            const uint32_t r = u / B, blk = u - r * B;
-            uint32_t t = sm.rel_gx;
-            for (uint32_t q = 0; q < r; ++q) t &= t - 1u;
-            m |= segmask[(size_t)(__ffs(t) - 1u) * B + blk];
+        for (uint32_t u = threadIdx.x; u < S * B; u += blockDim.x) {
+            const uint32_t st = u / B;
+            if ((sm.rel_gx >> st) & 1u) m |= segmask[u];
         }
         if (m) atomicOr(&sm.chunk_acc, m);
         __syncthreads();
-        owner_pass<true>(sm, tab, table_bytes, trace, sm.rel_gx, 0, B, sm.chunk_acc, sm.ph_inter, sm.rows_inter);
+        owner_pass<true>(sm, tab, table_bytes, trace, segmask, segrange, sm.rel_gx, 0, B, sm.chunk_acc, sm.ph_inter,
+                         sm.rows_inter);
     }
     __syncthreads();
 }
@@ -378,13 +540,24 @@ __device__ void check_blocks(Smem &sm, uint16_t *tab, uint32_t table_bytes, cons
 // Exact minimum-weight hitting set
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t unrank_colex(uint32_t rank, uint32_t k, uint32_t n, const MhsSmem &mh) {
+struct BinomTable {
+    uint32_t v[25][25];
+    constexpr BinomTable() : v() {
+        for (int n = 0; n < 25; ++n) {
+            v[n][0] = 1;
+            for (int k = 1; k <= n; ++k) v[n][k] = v[n - 1][k - 1] + (k <= n - 1 ? v[n - 1][k] : 0);
+        }
+    }
+};
+__constant__ BinomTable c_binom = BinomTable();
+
+__device__ __forceinline__ uint32_t unrank_colex(uint32_t rank, uint32_t k, uint32_t n) {
     uint32_t h = 0;
     int c = (int)n - 1;
     for (uint32_t i = k; i >= 1; --i) {
-        while (c >= 0 && mh.binom[c][i] > rank) --c;
+        while (c >= 0 && c_binom.v[c][i] > rank) --c;
         h |= 1u << c;
-        rank -= mh.binom[c][i];
+        rank -= c_binom.v[c][i];
         --c;
     }
     return h;
@@ -397,7 +570,7 @@ __device__ __forceinline__ uint32_t gosper_next(uint32_t h) {
 }
 
 // Least (weight, mask) with forced <= mask, mask & forbidden == 0, hitting
-// every clause of sm.cl[0..n_cl) and containing no negative clause neg[0..n_neg).
+// every clause of mh_cl(sm)[0..n_cl) and containing no negative clause neg[0..n_neg).
 // Result in sm.sol_found / sol_mask / sol_weight.  All threads must call.
 __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t *w, uint32_t n_cl,
                           const uint32_t *neg, uint32_t n_neg, uint32_t forced, uint32_t forbidden) {
@@ -407,27 +580,19 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
         mh.n_kept = 0;
         mh.n_negk = 0;
         mh.R = 0;
+        mh.U = 0;
         mh.unsat = (forced & forbidden) ? 1u : 0u;
         sm.best = ~0ull;
     }
     __syncthreads();
     for (uint32_t i = tid; i < n_cl; i += nt) {
-        const uint32_t c = sm.cl[i];
+        const uint32_t c = mh_cl(sm)[i];
         uint32_t pc = 0;
         if (!(c & forced)) {
             pc = c & ~forbidden;
             if (!pc) mh.unsat = 1;
         }
         mh.pc[i] = pc;
-    }
-    for (uint32_t i = tid; i < n_neg; i += nt) {
-        const uint32_t N = neg[i];
-        uint32_t v = 0;
-        if (!(N & forbidden)) {
-            v = N & ~forced;
-            if (!v) mh.unsat = 1;
-        }
-        mh.nraw[i] = v;
     }
     __syncthreads();
     if (mh.unsat) {
@@ -445,35 +610,43 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
             if (d && j != i && (d & ~c) == 0 && (d != c || j < i)) keep = false;
         }
         if (keep) {
-            const uint32_t k = atomicAdd(&mh.n_kept, 1u);
-            mh.khi[k] = c;
-            atomicOr(&mh.R, c);
+            if ((c & (c - 1u)) == 0) {
+                atomicOr(&mh.U, c);  // unit clause: its slot is on in every solution
+            } else {
+                const uint32_t k = atomicAdd(&mh.n_kept, 1u);
+                mh.khi[k] = c;
+                atomicOr(&mh.R, c);
+            }
         }
     }
     __syncthreads();
+    // a kept clause never contains a unit's slot (the unit subsumes it), so the
+    // units join the forced set and the search runs over the other variables
+    forced |= mh.U;
     const uint32_t R = mh.R;
     // variables outside every clause stay off; a negative clause with such a
-    // variable can never be violated
+    // variable can never be violated; one inside the forced set always is
     for (uint32_t i = tid; i < n_neg; i += nt) {
-        const uint32_t N = mh.nraw[i];
-        if (N && (N & ~R) == 0) {
+        const uint32_t N = neg[i];
+        if (N & forbidden) continue;
+        const uint32_t v = N & ~forced;
+        if (!v) {
+            mh.unsat = 1;
+        } else if ((v & ~R) == 0) {
             const uint32_t k = atomicAdd(&mh.n_negk, 1u);
-            mh.nhi[k] = N;
+            mh.nhi[k] = v;
         }
+    }
+    __syncthreads();
+    if (mh.unsat) {
+        if (tid == 0) sm.sol_found = 0;
+        __syncthreads();
+        return;
     }
     const uint32_t r = __popc(R);
     const uint32_t L = r < 5 ? r : 5;
     const uint32_t rh = r - L;
     const uint32_t lomask = (1u << L) - 1u;
-    for (uint32_t i = tid; i < 25 * 25; i += nt) {
-        const uint32_t n = i / 25, k = i - n * 25;
-        uint64_t c = 0;
-        if (k <= n) {
-            c = 1;
-            for (uint32_t q = 1; q <= k; ++q) c = c * (n - k + q) / q;
-        }
-        mh.binom[n][k] = (uint32_t)c;
-    }
     if (tid < GR_MAX_SLOTS) {
         uint32_t v = 0;
         if (tid < r) {
@@ -541,13 +714,13 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
     for (uint32_t kh = 0; kh <= rh; ++kh) {
         const unsigned long long cur = *(volatile unsigned long long *)&sm.best;
         if (cur != ~0ull && (unsigned long long)mh.lb[kh] > (cur >> 32)) break;  // uniform
-        const uint32_t total = mh.binom[rh][kh];
+        const uint32_t total = c_binom.v[rh][kh];
         const uint32_t per = (total + nt - 1u) / nt;
         const uint32_t start = tid * per;
         const uint32_t end = min(total, start + per);
         unsigned long long local = cur;
         if (start < end) {
-            uint32_t h = unrank_colex(start, kh, rh, mh);
+            uint32_t h = unrank_colex(start, kh, rh);
             for (uint32_t idx = start; idx < end; ++idx) {
                 const uint32_t wh = mh.w8[0][h & 255u] + mh.w8[1][(h >> 8) & 255u] + mh.w8[2][(h >> 16) & 255u];
                 const uint64_t lw = local >> 32;
@@ -610,8 +783,8 @@ __device__ void build_clauses(Smem &sm) {
         const uint32_t i = idx / S, j = idx - i * S;
         if (j < i) continue;
         const uint32_t rg = range_mask(i, j);
-        if ((sm.acc_intra[i] >> j) & 1u) sm.cl[atomicAdd(&sm.n_cl, 1u)] = rg;
-        if ((sm.acc_inter[i] >> j) & 1u) sm.cl[atomicAdd(&sm.n_cl, 1u)] = rg & P.grid_mask;
+        if ((sm.acc_intra[i] >> j) & 1u) mh_cl(sm)[atomicAdd(&sm.n_cl, 1u)] = rg;
+        if ((sm.acc_inter[i] >> j) & 1u) mh_cl(sm)[atomicAdd(&sm.n_cl, 1u)] = rg & P.grid_mask;
     }
     __syncthreads();
 }
@@ -704,18 +877,20 @@ __device__ void write_result(Smem &sm, gr_repair_result *out) {
     const DevProg &P = sm.prog;
     build_clauses(sm);
     const uint32_t n = sm.n_cl;
-    for (uint32_t i = threadIdx.x + n; i < kClauseCap; i += blockDim.x) sm.cl[i] = 0xFFFFFFFFu;
+    uint32_t np2 = 32;
+    while (np2 < n) np2 <<= 1;
+    for (uint32_t i = threadIdx.x + n; i < kClauseCap; i += blockDim.x) mh_cl(sm)[i] = 0xFFFFFFFFu;
     __syncthreads();
-    for (uint32_t k = 2; k <= kClauseCap; k <<= 1) {
+    for (uint32_t k = 2; k <= np2; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < kClauseCap; i += blockDim.x) {
+            for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
                 const uint32_t ixj = i ^ j;
                 if (ixj > i) {
                     const bool up = (i & k) == 0;
-                    const uint32_t a = sm.cl[i], b = sm.cl[ixj];
+                    const uint32_t a = mh_cl(sm)[i], b = mh_cl(sm)[ixj];
                     if ((a > b) == up) {
-                        sm.cl[i] = b;
-                        sm.cl[ixj] = a;
+                        mh_cl(sm)[i] = b;
+                        mh_cl(sm)[ixj] = a;
                     }
                 }
             }
@@ -724,10 +899,10 @@ __device__ void write_result(Smem &sm, gr_repair_result *out) {
     }
     // unique: position of element i = number of first occurrences before it
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t groups = kClauseCap / 32u;
+    const uint32_t groups = np2 / 32u;
     for (uint32_t g = warp; g < groups; g += nw) {
         const uint32_t i = g * 32u + lane;
-        const bool first = sm.cl[i] != 0xFFFFFFFFu && (i == 0 || sm.cl[i] != sm.cl[i - 1]);
+        const bool first = mh_cl(sm)[i] != 0xFFFFFFFFu && (i == 0 || mh_cl(sm)[i] != mh_cl(sm)[i - 1]);
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
         if (lane == 0) sm.scan[g] = __popc(bal);
     }
@@ -738,16 +913,16 @@ __device__ void write_result(Smem &sm, gr_repair_result *out) {
             const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
             if (lane >= o) v += t;
         }
-        if (lane < groups) sm.scan[lane] = v;  // inclusive
+        sm.scan[lane] = v;  // inclusive; lanes beyond the groups repeat the total
     }
     __syncthreads();
     const uint32_t n_unique = sm.scan[groups - 1];
     for (uint32_t g = warp; g < groups; g += nw) {
         const uint32_t i = g * 32u + lane;
-        const bool first = sm.cl[i] != 0xFFFFFFFFu && (i == 0 || sm.cl[i] != sm.cl[i - 1]);
+        const bool first = mh_cl(sm)[i] != 0xFFFFFFFFu && (i == 0 || mh_cl(sm)[i] != mh_cl(sm)[i - 1]);
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
         const uint32_t base = g ? sm.scan[g - 1] : 0u;
-        if (first) out->clauses[base + __popc(bal & ((1u << lane) - 1u))] = sm.cl[i];
+        if (first) out->clauses[base + __popc(bal & ((1u << lane) - 1u))] = mh_cl(sm)[i];
     }
     for (uint32_t i = threadIdx.x + n_unique; i < GR_MAX_CLAUSES; i += blockDim.x) out->clauses[i] = 0;
     for (uint32_t i = threadIdx.x; i < GR_MAX_ITERS; i += blockDim.x) out->traj[i] = i < sm.iters ? sm.traj[i] : 0u;
@@ -801,6 +976,7 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
     const uint64_t nseg = V.h->n_segments;
     uint16_t *traces = reinterpret_cast<uint16_t *>(scratch + V.h->scratch_trace_off);
     uint64_t *segmask = reinterpret_cast<uint64_t *>(scratch + V.h->scratch_segmask_off);
+    uint32_t *segrange = reinterpret_cast<uint32_t *>(scratch + V.h->scratch_segrange_off);
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -822,6 +998,7 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
         const uint32_t step = perm ? 1u : st.am;
         uint16_t *out = traces + P.trace_off + ((size_t)s * B + blk) * tpad;
         uint64_t chunks = 0;
+        uint32_t amin = 0xFFFFu, amax = 0;
         for (uint32_t v = lane; v < (tpad >> 3); v += 32) {
             const uint32_t t0 = v * 8u;
             // x = (step * t + base) mod M, advanced by one thread at a time
@@ -833,7 +1010,11 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
                 uint32_t a = 0;
                 if (t < T) {
                     a = perm ? V.perm[st.perm_off + x] : x;
-                    if (st.gk == 0 || t % st.gk == st.gr) chunks |= 1ull << (a >> kChunkShift);
+                    if (st.gk == 0 || t % st.gk == st.gr) {
+                        chunks |= 1ull << (a >> kChunkShift);
+                        amin = min(amin, a);
+                        amax = max(amax, a);
+                    }
                 }
                 w4[e >> 1] |= (a & 0xFFFFu) << ((e & 1u) * 16u);
                 x += step;
@@ -843,7 +1024,12 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
         }
         const uint32_t lo32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)chunks);
         const uint32_t hi32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(chunks >> 32));
-        if (lane == 0) segmask[P.segmask_off + (size_t)s * B + blk] = ((uint64_t)hi32 << 32) | lo32;
+        amin = __reduce_min_sync(0xFFFFFFFFu, amin);
+        amax = __reduce_max_sync(0xFFFFFFFFu, amax);
+        if (lane == 0) {
+            segmask[P.segmask_off + (size_t)s * B + blk] = ((uint64_t)hi32 << 32) | lo32;
+            segrange[P.segmask_off + (size_t)s * B + blk] = amin | (amax << 16);  // empty: min > max
+        }
     }
 }
 
@@ -864,7 +1050,7 @@ __device__ __forceinline__ Dyn dyn_smem() {
 
 // K4: persistent repair.  CTAs take programs from a queue in the host's order
 // (largest first) and run Algorithm 1 on each.
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_repair(const uint8_t *__restrict__ arena, uint32_t n, gr_options opts, uint8_t *__restrict__ scratch,
              gr_repair_result *__restrict__ out, uint32_t table_bytes) {
     Dyn d = dyn_smem();
@@ -872,7 +1058,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const ArenaView V = view(arena);
     const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
     const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
+    const uint32_t *segrange = reinterpret_cast<const uint32_t *>(scratch + V.h->scratch_segrange_off);
     uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
+    if (threadIdx.x == 0) sm.err = &ctrl[1];
     for (;;) {
         if (threadIdx.x == 0) sm.item = atomicAdd(&ctrl[0], 1u);
         __syncthreads();
@@ -882,12 +1070,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         load_program(sm, &V.progs[p]);
         const uint16_t *trace = traces + sm.prog.trace_off;
         const uint64_t *sgm = segmask + sm.prog.segmask_off;
+        const uint32_t *sgr = segrange + sm.prog.segmask_off;
         loop_init(sm, *d.mh, opts);
         while (!sm.done) {
             const uint32_t mask = sm.mask;
             prepare_check(sm, mask);
             check_misc(sm, mask);
-            check_blocks(sm, d.tab, table_bytes, trace, sgm, 0, sm.prog.blocks, true);
+            check_blocks(sm, d.tab, table_bytes, trace, sgm, sgr, 0, sm.prog.blocks, true);
             loop_step(sm, *d.mh);
         }
         write_result(sm, &out[p]);
@@ -895,7 +1084,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // One check per program under masks[p] (persistent, same queue).
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_check(const uint8_t *__restrict__ arena, uint32_t n, const uint32_t *__restrict__ masks,
             uint8_t *__restrict__ scratch, gr_witnesses *__restrict__ out, uint32_t table_bytes) {
     Dyn d = dyn_smem();
@@ -903,7 +1092,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const ArenaView V = view(arena);
     const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
     const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
+    const uint32_t *segrange = reinterpret_cast<const uint32_t *>(scratch + V.h->scratch_segrange_off);
     uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
+    if (threadIdx.x == 0) sm.err = &ctrl[1];
     for (;;) {
         if (threadIdx.x == 0) sm.item = atomicAdd(&ctrl[0], 1u);
         __syncthreads();
@@ -914,8 +1105,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t mask = masks[p];
         prepare_check(sm, mask);
         check_misc(sm, mask);
-        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off, 0,
-                     sm.prog.blocks, true);
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off,
+                     segrange + sm.prog.segmask_off, 0, sm.prog.blocks, true);
         if (threadIdx.x < 32) {
             out[p].race_intra[threadIdx.x] = sm.rows_intra[threadIdx.x];
             out[p].race_inter[threadIdx.x] = sm.rows_inter[threadIdx.x];
@@ -994,18 +1185,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const ArenaView V = view(arena);
     const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
     const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
+    const uint32_t *segrange = reinterpret_cast<const uint32_t *>(scratch + V.h->scratch_segrange_off);
+    if (threadIdx.x == 0) sm.err = const_cast<uint32_t *>(reinterpret_cast<const uint32_t *>(scratch)) + 1;
     load_program(sm, &V.progs[p]);
     const uint32_t mask = st->mask;
     prepare_check(sm, mask);
     const uint32_t B = sm.prog.blocks;
     const uint32_t b = blockIdx.x;
     if (b < B) {
-        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off, b, b + 1,
-                     false);
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off,
+                     segrange + sm.prog.segmask_off, b, b + 1, false);
     } else {
         check_misc(sm, mask);
-        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off, 0, 0,
-                     true);
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off,
+                     segrange + sm.prog.segmask_off, 0, 0, true);
         if (threadIdx.x == 0) {
             wit->diverge = sm.diverge;
             wit->access_pairs = sm.pairs;
@@ -1050,7 +1243,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(const uint32_t *__restric
     MhsSmem &mh = *d.mh;
     const uint32_t n_vars = in[0], n_pos = in[1], n_neg = in[2], forced = in[3], forbidden = in[4];
     const uint32_t *w = in + 5;
-    for (uint32_t i = threadIdx.x; i < n_pos; i += blockDim.x) sm.cl[i] = in[5 + GR_MAX_SLOTS + i];
+    for (uint32_t i = threadIdx.x; i < n_pos; i += blockDim.x) mh_cl(sm)[i] = in[5 + GR_MAX_SLOTS + i];
     // negative clauses live after the positive ones in the mhs scratch
     uint32_t *neg = mh.nlo;  // staging; mhs_solve reads neg[] before it writes nlo
     for (uint32_t i = threadIdx.x; i < n_neg; i += blockDim.x) neg[i] = in[5 + GR_MAX_SLOTS + n_pos + i];
@@ -1079,7 +1272,11 @@ cudaError_t configure_kernels(uint32_t max_dynamic_smem) {
     const void *fns[] = {(const void *)k_repair, (const void *)k_check, (const void *)k_plain_init,
                          (const void *)k_plain_check, (const void *)k_plain_solve, (const void *)k_solve};
     for (const void *f : fns) {
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dynamic_smem);
+        cudaFuncAttributes a;
+        e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess) return e;
+        const size_t cap = max_dynamic_smem > a.sharedSizeBytes ? max_dynamic_smem - a.sharedSizeBytes : 0;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -219,7 +219,8 @@ class Workload:
     affine_as: tuple = (1, 2)
     affine_b_max: int = 4
     strided_max: int = 32
-    block_offset: bool = False  # c in {a*T, T} (global block-offset maps)
+    block_offset: bool = False  # global block-offset maps a*(tid + T*blk) + b
+    p_halo: float = 0.0         # block-offset maps: fraction with a halo offset b in [1, 4]
     p_collide: float = 0.01     # programs given one deliberately colliding write
     extra: dict = field(default_factory=dict)
 
@@ -240,12 +241,14 @@ WORKLOADS: Dict[str, Workload] = {
         maps={"affine": 0.4, "strided": 0.3, "perm": 0.3}, p_write=0.4,
         guard_fraction=0.25),
     # 256 programs, 64 blocks x 256 threads, 16 statements over a 65,536-word
-    # global array, block-offset affine maps, 15 slots each block or grid
-    # (grid weight 4, block weight 1)
+    # global array, block-offset affine maps a*(tid + T*blk) + b (one stride
+    # a in {1,2} per program; b = 0, or a halo offset in [1,4] for 15% of the
+    # statements), 15 slots each block or grid (grid w.p. 0.75; grid weight 4,
+    # block weight 1)
     "interblock256_64x256_s16": Workload(
         name="interblock256_64x256_s16", seed=2, n_programs=256, blocks=64, threads=256,
         n_stmts=16, space=SPACE_GLOBAL, m_words=65536, maps={"affine": 1.0}, p_write=0.5,
-        guard_fraction=0.0, p_grid_slot=0.5, grid_weight=4, block_offset=True),
+        guard_fraction=0.0, p_grid_slot=0.75, grid_weight=4, block_offset=True, p_halo=0.15),
     # 4,096 uneven programs: threads log-uniform 32-1024, blocks uniform 1-16,
     # statements uniform 4-24, shared array of 4*threads words, guards on 0-30%
     # of statements, half repair (E=0) / half removal (E = all slots)
@@ -285,7 +288,7 @@ def _injective_on_threads(mult: int, m: int, threads: int) -> bool:
     return threads <= m // math.gcd(mult % m if mult % m else m, m)
 
 
-def _draw_map(rng: SplitMix64, wl: Workload, m: int, T: int, kinds, probs):
+def _draw_map(rng: SplitMix64, wl: Workload, m: int, T: int, kinds, probs, stride: int = 1):
     u = rng.uniform()
     acc = 0.0
     kind = kinds[-1]
@@ -295,12 +298,13 @@ def _draw_map(rng: SplitMix64, wl: Workload, m: int, T: int, kinds, probs):
             kind = kd
             break
     if kind == "affine":
+        if wl.block_offset:
+            a = stride
+            b = rng.randint(1, wl.affine_b_max) if rng.bernoulli(wl.p_halo) else 0
+            return MAP_AFFINE, a, b, a * T, a
         a = rng.choice(wl.affine_as)
         b = rng.randint(0, wl.affine_b_max)
-        c = 0
-        if wl.block_offset:
-            c = a * T if rng.bernoulli(0.5) else T
-        return MAP_AFFINE, a, b, c, a
+        return MAP_AFFINE, a, b, 0, a
     if kind == "strided":
         s = rng.randint(1, wl.strided_max)
         b = rng.randint(0, s - 1)
@@ -347,6 +351,7 @@ def generate_program(wl: Workload, p: int, **override) -> Program:
             else:
                 s += 1
 
+    stride = rng.choice(wl.affine_as) if wl.block_offset else 1
     collide_at = -1
     if wl.p_collide > 0 and rng.bernoulli(wl.p_collide):
         collide_at = rng.randint(0, S - 1)
@@ -356,10 +361,17 @@ def generate_program(wl: Workload, p: int, **override) -> Program:
     for s in range(S):
         is_w = rng.bernoulli(wl.p_write) or s == collide_at
         while True:
-            kind, a, b, c, mult = _draw_map(rng, wl, M, T, kinds, probs)
+            kind, a, b, c, mult = _draw_map(rng, wl, M, T, kinds, probs, stride)
             if kind == MAP_PERM:
                 break  # a permutation restricted to T <= M threads is injective
-            if not is_w or s == collide_at or _injective_on_threads(mult, M, T):
+            if not is_w or s == collide_at:
+                break
+            if wl.block_offset:
+                # a write must be injective over the whole grid: c == a*T makes
+                # the map a*(tid + T*blk) + b, injective iff B*T <= M / gcd(a, M)
+                if c == a * T and _injective_on_threads(a, M, B * T):
+                    break
+            elif _injective_on_threads(mult, M, T):
                 break
         st = {"op": OP_W if is_w else OP_R, "space": wl.space, "kind": kind,
               "a": a, "b": b, "c": c, "guard": guards[s]}
