@@ -232,6 +232,25 @@ gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_mas
                           void *d_scratch, uint64_t scratch_bytes, gr_witnesses *d_out,
                           void *stream);
 
+/* gr_repair_packed without a scratch buffer, for callers that cannot
+ * allocate device memory where they run the repair (inside a host callback or
+ * another allocation-free path, a plug-in whose host forbids allocation after
+ * start-up, a real-time loop that must not pay cudaMalloc's implicit device
+ * synchronisation).  The paper has no counterpart: this is a deployment
+ * variant of the same launch.
+ * The scratch is a fixed 64 MiB device array inside the library, held by
+ * every GPU that loads the library until the process exits; a batch whose
+ * gr_pack_size scratch figure exceeds it is rejected with GR_ECAPACITY.  The
+ * array's device address is looked up on the first call made on each device,
+ * so make that first call before any stream capture.  The call reads the
+ * 128-byte arena header back to the host (a synchronising copy on stream) and
+ * allocates nothing.  All calls share the array: calls whose GPU work
+ * overlaps (other streams, other threads) race and must not be issued.
+ * d_arena: a gr_pack arena in device memory, 256-byte aligned; d_out: n
+ * results in device memory.  Enqueued on stream. */
+gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, const gr_options *opts,
+                                   gr_repair_result *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

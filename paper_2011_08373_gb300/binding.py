@@ -72,7 +72,8 @@ _lib = None
 
 EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair", "gr_repair_plain",
            "gr_solve", "gr_repair_batch", "gr_check_batch", "gr_pack_size", "gr_pack",
-           "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded"]
+           "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded",
+           "gr_repair_packed_noalloc"]
 
 
 def lib():
@@ -106,6 +107,8 @@ def lib():
                                            C.c_uint64, C.c_void_p, C.c_void_p]
             L.gr_expand_packed.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]
             L.gr_repair_expanded.argtypes = L.gr_repair_packed.argtypes
+            L.gr_repair_packed_noalloc.argtypes = [C.c_void_p, C.c_uint32, P(gr_options), C.c_void_p,
+                                                   C.c_void_p]
             L.gr_check_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint64,
                                           C.c_void_p, C.c_void_p]
             for name in EXPORTS[2:]:

@@ -321,6 +321,21 @@ gr_status finish_sync(void *d_scratch, cudaStream_t st) {
 
 }  // namespace
 
+namespace gr {
+// Launch shape of the persistent repair for n packed programs on the current
+// device (used by gr_repair_packed_noalloc in noalloc.cu).
+LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status) {
+    Workspace *ws;
+    LaunchCfg c{1, kMinTableBytes};
+    if ((*status = current_ws(&ws)) != GR_OK) return c;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((*status = ensure_configured(*ws)) != GR_OK) return c;
+    return choose_cfg(*ws, n);
+}
+
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace gr
+
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------

@@ -1,0 +1,121 @@
+// noalloc.cu — gr_repair_packed_noalloc: the batched repair of a packed
+// arena with its scratch in a fixed device array instead of a caller buffer.
+//
+// Some callers cannot allocate device memory at the point where they run the
+// repair: code inside a host callback or a signal-safe path, a plug-in whose
+// host forbids allocation after start-up, or a real-time loop that must not
+// hit cudaMalloc's implicit device synchronisation and page-table work.  This
+// entry point lets them repair a batch with only their own input (the packed
+// arena) and output (the results) buffers.
+//
+// The scratch (address traces, per-segment masks and ranges, the work-queue
+// counter and the device error word) lives in `g_noalloc_scratch`, a file-scope
+// __device__ array of kNoAllocScratchBytes.  Every GPU that loads the library
+// holds it until the process exits.  Its device address is looked up once per
+// device, on the first call made with that device current; make that first
+// call before any stream capture.  Every call shares the one array and it
+// keeps the last call's contents: the control words are cleared on each call,
+// everything else is rewritten before it is read.  Calls that overlap on the
+// GPU (two streams, two host threads) race on the array and must not be
+// issued; the host-side lock below only orders the enqueueing.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "engine.cuh"
+
+namespace gr {
+
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB
+
+__device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices];
+int g_noalloc_sms[kNoAllocMaxDevices];
+
+}  // namespace
+void set_last_error(const char *msg);
+namespace {
+
+gr_status noalloc_fail(gr_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    set_last_error(buf);  // reported by gr_last_error()
+    return code;
+}
+
+// Device address of the scratch array on the current device (set up once).
+gr_status noalloc_setup(int *dev_out, void **ptr_out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return noalloc_fail(GR_ECUDA, "device index %d unsupported", dev);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return noalloc_fail(GR_ECUDA, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+        g_noalloc_sms[dev] = sms;
+        g_noalloc_ptr[dev] = p;
+    }
+    *dev_out = dev;
+    *ptr_out = g_noalloc_ptr[dev];
+    return GR_OK;
+}
+
+}  // namespace
+
+// Launch-shape helper shared with capi.cu (same choice as gr_repair_packed).
+LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status);
+
+}  // namespace gr
+
+using namespace gr;
+
+extern "C" gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, const gr_options *opts,
+                                              gr_repair_result *d_out, void *stream) {
+    if (!d_arena || !d_out || n == 0) return noalloc_fail(GR_EINVAL, "NULL buffer or n == 0");
+    if (reinterpret_cast<uintptr_t>(d_arena) % 256) return noalloc_fail(GR_EINVAL, "d_arena must be 256-byte aligned");
+    if (opts && opts->max_iters > GR_MAX_ITERS) return noalloc_fail(GR_EINVAL, "max_iters above %d", GR_MAX_ITERS);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    int dev = 0;
+    void *scratch = nullptr;
+    gr_status s = noalloc_setup(&dev, &scratch);
+    if (s != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the arena header says how much scratch the batch needs
+    ArenaHeader h;
+    cudaError_t e = cudaMemcpyAsync(&h, d_arena, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "reading the arena header: %s", cudaGetErrorString(e));
+    if (h.magic != kArenaMagic || h.n_progs != n)
+        return noalloc_fail(GR_EINVAL, "d_arena is not a packed arena of %u programs", n);
+    if (h.scratch_bytes > kNoAllocScratchBytes)
+        return noalloc_fail(GR_ECAPACITY, "batch needs %llu scratch bytes; the fixed array holds %llu",
+                            (unsigned long long)h.scratch_bytes, (unsigned long long)kNoAllocScratchBytes);
+    LaunchCfg cfg = packed_launch_cfg(n, &s);
+    if (s != GR_OK) return noalloc_fail(s, "launch configuration failed");
+    gr_options o;
+    memset(&o, 0, sizeof(o));
+    o.grid_enabled = opts ? opts->grid_enabled : 1;
+    o.max_iters = (opts && opts->max_iters) ? opts->max_iters : GR_MAX_ITERS;
+    // the queue counter and the error word must start at zero
+    e = cudaMemsetAsync(scratch, 0, 256, st);
+    if (e == cudaSuccess) e = launch_expand(d_arena, scratch, (uint32_t)g_noalloc_sms[dev] * 8u, st);
+    if (e == cudaSuccess) e = launch_repair(d_arena, n, o, scratch, d_out, cfg, st);
+    if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "launch: %s", cudaGetErrorString(e));
+    return GR_OK;
+}
