@@ -262,6 +262,67 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_serve(args, rank, world, local):
+    """Poisson request streams through the repair server (p50/p99 latency)."""
+    import torch
+
+    from paper_2011_08373_gb300 import binding
+    from paper_2011_08373_gb300.build import build
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build()
+    n = args.serve_requests
+    n_large = max(1, n // 20)
+    small = synth.generate("uneven4096_mixed", n - n_large, start=100000)
+    large = synth.generate("large_128x1024_s24", n_large)
+    rng = synth.SplitMix64(synth.program_seed(11, 0))
+    progs = list(small)
+    for p in large:  # 5% large programs at seeded positions
+        progs.insert(rng.randint(0, len(progs)), p)
+    lines = []
+    with binding.Server(mem_budget_bytes=args.serve_budget_gb << 30, n_slots=args.serve_slots) as srv:
+        # warm the server and the kernels
+        tk = [srv.submit(p) for p in progs[:64]]
+        srv.drain(600000)
+        for t in tk:
+            srv.poll(t)
+        for rate in args.serve_rates:
+            arrivals = synth.poisson_arrivals(rate, n, seed=int(rate))
+            tickets = []
+            lat = {}
+            with ClockSampler(local) as clk:
+                t0 = time.perf_counter()
+                for p, at in zip(progs, arrivals):
+                    while time.perf_counter() - t0 < at:
+                        pass
+                    tickets.append(srv.submit(p))
+                    # opportunistic harvesting keeps the done map small
+                    if len(tickets) % 64 == 0:
+                        for t in tickets[-128:-64]:
+                            if t not in lat:
+                                r = srv.poll(t)
+                                if r is not None:
+                                    lat[t] = r[1]
+                srv.drain(600000)
+                t_end = time.perf_counter()
+            for t in tickets:
+                if t not in lat:
+                    r = srv.poll(t)
+                    lat[t] = r[1]
+            ls = np.array([lat[t] for t in tickets]) * 1e6
+            line = {"metric": "p50/p99 repair latency (serving)", "rate_per_s": rate, "requests": n,
+                    "p50_us": float(np.percentile(ls, 50)), "p99_us": float(np.percentile(ls, 99)),
+                    "repairs_per_s": n / (t_end - t0), "offered_per_s": n / float(arrivals[-1]),
+                    "config": {"workload": "uneven4096_mixed + 5% large_128x1024_s24",
+                               "budget_gb": args.serve_budget_gb, "slots": args.serve_slots},
+                    "launches": srv.stats()["launches"], "clocks": clk.summary()}
+            lines.append(line)
+            print(json.dumps(line), flush=True)
+    return lines
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,12 +335,19 @@ def main():
     ap.add_argument("--plain-programs", type=int, default=64)
     ap.add_argument("--cpu-sample", type=int, default=32)
     ap.add_argument("--ref-sample", type=int, default=32)
+    ap.add_argument("--serve", action="store_true", help="Poisson request streams through the server")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 500.0, 2000.0])
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.serve:
+        run_serve(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -62,6 +62,7 @@ enum {
     GR_EINVAL = -1,    /* invalid argument; outputs untouched */
     GR_ENOMEM = -2,    /* device or host allocation failed */
     GR_ECUDA = -4,     /* a CUDA call failed (gr_last_error has the text) */
+    GR_EBUSY = -5,     /* gr_server_poll / gr_server_drain: not finished yet */
     GR_ECAPACITY = -6  /* a buffer the caller passed is too small */
 };
 
@@ -231,6 +232,39 @@ gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *
 gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_masks,
                           void *d_scratch, uint64_t scratch_bytes, gr_witnesses *d_out,
                           void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Repair server: continuous batching over a device-memory budget          */
+/* ---------------------------------------------------------------------- */
+
+/* A server repairs single programs submitted at any time (the repair loop of
+ * Algorithm 1 per request).  It owns n_slots (1..16) launch slots, each with
+ * its own stream and device buffers; together they take mem_budget_bytes of
+ * device memory, allocated here, and nothing more is allocated while
+ * serving.  A dispatcher thread admits queued requests in arrival order into
+ * whichever slot is idle, as many as fit the slot's share of the budget and
+ * the max_inflight cap, and runs them as one persistent repair launch;
+ * requests that arrive while other launches run are admitted by the next
+ * free slot and overlap with them on the device.  Each request's traces,
+ * clauses and masks stay on the device for its whole loop.  opts may be
+ * NULL.  The server binds to the device current at creation. */
+typedef struct gr_server gr_server;
+gr_status gr_server_create(uint64_t mem_budget_bytes, uint32_t n_slots, uint32_t max_inflight,
+                           const gr_options *opts, gr_server **out);
+/* Copy one program (the caller may free it on return) and queue it.  Returns
+ * a ticket.  GR_ECAPACITY if the program alone exceeds one slot's memory. */
+gr_status gr_server_submit(gr_server *s, const gr_program *prog, gr_launch launch, int32_t mode,
+                           uint64_t *ticket);
+/* GR_OK and the result (and, if latency_ns is not NULL, the time from submit
+ * to completion seen by the server) once the request is done, after which the
+ * ticket is forgotten; GR_EBUSY while it is queued or running. */
+gr_status gr_server_poll(gr_server *s, uint64_t ticket, gr_repair_result *out, uint64_t *latency_ns);
+/* Wait until nothing is queued or running (GR_OK) or timeout_ms passed (GR_EBUSY). */
+gr_status gr_server_drain(gr_server *s, uint32_t timeout_ms);
+/* Queued requests, requests on the device, launches issued so far. */
+gr_status gr_server_stats(gr_server *s, uint64_t *pending, uint64_t *inflight, uint64_t *launches);
+/* Stop the dispatcher, wait for the device, free everything. */
+gr_status gr_server_destroy(gr_server *s);
 
 /* gr_repair_packed without a scratch buffer, for callers that cannot
  * allocate device memory where they run the repair (inside a host callback or

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgpurepair.so")
 
 MAX_STMTS, MAX_SLOTS, MAX_ITERS, MAX_CLAUSES = 25, 24, 64, 656
-OK, UNSAT, EINVAL, ENOMEM, ECUDA, ECAPACITY = 0, 1, -1, -2, -4, -6
+OK, UNSAT, EINVAL, ENOMEM, ECUDA, EBUSY, ECAPACITY = 0, 1, -1, -2, -4, -5, -6
 REPAIRED, UNREPAIRABLE, ITER_CAP = 0, 1, 2
 
 
@@ -73,7 +73,8 @@ _lib = None
 EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair", "gr_repair_plain",
            "gr_solve", "gr_repair_batch", "gr_check_batch", "gr_pack_size", "gr_pack",
            "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded",
-           "gr_repair_packed_noalloc"]
+           "gr_repair_packed_noalloc", "gr_server_create", "gr_server_submit", "gr_server_poll",
+           "gr_server_drain", "gr_server_stats", "gr_server_destroy"]
 
 
 def lib():
@@ -109,6 +110,14 @@ def lib():
             L.gr_repair_expanded.argtypes = L.gr_repair_packed.argtypes
             L.gr_repair_packed_noalloc.argtypes = [C.c_void_p, C.c_uint32, P(gr_options), C.c_void_p,
                                                    C.c_void_p]
+            L.gr_server_create.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, P(gr_options),
+                                           P(C.c_void_p)]
+            L.gr_server_submit.argtypes = [C.c_void_p, P(gr_program), gr_launch, C.c_int32,
+                                           P(C.c_uint64)]
+            L.gr_server_poll.argtypes = [C.c_void_p, C.c_uint64, P(gr_repair_result), P(C.c_uint64)]
+            L.gr_server_drain.argtypes = [C.c_void_p, C.c_uint32]
+            L.gr_server_stats.argtypes = [C.c_void_p, P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]
+            L.gr_server_destroy.argtypes = [C.c_void_p]
             L.gr_check_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint64,
                                           C.c_void_p, C.c_void_p]
             for name in EXPORTS[2:]:
@@ -371,3 +380,55 @@ class DeviceBatch:
 
 def _aligned(ptr: int) -> int:
     return (ptr + 255) // 256 * 256
+
+
+# ---------------------------------------------------------------------------
+# Repair server (continuous batching)
+# ---------------------------------------------------------------------------
+
+class Server:
+    """gr_server_*: submit single programs at any time; poll for results."""
+
+    def __init__(self, mem_budget_bytes: int, n_slots: int = 4, max_inflight: int = 1 << 20,
+                 grid_enabled: bool = True, max_iters: int = 64):
+        self._h = C.c_void_p()
+        o = _options(grid_enabled, max_iters)
+        _check(lib().gr_server_create(mem_budget_bytes, n_slots, max_inflight, C.byref(o),
+                                      C.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, p, mode: Optional[int] = None) -> int:
+        c = CProgram(p)
+        t = C.c_uint64()
+        _check(lib().gr_server_submit(self._h, C.byref(c.s), c.launch,
+                                      c.mode if mode is None else mode, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """(result dict, latency seconds) when done, else None."""
+        r = gr_repair_result()
+        lat = C.c_uint64()
+        rc = _check(lib().gr_server_poll(self._h, ticket, C.byref(r), C.byref(lat)), allowed=(OK, EBUSY))
+        if rc == EBUSY:
+            return None
+        return result_dict(np.frombuffer(bytes(r), dtype=RESULT_DTYPE)[0]), lat.value * 1e-9
+
+    def drain(self, timeout_ms: int = 60000) -> bool:
+        return _check(lib().gr_server_drain(self._h, timeout_ms), allowed=(OK, EBUSY)) == OK
+
+    def stats(self) -> dict:
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(lib().gr_server_stats(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"pending": a.value, "inflight": b.value, "launches": c.value}
+
+    def close(self) -> None:
+        if self._h:
+            _check(lib().gr_server_destroy(self._h))
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False

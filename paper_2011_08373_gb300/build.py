@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libgpurepair.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
            "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["kernels.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "capi.cu", "noalloc.cu", "server.cu"]
 
 
 def _nvcc() -> str:

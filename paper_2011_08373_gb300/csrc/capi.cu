@@ -15,7 +15,7 @@
 
 using namespace gr;
 
-namespace {
+namespace gr {
 
 thread_local std::string g_last_error;
 
@@ -102,13 +102,6 @@ gr_status validate_opts(const gr_options *o) {
 // ---------------------------------------------------------------------------
 
 size_t align_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-struct Layout {
-    size_t progs_off, order_off, segbase_off, perm_off, arena_bytes;
-    size_t segmask_off, segrange_off, trace_off, scratch_bytes;
-    uint64_t n_segments;
-    std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
-};
 
 uint32_t t_pad_of(uint32_t T) { return (T + 7u) & ~7u; }
 
@@ -218,6 +211,10 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     std::iota(order, order + n, 0u);
     std::stable_sort(order, order + n, [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
 }
+
+}  // namespace gr
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // Per-device workspace

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "gpurepair.h"
 
@@ -76,6 +77,22 @@ struct LaunchCfg {
     uint32_t grid;         // CTAs of the persistent kernels
     uint32_t table_bytes;  // shared-memory owner-table budget per CTA
 };
+
+// Host-side helpers (capi.cu).
+struct Layout {
+    size_t progs_off, order_off, segbase_off, perm_off, arena_bytes;
+    size_t segmask_off, segrange_off, trace_off, scratch_bytes;
+    uint64_t n_segments;
+    std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
+};
+gr_status fail(gr_status code, const char *fmt, ...);
+gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx);
+size_t align_to(size_t x, size_t a);
+Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n);
+void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
+               uint8_t *arena);
+LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status);
+void set_last_error(const char *msg);
 
 // Host-callable launchers (kernels.cu).
 cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint32_t grid, cudaStream_t st);

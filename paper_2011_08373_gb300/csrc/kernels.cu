@@ -969,66 +969,78 @@ __device__ __forceinline__ ArenaView view(const uint8_t *arena) {
     return v;
 }
 
-// K0: one warp per (program, statement, block) segment of t_pad threads.
+// K0: one CTA per program (in the host's largest-first order), one warp per
+// (statement, block) segment of t_pad threads.  Writes the u16 address trace,
+// and per segment the mask of 1,024-word chunks and the [min, max] address of
+// its active accesses (min > max when none is active).
 __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ arena, uint8_t *__restrict__ scratch) {
     const ArenaView V = view(arena);
     const uint32_t n = V.h->n_progs;
-    const uint64_t nseg = V.h->n_segments;
     uint16_t *traces = reinterpret_cast<uint16_t *>(scratch + V.h->scratch_trace_off);
     uint64_t *segmask = reinterpret_cast<uint64_t *>(scratch + V.h->scratch_segmask_off);
     uint32_t *segrange = reinterpret_cast<uint32_t *>(scratch + V.h->scratch_segrange_off);
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t seg = warp0; seg < nseg; seg += nwarps) {
-        uint32_t lo = 0, hi = n;  // last p with segbase[p] <= seg
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (V.segbase[mid] <= seg) lo = mid; else hi = mid;
-        }
-        const uint32_t p = lo;
+    __shared__ DevStmt st_sh[GR_MAX_STMTS];
+    __shared__ uint32_t hdr[8];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t item = blockIdx.x; item < n; item += gridDim.x) {
+        const uint32_t p = V.order[item];
         const DevProg &P = V.progs[p];
-        const uint32_t local = (uint32_t)(seg - V.segbase[p]);
-        const uint32_t B = P.blocks, T = P.threads, tpad = P.t_pad;
-        const uint32_t s = local / B, blk = local - s * B;
-        const DevStmt st = P.stmts[s];
-        const uint32_t M = st.m;
-        const uint32_t base = (uint32_t)(((uint64_t)st.cm * blk + st.bm) % M);
-        const bool perm = st.kind == GR_PERM;
-        const uint32_t step = perm ? 1u : st.am;
-        uint16_t *out = traces + P.trace_off + ((size_t)s * B + blk) * tpad;
-        uint64_t chunks = 0;
-        uint32_t amin = 0xFFFFu, amax = 0;
-        for (uint32_t v = lane; v < (tpad >> 3); v += 32) {
-            const uint32_t t0 = v * 8u;
-            // x = (step * t + base) mod M, advanced by one thread at a time
-            uint32_t x = (uint32_t)(((uint64_t)step * t0 + base) % M);
-            uint32_t w4[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (uint32_t e = 0; e < 8; ++e) {
-                const uint32_t t = t0 + e;
-                uint32_t a = 0;
-                if (t < T) {
-                    a = perm ? V.perm[st.perm_off + x] : x;
-                    if (st.gk == 0 || t % st.gk == st.gr) {
-                        chunks |= 1ull << (a >> kChunkShift);
-                        amin = min(amin, a);
-                        amax = max(amax, a);
-                    }
-                }
-                w4[e >> 1] |= (a & 0xFFFFu) << ((e & 1u) * 16u);
-                x += step;
-                if (x >= M) x -= M;
-            }
-            reinterpret_cast<uint4 *>(out)[v] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        __syncthreads();
+        if (threadIdx.x < GR_MAX_STMTS * sizeof(DevStmt) / 16) {
+            reinterpret_cast<uint4 *>(st_sh)[threadIdx.x] = reinterpret_cast<const uint4 *>(P.stmts)[threadIdx.x];
         }
-        const uint32_t lo32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)chunks);
-        const uint32_t hi32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(chunks >> 32));
-        amin = __reduce_min_sync(0xFFFFFFFFu, amin);
-        amax = __reduce_max_sync(0xFFFFFFFFu, amax);
-        if (lane == 0) {
-            segmask[P.segmask_off + (size_t)s * B + blk] = ((uint64_t)hi32 << 32) | lo32;
-            segrange[P.segmask_off + (size_t)s * B + blk] = amin | (amax << 16);  // empty: min > max
+        if (threadIdx.x == 0) {
+            hdr[0] = P.n_stmts;
+            hdr[1] = P.blocks;
+            hdr[2] = P.threads;
+            hdr[3] = P.t_pad;
+        }
+        __syncthreads();
+        const uint32_t S = hdr[0], B = hdr[1], T = hdr[2], tpad = hdr[3];
+        uint16_t *tr = traces + P.trace_off;
+        uint64_t *sgm = segmask + P.segmask_off;
+        uint32_t *sgr = segrange + P.segmask_off;
+        for (uint32_t seg = warp; seg < S * B; seg += nwarps) {
+            const uint32_t s = seg / B, blk = seg - s * B;
+            const DevStmt &st = st_sh[s];
+            const uint32_t M = st.m;
+            const uint32_t base = (uint32_t)(((uint64_t)st.cm * blk + st.bm) % M);
+            const bool perm = st.kind == GR_PERM;
+            const uint32_t step = perm ? 1u : st.am;
+            uint16_t *out = tr + (size_t)seg * tpad;
+            uint64_t chunks = 0;
+            uint32_t amin = 0xFFFFu, amax = 0;
+            for (uint32_t v = lane; v < (tpad >> 3); v += 32) {
+                const uint32_t t0 = v * 8u;
+                // x = (step * t + base) mod M, advanced by one thread at a time
+                uint32_t x = (uint32_t)(((uint64_t)step * t0 + base) % M);
+                uint32_t w4[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (uint32_t e = 0; e < 8; ++e) {
+                    const uint32_t t = t0 + e;
+                    uint32_t a = 0;
+                    if (t < T) {
+                        a = perm ? V.perm[st.perm_off + x] : x;
+                        if (st.gk == 0 || t % st.gk == st.gr) {
+                            chunks |= 1ull << (a >> kChunkShift);
+                            amin = min(amin, a);
+                            amax = max(amax, a);
+                        }
+                    }
+                    w4[e >> 1] |= (a & 0xFFFFu) << ((e & 1u) * 16u);
+                    x += step;
+                    if (x >= M) x -= M;
+                }
+                reinterpret_cast<uint4 *>(out)[v] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
+            const uint32_t lo32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)chunks);
+            const uint32_t hi32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)(chunks >> 32));
+            amin = __reduce_min_sync(0xFFFFFFFFu, amin);
+            amax = __reduce_max_sync(0xFFFFFFFFu, amax);
+            if (lane == 0) {
+                sgm[seg] = ((uint64_t)hi32 << 32) | lo32;
+                sgr[seg] = amin | (amax << 16);
+            }
         }
     }
 }
