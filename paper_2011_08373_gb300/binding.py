@@ -186,11 +186,76 @@ def _options(grid_enabled: bool = True, max_iters: int = 64) -> gr_options:
     return o
 
 
+class ProgramBatch:
+    """Many programs marshalled into a few contiguous numpy buffers (one
+    gr_stmt array, one slot array of each kind, one permutation array) and a
+    gr_program array pointing into them.  Keeps every buffer alive."""
+
+    STMT_DTYPE = np.dtype(gr_stmt)
+    PROG_DTYPE = np.dtype([("n_stmts", np.uint32), ("stmts", np.uint64), ("slot_level", np.uint64),
+                           ("slot_guard", np.uint64), ("slot_weight", np.uint64),
+                           ("m_shared", np.uint32), ("m_global", np.uint32), ("perm", np.uint64),
+                           ("perm_len", np.uint32), ("existing_mask", np.uint32)], align=True)
+
+    def __init__(self, progs: Sequence):
+        assert self.PROG_DTYPE.itemsize == C.sizeof(gr_program)
+        n = len(progs)
+        S = np.array([p.op.shape[0] for p in progs], np.int64)
+        nsl = S - 1
+        s_off = np.concatenate([[0], np.cumsum(S)])
+        k_off = np.concatenate([[0], np.cumsum(nsl)])
+        st = np.zeros(int(s_off[-1]), self.STMT_DTYPE)
+        for name, attr in (("op", "op"), ("space", "space"), ("kind", "kind"), ("a", "a"), ("b", "b"),
+                           ("c", "c"), ("perm_off", "perm_off"), ("guard_k", "guard_k"),
+                           ("guard_r", "guard_r")):
+            st[name] = np.concatenate([getattr(p, attr) for p in progs])
+        self.stmts = st
+        self.level = np.ascontiguousarray(np.concatenate([p.slot_level for p in progs]).astype(np.uint8))
+        guard = np.zeros(2 * int(k_off[-1]) + 2, np.uint16)
+        guard[0:2 * int(k_off[-1]):2] = np.concatenate([p.slot_guard_k for p in progs])
+        guard[1:2 * int(k_off[-1]):2] = np.concatenate([p.slot_guard_r for p in progs])
+        self.guard = guard
+        self.weight = np.ascontiguousarray(np.concatenate([p.slot_weight for p in progs]).astype(np.uint32))
+        plen = np.array([len(p.perm) for p in progs], np.int64)
+        p_off = np.concatenate([[0], np.cumsum(plen)])
+        self.perm = (np.ascontiguousarray(np.concatenate([p.perm for p in progs]).astype(np.uint32))
+                     if p_off[-1] else np.zeros(1, np.uint32))
+        pa = np.zeros(n, self.PROG_DTYPE)
+        pa["n_stmts"] = S
+        pa["stmts"] = st.ctypes.data + s_off[:-1] * self.STMT_DTYPE.itemsize
+        has_slots = nsl > 0
+        pa["slot_level"] = np.where(has_slots, self.level.ctypes.data + k_off[:-1], 0)
+        pa["slot_guard"] = self.guard.ctypes.data + 4 * k_off[:-1]
+        pa["slot_weight"] = np.where(has_slots, self.weight.ctypes.data + 4 * k_off[:-1], 0)
+        pa["m_shared"] = [p.m_shared for p in progs]
+        pa["m_global"] = [p.m_global for p in progs]
+        pa["perm"] = np.where(plen > 0, self.perm.ctypes.data + 4 * p_off[:-1], 0)
+        pa["perm_len"] = plen
+        pa["existing_mask"] = [p.existing_mask for p in progs]
+        self.progs = pa
+        la = np.zeros((n, 2), np.uint32)
+        la[:, 0] = [p.blocks for p in progs]
+        la[:, 1] = [p.threads for p in progs]
+        self.launches = la
+        self.modes = np.ascontiguousarray(np.array([p.mode for p in progs], np.int32))
+        self.n = n
+
+    @property
+    def prog_ptr(self):
+        return C.cast(self.progs.ctypes.data, C.POINTER(gr_program))
+
+    @property
+    def launch_ptr(self):
+        return C.cast(self.launches.ctypes.data, C.POINTER(gr_launch))
+
+    @property
+    def mode_ptr(self):
+        return C.cast(self.modes.ctypes.data, C.POINTER(C.c_int32))
+
+
 def _program_array(progs: Sequence) -> tuple:
-    cps = [CProgram(p) for p in progs]
-    arr = (gr_program * len(cps))(*[c.s for c in cps])
-    la = (gr_launch * len(cps))(*[c.launch for c in cps])
-    return cps, arr, la
+    b = ProgramBatch(progs)
+    return b, b.prog_ptr, b.launch_ptr
 
 
 def witness_dict(w, S: int) -> dict:
@@ -257,13 +322,14 @@ def solve(n_vars: int, weights, pos, neg=(), forced: int = 0, forbidden: int = 0
     return None if rc == UNSAT else (m.value, wt.value)
 
 
-def repair_batch_raw(progs: Sequence, grid_enabled: bool = True, max_iters: int = 64,
-                     stream: int = 0) -> np.ndarray:
-    cps, arr, la = _program_array(progs)
-    modes = (C.c_int32 * len(cps))(*[c.mode for c in cps])
-    out = np.zeros(len(cps), dtype=RESULT_DTYPE)
+def repair_batch_raw(progs, grid_enabled: bool = True, max_iters: int = 64, stream: int = 0,
+                     out: Optional[np.ndarray] = None) -> np.ndarray:
+    """gr_repair_batch.  ``progs`` is a list of programs or a ProgramBatch."""
+    b = progs if isinstance(progs, ProgramBatch) else ProgramBatch(progs)
+    if out is None:
+        out = np.zeros(b.n, dtype=RESULT_DTYPE)
     o = _options(grid_enabled, max_iters)
-    _check(lib().gr_repair_batch(arr, la, modes, len(cps), C.byref(o), out.ctypes.data,
+    _check(lib().gr_repair_batch(b.prog_ptr, b.launch_ptr, b.mode_ptr, b.n, C.byref(o), out.ctypes.data,
                                  C.c_void_p(stream)))
     return out
 
@@ -274,10 +340,10 @@ def repair_batch(progs: Sequence, grid_enabled: bool = True, max_iters: int = 64
 
 
 def check_batch(progs: Sequence, masks: Sequence[int], stream: int = 0) -> List[dict]:
-    cps, arr, la = _program_array(progs)
-    m = (C.c_uint32 * len(cps))(*[int(x) for x in masks])
-    out = np.zeros(len(cps), dtype=WITNESS_DTYPE)
-    _check(lib().gr_check_batch(arr, la, m, len(cps), out.ctypes.data, C.c_void_p(stream)))
+    b, arr, la = _program_array(progs)
+    m = (C.c_uint32 * b.n)(*[int(x) for x in masks])
+    out = np.zeros(b.n, dtype=WITNESS_DTYPE)
+    _check(lib().gr_check_batch(arr, la, m, b.n, out.ctypes.data, C.c_void_p(stream)))
     return [witness_dict(out[i], progs[i].n_stmts) for i in range(len(progs))]
 
 
@@ -287,14 +353,13 @@ def check_batch(progs: Sequence, masks: Sequence[int], stream: int = 0) -> List[
 
 def pack(progs: Sequence) -> tuple:
     """(host arena as a 256-byte-aligned uint8 array, scratch bytes needed)."""
-    cps, arr, la = _program_array(progs)
+    b, arr, la = _program_array(progs)
     ab, sb = C.c_uint64(), C.c_uint64()
-    _check(lib().gr_pack_size(arr, la, len(cps), C.byref(ab), C.byref(sb)))
+    _check(lib().gr_pack_size(arr, la, b.n, C.byref(ab), C.byref(sb)))
     raw = np.zeros(ab.value + 256, np.uint8)
     off = (-raw.ctypes.data) % 256
     host = raw[off:off + ab.value]
-    modes = (C.c_int32 * len(cps))(*[c.mode for c in cps])
-    _check(lib().gr_pack(arr, la, modes, len(cps), host.ctypes.data, ab.value))
+    _check(lib().gr_pack(arr, la, b.mode_ptr, b.n, host.ctypes.data, ab.value))
     return host, sb.value
 
 

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -68,11 +70,16 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
             if (!p->perm) return fail(GR_EINVAL, "program %u stmt %u: permutation map without perm", idx, s);
             if ((uint64_t)st.perm_off + M > p->perm_len)
                 return fail(GR_EINVAL, "program %u stmt %u: perm_off + M beyond perm_len", idx, s);
-            std::vector<uint8_t> seen(M, 0);
+            // a permutation: M values below M, none repeated
+            thread_local uint64_t seen[GR_MAX_WORDS / 64];
+            memset(seen, 0, ((M + 63) / 64) * 8);
+            const uint32_t *tbl = p->perm + st.perm_off;
             for (uint32_t i = 0; i < M; ++i) {
-                const uint32_t v = p->perm[st.perm_off + i];
-                if (v >= M || seen[v]) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
-                seen[v] = 1;
+                const uint32_t v = tbl[i];
+                if (v >= M) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
+                const uint64_t bit = 1ull << (v & 63u);
+                if (seen[v >> 6] & bit) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
+                seen[v >> 6] |= bit;
             }
         }
     }
@@ -133,19 +140,55 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     return L;
 }
 
+// Run body(lo, hi) over [0, n) on up to 16 host threads (programs are
+// independent); small batches run inline.
+template <typename F>
+void parallel_over(uint32_t n, F body) {
+    const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const uint32_t nt = n >= 128 ? std::min(hw, (n + 63) / 64) : 1u;
+    if (nt <= 1) {
+        body(0u, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    const uint32_t per = (n + nt - 1) / nt;
+    for (uint32_t t = 0; t < nt; ++t) {
+        const uint32_t lo = t * per, hi = std::min(n, lo + per);
+        if (lo < hi) th.emplace_back(body, lo, hi);
+    }
+    for (auto &x : th) x.join();
+}
+
 gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     if (n == 0) return fail(GR_EINVAL, "no programs");
     if (!progs || !ls) return fail(GR_EINVAL, "progs or launches is NULL");
-    for (uint32_t p = 0; p < n; ++p) {
-        gr_status s = validate_one(&progs[p], ls[p], p);
-        if (s != GR_OK) return s;
-    }
-    return GR_OK;
+    // the first invalid program (lowest index) is reported, as in a serial scan
+    std::atomic<uint32_t> first_bad{n};
+    std::mutex mu;
+    std::string msg;
+    gr_status code = GR_OK;
+    parallel_over(n, [&](uint32_t lo, uint32_t hi) {
+        for (uint32_t p = lo; p < hi && p < first_bad.load(); ++p) {
+            gr_status s = validate_one(&progs[p], ls[p], p);
+            if (s != GR_OK) {
+                std::lock_guard<std::mutex> g(mu);
+                if (p < first_bad.load()) {
+                    first_bad.store(p);
+                    msg = g_last_error;
+                    code = s;
+                }
+                return;
+            }
+        }
+    });
+    if (code != GR_OK) g_last_error = msg;
+    return code;
 }
 
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
                uint8_t *arena) {
-    memset(arena, 0, L.arena_bytes);
+    // zero everything but the permutation area, which is fully overwritten
+    memset(arena, 0, L.perm_off);
     ArenaHeader *H = reinterpret_cast<ArenaHeader *>(arena);
     H->magic = kArenaMagic;
     H->n_progs = n;
@@ -163,7 +206,8 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     uint64_t *segbase = reinterpret_cast<uint64_t *>(arena + L.segbase_off);
     uint32_t *perm = reinterpret_cast<uint32_t *>(arena + L.perm_off);
     std::vector<uint64_t> cost(n);
-    for (uint32_t p = 0; p < n; ++p) {
+    parallel_over(n, [&](uint32_t lo, uint32_t hi) {
+    for (uint32_t p = lo; p < hi; ++p) {
         const gr_program &P = progs[p];
         DevProg &D = dp[p];
         const uint32_t S = P.n_stmts, nsl = S - 1;
@@ -207,6 +251,13 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
         segbase[p] = L.segmask_elem[p];
         cost[p] = (uint64_t)S * ls[p].blocks * t_pad_of(ls[p].threads);
     }
+    });
+    {
+        uint64_t perm_total = 0;
+        for (uint32_t p = 0; p < n; ++p) perm_total += progs[p].perm ? progs[p].perm_len : 0;
+        const size_t tail = L.perm_off + perm_total * 4;
+        if (tail < L.arena_bytes) memset(arena + tail, 0, L.arena_bytes - tail);
+    }
     segbase[n] = L.n_segments;
     std::iota(order, order + n, 0u);
     std::stable_sort(order, order + n, [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
@@ -243,7 +294,8 @@ struct Workspace {
     int smem_per_sm = 0;
     uint32_t max_dyn = 0;
     DeviceBuf arena, scratch, out, aux;
-    std::vector<uint8_t> host_arena;
+    uint8_t *host_arena = nullptr;  // pinned staging for the packed arena
+    size_t host_arena_cap = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -297,12 +349,22 @@ uint32_t expand_grid(const Workspace &ws) { return (uint32_t)ws.sms * 8u; }
 gr_status upload_batch(Workspace &ws, const gr_program *progs, const gr_launch *ls, const int32_t *modes,
                        uint32_t n, cudaStream_t st, Layout *Lout) {
     Layout L = layout_of(progs, ls, n);
-    ws.host_arena.resize(L.arena_bytes);
-    pack_into(progs, ls, modes, n, L, ws.host_arena.data());
+    if (ws.host_arena_cap < L.arena_bytes) {
+        if (ws.host_arena) cudaFreeHost(ws.host_arena);
+        ws.host_arena = nullptr;
+        ws.host_arena_cap = 0;
+        const size_t want = std::max<size_t>(L.arena_bytes, (size_t)1 << 20);
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&ws.host_arena), want, cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(staging)");
+        ws.host_arena_cap = want;
+    }
+    // the previous call on this workspace may still be reading the staging buffer
+    GR_CUDA(cudaStreamSynchronize(st));
+    pack_into(progs, ls, modes, n, L, ws.host_arena);
     gr_status s;
     if ((s = ws.arena.ensure(L.arena_bytes)) != GR_OK) return s;
     if ((s = ws.scratch.ensure(L.scratch_bytes)) != GR_OK) return s;
-    GR_CUDA(cudaMemcpyAsync(ws.arena.p, ws.host_arena.data(), L.arena_bytes, cudaMemcpyHostToDevice, st));
+    GR_CUDA(cudaMemcpyAsync(ws.arena.p, ws.host_arena, L.arena_bytes, cudaMemcpyHostToDevice, st));
     *Lout = L;
     return GR_OK;
 }
