@@ -146,6 +146,26 @@ def cpu_baseline_leg(workload, n_sample):
                       f"brute-force hitting set, {cores} threads, {dt:.1f} s"}
 
 
+def shard(workload, n, rank):
+    """Rank r repairs programs [r*n, (r+1)*n) of the workload: disjoint
+    batches, no data exchanged between ranks."""
+    return synth.generate(workload, n, start=rank * n)
+
+
+def whole_job(n_per_rank, t_step_local, world, device="cuda"):
+    """(whole-job repairs/s, max-over-ranks step time): every rank's batch
+    counts, the slowest rank sets the time."""
+    t = t_step_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        x = torch.tensor([t_step_local], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return n_per_rank * world / t, t
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -159,7 +179,7 @@ def run_ours(args, rank, world, local):
     build()
     wl = synth.WORKLOADS[args.workload]
     n = args.programs or wl.n_programs
-    progs = synth.generate(args.workload, n, start=rank * n)
+    progs = shard(args.workload, n, rank)
     batch = binding.DeviceBatch(progs)
     stream = torch.cuda.current_stream()
     l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -191,16 +211,14 @@ def run_ours(args, rank, world, local):
     repair_ms = [b.elapsed_time(c) for a, b, c in ev]
     expand_ms = [a.elapsed_time(b) for a, b, c in ev]
     t_step = sum(step_ms) / len(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    _, t_step = whole_job(n, t_step, world)
     res = batch.results_raw()
     checks = int(res["iters"].sum())
     pairs = int(res["access_pairs"].sum())
     status = np.bincount(res["status"].astype(np.int64), minlength=3)[:3].tolist()
     lat = (res["t_end_ns"].astype(np.int64) - int(res["t_start_ns"].min())) / 1e3
-    value = n * world / t_step
+    value, _ = whole_job(n, t_step, 1)
+    value *= world
 
     # algorithmic bytes of the repair kernel: each check reads the program's
     # trace once (S x B x T u16 addresses); the arena and results once per launch

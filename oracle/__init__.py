@@ -89,6 +89,9 @@ def _configure(path):
     lib.orc_repair_batch.argtypes = [C.POINTER(_Prog), C.POINTER(C.c_int32), C.c_uint32,
                                      C.c_int, C.c_uint32, C.POINTER(_Result), C.c_uint32]
     lib.orc_repair_batch.restype = None
+    lib.orc_check_pair.argtypes = [C.POINTER(_Prog), C.c_uint32, C.c_uint32, C.c_uint32,
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
+    lib.orc_check_pair.restype = None
     assert lib.orc_sizeof_result() == C.sizeof(_Result)
     assert lib.orc_sizeof_prog() == C.sizeof(_Prog)
     assert lib.orc_sizeof_witness() == C.sizeof(_Witness)
@@ -159,6 +162,16 @@ def check(p, mask: int) -> dict:
     S = p.op.shape[0]
     return {"intra": [w.intra[i] for i in range(S)], "inter": [w.inter[i] for i in range(S)],
             "diverge": w.diverge, "access_pairs": w.access_pairs}
+
+
+def check_pair(p, mask: int, i: int, j: int) -> tuple:
+    """(same-block witness, cross-block witness, thread pairs examined) for
+    statements i <= j under ``mask``: the check's definition on one pair."""
+    lib = _load()
+    m = _Marshalled(p)
+    a, b, n = C.c_int32(), C.c_int32(), C.c_uint64()
+    lib.orc_check_pair(C.byref(m.s), mask, i, j, C.byref(a), C.byref(b), C.byref(n))
+    return bool(a.value), bool(b.value), n.value
 
 
 def clauses(p, witness: dict) -> list:

@@ -162,6 +162,55 @@ void orc_check(const orc_prog *p, uint32_t mask, orc_witness *out) {
     }
 }
 
+/* The same definition for one statement pair (i <= j): whether a same-block
+ * and a cross-block witness (i, j) exist under mask m, and the thread pairs
+ * examined.  Used to sample full-size launches whose whole check is too slow
+ * to enumerate. */
+void orc_check_pair(const orc_prog *p, uint32_t mask, uint32_t i, uint32_t j, int32_t *intra, int32_t *inter,
+                    uint64_t *pairs) {
+    *intra = 0;
+    *inter = 0;
+    *pairs = 0;
+    const uint32_t B = p->blocks, T = p->threads;
+    if (i > j || j >= p->n_stmts) return;
+    if (p->space[i] != p->space[j]) return;
+    if (p->op[i] != 1 && p->op[j] != 1) return;
+    const int shared = p->space[i] == 0;
+    const int open_same = !orc_separated(p, mask, i, j, 0);
+    const int open_cross = !shared && !orc_separated(p, mask, i, j, 1);
+    if (!open_same && !open_cross) return;
+    const uint64_t G = (uint64_t)B * T;
+    uint32_t *ai = (uint32_t *)malloc(sizeof(uint32_t) * G);
+    uint32_t *aj = (uint32_t *)malloc(sizeof(uint32_t) * G);
+    for (uint32_t b = 0; b < B; b++)
+        for (uint32_t t = 0; t < T; t++) {
+            ai[(uint64_t)b * T + t] = orc_addr(p, i, b, t);
+            aj[(uint64_t)b * T + t] = orc_addr(p, j, b, t);
+        }
+    for (uint32_t b1 = 0; b1 < B; b1++) {
+        for (uint32_t t1 = 0; t1 < T; t1++) {
+            if (!orc_active(p->guard_k[i], p->guard_r[i], t1)) continue;
+            const uint32_t a1 = ai[(uint64_t)b1 * T + t1];
+            for (uint32_t b2 = 0; b2 < B; b2++) {
+                const int same = b1 == b2;
+                if (same && !open_same) continue;
+                if (!same && !open_cross) continue;
+                for (uint32_t t2 = 0; t2 < T; t2++) {
+                    if (same && t1 == t2) continue;
+                    if (i == j && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;
+                    if (!orc_active(p->guard_k[j], p->guard_r[j], t2)) continue;
+                    (*pairs)++;
+                    if (aj[(uint64_t)b2 * T + t2] != a1) continue;
+                    if (same) *intra = 1;
+                    else *inter = 1;
+                }
+            }
+        }
+    }
+    free(ai);
+    free(aj);
+}
+
 /* GenerateClause (Section 2.4): a race witness (i, j) is avoided exactly when
  * some barrier able to order it is on: any slot in i .. j-1 for a same-block
  * witness, a grid slot in i .. j-1 for a cross-block one.  (i, i) gives the

@@ -1,0 +1,168 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark times (the packed, device-resident batch, persistent launch).
+
+Where the oracle cannot enumerate a whole check (64 x 256 global arrays,
+128 x 1,024 launches) it is sampled: its one-pair check gives the
+unconstrained witness set W(0) pair by pair, its solver gives the expected
+final mask from W(0) (clauses are exact, so the loop ends at the lowest-key
+mask over all masks whose own check is clean, whatever the trajectory), and a
+launch-independent copy of the program (same threads and slot guards, no
+accesses) gives the divergent slots."""
+import concurrent.futures as cf
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_08373_gb300 import synth
+from paper_2011_08373_gb300.synth import MODE_REPAIR, OP_W
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses", "forbidden",
+        "access_pairs")
+N_THREADS = min(16, os.cpu_count() or 1)
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_08373_gb300.build import build
+    from paper_2011_08373_gb300 import binding
+
+    build()
+    binding.lib()
+    return binding
+
+
+def _run(gb, progs):
+    import torch
+
+    db = gb.DeviceBatch(progs)
+    db.run()
+    torch.cuda.synchronize()
+    return db, db.results()
+
+
+def _properties(p, r):
+    """Facts every result must satisfy, at any size."""
+    n = p.n_slots
+    assert r["iters"] <= n + 3
+    assert r["weight"] == sum(int(p.slot_weight[k]) for k in range(n) if (r["mask"] >> k) & 1)
+    assert r["clauses"] == sorted(set(r["clauses"]))
+    # repair mode starts at MHS(empty) = E, removal mode probes E
+    assert (r["iters"] == 0 and r["status"] == 1) or r["traj"][0] == p.existing_mask
+    if r["status"] == 0:
+        assert r["mask"] == r["traj"][-1]
+        assert all(r["mask"] & c for c in r["clauses"])
+        assert not (r["mask"] & r["forbidden"])
+
+
+def _w0_by_pairs(p, mask=0):
+    S = p.n_stmts
+    cand = [(i, j) for i in range(S) for j in range(i, S)
+            if p.space[i] == p.space[j] and (p.op[i] == OP_W or p.op[j] == OP_W)]
+    with cf.ThreadPoolExecutor(N_THREADS) as ex:
+        res = list(ex.map(lambda ij: oracle.check_pair(p, mask, *ij), cand))
+    intra, inter = [0] * S, [0] * S
+    pairs = 0
+    for (i, j), (a, b, n) in zip(cand, res):
+        intra[i] |= int(a) << j
+        inter[i] |= int(b) << j
+        pairs += n
+    return {"intra": intra, "inter": inter, "diverge": 0, "access_pairs": pairs}
+
+
+def _divergent_slots(p):
+    """Divergence depends only on the slot guards and the thread count: check
+    a copy with the same threads and slots whose statements touch nothing
+    that could race, under all slots on."""
+    q = synth.make_program([{"op": "R"} for _ in range(p.n_stmts)], blocks=1, threads=p.threads,
+                           m_shared=1, slot_level=p.slot_level.tolist(),
+                           slot_guard=list(zip(p.slot_guard_k.tolist(), p.slot_guard_r.tolist())),
+                           slot_weight=p.slot_weight.tolist())
+    return oracle.check(q, (1 << p.n_slots) - 1)["diverge"]
+
+
+def _expected_final(p, w0):
+    n = p.n_slots
+    forced = p.existing_mask if p.mode == MODE_REPAIR else 0
+    cls = oracle.clauses(p, w0)
+    sol = oracle.solve(n, [int(x) for x in p.slot_weight], cls, (), forced, _divergent_slots(p))
+    return sol, cls
+
+
+def test_batch1024_full_size(gb):
+    progs = synth.generate("batch1024_4x256_s24")
+    assert len(progs) == 1024
+    _, got = _run(gb, progs)
+    for p, r in zip(progs, got):
+        _properties(p, r)
+    sample = list(range(0, 1024, 43))
+    want = oracle.repair_batch([progs[i] for i in sample], n_threads=N_THREADS)
+    for i, w in zip(sample, want):
+        for k in KEYS:
+            assert got[i][k] == w[k], (i, k)
+
+
+def test_uneven4096_full_size(gb):
+    progs = synth.generate("uneven4096_mixed")
+    assert len(progs) == 4096
+    _, got = _run(gb, progs)
+    for p, r in zip(progs, got):
+        _properties(p, r)
+    sample = [i for i, p in enumerate(progs) if p.blocks * p.threads <= 1500][:48]
+    big = max(range(len(progs)), key=lambda i: progs[i].blocks * progs[i].threads * progs[i].n_stmts)
+    want = oracle.repair_batch([progs[i] for i in sample], n_threads=N_THREADS)
+    for i, w in zip(sample, want):
+        for k in KEYS:
+            assert got[i][k] == w[k], (i, k)
+    # the largest program of the batch: W(0) by sampled pairs, final mask by path independence
+    p = progs[big]
+    sol, _ = _expected_final(p, _w0_by_pairs(p))
+    r = got[big]
+    if sol is None:
+        assert r["status"] == 1
+    else:
+        assert r["status"] == 0 and (r["mask"], r["weight"]) == sol
+
+
+@pytest.mark.parametrize("idx", [3, 77])
+def test_interblock_full_size_sampled(gb, idx):
+    progs = synth.generate("interblock256_64x256_s16")
+    assert len(progs) == 256 and progs[idx].blocks == 64 and progs[idx].m_global == 65536
+    db, got = _run(gb, progs)
+    db.check([0] * len(progs))
+    import torch
+
+    torch.cuda.synchronize()
+    w_gpu = db.witnesses(progs)[idx]
+    p = progs[idx]
+    w0 = _w0_by_pairs(p)
+    assert w_gpu["intra"] == w0["intra"] and w_gpu["inter"] == w0["inter"]
+    assert w_gpu["access_pairs"] == w0["access_pairs"]
+    sol, cls = _expected_final(p, w0)
+    r = got[idx]
+    _properties(p, r)
+    if sol is None:
+        assert r["status"] == 1
+    else:
+        assert r["status"] == 0 and (r["mask"], r["weight"]) == sol
+    # repair mode with no existing barriers: the first check (mask 0) sees every race
+    assert r["clauses"] == cls
+
+
+def test_large_program_full_size(gb):
+    progs = synth.generate("large_128x1024_s24", 2)
+    _, got = _run(gb, progs)
+    for p, r in zip(progs, got):
+        _properties(p, r)
+        sol, _ = _expected_final(p, _w0_by_pairs(p))
+        if sol is None:
+            assert r["status"] == 1
+        else:
+            assert r["status"] == 0 and (r["mask"], r["weight"]) == sol

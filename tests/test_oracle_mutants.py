@@ -61,7 +61,7 @@ def _all_pins():
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_pins_reject_mutant(name, old, new, tmp_path):
     src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
-    assert src.count(old) == 1, "mutation site must be unique"
+    assert src.count(old) >= 1, "mutation site must exist"  # every copy of the site is mutated
     mutated = tmp_path / "oracle_mutant.c"
     mutated.write_text(src.replace(old, new))
     lib = tmp_path / "liboracle_mutant.so"

@@ -423,3 +423,20 @@ def test_repair_path_independence(seed):
                 assert (got["weight"], got["mask"]) == ref
                 assert got["added"] == got["mask"] & ~p.existing_mask
                 assert got["removed"] == p.existing_mask & ~got["mask"]
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_check_pair_matches_check(seed):
+    """The one-pair form used to sample full-size launches agrees with the
+    whole check on every pair."""
+    p = random_program(8000 + seed, s_max=5, b_max=3, t_max=8, m_max=12)
+    for m in {0, (1 << p.n_slots) - 1, (seed * 31) % (1 << p.n_slots) if p.n_slots else 0}:
+        full = oracle.check(p, m)
+        total = 0
+        for i in range(p.n_stmts):
+            for j in range(i, p.n_stmts):
+                a, b, n = oracle.check_pair(p, m, i, j)
+                assert a == bool((full["intra"][i] >> j) & 1)
+                assert b == bool((full["inter"][i] >> j) & 1)
+                total += n
+        assert total == full["access_pairs"]
