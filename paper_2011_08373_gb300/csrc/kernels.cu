@@ -168,10 +168,10 @@ __device__ void load_program(Smem &sm, const DevProg *gp) {
 // statements get a table row.  Chunks are processed in tiles of up to `cap`
 // chunks.  Per tile:
 //   clear — each row's owner entries over its own address range;
-//   build — pass 0 stores every access's owner, pass 1 turns an entry that sees
-//           another owner into MULTI (plain stores); only (statement, block)
-//           segments whose chunk mask meets the tile are read;
-//   probe — pass 2: an access (owner o, address a) of statement i and a pending
+//   build — every access installs its owner with a CAS on an empty entry and
+//           turns an entry holding another owner into MULTI; only (statement,
+//           block) segments whose chunk mask meets the tile are read;
+//   probe — an access (owner o, address a) of statement i and a pending
 //           partner j form a witness iff j's entry at a is neither empty nor
 //           o (a MULTI entry always differs; j == i is the self race).  Each
 //           thread probes its eight addresses per partner and skips partners
@@ -271,21 +271,24 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
             sm.chi[st] = c1;
         }
         __syncthreads();
-        // clear each row over the word-aligned span of its column range
-        {
-            const uint32_t wpr = cols >> 1;  // words per row
-            for (uint32_t u = threadIdx.x; u < n_rows * wpr; u += blockDim.x) {
-                const uint32_t r = u / wpr, w = u - r * wpr;
-                const uint32_t st = sm.row_list[r];
-                if (sm.clo[st] <= sm.chi[st] && w >= (sm.clo[st] >> 1) && w <= (sm.chi[st] >> 1))
-                    reinterpret_cast<uint32_t *>(tab + (size_t)st * cols)[w] = 0xFFFFFFFFu;
-            }
+        // clear each row over the word-aligned span of its column range (a warp per row)
+        for (uint32_t r = warp; r < n_rows; r += nwarps) {
+            const uint32_t st = sm.row_list[r];
+            const uint32_t c0 = sm.clo[st], c1 = sm.chi[st];
+            if (c0 > c1) continue;
+            uint32_t *row32 = reinterpret_cast<uint32_t *>(tab + (size_t)st * cols);
+            for (uint32_t w = (c0 >> 1) + lane; w <= (c1 >> 1); w += 32) row32[w] = 0xFFFFFFFFu;
         }
-        // pass 0: every access stores its owner (one of them wins);
-        // pass 1: an access that finds another owner stores MULTI;
-        // pass 2: probe the pending partners.
+        // pass 0: each access installs its owner with a CAS on an empty entry;
+        //         one that finds another owner stores MULTI (an entry only ever
+        //         goes empty -> one owner -> MULTI, so the end state is exact);
+        // pass 1: probe the pending partners.
+        // When the tile holds every remaining chunk and they are chunks 0..k-1
+        // of the address space, every access is in the tile and the column of
+        // an address is the address itself.
+        const bool identity = pending == 0 && sel == ((k >= 64) ? ~0ull : ((1ull << k) - 1ull));
         uint4 held0 = make_uint4(0, 0, 0, 0), held1 = held0;
-        for (uint32_t pass = 0; pass < 3; ++pass) {
+        for (uint32_t pass = 0; pass < 2; ++pass) {
             for (uint32_t base = 0; base < n_segs; base += kSegCap) {
                 if (pass == 0 || !one_batch) {
                     // segments of this batch whose chunks meet the tile
@@ -321,7 +324,7 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                     const uint32_t act8 = (sm.act[st][v >> 2] >> ((v & 3u) * 8u)) & 0xFFu;
                     if (!act8) continue;
                     uint32_t pend = 0;
-                    if (pass == 2) {
+                    if (pass == 1) {
                         pend = sm.pend_row[st] & ~*(volatile uint32_t *)&rows_out[st];
                         if (!pend) continue;
                     }
@@ -333,30 +336,36 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                         if (slot_i) held1 = q; else held0 = q;
                     }
                     const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-                    if (pass < 2) {
+                    if (pass == 0) {
                         uint16_t *row = tab + (size_t)st * cols;
 #pragma unroll
                         for (uint32_t e = 0; e < 8; ++e) {
                             if (!((act8 >> e) & 1u)) continue;
                             const uint32_t a = (w4[e >> 1] >> ((e & 1u) * 16u)) & 0xFFFFu;
-                            const uint32_t slot = sm.chunk_slot[a >> kChunkShift];
-                            if (slot == 0xFFu) continue;
-                            const uint32_t idx = slot * kChunkWords + (a & (kChunkWords - 1u));
-                            const uint16_t owner = kInter ? (uint16_t)blk : (uint16_t)(v * 8u + e);
-                            if (pass == 0) {
-                                row[idx] = owner;
-                            } else if (row[idx] != owner) {
-                                row[idx] = kMulti;
+                            uint32_t idx;
+                            if (identity) {
+                                idx = a;
+                            } else {
+                                const uint32_t slot = sm.chunk_slot[a >> kChunkShift];
+                                if (slot == 0xFFu) continue;
+                                idx = slot * kChunkWords + (a & (kChunkWords - 1u));
                             }
+                            const uint16_t owner = kInter ? (uint16_t)blk : (uint16_t)(v * 8u + e);
+                            const uint16_t old = atomicCAS(row + idx, kEmpty, owner);
+                            if (old != kEmpty && old != owner) row[idx] = kMulti;
                         }
                     } else {
                         uint32_t col[8];
 #pragma unroll
                         for (uint32_t e = 0; e < 8; ++e) {
                             const uint32_t a = (w4[e >> 1] >> ((e & 1u) * 16u)) & 0xFFFFu;
-                            const uint32_t slot = sm.chunk_slot[a >> kChunkShift];
-                            col[e] = (((act8 >> e) & 1u) && slot != 0xFFu)
-                                         ? slot * kChunkWords + (a & (kChunkWords - 1u)) : 0xFFFFFFFFu;
+                            if (identity) {
+                                col[e] = ((act8 >> e) & 1u) ? a : 0xFFFFFFFFu;
+                            } else {
+                                const uint32_t slot = sm.chunk_slot[a >> kChunkShift];
+                                col[e] = (((act8 >> e) & 1u) && slot != 0xFFu)
+                                             ? slot * kChunkWords + (a & (kChunkWords - 1u)) : 0xFFFFFFFFu;
+                            }
                         }
                         for (uint32_t jt = pend; jt; jt &= jt - 1u) {
                             const uint32_t j = __ffs(jt) - 1u;
