@@ -189,6 +189,7 @@ def run_ours(args, rank, world, local):
             dist.barrier()
         torch.cuda.synchronize()
 
+    shape = batch.tune()  # the autotuner picks the CTA shape for this batch
     for _ in range(args.warmup):
         batch.run()
     barrier()
@@ -264,6 +265,8 @@ def run_ours(args, rank, world, local):
             "config": {"workload": args.workload, "programs": n, "blocks": wl.blocks, "threads": wl.threads,
                        "stmts": wl.n_stmts, "m_words": wl.m_words, "seed": wl.seed,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "cta_shape": {"threads": [512, 256, 256, 1024][shape],
+                                     "ctas_per_sm": [2, 3, 4, 1][shape], "picked_by": "autotuner"},
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,

@@ -228,6 +228,16 @@ gr_status gr_expand_packed(const void *d_arena, void *d_scratch, uint64_t scratc
 gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                              uint64_t scratch_bytes, gr_repair_result *d_out, void *stream);
 
+/* Autotuner: time every CTA shape the persistent repair is built for (threads
+ * per CTA x CTAs per SM, with the owner-table budget that shape leaves) on
+ * this arena, remember the fastest for later gr_repair_packed /
+ * gr_repair_expanded / gr_check_packed calls on the same (d_arena, n), and
+ * return its index in shape_out (may be NULL).  Runs the repair several times
+ * into d_out and synchronises the stream.  The host-pointer batch calls tune
+ * the same way by themselves, once per batch size class. */
+gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                         uint64_t scratch_bytes, gr_repair_result *d_out, void *stream, uint32_t *shape_out);
+
 /* One check per program of a device-resident packed arena under d_masks[p]. */
 gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_masks,
                           void *d_scratch, uint64_t scratch_bytes, gr_witnesses *d_out,

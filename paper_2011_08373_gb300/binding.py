@@ -74,7 +74,7 @@ EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair"
            "gr_solve", "gr_repair_batch", "gr_check_batch", "gr_pack_size", "gr_pack",
            "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded",
            "gr_repair_packed_noalloc", "gr_server_create", "gr_server_submit", "gr_server_poll",
-           "gr_server_drain", "gr_server_stats", "gr_server_destroy"]
+           "gr_server_drain", "gr_server_stats", "gr_server_destroy", "gr_tune_packed"]
 
 
 def lib():
@@ -118,6 +118,8 @@ def lib():
             L.gr_server_drain.argtypes = [C.c_void_p, C.c_uint32]
             L.gr_server_stats.argtypes = [C.c_void_p, P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]
             L.gr_server_destroy.argtypes = [C.c_void_p]
+            L.gr_tune_packed.argtypes = [C.c_void_p, C.c_uint32, P(gr_options), C.c_void_p, C.c_uint64,
+                                         C.c_void_p, C.c_void_p, P(C.c_uint32)]
             L.gr_check_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint64,
                                           C.c_void_p, C.c_void_p]
             for name in EXPORTS[2:]:
@@ -397,6 +399,18 @@ class DeviceBatch:
         _check(lib().gr_repair_packed(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
                                       C.c_void_p(self._scratch_ptr), self.scratch_bytes,
                                       C.c_void_p(self._out_ptr), C.c_void_p(st)))
+
+    def tune(self, stream: Optional[int] = None) -> int:
+        """Pick the fastest CTA shape for this batch (gr_tune_packed)."""
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        shape = C.c_uint32()
+        _check(lib().gr_tune_packed(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
+                                    C.c_void_p(self._scratch_ptr), self.scratch_bytes,
+                                    C.c_void_p(self._out_ptr), C.c_void_p(st), C.byref(shape)))
+        self.shape = shape.value
+        return shape.value
 
     def expand(self, stream: Optional[int] = None) -> None:
         """Only the trace expansion (first half of run())."""

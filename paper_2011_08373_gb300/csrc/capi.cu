@@ -8,7 +8,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -192,6 +194,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     ArenaHeader *H = reinterpret_cast<ArenaHeader *>(arena);
     H->magic = kArenaMagic;
     H->n_progs = n;
+    for (uint32_t p = 0; p < n; ++p) H->s_max = std::max(H->s_max, progs[p].n_stmts);
     H->progs_off = L.progs_off;
     H->order_off = L.order_off;
     H->segbase_off = L.segbase_off;
@@ -271,6 +274,21 @@ namespace {
 // Per-device workspace
 // ---------------------------------------------------------------------------
 
+struct SizeClass {
+    uint32_t s_max, bt_log2, m_chunks, global, n_log2;
+    bool operator<(const SizeClass &o) const {
+        return std::tie(s_max, bt_log2, m_chunks, global, n_log2) <
+               std::tie(o.s_max, o.bt_log2, o.m_chunks, o.global, o.n_log2);
+    }
+};
+
+uint32_t ceil_log2(uint64_t x) {
+    uint32_t l = 0;
+    while ((1ull << l) < x) ++l;
+    return l;
+}
+
+
 struct DeviceBuf {
     void *p = nullptr;
     size_t cap = 0;
@@ -294,6 +312,8 @@ struct Workspace {
     int smem_per_sm = 0;
     uint32_t max_dyn = 0;
     DeviceBuf arena, scratch, out, aux;
+    std::map<SizeClass, uint32_t> class_shape;                         // tuned host batches
+    std::map<std::pair<const void *, uint32_t>, std::pair<uint32_t, uint32_t>> arena_shape;  // (shape, s_max)
     uint8_t *host_arena = nullptr;  // pinned staging for the packed arena
     size_t host_arena_cap = 0;
 };
@@ -324,24 +344,89 @@ gr_status ensure_configured(Workspace &ws) {
     return GR_OK;
 }
 
-LaunchCfg choose_cfg(const Workspace &ws, uint32_t n) {
-    // Two CTAs per SM: the owner table takes what is left of half the SM's
-    // shared memory after the fixed part (1 KB per CTA is reserved).
-    LaunchCfg c;
-    const size_t half = (size_t)ws.smem_per_sm / 2;
+// Launch configuration of CTA shape `shape` for n programs whose largest has
+// s_max statements: the owner table takes what is left of the SM's shared
+// memory share after the fixed part (1 KB per CTA is reserved).  table_bytes
+// is 0 when the shape cannot hold one address chunk of s_max rows.
+LaunchCfg shape_cfg(const Workspace &ws, uint32_t n, uint32_t shape, uint32_t s_max) {
+    const LaunchShape sh = kShapes[shape];
+    LaunchCfg c{0, 0, shape};
+    const size_t per_cta = (size_t)ws.smem_per_sm / sh.ctas_per_sm;
     const size_t fixed = fixed_smem_bytes() + 1024;
-    size_t table = half > fixed ? (half - fixed) / 2048 * 2048 : 0;
+    size_t table = per_cta > fixed ? (per_cta - fixed) / 2048 * 2048 : 0;
+    const size_t room = ws.max_dyn > fixed_smem_bytes() ? (ws.max_dyn - fixed_smem_bytes()) / 2048 * 2048 : 0;
+    table = std::min(table, room);
+    if (shape == 0) table = std::min<size_t>(table, 96u * 1024u);
+    const size_t need = std::max<size_t>((size_t)std::max(s_max, 1u) * 2u * kChunkWords, mhs_smem_bytes());
     static_assert(kMinTableBytes >= 25u * 2u * kChunkWords, "one chunk for 25 rows");
-    if (table > 96u * 1024u) table = 96u * 1024u;
-    uint32_t per_sm = 2;
-    if (table < kMinTableBytes) {
-        table = kMinTableBytes;
-        per_sm = 1;
-    }
+    if (table < need) return c;
     c.table_bytes = (uint32_t)table;
-    c.grid = std::min<uint32_t>(n, (uint32_t)ws.sms * per_sm);
-    if (c.grid == 0) c.grid = 1;
+    c.grid = std::max<uint32_t>(1u, std::min<uint32_t>(n, (uint32_t)ws.sms * sh.ctas_per_sm));
     return c;
+}
+
+// Default shape (512 threads, 2 CTAs per SM) unless it cannot hold the rows.
+LaunchCfg choose_cfg(const Workspace &ws, uint32_t n, uint32_t s_max = GR_MAX_STMTS) {
+    LaunchCfg c = shape_cfg(ws, n, 0, s_max);
+    if (!c.table_bytes) c = shape_cfg(ws, n, 3, s_max);
+    return c;
+}
+
+// ---- autotuner: the fastest CTA shape per batch size class ---------------
+
+SizeClass size_class(const gr_program *progs, const gr_launch *ls, uint32_t n) {
+    SizeClass k{0, 0, 0, 0, ceil_log2(n)};
+    for (uint32_t p = 0; p < n; ++p) {
+        k.s_max = std::max(k.s_max, progs[p].n_stmts);
+        k.bt_log2 = std::max(k.bt_log2, ceil_log2((uint64_t)ls[p].blocks * ls[p].threads));
+        const uint32_t m = std::max(progs[p].m_shared, progs[p].m_global);
+        k.m_chunks = std::max(k.m_chunks, (m + kChunkWords - 1) / kChunkWords);
+        for (uint32_t s = 0; s < progs[p].n_stmts; ++s)
+            if (progs[p].stmts[s].space == GR_GLOBAL) k.global = 1;
+    }
+    return k;
+}
+
+// Time every shape that can hold the batch (traces already expanded into
+// d_scratch) and return the fastest.  Synchronises the stream.
+gr_status tune_shapes(const Workspace &ws, const void *d_arena, uint32_t n, const gr_options &o, void *d_scratch,
+                      gr_repair_result *d_out, cudaStream_t st, uint32_t s_max, uint32_t *best_shape) {
+    float best = 1e30f;
+    *best_shape = choose_cfg(ws, n, s_max).shape;
+    cudaEvent_t e0, e1;
+    GR_CUDA(cudaEventCreate(&e0));
+    GR_CUDA(cudaEventCreate(&e1));
+    for (uint32_t sh = 0; sh < kNumShapes; ++sh) {
+        const LaunchCfg cfg = shape_cfg(ws, n, sh, s_max);
+        if (!cfg.table_bytes) continue;
+        float ms = 0;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run warms the shape
+            GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
+            GR_CUDA(cudaEventRecord(e0, st));
+            GR_CUDA(launch_repair(d_arena, n, o, d_scratch, d_out, cfg, st));
+            GR_CUDA(cudaEventRecord(e1, st));
+            GR_CUDA(cudaEventSynchronize(e1));
+            GR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (ms < best) {
+            best = ms;
+            *best_shape = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return GR_OK;
+}
+
+// Launch configuration for a device arena: its tuned shape if gr_tune_packed
+// ran on it, else the default.
+LaunchCfg packed_cfg(const Workspace &ws, const void *d_arena, uint32_t n) {
+    auto it = ws.arena_shape.find({d_arena, n});
+    if (it != ws.arena_shape.end()) {
+        const LaunchCfg c = shape_cfg(ws, n, it->second.first, it->second.second);
+        if (c.table_bytes) return c;
+    }
+    return choose_cfg(ws, n);
 }
 
 uint32_t expand_grid(const Workspace &ws) { return (uint32_t)ws.sms * 8u; }
@@ -462,7 +547,7 @@ gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *op
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
     GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
-    GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, choose_cfg(*ws, n), st));
+    GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
     return GR_OK;
 }
 
@@ -494,7 +579,33 @@ gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *
     if ((s = ensure_configured(*ws)) != GR_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
-    GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, choose_cfg(*ws, n), st));
+    GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
+    return GR_OK;
+}
+
+gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                         uint64_t scratch_bytes, gr_repair_result *d_out, void *stream, uint32_t *shape_out) {
+    if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    gr_status s = validate_opts(opts);
+    if (s != GR_OK) return s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ArenaHeader h;
+    GR_CUDA(cudaMemcpyAsync(&h, d_arena, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    if (h.magic != kArenaMagic || h.n_progs != n) return fail(GR_EINVAL, "d_arena is not a packed arena of %u programs", n);
+    if (scratch_bytes < h.scratch_bytes) return fail(GR_ECAPACITY, "scratch needs %llu bytes", (unsigned long long)h.scratch_bytes);
+    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
+    uint32_t shape = 0;
+    if ((s = tune_shapes(*ws, d_arena, n, opts_or_default(opts), d_scratch, d_out, st, h.s_max, &shape)) != GR_OK)
+        return s;
+    ws->arena_shape[{d_arena, n}] = {shape, h.s_max};
+    if (shape_out) *shape_out = shape;
     return GR_OK;
 }
 
@@ -512,7 +623,7 @@ gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_mas
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
     GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
-    GR_CUDA(launch_check(d_arena, n, d_masks, d_scratch, d_out, choose_cfg(*ws, n), st));
+    GR_CUDA(launch_check(d_arena, n, d_masks, d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
     return GR_OK;
 }
 
@@ -536,8 +647,21 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     if ((s = ws->out.ensure((size_t)n * sizeof(gr_repair_result))) != GR_OK) return s;
     GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
     GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
+    // the batch's size class picks the CTA shape; the first batch of a class tunes it
+    const SizeClass cls = size_class(progs, launches, n);
+    auto it = ws->class_shape.find(cls);
+    if (it == ws->class_shape.end()) {
+        uint32_t shape = 0;
+        gr_status ts = tune_shapes(*ws, ws->arena.p, n, opts_or_default(opts), ws->scratch.p,
+                                   static_cast<gr_repair_result *>(ws->out.p), st, cls.s_max, &shape);
+        if (ts != GR_OK) return ts;
+        it = ws->class_shape.emplace(cls, shape).first;
+    }
+    LaunchCfg cfg = shape_cfg(*ws, n, it->second, cls.s_max);
+    if (!cfg.table_bytes) cfg = choose_cfg(*ws, n, cls.s_max);
+    GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
     GR_CUDA(launch_repair(ws->arena.p, n, opts_or_default(opts), ws->scratch.p,
-                          static_cast<gr_repair_result *>(ws->out.p), choose_cfg(*ws, n), st));
+                          static_cast<gr_repair_result *>(ws->out.p), cfg, st));
     GR_CUDA(cudaMemcpyAsync(out, ws->out.p, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost, st));
     return finish_sync(ws->scratch.p, st);
 }
@@ -564,8 +688,12 @@ gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches, con
     GR_CUDA(cudaMemcpyAsync(ws->aux.p, masks, (size_t)n * 4, cudaMemcpyHostToDevice, st));
     GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
     GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
+    const SizeClass cls = size_class(progs, launches, n);
+    auto it = ws->class_shape.find(cls);
+    LaunchCfg cfg = it == ws->class_shape.end() ? choose_cfg(*ws, n, cls.s_max) : shape_cfg(*ws, n, it->second, cls.s_max);
+    if (!cfg.table_bytes) cfg = choose_cfg(*ws, n, cls.s_max);
     GR_CUDA(launch_check(ws->arena.p, n, static_cast<const uint32_t *>(ws->aux.p), ws->scratch.p,
-                         static_cast<gr_witnesses *>(ws->out.p), choose_cfg(*ws, n), st));
+                         static_cast<gr_witnesses *>(ws->out.p), cfg, st));
     GR_CUDA(cudaMemcpyAsync(out, ws->out.p, (size_t)n * sizeof(gr_witnesses), cudaMemcpyDeviceToHost, st));
     return finish_sync(ws->scratch.p, st);
 }

@@ -54,7 +54,7 @@ static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");
 // Arena = ArenaHeader | DevProg[n] | order[n] | seg_base[n+1] | perm[]
 // Scratch = ctrl (256 B) | segmask u64[] | segrange u32[] | trace u16[]
 struct ArenaHeader {
-    uint32_t magic, n_progs, _r0, _r1;
+    uint32_t magic, n_progs, s_max, _r1;  // s_max: most statements of any program
     uint64_t progs_off, order_off, segbase_off, perm_off;  // bytes from the arena start
     uint64_t n_segments;                                   // sum over programs of S*B
     uint64_t scratch_segmask_off, scratch_trace_off;       // bytes from the scratch start
@@ -76,7 +76,17 @@ struct LoopState {
 struct LaunchCfg {
     uint32_t grid;         // CTAs of the persistent kernels
     uint32_t table_bytes;  // shared-memory owner-table budget per CTA
+    uint32_t shape;        // index into kShapes
 };
+
+// CTA shapes the persistent kernels are instantiated for.
+struct LaunchShape {
+    uint32_t threads, ctas_per_sm;
+};
+constexpr uint32_t kNumShapes = 4;
+extern const LaunchShape kShapes[kNumShapes];
+size_t dyn_bytes(uint32_t table_bytes);
+size_t mhs_smem_bytes();
 
 // Host-side helpers (capi.cu).
 struct Layout {

@@ -81,6 +81,7 @@ __device__ __forceinline__ uint32_t *mh_cl(Smem &sm) {
 }
 
 size_t fixed_smem_bytes() { return kFixedSmem; }
+size_t mhs_smem_bytes() { return align_up(sizeof(MhsSmem), 16); }
 
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
@@ -1070,8 +1071,10 @@ __device__ __forceinline__ Dyn dyn_smem() {
 }
 
 // K4: persistent repair.  CTAs take programs from a queue in the host's order
-// (largest first) and run Algorithm 1 on each.
-__global__ void __launch_bounds__(kThreads, 2)
+// (largest first) and run Algorithm 1 on each.  Instantiated for several CTA
+// shapes (threads x CTAs per SM); the host picks one per batch.
+template <uint32_t NT, uint32_t MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_repair(const uint8_t *__restrict__ arena, uint32_t n, gr_options opts, uint8_t *__restrict__ scratch,
              gr_repair_result *__restrict__ out, uint32_t table_bytes) {
     Dyn d = dyn_smem();
@@ -1105,7 +1108,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // One check per program under masks[p] (persistent, same queue).
-__global__ void __launch_bounds__(kThreads, 2)
+template <uint32_t NT, uint32_t MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_check(const uint8_t *__restrict__ arena, uint32_t n, const uint32_t *__restrict__ masks,
             uint8_t *__restrict__ scratch, gr_witnesses *__restrict__ out, uint32_t table_bytes) {
     Dyn d = dyn_smem();
@@ -1283,15 +1287,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(const uint32_t *__restric
 // Host launchers
 // ---------------------------------------------------------------------------
 
-static size_t dyn_bytes(uint32_t table_bytes) {
+size_t dyn_bytes(uint32_t table_bytes) {
     const size_t region = table_bytes > sizeof(MhsSmem) ? table_bytes : sizeof(MhsSmem);
     return kFixedSmem + align_up(region, 16);
 }
 
+// The CTA shapes of the persistent kernels: {threads, CTAs per SM}.
+const LaunchShape kShapes[kNumShapes] = {{512, 2}, {256, 3}, {256, 4}, {1024, 1}};
+
+template <typename F>
+static cudaError_t set_smem(F *f, uint32_t max_dynamic_smem) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, (const void *)f);
+    if (e != cudaSuccess) return e;
+    const size_t cap = max_dynamic_smem > a.sharedSizeBytes ? max_dynamic_smem - a.sharedSizeBytes : 0;
+    return cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+}
+
 cudaError_t configure_kernels(uint32_t max_dynamic_smem) {
     cudaError_t e;
-    const void *fns[] = {(const void *)k_repair, (const void *)k_check, (const void *)k_plain_init,
-                         (const void *)k_plain_check, (const void *)k_plain_solve, (const void *)k_solve};
+    const void *fns[] = {(const void *)k_plain_init, (const void *)k_plain_check, (const void *)k_plain_solve,
+                         (const void *)k_solve};
     for (const void *f : fns) {
         cudaFuncAttributes a;
         e = cudaFuncGetAttributes(&a, f);
@@ -1300,6 +1316,14 @@ cudaError_t configure_kernels(uint32_t max_dynamic_smem) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
         if (e != cudaSuccess) return e;
     }
+    if ((e = set_smem(k_repair<512, 2>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_repair<256, 3>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_repair<256, 4>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_repair<1024, 1>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_check<512, 2>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_check<256, 3>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_check<256, 4>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_check<1024, 1>, max_dynamic_smem)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1310,16 +1334,29 @@ cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint32_t grid, c
 
 cudaError_t launch_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
                           gr_repair_result *d_out, LaunchCfg cfg, cudaStream_t st) {
-    k_repair<<<cfg.grid, kThreads, dyn_bytes(cfg.table_bytes), st>>>(
-        static_cast<const uint8_t *>(d_arena), n, opts, static_cast<uint8_t *>(d_scratch), d_out, cfg.table_bytes);
+    const uint8_t *a = static_cast<const uint8_t *>(d_arena);
+    uint8_t *sc = static_cast<uint8_t *>(d_scratch);
+    const size_t smem = dyn_bytes(cfg.table_bytes);
+    switch (cfg.shape) {
+        case 1: k_repair<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
+        case 2: k_repair<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
+        case 3: k_repair<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
+        default: k_repair<512, 2><<<cfg.grid, 512, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
                          gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st) {
-    k_check<<<cfg.grid, kThreads, dyn_bytes(cfg.table_bytes), st>>>(
-        static_cast<const uint8_t *>(d_arena), n, d_masks, static_cast<uint8_t *>(d_scratch), d_out,
-        cfg.table_bytes);
+    const uint8_t *a = static_cast<const uint8_t *>(d_arena);
+    uint8_t *sc = static_cast<uint8_t *>(d_scratch);
+    const size_t smem = dyn_bytes(cfg.table_bytes);
+    switch (cfg.shape) {
+        case 1: k_check<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
+        case 2: k_check<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
+        case 3: k_check<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
+        default: k_check<512, 2><<<cfg.grid, 512, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
+    }
     return cudaGetLastError();
 }
 
