@@ -250,6 +250,20 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             if (st.space == GR_SHARED) D.shared_rows |= 1u << s;
             else D.global_rows |= 1u << s;
         }
+        // access-pattern classes: statements with the same array, map and
+        // guard touch the same words from the same threads
+        for (uint32_t s = 0; s < 32; ++s) D.rep[s] = (uint8_t)s;
+        for (uint32_t s = 1; s < S; ++s) {
+            const DevStmt &a = D.stmts[s];
+            for (uint32_t q = 0; q < s; ++q) {
+                const DevStmt &b = D.stmts[q];
+                if (a.space == b.space && a.kind == b.kind && a.am == b.am && a.bm == b.bm && a.cm == b.cm &&
+                    a.perm_off == b.perm_off && a.gk == b.gk && a.gr == b.gr && a.m == b.m) {
+                    D.rep[s] = (uint8_t)q;
+                    break;
+                }
+            }
+        }
         if (P.perm && P.perm_len) memcpy(perm + L.perm_base[p], P.perm, (size_t)P.perm_len * 4);
         segbase[p] = L.segmask_elem[p];
         cost[p] = (uint64_t)S * ls[p].blocks * t_pad_of(ls[p].threads);

@@ -47,6 +47,7 @@ struct DevProg {
     uint32_t weights[GR_MAX_SLOTS];
     uint16_t slot_gk[GR_MAX_SLOTS];
     uint16_t slot_gr[GR_MAX_SLOTS];
+    uint8_t rep[32];       // lowest statement with the same array, map and guard
     DevStmt stmts[GR_MAX_STMTS];
 };
 static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");

@@ -53,6 +53,7 @@ struct Smem {
     uint32_t traj[GR_MAX_ITERS];
     uint32_t row_list[32];
     uint32_t pend_row[32];  // pending partners of each statement in the current pass
+    uint32_t rep_pend[32], rep_conf[32];  // pending / witnessed pattern pairs (lower -> higher)
     uint32_t n_seg_list, pass_rows;
     uint32_t rlo[32], rhi[32], clo[32], chi[32];
     uint32_t seg_list[kSegCap];
@@ -177,6 +178,10 @@ __device__ void load_program(Smem &sm, const DevProg *gp) {
 //           o (a MULTI entry always differs; j == i is the self race).  Each
 //           thread probes its eight addresses per partner and skips partners
 //           already witnessed.
+// Statements with the same array, map and guard touch the same addresses from
+// the same threads, so they share one row: the pass works on the lowest
+// statement of each such class, and a pair inside one class conflicts iff the
+// class's row holds a MULTI (its self pair).
 template <bool kInter>
 __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const uint16_t *trace,
                            const uint64_t *segmask, const uint32_t *segrange, uint32_t rows,
@@ -196,12 +201,22 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
         uint32_t pend = 0;
         if (in) pend = rows & ph[i] & ~((1u << i) - 1u) & (((wmask >> i) & 1u) ? 0xFFFFFFFFu : wmask) & ~rows_out[i];
         sm.pend_row[i] = pend;
-        // statements of pending pairs
-        uint32_t involved = pend | (pend ? (1u << i) : 0u);
+        // statements with the same access pattern have the same owner row: a
+        // pending pair becomes a pair of pattern representatives (lower first)
+        sm.rep_pend[lane] = 0;
+        sm.rep_conf[lane] = 0;
+        __syncwarp();
+        for (uint32_t t = pend; t; t &= t - 1u) {
+            const uint32_t ri = sm.prog.rep[i], rj = sm.prog.rep[__ffs(t) - 1u];
+            atomicOr(&sm.rep_pend[min(ri, rj)], 1u << max(ri, rj));
+        }
+        __syncwarp();
+        const uint32_t rp = sm.rep_pend[lane];
+        uint32_t involved = rp | (rp ? (1u << lane) : 0u);
         for (uint32_t o = 16; o > 0; o >>= 1) involved |= __shfl_xor_sync(0xFFFFFFFFu, involved, o);
-        const bool keep = (involved >> i) & 1u;
+        const bool keep = (involved >> lane) & 1u;
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-        if (keep) sm.row_list[__popc(bal & ((1u << lane) - 1u))] = i;
+        if (keep) sm.row_list[__popc(bal & ((1u << lane) - 1u))] = lane;
         if (lane == 0) sm.pass_rows = involved;
         sm.rlo[lane] = 0xFFFFu;
         sm.rhi[lane] = 0u;
@@ -326,7 +341,7 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                     if (!act8) continue;
                     uint32_t pend = 0;
                     if (pass == 1) {
-                        pend = sm.pend_row[st] & ~*(volatile uint32_t *)&rows_out[st];
+                        pend = sm.rep_pend[st] & ~*(volatile uint32_t *)&sm.rep_conf[st];
                         if (!pend) continue;
                     }
                     uint4 q;
@@ -370,7 +385,7 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                         }
                         for (uint32_t jt = pend; jt; jt &= jt - 1u) {
                             const uint32_t j = __ffs(jt) - 1u;
-                            if ((*(volatile uint32_t *)&rows_out[st] >> j) & 1u) continue;
+                            if ((*(volatile uint32_t *)&sm.rep_conf[st] >> j) & 1u) continue;
                             const uint32_t c0 = sm.clo[j], c1 = sm.chi[j];
                             const uint16_t *rj = tab + (size_t)j * cols;
                             bool hit = false;
@@ -383,7 +398,7 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                                     hit |= o != kEmpty && o != mine;
                                 }
                             }
-                            if (hit) atomicOr(&rows_out[st], 1u << j);
+                            if (hit) atomicOr(&sm.rep_conf[st], 1u << j);
                         }
                     }
                 }
@@ -391,6 +406,18 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
             __syncthreads();
         }
     }
+    // pattern conflicts back to statement pairs
+    if (warp == 0) {
+        const uint32_t i = lane;
+        uint32_t conf = 0;
+        for (uint32_t t = sm.pend_row[i]; t; t &= t - 1u) {
+            const uint32_t j = __ffs(t) - 1u;
+            const uint32_t ri = sm.prog.rep[i], rj = sm.prog.rep[j];
+            if ((sm.rep_conf[min(ri, rj)] >> max(ri, rj)) & 1u) conf |= 1u << j;
+        }
+        if (conf) atomicOr(&rows_out[i], conf);
+    }
+    __syncthreads();
 }
 
 __device__ uint64_t block_chunks(const uint64_t *segmask, uint32_t B, uint32_t rows, uint32_t blk) {
