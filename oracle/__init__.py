@@ -83,11 +83,14 @@ def _configure(path):
                               C.c_uint32, C.POINTER(C.c_uint32), C.c_uint32, C.c_uint32,
                               C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]
     lib.orc_solve.restype = C.c_int
-    lib.orc_repair.argtypes = [C.POINTER(_Prog), C.c_int, C.c_int, C.c_uint32,
+    lib.orc_repair.argtypes = [C.POINTER(_Prog), C.c_int, C.c_int, C.c_uint32, C.c_int,
                                C.POINTER(_Result)]
+    lib.orc_greedy.argtypes = [C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.c_uint32,
+                               C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32)]
+    lib.orc_greedy.restype = C.c_int
     lib.orc_repair.restype = None
     lib.orc_repair_batch.argtypes = [C.POINTER(_Prog), C.POINTER(C.c_int32), C.c_uint32,
-                                     C.c_int, C.c_uint32, C.POINTER(_Result), C.c_uint32]
+                                     C.c_int, C.c_uint32, C.c_int, C.POINTER(_Result), C.c_uint32]
     lib.orc_repair_batch.restype = None
     lib.orc_check_pair.argtypes = [C.POINTER(_Prog), C.c_uint32, C.c_uint32, C.c_uint32,
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
@@ -212,23 +215,35 @@ def _result_dict(r: _Result) -> dict:
             "access_pairs": r.access_pairs}
 
 
-def repair(p, mode=None, grid_enabled: bool = True, max_iters: int = 64) -> dict:
-    """Algorithm 1 on one program (mode defaults to ``p.mode``)."""
+def greedy(n_vars: int, weights, pos, forced: int = 0, forbidden: int = 0):
+    """The mhs strategy's greedy minimal hitting set, or None if infeasible."""
+    lib = _load()
+    w = (C.c_uint32 * max(1, n_vars))(*[int(x) for x in weights])
+    pa = (C.c_uint32 * max(1, len(pos)))(*[int(x) for x in pos])
+    mask = C.c_uint32()
+    if lib.orc_greedy(n_vars, w, pa, len(pos), forced, forbidden, C.byref(mask)):
+        return None
+    return mask.value
+
+
+def repair(p, mode=None, grid_enabled: bool = True, max_iters: int = 64, strategy: int = 0) -> dict:
+    """Algorithm 1 on one program (mode defaults to ``p.mode``); strategy 0 =
+    MaxSAT proposals, 1 = the mhs strategy."""
     lib = _load()
     m = _Marshalled(p)
     r = _Result()
     lib.orc_repair(C.byref(m.s), int(p.mode if mode is None else mode), int(grid_enabled),
-                   max_iters, C.byref(r))
+                   max_iters, strategy, C.byref(r))
     return _result_dict(r)
 
 
 def repair_batch(progs, grid_enabled: bool = True, max_iters: int = 64,
-                 n_threads: int = 1) -> list:
+                 n_threads: int = 1, strategy: int = 0) -> list:
     """Algorithm 1 on many programs, spread over ``n_threads`` CPU threads."""
     lib = _load()
     ms = [_Marshalled(p) for p in progs]
     arr = (_Prog * len(progs))(*[m.s for m in ms])
     modes = (C.c_int32 * len(progs))(*[int(p.mode) for p in progs])
     out = (_Result * len(progs))()
-    lib.orc_repair_batch(arr, modes, len(progs), int(grid_enabled), max_iters, out, n_threads)
+    lib.orc_repair_batch(arr, modes, len(progs), int(grid_enabled), max_iters, strategy, out, n_threads)
     return [_result_dict(out[i]) for i in range(len(progs))]

@@ -280,7 +280,57 @@ int orc_solve(uint32_t n, const uint32_t *w, const uint32_t *pos, uint32_t n_pos
     return 0;
 }
 
+/* The mhs strategy's hitting set (Section 2.4: a polynomial greedy algorithm
+ * after Johnson, 1974, giving a minimal hitting set).  Starting from the forced
+ * variables, repeatedly take the allowed (not forbidden) variable that hits the
+ * most clauses not yet hit per unit of weight — ratios compared by cross
+ * multiplication, ties to the lower index — until every clause is hit; then
+ * make the set minimal by dropping, from the highest index down, each
+ * non-forced variable whose removal leaves every clause hit.
+ * Returns 0 and the mask, or 1 if some clause has no allowed variable. */
+int orc_greedy(uint32_t n, const uint32_t *w, const uint32_t *pos, uint32_t n_pos, uint32_t forced,
+               uint32_t forbidden, uint32_t *mask_out) {
+    uint32_t x = forced;
+    if (forced & forbidden) return 1;
+    for (uint32_t c = 0; c < n_pos; c++)
+        if (!(pos[c] & x) && !(pos[c] & ~forbidden)) return 1;
+    for (;;) {
+        int best = -1;
+        uint32_t best_hits = 0;
+        for (uint32_t k = 0; k < n; k++) {
+            if (((x >> k) & 1u) || ((forbidden >> k) & 1u)) continue;
+            uint32_t hits = 0;
+            for (uint32_t c = 0; c < n_pos; c++)
+                if (!(pos[c] & x) && ((pos[c] >> k) & 1u)) hits++;
+            if (hits == 0) continue;
+            if (best < 0 || (uint64_t)hits * w[best] > (uint64_t)best_hits * w[k]) {
+                best = (int)k;
+                best_hits = hits;
+            }
+        }
+        if (best < 0) break;
+        x |= 1u << best;
+    }
+    for (int k = (int)n - 1; k >= 0; k--) {
+        if (!((x >> k) & 1u) || ((forced >> k) & 1u)) continue;
+        const uint32_t y = x & ~(1u << k);
+        int ok = 1;
+        for (uint32_t c = 0; c < n_pos && ok; c++)
+            if (!(pos[c] & y)) ok = 0;
+        if (ok) x = y;
+    }
+    *mask_out = x;
+    return 0;
+}
+
 /* Algorithm 1, with the exact clause of each witness.
+ *   strategy 0 (the paper's MaxSAT strategy): every proposal is the minimum
+ *     hitting set of the clauses so far.
+ *   strategy 1 (the paper's mhs strategy, its default): proposals are greedy
+ *     minimal hitting sets; when a clause has no allowed variable the MaxSAT
+ *     solve is used instead; once a greedy proposal is clean, one exact solve
+ *     decides: the same mask ends the loop, a lighter one is checked next and
+ *     the loop continues with exact proposals.
  *   mode 0 (repair, inspection off): existing barriers are forced on.
  *   mode 1 (remove, inspection on): no slot is forced; the existing mask is
  *     checked first as a probe whose witnesses seed the clause set, and is not
@@ -290,7 +340,7 @@ int orc_solve(uint32_t n, const uint32_t *w, const uint32_t *pos, uint32_t n_pos
  * proposed mask has no witness (repaired) or the clauses are unsatisfiable
  * (unrepairable); each race witness adds its clause, each divergent slot a
  * negative unit clause.  More than max_iters checks ends with status 2. */
-void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iters, orc_result *r) {
+void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iters, int strategy, orc_result *r) {
     memset(r, 0, sizeof(*r));
     const uint32_t n = p->n_stmts - 1;
     uint32_t grid = 0;
@@ -303,6 +353,7 @@ void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iter
     uint32_t m = 0;
     int probe = 0;
     int status = 0;
+    int greedy = strategy == 1;
     if (mode == 1) {
         m = p->existing_mask;
         probe = 1;
@@ -327,6 +378,16 @@ void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iter
         for (uint32_t i = 0; i < p->n_stmts; i++)
             if (w.intra[i] | w.inter[i]) any = 1;
         if (!any && !probe) {
+            if (greedy) {
+                /* one exact query: is the clean greedy proposal also the minimum? */
+                uint32_t xs;
+                uint64_t wt;
+                greedy = 0;
+                if (!orc_solve(n, p->slot_weight, clauses, n_cl, NULL, 0, forced, forbidden, &xs, &wt) && xs != m) {
+                    m = xs;
+                    continue;
+                }
+            }
             status = 0;
             r->mask = m;
             break;
@@ -335,6 +396,7 @@ void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iter
         n_cl = orc_clauses(p, &w, clauses, n_cl);
         forbidden |= w.diverge;
         uint64_t wt;
+        if (greedy && !orc_greedy(n, p->slot_weight, clauses, n_cl, forced, forbidden, &m)) continue;
         if (orc_solve(n, p->slot_weight, clauses, n_cl, NULL, 0, forced, forbidden, &m, &wt)) {
             status = 1;
             break;
@@ -356,7 +418,7 @@ done:
 typedef struct {
     const orc_prog *progs;
     const int32_t *modes;
-    int grid_enabled;
+    int grid_enabled, strategy;
     uint32_t max_iters;
     orc_result *out;
     uint32_t n, stride, first;
@@ -365,18 +427,18 @@ typedef struct {
 static void *orc_worker(void *arg) {
     orc_job *j = (orc_job *)arg;
     for (uint32_t i = j->first; i < j->n; i += j->stride)
-        orc_repair(&j->progs[i], j->modes[i], j->grid_enabled, j->max_iters, &j->out[i]);
+        orc_repair(&j->progs[i], j->modes[i], j->grid_enabled, j->max_iters, j->strategy, &j->out[i]);
     return NULL;
 }
 
 void orc_repair_batch(const orc_prog *progs, const int32_t *modes, uint32_t n, int grid_enabled,
-                      uint32_t max_iters, orc_result *out, uint32_t n_threads) {
+                      uint32_t max_iters, int strategy, orc_result *out, uint32_t n_threads) {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
     pthread_t th[256];
     orc_job jobs[256];
     for (uint32_t t = 0; t < n_threads; t++) {
-        jobs[t] = (orc_job){progs, modes, grid_enabled, max_iters, out, n, n_threads, t};
+        jobs[t] = (orc_job){progs, modes, grid_enabled, strategy, max_iters, out, n, n_threads, t};
         pthread_create(&th[t], NULL, orc_worker, &jobs[t]);
     }
     for (uint32_t t = 0; t < n_threads; t++) pthread_join(th[t], NULL);

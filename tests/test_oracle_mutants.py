@@ -36,6 +36,9 @@ MUTANTS = [
     ("read_read_pairs", "if (p->op[i] != 1 && p->op[j] != 1) continue;", ""),
     ("guard_negated", "return k == 0 || tid % k == r;", "return k == 0 || tid % k != r;"),
     ("weight_of_all_slots", "if ((x >> k) & 1u) wt += w[k];", "wt += w[k];"),
+    ("greedy_tie_to_higher_index", "(uint64_t)hits * w[best] > (uint64_t)best_hits * w[k]",
+     "(uint64_t)hits * w[best] >= (uint64_t)best_hits * w[k]"),
+    ("greedy_not_minimal", "        if (ok) x = y;", "        (void)ok;"),
     ("pairs_double_counted",
      "if (i == j && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;", ""),
 ]
@@ -47,6 +50,9 @@ def _all_pins():
         yield lambda c=case: pins.test_listing_repairs(c)
     for case in pins.GOLD["solver_cases"]:
         yield lambda c=case: pins.test_solver_paper_example(c)
+    yield pins.test_greedy_paper_example
+    for case in pins.GOLD["greedy_cases"]:
+        yield lambda c=case: pins.test_greedy_worked_cases(c)
     for s in range(16):
         yield lambda s=s: pins.test_check_matches_flag_reset_detector(s)
         yield lambda s=s: pins.test_check_matches_affine_closed_form(s)
@@ -56,6 +62,7 @@ def _all_pins():
         yield lambda s=s: pins.test_check_antitone_in_mask(s)
         yield lambda s=s: pins.test_clause_is_exact_filter(s)
         yield lambda s=s: pins.test_repair_path_independence(s)
+        yield lambda s=s: pins.test_greedy_minimal_and_within_johnson_bound(s)
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])

@@ -440,3 +440,65 @@ def test_check_pair_matches_check(seed):
                 assert b == bool((full["inter"][i] >> j) & 1)
                 total += n
         assert total == full["access_pairs"]
+
+
+# --------------------------------------------------------------------------
+# The mhs strategy (Section 2.4): greedy minimal hitting sets
+# --------------------------------------------------------------------------
+
+def test_greedy_paper_example():
+    """Section 2.4: on the positive clauses of the example the mhs is {b1, b2},
+    which breaks the negative clause; the strategy then falls back."""
+    case = GOLD["solver_cases"][0]
+    g = oracle.greedy(case["n_vars"], case["weights"], case["pos"])
+    assert g == case["greedy_mhs"]
+    assert any(g & n == n for n in case["neg"])
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_greedy_minimal_and_within_johnson_bound(seed):
+    """A greedy hitting set is minimal (no element can be dropped) and within
+    H(d) of the optimum, d the most clauses one variable hits (Johnson 1974,
+    Chvatal 1979 for weights)."""
+    rng = synth.SplitMix64(synth.program_seed(555, seed))
+    n = rng.randint(1, 12)
+    full = (1 << n) - 1
+    w = [rng.randint(1, 6) for _ in range(n)]
+    pos = [(rng.randint(1, full) & rng.randint(1, full)) or 1 for _ in range(rng.randint(1, 14))]
+    forced = rng.randint(0, full) & rng.randint(0, full) & rng.randint(0, full)
+    forbidden = rng.randint(0, full) & rng.randint(0, full) & rng.randint(0, full) & ~forced
+    g = oracle.greedy(n, w, pos, forced, forbidden)
+    opt = oracle.solve(n, w, pos, (), forced, forbidden)
+    if opt is None:
+        assert g is None
+        return
+    assert g is not None
+    assert (g & forced) == forced and not (g & forbidden)
+    assert all(g & c for c in pos)
+    for k in range(n):
+        if (g >> k) & 1 and not (forced >> k) & 1:
+            assert not all((g & ~(1 << k)) & c for c in pos), "not minimal"
+    live = [c for c in pos if not (c & forced)]
+    d = max([sum(1 for c in live if (c >> k) & 1) for k in range(n)] + [1])
+    harmonic = sum(1.0 / i for i in range(1, d + 1))
+    wf = sum(w[k] for k in range(n) if (forced >> k) & 1)
+    wg = sum(w[k] for k in range(n) if (g >> k) & 1)
+    assert wg - wf <= harmonic * (opt[1] - wf) + 1e-9
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_mhs_strategy_reaches_the_same_repair(seed):
+    """Clauses are exact, so the mhs strategy ends at the same lowest-key clean
+    mask as the MaxSAT strategy; only the trajectory differs."""
+    p = random_program(9500 + seed, s_max=6, b_max=2, t_max=8, m_max=12)
+    for grid_enabled in (True, False):
+        a = oracle.repair(p, grid_enabled=grid_enabled, strategy=0)
+        b = oracle.repair(p, grid_enabled=grid_enabled, strategy=1)
+        assert (a["status"], a["mask"], a["weight"]) == (b["status"], b["mask"], b["weight"])
+        assert b["iters"] <= 2 * p.n_slots + 4
+
+
+@pytest.mark.parametrize("case", GOLD["greedy_cases"], ids=[c["name"] for c in GOLD["greedy_cases"]])
+def test_greedy_worked_cases(case):
+    got = oracle.greedy(case["n_vars"], case["weights"], case["pos"], case["forced"], case["forbidden"])
+    assert got == case["expect"], case["cite"]
