@@ -123,9 +123,18 @@ typedef struct {
                                 pairs (global only) unless an enabled grid slot does */
 } gr_witnesses;
 
+/* Proposal strategies of Algorithm 1's Solve step (Section 2.4). */
+enum {
+    GR_STRATEGY_MAXSAT = 0, /* every proposal is the minimum-weight hitting set (--maxsat) */
+    GR_STRATEGY_MHS = 1     /* greedy minimal hitting sets (Johnson), the MaxSAT solve as the
+                               fallback when a clause cannot be hit, and one exact query once a
+                               proposal is clean (the paper's default) */
+};
+
 typedef struct {
     uint8_t grid_enabled; /* 0 = --disable-grid: every grid slot is forbidden */
-    uint8_t _pad[3];
+    uint8_t strategy;     /* GR_STRATEGY_*; both end at the same minimum mask */
+    uint8_t _pad[2];
     uint32_t max_iters;   /* checks allowed per program, 1..GR_MAX_ITERS; 0 = 64 */
 } gr_options;
 

@@ -103,6 +103,7 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
 
 gr_status validate_opts(const gr_options *o) {
     if (o && o->max_iters > GR_MAX_ITERS) return fail(GR_EINVAL, "max_iters above %d", GR_MAX_ITERS);
+    if (o && o->strategy > GR_STRATEGY_MHS) return fail(GR_EINVAL, "unknown strategy %u", o->strategy);
     return GR_OK;
 }
 
@@ -541,6 +542,7 @@ static gr_options opts_or_default(const gr_options *o) {
     d.max_iters = GR_MAX_ITERS;
     if (o) {
         d.grid_enabled = o->grid_enabled;
+        d.strategy = o->strategy;
         d.max_iters = o->max_iters ? o->max_iters : GR_MAX_ITERS;
     }
     return d;

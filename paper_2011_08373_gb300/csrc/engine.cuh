@@ -69,6 +69,7 @@ static_assert(sizeof(ArenaHeader) == 128, "ArenaHeader layout");
 // device memory between launches).
 struct LoopState {
     uint32_t mask, probe, done, status, iters, forced, forbidden, max_iters;
+    uint32_t greedy, _pad0;
     uint64_t access_pairs, t_start;
     uint32_t traj[GR_MAX_ITERS];
     uint32_t acc_intra[32], acc_inter[32];

@@ -68,6 +68,7 @@ struct Smem {
     unsigned long long chunk_acc;
     // loop state
     uint32_t mask, probe, done, status, iters, forced, forbidden, max_iters;
+    uint32_t greedy, step;  // mhs strategy: greedy proposals pending; kind of this step
     uint32_t diverge, n_cl, n_rows, item;
     uint32_t rel_sh, rel_gi, rel_gx, sol_found, sol_mask, sol_weight;
     uint32_t *err;  // device error word (scratch control area)
@@ -804,6 +805,83 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
     __syncthreads();
 }
 
+// The mhs strategy's proposal (Section 2.4, after Johnson 1974): starting from
+// the forced slots, repeatedly take the allowed slot that hits the most clauses
+// not yet hit per unit of weight (cross-multiplied ratios, ties to the lower
+// slot), then drop, from the highest slot down, every non-forced slot whose
+// removal leaves every clause hit.  sm.sol_found = 0 when a clause has no
+// allowed slot (or a forced slot is forbidden).  All threads must call.
+__device__ void mhs_greedy(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t *w, uint32_t n_cl,
+                           uint32_t forced, uint32_t forbidden) {
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31u;
+    const uint32_t *cl = mh.cl;
+    uint32_t *cnt = mh.wlo;  // hit counts per slot (the exact solver's table is free here)
+    __syncthreads();
+    if (tid == 0) {
+        mh.unsat = (forced & forbidden) ? 1u : 0u;
+        mh.R = forced;
+        mh.n_kept = 0;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < n_cl; i += nt)
+        if (!(cl[i] & forced) && !(cl[i] & ~forbidden)) mh.unsat = 1;
+    __syncthreads();
+    if (mh.unsat) {
+        if (tid == 0) sm.sol_found = 0;
+        __syncthreads();
+        return;
+    }
+    for (;;) {
+        const uint32_t x = *(volatile uint32_t *)&mh.R;
+        if (tid < 32) cnt[tid] = 0;
+        __syncthreads();
+        for (uint32_t i = tid; i < n_cl; i += nt) {
+            const uint32_t c = cl[i];
+            if (c & x) continue;
+            for (uint32_t t = c & ~forbidden; t; t &= t - 1u) atomicAdd(&cnt[__ffs(t) - 1u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // lane k's candidate; reduce to the best by hits/weight, ties to the lower slot
+            uint32_t h = (lane < n_vars && !((x >> lane) & 1u) && !((forbidden >> lane) & 1u)) ? cnt[lane] : 0u;
+            uint32_t wk = lane < n_vars ? w[lane] : 1u, k = lane;
+            for (uint32_t o = 16; o > 0; o >>= 1) {
+                const uint32_t h2 = __shfl_down_sync(0xFFFFFFFFu, h, o);
+                const uint32_t w2 = __shfl_down_sync(0xFFFFFFFFu, wk, o);
+                const uint32_t k2 = __shfl_down_sync(0xFFFFFFFFu, k, o);
+                const uint64_t a = (uint64_t)h2 * wk, b = (uint64_t)h * w2;
+                if (h2 && (!h || a > b || (a == b && k2 < k))) {
+                    h = h2;
+                    wk = w2;
+                    k = k2;
+                }
+            }
+            if (lane == 0) {
+                if (h) mh.R = x | (1u << k);
+                else mh.n_kept = 1;  // every clause is hit
+            }
+        }
+        __syncthreads();
+        if (mh.n_kept) break;
+    }
+    uint32_t x = mh.R;
+    for (int k = (int)n_vars - 1; k >= 0; --k) {
+        if (!((x >> k) & 1u) || ((forced >> k) & 1u)) continue;
+        const uint32_t y = x & ~(1u << k);
+        bool ok = true;
+        for (uint32_t i = tid; i < n_cl && ok; i += nt) ok = (cl[i] & y) != 0;
+        if (__syncthreads_and(ok)) x = y;
+    }
+    if (tid == 0) {
+        uint32_t wt = 0;
+        for (uint32_t t = x; t; t &= t - 1u) wt += w[__ffs(t) - 1u];
+        sm.sol_found = 1;
+        sm.sol_mask = x;
+        sm.sol_weight = wt;
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Loop steps (Algorithm 1)
 // ---------------------------------------------------------------------------
@@ -840,6 +918,7 @@ __device__ void loop_init(Smem &sm, MhsSmem &mh, const gr_options &opts) {
         sm.n_cl = 0;
         sm.t_start = globaltimer();
         sm.probe = P.mode == GR_MODE_REMOVE ? 1u : 0u;
+        sm.greedy = opts.strategy == GR_STRATEGY_MHS ? 1u : 0u;
         sm.mask = P.existing;
     }
     if (threadIdx.x < 32) {
@@ -877,9 +956,16 @@ __device__ void loop_step(Smem &sm, MhsSmem &mh) {
         sm.access_pairs += sm.pairs;
         uint32_t any = sm.diverge;
         for (uint32_t i = 0; i < P.n_stmts; ++i) any |= sm.rows_intra[i] | sm.rows_inter[i];
+        sm.step = 0;  // a new proposal is needed
         if (!any && !sm.probe) {
-            sm.status = GR_REPAIRED;
-            sm.done = 1;
+            if (sm.greedy) {  // a clean greedy proposal: one exact query decides
+                sm.greedy = 0;
+                sm.step = 1;
+            } else {
+                sm.status = GR_REPAIRED;
+                sm.done = 1;
+                sm.step = 2;
+            }
         } else {
             sm.probe = 0;
             for (uint32_t i = 0; i < P.n_stmts; ++i) {
@@ -890,11 +976,20 @@ __device__ void loop_step(Smem &sm, MhsSmem &mh) {
         }
     }
     __syncthreads();
-    if (sm.done) return;
+    const uint32_t step = sm.step;
+    if (step == 2) return;
     build_clauses(sm);
-    mhs_solve(sm, mh, P.n_slots, P.weights, sm.n_cl, nullptr, 0, sm.forced, sm.forbidden);
+    bool solved = false;
+    if (step == 0 && sm.greedy) {
+        mhs_greedy(sm, mh, P.n_slots, P.weights, sm.n_cl, sm.forced, sm.forbidden);
+        solved = sm.sol_found != 0;  // else fall back to the MaxSAT solve
+    }
+    if (!solved) mhs_solve(sm, mh, P.n_slots, P.weights, sm.n_cl, nullptr, 0, sm.forced, sm.forbidden);
     if (threadIdx.x == 0) {
-        if (!sm.sol_found) {
+        if (step == 1 && (!sm.sol_found || sm.sol_mask == sm.mask)) {
+            sm.status = GR_REPAIRED;  // the greedy proposal is the minimum
+            sm.done = 1;
+        } else if (!sm.sol_found) {
             sm.status = GR_UNREPAIRABLE;
             sm.done = 1;
         } else {
@@ -1186,6 +1281,7 @@ __device__ void state_to_smem(Smem &sm, const LoopState *st) {
         sm.max_iters = st->max_iters;
         sm.access_pairs = st->access_pairs;
         sm.t_start = st->t_start;
+        sm.greedy = st->greedy;
     }
     if (threadIdx.x < 32) {
         sm.acc_intra[threadIdx.x] = st->acc_intra[threadIdx.x];
@@ -1208,6 +1304,7 @@ __device__ void state_from_smem(const Smem &sm, LoopState *st) {
         st->max_iters = sm.max_iters;
         st->access_pairs = sm.access_pairs;
         st->t_start = sm.t_start;
+        st->greedy = sm.greedy;
     }
     if (threadIdx.x < 32) {
         st->acc_intra[threadIdx.x] = sm.acc_intra[threadIdx.x];

@@ -111,6 +111,7 @@ extern "C" gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, c
     gr_options o;
     memset(&o, 0, sizeof(o));
     o.grid_enabled = opts ? opts->grid_enabled : 1;
+    o.strategy = opts ? opts->strategy : 0;
     o.max_iters = (opts && opts->max_iters) ? opts->max_iters : GR_MAX_ITERS;
     // the queue counter and the error word must start at zero
     e = cudaMemsetAsync(scratch, 0, 256, st);

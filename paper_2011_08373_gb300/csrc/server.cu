@@ -260,6 +260,7 @@ gr_status gr_server_create(uint64_t mem_budget_bytes, uint32_t n_slots, uint32_t
     cudaGetDevice(&s->device);
     memset(&s->opts, 0, sizeof(s->opts));
     s->opts.grid_enabled = opts ? opts->grid_enabled : 1;
+    s->opts.strategy = opts ? opts->strategy : 0;
     s->opts.max_iters = (opts && opts->max_iters) ? opts->max_iters : GR_MAX_ITERS;
     s->max_inflight = max_inflight;
     s->slots.resize(n_slots);

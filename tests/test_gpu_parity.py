@@ -165,3 +165,26 @@ def test_device_resident_matches_host_path(gb):
     torch.cuda.synchronize()
     for a, b in zip(host, db.results()):
         _same_result(a, b)
+
+
+def test_mhs_strategy_matches_oracle(gb):
+    """The paper's default mhs strategy (greedy proposals, MaxSAT fallback,
+    one exact query at the end): every field, trajectories included."""
+    progs = [random_program(50000 + seed, s_max=8, b_max=3, t_max=12, m_max=24) for seed in range(150)]
+    progs += synth.generate("batch1024_4x256_s24", 6, blocks=2, threads=64, n_stmts=14, m_words=256)
+    for grid_enabled in (True, False):
+        got = gb.repair_batch(progs, grid_enabled=grid_enabled, strategy=gb.STRATEGY_MHS)
+        for p, g in zip(progs, got):
+            _same_result(g, oracle.repair(p, grid_enabled=grid_enabled, strategy=1))
+    for p in progs[:4]:
+        _same_result(gb.repair_plain(p, strategy=gb.STRATEGY_MHS), oracle.repair(p, strategy=1))
+
+
+def test_mhs_strategy_listings(gb):
+    for case in GOLD["cases"]:
+        p = program_from_spec(case["program"])
+        for exp in case["repairs"]:
+            got = gb.repair(p, mode=exp["mode"], strategy=gb.STRATEGY_MHS)
+            want = oracle.repair(p, mode=exp["mode"], strategy=1)
+            _same_result(got, want, case["name"])
+            assert (got["status"], got["mask"]) == (exp["status"], exp["mask"])
