@@ -253,6 +253,34 @@ def run_ours(args, rank, world, local):
         for p in sub:
             binding.repair_plain(p)
         plain = len(sub) / (time.perf_counter() - t0)
+    strategies = None
+    if rank == 0 and args.strategy_steps > 0:
+        # the paper's mhs strategy against the exact (MaxSAT) strategy on the
+        # same batch: masks checked per repair (the verifier-call analogue) and
+        # the repair kernel's time; both must end at the same masks
+        gb = binding.DeviceBatch(progs, strategy=binding.STRATEGY_MHS)
+        gb.tune()
+        gb.expand()
+        gb.repair_expanded()
+        torch.cuda.synchronize()
+        g_ms = []
+        for _ in range(args.strategy_steps):
+            l2_flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            gb.expand()
+            a.record(stream)
+            gb.repair_expanded()
+            b.record(stream)
+            torch.cuda.synchronize()
+            g_ms.append(a.elapsed_time(b))
+        gres = gb.results_raw()
+        strategies = {
+            "maxsat": {"checks_per_repair": checks / n, "repair_kernel_ms": statistics.mean(repair_ms)},
+            "mhs": {"checks_per_repair": int(gres["iters"].sum()) / n,
+                    "repair_kernel_ms": statistics.mean(g_ms)},
+            "same_final_mask": float(np.mean((gres["mask"] == res["mask"]) & (gres["status"] == res["status"]))),
+        }
+        del gb
     cpu = None
     if rank == 0 and args.cpu_sample > 0:
         cpu = cpu_baseline_leg(args.workload, args.cpu_sample)
@@ -281,7 +309,7 @@ def run_ours(args, rank, world, local):
             "expand_ms": statistics.mean(expand_ms), "repair_kernel_ms": statistics.mean(repair_ms),
             "latency_in_batch_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "status_counts": {"repaired": status[0], "unrepairable": status[1], "iter_cap": status[2]},
-            "checks_per_repair": checks / n, "wall_s": wall,
+            "checks_per_repair": checks / n, "strategies": strategies, "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -359,6 +387,8 @@ def main():
     ap.add_argument("--programs", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--plain-programs", type=int, default=64)
+    ap.add_argument("--strategy-steps", type=int, default=5,
+                    help="timed launches of the mhs strategy on the same batch (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=32)
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--serve", action="store_true", help="Poisson request streams through the server")
