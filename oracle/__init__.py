@@ -31,6 +31,38 @@ _lib = None
 
 MAX_TRAJ = 64
 MAX_CLAUSES = 656
+MAX_STMTS = 25
+
+
+def _check_loops(loops, S):
+    """Loops must be counted ranges lo..hi (1 <= lo <= hi < S, trips >= 1),
+    pairwise nested or disjoint, a nested loop starting strictly after its
+    parent (so that every loop has its own head slot)."""
+    for lo, hi, trips in loops:
+        if not (1 <= lo <= hi < S) or trips < 1:
+            raise ValueError(f"bad loop {(lo, hi, trips)} for {S} statements")
+    for x, (lo1, hi1, _) in enumerate(loops):
+        for lo2, hi2, _ in loops[x + 1:]:
+            disjoint = hi1 < lo2 or hi2 < lo1
+            nested = (lo1 < lo2 and hi2 <= hi1) or (lo2 < lo1 and hi1 <= hi2)
+            if not (disjoint or nested):
+                raise ValueError("loops must be nested (starting strictly inside) or disjoint")
+
+
+def unroll_count(prog_struct) -> int:
+    st = (C.c_uint32 * MAX_STMTS)()
+    it = (C.c_uint32 * MAX_STMTS)()
+    return int(_load().orc_unroll(C.byref(prog_struct), st, it))
+
+
+def unroll(p):
+    """The executed statement instances of p in order: (statement, counter of
+    its innermost loop) pairs."""
+    m = _Marshalled(p)
+    st = (C.c_uint32 * MAX_STMTS)()
+    it = (C.c_uint32 * MAX_STMTS)()
+    n = int(_load().orc_unroll(C.byref(m.s), st, it))
+    return [(st[x], it[x]) for x in range(n)]
 
 
 def build(force: bool = False) -> str:
@@ -56,6 +88,9 @@ class _Prog(C.Structure):
         ("perm", C.c_void_p), ("perm_len", C.c_uint32),
         ("existing_mask", C.c_uint32),
         ("blocks", C.c_uint32), ("threads", C.c_uint32),
+        ("n_loops", C.c_uint32),
+        ("loop_lo", C.c_void_p), ("loop_hi", C.c_void_p), ("loop_trips", C.c_void_p),
+        ("iter_coef", C.c_void_p),
     ]
 
 
@@ -95,6 +130,8 @@ def _configure(path):
     lib.orc_check_pair.argtypes = [C.POINTER(_Prog), C.c_uint32, C.c_uint32, C.c_uint32,
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
     lib.orc_check_pair.restype = None
+    lib.orc_unroll.argtypes = [C.POINTER(_Prog), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+    lib.orc_unroll.restype = C.c_uint32
     assert lib.orc_sizeof_result() == C.sizeof(_Result)
     assert lib.orc_sizeof_prog() == C.sizeof(_Prog)
     assert lib.orc_sizeof_witness() == C.sizeof(_Witness)
@@ -148,28 +185,40 @@ class _Marshalled:
             _u32(p.perm) if len(p.perm) else np.zeros(1, np.uint32),
         ]
         assert len(p.slot_level) == n
+        loops = list(getattr(p, "loops", ()) or ())
+        _check_loops(loops, p.op.shape[0])
+        coef = getattr(p, "iter_coef", None)
+        self.keep += [_u32([l[0] for l in loops] or [0]), _u32([l[1] for l in loops] or [0]),
+                      _u32([l[2] for l in loops] or [0]),
+                      _u32(coef) if coef is not None else np.zeros(p.op.shape[0], np.uint32)]
         k = self.keep
         ptr = lambda arr: arr.ctypes.data
         self.s = _Prog(p.op.shape[0], ptr(k[0]), ptr(k[1]), ptr(k[2]), ptr(k[3]), ptr(k[4]),
                        ptr(k[5]), ptr(k[6]), ptr(k[7]), ptr(k[8]), ptr(k[9]), ptr(k[10]),
                        ptr(k[11]), ptr(k[12]), int(p.m_shared), int(p.m_global), ptr(k[13]),
-                       len(p.perm), int(p.existing_mask), int(p.blocks), int(p.threads))
+                       len(p.perm), int(p.existing_mask), int(p.blocks), int(p.threads),
+                       len(loops), ptr(k[14]), ptr(k[15]), ptr(k[16]), ptr(k[17]))
+        self.n_exec = unroll_count(self.s) if loops else p.op.shape[0]
+        if self.n_exec > MAX_STMTS:
+            raise ValueError(f"{self.n_exec} executed statement instances (at most {MAX_STMTS})")
 
 
 def check(p, mask: int) -> dict:
-    """Witnesses of program ``p`` under barrier mask ``mask``."""
+    """Witnesses of program ``p`` under barrier mask ``mask``; rows index the
+    executed statement instances (the statements themselves without loops)."""
     lib = _load()
     m = _Marshalled(p)
     w = _Witness()
     lib.orc_check(C.byref(m.s), mask, C.byref(w))
-    S = p.op.shape[0]
+    S = m.n_exec
     return {"intra": [w.intra[i] for i in range(S)], "inter": [w.inter[i] for i in range(S)],
             "diverge": w.diverge, "access_pairs": w.access_pairs}
 
 
 def check_pair(p, mask: int, i: int, j: int) -> tuple:
     """(same-block witness, cross-block witness, thread pairs examined) for
-    statements i <= j under ``mask``: the check's definition on one pair."""
+    executed instances i <= j under ``mask``: the check's definition on one
+    pair."""
     lib = _load()
     m = _Marshalled(p)
     a, b, n = C.c_int32(), C.c_int32(), C.c_uint64()

@@ -16,6 +16,11 @@
  *   and guard (k, r): statement s runs for thread tid iff k == 0 or tid%k == r.
  *   slot k (between statements k and k+1): level (0 block / 1 grid),
  *   guard (k, r) with the same meaning, weight w_k.
+ *   counted loops (lo, hi, trips): statements lo..hi run trips times; a
+ *   statement's address adds d*t, t the counter (0..trips-1) of its innermost
+ *   loop.  The barrier of slot k stands just before statement k+1, so it runs
+ *   every time control reaches statement k+1: the loop-head slot lo-1 runs
+ *   before every iteration, the exit slot hi once after the last one.
  *
  * Parity-pinned functions (see tests/test_oracle_pins.py):
  *   orc_check  -- pinned by the paper's listings (Section 1, Appendix A.4),
@@ -49,6 +54,9 @@ typedef struct {
     uint32_t perm_len;
     uint32_t existing_mask;
     uint32_t blocks, threads;
+    uint32_t n_loops;
+    const uint32_t *loop_lo, *loop_hi, *loop_trips; /* per loop */
+    const uint32_t *iter_coef;                      /* per statement; NULL = 0 */
 } orc_prog;
 
 typedef struct {
@@ -74,75 +82,123 @@ static int orc_active(uint32_t k, uint32_t r, uint32_t tid) {
     return k == 0 || tid % k == r;
 }
 
-static uint32_t orc_addr(const orc_prog *p, uint32_t s, uint32_t blk, uint32_t tid) {
+/* Address of statement s for thread tid of block blk in iteration it of the
+ * statement's innermost loop (it = 0 outside loops). */
+static uint32_t orc_addr(const orc_prog *p, uint32_t s, uint32_t blk, uint32_t tid, uint32_t it) {
     uint64_t M = p->space[s] == 0 ? p->m_shared : p->m_global;
+    const uint64_t d = p->iter_coef ? (uint64_t)p->iter_coef[s] * it : 0;
     if (p->kind[s] == 2) {
-        uint64_t idx = ((uint64_t)tid + (uint64_t)p->c[s] * blk + p->b[s]) % M;
+        uint64_t idx = ((uint64_t)tid + (uint64_t)p->c[s] * blk + p->b[s] + d) % M;
         return p->perm[p->perm_off[s] + idx];
     }
-    return (uint32_t)(((uint64_t)p->a[s] * tid + (uint64_t)p->c[s] * blk + p->b[s]) % M);
+    return (uint32_t)(((uint64_t)p->a[s] * tid + (uint64_t)p->c[s] * blk + p->b[s] + d) % M);
 }
 
-/* Is there an enabled slot (any level / grid level) among slots i .. j-1?
- * A block barrier orders the accesses of threads in the same block, a grid
- * barrier those of every pair of threads (Section 2.2, flag reset). */
-static int orc_separated(const orc_prog *p, uint32_t mask, uint32_t i, uint32_t j, int grid_only) {
-    for (uint32_t k = i; k < j; k++)
+/* The statements in execution order (each statement of a loop body once per
+ * iteration): st[x] is the statement of the x-th executed instance, it[x] the
+ * counter of its innermost loop.  Statements lo..hi of the range, which is
+ * the body of loop `in` (-1: the whole program) in its iteration t. */
+static void orc_emit(const orc_prog *p, uint32_t lo, uint32_t hi, int in, uint32_t t, uint32_t *st,
+                     uint32_t *it, uint32_t *n) {
+    uint32_t s = lo;
+    while (s <= hi) {
+        int l = -1;
+        for (uint32_t q = 0; q < p->n_loops; q++)
+            if ((int)q != in && p->loop_lo[q] == s) l = (int)q;
+        if (l < 0) {
+            if (*n < ORC_MAX_STMTS) {
+                st[*n] = s;
+                it[*n] = t;
+            }
+            (*n)++;
+            s++;
+            continue;
+        }
+        for (uint32_t t2 = 0; t2 < p->loop_trips[l]; t2++)
+            orc_emit(p, p->loop_lo[l], p->loop_hi[l], l, t2, st, it, n);
+        s = p->loop_hi[l] + 1;
+    }
+}
+
+/* Number of executed statement instances (at most ORC_MAX_STMTS are stored). */
+uint32_t orc_unroll(const orc_prog *p, uint32_t *st, uint32_t *it) {
+    uint32_t n = 0;
+    orc_emit(p, 0, p->n_stmts - 1, -1, 0, st, it, &n);
+    return n;
+}
+
+/* Is there an enabled barrier (any level / grid level) among those that run
+ * between instances x < y?  Slot k's barrier runs each time control reaches
+ * statement k+1.  A block barrier orders the accesses of threads in the same
+ * block, a grid barrier those of every pair of threads (Section 2.2, flag
+ * reset). */
+static int orc_separated(const orc_prog *p, const uint32_t *st, uint32_t mask, uint32_t x, uint32_t y,
+                         int grid_only) {
+    for (uint32_t z = x + 1; z <= y; z++) {
+        const uint32_t k = st[z] - 1;
         if ((mask >> k) & 1u)
             if (!grid_only || p->slot_level[k] == 1) return 1;
+    }
     return 0;
 }
 
-/* Check P under barrier mask m: every race witness (i, j) and every
- * divergent enabled slot.  Definition by enumeration of all thread pairs.
- *   (i, j), i <= j, same space, at least one write: a witness exists iff there
- *   are distinct threads g1 (running i) and g2 (running j) with the same
- *   address in the same array instance (same block for shared arrays), and no
- *   enabled barrier separating them.  Same-block pairs go to intra[i], cross
- *   block pairs to inter[i].  Values are not modelled: equal-value writes race
+/* Check P under barrier mask m: every race witness (x, y) and every
+ * divergent enabled slot.  Definition by enumeration of all thread pairs over
+ * the executed statement instances x <= y (orc_unroll; without loops
+ * instance x is statement x).
+ *   (x, y), same space, at least one write: a witness exists iff there are
+ *   distinct threads g1 (running x) and g2 (running y) with the same address
+ *   in the same array instance (same block for shared arrays), and no enabled
+ *   barrier runs between x and y.  Same-block pairs go to intra[x], cross
+ *   block pairs to inter[x].  Values are not modelled: equal-value writes race
  *   (Appendix A.4, write-write race).
  *   Slot k diverges iff it is enabled and its guard is true for some thread
  *   of a block and false for another (Section 1, barrier divergence).
- * access_pairs counts the thread pairs examined: for i < j ordered pairs
- * (g1 at i, g2 at j), for i == j unordered pairs, each only while its scope
+ * access_pairs counts the thread pairs examined: for x < y ordered pairs
+ * (g1 at x, g2 at y), for x == y unordered pairs, each only while its scope
  * (same block / cross block) is not separated under m. */
 void orc_check(const orc_prog *p, uint32_t mask, orc_witness *out) {
     memset(out, 0, sizeof(*out));
-    const uint32_t S = p->n_stmts, B = p->blocks, T = p->threads;
+    uint32_t st[ORC_MAX_STMTS], it[ORC_MAX_STMTS];
+    const uint32_t X = orc_unroll(p, st, it);
+    if (X > ORC_MAX_STMTS) return;
+    const uint32_t B = p->blocks, T = p->threads;
     const uint64_t G = (uint64_t)B * T;
-    /* each statement's address and guard, evaluated once per thread */
-    uint32_t *addr = (uint32_t *)malloc(sizeof(uint32_t) * S * G);
-    uint8_t *act = (uint8_t *)malloc(S * (size_t)T);
-    for (uint32_t s = 0; s < S; s++) {
-        for (uint32_t t = 0; t < T; t++) act[(size_t)s * T + t] = (uint8_t)orc_active(p->guard_k[s], p->guard_r[s], t);
+    /* each instance's address and guard, evaluated once per thread */
+    uint32_t *addr = (uint32_t *)malloc(sizeof(uint32_t) * X * G);
+    uint8_t *act = (uint8_t *)malloc(X * (size_t)T);
+    for (uint32_t x = 0; x < X; x++) {
+        const uint32_t s = st[x];
+        for (uint32_t t = 0; t < T; t++) act[(size_t)x * T + t] = (uint8_t)orc_active(p->guard_k[s], p->guard_r[s], t);
         for (uint32_t b = 0; b < B; b++)
-            for (uint32_t t = 0; t < T; t++) addr[s * G + (uint64_t)b * T + t] = orc_addr(p, s, b, t);
+            for (uint32_t t = 0; t < T; t++) addr[x * G + (uint64_t)b * T + t] = orc_addr(p, s, b, t, it[x]);
     }
-    for (uint32_t i = 0; i < S; i++) {
-        for (uint32_t j = i; j < S; j++) {
+    for (uint32_t x = 0; x < X; x++) {
+        for (uint32_t y = x; y < X; y++) {
+            const uint32_t i = st[x], j = st[y];
             if (p->space[i] != p->space[j]) continue;
             if (p->op[i] != 1 && p->op[j] != 1) continue;
             const int shared = p->space[i] == 0;
-            const int open_same = !orc_separated(p, mask, i, j, 0);
-            const int open_cross = !shared && !orc_separated(p, mask, i, j, 1);
+            const int open_same = !orc_separated(p, st, mask, x, y, 0);
+            const int open_cross = !shared && !orc_separated(p, st, mask, x, y, 1);
             if (!open_same && !open_cross) continue;
             for (uint32_t b1 = 0; b1 < B; b1++) {
                 for (uint32_t t1 = 0; t1 < T; t1++) {
-                    if (!act[(size_t)i * T + t1]) continue;
-                    const uint32_t a1 = addr[i * G + (uint64_t)b1 * T + t1];
+                    if (!act[(size_t)x * T + t1]) continue;
+                    const uint32_t a1 = addr[x * G + (uint64_t)b1 * T + t1];
                     for (uint32_t b2 = 0; b2 < B; b2++) {
                         const int same = b1 == b2;
                         if (same && !open_same) continue;
                         if (!same && !open_cross) continue;
                         for (uint32_t t2 = 0; t2 < T; t2++) {
                             if (same && t1 == t2) continue;
-                            /* statement i == j: count each unordered pair once */
-                            if (i == j && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;
-                            if (!act[(size_t)j * T + t2]) continue;
+                            /* one instance: count each unordered pair once */
+                            if (x == y && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;
+                            if (!act[(size_t)y * T + t2]) continue;
                             out->access_pairs++;
-                            if (addr[j * G + (uint64_t)b2 * T + t2] != a1) continue;
-                            if (same) out->intra[i] |= 1u << j;
-                            else out->inter[i] |= 1u << j;
+                            if (addr[y * G + (uint64_t)b2 * T + t2] != a1) continue;
+                            if (same) out->intra[x] |= 1u << y;
+                            else out->inter[x] |= 1u << y;
                         }
                     }
                 }
@@ -151,7 +207,7 @@ void orc_check(const orc_prog *p, uint32_t mask, orc_witness *out) {
     }
     free(addr);
     free(act);
-    for (uint32_t k = 0; k + 1 < S; k++) {
+    for (uint32_t k = 0; k + 1 < p->n_stmts; k++) {
         if (!((mask >> k) & 1u) || p->slot_guard_k[k] == 0) continue;
         int seen_true = 0, seen_false = 0;
         for (uint32_t t = 0; t < T; t++) {
@@ -162,30 +218,33 @@ void orc_check(const orc_prog *p, uint32_t mask, orc_witness *out) {
     }
 }
 
-/* The same definition for one statement pair (i <= j): whether a same-block
- * and a cross-block witness (i, j) exist under mask m, and the thread pairs
+/* The same definition for one instance pair (x <= y): whether a same-block
+ * and a cross-block witness (x, y) exist under mask m, and the thread pairs
  * examined.  Used to sample full-size launches whose whole check is too slow
  * to enumerate. */
-void orc_check_pair(const orc_prog *p, uint32_t mask, uint32_t i, uint32_t j, int32_t *intra, int32_t *inter,
+void orc_check_pair(const orc_prog *p, uint32_t mask, uint32_t x, uint32_t y, int32_t *intra, int32_t *inter,
                     uint64_t *pairs) {
     *intra = 0;
     *inter = 0;
     *pairs = 0;
+    uint32_t st[ORC_MAX_STMTS], it[ORC_MAX_STMTS];
+    const uint32_t X = orc_unroll(p, st, it);
     const uint32_t B = p->blocks, T = p->threads;
-    if (i > j || j >= p->n_stmts) return;
+    if (X > ORC_MAX_STMTS || x > y || y >= X) return;
+    const uint32_t i = st[x], j = st[y];
     if (p->space[i] != p->space[j]) return;
     if (p->op[i] != 1 && p->op[j] != 1) return;
     const int shared = p->space[i] == 0;
-    const int open_same = !orc_separated(p, mask, i, j, 0);
-    const int open_cross = !shared && !orc_separated(p, mask, i, j, 1);
+    const int open_same = !orc_separated(p, st, mask, x, y, 0);
+    const int open_cross = !shared && !orc_separated(p, st, mask, x, y, 1);
     if (!open_same && !open_cross) return;
     const uint64_t G = (uint64_t)B * T;
     uint32_t *ai = (uint32_t *)malloc(sizeof(uint32_t) * G);
     uint32_t *aj = (uint32_t *)malloc(sizeof(uint32_t) * G);
     for (uint32_t b = 0; b < B; b++)
         for (uint32_t t = 0; t < T; t++) {
-            ai[(uint64_t)b * T + t] = orc_addr(p, i, b, t);
-            aj[(uint64_t)b * T + t] = orc_addr(p, j, b, t);
+            ai[(uint64_t)b * T + t] = orc_addr(p, i, b, t, it[x]);
+            aj[(uint64_t)b * T + t] = orc_addr(p, j, b, t, it[y]);
         }
     for (uint32_t b1 = 0; b1 < B; b1++) {
         for (uint32_t t1 = 0; t1 < T; t1++) {
@@ -197,7 +256,7 @@ void orc_check_pair(const orc_prog *p, uint32_t mask, uint32_t i, uint32_t j, in
                 if (!same && !open_cross) continue;
                 for (uint32_t t2 = 0; t2 < T; t2++) {
                     if (same && t1 == t2) continue;
-                    if (i == j && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;
+                    if (x == y && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;
                     if (!orc_active(p->guard_k[j], p->guard_r[j], t2)) continue;
                     (*pairs)++;
                     if (aj[(uint64_t)b2 * T + t2] != a1) continue;
@@ -211,18 +270,19 @@ void orc_check_pair(const orc_prog *p, uint32_t mask, uint32_t i, uint32_t j, in
     free(aj);
 }
 
-/* GenerateClause (Section 2.4): a race witness (i, j) is avoided exactly when
- * some barrier able to order it is on: any slot in i .. j-1 for a same-block
- * witness, a grid slot in i .. j-1 for a cross-block one.  (i, i) gives the
+/* GenerateClause (Section 2.4): a race witness (x, y) is avoided exactly when
+ * some barrier able to order it is on: any slot whose barrier runs between
+ * instances x and y for a same-block witness, such a grid slot for a
+ * cross-block one.  Without loops that is slots x .. y-1; (x, x) gives the
  * empty clause.  Result: the set of clauses as sorted unique masks. */
 static int orc_cmp_u32(const void *x, const void *y) {
     uint32_t a = *(const uint32_t *)x, b = *(const uint32_t *)y;
     return a < b ? -1 : a > b;
 }
 
-static uint32_t orc_slot_range(uint32_t i, uint32_t j) {
+static uint32_t orc_slots_between(const uint32_t *st, uint32_t x, uint32_t y) {
     uint32_t m = 0;
-    for (uint32_t k = i; k < j; k++) m |= 1u << k;
+    for (uint32_t z = x + 1; z <= y; z++) m |= 1u << (st[z] - 1u);
     return m;
 }
 
@@ -230,10 +290,13 @@ uint32_t orc_clauses(const orc_prog *p, const orc_witness *w, uint32_t *clauses,
     uint32_t grid = 0, n = n_in;
     for (uint32_t k = 0; k + 1 < p->n_stmts; k++)
         if (p->slot_level[k] == 1) grid |= 1u << k;
-    for (uint32_t i = 0; i < p->n_stmts; i++) {
-        for (uint32_t j = i; j < p->n_stmts; j++) {
-            if ((w->intra[i] >> j) & 1u) clauses[n++] = orc_slot_range(i, j);
-            if ((w->inter[i] >> j) & 1u) clauses[n++] = orc_slot_range(i, j) & grid;
+    uint32_t st[ORC_MAX_STMTS], it[ORC_MAX_STMTS];
+    const uint32_t X = orc_unroll(p, st, it);
+    if (X > ORC_MAX_STMTS) return n_in;
+    for (uint32_t x = 0; x < X; x++) {
+        for (uint32_t y = x; y < X; y++) {
+            if ((w->intra[x] >> y) & 1u) clauses[n++] = orc_slots_between(st, x, y);
+            if ((w->inter[x] >> y) & 1u) clauses[n++] = orc_slots_between(st, x, y) & grid;
         }
     }
     qsort(clauses, n, sizeof(uint32_t), orc_cmp_u32);

@@ -122,6 +122,14 @@ class Program:
     blocks: int
     threads: int
     mode: int = MODE_REPAIR
+    # counted loops (lo, hi, trips): statements lo..hi run `trips` times; the
+    # slot before statement lo is the loop head (it runs before every
+    # iteration).  Ranges are nested or disjoint, lo >= 1, nested loops start
+    # strictly inside their parent.
+    loops: tuple = ()
+    # per-statement coefficient d of the innermost enclosing loop's counter
+    # (0..trips-1) in the address map; None = all zero
+    iter_coef: Optional[np.ndarray] = None
 
     @property
     def n_stmts(self) -> int:
@@ -142,12 +150,14 @@ class Program:
 def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int = 0,
                  m_global: int = 0, slot_level=None, slot_guard=None, slot_weight=None,
                  perms: Optional[List[np.ndarray]] = None, existing_mask: int = 0,
-                 mode: int = MODE_REPAIR) -> Program:
+                 mode: int = MODE_REPAIR, loops=()) -> Program:
     """Build a Program from a list of statement dicts.
 
     Each dict: op ('R'/'W' or 0/1), space ('shared'/'global' or 0/1), kind
     ('affine'/'strided'/'perm' or 0/1/2), a, b, c, perm (index into ``perms``),
-    guard (k, r).  Missing fields default to an unguarded shared affine read.
+    guard (k, r), d (coefficient of the innermost loop counter).  Missing
+    fields default to an unguarded shared affine read.  ``loops``: (lo, hi,
+    trips) triples.
     """
     S = len(stmts)
     enc_op = {"R": OP_R, "W": OP_W, OP_R: OP_R, OP_W: OP_W}
@@ -160,7 +170,7 @@ def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int 
         offs.append(o)
         o += len(pt)
     perm = np.concatenate(perms).astype(np.uint32) if perms else np.zeros(0, np.uint32)
-    cols = {n: [] for n in ("op", "space", "kind", "a", "b", "c", "perm_off", "gk", "gr")}
+    cols = {n: [] for n in ("op", "space", "kind", "a", "b", "c", "perm_off", "gk", "gr", "d")}
     for st in stmts:
         cols["op"].append(enc_op[st.get("op", "R")])
         cols["space"].append(enc_sp[st.get("space", "shared")])
@@ -172,6 +182,7 @@ def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int 
         gk, gr = st.get("guard", (0, 0))
         cols["gk"].append(gk)
         cols["gr"].append(gr)
+        cols["d"].append(int(st.get("d", 0)))
     n = S - 1
     if slot_level is None:
         slot_level = [LEVEL_BLOCK] * n
@@ -190,7 +201,9 @@ def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int 
         slot_guard_r=np.array([g[1] for g in slot_guard], np.uint16).reshape(n),
         slot_weight=np.array(slot_weight, np.uint32).reshape(n),
         m_shared=int(m_shared), m_global=int(m_global), perm=perm,
-        existing_mask=int(existing_mask), blocks=int(blocks), threads=int(threads), mode=int(mode))
+        existing_mask=int(existing_mask), blocks=int(blocks), threads=int(threads), mode=int(mode),
+        loops=tuple((int(lo), int(hi), int(tr)) for lo, hi, tr in loops),
+        iter_coef=np.array(cols["d"], np.uint32))
 
 
 # ---------------------------------------------------------------------------

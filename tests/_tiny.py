@@ -43,3 +43,45 @@ def random_program(seed, *, s_max=5, b_max=3, t_max=8, m_max=16, spaces=(0, 1),
     return make_program(stmts, blocks=B, threads=T, m_shared=m_sh, m_global=m_gl,
                         slot_level=levels, slot_guard=sguard, slot_weight=weights,
                         perms=perms, existing_mask=existing, mode=mode)
+
+
+def random_loops(rng, S, max_exec=25, trips_max=3):
+    """Up to two counted loops over statements 1..S-1 (nested or disjoint, a
+    nested loop starting strictly inside its parent), with at most
+    ``max_exec`` executed statement instances."""
+    if S < 2:
+        return []
+    for _ in range(20):
+        loops = []
+        lo = rng.randint(1, S - 1)
+        hi = rng.randint(lo, S - 1)
+        t1 = rng.randint(1, trips_max)
+        loops.append((lo, hi, t1))
+        count = S + (t1 - 1) * (hi - lo + 1)
+        if rng.bernoulli(0.5):
+            if hi > lo and rng.bernoulli(0.5):  # nested
+                lo2 = rng.randint(lo + 1, hi)
+                hi2 = rng.randint(lo2, hi)
+                t2 = rng.randint(1, trips_max)
+                loops.append((lo2, hi2, t2))
+                count += t1 * (t2 - 1) * (hi2 - lo2 + 1)
+            elif hi + 1 <= S - 1:  # disjoint, after the first
+                lo2 = rng.randint(hi + 1, S - 1)
+                hi2 = rng.randint(lo2, S - 1)
+                t2 = rng.randint(1, trips_max)
+                loops.append((lo2, hi2, t2))
+                count += (t2 - 1) * (hi2 - lo2 + 1)
+        if count <= max_exec:
+            return loops
+    return []
+
+
+def random_loop_program(seed, *, s_max=5, b_max=3, t_max=6, m_max=12, d_max=3, trips_max=3,
+                        max_exec=25, **kw):
+    """random_program plus counted loops and per-statement loop-counter
+    coefficients."""
+    p = random_program(seed, s_max=s_max, b_max=b_max, t_max=t_max, m_max=m_max, **kw)
+    rng = SplitMix64(program_seed(0x100F5, seed))
+    p.loops = tuple(random_loops(rng, p.n_stmts, max_exec, trips_max))
+    p.iter_coef = np.array([rng.randint(0, d_max) for _ in range(p.n_stmts)], np.uint32)
+    return p

@@ -36,4 +36,5 @@ def program_from_spec(spec):
         m_shared=spec.get("m_shared", 0), m_global=spec.get("m_global", 0),
         slot_level=spec["slot_level"], slot_guard=[tuple(g) for g in spec["slot_guard"]],
         slot_weight=spec["slot_weight"], existing_mask=spec["existing_mask"],
-        perms=[np.array(t, np.uint32) for t in spec.get("perms", [])])
+        perms=[np.array(t, np.uint32) for t in spec.get("perms", [])],
+        loops=[tuple(l) for l in spec.get("loops", [])])

@@ -11,15 +11,14 @@ import oracle
 import test_oracle_pins as pins
 
 MUTANTS = [
-    ("separation_off_by_one", "for (uint32_t k = i; k < j; k++)\n        if ((mask >> k) & 1u)",
-     "for (uint32_t k = i; k <= j; k++)\n        if ((mask >> k) & 1u)"),
+    ("separation_off_by_one", "for (uint32_t z = x + 1; z <= y; z++) {\n        const uint32_t k",
+     "for (uint32_t z = x + 1; z < y; z++) {\n        const uint32_t k"),
     ("block_barrier_orders_blocks", "if (!grid_only || p->slot_level[k] == 1) return 1;", "return 1;"),
     ("shared_arrays_cross_blocks", "const int open_cross = !shared && ", "const int open_cross = "),
     ("same_thread_races", "if (same && t1 == t2) continue;", ""),
-    ("clause_range_inclusive", "for (uint32_t k = i; k < j; k++) m |= 1u << k;",
-     "for (uint32_t k = i; k <= j; k++) m |= 1u << k;"),
-    ("inter_clause_not_grid_only", "clauses[n++] = orc_slot_range(i, j) & grid;",
-     "clauses[n++] = orc_slot_range(i, j);"),
+    ("clause_range_shifted", "m |= 1u << (st[z] - 1u);", "m |= 1u << (st[z] % 24u);"),
+    ("inter_clause_not_grid_only", "clauses[n++] = orc_slots_between(st, x, y) & grid;",
+     "clauses[n++] = orc_slots_between(st, x, y);"),
     ("tie_break_reversed", "(wt == best_w && x < best_x)", "(wt == best_w && x > best_x)"),
     ("forbidden_ignored", "if (x & forbidden) continue;", ""),
     ("negative_clause_wrong", "if ((x & neg[c]) == neg[c]) ok = 0;", "if ((x & neg[c]) != 0) ok = 0;"),
@@ -29,10 +28,10 @@ MUTANTS = [
     ("existing_not_forced", "const uint32_t forced = mode == 0 ? p->existing_mask : 0;",
      "const uint32_t forced = 0;"),
     ("divergence_not_forbidden", "forbidden |= w.diverge;", ""),
-    ("perm_offset_dropped", "((uint64_t)tid + (uint64_t)p->c[s] * blk + p->b[s]) % M;",
-     "((uint64_t)tid + (uint64_t)p->c[s] * blk) % M;"),
-    ("block_term_dropped", "(((uint64_t)p->a[s] * tid + (uint64_t)p->c[s] * blk + p->b[s]) % M)",
-     "(((uint64_t)p->a[s] * tid + p->b[s]) % M)"),
+    ("perm_offset_dropped", "((uint64_t)tid + (uint64_t)p->c[s] * blk + p->b[s] + d) % M;",
+     "((uint64_t)tid + (uint64_t)p->c[s] * blk + d) % M;"),
+    ("block_term_dropped", "(((uint64_t)p->a[s] * tid + (uint64_t)p->c[s] * blk + p->b[s] + d) % M)",
+     "(((uint64_t)p->a[s] * tid + p->b[s] + d) % M)"),
     ("read_read_pairs", "if (p->op[i] != 1 && p->op[j] != 1) continue;", ""),
     ("guard_negated", "return k == 0 || tid % k == r;", "return k == 0 || tid % k != r;"),
     ("weight_of_all_slots", "if ((x >> k) & 1u) wt += w[k];", "wt += w[k];"),
@@ -40,7 +39,16 @@ MUTANTS = [
      "(uint64_t)hits * w[best] >= (uint64_t)best_hits * w[k]"),
     ("greedy_not_minimal", "        if (ok) x = y;", "        (void)ok;"),
     ("pairs_double_counted",
-     "if (i == j && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;", ""),
+     "if (x == y && (uint64_t)b2 * T + t2 < (uint64_t)b1 * T + t1) continue;", ""),
+    # counted loops
+    ("loop_counter_term_dropped", "const uint64_t d = p->iter_coef ? (uint64_t)p->iter_coef[s] * it : 0;",
+     "const uint64_t d = 0;"),
+    ("instance_index_taken_for_statement", "const uint32_t k = st[z] - 1;", "const uint32_t k = z - 1;"),
+    ("loop_trips_off_by_one", "for (uint32_t t2 = 0; t2 < p->loop_trips[l]; t2++)",
+     "for (uint32_t t2 = 0; t2 + 1 < p->loop_trips[l]; t2++)"),
+    ("inner_statements_use_outer_counter", "orc_emit(p, p->loop_lo[l], p->loop_hi[l], l, t2, st, it, n);",
+     "orc_emit(p, p->loop_lo[l], p->loop_hi[l], l, t, st, it, n);"),
+    ("head_slot_taken_after_statement", "m |= 1u << (st[z] - 1u);", "m |= 1u << (st[z - 1] % 24u);"),
 ]
 
 
@@ -53,6 +61,8 @@ def _all_pins():
     yield pins.test_greedy_paper_example
     for case in pins.GOLD["greedy_cases"]:
         yield lambda c=case: pins.test_greedy_worked_cases(c)
+    for case in pins.GOLD["loop_cases"]:
+        yield lambda c=case: pins.test_loop_cases(c)
     for s in range(16):
         yield lambda s=s: pins.test_check_matches_flag_reset_detector(s)
         yield lambda s=s: pins.test_check_matches_affine_closed_form(s)
@@ -63,6 +73,9 @@ def _all_pins():
         yield lambda s=s: pins.test_clause_is_exact_filter(s)
         yield lambda s=s: pins.test_repair_path_independence(s)
         yield lambda s=s: pins.test_greedy_minimal_and_within_johnson_bound(s)
+        yield lambda s=s: pins.test_loop_check_matches_interpreter(s)
+        yield lambda s=s: pins.test_loop_repair_path_independence(s)
+        yield lambda s=s: pins.test_loop_clause_is_exact_filter(s)
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])

@@ -502,3 +502,171 @@ def test_mhs_strategy_reaches_the_same_repair(seed):
 def test_greedy_worked_cases(case):
     got = oracle.greedy(case["n_vars"], case["weights"], case["pos"], case["forced"], case["forbidden"])
     assert got == case["expect"], case["cite"]
+
+
+# --------------------------------------------------------------------------
+# Counted loops: hand-derived cases, a control-flow interpreter with flag
+# resets (written from Section 2.2's barrier semantics, independent of the
+# oracle's unrolled ranges), and the invariants on loop programs
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLD["loop_cases"], ids=[c["name"] for c in GOLD["loop_cases"]])
+def test_loop_cases(case):
+    p = program_from_spec(case["program"])
+    assert [list(x) for x in oracle.unroll(p)] == case["unrolled"]
+    for chk in case["checks"]:
+        got = oracle.check(p, chk["mask"])
+        for key in ("intra", "inter", "diverge", "access_pairs"):
+            if key in chk:
+                assert got[key] == chk[key], (key, chk["mask"], case["cite"])
+    for exp in case["repairs"]:
+        got = oracle.repair(p, mode=exp["mode"])
+        for key in ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses",
+                    "forbidden"):
+            assert got[key] == exp[key], (key, case["cite"])
+
+
+def _interpret(p):
+    """Run the program's control flow once: a program counter over the
+    statements that jumps back to a loop's first statement while iterations
+    remain.  The barrier of slot k is passed each time control arrives at
+    statement k+1.  Returns events ('bar', k) and ('st', s, counter)."""
+    S = p.n_stmts
+    loops = list(p.loops)
+    count = [0] * len(loops)
+    events, pc = [], 0
+    while pc < S:
+        if pc > 0:
+            events.append(("bar", pc - 1))
+        inner = [q for q, (lo, hi, _) in enumerate(loops) if lo <= pc <= hi]
+        q_in = max(inner, key=lambda q: loops[q][0]) if inner else None
+        events.append(("st", pc, count[q_in] if q_in is not None else 0))
+        nxt = pc + 1
+        for q in sorted((q for q, l in enumerate(loops) if l[1] == pc), key=lambda q: -loops[q][0]):
+            if count[q] + 1 < loops[q][2]:
+                count[q] += 1
+                nxt = loops[q][0]
+                break
+            count[q] = 0
+        pc = nxt
+    return events
+
+
+def _addr_it(p, s, blk, tid, it):
+    M = p.m_shared if p.space[s] == SPACE_SHARED else p.m_global
+    d = int(p.iter_coef[s]) * it
+    if p.kind[s] == MAP_PERM:
+        return int(p.perm[int(p.perm_off[s]) + (tid + int(p.c[s]) * blk + int(p.b[s]) + d) % M])
+    return (int(p.a[s]) * tid + int(p.c[s]) * blk + int(p.b[s]) + d) % M
+
+
+def loop_flag_reset_detector(p, mask):
+    events = _interpret(p)
+    X = sum(1 for e in events if e[0] == "st")
+    B, T = p.blocks, p.threads
+    intra, inter = [0] * X, [0] * X
+    threads = [(b, t) for b in range(B) for t in range(T)]
+    for x, y in itertools.combinations(range(len(threads)), 2):
+        pair = (threads[x], threads[y])
+        same = pair[0][0] == pair[1][0]
+        logs = ([], [])
+        n = -1
+        for e in events:
+            if e[0] == "bar":
+                k = e[1]
+                if (mask >> k) & 1 and (same or p.slot_level[k] == LEVEL_GRID):
+                    logs = ([], [])
+                continue
+            _, s, it = e
+            n += 1
+            fresh = []
+            for who, (b, t) in enumerate(pair):
+                if _runs(int(p.guard_k[s]), int(p.guard_r[s]), t):
+                    inst = ("shared", b) if p.space[s] == SPACE_SHARED else ("global",)
+                    ev = (inst, _addr_it(p, s, b, t, it), p.op[s] == 1, n)
+                    logs[who].append(ev)
+                    fresh.append((who, ev))
+            for who, ev in fresh:
+                for f in logs[1 - who]:
+                    if f[0] == ev[0] and f[1] == ev[1] and (ev[2] or f[2]):
+                        i, j = min(ev[3], f[3]), max(ev[3], f[3])
+                        if same:
+                            intra[i] |= 1 << j
+                        else:
+                            inter[i] |= 1 << j
+    return intra, inter
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_loop_check_matches_interpreter(seed):
+    from _tiny import random_loop_program
+
+    p = random_loop_program(seed, s_min=3, s_max=5, b_max=2, t_max=5, m_max=10)
+    n = p.n_slots
+    masks = sorted({0, (1 << n) - 1} | {(seed * 2654435761 + k * 40503) % (1 << n) for k in range(3)}) \
+        if n > 0 else [0]
+    for m in masks:
+        got = oracle.check(p, m)
+        intra, inter = loop_flag_reset_detector(p, m)
+        assert got["intra"] == intra, (p.loops, m)
+        assert got["inter"] == inter, (p.loops, m)
+
+
+def test_loop_interpreter_order_is_the_unrolled_order():
+    from _tiny import random_loop_program
+
+    for seed in range(80):
+        p = random_loop_program(seed, s_max=6)
+        ev = [(e[1], e[2]) for e in _interpret(p) if e[0] == "st"]
+        assert ev == oracle.unroll(p), p.loops
+
+
+def test_one_trip_loops_change_nothing():
+    """A loop that runs once is the straight-line program."""
+    from _tiny import random_loops
+
+    for seed in range(40):
+        p = random_program(11000 + seed, s_max=6, b_max=2, t_max=6, m_max=10)
+        rng = synth.SplitMix64(seed)
+        q = random_program(11000 + seed, s_max=6, b_max=2, t_max=6, m_max=10)
+        q.loops = tuple((lo, hi, 1) for lo, hi, _ in random_loops(rng, q.n_stmts))
+        q.iter_coef = np.arange(q.n_stmts, dtype=np.uint32)
+        for m in (0, (1 << p.n_slots) - 1):
+            assert oracle.check(p, m) == oracle.check(q, m)
+        assert oracle.repair(p) == oracle.repair(q)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_loop_repair_path_independence(seed):
+    from _tiny import random_loop_program
+
+    p = random_loop_program(12000 + seed, s_min=3, s_max=5, b_max=2, t_max=5, m_max=10)
+    for mode in (MODE_REPAIR, MODE_REMOVE):
+        got = oracle.repair(p, mode=mode)
+        ref = _lowest_safe_mask(p, mode, True)
+        assert got["iters"] <= p.n_slots + 3
+        if ref is None:
+            assert got["status"] == 1 and got["mask"] == 0
+        else:
+            assert got["status"] == 0 and (got["weight"], got["mask"]) == ref
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_loop_clause_is_exact_filter(seed):
+    from _tiny import random_loop_program
+
+    p = random_loop_program(13000 + seed, s_min=3, s_max=5, b_max=2, t_max=5, m_max=10)
+    n = p.n_slots
+    w0 = oracle.check(p, 0)
+    X = len(w0["intra"])
+    checks = {m: oracle.check(p, m) for m in range(1 << n)}
+    for i in range(X):
+        for j in range(X):
+            for scope in ("intra", "inter"):
+                if not (w0[scope][i] >> j) & 1:
+                    continue
+                single = {"intra": [0] * X, "inter": [0] * X, "diverge": 0}
+                single[scope][i] = 1 << j
+                (cl,) = oracle.clauses(p, single)
+                for m in checks:
+                    assert bool((checks[m][scope][i] >> j) & 1) == ((m & cl) == 0)
