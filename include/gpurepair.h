@@ -54,6 +54,7 @@ extern "C" {
 #define GR_MAX_WEIGHT (1u << 24)
 #define GR_MAX_CLAUSES 656
 #define GR_MAX_ITERS 64
+#define GR_MAX_LOOPS 4
 
 typedef int32_t gr_status;
 enum {
@@ -93,6 +94,19 @@ typedef struct {
     uint16_t guard_r;
 } gr_stmt;
 
+/* A counted loop (Section 2.2 places candidate barriers at loop heads;
+ * Section 2.4 weighs a barrier by the depth of its loop, lw^ld).  Statements
+ * lo..hi run `trips` times.  The barrier of slot k stands just before
+ * statement k+1 and runs every time control reaches statement k+1, so slot
+ * lo-1 is the loop head: it runs before every iteration; slot hi runs once
+ * after the last.  Requirements: 1 <= lo <= hi < n_stmts, trips >= 1; two
+ * loops are disjoint or nested with the inner one starting after the outer
+ * one's first statement; the statement instances executed in all (a loop
+ * body once per iteration, recursively) number at most GR_MAX_STMTS. */
+typedef struct {
+    uint32_t lo, hi, trips;
+} gr_loop;
+
 typedef struct {
     uint32_t n_stmts;             /* 1..GR_MAX_STMTS */
     const gr_stmt *stmts;         /* n_stmts entries */
@@ -104,6 +118,11 @@ typedef struct {
     const uint32_t *perm;         /* concatenated permutation tables (may be NULL if unused) */
     uint32_t perm_len;
     uint32_t existing_mask;       /* barriers the programmer wrote (E) */
+    uint32_t n_loops;             /* 0..GR_MAX_LOOPS counted loops */
+    const gr_loop *loops;         /* n_loops entries (may be NULL if n_loops == 0) */
+    const uint32_t *iter_coef;    /* n_stmts entries or NULL (= 0): statement s's address
+                                     adds iter_coef[s] * t, t in 0..trips-1 the counter of
+                                     the innermost loop holding s (0 outside loops) */
 } gr_program;
 
 typedef struct {
@@ -111,16 +130,19 @@ typedef struct {
     uint32_t threads;  /* 1..GR_MAX_THREADS */
 } gr_launch;
 
+/* Witness rows index the executed statement instances in execution order
+ * (the statements themselves when the program has no loop). */
 typedef struct {
     uint32_t race_intra[32]; /* row i, bit j (j >= i): same-block race witness (i, j) */
     uint32_t race_inter[32]; /* row i, bit j (j >= i): cross-block race witness (i, j) */
     uint32_t diverge;        /* bit k: enabled slot k is divergent */
-    uint32_t n_stmts;
+    uint32_t n_stmts;        /* executed statement instances (rows in use) */
     uint64_t access_pairs;   /* thread pairs a pairwise checker would examine under the
-                                mask: statement pairs (i <= j) of one space with a write;
+                                mask: instance pairs (i <= j) of one space with a write;
                                 ordered pairs for i < j, unordered for i == j; same-block
-                                pairs unless an enabled slot lies in [i, j-1], cross-block
-                                pairs (global only) unless an enabled grid slot does */
+                                pairs unless an enabled barrier runs between i and j (slots
+                                i..j-1 without loops), cross-block pairs (global only)
+                                unless an enabled grid barrier does */
 } gr_witnesses;
 
 /* Proposal strategies of Algorithm 1's Solve step (Section 2.4). */

@@ -35,12 +35,17 @@ class gr_stmt(C.Structure):
                 ("guard_k", C.c_uint16), ("guard_r", C.c_uint16)]
 
 
+class gr_loop(C.Structure):
+    _fields_ = [("lo", C.c_uint32), ("hi", C.c_uint32), ("trips", C.c_uint32)]
+
+
 class gr_program(C.Structure):
     _fields_ = [("n_stmts", C.c_uint32), ("stmts", C.POINTER(gr_stmt)),
                 ("slot_level", C.POINTER(C.c_uint8)), ("slot_guard", C.POINTER(C.c_uint16)),
                 ("slot_weight", C.POINTER(C.c_uint32)), ("m_shared", C.c_uint32),
                 ("m_global", C.c_uint32), ("perm", C.POINTER(C.c_uint32)), ("perm_len", C.c_uint32),
-                ("existing_mask", C.c_uint32)]
+                ("existing_mask", C.c_uint32), ("n_loops", C.c_uint32),
+                ("loops", C.POINTER(gr_loop)), ("iter_coef", C.POINTER(C.c_uint32))]
 
 
 class gr_launch(C.Structure):
@@ -178,6 +183,15 @@ class CProgram:
             self.s.perm = self.perm.ctypes.data_as(C.POINTER(C.c_uint32))
             self.s.perm_len = len(self.perm)
         self.s.existing_mask = int(p.existing_mask)
+        loops = list(getattr(p, "loops", ()) or ())
+        if loops:
+            self.loops = (gr_loop * len(loops))(*[gr_loop(int(a), int(b), int(c)) for a, b, c in loops])
+            self.s.n_loops = len(loops)
+            self.s.loops = C.cast(self.loops, C.POINTER(gr_loop))
+        coef = getattr(p, "iter_coef", None)
+        if coef is not None:
+            self.coef = np.ascontiguousarray(coef, dtype=np.uint32)
+            self.s.iter_coef = self.coef.ctypes.data_as(C.POINTER(C.c_uint32))
         self.launch = gr_launch(int(p.blocks), int(p.threads))
         self.mode = int(p.mode)
 
@@ -202,7 +216,9 @@ class ProgramBatch:
     PROG_DTYPE = np.dtype([("n_stmts", np.uint32), ("stmts", np.uint64), ("slot_level", np.uint64),
                            ("slot_guard", np.uint64), ("slot_weight", np.uint64),
                            ("m_shared", np.uint32), ("m_global", np.uint32), ("perm", np.uint64),
-                           ("perm_len", np.uint32), ("existing_mask", np.uint32)], align=True)
+                           ("perm_len", np.uint32), ("existing_mask", np.uint32),
+                           ("n_loops", np.uint32), ("loops", np.uint64), ("iter_coef", np.uint64)],
+                          align=True)
 
     def __init__(self, progs: Sequence):
         assert self.PROG_DTYPE.itemsize == C.sizeof(gr_program)
@@ -239,6 +255,20 @@ class ProgramBatch:
         pa["perm"] = np.where(plen > 0, self.perm.ctypes.data + 4 * p_off[:-1], 0)
         pa["perm_len"] = plen
         pa["existing_mask"] = [p.existing_mask for p in progs]
+        # counted loops (lo, hi, trips) and loop-counter coefficients
+        nloop = np.array([len(getattr(p, "loops", ()) or ()) for p in progs], np.int64)
+        if nloop.any():
+            l_off = np.concatenate([[0], np.cumsum(nloop)])
+            self.loop_arr = np.ascontiguousarray(
+                np.array([l for p in progs for l in (getattr(p, "loops", ()) or ())], np.uint32).reshape(-1, 3))
+            pa["n_loops"] = nloop
+            pa["loops"] = np.where(nloop > 0, self.loop_arr.ctypes.data + 12 * l_off[:-1], 0)
+        has_coef = np.array([getattr(p, "iter_coef", None) is not None for p in progs])
+        if has_coef.any():
+            self.coef = np.ascontiguousarray(np.concatenate(
+                [p.iter_coef if c else np.zeros(len(p.op), np.uint32) for p, c in zip(progs, has_coef)]
+            ).astype(np.uint32))
+            pa["iter_coef"] = np.where(has_coef, self.coef.ctypes.data + 4 * s_off[:-1], 0)
         self.progs = pa
         la = np.zeros((n, 2), np.uint32)
         la[:, 0] = [p.blocks for p in progs]
@@ -296,7 +326,7 @@ def check(p, mask: int) -> dict:
     w = gr_witnesses()
     _check(lib().gr_check(C.byref(c.s), c.launch, mask, C.byref(w)))
     arr = np.frombuffer(bytes(w), dtype=WITNESS_DTYPE)[0]
-    return witness_dict(arr, p.n_stmts)
+    return witness_dict(arr, int(arr["n_stmts"]))
 
 
 def repair(p, mode: Optional[int] = None, grid_enabled: bool = True, max_iters: int = 64,
@@ -353,7 +383,7 @@ def check_batch(progs: Sequence, masks: Sequence[int], stream: int = 0) -> List[
     m = (C.c_uint32 * b.n)(*[int(x) for x in masks])
     out = np.zeros(b.n, dtype=WITNESS_DTYPE)
     _check(lib().gr_check_batch(arr, la, m, b.n, out.ctypes.data, C.c_void_p(stream)))
-    return [witness_dict(out[i], progs[i].n_stmts) for i in range(len(progs))]
+    return [witness_dict(out[i], int(out[i]["n_stmts"])) for i in range(len(progs))]
 
 
 # ---------------------------------------------------------------------------
@@ -461,7 +491,7 @@ class DeviceBatch:
     def witnesses(self, progs) -> List[dict]:
         off = _aligned(self.wit.data_ptr()) - self.wit.data_ptr()
         b = self.wit[off:off + self.n * WITNESS_DTYPE.itemsize].cpu().numpy().view(WITNESS_DTYPE)
-        return [witness_dict(b[i], progs[i].n_stmts) for i in range(self.n)]
+        return [witness_dict(b[i], int(b[i]["n_stmts"])) for i in range(self.n)]
 
 
 def _aligned(ptr: int) -> int:

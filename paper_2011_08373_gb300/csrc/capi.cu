@@ -48,6 +48,69 @@ uint32_t slot_weight_of(const gr_program &p, uint32_t k) {
     return p.slot_level[k] == GR_GRID ? 13u : 1u;  // (gw*gb) + lw^0 with gw = 12
 }
 
+// Control runs through the statements; after the last statement of a loop
+// body it jumps back to the body's first statement while iterations remain
+// (the innermost loop ending there first, then its parents).
+uint32_t exec_order(const gr_program &p, uint8_t *st, uint8_t *ctr, uint32_t cap) {
+    uint32_t count[GR_MAX_LOOPS] = {0, 0, 0, 0};
+    const uint32_t nl = std::min<uint32_t>(p.n_loops, GR_MAX_LOOPS);
+    uint32_t n = 0, pc = 0;
+    while (pc < p.n_stmts) {
+        int inner = -1;
+        for (uint32_t q = 0; q < nl; ++q)
+            if (p.loops[q].lo <= pc && pc <= p.loops[q].hi && (inner < 0 || p.loops[q].lo > p.loops[inner].lo))
+                inner = (int)q;
+        if (n < cap) {
+            st[n] = (uint8_t)pc;
+            ctr[n] = (uint8_t)(inner < 0 ? 0u : count[inner]);
+        }
+        if (++n > cap) return n;
+        uint32_t next = pc + 1;
+        for (;;) {  // loops ending at pc, innermost (latest start) first
+            int q = -1;
+            for (uint32_t r = 0; r < nl; ++r)
+                if (p.loops[r].hi == pc && (count[r] != 0xFFFFFFFFu) && (q < 0 || p.loops[r].lo > p.loops[q].lo))
+                    q = (int)r;
+            if (q < 0) break;
+            if (count[q] + 1 < p.loops[q].trips) {
+                ++count[q];
+                next = p.loops[q].lo;
+                break;
+            }
+            count[q] = 0xFFFFFFFFu;  // finished: skip it while looking for a parent
+        }
+        for (uint32_t r = 0; r < nl; ++r)
+            if (count[r] == 0xFFFFFFFFu) count[r] = 0;
+        pc = next;
+    }
+    return n;
+}
+
+gr_status validate_loops(const gr_program *p, uint32_t idx) {
+    if (p->n_loops == 0) return GR_OK;
+    if (p->n_loops > GR_MAX_LOOPS) return fail(GR_EINVAL, "program %u: more than %d loops", idx, GR_MAX_LOOPS);
+    if (!p->loops) return fail(GR_EINVAL, "program %u: loops is NULL", idx);
+    for (uint32_t q = 0; q < p->n_loops; ++q) {
+        const gr_loop &a = p->loops[q];
+        if (a.lo < 1 || a.lo > a.hi || a.hi >= p->n_stmts || a.trips < 1)
+            return fail(GR_EINVAL, "program %u loop %u: needs 1 <= lo <= hi < n_stmts and trips >= 1", idx, q);
+        if (a.trips > GR_MAX_STMTS)
+            return fail(GR_EINVAL, "program %u loop %u: more than %d trips", idx, q, GR_MAX_STMTS);
+        for (uint32_t r = 0; r < q; ++r) {
+            const gr_loop &b = p->loops[r];
+            const bool disjoint = a.hi < b.lo || b.hi < a.lo;
+            const bool nested = (a.lo < b.lo && b.hi <= a.hi) || (b.lo < a.lo && a.hi <= b.hi);
+            if (!disjoint && !nested)
+                return fail(GR_EINVAL, "program %u loops %u, %u: neither disjoint nor nested inside the first "
+                                       "statement", idx, r, q);
+        }
+    }
+    const uint32_t x = exec_count(*p);
+    if (x > GR_MAX_STMTS)
+        return fail(GR_EINVAL, "program %u: more than %d statement instances executed", idx, GR_MAX_STMTS);
+    return GR_OK;
+}
+
 gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
     if (!p) return fail(GR_EINVAL, "program %u: NULL", idx);
     if (p->n_stmts < 1 || p->n_stmts > GR_MAX_STMTS)
@@ -98,7 +161,7 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
     }
     if (n < 32 && (p->existing_mask >> n) != 0)
         return fail(GR_EINVAL, "program %u: existing_mask has bits beyond slot %u", idx, n);
-    return GR_OK;
+    return validate_loops(p, idx);
 }
 
 gr_status validate_opts(const gr_options *o) {
@@ -129,7 +192,7 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
         L.perm_base[p] = perm_total;
         perm_total += progs[p].perm ? progs[p].perm_len : 0;
         L.segmask_elem[p] = seg_total;
-        const uint64_t segs = (uint64_t)progs[p].n_stmts * ls[p].blocks;
+        const uint64_t segs = (uint64_t)exec_count(progs[p]) * ls[p].blocks;
         seg_total += segs;
         L.trace_elem[p] = trace_total;
         trace_total += align_to(segs * t_pad_of(ls[p].threads), 128);
@@ -195,7 +258,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     ArenaHeader *H = reinterpret_cast<ArenaHeader *>(arena);
     H->magic = kArenaMagic;
     H->n_progs = n;
-    for (uint32_t p = 0; p < n; ++p) H->s_max = std::max(H->s_max, progs[p].n_stmts);
+    for (uint32_t p = 0; p < n; ++p) H->s_max = std::max(H->s_max, exec_count(progs[p]));
     H->progs_off = L.progs_off;
     H->order_off = L.order_off;
     H->segbase_off = L.segbase_off;
@@ -214,7 +277,19 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     for (uint32_t p = lo; p < hi; ++p) {
         const gr_program &P = progs[p];
         DevProg &D = dp[p];
-        const uint32_t S = P.n_stmts, nsl = S - 1;
+        const uint32_t nsl = P.n_stmts - 1;
+        // executed statement instances: identity without loops
+        uint8_t st_of[GR_MAX_STMTS], ctr_of[GR_MAX_STMTS];
+        uint32_t S = P.n_stmts;
+        if (P.n_loops) {
+            S = exec_order(P, st_of, ctr_of, GR_MAX_STMTS);
+            D.looped = 1;
+        } else {
+            for (uint32_t s = 0; s < S; ++s) {
+                st_of[s] = (uint8_t)s;
+                ctr_of[s] = 0;
+            }
+        }
         D.n_stmts = S;
         D.n_slots = nsl;
         D.blocks = ls[p].blocks;
@@ -233,15 +308,20 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             D.slot_gr[k] = P.slot_guard ? P.slot_guard[2 * k + 1] : 0;
             if (D.slot_gk[k]) D.guarded_slots |= 1u << k;
         }
+        for (uint32_t s = 0; s + 1 < S; ++s) {
+            D.vslot[s] = (uint8_t)(st_of[s + 1] - 1u);  // the barrier before the next instance
+            if (P.slot_level[D.vslot[s]] == GR_GRID) D.vgrid_mask |= 1u << s;
+        }
         for (uint32_t s = 0; s < S; ++s) {
-            const gr_stmt &st = P.stmts[s];
+            const gr_stmt &st = P.stmts[st_of[s]];
             DevStmt &ds = D.stmts[s];
             const uint32_t M = st.space == GR_SHARED ? P.m_shared : P.m_global;
+            const uint64_t d = P.iter_coef ? (uint64_t)(P.iter_coef[st_of[s]] % M) * ctr_of[s] : 0u;
             ds.op = st.op;
             ds.space = st.space;
             ds.kind = st.kind;
             ds.am = st.a % M;
-            ds.bm = st.b % M;
+            ds.bm = (uint32_t)(((uint64_t)(st.b % M) + d) % M);
             ds.cm = st.c % M;
             ds.perm_off = st.kind == GR_PERM ? (uint32_t)(L.perm_base[p] + st.perm_off) : 0u;
             ds.gk = st.guard_k;
@@ -392,7 +472,7 @@ LaunchCfg choose_cfg(const Workspace &ws, uint32_t n, uint32_t s_max = GR_MAX_ST
 SizeClass size_class(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     SizeClass k{0, 0, 0, 0, ceil_log2(n)};
     for (uint32_t p = 0; p < n; ++p) {
-        k.s_max = std::max(k.s_max, progs[p].n_stmts);
+        k.s_max = std::max(k.s_max, exec_count(progs[p]));
         k.bt_log2 = std::max(k.bt_log2, ceil_log2((uint64_t)ls[p].blocks * ls[p].threads));
         const uint32_t m = std::max(progs[p].m_shared, progs[p].m_global);
         k.m_chunks = std::max(k.m_chunks, (m + kChunkWords - 1) / kChunkWords);

@@ -34,21 +34,27 @@ struct DevStmt {
 };
 static_assert(sizeof(DevStmt) == 32, "DevStmt layout");
 
-// One program: header + statements + slots.  16-byte aligned, fixed size.
+// One program: header + executed statement instances + slots.  n_stmts counts
+// the instances (a loop body once per iteration); n_slots the program's slots.
+// Instance k and k+1 are separated by the barrier of slot vslot[k] (k without
+// loops).  16-byte aligned, fixed size.
 struct DevProg {
     uint32_t n_stmts, n_slots, blocks, threads;
     uint32_t t_pad;        // threads rounded up to a multiple of 8
     uint32_t m_shared, m_global;
     int32_t mode;          // GR_MODE_*
     uint32_t existing, grid_mask, write_mask, shared_rows;
-    uint32_t global_rows, guarded_slots, _r1, _r2;
+    uint32_t global_rows, guarded_slots;
+    uint32_t vgrid_mask;   // grid level of the gaps between executed instances
+    uint32_t looped;       // 1: instances differ from statements (counted loops)
     uint64_t trace_off;    // u16 elements from the scratch trace base; layout [S][B][t_pad]
     uint64_t segmask_off;  // element index of the program's [S][B] segment masks and ranges
     uint32_t weights[GR_MAX_SLOTS];
     uint16_t slot_gk[GR_MAX_SLOTS];
     uint16_t slot_gr[GR_MAX_SLOTS];
-    uint8_t rep[32];       // lowest statement with the same array, map and guard
-    DevStmt stmts[GR_MAX_STMTS];
+    uint8_t rep[32];       // lowest instance with the same array, map and guard
+    uint8_t vslot[32];     // slot whose barrier runs between instances k and k+1
+    DevStmt stmts[GR_MAX_STMTS];  // one per executed statement instance
 };
 static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");
 
@@ -99,6 +105,15 @@ struct Layout {
 };
 gr_status fail(gr_status code, const char *fmt, ...);
 gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx);
+// Statement instances in execution order (st: statement, ctr: counter of its
+// innermost loop); returns how many run, storing at most cap (counting stops
+// past cap).
+uint32_t exec_order(const gr_program &p, uint8_t *st, uint8_t *ctr, uint32_t cap);
+inline uint32_t exec_count(const gr_program &p) {
+    if (p.n_loops == 0) return p.n_stmts;
+    uint8_t st[GR_MAX_STMTS], ctr[GR_MAX_STMTS];
+    return exec_order(p, st, ctr, GR_MAX_STMTS);
+}
 size_t align_to(size_t x, size_t a);
 Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n);
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,

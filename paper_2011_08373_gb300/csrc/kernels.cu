@@ -96,8 +96,26 @@ __device__ __forceinline__ uint32_t range_mask(uint32_t i, uint32_t j) {  // bit
     return hi & ~((1u << i) - 1u);
 }
 
-// Statements in the same phase as s when the slots in `cut` are enabled:
-// slot k separates statements k and k+1.
+// Gaps between executed instances whose barrier is on under the slot mask:
+// gap k (between instances k and k+1) runs the barrier of slot vslot[k].
+__device__ __forceinline__ uint32_t gap_mask(const DevProg &P, uint32_t mask) {
+    if (!P.looped) return mask;
+    uint32_t g = 0;
+    for (uint32_t k = 0; k + 1 < P.n_stmts; ++k)
+        if ((mask >> P.vslot[k]) & 1u) g |= 1u << k;
+    return g;
+}
+
+// The slots whose barriers run in the gaps `gaps`.
+__device__ __forceinline__ uint32_t slots_of_gaps(const DevProg &P, uint32_t gaps) {
+    if (!P.looped) return gaps;
+    uint32_t m = 0;
+    for (uint32_t t = gaps; t; t &= t - 1u) m |= 1u << P.vslot[__ffs(t) - 1u];
+    return m;
+}
+
+// Instances in the same phase as s when the gaps in `cut` hold an enabled
+// barrier: gap k separates instances k and k+1.
 __device__ __forceinline__ uint32_t phase_of(uint32_t s, uint32_t cut, uint32_t S) {
     const uint32_t below = cut & ((1u << s) - 1u);
     const uint32_t start = below ? 32u - __clz(below) : 0u;
@@ -433,11 +451,12 @@ __device__ void prepare_check(Smem &sm, uint32_t mask) {
     const uint32_t S = P.n_stmts;
     if (threadIdx.x < 32) {
         const uint32_t s = threadIdx.x;
+        const uint32_t gaps = gap_mask(P, mask);
         sm.rows_intra[s] = 0;
         sm.rows_inter[s] = 0;
         if (s < S) {
-            sm.ph_intra[s] = phase_of(s, mask, S);
-            sm.ph_inter[s] = phase_of(s, mask & P.grid_mask, S);
+            sm.ph_intra[s] = phase_of(s, gaps, S);
+            sm.ph_inter[s] = phase_of(s, gaps & P.vgrid_mask, S);
         } else {
             sm.ph_intra[s] = sm.ph_inter[s] = 0;
         }
@@ -514,13 +533,14 @@ __device__ void check_misc(Smem &sm, uint32_t mask) {
         sm.diverge = dv;
     }
     unsigned long long local = 0;
+    const uint32_t gaps = gap_mask(P, mask);
     for (uint32_t idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
         const uint32_t i = idx / S, j = idx - i * S;
         if (j < i) continue;
         const uint32_t rg = range_mask(i, j);
         const uint32_t t = tri_index(i, j, S);
-        if ((mask & rg) == 0) local += sm.npair[0][t];
-        if ((mask & P.grid_mask & rg) == 0) local += sm.npair[1][t];
+        if ((gaps & rg) == 0) local += sm.npair[0][t];
+        if ((gaps & P.vgrid_mask & rg) == 0) local += sm.npair[1][t];
     }
     for (uint32_t o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xFFFFFFFFu, local, o);
     if ((threadIdx.x & 31u) == 0 && local) atomicAdd(&sm.pairs, local);
@@ -886,8 +906,9 @@ __device__ void mhs_greedy(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_
 // Loop steps (Algorithm 1)
 // ---------------------------------------------------------------------------
 
-// Clause list from the accumulated witnesses: same-block (i, j) -> slots in
-// [i, j-1]; cross-block (i, j) -> grid slots in [i, j-1] (GenerateClause).
+// Clause list from the accumulated witnesses: same-block (i, j) -> the slots
+// whose barriers run in gaps i..j-1 (slots i..j-1 without loops); cross-block
+// (i, j) -> the grid slots among them (GenerateClause).
 __device__ void build_clauses(Smem &sm) {
     const DevProg &P = sm.prog;
     const uint32_t S = P.n_stmts;
@@ -897,7 +918,7 @@ __device__ void build_clauses(Smem &sm) {
     for (uint32_t idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
         const uint32_t i = idx / S, j = idx - i * S;
         if (j < i) continue;
-        const uint32_t rg = range_mask(i, j);
+        const uint32_t rg = slots_of_gaps(P, range_mask(i, j));
         if ((sm.acc_intra[i] >> j) & 1u) mh_cl(sm)[atomicAdd(&sm.n_cl, 1u)] = rg;
         if ((sm.acc_inter[i] >> j) & 1u) mh_cl(sm)[atomicAdd(&sm.n_cl, 1u)] = rg & P.grid_mask;
     }

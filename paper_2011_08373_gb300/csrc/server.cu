@@ -40,7 +40,8 @@ struct ProgramCopy {
     std::vector<gr_stmt> stmts;
     std::vector<uint8_t> level;
     std::vector<uint16_t> guard;
-    std::vector<uint32_t> weight, perm;
+    std::vector<uint32_t> weight, perm, coef;
+    std::vector<gr_loop> loops;
     gr_program p;
     void take(const gr_program &src) {
         const uint32_t n = src.n_stmts - 1;
@@ -49,6 +50,8 @@ struct ProgramCopy {
         if (src.slot_guard) guard.assign(src.slot_guard, src.slot_guard + 2 * n);
         if (src.slot_weight) weight.assign(src.slot_weight, src.slot_weight + n);
         if (src.perm) perm.assign(src.perm, src.perm + src.perm_len);
+        if (src.n_loops) loops.assign(src.loops, src.loops + src.n_loops);
+        if (src.iter_coef) coef.assign(src.iter_coef, src.iter_coef + src.n_stmts);
         p = src;
         rebind();
     }
@@ -58,6 +61,8 @@ struct ProgramCopy {
         p.slot_guard = guard.empty() ? nullptr : guard.data();
         p.slot_weight = weight.empty() ? nullptr : weight.data();
         p.perm = perm.empty() ? nullptr : perm.data();
+        p.loops = loops.empty() ? nullptr : loops.data();
+        p.iter_coef = coef.empty() ? nullptr : coef.data();
     }
 };
 
@@ -113,7 +118,7 @@ namespace {
 // Room a single program takes in a packed batch (arena, scratch), with the
 // per-item alignment the packer uses.
 void footprint(const gr_program &p, gr_launch l, size_t *arena, size_t *scratch) {
-    const uint64_t segs = (uint64_t)p.n_stmts * l.blocks;
+    const uint64_t segs = (uint64_t)exec_count(p) * l.blocks;
     const uint64_t tpad = (l.threads + 7u) & ~7u;
     *arena = sizeof(DevProg) + 4 + 8 + 64 + (size_t)(p.perm ? p.perm_len : 0) * 4;
     *scratch = segs * 12 + 512 + align_to(segs * tpad, 128) * 2;

@@ -235,6 +235,17 @@ class Workload:
     block_offset: bool = False  # global block-offset maps a*(tid + T*blk) + b
     p_halo: float = 0.0         # block-offset maps: fraction with a halo offset b in [1, 4]
     p_collide: float = 0.01     # programs given one deliberately colliding write
+    # counted loops: probability that a program has one, trip counts of the
+    # outer / nested loop, probability of a nested loop, the loop-counter
+    # coefficients d of statements inside loops (0, 1, 2 or "T" = threads)
+    p_loop: float = 0.0
+    loop_len: tuple = (2, 5)
+    outer_trips: tuple = (2, 4)
+    p_nested: float = 0.5
+    inner_len: tuple = (1, 3)
+    inner_trips: tuple = (2, 3)
+    iter_coefs: Dict[object, float] = field(default_factory=lambda: {0: 0.4, 1: 0.2, 2: 0.1, "T": 0.3})
+    loop_weight_base: int = 10  # lw of the weight (gw*gb) + lw^ld
     extra: dict = field(default_factory=dict)
 
 
@@ -270,6 +281,18 @@ WORKLOADS: Dict[str, Workload] = {
         threads=("loguniform", 32, 1024), n_stmts=("uniform", 4, 24), space=SPACE_SHARED,
         m_words=("times_threads", 4), maps={"affine": 0.4, "strided": 0.3, "perm": 0.3},
         p_write=0.4, guard_fraction=("uniform", 0.0, 0.3), mode=("mixed", 0.5)),
+    # 512 programs with counted loops: 4 blocks x 256 threads, 12 statements
+    # (11 block slots) over a 1,024-word shared array, maps and reads as in
+    # the 1,024-program batch, guards on 15% of statements; every program has
+    # a loop of 2-5 statements run 2-4 times, half of them a nested loop of
+    # 1-3 statements run 2-3 times (at most 25 statement instances run);
+    # addresses inside loops move by d*t, d in {0, 1, 2, threads}; slot
+    # weights lw^ld with lw = 10 (1, 10, 100 by loop depth)
+    "loops512_4x256_s12": Workload(
+        name="loops512_4x256_s12", seed=5, n_programs=512, blocks=4, threads=256,
+        n_stmts=12, space=SPACE_SHARED, m_words=1024,
+        maps={"affine": 0.4, "strided": 0.3, "perm": 0.3}, p_write=0.4,
+        guard_fraction=0.15, p_loop=1.0),
     # the large programs mixed into the serving stream: 128 blocks x 1,024
     # threads, 24 statements, 4,096-word shared array
     "large_128x1024_s24": Workload(
@@ -407,14 +430,71 @@ def generate_program(wl: Workload, p: int, **override) -> Program:
     for k in range(n):
         g0, g1 = guards[k], guards[k + 1]
         sguard.append(g0 if (g0[0] != 0 and g0 == g1) else (0, 0))
-    weights = [wl.grid_weight if lv == LEVEL_GRID else 1 for lv in levels]
+    loops = _draw_loops(wl, p, S) if wl.p_loop > 0 else []
+    depth = [sum(1 for lo, hi, _ in loops if lo <= s <= hi) for s in range(S)]
+    if loops:
+        rng_d = SplitMix64(program_seed(wl.seed ^ 0x100F5, p))
+        dk = list(wl.iter_coefs.keys())
+        dp = [wl.iter_coefs[k] for k in dk]
+        for s in range(S):
+            if depth[s] and s != collide_at:
+                d = dk[_choose(rng_d, dp)]
+                stmts[s]["d"] = T if d == "T" else int(d)
+    # weight (gw*gb) + lw^ld; the barrier of slot k runs at statement k+1, so
+    # its loop depth is that statement's
+    weights = [(wl.grid_weight - 1 if lv == LEVEL_GRID else 0) + wl.loop_weight_base ** depth[k + 1]
+               for k, lv in enumerate(levels)]
     existing = ((1 << n) - 1) if mode == MODE_REMOVE else 0
     return make_program(
         stmts, blocks=B, threads=T,
         m_shared=M if wl.space == SPACE_SHARED else 0,
         m_global=M if wl.space == SPACE_GLOBAL else 0,
         slot_level=levels, slot_guard=sguard, slot_weight=weights, perms=perms,
-        existing_mask=existing, mode=mode)
+        existing_mask=existing, mode=mode, loops=loops)
+
+
+def _choose(rng: SplitMix64, probs) -> int:
+    u = rng.uniform()
+    acc = 0.0
+    for i, q in enumerate(probs):
+        acc += q
+        if u < acc:
+            return i
+    return len(probs) - 1
+
+
+def _draw_loops(wl: Workload, p: int, S: int, max_exec: int = 25) -> list:
+    """A counted loop over statements lo..hi (lo >= 1, so its head slot
+    exists) and, with probability p_nested, a loop nested strictly inside it;
+    trip counts are lowered until at most max_exec instances run."""
+    rng = SplitMix64(program_seed(wl.seed ^ 0x1009, p))
+    if S < 3 or not rng.bernoulli(wl.p_loop):
+        return []
+    length = min(rng.randint(*wl.loop_len), S - 1)
+    lo = rng.randint(1, S - length)
+    hi = lo + length - 1
+    t1 = rng.randint(*wl.outer_trips)
+    inner = None
+    if hi > lo and rng.bernoulli(wl.p_nested):
+        l2 = min(rng.randint(*wl.inner_len), hi - lo)
+        lo2 = rng.randint(lo + 1, hi - l2 + 1)
+        inner = [lo2, lo2 + l2 - 1, rng.randint(*wl.inner_trips)]
+
+    def count():
+        c = S + (t1 - 1) * length
+        if inner:
+            c += t1 * (inner[2] - 1) * (inner[1] - inner[0] + 1)
+        return c
+
+    while count() > max_exec:
+        if inner and inner[2] > 1:
+            inner[2] -= 1
+        else:
+            t1 -= 1
+    loops = [(lo, hi, t1)]
+    if inner:
+        loops.append(tuple(inner))
+    return loops
 
 
 def generate(workload: str, n_programs: Optional[int] = None, start: int = 0,

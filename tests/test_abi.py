@@ -47,6 +47,8 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(gb.gr_stmt) == 24
     assert C.sizeof(gb.gr_witnesses) == 272
     assert C.sizeof(gb.gr_repair_result) == 2944
+    assert C.sizeof(gb.gr_program) == 88
+    assert C.sizeof(gb.gr_loop) == 12
 
 
 def _prog(**over):
@@ -142,3 +144,70 @@ def test_workload_shapes():
     for p in synth.generate("uneven4096_mixed", 40):
         assert 1 <= p.blocks <= 16 and 32 <= p.threads <= 1024 and 4 <= p.n_stmts <= 24
         assert p.m_shared == 4 * p.threads
+
+
+def _loop_prog(loops, S=6):
+    p = synth.make_program([{"op": "W" if s % 2 else "R", "a": 1, "b": s} for s in range(S)],
+                           blocks=1, threads=8, m_shared=64, loops=loops)
+    return p
+
+
+@pytest.mark.parametrize("loops,msg", [
+    ([(0, 2, 2)], "lo <= hi"),           # no head slot before statement 0
+    ([(3, 2, 2)], "lo <= hi"),
+    ([(2, 6, 2)], "hi < n_stmts"),
+    ([(2, 3, 0)], "trips"),
+    ([(1, 3, 2), (2, 4, 2)], "neither disjoint nor nested"),
+    ([(1, 3, 2), (1, 2, 2)], "neither disjoint nor nested"),  # nested loops need their own heads
+    ([(1, 5, 6)], "statement instances"),
+    ([(1, 1, 2), (2, 2, 2), (3, 3, 2), (4, 4, 2), (5, 5, 2)], "loops"),
+])
+def test_validation_rejects_bad_loops(lib, loops, msg):
+    with pytest.raises(gb.GrError) as e:
+        gb.validate(_loop_prog(loops))
+    assert e.value.code == gb.EINVAL
+    assert msg in str(e.value)
+
+
+def test_validation_accepts_loops(lib):
+    for loops in ([(1, 5, 4)], [(1, 4, 2), (2, 3, 3)], [(1, 2, 3), (3, 5, 2)], [(5, 5, 20)]):
+        gb.validate(_loop_prog(loops))
+
+
+# DevProg layout (bytes): n_stmts 0, n_slots 4, vgrid_mask 56, looped 60,
+# vslot 304..335, stmts 336 + 32*k (op 0, space 1, kind 2, bm 8, gk 20, gr 22)
+def _devprog(arena, i):
+    progs_off = int(arena[16:24].view(np.uint64)[0])
+    base = progs_off + 1136 * i
+    return arena[base:base + 1136]
+
+
+def test_packer_lays_out_executed_instances(lib):
+    """Host-side packing of loop programs: one packed statement per executed
+    instance, in the oracle's execution order, with the loop-counter term in
+    its offset, and the slot whose barrier runs between consecutive instances."""
+    import oracle
+    from _tiny import random_loop_program
+
+    progs = [random_loop_program(seed, s_min=3, s_max=8, m_max=40) for seed in range(40)]
+    arena, _ = gb.pack(progs)
+    for i, p in enumerate(progs):
+        d = _devprog(arena, i)
+        order = oracle.unroll(p)
+        assert int(d[0:4].view(np.uint32)[0]) == len(order)
+        assert int(d[4:8].view(np.uint32)[0]) == p.n_slots
+        assert int(d[60:64].view(np.uint32)[0]) == (1 if p.loops else 0)
+        vgrid = 0
+        for z, (s, ctr) in enumerate(order):
+            st = d[336 + 32 * z:336 + 32 * z + 32]
+            M = p.m_shared if p.space[s] == 0 else p.m_global
+            assert st[0] == p.op[s] and st[1] == p.space[s] and st[2] == p.kind[s]
+            want_b = (int(p.b[s]) % M + (int(p.iter_coef[s]) % M) * ctr) % M
+            assert int(st[8:12].view(np.uint32)[0]) == want_b
+            assert int(st[20:22].view(np.uint16)[0]) == p.guard_k[s]
+            if z + 1 < len(order):
+                k = order[z + 1][0] - 1
+                assert d[304 + z] == k
+                if p.slot_level[k] == 1:
+                    vgrid |= 1 << z
+        assert int(d[56:60].view(np.uint32)[0]) == vgrid

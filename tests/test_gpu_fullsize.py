@@ -166,3 +166,16 @@ def test_large_program_full_size(gb):
             assert r["status"] == 1
         else:
             assert r["status"] == 0 and (r["mask"], r["weight"]) == sol
+
+
+def test_loops512_full_size(gb):
+    progs = synth.generate("loops512_4x256_s12")
+    assert len(progs) == 512 and all(p.loops for p in progs)
+    _, got = _run(gb, progs)
+    for p, r in zip(progs, got):
+        _properties(p, r)
+    sample = list(range(0, 512, 16))
+    want = oracle.repair_batch([progs[i] for i in sample], n_threads=N_THREADS)
+    for i, w in zip(sample, want):
+        for k in KEYS:
+            assert got[i][k] == w[k], (i, k)

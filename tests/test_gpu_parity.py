@@ -188,3 +188,64 @@ def test_mhs_strategy_listings(gb):
             want = oracle.repair(p, mode=exp["mode"], strategy=1)
             _same_result(got, want, case["name"])
             assert (got["status"], got["mask"]) == (exp["status"], exp["mask"])
+
+
+# --------------------------------------------------------------------------
+# Counted loops: witnesses over executed instances, clauses over slots
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLD["loop_cases"], ids=[c["name"] for c in GOLD["loop_cases"]])
+def test_loop_cases(gb, case):
+    p = program_from_spec(case["program"])
+    for chk in case["checks"]:
+        got = gb.check(p, chk["mask"])
+        for key in ("intra", "inter", "diverge", "access_pairs"):
+            if key in chk:
+                assert got[key] == chk[key], (key, chk["mask"])
+    for exp in case["repairs"]:
+        for fn in (gb.repair, gb.repair_plain):
+            got = fn(p, mode=exp["mode"])
+            for key in ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses",
+                        "forbidden"):
+                assert got[key] == exp[key], (fn.__name__, key)
+
+
+def test_loop_checks_all_masks(gb):
+    from _tiny import random_loop_program
+
+    progs, masks = [], []
+    for seed in range(120):
+        p = random_loop_program(60000 + seed, s_min=2, s_max=5, b_max=3, t_max=9, m_max=16)
+        for m in range(1 << p.n_slots):
+            progs.append(p)
+            masks.append(m)
+    got = gb.check_batch(progs, masks)
+    for p, m, g in zip(progs, masks, got):
+        assert g == oracle.check(p, m), (p.loops, m)
+
+
+def test_loop_repairs_both_strategies(gb):
+    from _tiny import random_loop_program
+
+    progs = [random_loop_program(61000 + seed, s_min=2, s_max=7, b_max=3, t_max=12, m_max=24)
+             for seed in range(160)]
+    for strategy in (0, 1):
+        for grid_enabled in (True, False):
+            got = gb.repair_batch(progs, grid_enabled=grid_enabled, strategy=strategy)
+            for p, g in zip(progs, got):
+                _same_result(g, oracle.repair(p, grid_enabled=grid_enabled, strategy=strategy), p.loops)
+    for p in progs[:6]:
+        _same_result(gb.repair_plain(p), oracle.repair(p))
+
+
+def test_loop_medium_programs(gb):
+    """Several address chunks, ragged thread counts, loop-counter terms that
+    move a statement's addresses between iterations."""
+    from _tiny import random_loop_program
+
+    progs = [random_loop_program(62000 + seed, s_min=4, s_max=10, b_min=1, b_max=3, t_min=20, t_max=160,
+                                 m_max=2500, a_max=9, c_max=700, d_max=70, trips_max=4)
+             for seed in range(20)]
+    got = gb.repair_batch(progs)
+    for p, g in zip(progs, got):
+        _same_result(g, oracle.repair(p), p.loops)
