@@ -251,6 +251,20 @@ gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *op
                            void *d_scratch, uint64_t scratch_bytes, gr_repair_result *d_out,
                            void *stream);
 
+/* The same repair as gr_repair_packed, spread wide for programs with many
+ * blocks: every check runs one CTA per (program, block) for the same-block
+ * passes plus one CTA per program for the cross-block pass, divergence and the
+ * pair count, and one CTA per program takes each loop step (Algorithm 1's
+ * clause building and Solve).  The loop itself runs on the device as a CUDA
+ * graph whose while-node repeats [check, step] until every program is decided
+ * (bounded: GR_MAX_ITERS + 4 rounds; running past the bound sets the device
+ * error word).  Results equal gr_repair_packed's.  Reads the 128-byte arena
+ * header back to the host (a synchronising copy on stream), then enqueues the
+ * expansion and the graph on stream.  n <= 65,535. */
+gr_status gr_repair_packed_wide(const void *d_arena, uint32_t n, const gr_options *opts,
+                                void *d_scratch, uint64_t scratch_bytes, gr_repair_result *d_out,
+                                void *stream);
+
 /* The two halves of gr_repair_packed, for callers that time or overlap them:
  * gr_expand_packed writes the address traces and chunk masks of every
  * program into d_scratch; gr_repair_expanded runs the persistent repair

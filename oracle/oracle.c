@@ -437,8 +437,10 @@ void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iter
         if (r->iters < ORC_MAX_TRAJ) r->traj[r->iters] = m;
         r->iters++;
         r->access_pairs += w.access_pairs;
+        /* any witness row: one per executed instance (rows past the last
+           instance are zero) */
         int any = w.diverge != 0;
-        for (uint32_t i = 0; i < p->n_stmts; i++)
+        for (uint32_t i = 0; i < 32; i++)
             if (w.intra[i] | w.inter[i]) any = 1;
         if (!any && !probe) {
             if (greedy) {

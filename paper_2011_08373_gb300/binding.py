@@ -80,7 +80,8 @@ EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair"
            "gr_solve", "gr_repair_batch", "gr_check_batch", "gr_pack_size", "gr_pack",
            "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded",
            "gr_repair_packed_noalloc", "gr_server_create", "gr_server_submit", "gr_server_poll",
-           "gr_server_drain", "gr_server_stats", "gr_server_destroy", "gr_tune_packed"]
+           "gr_server_drain", "gr_server_stats", "gr_server_destroy", "gr_tune_packed",
+           "gr_repair_packed_wide"]
 
 
 def lib():
@@ -113,6 +114,7 @@ def lib():
             L.gr_repair_packed.argtypes = [C.c_void_p, C.c_uint32, P(gr_options), C.c_void_p,
                                            C.c_uint64, C.c_void_p, C.c_void_p]
             L.gr_expand_packed.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]
+            L.gr_repair_packed_wide.argtypes = L.gr_repair_packed.argtypes
             L.gr_repair_expanded.argtypes = L.gr_repair_packed.argtypes
             L.gr_repair_packed_noalloc.argtypes = [C.c_void_p, C.c_uint32, P(gr_options), C.c_void_p,
                                                    C.c_void_p]
@@ -436,6 +438,16 @@ class DeviceBatch:
         _check(lib().gr_repair_packed(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
                                       C.c_void_p(self._scratch_ptr), self.scratch_bytes,
                                       C.c_void_p(self._out_ptr), C.c_void_p(st)))
+
+    def run_wide(self, stream: Optional[int] = None) -> None:
+        """The same repair on the wide lane (gr_repair_packed_wide): one CTA per
+        (program, block) per check, the loop as a device-side graph."""
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_repair_packed_wide(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
+                                           C.c_void_p(self._scratch_ptr), self.scratch_bytes,
+                                           C.c_void_p(self._out_ptr), C.c_void_p(st)))
 
     def tune(self, stream: Optional[int] = None) -> int:
         """Pick the fastest CTA shape for this batch (gr_tune_packed)."""

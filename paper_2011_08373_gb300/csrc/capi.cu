@@ -202,7 +202,8 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     L.segmask_off = 256;
     L.segrange_off = align_to(L.segmask_off + seg_total * 8, 256);
     L.trace_off = align_to(L.segrange_off + seg_total * 4, 256);
-    L.scratch_bytes = align_to(L.trace_off + trace_total * 2, 256);
+    L.wide_off = align_to(L.trace_off + trace_total * 2, 256);
+    L.scratch_bytes = align_to(L.wide_off + wide_bytes(n), 256);
     return L;
 }
 
@@ -258,7 +259,10 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     ArenaHeader *H = reinterpret_cast<ArenaHeader *>(arena);
     H->magic = kArenaMagic;
     H->n_progs = n;
-    for (uint32_t p = 0; p < n; ++p) H->s_max = std::max(H->s_max, exec_count(progs[p]));
+    for (uint32_t p = 0; p < n; ++p) {
+        H->s_max = std::max(H->s_max, exec_count(progs[p]));
+        H->b_max = std::max(H->b_max, ls[p].blocks);
+    }
     H->progs_off = L.progs_off;
     H->order_off = L.order_off;
     H->segbase_off = L.segbase_off;
@@ -267,6 +271,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     H->scratch_segmask_off = L.segmask_off;
     H->scratch_trace_off = L.trace_off;
     H->scratch_segrange_off = L.segrange_off;
+    H->scratch_wide_off = L.wide_off;
     H->scratch_bytes = L.scratch_bytes;
     DevProg *dp = reinterpret_cast<DevProg *>(arena + L.progs_off);
     uint32_t *order = reinterpret_cast<uint32_t *>(arena + L.order_off);
@@ -572,6 +577,17 @@ LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status) {
     return choose_cfg(*ws, n);
 }
 
+// Owner-table budget of the wide lane's check CTAs (512 threads, two per SM)
+// for programs of up to s_max statement instances.
+LaunchCfg wide_launch_cfg(uint32_t n, uint32_t s_max, gr_status *status) {
+    Workspace *ws;
+    LaunchCfg c{1, kMinTableBytes};
+    if ((*status = current_ws(&ws)) != GR_OK) return c;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((*status = ensure_configured(*ws)) != GR_OK) return c;
+    return shape_cfg(*ws, n, 0, s_max);
+}
+
 void set_last_error(const char *msg) { g_last_error = msg; }
 }  // namespace gr
 
@@ -644,6 +660,34 @@ gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *op
     GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
     GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
     GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
+    return GR_OK;
+}
+
+gr_status gr_repair_packed_wide(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                                uint64_t scratch_bytes, gr_repair_result *d_out, void *stream) {
+    if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    if (n > 65535) return fail(GR_EINVAL, "the wide lane takes at most 65,535 programs per call");
+    gr_status s = validate_opts(opts);
+    if (s != GR_OK) return s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ArenaHeader h;
+    GR_CUDA(cudaMemcpyAsync(&h, d_arena, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    if (h.magic != kArenaMagic || h.n_progs < n) return fail(GR_EINVAL, "not a packed arena of %u programs", n);
+    if (scratch_bytes < h.scratch_bytes)
+        return fail(GR_ECAPACITY, "scratch needs %llu bytes", (unsigned long long)h.scratch_bytes);
+    const LaunchCfg cfg = shape_cfg(*ws, n, 0, h.s_max);  // 512 threads, two CTAs per SM
+    if (!cfg.table_bytes) return fail(GR_ECAPACITY, "no owner-table room for %u rows", h.s_max);
+    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
+    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
+    GR_CUDA(launch_wide(d_arena, n, h.b_max, opts_or_default(opts), d_scratch, h.scratch_wide_off, d_out,
+                        cfg.table_bytes, st));
     return GR_OK;
 }
 

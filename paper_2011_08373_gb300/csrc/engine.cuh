@@ -13,6 +13,7 @@ namespace gr {
 
 constexpr uint32_t kArenaMagic = 0x47525031u;  // "GRP1"
 constexpr uint32_t kThreads = 512;             // threads per CTA of the repair kernels
+constexpr uint32_t kWideThreads = 512;         // threads per CTA of the wide lane (two CTAs per SM)
 constexpr uint32_t kChunkShift = 10;           // address chunk = 1,024 words
 constexpr uint32_t kChunkWords = 1u << kChunkShift;
 constexpr uint32_t kMaxTileChunks = 8;           // address chunks per owner-table tile
@@ -61,13 +62,14 @@ static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");
 // Arena = ArenaHeader | DevProg[n] | order[n] | seg_base[n+1] | perm[]
 // Scratch = ctrl (256 B) | segmask u64[] | segrange u32[] | trace u16[]
 struct ArenaHeader {
-    uint32_t magic, n_progs, s_max, _r1;  // s_max: most statements of any program
+    uint32_t magic, n_progs, s_max, b_max;  // most statement instances / blocks of any program
     uint64_t progs_off, order_off, segbase_off, perm_off;  // bytes from the arena start
     uint64_t n_segments;                                   // sum over programs of S*B
     uint64_t scratch_segmask_off, scratch_trace_off;       // bytes from the scratch start
     uint64_t scratch_bytes;
     uint64_t scratch_segrange_off;
-    uint64_t _r2[5];
+    uint64_t scratch_wide_off;  // wide lane: LoopState[n] | gr_witnesses[n] | WideCtl
+    uint64_t _r2[4];
 };
 static_assert(sizeof(ArenaHeader) == 128, "ArenaHeader layout");
 
@@ -79,6 +81,14 @@ struct LoopState {
     uint64_t access_pairs, t_start;
     uint32_t traj[GR_MAX_ITERS];
     uint32_t acc_intra[32], acc_inter[32];
+};
+
+// Round bookkeeping of the wide lane's device-side loop (a graph while-node).
+struct WideCtl {
+    uint32_t arrived;  // solve CTAs finished in this round
+    uint32_t active;   // of them, programs still running
+    uint32_t rounds;   // rounds so far (bounded)
+    uint32_t _pad;
 };
 
 struct LaunchCfg {
@@ -99,7 +109,7 @@ size_t mhs_smem_bytes();
 // Host-side helpers (capi.cu).
 struct Layout {
     size_t progs_off, order_off, segbase_off, perm_off, arena_bytes;
-    size_t segmask_off, segrange_off, trace_off, scratch_bytes;
+    size_t segmask_off, segrange_off, trace_off, wide_off, scratch_bytes;
     uint64_t n_segments;
     std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
 };
@@ -135,6 +145,17 @@ cudaError_t launch_plain_check(const void *d_arena, uint32_t p, void *d_scratch,
 cudaError_t launch_plain_solve(const void *d_arena, uint32_t p, LoopState *d_state,
                                const gr_witnesses *d_wit, gr_repair_result *d_out, cudaStream_t st);
 cudaError_t launch_solve(const uint32_t *d_in, uint32_t *d_out, cudaStream_t st);
+// Wide lane: initial solve of every program, then a graph whose while-node
+// repeats [check: one CTA per (program, block) + one per program for the
+// cross-block pass; solve: one CTA per program] until every program is done
+// (at most kWideRounds rounds).  Builds, launches and releases the graph.
+constexpr uint32_t kWideRounds = GR_MAX_ITERS + 4;
+constexpr uint32_t kErrWideRounds = 2u;  // device error word bit: the round bound was hit
+cudaError_t launch_wide(const void *d_arena, uint32_t n, uint32_t max_blocks, const gr_options &opts,
+                        void *d_scratch, uint64_t wide_off, gr_repair_result *d_out, uint32_t table_bytes,
+                        cudaStream_t st);
+size_t wide_bytes(uint32_t n);
+LaunchCfg wide_launch_cfg(uint32_t n, uint32_t s_max, gr_status *status);
 size_t fixed_smem_bytes();
 cudaError_t configure_kernels(uint32_t max_dynamic_smem);
 

@@ -1405,6 +1405,140 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (sm.done) write_result(sm, out);
 }
 
+// ---- wide lane: one CTA per (program, block), the loop on the device -------
+
+struct WideView {
+    LoopState *st;
+    gr_witnesses *wit;
+    WideCtl *ctl;
+};
+
+__device__ __forceinline__ WideView wide_view(uint8_t *scratch, uint64_t wide_off, uint32_t n) {
+    WideView v;
+    v.st = reinterpret_cast<LoopState *>(scratch + wide_off);
+    const size_t st_bytes = ((size_t)n * sizeof(LoopState) + 255) & ~(size_t)255;
+    v.wit = reinterpret_cast<gr_witnesses *>(scratch + wide_off + st_bytes);
+    const size_t wit_bytes = ((size_t)n * sizeof(gr_witnesses) + 255) & ~(size_t)255;
+    v.ctl = reinterpret_cast<WideCtl *>(scratch + wide_off + st_bytes + wit_bytes);
+    return v;
+}
+
+__device__ void zero_witness(gr_witnesses *w) {
+    uint32_t *u = reinterpret_cast<uint32_t *>(w);
+    for (uint32_t i = threadIdx.x; i < sizeof(gr_witnesses) / 4; i += blockDim.x) u[i] = 0;
+}
+
+// CTA p: the initial proposal of program p (Algorithm 1's first Solve, or the
+// removal-mode probe); a program already decided writes its result.
+__global__ void __launch_bounds__(kWideThreads, 2)
+    k_wide_init(const uint8_t *__restrict__ arena, uint32_t n, gr_options opts, uint8_t *scratch, uint64_t wide_off,
+                gr_repair_result *out) {
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    const ArenaView V = view(arena);
+    const WideView W = wide_view(scratch, wide_off, n);
+    const uint32_t p = blockIdx.x;
+    if (p == 0 && threadIdx.x == 0) *W.ctl = WideCtl{0u, 0u, 0u, 0u};
+    load_program(sm, &V.progs[p]);
+    loop_init(sm, *d.mh, opts);
+    state_from_smem(sm, &W.st[p]);
+    zero_witness(&W.wit[p]);
+    if (sm.done) write_result(sm, &out[p]);
+}
+
+// CTA (b, p): b < B_p the same-block passes of block b of program p; b == B_p
+// the cross-block pass, divergence and pair count.  Programs already done and
+// CTAs beyond their program's blocks return at once.
+__global__ void __launch_bounds__(kWideThreads, 2)
+    k_wide_check(const uint8_t *__restrict__ arena, uint32_t n, uint8_t *scratch, uint64_t wide_off,
+                 uint32_t table_bytes) {
+    const ArenaView V = view(arena);
+    const WideView W = wide_view(scratch, wide_off, n);
+    const uint32_t p = blockIdx.y, b = blockIdx.x;
+    if (W.st[p].done || b > V.progs[p].blocks) return;  // uniform over the CTA
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
+    const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
+    const uint32_t *segrange = reinterpret_cast<const uint32_t *>(scratch + V.h->scratch_segrange_off);
+    if (threadIdx.x == 0) sm.err = reinterpret_cast<uint32_t *>(scratch) + 1;
+    load_program(sm, &V.progs[p]);
+    const uint32_t mask = W.st[p].mask;
+    prepare_check(sm, mask);
+    const uint32_t B = sm.prog.blocks;
+    gr_witnesses *wit = &W.wit[p];
+    if (b < B) {
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off,
+                     segrange + sm.prog.segmask_off, b, b + 1, false);
+    } else {
+        check_misc(sm, mask);
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off,
+                     segrange + sm.prog.segmask_off, 0, 0, true);
+        if (threadIdx.x == 0) {
+            wit->diverge = sm.diverge;
+            wit->access_pairs = sm.pairs;
+            wit->n_stmts = sm.prog.n_stmts;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        if (sm.rows_intra[threadIdx.x]) atomicOr(&wit->race_intra[threadIdx.x], sm.rows_intra[threadIdx.x]);
+        if (sm.rows_inter[threadIdx.x]) atomicOr(&wit->race_inter[threadIdx.x], sm.rows_inter[threadIdx.x]);
+    }
+}
+
+// CTA p: clauses from the check's witnesses, the next proposal (one loop step
+// of Algorithm 1), the result once decided, the witness buffer cleared for the
+// next round.  The last CTA of the round to finish sets the while-node's
+// condition: another round while some program runs and the bound is not hit.
+__global__ void __launch_bounds__(kWideThreads, 2)
+    k_wide_solve(const uint8_t *__restrict__ arena, uint32_t n, uint8_t *scratch, uint64_t wide_off,
+                 gr_repair_result *out, cudaGraphConditionalHandle cond) {
+    Dyn d = dyn_smem();
+    Smem &sm = *d.sm;
+    const ArenaView V = view(arena);
+    const WideView W = wide_view(scratch, wide_off, n);
+    const uint32_t p = blockIdx.x;
+    __shared__ uint32_t was_done;
+    if (threadIdx.x == 0) was_done = W.st[p].done;
+    __syncthreads();
+    if (!was_done) {
+        load_program(sm, &V.progs[p]);
+        state_to_smem(sm, &W.st[p]);
+        const gr_witnesses *wit = &W.wit[p];
+        if (threadIdx.x < 32) {
+            sm.rows_intra[threadIdx.x] = wit->race_intra[threadIdx.x];
+            sm.rows_inter[threadIdx.x] = wit->race_inter[threadIdx.x];
+        }
+        if (threadIdx.x == 0) {
+            sm.diverge = wit->diverge;
+            sm.pairs = wit->access_pairs;
+        }
+        __syncthreads();
+        loop_step(sm, *d.mh);
+        state_from_smem(sm, &W.st[p]);
+        if (sm.done) write_result(sm, &out[p]);
+        zero_witness(&W.wit[p]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t running = was_done ? 0u : (sm.done ? 0u : 1u);
+        if (running) atomicAdd(&W.ctl->active, 1u);
+        __threadfence();
+        if (atomicAdd(&W.ctl->arrived, 1u) == n - 1u) {  // the last CTA of this round
+            __threadfence();
+            const uint32_t active = atomicAdd(&W.ctl->active, 0u);
+            const uint32_t rounds = W.ctl->rounds + 1u;
+            W.ctl->rounds = rounds;
+            W.ctl->arrived = 0u;
+            W.ctl->active = 0u;
+            const bool bound = rounds >= kWideRounds;
+            if (active && bound) atomicOr(reinterpret_cast<uint32_t *>(scratch) + 1, kErrWideRounds);
+            cudaGraphSetConditional(cond, (active && !bound) ? 1u : 0u);
+        }
+    }
+}
+
 // gr_solve: in = [n_vars, n_pos, n_neg, forced, forbidden, w[24], pos..., neg...];
 // out = [found, mask, weight].
 __global__ void __launch_bounds__(kThreads, 1) k_solve(const uint32_t *__restrict__ in, uint32_t *__restrict__ out) {
@@ -1452,7 +1586,8 @@ static cudaError_t set_smem(F *f, uint32_t max_dynamic_smem) {
 cudaError_t configure_kernels(uint32_t max_dynamic_smem) {
     cudaError_t e;
     const void *fns[] = {(const void *)k_plain_init, (const void *)k_plain_check, (const void *)k_plain_solve,
-                         (const void *)k_solve};
+                         (const void *)k_solve, (const void *)k_wide_init, (const void *)k_wide_check,
+                         (const void *)k_wide_solve};
     for (const void *f : fns) {
         cudaFuncAttributes a;
         e = cudaFuncGetAttributes(&a, f);
@@ -1525,6 +1660,59 @@ cudaError_t launch_plain_solve(const void *d_arena, uint32_t p, LoopState *d_sta
     k_plain_solve<<<1, kThreads, dyn_bytes(kMinTableBytes), st>>>(static_cast<const uint8_t *>(d_arena), p,
                                                                    d_state, d_wit, out);
     return cudaGetLastError();
+}
+
+size_t wide_bytes(uint32_t n) {
+    const size_t a = ((size_t)n * sizeof(LoopState) + 255) & ~(size_t)255;
+    const size_t b = ((size_t)n * sizeof(gr_witnesses) + 255) & ~(size_t)255;
+    return a + b + 256;
+}
+
+cudaError_t launch_wide(const void *d_arena, uint32_t n, uint32_t max_blocks, const gr_options &opts,
+                        void *d_scratch, uint64_t wide_off, gr_repair_result *d_out, uint32_t table_bytes,
+                        cudaStream_t st) {
+    const uint8_t *a = static_cast<const uint8_t *>(d_arena);
+    uint8_t *sc = static_cast<uint8_t *>(d_scratch);
+    const size_t small = dyn_bytes(kMinTableBytes);
+    k_wide_init<<<n, kWideThreads, small, st>>>(a, n, opts, sc, wide_off, d_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the loop: a graph whose while-node runs [check, solve] until the solve
+    // kernel clears the condition
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    cudaStream_t cap = nullptr;
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            k_wide_check<<<dim3(max_blocks + 1, n), kWideThreads, dyn_bytes(table_bytes), cap>>>(a, n, sc, wide_off,
+                                                                                               table_bytes);
+            cudaError_t e1 = cudaGetLastError();
+            k_wide_solve<<<n, kWideThreads, small, cap>>>(a, n, sc, wide_off, d_out, cond);
+            cudaError_t e2 = cudaGetLastError();
+            e = cudaStreamEndCapture(cap, &body);
+            if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x, st);
+    // released once the launch completes
+    if (x) cudaGraphExecDestroy(x);
+    if (cap) cudaStreamDestroy(cap);
+    cudaGraphDestroy(g);
+    return e;
 }
 
 cudaError_t launch_solve(const uint32_t *d_in, uint32_t *d_out, cudaStream_t st) {

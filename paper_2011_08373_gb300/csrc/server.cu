@@ -66,6 +66,11 @@ struct ProgramCopy {
     }
 };
 
+// Programs with at least this many blocks take the wide lane (one CTA per
+// block per check, the loop as a device-side graph); the rest share the
+// persistent launch, one CTA per program.
+constexpr uint32_t kWideMinBlocks = 32;
+
 struct Request {
     uint64_t ticket;
     ProgramCopy prog;
@@ -73,6 +78,7 @@ struct Request {
     int32_t mode;
     size_t arena_bytes, scratch_bytes;
     Clock::time_point t_submit;
+    bool wide() const { return launch.blocks >= kWideMinBlocks; }
 };
 
 struct Done {
@@ -121,7 +127,7 @@ void footprint(const gr_program &p, gr_launch l, size_t *arena, size_t *scratch)
     const uint64_t segs = (uint64_t)exec_count(p) * l.blocks;
     const uint64_t tpad = (l.threads + 7u) & ~7u;
     *arena = sizeof(DevProg) + 4 + 8 + 64 + (size_t)(p.perm ? p.perm_len : 0) * 4;
-    *scratch = segs * 12 + 512 + align_to(segs * tpad, 128) * 2;
+    *scratch = segs * 12 + 512 + align_to(segs * tpad, 128) * 2 + wide_bytes(1);
 }
 
 void set_error(gr_server *s, gr_status code, const char *what, cudaError_t e) {
@@ -134,8 +140,12 @@ void set_error(gr_server *s, gr_status code, const char *what, cudaError_t e) {
 bool dispatch(gr_server *s, Slot &sl, std::unique_lock<std::mutex> &lk) {
     std::vector<Request> batch;
     size_t a_sum = sizeof(ArenaHeader) + 256, s_sum = 1024;
+    // one lane per launch: the queue's head decides, and the batch stops at
+    // the first request of the other lane (arrival order is kept)
+    const bool wide = !s->pending.empty() && s->pending.front().wide();
     while (!s->pending.empty() && s->inflight + batch.size() < s->max_inflight && batch.size() < s->max_batch) {
         const Request &r = s->pending.front();
+        if (r.wide() != wide || (wide && batch.size() >= 65535u)) break;
         if (!batch.empty() && (a_sum + r.arena_bytes > sl.arena_cap || s_sum + r.scratch_bytes > sl.scratch_cap)) break;
         a_sum += r.arena_bytes;
         s_sum += r.scratch_bytes;
@@ -173,11 +183,22 @@ bool dispatch(gr_server *s, Slot &sl, std::unique_lock<std::mutex> &lk) {
     }
     pack_into(progs.data(), ls.data(), modes.data(), n, L, sl.h_arena);
     gr_status cs = GR_OK;
-    const LaunchCfg cfg = packed_launch_cfg(n, &cs);
+    uint32_t s_max = 1, b_max = 1;
+    for (uint32_t i = 0; i < n; ++i) {
+        s_max = std::max(s_max, exec_count(progs[i]));
+        b_max = std::max(b_max, ls[i].blocks);
+    }
+    const LaunchCfg cfg = wide ? wide_launch_cfg(n, s_max, &cs) : packed_launch_cfg(n, &cs);
     e = cudaMemcpyAsync(sl.d_arena, sl.h_arena, L.arena_bytes, cudaMemcpyHostToDevice, sl.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_scratch, 0, 256, sl.stream);
     if (e == cudaSuccess) e = launch_expand(sl.d_arena, sl.d_scratch, std::min<uint32_t>(n, 1024u), sl.stream);
-    if (e == cudaSuccess) e = launch_repair(sl.d_arena, n, s->opts, sl.d_scratch, sl.d_out, cfg, sl.stream);
+    if (e == cudaSuccess) {
+        if (wide)
+            e = launch_wide(sl.d_arena, n, b_max, s->opts, sl.d_scratch, L.wide_off, sl.d_out, cfg.table_bytes,
+                            sl.stream);
+        else
+            e = launch_repair(sl.d_arena, n, s->opts, sl.d_scratch, sl.d_out, cfg, sl.stream);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost,
                             sl.stream);

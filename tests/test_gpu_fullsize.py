@@ -179,3 +179,29 @@ def test_loops512_full_size(gb):
     for i, w in zip(sample, want):
         for k in KEYS:
             assert got[i][k] == w[k], (i, k)
+
+
+def test_wide_lane_full_size(gb):
+    """The wide lane at full size: the inter-block batch and large programs
+    give the same results as the persistent launch (itself pinned above)."""
+    import torch
+
+    for progs in (synth.generate("interblock256_64x256_s16"), synth.generate("large_128x1024_s24", 3)):
+        db = gb.DeviceBatch(progs)
+        db.run()
+        torch.cuda.synchronize()
+        narrow = db.results()
+        db.run_wide()
+        torch.cuda.synchronize()
+        wide = db.results()
+        for p, w, n in zip(progs, wide, narrow):
+            _properties(p, w)
+            for k in KEYS:
+                assert w[k] == n[k], k
+    p = synth.generate("large_128x1024_s24", 1)[0]
+    sol, _ = _expected_final(p, _w0_by_pairs(p))
+    w = wide[0]
+    if sol is None:
+        assert w["status"] == 1
+    else:
+        assert w["status"] == 0 and (w["mask"], w["weight"]) == sol

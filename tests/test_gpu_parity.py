@@ -249,3 +249,56 @@ def test_loop_medium_programs(gb):
     got = gb.repair_batch(progs)
     for p, g in zip(progs, got):
         _same_result(g, oracle.repair(p), p.loops)
+
+
+# --------------------------------------------------------------------------
+# Wide lane: one CTA per (program, block), the loop as a device-side graph
+# --------------------------------------------------------------------------
+
+def _wide(gb, progs, **kw):
+    import torch
+
+    db = gb.DeviceBatch(progs, **kw)
+    db.run_wide()
+    torch.cuda.synchronize()
+    wide = db.results()
+    db.run()
+    torch.cuda.synchronize()
+    return wide, db.results()
+
+
+def test_wide_lane_matches_oracle(gb):
+    from _tiny import random_loop_program
+
+    progs = [random_program(70000 + seed, s_max=7, b_max=4, t_max=12, m_max=24) for seed in range(80)]
+    progs += [random_loop_program(71000 + seed, s_min=3, s_max=6, b_max=3, t_max=10, m_max=20)
+              for seed in range(40)]
+    progs += [random_program(72000 + seed, s_min=6, s_max=12, b_min=1, b_max=5, t_min=20, t_max=160,
+                             m_max=2500, a_max=9, c_max=700) for seed in range(12)]
+    for strategy in (0, 1):
+        for grid_enabled in (True, False):
+            wide, narrow = _wide(gb, progs, grid_enabled=grid_enabled, strategy=strategy)
+            for p, w, n in zip(progs, wide, narrow):
+                _same_result(w, oracle.repair(p, grid_enabled=grid_enabled, strategy=strategy))
+                assert w["t_end_ns"] >= w["t_start_ns"]
+                _same_result(w, n)
+
+
+def test_wide_lane_iteration_cap(gb):
+    progs = [random_program(30000 + seed, s_min=4, s_max=8, b_max=2, t_max=16, m_max=24)
+             for seed in range(40)]
+    for cap in (1, 2):
+        wide, _ = _wide(gb, progs, max_iters=cap)
+        for p, w in zip(progs, wide):
+            _same_result(w, oracle.repair(p, max_iters=cap))
+
+
+def test_wide_lane_workload_samples(gb):
+    progs = synth.generate("interblock256_64x256_s16", 6, blocks=6, threads=32, m_words=4096)
+    progs += synth.generate("batch1024_4x256_s24", 8)
+    progs += [p for p in synth.generate("uneven4096_mixed", 120) if p.blocks * p.threads <= 1200][:20]
+    want = oracle.repair_batch(progs, n_threads=16)
+    wide, narrow = _wide(gb, progs)
+    for w, n, o in zip(wide, narrow, want):
+        _same_result(w, o)
+        _same_result(n, o)

@@ -48,6 +48,9 @@ MUTANTS = [
      "for (uint32_t t2 = 0; t2 + 1 < p->loop_trips[l]; t2++)"),
     ("inner_statements_use_outer_counter", "orc_emit(p, p->loop_lo[l], p->loop_hi[l], l, t2, st, it, n);",
      "orc_emit(p, p->loop_lo[l], p->loop_hi[l], l, t, st, it, n);"),
+    ("loop_rows_past_statements_ignored",
+     "for (uint32_t i = 0; i < 32; i++)\n            if (w.intra[i] | w.inter[i]) any = 1;",
+     "for (uint32_t i = 0; i < p->n_stmts; i++)\n            if (w.intra[i] | w.inter[i]) any = 1;"),
     ("head_slot_taken_after_statement", "m |= 1u << (st[z] - 1u);", "m |= 1u << (st[z - 1] % 24u);"),
 ]
 

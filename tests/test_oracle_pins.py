@@ -636,11 +636,11 @@ def test_one_trip_loops_change_nothing():
         assert oracle.repair(p) == oracle.repair(q)
 
 
-@pytest.mark.parametrize("seed", range(40))
+@pytest.mark.parametrize("seed", range(80))
 def test_loop_repair_path_independence(seed):
     from _tiny import random_loop_program
 
-    p = random_loop_program(12000 + seed, s_min=3, s_max=5, b_max=2, t_max=5, m_max=10)
+    p = random_loop_program(12000 + seed, s_min=3, s_max=5 + seed % 2, b_max=2, t_max=5, m_max=10)
     for mode in (MODE_REPAIR, MODE_REMOVE):
         got = oracle.repair(p, mode=mode)
         ref = _lowest_safe_mask(p, mode, True)
