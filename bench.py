@@ -281,6 +281,23 @@ def run_ours(args, rank, world, local):
             "same_final_mask": float(np.mean((gres["mask"] == res["mask"]) & (gres["status"] == res["status"]))),
         }
         del gb
+    wide = None
+    if rank == 0 and args.wide_steps > 0:
+        # the wide lane on the same batch: one CTA per (program, block) per
+        # check, the loop as a device-side graph; host wall time per call
+        # (header read, expansion, graph build and launch, completion)
+        batch.run_wide()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.wide_steps):
+            batch.run_wide()
+            torch.cuda.synchronize()
+        t_w = (time.perf_counter() - t0) / args.wide_steps
+        wres = batch.results_raw()
+        wide = {"repairs_per_s": n / t_w, "ms_per_call": t_w * 1000,
+                "same_results": bool(np.array_equal(wres["mask"], res["mask"])
+                                     and np.array_equal(wres["iters"], res["iters"])),
+                "note": "gr_repair_packed_wide, host wall clock per call incl. synchronisation"}
     cpu = None
     if rank == 0 and args.cpu_sample > 0:
         cpu = cpu_baseline_leg(args.workload, args.cpu_sample)
@@ -309,7 +326,7 @@ def run_ours(args, rank, world, local):
             "expand_ms": statistics.mean(expand_ms), "repair_kernel_ms": statistics.mean(repair_ms),
             "latency_in_batch_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "status_counts": {"repaired": status[0], "unrepairable": status[1], "iter_cap": status[2]},
-            "checks_per_repair": checks / n, "strategies": strategies, "wall_s": wall,
+            "checks_per_repair": checks / n, "strategies": strategies, "wide_lane": wide, "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -387,6 +404,8 @@ def main():
     ap.add_argument("--programs", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--plain-programs", type=int, default=64)
+    ap.add_argument("--wide-steps", type=int, default=5,
+                    help="calls of the wide lane on the same batch (0: skip)")
     ap.add_argument("--strategy-steps", type=int, default=5,
                     help="timed launches of the mhs strategy on the same batch (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=32)

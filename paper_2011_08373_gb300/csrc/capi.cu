@@ -183,7 +183,11 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     L.progs_off = sizeof(ArenaHeader);
     L.order_off = align_to(L.progs_off + (size_t)n * sizeof(DevProg), 16);
     L.segbase_off = align_to(L.order_off + (size_t)n * 4, 16);
-    L.perm_off = align_to(L.segbase_off + (size_t)(n + 1) * 8, 16);
+    L.items_off = align_to(L.segbase_off + (size_t)(n + 1) * 8, 16);
+    L.n_items = 0;
+    for (uint32_t p = 0; p < n; ++p)
+        L.n_items += ((uint64_t)exec_count(progs[p]) * ls[p].blocks + kItemSegs - 1) / kItemSegs;
+    L.perm_off = align_to(L.items_off + (size_t)L.n_items * 16, 16);
     L.trace_elem.resize(n);
     L.segmask_elem.resize(n);
     L.perm_base.resize(n);
@@ -266,6 +270,8 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     H->progs_off = L.progs_off;
     H->order_off = L.order_off;
     H->segbase_off = L.segbase_off;
+    H->items_off = L.items_off;
+    H->n_items = L.n_items;
     H->perm_off = L.perm_off;
     H->n_segments = L.n_segments;
     H->scratch_segmask_off = L.segmask_off;
@@ -364,6 +370,19 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     segbase[n] = L.n_segments;
     std::iota(order, order + n, 0u);
     std::stable_sort(order, order + n, [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    // expansion items: runs of up to kItemSegs segments, largest programs first
+    uint32_t *items = reinterpret_cast<uint32_t *>(arena + L.items_off);
+    uint64_t k = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const uint32_t p = order[i];
+        const uint32_t segs = (uint32_t)(segbase[p + 1] - segbase[p]);
+        for (uint32_t lo = 0; lo < segs; lo += kItemSegs, ++k) {
+            items[4 * k] = p;
+            items[4 * k + 1] = lo;
+            items[4 * k + 2] = std::min(segs, lo + kItemSegs);
+            items[4 * k + 3] = 0;
+        }
+    }
 }
 
 }  // namespace gr

@@ -18,6 +18,7 @@ constexpr uint32_t kChunkShift = 10;           // address chunk = 1,024 words
 constexpr uint32_t kChunkWords = 1u << kChunkShift;
 constexpr uint32_t kMaxTileChunks = 8;           // address chunks per owner-table tile
 constexpr uint32_t kSegCap = 512;                // (statement, block) segments listed per batch
+constexpr uint32_t kItemSegs = 64;               // segments per trace-expansion work item
 constexpr uint16_t kEmpty = 0xFFFFu;           // owner-table sentinels
 constexpr uint16_t kMulti = 0xFFFEu;
 constexpr uint32_t kClauseCap = 1024;          // clause buffer (>= 2 * 25 * 26 / 2)
@@ -59,7 +60,7 @@ struct DevProg {
 };
 static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");
 
-// Arena = ArenaHeader | DevProg[n] | order[n] | seg_base[n+1] | perm[]
+// Arena = ArenaHeader | DevProg[n] | order[n] | seg_base[n+1] | items[] | perm[]
 // Scratch = ctrl (256 B) | segmask u64[] | segrange u32[] | trace u16[]
 struct ArenaHeader {
     uint32_t magic, n_progs, s_max, b_max;  // most statement instances / blocks of any program
@@ -69,7 +70,8 @@ struct ArenaHeader {
     uint64_t scratch_bytes;
     uint64_t scratch_segrange_off;
     uint64_t scratch_wide_off;  // wide lane: LoopState[n] | gr_witnesses[n] | WideCtl
-    uint64_t _r2[4];
+    uint64_t items_off, n_items;  // expansion work items (uint4: program, first, end segment)
+    uint64_t _r2[2];
 };
 static_assert(sizeof(ArenaHeader) == 128, "ArenaHeader layout");
 
@@ -108,7 +110,8 @@ size_t mhs_smem_bytes();
 
 // Host-side helpers (capi.cu).
 struct Layout {
-    size_t progs_off, order_off, segbase_off, perm_off, arena_bytes;
+    size_t progs_off, order_off, segbase_off, items_off, perm_off, arena_bytes;
+    uint64_t n_items;
     size_t segmask_off, segrange_off, trace_off, wide_off, scratch_bytes;
     uint64_t n_segments;
     std::vector<uint64_t> trace_elem, segmask_elem, perm_base;

@@ -1122,45 +1122,43 @@ __device__ __forceinline__ ArenaView view(const uint8_t *arena) {
     return v;
 }
 
-// K0: one CTA per program (in the host's largest-first order), one warp per
-// (statement, block) segment of t_pad threads.  Writes the u16 address trace,
-// and per segment the mask of 1,024-word chunks and the [min, max] address of
-// its active accesses (min > max when none is active).
+// K0: CTAs take work items (runs of up to kItemSegs (statement, block)
+// segments of one program, largest programs first, so that a few large
+// programs spread over many CTAs and many small ones share them); one warp
+// per segment of t_pad threads.  Writes the u16 address trace, and per
+// segment the mask of 1,024-word chunks and the [min, max] address of its
+// active accesses (min > max when none is active).
 __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ arena, uint8_t *__restrict__ scratch) {
     const ArenaView V = view(arena);
-    const uint32_t n = V.h->n_progs;
+    const uint64_t n_items = V.h->n_items;
+    const uint4 *items = reinterpret_cast<const uint4 *>(arena + V.h->items_off);
     uint16_t *traces = reinterpret_cast<uint16_t *>(scratch + V.h->scratch_trace_off);
     uint64_t *segmask = reinterpret_cast<uint64_t *>(scratch + V.h->scratch_segmask_off);
     uint32_t *segrange = reinterpret_cast<uint32_t *>(scratch + V.h->scratch_segrange_off);
     __shared__ DevStmt st_sh[GR_MAX_STMTS];
-    __shared__ uint32_t hdr[8];
+    __shared__ uint32_t hdr[4];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (uint32_t item = blockIdx.x; item < n; item += gridDim.x) {
-        const uint32_t p = V.order[item];
-        const DevProg &P = V.progs[p];
+    for (uint64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const uint4 it = items[item];
+        const DevProg &P = V.progs[it.x];
         __syncthreads();
-        if (threadIdx.x < GR_MAX_STMTS * sizeof(DevStmt) / 16) {
+        if (threadIdx.x < GR_MAX_STMTS * sizeof(DevStmt) / 16)
             reinterpret_cast<uint4 *>(st_sh)[threadIdx.x] = reinterpret_cast<const uint4 *>(P.stmts)[threadIdx.x];
-        }
         if (threadIdx.x == 0) {
-            hdr[0] = P.n_stmts;
-            hdr[1] = P.blocks;
-            hdr[2] = P.threads;
-            hdr[3] = P.t_pad;
+            hdr[0] = P.blocks;
+            hdr[1] = P.threads;
+            hdr[2] = P.t_pad;
         }
         __syncthreads();
-        const uint32_t S = hdr[0], B = hdr[1], T = hdr[2], tpad = hdr[3];
-        uint16_t *tr = traces + P.trace_off;
-        uint64_t *sgm = segmask + P.segmask_off;
-        uint32_t *sgr = segrange + P.segmask_off;
-        for (uint32_t seg = warp; seg < S * B; seg += nwarps) {
+        const uint32_t B = hdr[0], T = hdr[1], tpad = hdr[2];
+        for (uint32_t seg = it.y + warp; seg < it.z; seg += nwarps) {
             const uint32_t s = seg / B, blk = seg - s * B;
             const DevStmt &st = st_sh[s];
             const uint32_t M = st.m;
             const uint32_t base = (uint32_t)(((uint64_t)st.cm * blk + st.bm) % M);
             const bool perm = st.kind == GR_PERM;
             const uint32_t step = perm ? 1u : st.am;
-            uint16_t *out = tr + (size_t)seg * tpad;
+            uint16_t *out = traces + P.trace_off + (size_t)seg * tpad;
             uint64_t chunks = 0;
             uint32_t amin = 0xFFFFu, amax = 0;
             for (uint32_t v = lane; v < (tpad >> 3); v += 32) {
@@ -1191,8 +1189,8 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
             amin = __reduce_min_sync(0xFFFFFFFFu, amin);
             amax = __reduce_max_sync(0xFFFFFFFFu, amax);
             if (lane == 0) {
-                sgm[seg] = ((uint64_t)hi32 << 32) | lo32;
-                sgr[seg] = amin | (amax << 16);
+                segmask[P.segmask_off + seg] = ((uint64_t)hi32 << 32) | lo32;
+                segrange[P.segmask_off + seg] = amin | (amax << 16);
             }
         }
     }

@@ -110,6 +110,7 @@ struct gr_server {
     gr_status error = GR_OK;
     char error_text[256] = {0};
     int device = 0;
+    uint32_t expand_grid = 1216;  // CTAs of the trace expansion: 8 per SM
     gr_options opts;
     uint32_t max_inflight = 0, inflight = 0, max_batch = 0;
     uint64_t next_ticket = 1;
@@ -191,7 +192,7 @@ bool dispatch(gr_server *s, Slot &sl, std::unique_lock<std::mutex> &lk) {
     const LaunchCfg cfg = wide ? wide_launch_cfg(n, s_max, &cs) : packed_launch_cfg(n, &cs);
     e = cudaMemcpyAsync(sl.d_arena, sl.h_arena, L.arena_bytes, cudaMemcpyHostToDevice, sl.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_scratch, 0, 256, sl.stream);
-    if (e == cudaSuccess) e = launch_expand(sl.d_arena, sl.d_scratch, std::min<uint32_t>(n, 1024u), sl.stream);
+    if (e == cudaSuccess) e = launch_expand(sl.d_arena, sl.d_scratch, s->expand_grid, sl.stream);
     if (e == cudaSuccess) {
         if (wide)
             e = launch_wide(sl.d_arena, n, b_max, s->opts, sl.d_scratch, L.wide_off, sl.d_out, cfg.table_bytes,
@@ -284,6 +285,9 @@ gr_status gr_server_create(uint64_t mem_budget_bytes, uint32_t n_slots, uint32_t
     if (cs != GR_OK) return cs;
     gr_server *s = new gr_server();
     cudaGetDevice(&s->device);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess && sms > 0)
+        s->expand_grid = 8u * (uint32_t)sms;
     memset(&s->opts, 0, sizeof(s->opts));
     s->opts.grid_enabled = opts ? opts->grid_enabled : 1;
     s->opts.strategy = opts ? opts->strategy : 0;

@@ -211,3 +211,29 @@ def test_packer_lays_out_executed_instances(lib):
                 if p.slot_level[k] == 1:
                     vgrid |= 1 << z
         assert int(d[56:60].view(np.uint32)[0]) == vgrid
+
+
+def test_expansion_items_cover_every_segment_once(lib):
+    """The packer's trace-expansion work items: runs of at most 64 (statement,
+    block) segments of one program, together covering each program's
+    segments exactly once, larger programs first."""
+    from _tiny import random_loop_program
+
+    progs = synth.generate("uneven4096_mixed", 40) + [random_loop_program(s, s_min=3, m_max=40) for s in range(10)]
+    arena, _ = gb.pack(progs)
+    h = arena[:128].view(np.uint64)
+    segbase_off, items_off, n_items = int(h[4]), int(h[12]), int(h[13])
+    n = len(progs)
+    segbase = arena[segbase_off:segbase_off + 8 * (n + 1)].view(np.uint64)
+    items = arena[items_off:items_off + 16 * n_items].view(np.uint32).reshape(-1, 4)
+    covered = [np.zeros(int(segbase[p + 1] - segbase[p]), np.int64) for p in range(n)]
+    order = []
+    for p, lo, hi, _ in items.tolist():
+        assert 0 < hi - lo <= 64
+        covered[p][lo:hi] += 1
+        if not order or order[-1] != p:
+            order.append(p)
+    assert all((c == 1).all() for c in covered)
+    assert sorted(order) == list(range(n))
+    cost = [int(segbase[p + 1] - segbase[p]) * ((progs[p].threads + 7) // 8 * 8) for p in order]
+    assert cost == sorted(cost, reverse=True)
