@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <functional>
 #include <thread>
 #include <cstdarg>
 #include <cstdio>
@@ -135,17 +137,22 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
             if (!p->perm) return fail(GR_EINVAL, "program %u stmt %u: permutation map without perm", idx, s);
             if ((uint64_t)st.perm_off + M > p->perm_len)
                 return fail(GR_EINVAL, "program %u stmt %u: perm_off + M beyond perm_len", idx, s);
-            // a permutation: M values below M, none repeated
-            thread_local uint64_t seen[GR_MAX_WORDS / 64];
-            memset(seen, 0, ((M + 63) / 64) * 8);
+            // a permutation: M values below M, none repeated (M values below M
+            // that fill all M bits of a bitmap)
+            uint64_t seen[GR_MAX_WORDS / 64];
+            const uint32_t words = (M + 63) / 64;
+            memset(seen, 0, words * 8);
             const uint32_t *tbl = p->perm + st.perm_off;
+            uint32_t bad = 0;
             for (uint32_t i = 0; i < M; ++i) {
                 const uint32_t v = tbl[i];
-                if (v >= M) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
-                const uint64_t bit = 1ull << (v & 63u);
-                if (seen[v >> 6] & bit) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
-                seen[v >> 6] |= bit;
+                bad |= v >= M;
+                const uint32_t w = v < M ? v : 0u;
+                seen[w >> 6] |= 1ull << (w & 63u);
             }
+            uint32_t filled = 0;
+            for (uint32_t w = 0; w < words; ++w) filled += (uint32_t)__builtin_popcountll(seen[w]);
+            if (bad || filled != M) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
         }
     }
     if (n > 0 && !p->slot_level) return fail(GR_EINVAL, "program %u: slot_level is NULL", idx);
@@ -202,7 +209,7 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
         trace_total += align_to(segs * t_pad_of(ls[p].threads), 128);
     }
     L.n_segments = seg_total;
-    L.arena_bytes = align_to(L.perm_off + perm_total * 4, 256);
+    L.arena_bytes = align_to(L.perm_off + perm_total * 2, 256);  // tables as u16 (M <= 65,536)
     L.segmask_off = 256;
     L.segrange_off = align_to(L.segmask_off + seg_total * 8, 256);
     L.trace_off = align_to(L.segrange_off + seg_total * 4, 256);
@@ -211,23 +218,79 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     return L;
 }
 
-// Run body(lo, hi) over [0, n) on up to 16 host threads (programs are
-// independent); small batches run inline.
+// A pool of host workers started once (up to 16, one per core) for the
+// per-program host work of a batch: validation and packing.  Programs are
+// independent, so each worker takes a contiguous range.  One batch uses the
+// pool at a time; a call that finds it busy (another host thread) or that
+// has few programs runs inline.
+class HostPool {
+  public:
+    static HostPool &get() {
+        static HostPool *pool = new HostPool();  // never destroyed: its workers never exit
+        return *pool;
+    }
+    template <typename F>
+    void run(uint32_t n, F &body) {
+        const uint32_t parts = n >= 128 ? std::min<uint32_t>(n_workers_ + 1, (n + 63) / 64) : 1u;
+        std::unique_lock<std::mutex> busy(use_, std::try_to_lock);
+        if (parts <= 1 || !busy.owns_lock()) {
+            body(0u, n);
+            return;
+        }
+        const uint32_t per = (n + parts - 1) / parts;
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            job_ = [&body](uint32_t lo, uint32_t hi) { body(lo, hi); };
+            n_ = n;
+            per_ = per;
+            next_.store(1);  // part 0 runs on the calling thread
+            parts_ = parts;
+            pending_ = parts - 1;
+            ++gen_;
+        }
+        cv_.notify_all();
+        body(0u, std::min(n, per));
+        std::unique_lock<std::mutex> g(mu_);
+        done_.wait(g, [&] { return pending_ == 0; });
+    }
+
+  private:
+    HostPool() {
+        const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        n_workers_ = hw - 1;
+        for (uint32_t i = 0; i < n_workers_; ++i) threads_.emplace_back([this] { loop(); });
+        for (auto &th : threads_) th.detach();  // live until the process exits
+    }
+    void loop() {
+        uint64_t seen = 0;
+        for (;;) {
+            std::unique_lock<std::mutex> g(mu_);
+            cv_.wait(g, [&] { return gen_ != seen; });
+            seen = gen_;
+            for (;;) {
+                const uint32_t k = next_.fetch_add(1);
+                if (k >= parts_) break;
+                const uint32_t lo = k * per_, hi = std::min(n_, lo + per_);
+                g.unlock();
+                if (lo < hi) job_(lo, hi);
+                g.lock();
+                if (--pending_ == 0) done_.notify_all();
+            }
+        }
+    }
+    std::mutex use_, mu_;
+    std::condition_variable cv_, done_;
+    std::vector<std::thread> threads_;
+    std::function<void(uint32_t, uint32_t)> job_;
+    std::atomic<uint32_t> next_{0};
+    uint32_t n_workers_ = 0, n_ = 0, per_ = 0, parts_ = 0, pending_ = 0;
+    uint64_t gen_ = 0;
+};
+
+// Run body(lo, hi) over [0, n) on the host pool (programs are independent).
 template <typename F>
 void parallel_over(uint32_t n, F body) {
-    const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const uint32_t nt = n >= 128 ? std::min(hw, (n + 63) / 64) : 1u;
-    if (nt <= 1) {
-        body(0u, n);
-        return;
-    }
-    std::vector<std::thread> th;
-    const uint32_t per = (n + nt - 1) / nt;
-    for (uint32_t t = 0; t < nt; ++t) {
-        const uint32_t lo = t * per, hi = std::min(n, lo + per);
-        if (lo < hi) th.emplace_back(body, lo, hi);
-    }
-    for (auto &x : th) x.join();
+    HostPool::get().run(n, body);
 }
 
 gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n) {
@@ -282,7 +345,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     DevProg *dp = reinterpret_cast<DevProg *>(arena + L.progs_off);
     uint32_t *order = reinterpret_cast<uint32_t *>(arena + L.order_off);
     uint64_t *segbase = reinterpret_cast<uint64_t *>(arena + L.segbase_off);
-    uint32_t *perm = reinterpret_cast<uint32_t *>(arena + L.perm_off);
+    uint16_t *perm = reinterpret_cast<uint16_t *>(arena + L.perm_off);
     std::vector<uint64_t> cost(n);
     parallel_over(n, [&](uint32_t lo, uint32_t hi) {
     for (uint32_t p = lo; p < hi; ++p) {
@@ -356,7 +419,10 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
                 }
             }
         }
-        if (P.perm && P.perm_len) memcpy(perm + L.perm_base[p], P.perm, (size_t)P.perm_len * 4);
+        if (P.perm && P.perm_len) {  // validated: every used entry is below its table's M <= 65,536
+            uint16_t *dst = perm + L.perm_base[p];
+            for (uint32_t i = 0; i < P.perm_len; ++i) dst[i] = (uint16_t)P.perm[i];
+        }
         segbase[p] = L.segmask_elem[p];
         cost[p] = (uint64_t)S * ls[p].blocks * t_pad_of(ls[p].threads);
     }
@@ -364,7 +430,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     {
         uint64_t perm_total = 0;
         for (uint32_t p = 0; p < n; ++p) perm_total += progs[p].perm ? progs[p].perm_len : 0;
-        const size_t tail = L.perm_off + perm_total * 4;
+        const size_t tail = L.perm_off + perm_total * 2;
         if (tail < L.arena_bytes) memset(arena + tail, 0, L.arena_bytes - tail);
     }
     segbase[n] = L.n_segments;

@@ -1109,7 +1109,7 @@ struct ArenaView {
     const DevProg *progs;
     const uint32_t *order;
     const uint64_t *segbase;
-    const uint32_t *perm;
+    const uint16_t *perm;  // permutation tables, entries below 65,536
 };
 
 __device__ __forceinline__ ArenaView view(const uint8_t *arena) {
@@ -1118,7 +1118,7 @@ __device__ __forceinline__ ArenaView view(const uint8_t *arena) {
     v.progs = reinterpret_cast<const DevProg *>(arena + v.h->progs_off);
     v.order = reinterpret_cast<const uint32_t *>(arena + v.h->order_off);
     v.segbase = reinterpret_cast<const uint64_t *>(arena + v.h->segbase_off);
-    v.perm = reinterpret_cast<const uint32_t *>(arena + v.h->perm_off);
+    v.perm = reinterpret_cast<const uint16_t *>(arena + v.h->perm_off);
     return v;
 }
 

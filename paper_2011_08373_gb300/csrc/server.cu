@@ -127,7 +127,8 @@ namespace {
 void footprint(const gr_program &p, gr_launch l, size_t *arena, size_t *scratch) {
     const uint64_t segs = (uint64_t)exec_count(p) * l.blocks;
     const uint64_t tpad = (l.threads + 7u) & ~7u;
-    *arena = sizeof(DevProg) + 4 + 8 + 64 + (size_t)(p.perm ? p.perm_len : 0) * 4;
+    *arena = sizeof(DevProg) + 4 + 8 + 64 + 16 * ((segs + kItemSegs - 1) / kItemSegs) +
+             (size_t)(p.perm ? p.perm_len : 0) * 2 + 16;
     *scratch = segs * 12 + 512 + align_to(segs * tpad, 128) * 2 + wide_bytes(1);
 }
 
