@@ -137,21 +137,18 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
             if (!p->perm) return fail(GR_EINVAL, "program %u stmt %u: permutation map without perm", idx, s);
             if ((uint64_t)st.perm_off + M > p->perm_len)
                 return fail(GR_EINVAL, "program %u stmt %u: perm_off + M beyond perm_len", idx, s);
-            // a permutation: M values below M, none repeated (M values below M
-            // that fill all M bits of a bitmap)
-            uint64_t seen[GR_MAX_WORDS / 64];
-            const uint32_t words = (M + 63) / 64;
-            memset(seen, 0, words * 8);
+            // a permutation: M values below M marking M distinct entries
+            uint8_t mark[GR_MAX_WORDS];
+            memset(mark, 0, M);
             const uint32_t *tbl = p->perm + st.perm_off;
             uint32_t bad = 0;
             for (uint32_t i = 0; i < M; ++i) {
                 const uint32_t v = tbl[i];
                 bad |= v >= M;
-                const uint32_t w = v < M ? v : 0u;
-                seen[w >> 6] |= 1ull << (w & 63u);
+                mark[v < M ? v : 0u] = 1;
             }
             uint32_t filled = 0;
-            for (uint32_t w = 0; w < words; ++w) filled += (uint32_t)__builtin_popcountll(seen[w]);
+            for (uint32_t i = 0; i < M; ++i) filled += mark[i];
             if (bad || filled != M) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
         }
     }
