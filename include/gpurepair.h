@@ -277,7 +277,9 @@ gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *
  * per CTA x CTAs per SM, with the owner-table budget that shape leaves) on
  * this arena, remember the fastest for later gr_repair_packed /
  * gr_repair_expanded / gr_check_packed calls on the same (d_arena, n), and
- * return its index in shape_out (may be NULL).  Runs the repair several times
+ * return it in shape_out (may be NULL): bits 0-3 index the CTA shape, bit 4
+ * is set when the grid is cut so that every CTA gets the same number of
+ * programs (fewer CTAs than fit, no partly filled last round).  Runs the repair several times
  * into d_out and synchronises the stream.  The host-pointer batch calls tune
  * the same way by themselves, once per batch size class. */
 gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,

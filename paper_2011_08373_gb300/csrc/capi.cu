@@ -531,7 +531,7 @@ gr_status ensure_configured(Workspace &ws) {
 // memory share after the fixed part (1 KB per CTA is reserved).  table_bytes
 // is 0 when the shape cannot hold one address chunk of s_max rows.
 LaunchCfg shape_cfg(const Workspace &ws, uint32_t n, uint32_t shape, uint32_t s_max) {
-    const LaunchShape sh = kShapes[shape];
+    const LaunchShape sh = kShapes[shape & kShapeMask];
     LaunchCfg c{0, 0, shape};
     const size_t per_cta = (size_t)ws.smem_per_sm / sh.ctas_per_sm;
     const size_t fixed = fixed_smem_bytes() + 1024;
@@ -543,7 +543,12 @@ LaunchCfg shape_cfg(const Workspace &ws, uint32_t n, uint32_t shape, uint32_t s_
     static_assert(kMinTableBytes >= 25u * 2u * kChunkWords, "one chunk for 25 rows");
     if (table < need) return c;
     c.table_bytes = (uint32_t)table;
-    c.grid = std::max<uint32_t>(1u, std::min<uint32_t>(n, (uint32_t)ws.sms * sh.ctas_per_sm));
+    const uint32_t resident = (uint32_t)ws.sms * sh.ctas_per_sm;
+    c.grid = std::max<uint32_t>(1u, std::min<uint32_t>(n, resident));
+    if (shape & kShapeBalanced) {  // as many CTAs as give every CTA the same number of programs
+        const uint32_t waves = (n + resident - 1) / resident;
+        c.grid = std::max<uint32_t>(1u, (n + waves - 1) / waves);
+    }
     return c;
 }
 
@@ -578,9 +583,11 @@ gr_status tune_shapes(const Workspace &ws, const void *d_arena, uint32_t n, cons
     cudaEvent_t e0, e1;
     GR_CUDA(cudaEventCreate(&e0));
     GR_CUDA(cudaEventCreate(&e1));
-    for (uint32_t sh = 0; sh < kNumShapes; ++sh) {
+    for (uint32_t v = 0; v < 2 * kNumShapes; ++v) {
+        const uint32_t sh = v < kNumShapes ? v : ((v - kNumShapes) | kShapeBalanced);
         const LaunchCfg cfg = shape_cfg(ws, n, sh, s_max);
         if (!cfg.table_bytes) continue;
+        if ((sh & kShapeBalanced) && cfg.grid == shape_cfg(ws, n, sh & kShapeMask, s_max).grid) continue;
         float ms = 0;
         for (int rep = 0; rep < 2; ++rep) {  // the first run warms the shape
             GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));

@@ -104,6 +104,8 @@ struct LaunchShape {
     uint32_t threads, ctas_per_sm;
 };
 constexpr uint32_t kNumShapes = 4;
+constexpr uint32_t kShapeMask = 15u;      // LaunchCfg::shape: index into kShapes ...
+constexpr uint32_t kShapeBalanced = 16u;  // ... plus: grid cut so every CTA gets the same number of programs
 extern const LaunchShape kShapes[kNumShapes];
 size_t dyn_bytes(uint32_t table_bytes);
 size_t mhs_smem_bytes();

@@ -1615,7 +1615,7 @@ cudaError_t launch_repair(const void *d_arena, uint32_t n, const gr_options &opt
     const uint8_t *a = static_cast<const uint8_t *>(d_arena);
     uint8_t *sc = static_cast<uint8_t *>(d_scratch);
     const size_t smem = dyn_bytes(cfg.table_bytes);
-    switch (cfg.shape) {
+    switch (cfg.shape & kShapeMask) {
         case 1: k_repair<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
         case 2: k_repair<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
         case 3: k_repair<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
@@ -1629,7 +1629,7 @@ cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_mask
     const uint8_t *a = static_cast<const uint8_t *>(d_arena);
     uint8_t *sc = static_cast<uint8_t *>(d_scratch);
     const size_t smem = dyn_bytes(cfg.table_bytes);
-    switch (cfg.shape) {
+    switch (cfg.shape & kShapeMask) {
         case 1: k_check<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
         case 2: k_check<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
         case 3: k_check<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
