@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 from paper_2011_08373_gb300 import synth  # noqa: E402
 
 WORKLOAD = "batch1024_4x256_s24"
+# DRAM bytes (read + write) of one k_repair launch, from the ncu capture summarised in
+# profiles/k_repair_batch1024_4x256_s24.md; reset to None whenever k_repair changes.
+NCU_TRAFFIC = {"batch1024_4x256_s24": 37_508_352 + 2_304}
 
 
 def _peaks():
@@ -228,6 +231,7 @@ def run_ours(args, rank, world, local):
     t_rep = statistics.mean(repair_ms) / 1000.0
     peak, peak_kind = _peaks()
     achieved = launch_bytes / t_rep / 1e9
+    traffic = NCU_TRAFFIC.get(args.workload)
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
         # the C-ABI call with host buffers: validate + pack into pinned staging
@@ -317,8 +321,8 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_repair",
-                         "peak_kind": peak_kind},
+                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_repair",
+                         "algorithmic_bytes": launch_bytes, "peak_kind": peak_kind},
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "checks_per_s": checks * world / t_step,
