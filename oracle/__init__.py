@@ -91,6 +91,7 @@ class _Prog(C.Structure):
         ("n_loops", C.c_uint32),
         ("loop_lo", C.c_void_p), ("loop_hi", C.c_void_p), ("loop_trips", C.c_void_p),
         ("iter_coef", C.c_void_p),
+        ("n_neg", C.c_uint32), ("neg", C.c_void_p),
     ]
 
 
@@ -191,13 +192,16 @@ class _Marshalled:
         self.keep += [_u32([l[0] for l in loops] or [0]), _u32([l[1] for l in loops] or [0]),
                       _u32([l[2] for l in loops] or [0]),
                       _u32(coef) if coef is not None else np.zeros(p.op.shape[0], np.uint32)]
+        negs = [int(x) for x in (getattr(p, "neg_clauses", ()) or ())]
+        self.keep.append(_u32(negs or [0]))
         k = self.keep
         ptr = lambda arr: arr.ctypes.data
         self.s = _Prog(p.op.shape[0], ptr(k[0]), ptr(k[1]), ptr(k[2]), ptr(k[3]), ptr(k[4]),
                        ptr(k[5]), ptr(k[6]), ptr(k[7]), ptr(k[8]), ptr(k[9]), ptr(k[10]),
                        ptr(k[11]), ptr(k[12]), int(p.m_shared), int(p.m_global), ptr(k[13]),
                        len(p.perm), int(p.existing_mask), int(p.blocks), int(p.threads),
-                       len(loops), ptr(k[14]), ptr(k[15]), ptr(k[16]), ptr(k[17]))
+                       len(loops), ptr(k[14]), ptr(k[15]), ptr(k[16]), ptr(k[17]),
+                       len(negs), ptr(k[18]))
         self.n_exec = unroll_count(self.s) if loops else p.op.shape[0]
         if self.n_exec > MAX_STMTS:
             raise ValueError(f"{self.n_exec} executed statement instances (at most {MAX_STMTS})")

@@ -57,6 +57,8 @@ typedef struct {
     uint32_t n_loops;
     const uint32_t *loop_lo, *loop_hi, *loop_trips; /* per loop */
     const uint32_t *iter_coef;                      /* per statement; NULL = 0 */
+    uint32_t n_neg;                                 /* negative clauses given with the program */
+    const uint32_t *neg;                            /* each: not all of these slots together */
 } orc_prog;
 
 typedef struct {
@@ -399,6 +401,9 @@ int orc_greedy(uint32_t n, const uint32_t *w, const uint32_t *pos, uint32_t n_po
  *     checked first as a probe whose witnesses seed the clause set, and is not
  *     itself returned.
  *   grid_enabled == 0 forbids every grid slot.
+ *   Negative clauses given with the program (p->neg) hold throughout: no
+ *   proposal contains all slots of one; a greedy proposal that does is
+ *   replaced by the MaxSAT solve (the fallback of Section 2.4).
  * Loop: propose the minimum hitting set of the clauses so far; stop when a
  * proposed mask has no witness (repaired) or the clauses are unsatisfiable
  * (unrepairable); each race witness adds its clause, each divergent slot a
@@ -422,7 +427,7 @@ void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iter
         probe = 1;
     } else {
         uint64_t wt;
-        if (orc_solve(n, p->slot_weight, NULL, 0, NULL, 0, forced, forbidden, &m, &wt)) {
+        if (orc_solve(n, p->slot_weight, NULL, 0, p->neg, p->n_neg, forced, forbidden, &m, &wt)) {
             status = 1;
             goto done;
         }
@@ -448,7 +453,8 @@ void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iter
                 uint32_t xs;
                 uint64_t wt;
                 greedy = 0;
-                if (!orc_solve(n, p->slot_weight, clauses, n_cl, NULL, 0, forced, forbidden, &xs, &wt) && xs != m) {
+                if (!orc_solve(n, p->slot_weight, clauses, n_cl, p->neg, p->n_neg, forced, forbidden, &xs, &wt) &&
+                    xs != m) {
                     m = xs;
                     continue;
                 }
@@ -461,8 +467,13 @@ void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iter
         n_cl = orc_clauses(p, &w, clauses, n_cl);
         forbidden |= w.diverge;
         uint64_t wt;
-        if (greedy && !orc_greedy(n, p->slot_weight, clauses, n_cl, forced, forbidden, &m)) continue;
-        if (orc_solve(n, p->slot_weight, clauses, n_cl, NULL, 0, forced, forbidden, &m, &wt)) {
+        if (greedy && !orc_greedy(n, p->slot_weight, clauses, n_cl, forced, forbidden, &m)) {
+            int ok = 1;
+            for (uint32_t c = 0; c < p->n_neg; c++)
+                if ((m & p->neg[c]) == p->neg[c]) ok = 0;
+            if (ok) continue;
+        }
+        if (orc_solve(n, p->slot_weight, clauses, n_cl, p->neg, p->n_neg, forced, forbidden, &m, &wt)) {
             status = 1;
             break;
         }

@@ -130,6 +130,10 @@ class Program:
     # per-statement coefficient d of the innermost enclosing loop's counter
     # (0..trips-1) in the address map; None = all zero
     iter_coef: Optional[np.ndarray] = None
+    # negative clauses given with the program: no repair may enable every
+    # slot of one of these masks (constraints from outside the model, e.g. a
+    # pair of barriers the programmer rules out)
+    neg_clauses: tuple = ()
 
     @property
     def n_stmts(self) -> int:
@@ -150,7 +154,7 @@ class Program:
 def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int = 0,
                  m_global: int = 0, slot_level=None, slot_guard=None, slot_weight=None,
                  perms: Optional[List[np.ndarray]] = None, existing_mask: int = 0,
-                 mode: int = MODE_REPAIR, loops=()) -> Program:
+                 mode: int = MODE_REPAIR, loops=(), neg_clauses=()) -> Program:
     """Build a Program from a list of statement dicts.
 
     Each dict: op ('R'/'W' or 0/1), space ('shared'/'global' or 0/1), kind
@@ -203,7 +207,7 @@ def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int 
         m_shared=int(m_shared), m_global=int(m_global), perm=perm,
         existing_mask=int(existing_mask), blocks=int(blocks), threads=int(threads), mode=int(mode),
         loops=tuple((int(lo), int(hi), int(tr)) for lo, hi, tr in loops),
-        iter_coef=np.array(cols["d"], np.uint32))
+        iter_coef=np.array(cols["d"], np.uint32), neg_clauses=tuple(int(x) for x in neg_clauses))
 
 
 # ---------------------------------------------------------------------------

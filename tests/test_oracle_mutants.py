@@ -51,6 +51,9 @@ MUTANTS = [
     ("loop_rows_past_statements_ignored",
      "for (uint32_t i = 0; i < 32; i++)\n            if (w.intra[i] | w.inter[i]) any = 1;",
      "for (uint32_t i = 0; i < p->n_stmts; i++)\n            if (w.intra[i] | w.inter[i]) any = 1;"),
+    ("negative_clauses_ignored", "clauses, n_cl, p->neg, p->n_neg, forced, forbidden, &m, &wt)",
+     "clauses, n_cl, NULL, 0, forced, forbidden, &m, &wt)"),
+    ("greedy_negative_check_skipped", "                if ((m & p->neg[c]) == p->neg[c]) ok = 0;", ""),
     ("head_slot_taken_after_statement", "m |= 1u << (st[z] - 1u);", "m |= 1u << (st[z - 1] % 24u);"),
 ]
 
@@ -66,6 +69,8 @@ def _all_pins():
         yield lambda c=case: pins.test_greedy_worked_cases(c)
     for case in pins.GOLD["loop_cases"]:
         yield lambda c=case: pins.test_loop_cases(c)
+    for case in pins.GOLD["neg_cases"]:
+        yield lambda c=case: pins.test_neg_cases(c)
     for s in range(16):
         yield lambda s=s: pins.test_check_matches_flag_reset_detector(s)
         yield lambda s=s: pins.test_check_matches_affine_closed_form(s)
@@ -79,6 +84,7 @@ def _all_pins():
         yield lambda s=s: pins.test_loop_check_matches_interpreter(s)
         yield lambda s=s: pins.test_loop_repair_path_independence(s)
         yield lambda s=s: pins.test_loop_clause_is_exact_filter(s)
+        yield lambda s=s: pins.test_repair_path_independence_with_negative_clauses(s)
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])

@@ -670,3 +670,63 @@ def test_loop_clause_is_exact_filter(seed):
                 (cl,) = oracle.clauses(p, single)
                 for m in checks:
                     assert bool((checks[m][scope][i] >> j) & 1) == ((m & cl) == 0)
+
+
+# --------------------------------------------------------------------------
+# Negative clauses given with the program (Section 2.4: phi holds positive and
+# negative monotone clauses; the mhs strategy falls back to MaxSAT)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLD["neg_cases"], ids=[c["name"] for c in GOLD["neg_cases"]])
+def test_neg_cases(case):
+    p = program_from_spec(case["program"])
+    n = p.n_slots
+    w = [int(x) for x in p.slot_weight]
+    g = oracle.greedy(n, w, case["repairs"][0]["clauses"])
+    assert g == case["greedy_mhs"]
+    if case["program"]["neg_clauses"]:
+        # the greedy hitting set breaks a negative clause: the strategy must fall back
+        assert any(g & c == c for c in case["program"]["neg_clauses"])
+    for exp in case["repairs"]:
+        got = oracle.repair(p, mode=exp["mode"], strategy=exp["strategy"])
+        for key in ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses", "forbidden"):
+            assert got[key] == exp[key], (key, case["cite"])
+
+
+def _random_negs(seed, n):
+    rng = synth.SplitMix64(synth.program_seed(4242, seed))
+    negs = []
+    for _ in range(rng.randint(0, 3)):
+        m = 0
+        for _ in range(rng.randint(1, 2)):
+            m |= 1 << rng.randint(0, n - 1)
+        negs.append(m)
+    return tuple(negs)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_repair_path_independence_with_negative_clauses(seed):
+    """With negative clauses the loop ends at the lowest-key clean mask that
+    contains none of them, for both strategies."""
+    from _tiny import random_loop_program
+
+    p = random_program(14000 + seed, s_min=3, s_max=6, b_max=2, t_max=6, m_max=10) if seed % 2 else \
+        random_loop_program(14000 + seed, s_min=3, s_max=5, b_max=2, t_max=5, m_max=10)
+    p.neg_clauses = _random_negs(seed, p.n_slots)
+    for mode in (MODE_REPAIR, MODE_REMOVE):
+        forced = p.existing_mask if mode == MODE_REPAIR else 0
+        best = None
+        for x in range(1 << p.n_slots):
+            if (x & forced) != forced or any(x & c == c for c in p.neg_clauses):
+                continue
+            c = oracle.check(p, x)
+            if any(c["intra"]) or any(c["inter"]) or c["diverge"]:
+                continue
+            key = (sum(int(p.slot_weight[k]) for k in range(p.n_slots) if (x >> k) & 1), x)
+            best = key if best is None or key < best else best
+        for strategy in (0, 1):
+            got = oracle.repair(p, mode=mode, strategy=strategy)
+            if best is None:
+                assert got["status"] == 1 and got["mask"] == 0
+            else:
+                assert got["status"] == 0 and (got["weight"], got["mask"]) == best, (strategy, p.neg_clauses)
