@@ -55,6 +55,7 @@ extern "C" {
 #define GR_MAX_CLAUSES 656
 #define GR_MAX_ITERS 64
 #define GR_MAX_LOOPS 4
+#define GR_MAX_NEG 32
 
 typedef int32_t gr_status;
 enum {
@@ -123,6 +124,12 @@ typedef struct {
     const uint32_t *iter_coef;    /* n_stmts entries or NULL (= 0): statement s's address
                                      adds iter_coef[s] * t, t in 0..trips-1 the counter of
                                      the innermost loop holding s (0 outside loops) */
+    uint32_t n_neg;               /* 0..GR_MAX_NEG negative clauses given with the program */
+    const uint32_t *neg;          /* n_neg nonzero slot masks: no repair enables every slot of
+                                     one (Section 2.4's negative monotone clauses, supplied from
+                                     outside the model, e.g. barrier pairs the programmer rules
+                                     out); they join every Solve of the loop, and a greedy (mhs)
+                                     proposal that breaks one is replaced by the MaxSAT solve */
 } gr_program;
 
 typedef struct {

@@ -45,7 +45,8 @@ class gr_program(C.Structure):
                 ("slot_weight", C.POINTER(C.c_uint32)), ("m_shared", C.c_uint32),
                 ("m_global", C.c_uint32), ("perm", C.POINTER(C.c_uint32)), ("perm_len", C.c_uint32),
                 ("existing_mask", C.c_uint32), ("n_loops", C.c_uint32),
-                ("loops", C.POINTER(gr_loop)), ("iter_coef", C.POINTER(C.c_uint32))]
+                ("loops", C.POINTER(gr_loop)), ("iter_coef", C.POINTER(C.c_uint32)),
+                ("n_neg", C.c_uint32), ("neg", C.POINTER(C.c_uint32))]
 
 
 class gr_launch(C.Structure):
@@ -194,6 +195,11 @@ class CProgram:
         if coef is not None:
             self.coef = np.ascontiguousarray(coef, dtype=np.uint32)
             self.s.iter_coef = self.coef.ctypes.data_as(C.POINTER(C.c_uint32))
+        negs = list(getattr(p, "neg_clauses", ()) or ())
+        if negs:
+            self.neg = np.ascontiguousarray(np.array(negs, np.uint32))
+            self.s.n_neg = len(negs)
+            self.s.neg = self.neg.ctypes.data_as(C.POINTER(C.c_uint32))
         self.launch = gr_launch(int(p.blocks), int(p.threads))
         self.mode = int(p.mode)
 
@@ -219,7 +225,8 @@ class ProgramBatch:
                            ("slot_guard", np.uint64), ("slot_weight", np.uint64),
                            ("m_shared", np.uint32), ("m_global", np.uint32), ("perm", np.uint64),
                            ("perm_len", np.uint32), ("existing_mask", np.uint32),
-                           ("n_loops", np.uint32), ("loops", np.uint64), ("iter_coef", np.uint64)],
+                           ("n_loops", np.uint32), ("loops", np.uint64), ("iter_coef", np.uint64),
+                           ("n_neg", np.uint32), ("neg", np.uint64)],
                           align=True)
 
     def __init__(self, progs: Sequence):
@@ -271,6 +278,13 @@ class ProgramBatch:
                 [p.iter_coef if c else np.zeros(len(p.op), np.uint32) for p, c in zip(progs, has_coef)]
             ).astype(np.uint32))
             pa["iter_coef"] = np.where(has_coef, self.coef.ctypes.data + 4 * s_off[:-1], 0)
+        nneg = np.array([len(getattr(p, "neg_clauses", ()) or ()) for p in progs], np.int64)
+        if nneg.any():
+            n_off = np.concatenate([[0], np.cumsum(nneg)])
+            self.neg_arr = np.ascontiguousarray(
+                np.array([c for p in progs for c in (getattr(p, "neg_clauses", ()) or ())], np.uint32))
+            pa["n_neg"] = nneg
+            pa["neg"] = np.where(nneg > 0, self.neg_arr.ctypes.data + 4 * n_off[:-1], 0)
         self.progs = pa
         la = np.zeros((n, 2), np.uint32)
         la[:, 0] = [p.blocks for p in progs]

@@ -165,6 +165,11 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
     }
     if (n < 32 && (p->existing_mask >> n) != 0)
         return fail(GR_EINVAL, "program %u: existing_mask has bits beyond slot %u", idx, n);
+    if (p->n_neg > GR_MAX_NEG) return fail(GR_EINVAL, "program %u: more than %d negative clauses", idx, GR_MAX_NEG);
+    if (p->n_neg && !p->neg) return fail(GR_EINVAL, "program %u: neg is NULL", idx);
+    for (uint32_t c = 0; c < p->n_neg; ++c)
+        if (p->neg[c] == 0 || (n < 32 && (p->neg[c] >> n) != 0))
+            return fail(GR_EINVAL, "program %u negative clause %u: empty or beyond slot %u", idx, c, n);
     return validate_loops(p, idx);
 }
 
@@ -370,6 +375,8 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
         D.m_global = P.m_global;
         D.mode = modes ? modes[p] : GR_MODE_REPAIR;
         D.existing = P.existing_mask;
+        D.n_neg = P.n_neg;
+        for (uint32_t c = 0; c < P.n_neg; ++c) D.neg[c] = P.neg[c];
         D.trace_off = L.trace_elem[p];
         D.segmask_off = L.segmask_elem[p];
         for (uint32_t k = 0; k < nsl; ++k) {

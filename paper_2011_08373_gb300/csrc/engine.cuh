@@ -56,6 +56,8 @@ struct DevProg {
     uint16_t slot_gr[GR_MAX_SLOTS];
     uint8_t rep[32];       // lowest instance with the same array, map and guard
     uint8_t vslot[32];     // slot whose barrier runs between instances k and k+1
+    uint32_t n_neg, _r3[3];
+    uint32_t neg[GR_MAX_NEG];  // negative clauses given with the program
     DevStmt stmts[GR_MAX_STMTS];  // one per executed statement instance
 };
 static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");

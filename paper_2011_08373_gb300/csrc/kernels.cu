@@ -948,7 +948,7 @@ __device__ void loop_init(Smem &sm, MhsSmem &mh, const gr_options &opts) {
     }
     __syncthreads();
     if (P.mode != GR_MODE_REMOVE) {
-        mhs_solve(sm, mh, P.n_slots, P.weights, 0, nullptr, 0, sm.forced, sm.forbidden);
+        mhs_solve(sm, mh, P.n_slots, P.weights, 0, P.neg, P.n_neg, sm.forced, sm.forbidden);
         if (threadIdx.x == 0) {
             if (sm.sol_found) {
                 sm.mask = sm.sol_mask;
@@ -1003,9 +1003,13 @@ __device__ void loop_step(Smem &sm, MhsSmem &mh) {
     bool solved = false;
     if (step == 0 && sm.greedy) {
         mhs_greedy(sm, mh, P.n_slots, P.weights, sm.n_cl, sm.forced, sm.forbidden);
-        solved = sm.sol_found != 0;  // else fall back to the MaxSAT solve
+        // a greedy set that breaks a negative clause falls back to the MaxSAT solve
+        bool ok = sm.sol_found != 0;
+        for (uint32_t c = 0; c < P.n_neg && ok; ++c)
+            if ((sm.sol_mask & P.neg[c]) == P.neg[c]) ok = false;
+        solved = ok;
     }
-    if (!solved) mhs_solve(sm, mh, P.n_slots, P.weights, sm.n_cl, nullptr, 0, sm.forced, sm.forbidden);
+    if (!solved) mhs_solve(sm, mh, P.n_slots, P.weights, sm.n_cl, P.neg, P.n_neg, sm.forced, sm.forbidden);
     if (threadIdx.x == 0) {
         if (step == 1 && (!sm.sol_found || sm.sol_mask == sm.mask)) {
             sm.status = GR_REPAIRED;  // the greedy proposal is the minimum

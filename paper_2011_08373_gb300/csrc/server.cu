@@ -40,7 +40,7 @@ struct ProgramCopy {
     std::vector<gr_stmt> stmts;
     std::vector<uint8_t> level;
     std::vector<uint16_t> guard;
-    std::vector<uint32_t> weight, perm, coef;
+    std::vector<uint32_t> weight, perm, coef, neg;
     std::vector<gr_loop> loops;
     gr_program p;
     void take(const gr_program &src) {
@@ -52,6 +52,7 @@ struct ProgramCopy {
         if (src.perm) perm.assign(src.perm, src.perm + src.perm_len);
         if (src.n_loops) loops.assign(src.loops, src.loops + src.n_loops);
         if (src.iter_coef) coef.assign(src.iter_coef, src.iter_coef + src.n_stmts);
+        if (src.n_neg) neg.assign(src.neg, src.neg + src.n_neg);
         p = src;
         rebind();
     }
@@ -63,6 +64,7 @@ struct ProgramCopy {
         p.perm = perm.empty() ? nullptr : perm.data();
         p.loops = loops.empty() ? nullptr : loops.data();
         p.iter_coef = coef.empty() ? nullptr : coef.data();
+        p.neg = neg.empty() ? nullptr : neg.data();
     }
 };
 

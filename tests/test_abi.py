@@ -47,7 +47,7 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(gb.gr_stmt) == 24
     assert C.sizeof(gb.gr_witnesses) == 272
     assert C.sizeof(gb.gr_repair_result) == 2944
-    assert C.sizeof(gb.gr_program) == 88
+    assert C.sizeof(gb.gr_program) == 104
     assert C.sizeof(gb.gr_loop) == 12
 
 
@@ -175,11 +175,15 @@ def test_validation_accepts_loops(lib):
 
 
 # DevProg layout (bytes): n_stmts 0, n_slots 4, vgrid_mask 56, looped 60,
-# vslot 304..335, stmts 336 + 32*k (op 0, space 1, kind 2, bm 8, gk 20, gr 22)
+# vslot 304..335, n_neg 336, neg 352..479, stmts 480 + 32*k (op 0, space 1,
+# kind 2, bm 8, gk 20, gr 22)
+DEVPROG_BYTES, STMT0 = 1280, 480
+
+
 def _devprog(arena, i):
     progs_off = int(arena[16:24].view(np.uint64)[0])
-    base = progs_off + 1136 * i
-    return arena[base:base + 1136]
+    base = progs_off + DEVPROG_BYTES * i
+    return arena[base:base + DEVPROG_BYTES]
 
 
 def test_packer_lays_out_executed_instances(lib):
@@ -199,7 +203,7 @@ def test_packer_lays_out_executed_instances(lib):
         assert int(d[60:64].view(np.uint32)[0]) == (1 if p.loops else 0)
         vgrid = 0
         for z, (s, ctr) in enumerate(order):
-            st = d[336 + 32 * z:336 + 32 * z + 32]
+            st = d[STMT0 + 32 * z:STMT0 + 32 * z + 32]
             M = p.m_shared if p.space[s] == 0 else p.m_global
             assert st[0] == p.op[s] and st[1] == p.space[s] and st[2] == p.kind[s]
             want_b = (int(p.b[s]) % M + (int(p.iter_coef[s]) % M) * ctr) % M
@@ -237,3 +241,20 @@ def test_expansion_items_cover_every_segment_once(lib):
     assert sorted(order) == list(range(n))
     cost = [int(segbase[p + 1] - segbase[p]) * ((progs[p].threads + 7) // 8 * 8) for p in order]
     assert cost == sorted(cost, reverse=True)
+
+
+@pytest.mark.parametrize("negs,msg", [([0], "empty"), ([1 << 7], "beyond slot"), ([1] * 33, "negative clauses")])
+def test_validation_rejects_bad_negative_clauses(lib, negs, msg):
+    with pytest.raises(gb.GrError) as e:
+        gb.validate(_prog(neg_clauses=tuple(negs)))
+    assert e.value.code == gb.EINVAL and msg in str(e.value)
+
+
+def test_packer_copies_negative_clauses(lib):
+    progs = [_prog(neg_clauses=(3, 96)), _prog(), _prog(neg_clauses=(64,))]
+    arena, _ = gb.pack(progs)
+    for i, p in enumerate(progs):
+        d = _devprog(arena, i)
+        n = int(d[336:340].view(np.uint32)[0])
+        assert n == len(p.neg_clauses)
+        assert d[352:352 + 4 * n].view(np.uint32).tolist() == list(p.neg_clauses)

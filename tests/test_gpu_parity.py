@@ -302,3 +302,36 @@ def test_wide_lane_workload_samples(gb):
     for w, n, o in zip(wide, narrow, want):
         _same_result(w, o)
         _same_result(n, o)
+
+
+# --------------------------------------------------------------------------
+# Negative clauses given with the program
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLD["neg_cases"], ids=[c["name"] for c in GOLD["neg_cases"]])
+def test_neg_cases(gb, case):
+    p = program_from_spec(case["program"])
+    for exp in case["repairs"]:
+        for fn in (gb.repair, gb.repair_plain):
+            got = fn(p, mode=exp["mode"], strategy=exp["strategy"])
+            for key in ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses", "forbidden"):
+                assert got[key] == exp[key], (fn.__name__, key)
+
+
+def test_negative_clauses_random(gb):
+    from _tiny import random_loop_program
+    from test_oracle_pins import _random_negs
+
+    progs = []
+    for seed in range(120):
+        p = random_program(80000 + seed, s_min=3, s_max=8, b_max=3, t_max=12, m_max=24) if seed % 3 else \
+            random_loop_program(80000 + seed, s_min=3, s_max=6, b_max=3, t_max=10, m_max=20)
+        p.neg_clauses = _random_negs(seed, p.n_slots)
+        progs.append(p)
+    for strategy in (0, 1):
+        got = gb.repair_batch(progs, strategy=strategy)
+        for p, g in zip(progs, got):
+            _same_result(g, oracle.repair(p, strategy=strategy), p.neg_clauses)
+        wide, narrow = _wide(gb, progs, strategy=strategy)
+        for w, n in zip(wide, got):
+            _same_result(w, n)
