@@ -92,6 +92,7 @@ class _Prog(C.Structure):
         ("loop_lo", C.c_void_p), ("loop_hi", C.c_void_p), ("loop_trips", C.c_void_p),
         ("iter_coef", C.c_void_p),
         ("n_neg", C.c_uint32), ("neg", C.c_void_p),
+        ("n_slots", C.c_uint32), ("slot_pos", C.c_void_p),
     ]
 
 
@@ -178,14 +179,16 @@ class _Marshalled:
     """Keeps the numpy buffers of one program alive while C reads them."""
 
     def __init__(self, p):
-        n = p.op.shape[0] - 1
+        n = len(p.slot_level)
         self.keep = [
             _u8(p.op), _u8(p.space), _u8(p.kind), _u32(p.a), _u32(p.b), _u32(p.c),
             _u32(p.perm_off), _u32(p.guard_k), _u32(p.guard_r), _u8(p.slot_level),
             _u32(p.slot_guard_k), _u32(p.slot_guard_r), _u32(p.slot_weight),
             _u32(p.perm) if len(p.perm) else np.zeros(1, np.uint32),
         ]
-        assert len(p.slot_level) == n
+        pos = getattr(p, "slot_pos", None)
+        if pos is None:
+            assert n == p.op.shape[0] - 1
         loops = list(getattr(p, "loops", ()) or ())
         _check_loops(loops, p.op.shape[0])
         coef = getattr(p, "iter_coef", None)
@@ -194,6 +197,7 @@ class _Marshalled:
                       _u32(coef) if coef is not None else np.zeros(p.op.shape[0], np.uint32)]
         negs = [int(x) for x in (getattr(p, "neg_clauses", ()) or ())]
         self.keep.append(_u32(negs or [0]))
+        self.keep.append(_u32(pos) if pos is not None else np.zeros(1, np.uint32))
         k = self.keep
         ptr = lambda arr: arr.ctypes.data
         self.s = _Prog(p.op.shape[0], ptr(k[0]), ptr(k[1]), ptr(k[2]), ptr(k[3]), ptr(k[4]),
@@ -201,7 +205,7 @@ class _Marshalled:
                        ptr(k[11]), ptr(k[12]), int(p.m_shared), int(p.m_global), ptr(k[13]),
                        len(p.perm), int(p.existing_mask), int(p.blocks), int(p.threads),
                        len(loops), ptr(k[14]), ptr(k[15]), ptr(k[16]), ptr(k[17]),
-                       len(negs), ptr(k[18]))
+                       len(negs), ptr(k[18]), n, ptr(k[19]) if pos is not None else 0)
         self.n_exec = unroll_count(self.s) if loops else p.op.shape[0]
         if self.n_exec > MAX_STMTS:
             raise ValueError(f"{self.n_exec} executed statement instances (at most {MAX_STMTS})")

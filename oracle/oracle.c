@@ -15,7 +15,10 @@
  *     permutation     : perm[perm_off + ((tid + c*blk + b) mod M)]
  *   and guard (k, r): statement s runs for thread tid iff k == 0 or tid%k == r.
  *   slot k (between statements k and k+1): level (0 block / 1 grid),
- *   guard (k, r) with the same meaning, weight w_k.
+ *   guard (k, r) with the same meaning, weight w_k.  With explicit slot
+ *   positions several slots may share one place: slot k then sits after
+ *   statement slot_pos[k] (two slots per place, one block and one grid, give
+ *   the paper's two barrier variables per candidate site).
  *   counted loops (lo, hi, trips): statements lo..hi run trips times; a
  *   statement's address adds d*t, t the counter (0..trips-1) of its innermost
  *   loop.  The barrier of slot k stands just before statement k+1, so it runs
@@ -59,6 +62,8 @@ typedef struct {
     const uint32_t *iter_coef;                      /* per statement; NULL = 0 */
     uint32_t n_neg;                                 /* negative clauses given with the program */
     const uint32_t *neg;                            /* each: not all of these slots together */
+    uint32_t n_slots;                               /* 0: n_stmts - 1, one slot per place */
+    const uint32_t *slot_pos;                       /* per slot: the statement it follows; NULL: k */
 } orc_prog;
 
 typedef struct {
@@ -129,17 +134,22 @@ uint32_t orc_unroll(const orc_prog *p, uint32_t *st, uint32_t *it) {
     return n;
 }
 
+static uint32_t orc_nslots(const orc_prog *p) { return p->n_slots ? p->n_slots : p->n_stmts - 1; }
+
+static uint32_t orc_pos(const orc_prog *p, uint32_t k) { return p->slot_pos ? p->slot_pos[k] : k; }
+
 /* Is there an enabled barrier (any level / grid level) among those that run
- * between instances x < y?  Slot k's barrier runs each time control reaches
- * statement k+1.  A block barrier orders the accesses of threads in the same
+ * between instances x < y?  The barrier of a slot after statement q runs each
+ * time control reaches statement q+1.  A block barrier orders the accesses of threads in the same
  * block, a grid barrier those of every pair of threads (Section 2.2, flag
  * reset). */
 static int orc_separated(const orc_prog *p, const uint32_t *st, uint32_t mask, uint32_t x, uint32_t y,
                          int grid_only) {
     for (uint32_t z = x + 1; z <= y; z++) {
-        const uint32_t k = st[z] - 1;
-        if ((mask >> k) & 1u)
-            if (!grid_only || p->slot_level[k] == 1) return 1;
+        const uint32_t q = st[z] - 1;
+        for (uint32_t k = 0; k < orc_nslots(p); k++)
+            if (orc_pos(p, k) == q && ((mask >> k) & 1u))
+                if (!grid_only || p->slot_level[k] == 1) return 1;
     }
     return 0;
 }
@@ -209,7 +219,7 @@ void orc_check(const orc_prog *p, uint32_t mask, orc_witness *out) {
     }
     free(addr);
     free(act);
-    for (uint32_t k = 0; k + 1 < p->n_stmts; k++) {
+    for (uint32_t k = 0; k < orc_nslots(p); k++) {
         if (!((mask >> k) & 1u) || p->slot_guard_k[k] == 0) continue;
         int seen_true = 0, seen_false = 0;
         for (uint32_t t = 0; t < T; t++) {
@@ -282,23 +292,25 @@ static int orc_cmp_u32(const void *x, const void *y) {
     return a < b ? -1 : a > b;
 }
 
-static uint32_t orc_slots_between(const uint32_t *st, uint32_t x, uint32_t y) {
+static uint32_t orc_slots_between(const orc_prog *p, const uint32_t *st, uint32_t x, uint32_t y) {
     uint32_t m = 0;
-    for (uint32_t z = x + 1; z <= y; z++) m |= 1u << (st[z] - 1u);
+    for (uint32_t z = x + 1; z <= y; z++)
+        for (uint32_t k = 0; k < orc_nslots(p); k++)
+            if (orc_pos(p, k) == st[z] - 1u) m |= 1u << k;
     return m;
 }
 
 uint32_t orc_clauses(const orc_prog *p, const orc_witness *w, uint32_t *clauses, uint32_t n_in) {
     uint32_t grid = 0, n = n_in;
-    for (uint32_t k = 0; k + 1 < p->n_stmts; k++)
+    for (uint32_t k = 0; k < orc_nslots(p); k++)
         if (p->slot_level[k] == 1) grid |= 1u << k;
     uint32_t st[ORC_MAX_STMTS], it[ORC_MAX_STMTS];
     const uint32_t X = orc_unroll(p, st, it);
     if (X > ORC_MAX_STMTS) return n_in;
     for (uint32_t x = 0; x < X; x++) {
         for (uint32_t y = x; y < X; y++) {
-            if ((w->intra[x] >> y) & 1u) clauses[n++] = orc_slots_between(st, x, y);
-            if ((w->inter[x] >> y) & 1u) clauses[n++] = orc_slots_between(st, x, y) & grid;
+            if ((w->intra[x] >> y) & 1u) clauses[n++] = orc_slots_between(p, st, x, y);
+            if ((w->inter[x] >> y) & 1u) clauses[n++] = orc_slots_between(p, st, x, y) & grid;
         }
     }
     qsort(clauses, n, sizeof(uint32_t), orc_cmp_u32);
@@ -410,7 +422,7 @@ int orc_greedy(uint32_t n, const uint32_t *w, const uint32_t *pos, uint32_t n_po
  * negative unit clause.  More than max_iters checks ends with status 2. */
 void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iters, int strategy, orc_result *r) {
     memset(r, 0, sizeof(*r));
-    const uint32_t n = p->n_stmts - 1;
+    const uint32_t n = orc_nslots(p);
     uint32_t grid = 0;
     for (uint32_t k = 0; k < n; k++)
         if (p->slot_level[k] == 1) grid |= 1u << k;

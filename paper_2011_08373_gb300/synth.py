@@ -111,10 +111,10 @@ class Program:
     perm_off: np.ndarray    # uint32 [S]  offset of the statement's table in perm
     guard_k: np.ndarray     # uint16 [S]
     guard_r: np.ndarray     # uint16 [S]
-    slot_level: np.ndarray  # uint8  [S-1]
-    slot_guard_k: np.ndarray  # uint16 [S-1]
-    slot_guard_r: np.ndarray  # uint16 [S-1]
-    slot_weight: np.ndarray   # uint32 [S-1]
+    slot_level: np.ndarray  # uint8  [n_slots] (S-1 unless slot_pos is given)
+    slot_guard_k: np.ndarray  # uint16 [n_slots]
+    slot_guard_r: np.ndarray  # uint16 [n_slots]
+    slot_weight: np.ndarray   # uint32 [n_slots]
     m_shared: int
     m_global: int
     perm: np.ndarray        # uint32 concatenated permutation tables
@@ -134,6 +134,10 @@ class Program:
     # slot of one of these masks (constraints from outside the model, e.g. a
     # pair of barriers the programmer rules out)
     neg_clauses: tuple = ()
+    # per slot, the statement it follows (several slots may share a place,
+    # e.g. a block and a grid candidate at every site); None: slot k follows
+    # statement k
+    slot_pos: Optional[np.ndarray] = None
 
     @property
     def n_stmts(self) -> int:
@@ -141,7 +145,7 @@ class Program:
 
     @property
     def n_slots(self) -> int:
-        return self.n_stmts - 1
+        return int(self.slot_level.shape[0])
 
     def grid_mask(self) -> int:
         m = 0
@@ -154,7 +158,7 @@ class Program:
 def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int = 0,
                  m_global: int = 0, slot_level=None, slot_guard=None, slot_weight=None,
                  perms: Optional[List[np.ndarray]] = None, existing_mask: int = 0,
-                 mode: int = MODE_REPAIR, loops=(), neg_clauses=()) -> Program:
+                 mode: int = MODE_REPAIR, loops=(), neg_clauses=(), slot_pos=None) -> Program:
     """Build a Program from a list of statement dicts.
 
     Each dict: op ('R'/'W' or 0/1), space ('shared'/'global' or 0/1), kind
@@ -187,7 +191,7 @@ def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int 
         cols["gk"].append(gk)
         cols["gr"].append(gr)
         cols["d"].append(int(st.get("d", 0)))
-    n = S - 1
+    n = S - 1 if slot_pos is None else len(slot_pos)
     if slot_level is None:
         slot_level = [LEVEL_BLOCK] * n
     if slot_guard is None:
@@ -207,7 +211,8 @@ def make_program(stmts: List[dict], *, blocks: int, threads: int, m_shared: int 
         m_shared=int(m_shared), m_global=int(m_global), perm=perm,
         existing_mask=int(existing_mask), blocks=int(blocks), threads=int(threads), mode=int(mode),
         loops=tuple((int(lo), int(hi), int(tr)) for lo, hi, tr in loops),
-        iter_coef=np.array(cols["d"], np.uint32), neg_clauses=tuple(int(x) for x in neg_clauses))
+        iter_coef=np.array(cols["d"], np.uint32), neg_clauses=tuple(int(x) for x in neg_clauses),
+        slot_pos=None if slot_pos is None else np.array(slot_pos, np.uint32).reshape(n))
 
 
 # ---------------------------------------------------------------------------

@@ -85,3 +85,27 @@ def random_loop_program(seed, *, s_max=5, b_max=3, t_max=6, m_max=12, d_max=3, t
     p.loops = tuple(random_loops(rng, p.n_stmts, max_exec, trips_max))
     p.iter_coef = np.array([rng.randint(0, d_max) for _ in range(p.n_stmts)], np.uint32)
     return p
+
+
+def with_sites(p, seed, p_both=0.5):
+    """Re-lay the slots of p as candidate sites: each place between two
+    statements gets one slot of its drawn level or, with probability p_both,
+    two slots (a block and a grid candidate, the grid one heavier)."""
+    rng = SplitMix64(program_seed(0x517E5, seed))
+    pos, lv, gk, gr, w = [], [], [], [], []
+    for g in range(p.n_stmts - 1):
+        kinds = [LEVEL_BLOCK, LEVEL_GRID] if rng.bernoulli(p_both) else [int(p.slot_level[g])]
+        for level in kinds:
+            pos.append(g)
+            lv.append(level)
+            gk.append(int(p.slot_guard_k[g]))
+            gr.append(int(p.slot_guard_r[g]))
+            w.append(rng.randint(1, 4) + (rng.randint(1, 6) if level == LEVEL_GRID else 0))
+    n = len(pos)
+    p.slot_pos = np.array(pos, np.uint32)
+    p.slot_level = np.array(lv, np.uint8)
+    p.slot_guard_k = np.array(gk, np.uint16)
+    p.slot_guard_r = np.array(gr, np.uint16)
+    p.slot_weight = np.array(w, np.uint32)
+    p.existing_mask = rng.randint(0, (1 << n) - 1) if n else 0
+    return p

@@ -37,4 +37,5 @@ def program_from_spec(spec):
         slot_level=spec["slot_level"], slot_guard=[tuple(g) for g in spec["slot_guard"]],
         slot_weight=spec["slot_weight"], existing_mask=spec["existing_mask"],
         perms=[np.array(t, np.uint32) for t in spec.get("perms", [])],
-        loops=[tuple(l) for l in spec.get("loops", [])], neg_clauses=spec.get("neg_clauses", []))
+        loops=[tuple(l) for l in spec.get("loops", [])], neg_clauses=spec.get("neg_clauses", []),
+        slot_pos=spec.get("slot_pos"))

@@ -11,14 +11,15 @@ import oracle
 import test_oracle_pins as pins
 
 MUTANTS = [
-    ("separation_off_by_one", "for (uint32_t z = x + 1; z <= y; z++) {\n        const uint32_t k",
-     "for (uint32_t z = x + 1; z < y; z++) {\n        const uint32_t k"),
+    ("separation_off_by_one", "for (uint32_t z = x + 1; z <= y; z++) {\n        const uint32_t q",
+     "for (uint32_t z = x + 1; z < y; z++) {\n        const uint32_t q"),
     ("block_barrier_orders_blocks", "if (!grid_only || p->slot_level[k] == 1) return 1;", "return 1;"),
     ("shared_arrays_cross_blocks", "const int open_cross = !shared && ", "const int open_cross = "),
     ("same_thread_races", "if (same && t1 == t2) continue;", ""),
-    ("clause_range_shifted", "m |= 1u << (st[z] - 1u);", "m |= 1u << (st[z] % 24u);"),
-    ("inter_clause_not_grid_only", "clauses[n++] = orc_slots_between(st, x, y) & grid;",
-     "clauses[n++] = orc_slots_between(st, x, y);"),
+    ("clause_range_shifted", "if (orc_pos(p, k) == st[z] - 1u) m |= 1u << k;",
+     "if (orc_pos(p, k) == st[z] % 24u) m |= 1u << k;"),
+    ("inter_clause_not_grid_only", "clauses[n++] = orc_slots_between(p, st, x, y) & grid;",
+     "clauses[n++] = orc_slots_between(p, st, x, y);"),
     ("tie_break_reversed", "(wt == best_w && x < best_x)", "(wt == best_w && x > best_x)"),
     ("forbidden_ignored", "if (x & forbidden) continue;", ""),
     ("negative_clause_wrong", "if ((x & neg[c]) == neg[c]) ok = 0;", "if ((x & neg[c]) != 0) ok = 0;"),
@@ -43,7 +44,7 @@ MUTANTS = [
     # counted loops
     ("loop_counter_term_dropped", "const uint64_t d = p->iter_coef ? (uint64_t)p->iter_coef[s] * it : 0;",
      "const uint64_t d = 0;"),
-    ("instance_index_taken_for_statement", "const uint32_t k = st[z] - 1;", "const uint32_t k = z - 1;"),
+    ("instance_index_taken_for_statement", "const uint32_t q = st[z] - 1;", "const uint32_t q = z - 1;"),
     ("loop_trips_off_by_one", "for (uint32_t t2 = 0; t2 < p->loop_trips[l]; t2++)",
      "for (uint32_t t2 = 0; t2 + 1 < p->loop_trips[l]; t2++)"),
     ("inner_statements_use_outer_counter", "orc_emit(p, p->loop_lo[l], p->loop_hi[l], l, t2, st, it, n);",
@@ -54,7 +55,9 @@ MUTANTS = [
     ("negative_clauses_ignored", "clauses, n_cl, p->neg, p->n_neg, forced, forbidden, &m, &wt)",
      "clauses, n_cl, NULL, 0, forced, forbidden, &m, &wt)"),
     ("greedy_negative_check_skipped", "                if ((m & p->neg[c]) == p->neg[c]) ok = 0;", ""),
-    ("head_slot_taken_after_statement", "m |= 1u << (st[z] - 1u);", "m |= 1u << (st[z - 1] % 24u);"),
+    ("head_slot_taken_after_statement", "if (orc_pos(p, k) == st[z] - 1u) m |= 1u << k;",
+     "if (orc_pos(p, k) == st[z - 1]) m |= 1u << k;"),
+    ("slot_position_ignored", "return p->slot_pos ? p->slot_pos[k] : k;", "return k;"),
 ]
 
 
@@ -71,6 +74,8 @@ def _all_pins():
         yield lambda c=case: pins.test_loop_cases(c)
     for case in pins.GOLD["neg_cases"]:
         yield lambda c=case: pins.test_neg_cases(c)
+    for case in pins.GOLD["site_cases"]:
+        yield lambda c=case: pins.test_site_cases(c)
     for s in range(16):
         yield lambda s=s: pins.test_check_matches_flag_reset_detector(s)
         yield lambda s=s: pins.test_check_matches_affine_closed_form(s)
@@ -85,6 +90,8 @@ def _all_pins():
         yield lambda s=s: pins.test_loop_repair_path_independence(s)
         yield lambda s=s: pins.test_loop_clause_is_exact_filter(s)
         yield lambda s=s: pins.test_repair_path_independence_with_negative_clauses(s)
+        yield lambda s=s: pins.test_site_check_matches_interpreter(s)
+        yield lambda s=s: pins.test_site_repair_path_independence(s)
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])

@@ -730,3 +730,112 @@ def test_repair_path_independence_with_negative_clauses(seed):
                 assert got["status"] == 1 and got["mask"] == 0
             else:
                 assert got["status"] == 0 and (got["weight"], got["mask"]) == best, (strategy, p.neg_clauses)
+
+
+# --------------------------------------------------------------------------
+# Two barrier variables per site (slots with explicit places)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLD["site_cases"], ids=[c["name"] for c in GOLD["site_cases"]])
+def test_site_cases(case):
+    p = program_from_spec(case["program"])
+    for chk in case["checks"]:
+        got = oracle.check(p, chk["mask"])
+        for key in ("intra", "inter", "diverge", "access_pairs"):
+            if key in chk:
+                assert got[key] == chk[key], (key, chk["mask"], case["cite"])
+    for exp in case["repairs"]:
+        got = oracle.repair(p, mode=exp["mode"], grid_enabled=exp["grid_enabled"])
+        for key in ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses", "forbidden"):
+            assert got[key] == exp[key], (key, case["cite"])
+
+
+def _interpret_sites(p):
+    """_interpret with several slots per place: every slot placed after
+    statement q is passed when control arrives at statement q+1."""
+    pos = list(range(p.n_stmts - 1)) if p.slot_pos is None else [int(x) for x in p.slot_pos]
+    out = []
+    for e in _interpret(p):
+        if e[0] == "bar":
+            out += [("bar", k) for k in range(len(pos)) if pos[k] == e[1]]
+        else:
+            out.append(e)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(50))
+def test_site_check_matches_interpreter(seed):
+    from _tiny import random_loop_program, with_sites
+
+    p = with_sites(random_loop_program(15000 + seed, s_min=2, s_max=5, b_max=3, t_max=5, m_max=10), seed)
+    n = p.n_slots
+    masks = sorted({0, (1 << n) - 1} | {(seed * 2654435761 + k * 40503) % (1 << n) for k in range(4)})
+    events = _interpret_sites(p)
+    for m in masks:
+        got = oracle.check(p, m)
+        intra, inter = _flag_reset_on_events(p, events, m)
+        assert got["intra"] == intra, (m, p.slot_pos)
+        assert got["inter"] == inter, (m, p.slot_pos)
+
+
+def _flag_reset_on_events(p, events, mask):
+    X = sum(1 for e in events if e[0] == "st")
+    B, T = p.blocks, p.threads
+    intra, inter = [0] * X, [0] * X
+    threads = [(b, t) for b in range(B) for t in range(T)]
+    for x, y in itertools.combinations(range(len(threads)), 2):
+        pair = (threads[x], threads[y])
+        same = pair[0][0] == pair[1][0]
+        logs = ([], [])
+        n = -1
+        for e in events:
+            if e[0] == "bar":
+                k = e[1]
+                if (mask >> k) & 1 and (same or p.slot_level[k] == LEVEL_GRID):
+                    logs = ([], [])
+                continue
+            _, s, it = e
+            n += 1
+            fresh = []
+            for who, (b, t) in enumerate(pair):
+                if _runs(int(p.guard_k[s]), int(p.guard_r[s]), t):
+                    inst = ("shared", b) if p.space[s] == SPACE_SHARED else ("global",)
+                    ev = (inst, _addr_it(p, s, b, t, it), p.op[s] == 1, n)
+                    logs[who].append(ev)
+                    fresh.append((who, ev))
+            for who, ev in fresh:
+                for f in logs[1 - who]:
+                    if f[0] == ev[0] and f[1] == ev[1] and (ev[2] or f[2]):
+                        i, j = min(ev[3], f[3]), max(ev[3], f[3])
+                        if same:
+                            intra[i] |= 1 << j
+                        else:
+                            inter[i] |= 1 << j
+    return intra, inter
+
+
+@pytest.mark.parametrize("seed", range(50))
+def test_site_repair_path_independence(seed):
+    """Two variables per site: the loop still ends at the lowest-key clean
+    mask; a site never needs both of its variables (grid orders all a block
+    barrier orders, and costs less than both)."""
+    from _tiny import random_loop_program, with_sites
+
+    p = with_sites(random_program(16000 + seed, s_min=3, s_max=6, b_max=3, t_max=6, m_max=10) if seed % 2 else
+                   random_loop_program(16000 + seed, s_min=3, s_max=5, b_max=2, t_max=5, m_max=10), seed)
+    for mode in (MODE_REPAIR, MODE_REMOVE):
+        for grid_enabled in (True, False):
+            for strategy in (0, 1):
+                got = oracle.repair(p, mode=mode, grid_enabled=grid_enabled, strategy=strategy)
+                ref = _lowest_safe_mask(p, mode, grid_enabled)
+                if ref is None:
+                    assert got["status"] == 1 and got["mask"] == 0
+                else:
+                    assert got["status"] == 0 and (got["weight"], got["mask"]) == ref
+                    if mode == MODE_REPAIR:
+                        continue  # forced existing barriers may hold both variables of a site
+                    pos = [int(x) for x in p.slot_pos]
+                    for a in range(p.n_slots):
+                        for b in range(a + 1, p.n_slots):
+                            if pos[a] == pos[b]:
+                                assert not ((got["mask"] >> a) & 1 and (got["mask"] >> b) & 1)
