@@ -47,7 +47,7 @@ extern "C" {
 #endif
 
 #define GR_MAX_STMTS 25
-#define GR_MAX_SLOTS 24
+#define GR_MAX_SLOTS 32
 #define GR_MAX_THREADS 1024
 #define GR_MAX_BLOCKS 65533
 #define GR_MAX_WORDS 65536
@@ -111,9 +111,10 @@ typedef struct {
 typedef struct {
     uint32_t n_stmts;             /* 1..GR_MAX_STMTS */
     const gr_stmt *stmts;         /* n_stmts entries */
-    const uint8_t *slot_level;    /* n_stmts-1 entries: GR_BLOCK / GR_GRID */
-    const uint16_t *slot_guard;   /* 2*(n_stmts-1) entries: (k, r) per slot; NULL = unguarded */
-    const uint32_t *slot_weight;  /* n_stmts-1 entries in 1..GR_MAX_WEIGHT; NULL = paper
+    const uint8_t *slot_level;    /* one per slot (n_slots, or n_stmts-1 if n_slots is 0):
+                                     GR_BLOCK / GR_GRID */
+    const uint16_t *slot_guard;   /* two per slot: (k, r); NULL = unguarded */
+    const uint32_t *slot_weight;  /* one per slot, in 1..GR_MAX_WEIGHT; NULL = paper
                                      defaults gw=12, ld=0: block 1, grid 13 */
     uint32_t m_shared, m_global;  /* words (1..GR_MAX_WORDS) of each array a statement uses */
     const uint32_t *perm;         /* concatenated permutation tables (may be NULL if unused) */
@@ -124,6 +125,13 @@ typedef struct {
     const uint32_t *iter_coef;    /* n_stmts entries or NULL (= 0): statement s's address
                                      adds iter_coef[s] * t, t in 0..trips-1 the counter of
                                      the innermost loop holding s (0 outside loops) */
+    uint32_t n_slots;             /* 0: one slot per place, slot k after statement k (n_stmts-1
+                                     slots); else 1..GR_MAX_SLOTS slots placed by slot_pos */
+    const uint8_t *slot_pos;      /* n_slots entries or NULL: the statement (0..n_stmts-2) each
+                                     slot follows; several slots may share a place, e.g. a block
+                                     and a grid candidate at every site (Section 2.2 instruments
+                                     both variables per site).  slot_level, slot_guard,
+                                     slot_weight, existing_mask and neg index slots. */
     uint32_t n_neg;               /* 0..GR_MAX_NEG negative clauses given with the program */
     const uint32_t *neg;          /* n_neg nonzero slot masks: no repair enables every slot of
                                      one (Section 2.4's negative monotone clauses, supplied from

@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgpurepair.so")
 
-MAX_STMTS, MAX_SLOTS, MAX_ITERS, MAX_CLAUSES = 25, 24, 64, 656
+MAX_STMTS, MAX_SLOTS, MAX_ITERS, MAX_CLAUSES = 25, 32, 64, 656
 OK, UNSAT, EINVAL, ENOMEM, ECUDA, EBUSY, ECAPACITY = 0, 1, -1, -2, -4, -5, -6
 REPAIRED, UNREPAIRABLE, ITER_CAP = 0, 1, 2
 
@@ -46,6 +46,7 @@ class gr_program(C.Structure):
                 ("m_global", C.c_uint32), ("perm", C.POINTER(C.c_uint32)), ("perm_len", C.c_uint32),
                 ("existing_mask", C.c_uint32), ("n_loops", C.c_uint32),
                 ("loops", C.POINTER(gr_loop)), ("iter_coef", C.POINTER(C.c_uint32)),
+                ("n_slots", C.c_uint32), ("slot_pos", C.POINTER(C.c_uint8)),
                 ("n_neg", C.c_uint32), ("neg", C.POINTER(C.c_uint32))]
 
 
@@ -160,7 +161,7 @@ class CProgram:
 
     def __init__(self, p):
         S = int(p.op.shape[0])
-        n = S - 1
+        n = int(len(p.slot_level))
         st = (gr_stmt * S)()
         for s in range(S):
             st[s].op, st[s].space, st[s].kind = int(p.op[s]), int(p.space[s]), int(p.kind[s])
@@ -195,6 +196,11 @@ class CProgram:
         if coef is not None:
             self.coef = np.ascontiguousarray(coef, dtype=np.uint32)
             self.s.iter_coef = self.coef.ctypes.data_as(C.POINTER(C.c_uint32))
+        pos = getattr(p, "slot_pos", None)
+        if pos is not None:
+            self.pos = np.ascontiguousarray(np.asarray(pos, dtype=np.uint8))
+            self.s.n_slots = n
+            self.s.slot_pos = self.pos.ctypes.data_as(C.POINTER(C.c_uint8))
         negs = list(getattr(p, "neg_clauses", ()) or ())
         if negs:
             self.neg = np.ascontiguousarray(np.array(negs, np.uint32))
@@ -226,6 +232,7 @@ class ProgramBatch:
                            ("m_shared", np.uint32), ("m_global", np.uint32), ("perm", np.uint64),
                            ("perm_len", np.uint32), ("existing_mask", np.uint32),
                            ("n_loops", np.uint32), ("loops", np.uint64), ("iter_coef", np.uint64),
+                           ("n_slots", np.uint32), ("slot_pos", np.uint64),
                            ("n_neg", np.uint32), ("neg", np.uint64)],
                           align=True)
 
@@ -233,7 +240,7 @@ class ProgramBatch:
         assert self.PROG_DTYPE.itemsize == C.sizeof(gr_program)
         n = len(progs)
         S = np.array([p.op.shape[0] for p in progs], np.int64)
-        nsl = S - 1
+        nsl = np.array([len(p.slot_level) for p in progs], np.int64)
         s_off = np.concatenate([[0], np.cumsum(S)])
         k_off = np.concatenate([[0], np.cumsum(nsl)])
         st = np.zeros(int(s_off[-1]), self.STMT_DTYPE)
@@ -278,6 +285,15 @@ class ProgramBatch:
                 [p.iter_coef if c else np.zeros(len(p.op), np.uint32) for p, c in zip(progs, has_coef)]
             ).astype(np.uint32))
             pa["iter_coef"] = np.where(has_coef, self.coef.ctypes.data + 4 * s_off[:-1], 0)
+        has_pos = np.array([getattr(p, "slot_pos", None) is not None for p in progs])
+        if has_pos.any():
+            self.pos_arr = np.ascontiguousarray(np.concatenate(
+                [np.asarray(p.slot_pos, np.uint8) if h else np.zeros(0, np.uint8) for p, h in zip(progs, has_pos)]
+                + [np.zeros(1, np.uint8)]))
+            pos_len = np.array([len(p.slot_level) if h else 0 for p, h in zip(progs, has_pos)], np.int64)
+            p_off2 = np.concatenate([[0], np.cumsum(pos_len)])
+            pa["n_slots"] = np.where(has_pos, nsl, 0)
+            pa["slot_pos"] = np.where(has_pos, self.pos_arr.ctypes.data + p_off2[:-1], 0)
         nneg = np.array([len(getattr(p, "neg_clauses", ()) or ()) for p in progs], np.int64)
         if nneg.any():
             n_off = np.concatenate([[0], np.cumsum(nneg)])

@@ -124,7 +124,15 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
         return fail(GR_EINVAL, "program %u: threads %u outside 1..%d", idx, l.threads, GR_MAX_THREADS);
     if (p->m_shared > GR_MAX_WORDS || p->m_global > GR_MAX_WORDS)
         return fail(GR_EINVAL, "program %u: array size above %d words", idx, GR_MAX_WORDS);
-    const uint32_t n = p->n_stmts - 1;
+    if (p->n_slots > GR_MAX_SLOTS) return fail(GR_EINVAL, "program %u: more than %d slots", idx, GR_MAX_SLOTS);
+    if (!p->slot_pos && p->n_slots && p->n_slots != p->n_stmts - 1)
+        return fail(GR_EINVAL, "program %u: %u slots without slot_pos (one per place needs %u)", idx, p->n_slots,
+                    p->n_stmts - 1);
+    if (p->slot_pos && !p->n_slots) return fail(GR_EINVAL, "program %u: slot_pos needs n_slots", idx);
+    const uint32_t n = slots_of(*p);
+    for (uint32_t k = 0; p->slot_pos && k < n; ++k)
+        if (p->slot_pos[k] + 1u >= p->n_stmts)
+            return fail(GR_EINVAL, "program %u slot %u: place %u is not between two statements", idx, k, p->slot_pos[k]);
     for (uint32_t s = 0; s < p->n_stmts; ++s) {
         const gr_stmt &st = p->stmts[s];
         if (st.op > GR_W || st.space > GR_GLOBAL || st.kind > GR_PERM)
@@ -353,13 +361,13 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     for (uint32_t p = lo; p < hi; ++p) {
         const gr_program &P = progs[p];
         DevProg &D = dp[p];
-        const uint32_t nsl = P.n_stmts - 1;
+        const uint32_t nsl = slots_of(P);
         // executed statement instances: identity without loops
         uint8_t st_of[GR_MAX_STMTS], ctr_of[GR_MAX_STMTS];
         uint32_t S = P.n_stmts;
+        D.general = (P.n_loops || P.slot_pos) ? 1u : 0u;
         if (P.n_loops) {
             S = exec_order(P, st_of, ctr_of, GR_MAX_STMTS);
-            D.looped = 1;
         } else {
             for (uint32_t s = 0; s < S; ++s) {
                 st_of[s] = (uint8_t)s;
@@ -386,9 +394,14 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             D.slot_gr[k] = P.slot_guard ? P.slot_guard[2 * k + 1] : 0;
             if (D.slot_gk[k]) D.guarded_slots |= 1u << k;
         }
+        // the slots whose barriers run before the next instance: those placed
+        // after the statement preceding it
         for (uint32_t s = 0; s + 1 < S; ++s) {
-            D.vslot[s] = (uint8_t)(st_of[s + 1] - 1u);  // the barrier before the next instance
-            if (P.slot_level[D.vslot[s]] == GR_GRID) D.vgrid_mask |= 1u << s;
+            const uint32_t place = st_of[s + 1] - 1u;
+            uint32_t m = 0;
+            for (uint32_t k = 0; k < nsl; ++k)
+                if ((P.slot_pos ? P.slot_pos[k] : k) == place) m |= 1u << k;
+            D.gapslots[s] = m;
         }
         for (uint32_t s = 0; s < S; ++s) {
             const gr_stmt &st = P.stmts[st_of[s]];
@@ -908,7 +921,7 @@ gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches, con
     gr_status s = validate_all(progs, launches, n);
     if (s != GR_OK) return s;
     for (uint32_t p = 0; p < n; ++p) {
-        const uint32_t nsl = progs[p].n_stmts - 1;
+        const uint32_t nsl = slots_of(progs[p]);
         if (nsl < 32 && (masks[p] >> nsl)) return fail(GR_EINVAL, "program %u: mask has bits beyond slot %u", p, nsl);
     }
     Workspace *ws;

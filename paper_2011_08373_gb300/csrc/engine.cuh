@@ -38,8 +38,8 @@ static_assert(sizeof(DevStmt) == 32, "DevStmt layout");
 
 // One program: header + executed statement instances + slots.  n_stmts counts
 // the instances (a loop body once per iteration); n_slots the program's slots.
-// Instance k and k+1 are separated by the barrier of slot vslot[k] (k without
-// loops).  16-byte aligned, fixed size.
+// Instances k and k+1 are separated by the barriers of the slots gapslots[k] (slot k without
+// loops and explicit places).  16-byte aligned, fixed size.
 struct DevProg {
     uint32_t n_stmts, n_slots, blocks, threads;
     uint32_t t_pad;        // threads rounded up to a multiple of 8
@@ -47,15 +47,15 @@ struct DevProg {
     int32_t mode;          // GR_MODE_*
     uint32_t existing, grid_mask, write_mask, shared_rows;
     uint32_t global_rows, guarded_slots;
-    uint32_t vgrid_mask;   // grid level of the gaps between executed instances
-    uint32_t looped;       // 1: instances differ from statements (counted loops)
+    uint32_t _r4;
+    uint32_t general;      // 1: counted loops or explicit slot places (gaps differ from slots)
     uint64_t trace_off;    // u16 elements from the scratch trace base; layout [S][B][t_pad]
     uint64_t segmask_off;  // element index of the program's [S][B] segment masks and ranges
     uint32_t weights[GR_MAX_SLOTS];
     uint16_t slot_gk[GR_MAX_SLOTS];
     uint16_t slot_gr[GR_MAX_SLOTS];
     uint8_t rep[32];       // lowest instance with the same array, map and guard
-    uint8_t vslot[32];     // slot whose barrier runs between instances k and k+1
+    uint32_t gapslots[32]; // slots whose barriers run between instances k and k+1
     uint32_t n_neg, _r3[3];
     uint32_t neg[GR_MAX_NEG];  // negative clauses given with the program
     DevStmt stmts[GR_MAX_STMTS];  // one per executed statement instance
@@ -126,6 +126,7 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx);
 // innermost loop); returns how many run, storing at most cap (counting stops
 // past cap).
 uint32_t exec_order(const gr_program &p, uint8_t *st, uint8_t *ctr, uint32_t cap);
+inline uint32_t slots_of(const gr_program &p) { return p.n_slots ? p.n_slots : p.n_stmts - 1; }
 inline uint32_t exec_count(const gr_program &p) {
     if (p.n_loops == 0) return p.n_stmts;
     uint8_t st[GR_MAX_STMTS], ctr[GR_MAX_STMTS];

@@ -37,9 +37,9 @@ struct MhsSmem {
     uint32_t nraw[kClauseCap]; // negative clauses after preprocessing (0 = dropped)
     uint32_t nhi[kClauseCap];
     uint32_t nlo[kClauseCap];
-    uint32_t w8[3][256];       // weight of each byte of the high part
+    uint32_t w8[4][256];       // weight of each byte of the high part
     uint32_t wlo[32];          // weight of each low assignment
-    uint32_t lb[26];           // sum of the k smallest high weights
+    uint32_t lb[GR_MAX_SLOTS + 2];  // sum of the k smallest high weights
     uint32_t wc[GR_MAX_SLOTS]; // compact weights
     uint32_t n_kept, n_negk, R, U, unsat;
 };
@@ -96,21 +96,22 @@ __device__ __forceinline__ uint32_t range_mask(uint32_t i, uint32_t j) {  // bit
     return hi & ~((1u << i) - 1u);
 }
 
-// Gaps between executed instances whose barrier is on under the slot mask:
-// gap k (between instances k and k+1) runs the barrier of slot vslot[k].
+// Gaps between executed instances where an enabled barrier (of the slots in
+// `mask`) runs: gap k (between instances k and k+1) runs the barriers of the
+// slots gapslots[k].  Without loops or explicit places gap k is slot k.
 __device__ __forceinline__ uint32_t gap_mask(const DevProg &P, uint32_t mask) {
-    if (!P.looped) return mask;
+    if (!P.general) return mask;
     uint32_t g = 0;
     for (uint32_t k = 0; k + 1 < P.n_stmts; ++k)
-        if ((mask >> P.vslot[k]) & 1u) g |= 1u << k;
+        if (P.gapslots[k] & mask) g |= 1u << k;
     return g;
 }
 
 // The slots whose barriers run in the gaps `gaps`.
 __device__ __forceinline__ uint32_t slots_of_gaps(const DevProg &P, uint32_t gaps) {
-    if (!P.looped) return gaps;
+    if (!P.general) return gaps;
     uint32_t m = 0;
-    for (uint32_t t = gaps; t; t &= t - 1u) m |= 1u << P.vslot[__ffs(t) - 1u];
+    for (uint32_t t = gaps; t; t &= t - 1u) m |= P.gapslots[__ffs(t) - 1u];
     return m;
 }
 
@@ -456,7 +457,7 @@ __device__ void prepare_check(Smem &sm, uint32_t mask) {
         sm.rows_inter[s] = 0;
         if (s < S) {
             sm.ph_intra[s] = phase_of(s, gaps, S);
-            sm.ph_inter[s] = phase_of(s, gaps & P.vgrid_mask, S);
+            sm.ph_inter[s] = phase_of(s, gap_mask(P, mask & P.grid_mask), S);
         } else {
             sm.ph_intra[s] = sm.ph_inter[s] = 0;
         }
@@ -533,14 +534,14 @@ __device__ void check_misc(Smem &sm, uint32_t mask) {
         sm.diverge = dv;
     }
     unsigned long long local = 0;
-    const uint32_t gaps = gap_mask(P, mask);
+    const uint32_t gaps = gap_mask(P, mask), grid_gaps = gap_mask(P, mask & P.grid_mask);
     for (uint32_t idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
         const uint32_t i = idx / S, j = idx - i * S;
         if (j < i) continue;
         const uint32_t rg = range_mask(i, j);
         const uint32_t t = tri_index(i, j, S);
         if ((gaps & rg) == 0) local += sm.npair[0][t];
-        if ((gaps & P.vgrid_mask & rg) == 0) local += sm.npair[1][t];
+        if ((grid_gaps & rg) == 0) local += sm.npair[1][t];
     }
     for (uint32_t o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xFFFFFFFFu, local, o);
     if ((threadIdx.x & 31u) == 0 && local) atomicAdd(&sm.pairs, local);
@@ -599,9 +600,9 @@ __device__ void check_blocks(Smem &sm, uint16_t *tab, uint32_t table_bytes, cons
 // ---------------------------------------------------------------------------
 
 struct BinomTable {
-    uint32_t v[25][25];
+    uint32_t v[GR_MAX_SLOTS + 1][GR_MAX_SLOTS + 1];  // C(n, k), n <= 32: at most C(32, 16) < 2^32
     constexpr BinomTable() : v() {
-        for (int n = 0; n < 25; ++n) {
+        for (int n = 0; n <= GR_MAX_SLOTS; ++n) {
             v[n][0] = 1;
             for (int k = 1; k <= n; ++k) v[n][k] = v[n - 1][k - 1] + (k <= n - 1 ? v[n - 1][k] : 0);
         }
@@ -738,7 +739,7 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
             if ((tid >> b) & 1u) v += mh.wc[b];
         mh.wlo[tid] = v;
     }
-    for (uint32_t e = tid; e < 3 * 256; e += nt) {
+    for (uint32_t e = tid; e < 4 * 256; e += nt) {
         const uint32_t q = e >> 8, byte = e & 255u;
         uint32_t v = 0;
         for (uint32_t b = 0; b < 8; ++b) {
@@ -780,7 +781,8 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
         if (start < end) {
             uint32_t h = unrank_colex(start, kh, rh);
             for (uint32_t idx = start; idx < end; ++idx) {
-                const uint32_t wh = mh.w8[0][h & 255u] + mh.w8[1][(h >> 8) & 255u] + mh.w8[2][(h >> 16) & 255u];
+                const uint32_t wh = mh.w8[0][h & 255u] + mh.w8[1][(h >> 8) & 255u] + mh.w8[2][(h >> 16) & 255u] +
+                                    mh.w8[3][h >> 24];
                 const uint64_t lw = local >> 32;
                 bool skip = (uint64_t)wh > lw || ((uint64_t)wh == lw && (h << L) > (uint32_t)local);
                 if (!skip) {

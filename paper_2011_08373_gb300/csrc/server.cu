@@ -38,14 +38,15 @@ using Clock = std::chrono::steady_clock;
 // A request's program, deep-copied so the caller may free its buffers.
 struct ProgramCopy {
     std::vector<gr_stmt> stmts;
-    std::vector<uint8_t> level;
+    std::vector<uint8_t> level, pos;
     std::vector<uint16_t> guard;
     std::vector<uint32_t> weight, perm, coef, neg;
     std::vector<gr_loop> loops;
     gr_program p;
     void take(const gr_program &src) {
-        const uint32_t n = src.n_stmts - 1;
+        const uint32_t n = slots_of(src);
         stmts.assign(src.stmts, src.stmts + src.n_stmts);
+        if (src.slot_pos) pos.assign(src.slot_pos, src.slot_pos + n);
         level.assign(src.slot_level, src.slot_level + n);
         if (src.slot_guard) guard.assign(src.slot_guard, src.slot_guard + 2 * n);
         if (src.slot_weight) weight.assign(src.slot_weight, src.slot_weight + n);
@@ -65,6 +66,7 @@ struct ProgramCopy {
         p.loops = loops.empty() ? nullptr : loops.data();
         p.iter_coef = coef.empty() ? nullptr : coef.data();
         p.neg = neg.empty() ? nullptr : neg.data();
+        p.slot_pos = pos.empty() ? nullptr : pos.data();
     }
 };
 

@@ -255,6 +255,7 @@ class Workload:
     inner_trips: tuple = (2, 3)
     iter_coefs: Dict[object, float] = field(default_factory=lambda: {0: 0.4, 1: 0.2, 2: 0.1, "T": 0.3})
     loop_weight_base: int = 10  # lw of the weight (gw*gb) + lw^ld
+    both_sites: bool = False    # a block and a grid candidate at every site (two slots per place)
     extra: dict = field(default_factory=dict)
 
 
@@ -302,6 +303,15 @@ WORKLOADS: Dict[str, Workload] = {
         n_stmts=12, space=SPACE_SHARED, m_words=1024,
         maps={"affine": 0.4, "strided": 0.3, "perm": 0.3}, p_write=0.4,
         guard_fraction=0.15, p_loop=1.0),
+    # 128 programs, 16 blocks x 256 threads, 16 statements over a 16,384-word
+    # global array with block-offset maps as in the inter-block workload, and
+    # at each of the 15 sites both a block candidate (weight 1) and a grid
+    # candidate (weight 13 = gw + lw^0 with the paper's gw = 12): 30 barrier
+    # variables per program
+    "sites128_16x256_s16": Workload(
+        name="sites128_16x256_s16", seed=6, n_programs=128, blocks=16, threads=256,
+        n_stmts=16, space=SPACE_GLOBAL, m_words=16384, maps={"affine": 1.0}, p_write=0.5,
+        guard_fraction=0.0, grid_weight=13, block_offset=True, p_halo=0.15, both_sites=True),
     # the large programs mixed into the serving stream: 128 blocks x 1,024
     # threads, 24 statements, 4,096-word shared array
     "large_128x1024_s24": Workload(
@@ -453,13 +463,21 @@ def generate_program(wl: Workload, p: int, **override) -> Program:
     # its loop depth is that statement's
     weights = [(wl.grid_weight - 1 if lv == LEVEL_GRID else 0) + wl.loop_weight_base ** depth[k + 1]
                for k, lv in enumerate(levels)]
+    slot_pos = None
+    if wl.both_sites:  # every place gets a block and a grid slot
+        slot_pos = [k for k in range(n) for _ in (0, 1)]
+        levels = [lv for _ in range(n) for lv in (LEVEL_BLOCK, LEVEL_GRID)]
+        sguard = [g for g in sguard for _ in (0, 1)]
+        weights = [(wl.grid_weight - 1 if lv == LEVEL_GRID else 0) + wl.loop_weight_base ** depth[slot_pos[k] + 1]
+                   for k, lv in enumerate(levels)]
+        n = len(slot_pos)
     existing = ((1 << n) - 1) if mode == MODE_REMOVE else 0
     return make_program(
         stmts, blocks=B, threads=T,
         m_shared=M if wl.space == SPACE_SHARED else 0,
         m_global=M if wl.space == SPACE_GLOBAL else 0,
         slot_level=levels, slot_guard=sguard, slot_weight=weights, perms=perms,
-        existing_mask=existing, mode=mode, loops=loops)
+        existing_mask=existing, mode=mode, loops=loops, slot_pos=slot_pos)
 
 
 def _choose(rng: SplitMix64, probs) -> int:

@@ -47,7 +47,7 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(gb.gr_stmt) == 24
     assert C.sizeof(gb.gr_witnesses) == 272
     assert C.sizeof(gb.gr_repair_result) == 2944
-    assert C.sizeof(gb.gr_program) == 104
+    assert C.sizeof(gb.gr_program) == 120
     assert C.sizeof(gb.gr_loop) == 12
 
 
@@ -174,10 +174,10 @@ def test_validation_accepts_loops(lib):
         gb.validate(_loop_prog(loops))
 
 
-# DevProg layout (bytes): n_stmts 0, n_slots 4, vgrid_mask 56, looped 60,
-# vslot 304..335, n_neg 336, neg 352..479, stmts 480 + 32*k (op 0, space 1,
-# kind 2, bm 8, gk 20, gr 22)
-DEVPROG_BYTES, STMT0 = 1280, 480
+# DevProg layout (bytes): n_stmts 0, n_slots 4, general 60, gapslots
+# 368..495, n_neg 496, neg 512..639, stmts 640 + 32*k (op 0, space 1, kind 2,
+# bm 8, gk 20, gr 22)
+DEVPROG_BYTES, STMT0, GAPS0, NEG0 = 1440, 640, 368, 496
 
 
 def _devprog(arena, i):
@@ -201,7 +201,6 @@ def test_packer_lays_out_executed_instances(lib):
         assert int(d[0:4].view(np.uint32)[0]) == len(order)
         assert int(d[4:8].view(np.uint32)[0]) == p.n_slots
         assert int(d[60:64].view(np.uint32)[0]) == (1 if p.loops else 0)
-        vgrid = 0
         for z, (s, ctr) in enumerate(order):
             st = d[STMT0 + 32 * z:STMT0 + 32 * z + 32]
             M = p.m_shared if p.space[s] == 0 else p.m_global
@@ -211,10 +210,7 @@ def test_packer_lays_out_executed_instances(lib):
             assert int(st[20:22].view(np.uint16)[0]) == p.guard_k[s]
             if z + 1 < len(order):
                 k = order[z + 1][0] - 1
-                assert d[304 + z] == k
-                if p.slot_level[k] == 1:
-                    vgrid |= 1 << z
-        assert int(d[56:60].view(np.uint32)[0]) == vgrid
+                assert int(d[GAPS0 + 4 * z:GAPS0 + 4 * z + 4].view(np.uint32)[0]) == 1 << k
 
 
 def test_expansion_items_cover_every_segment_once(lib):
@@ -255,6 +251,41 @@ def test_packer_copies_negative_clauses(lib):
     arena, _ = gb.pack(progs)
     for i, p in enumerate(progs):
         d = _devprog(arena, i)
-        n = int(d[336:340].view(np.uint32)[0])
+        n = int(d[NEG0:NEG0 + 4].view(np.uint32)[0])
         assert n == len(p.neg_clauses)
-        assert d[352:352 + 4 * n].view(np.uint32).tolist() == list(p.neg_clauses)
+        assert d[NEG0 + 16:NEG0 + 16 + 4 * n].view(np.uint32).tolist() == list(p.neg_clauses)
+
+
+def test_packer_places_slots(lib):
+    """Explicit slot places: the slots whose barriers run in each gap between
+    executed instances."""
+    import oracle
+    from _tiny import random_loop_program, random_program, with_sites
+
+    progs = [with_sites(random_program(s, s_min=3, s_max=8), s) for s in range(20)]
+    progs += [with_sites(random_loop_program(100 + s, s_min=3, s_max=6), s) for s in range(20)]
+    arena, _ = gb.pack(progs)
+    for i, p in enumerate(progs):
+        d = _devprog(arena, i)
+        order = oracle.unroll(p)
+        assert int(d[4:8].view(np.uint32)[0]) == p.n_slots
+        assert int(d[60:64].view(np.uint32)[0]) == 1
+        for z in range(len(order) - 1):
+            place = order[z + 1][0] - 1
+            want = sum(1 << k for k in range(p.n_slots) if int(p.slot_pos[k]) == place)
+            assert int(d[GAPS0 + 4 * z:GAPS0 + 4 * z + 4].view(np.uint32)[0]) == want
+
+
+@pytest.mark.parametrize("pos,msg", [([0, 7], "place"), ([0] * 33, "more than 32 slots")])
+def test_validation_rejects_bad_places(lib, pos, msg):
+    p = _prog()
+    n = len(pos)
+    p.slot_pos = np.array(pos, np.uint32)
+    p.slot_level = np.zeros(n, np.uint8)
+    p.slot_guard_k = np.zeros(n, np.uint16)
+    p.slot_guard_r = np.zeros(n, np.uint16)
+    p.slot_weight = np.ones(n, np.uint32)
+    p.existing_mask = 0
+    with pytest.raises(gb.GrError) as e:
+        gb.validate(p)
+    assert e.value.code == gb.EINVAL and msg in str(e.value)

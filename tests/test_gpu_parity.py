@@ -335,3 +335,90 @@ def test_negative_clauses_random(gb):
         wide, narrow = _wide(gb, progs, strategy=strategy)
         for w, n in zip(wide, got):
             _same_result(w, n)
+
+
+# --------------------------------------------------------------------------
+# Two barrier variables per site (slots with explicit places), up to 32 slots
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", GOLD["site_cases"], ids=[c["name"] for c in GOLD["site_cases"]])
+def test_site_cases(gb, case):
+    p = program_from_spec(case["program"])
+    for chk in case["checks"]:
+        got = gb.check(p, chk["mask"])
+        for key in ("intra", "inter", "diverge", "access_pairs"):
+            if key in chk:
+                assert got[key] == chk[key], (key, chk["mask"])
+    for exp in case["repairs"]:
+        for fn in (gb.repair, gb.repair_plain):
+            got = fn(p, mode=exp["mode"], grid_enabled=exp["grid_enabled"])
+            for key in ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses", "forbidden"):
+                assert got[key] == exp[key], (fn.__name__, key)
+
+
+def test_site_programs_match_oracle(gb):
+    from _tiny import random_loop_program, with_sites
+
+    progs = [with_sites(random_program(90000 + s, s_min=2, s_max=7, b_max=3, t_max=10, m_max=20), s)
+             for s in range(100)]
+    progs += [with_sites(random_loop_program(91000 + s, s_min=3, s_max=5, b_max=3, t_max=8, m_max=16), s)
+              for s in range(40)]
+    for strategy in (0, 1):
+        for grid_enabled in (True, False):
+            got = gb.repair_batch(progs, grid_enabled=grid_enabled, strategy=strategy)
+            for p, g in zip(progs, got):
+                _same_result(g, oracle.repair(p, grid_enabled=grid_enabled, strategy=strategy), p.slot_pos)
+    tiny = [p for p in progs if p.n_slots <= 8][:40]
+    ps, ms = [], []
+    for p in tiny:
+        for m in range(1 << p.n_slots):
+            ps.append(p)
+            ms.append(m)
+    for p, m, g in zip(ps, ms, gb.check_batch(ps, ms)):
+        assert g == oracle.check(p, m)
+    wide, narrow = _wide(gb, progs[:60])
+    for w, n in zip(wide, narrow):
+        _same_result(w, n)
+
+
+def test_solver_up_to_32_variables(gb):
+    pytest.importorskip("scipy.optimize")
+    from test_oracle_pins import milp_lowest_key
+
+    for seed in range(24):
+        rng = synth.SplitMix64(synth.program_seed(321, seed))
+        n = rng.randint(25, 32)
+        full = (1 << n) - 1
+        w = [rng.randint(1, 1 << rng.randint(0, 8)) for _ in range(n)]
+        pos = [rng.randint(1, full) & rng.randint(1, full) & rng.randint(1, full) or 1
+               for _ in range(rng.randint(1, 30))]
+        neg = [rng.randint(1, full) | rng.randint(1, full) for _ in range(rng.randint(0, 3))]
+        forced = rng.randint(0, full) & rng.randint(0, full) & rng.randint(0, full) & rng.randint(0, full)
+        forbidden = rng.randint(0, full) & rng.randint(0, full) & rng.randint(0, full) & ~forced
+        got = gb.solve(n, w, pos, neg, forced, forbidden)
+        assert got == milp_lowest_key(n, w, pos, neg, forced, forbidden), (seed, n)
+
+
+def test_sites_workload_reduced(gb):
+    """30 barrier variables per program (a block and a grid candidate at 15
+    sites): the check against the oracle, the final repair against the
+    lowest-key mask over the oracle's unconstrained witnesses (path
+    independence), solved by integer programming."""
+    pytest.importorskip("scipy.optimize")
+    from test_oracle_pins import milp_lowest_key
+
+    progs = synth.generate("sites128_16x256_s16", 12, blocks=3, threads=16, m_words=1024)
+    assert all(p.n_slots == 30 for p in progs)
+    got = gb.repair_batch(progs)
+    for p, g in zip(progs, got):
+        w0 = oracle.check(p, 0)
+        assert gb.check(p, 0) == w0
+        cls = oracle.clauses(p, w0)
+        div = oracle.check(p, (1 << p.n_slots) - 1)["diverge"]
+        want = milp_lowest_key(p.n_slots, [int(x) for x in p.slot_weight], cls, (), 0, div)
+        if want is None:
+            assert g["status"] == 1
+        else:
+            assert g["status"] == 0 and (g["mask"], g["weight"]) == want
+            assert set(g["clauses"]) <= set(cls)
+            assert oracle.check(p, g["mask"]) == gb.check(p, g["mask"])

@@ -293,6 +293,23 @@ def _milp_min(n, w, pos, neg, forced, forbidden, extra_zero=(), weight_eq=None):
     return np.rint(res.x).astype(int)
 
 
+def milp_lowest_key(n, w, pos, neg=(), forced=0, forbidden=0):
+    """The least (weight, mask) hitting set by integer programming: the minimum
+    weight, then the lowest mask among the sets of that weight (clear bits from
+    the top while a set of that weight stays feasible).  None if infeasible."""
+    x = _milp_min(n, w, pos, neg, forced, forbidden)
+    if x is None:
+        return None
+    wstar = int(np.dot(w, x))
+    zero, mask = [], 0
+    for k in reversed(range(n)):
+        if _milp_min(n, w, pos, neg, forced, forbidden, extra_zero=zero + [k], weight_eq=wstar) is not None:
+            zero.append(k)
+        else:
+            mask |= 1 << k
+    return mask, wstar
+
+
 @pytest.mark.parametrize("seed", range(40))
 def test_solve_matches_milp(seed):
     pytest.importorskip("scipy.optimize")
