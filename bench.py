@@ -99,11 +99,25 @@ def dist_env():
     return rank, world, local
 
 
+# the oracle's hitting set is brute force over 2^slots masks: beyond 24 slots
+# one solve takes minutes, so no bounded sample exists
+ORACLE_MAX_SLOTS = 24
+
+
+def _oracle_feasible(workload):
+    return synth.generate(workload, 1)[0].n_slots <= ORACLE_MAX_SLOTS
+
+
 def run_reference(args, rank, world):
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle
 
     if rank != 0:
+        return
+    if not _oracle_feasible(args.workload):
+        print(json.dumps({"impl": "reference", "unavailable": f"{args.workload} has more than "
+                          f"{ORACLE_MAX_SLOTS} slots: the oracle's brute-force hitting set over 2^slots "
+                          "masks has no bounded sample"}), flush=True)
         return
     cores = os.cpu_count() or 1
     wl = synth.WORKLOADS[args.workload]
@@ -138,6 +152,8 @@ def run_reference(args, rank, world):
 def cpu_baseline_leg(workload, n_sample):
     import oracle
 
+    if not _oracle_feasible(workload):
+        return None
     cores = os.cpu_count() or 1
     progs = synth.generate(workload, n_sample)
     oracle.repair_batch(progs[:2], n_threads=cores)  # build + warm
