@@ -326,7 +326,10 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
         uint4 held0 = make_uint4(0, 0, 0, 0), held1 = held0;
         for (uint32_t pass = 0; pass < 2; ++pass) {
             for (uint32_t base = 0; base < n_segs; base += kSegCap) {
-                if (pass == 0 || !one_batch) {
+                // with every remaining chunk in the tile each segment meets it
+                // (a segment with no active thread has none in any chunk), so
+                // the identity tile needs no segment list
+                if (!identity && (pass == 0 || !one_batch)) {
                     // segments of this batch whose chunks meet the tile
                     __syncthreads();
                     if (threadIdx.x == 0) sm.n_seg_list = 0;
@@ -350,13 +353,22 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                     }
                 }
                 __syncthreads();
-                const uint32_t units = sm.n_seg_list * nv;
+                const uint32_t n_list = identity ? min(n_segs - base, kSegCap) : sm.n_seg_list;
+                const uint32_t units = n_list * nv;
                 const bool hold = one_batch && units <= 2u * blockDim.x;
                 uint32_t slot_i = 0;
                 for (uint32_t u = threadIdx.x; u < units; u += blockDim.x, ++slot_i) {
-                    const uint32_t code = sm.seg_list[u / nv];
                     const uint32_t v = u % nv;
-                    const uint32_t st = code >> 16, blk = blk_lo + (code & 0xFFFFu);
+                    uint32_t st, blk;
+                    if (identity) {
+                        const uint32_t g = base + u / nv, r = g / nb;
+                        st = sm.row_list[r];
+                        blk = blk_lo + (g - r * nb);
+                    } else {
+                        const uint32_t code = sm.seg_list[u / nv];
+                        st = code >> 16;
+                        blk = blk_lo + (code & 0xFFFFu);
+                    }
                     const uint32_t act8 = (sm.act[st][v >> 2] >> ((v & 3u) * 8u)) & 0xFFu;
                     if (!act8) continue;
                     uint32_t pend = 0;
