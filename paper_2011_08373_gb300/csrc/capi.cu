@@ -88,6 +88,32 @@ uint32_t exec_order(const gr_program &p, uint8_t *st, uint8_t *ctr, uint32_t cap
     return n;
 }
 
+// Blocks see one access pattern when, in each array, either no statement's
+// address depends on the block (c = 0 mod M) or every statement is affine /
+// strided with the same c mod M: block b then shifts all addresses of the
+// array by the same c*b mod M, a bijection that keeps every equality between
+// two addresses.  Guards depend on tid only, so block b's same-block
+// witnesses are block 0's.
+bool blocks_alike(const gr_program &p) {
+    for (uint32_t sp = 0; sp < 2; ++sp) {
+        const uint32_t M = sp == GR_SHARED ? p.m_shared : p.m_global;
+        bool any = false, perm_any = false, all_zero = true, same = true;
+        uint32_t c0 = 0;
+        for (uint32_t s = 0; s < p.n_stmts; ++s) {
+            const gr_stmt &st = p.stmts[s];
+            if (st.space != sp) continue;
+            const uint32_t cm = st.c % M;
+            if (!any) c0 = cm;
+            any = true;
+            perm_any |= st.kind == GR_PERM;
+            all_zero &= cm == 0;
+            same &= cm == c0;
+        }
+        if (any && !all_zero && (perm_any || !same)) return false;
+    }
+    return true;
+}
+
 gr_status validate_loops(const gr_program *p, uint32_t idx) {
     if (p->n_loops == 0) return GR_OK;
     if (p->n_loops > GR_MAX_LOOPS) return fail(GR_EINVAL, "program %u: more than %d loops", idx, GR_MAX_LOOPS);
@@ -422,6 +448,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             if (st.space == GR_SHARED) D.shared_rows |= 1u << s;
             else D.global_rows |= 1u << s;
         }
+        D.blk_invariant = blocks_alike(P) ? 1u : 0u;
         // access-pattern classes: statements with the same array, map and
         // guard touch the same words from the same threads
         for (uint32_t s = 0; s < 32; ++s) D.rep[s] = (uint8_t)s;

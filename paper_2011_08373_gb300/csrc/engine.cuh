@@ -47,7 +47,7 @@ struct DevProg {
     int32_t mode;          // GR_MODE_*
     uint32_t existing, grid_mask, write_mask, shared_rows;
     uint32_t global_rows, guarded_slots;
-    uint32_t _r4;
+    uint32_t blk_invariant;  // 1: every block has the same same-block witnesses (see the packer)
     uint32_t general;      // 1: counted loops or explicit slot places (gaps differ from slots)
     uint64_t trace_off;    // u16 elements from the scratch trace base; layout [S][B][t_pad]
     uint64_t segmask_off;  // element index of the program's [S][B] segment masks and ranges
@@ -127,6 +127,8 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx);
 // past cap).
 uint32_t exec_order(const gr_program &p, uint8_t *st, uint8_t *ctr, uint32_t cap);
 inline uint32_t slots_of(const gr_program &p) { return p.n_slots ? p.n_slots : p.n_stmts - 1; }
+// Every block of the launch has the same same-block witnesses (a validated program).
+bool blocks_alike(const gr_program &p);
 inline uint32_t exec_count(const gr_program &p) {
     if (p.n_loops == 0) return p.n_stmts;
     uint8_t st[GR_MAX_STMTS], ctr[GR_MAX_STMTS];

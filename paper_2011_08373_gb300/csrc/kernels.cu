@@ -560,11 +560,15 @@ __device__ void check_misc(Smem &sm, uint32_t mask) {
 }
 
 // Same-block passes for blocks [b0, b1) and, if requested, the cross-block pass.
+// When every block sees one access pattern (blk_invariant: see the packer)
+// the same-block witnesses of any block are block 0's, so only block 0 is
+// checked.
 __device__ void check_blocks(Smem &sm, uint16_t *tab, uint32_t table_bytes, const uint16_t *trace,
                              const uint64_t *segmask, const uint32_t *segrange, uint32_t b0, uint32_t b1,
                              bool inter) {
     const DevProg &P = sm.prog;
     const uint32_t B = P.blocks, S = P.n_stmts;
+    if (P.blk_invariant) b1 = b0 == 0 ? min(b1, 1u) : b0;  // uniform
     const bool cached = b1 - b0 <= 64;
     if (cached) {  // chunk masks of every block of the range, OR-reduced in parallel
         __syncthreads();

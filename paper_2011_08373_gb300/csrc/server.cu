@@ -70,9 +70,10 @@ struct ProgramCopy {
     }
 };
 
-// Programs with at least this many blocks take the wide lane (one CTA per
-// block per check, the loop as a device-side graph); the rest share the
-// persistent launch, one CTA per program.
+// Programs with at least this many blocks whose blocks differ (see
+// blocks_alike) take the wide lane (one CTA per block per check, the loop as
+// a device-side graph); the rest share the persistent launch, one CTA per
+// program, which checks a single block when all blocks are alike.
 constexpr uint32_t kWideMinBlocks = 32;
 
 struct Request {
@@ -82,7 +83,8 @@ struct Request {
     int32_t mode;
     size_t arena_bytes, scratch_bytes;
     Clock::time_point t_submit;
-    bool wide() const { return launch.blocks >= kWideMinBlocks; }
+    bool spread = false;  // set at submit: many blocks that differ
+    bool wide() const { return spread; }
 };
 
 struct Done {
@@ -336,6 +338,7 @@ gr_status gr_server_submit(gr_server *s, const gr_program *prog, gr_launch launc
     r.launch = launch;
     r.mode = mode;
     footprint(*prog, launch, &r.arena_bytes, &r.scratch_bytes);
+    r.spread = launch.blocks >= kWideMinBlocks && !blocks_alike(*prog);
     {
         std::lock_guard<std::mutex> g(s->mu);
         if (s->error != GR_OK) return fail(s->error, "server failed: %s", s->error_text);

@@ -10,7 +10,7 @@ from paper_2011_08373_gb300.synth import (
 def random_program(seed, *, s_max=5, b_max=3, t_max=8, m_max=16, spaces=(0, 1),
                    kinds=(MAP_AFFINE, MAP_STRIDED, MAP_PERM), a_max=5, c_max=8,
                    guard_ks=(0, 0, 1, 2, 3, 4), p_write=0.5, weight_max=5, s_min=1,
-                   t_min=1, b_min=1):
+                   t_min=1, b_min=1, shared_c=False):
     rng = SplitMix64(program_seed(0xC0FFEE, seed))
     S = rng.randint(s_min, s_max)
     B = rng.randint(b_min, b_max)
@@ -26,7 +26,7 @@ def random_program(seed, *, s_max=5, b_max=3, t_max=8, m_max=16, spaces=(0, 1),
         gr = rng.randint(0, gk - 1) if gk > 0 else 0
         st = {"op": 1 if rng.bernoulli(p_write) else 0, "space": space, "kind": kind,
               "a": rng.randint(0, a_max), "b": rng.randint(0, 3 * m_max),
-              "c": rng.randint(0, c_max) if space == SPACE_GLOBAL else 0, "guard": (gk, gr)}
+              "c": rng.randint(0, c_max) if (space == SPACE_GLOBAL or shared_c) else 0, "guard": (gk, gr)}
         if kind == MAP_PERM:
             st["perm"] = len(perms)
             perms.append(rng.permutation(M))

@@ -289,3 +289,34 @@ def test_validation_rejects_bad_places(lib, pos, msg):
     with pytest.raises(gb.GrError) as e:
         gb.validate(p)
     assert e.value.code == gb.EINVAL and msg in str(e.value)
+
+
+def test_block_invariance_flag_is_sound(lib):
+    """The packer marks a program block-invariant only when, for every pair of
+    statements of one array and every pair of threads, two addresses agree in
+    block b exactly when they agree in block 0 (so block 0's same-block
+    witnesses are every block's)."""
+    from _tiny import random_program
+
+    flagged = 0
+    progs = [random_program(s, s_min=2, s_max=5, b_min=2, b_max=4, t_max=6, m_max=12, c_max=3) for s in range(300)]
+    arena, _ = gb.pack(progs)
+    for i, p in enumerate(progs):
+        inv = int(_devprog(arena, i)[56:60].view(np.uint32)[0])
+        if not inv:
+            continue
+        flagged += 1
+        def addr(s, t, b):
+            M = p.m_shared if p.space[s] == 0 else p.m_global
+            if p.kind[s] == 2:
+                return int(p.perm[int(p.perm_off[s]) + (t + int(p.c[s]) * b + int(p.b[s])) % M])
+            return (int(p.a[s]) * t + int(p.c[s]) * b + int(p.b[s])) % M
+        for s1 in range(p.n_stmts):
+            for s2 in range(p.n_stmts):
+                if p.space[s1] != p.space[s2]:
+                    continue
+                for b in range(1, p.blocks):
+                    for t1 in range(p.threads):
+                        for t2 in range(p.threads):
+                            assert (addr(s1, t1, b) == addr(s2, t2, b)) == (addr(s1, t1, 0) == addr(s2, t2, 0))
+    assert flagged >= 50

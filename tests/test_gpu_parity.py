@@ -422,3 +422,26 @@ def test_sites_workload_reduced(gb):
             assert g["status"] == 0 and (g["mask"], g["weight"]) == want
             assert set(g["clauses"]) <= set(cls)
             assert oracle.check(p, g["mask"]) == gb.check(p, g["mask"])
+
+
+def test_blocks_that_differ(gb):
+    """Block offsets on shared and global arrays (blocks see different access
+    patterns, or the same one up to a shift): every block's same-block
+    witnesses must be found, whichever blocks the engine checks."""
+    progs = [random_program(95000 + s, s_min=2, s_max=7, b_min=2, b_max=5, t_max=10, m_max=24, c_max=6,
+                            shared_c=True) for s in range(160)]
+    got = gb.repair_batch(progs)
+    for p, g in zip(progs, got):
+        _same_result(g, oracle.repair(p))
+    ps, ms = [], []
+    for p in progs[:40]:
+        for m in (0, (1 << p.n_slots) - 1, 1 if p.n_slots else 0):
+            ps.append(p)
+            ms.append(m)
+    for p, m, g in zip(ps, ms, gb.check_batch(ps, ms)):
+        assert g == oracle.check(p, m)
+    wide, narrow = _wide(gb, progs[:60])
+    for w, n in zip(wide, narrow):
+        _same_result(w, n)
+    for p in progs[:8]:
+        _same_result(gb.repair_plain(p), oracle.repair(p))

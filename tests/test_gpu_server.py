@@ -94,9 +94,11 @@ def test_server_rejects_oversized_and_unknown(gb):
 
 
 def test_wide_lane_requests_match_oracle(gb):
-    """Programs with many blocks take the server's wide lane; interleaved with
-    small ones, every result equals the oracle's."""
+    """Programs with many blocks that differ take the server's wide lane;
+    interleaved with small ones, every result equals the oracle's."""
     wide = synth.generate("interblock256_64x256_s16", 6, blocks=40, threads=16, m_words=2048)
+    for p in wide:  # one statement's block offset differs: blocks see different patterns
+        p.c[0] = p.c[0] + 1
     small = [p for p in synth.generate("uneven4096_mixed", 200, start=500) if p.blocks * p.threads <= 400][:12]
     progs = [x for pair in zip(small, wide) for x in pair] + small[len(wide):]
     with gb.Server(mem_budget_bytes=512 << 20, n_slots=3) as srv:
