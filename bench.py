@@ -165,6 +165,22 @@ def cpu_baseline_leg(workload, n_sample):
                       f"brute-force hitting set, {cores} threads, {dt:.1f} s"}
 
 
+# DevProg fields of a packed arena (bytes): n_stmts 0, blocks 8, threads 12,
+# shared_rows 44, global_rows 48, blocks alike 56; records of 1,440 bytes
+DEVPROG_BYTES = 1440
+
+
+def check_bytes(arena, i):
+    """Trace bytes one check of packed program i reads."""
+    off = int(arena[16:24].view(np.uint64)[0]) + DEVPROG_BYTES * i
+    f = arena[off:off + 64].view(np.uint32)
+    n_inst, blocks, threads = int(f[0]), int(f[2]), int(f[3])
+    shared, glob, alike = int(f[11]), int(f[12]), int(f[14])
+    if alike and blocks > 1:
+        return (bin(shared).count("1") + bin(glob).count("1") * blocks) * threads * 2
+    return n_inst * blocks * threads * 2
+
+
 def shard(workload, n, rank):
     """Rank r repairs programs [r*n, (r+1)*n) of the workload: disjoint
     batches, no data exchanged between ranks."""
@@ -240,9 +256,11 @@ def run_ours(args, rank, world, local):
     value, _ = whole_job(n, t_step, 1)
     value *= world
 
-    # algorithmic bytes of the repair kernel: each check reads the program's
-    # trace once (S x B x T u16 addresses); the arena and results once per launch
-    trace_bytes = sum(int(p.n_stmts) * p.blocks * p.threads * 2 * int(r["iters"]) for p, r in zip(progs, res))
+    # algorithmic bytes of the repair kernel: each check reads the traces it
+    # needs once (u16 addresses of T threads per (statement instance, block):
+    # every block, or block 0 of the shared-array statements when the
+    # program's blocks are alike); the arena and results once per launch
+    trace_bytes = sum(check_bytes(batch.host_arena, i) * int(r["iters"]) for i, r in enumerate(res))
     launch_bytes = trace_bytes + batch.arena_bytes + n * binding.RESULT_DTYPE.itemsize
     t_rep = statistics.mean(repair_ms) / 1000.0
     peak, peak_kind = _peaks()

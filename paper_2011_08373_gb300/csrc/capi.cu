@@ -227,9 +227,11 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     L.order_off = align_to(L.progs_off + (size_t)n * sizeof(DevProg), 16);
     L.segbase_off = align_to(L.order_off + (size_t)n * 4, 16);
     L.items_off = align_to(L.segbase_off + (size_t)(n + 1) * 8, 16);
-    L.n_items = 0;
-    for (uint32_t p = 0; p < n; ++p)
-        L.n_items += ((uint64_t)exec_count(progs[p]) * ls[p].blocks + kItemSegs - 1) / kItemSegs;
+    L.n_items = 0;  // room for either item layout of each program (see pack_into)
+    for (uint32_t p = 0; p < n; ++p) {
+        const uint64_t x = exec_count(progs[p]);
+        L.n_items += (x * ls[p].blocks + kItemSegs - 1) / kItemSegs + x + 1;
+    }
     L.perm_off = align_to(L.items_off + (size_t)L.n_items * 16, 16);
     L.trace_elem.resize(n);
     L.segmask_elem.resize(n);
@@ -480,19 +482,36 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     segbase[n] = L.n_segments;
     std::iota(order, order + n, 0u);
     std::stable_sort(order, order + n, [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
-    // expansion items: runs of up to kItemSegs segments, largest programs first
+    // expansion items, largest programs first: runs of up to kItemSegs
+    // segments (kind 0); for a program whose blocks are alike the same-block
+    // passes read block 0 only and only global statements have a cross-block
+    // pass, so one item (kind 1) expands block 0 of its shared-array
+    // statements and kind-0 items cover the global statements' segments
     uint32_t *items = reinterpret_cast<uint32_t *>(arena + L.items_off);
     uint64_t k = 0;
+    auto emit = [&](uint32_t p, uint32_t lo, uint32_t hi, uint32_t kind) {
+        items[4 * k] = p;
+        items[4 * k + 1] = lo;
+        items[4 * k + 2] = hi;
+        items[4 * k + 3] = kind;
+        ++k;
+    };
     for (uint32_t i = 0; i < n; ++i) {
         const uint32_t p = order[i];
+        const DevProg &D = dp[p];
         const uint32_t segs = (uint32_t)(segbase[p + 1] - segbase[p]);
-        for (uint32_t lo = 0; lo < segs; lo += kItemSegs, ++k) {
-            items[4 * k] = p;
-            items[4 * k + 1] = lo;
-            items[4 * k + 2] = std::min(segs, lo + kItemSegs);
-            items[4 * k + 3] = 0;
+        if (D.blk_invariant && D.blocks > 1) {
+            if (D.shared_rows) emit(p, 0, D.n_stmts, 1u);
+            for (uint32_t s = 0; s < D.n_stmts; ++s) {
+                if (!((D.global_rows >> s) & 1u)) continue;
+                for (uint32_t lo = s * D.blocks; lo < (s + 1) * D.blocks; lo += kItemSegs)
+                    emit(p, lo, std::min((s + 1) * D.blocks, lo + kItemSegs), 0u);
+            }
+        } else {
+            for (uint32_t lo = 0; lo < segs; lo += kItemSegs) emit(p, lo, std::min(segs, lo + kItemSegs), 0u);
         }
     }
+    H->n_items = k;
 }
 
 }  // namespace gr

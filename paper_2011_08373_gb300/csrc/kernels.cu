@@ -1146,8 +1146,9 @@ __device__ __forceinline__ ArenaView view(const uint8_t *arena) {
 
 // K0: CTAs take work items (runs of up to kItemSegs (statement, block)
 // segments of one program, largest programs first, so that a few large
-// programs spread over many CTAs and many small ones share them); one warp
-// per segment of t_pad threads.  Writes the u16 address trace, and per
+// programs spread over many CTAs and many small ones share them; or block 0
+// of a program's shared-array statements when its blocks are alike); one
+// warp per segment of t_pad threads.  Writes the u16 address trace, and per
 // segment the mask of 1,024-word chunks and the [min, max] address of its
 // active accesses (min > max when none is active).
 __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ arena, uint8_t *__restrict__ scratch) {
@@ -1173,7 +1174,11 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
         }
         __syncthreads();
         const uint32_t B = hdr[0], T = hdr[1], tpad = hdr[2];
-        for (uint32_t seg = it.y + warp; seg < it.z; seg += nwarps) {
+        // kind 0: segments it.y..it.z-1; kind 1: block 0 of the shared-array
+        // statements it.y..it.z-1 (blocks alike: no other block is read)
+        for (uint32_t u = it.y + warp; u < it.z; u += nwarps) {
+            if (it.w == 1u && st_sh[u].space != GR_SHARED) continue;
+            const uint32_t seg = it.w == 1u ? u * B : u;
             const uint32_t s = seg / B, blk = seg - s * B;
             const DevStmt &st = st_sh[s];
             const uint32_t M = st.m;

@@ -215,11 +215,14 @@ def test_packer_lays_out_executed_instances(lib):
 
 def test_expansion_items_cover_every_segment_once(lib):
     """The packer's trace-expansion work items: runs of at most 64 (statement,
-    block) segments of one program, together covering each program's
-    segments exactly once, larger programs first."""
-    from _tiny import random_loop_program
+    block) segments of one program (kind 0), or block 0 of a program's
+    shared-array statements when its blocks are alike (kind 1), together
+    covering each segment a check reads exactly once, larger programs first."""
+    import oracle
+    from _tiny import random_loop_program, random_program
 
-    progs = synth.generate("uneven4096_mixed", 40) + [random_loop_program(s, s_min=3, m_max=40) for s in range(10)]
+    progs = synth.generate("uneven4096_mixed", 30) + [random_loop_program(s, s_min=3, m_max=40) for s in range(10)]
+    progs += [random_program(50 + s, s_min=2, s_max=6, b_min=2, b_max=5, c_max=3, shared_c=True) for s in range(20)]
     arena, _ = gb.pack(progs)
     h = arena[:128].view(np.uint64)
     segbase_off, items_off, n_items = int(h[4]), int(h[12]), int(h[13])
@@ -228,12 +231,27 @@ def test_expansion_items_cover_every_segment_once(lib):
     items = arena[items_off:items_off + 16 * n_items].view(np.uint32).reshape(-1, 4)
     covered = [np.zeros(int(segbase[p + 1] - segbase[p]), np.int64) for p in range(n)]
     order = []
-    for p, lo, hi, _ in items.tolist():
-        assert 0 < hi - lo <= 64
-        covered[p][lo:hi] += 1
+    for p, lo, hi, kind in items.tolist():
+        B = progs[p].blocks
+        if kind == 1:
+            for x, (s, _) in enumerate(oracle.unroll(progs[p])):
+                if lo <= x < hi and progs[p].space[s] == 0:
+                    covered[p][x * B] += 1
+        else:
+            assert 0 < hi - lo <= 64
+            covered[p][lo:hi] += 1
         if not order or order[-1] != p:
             order.append(p)
-    assert all((c == 1).all() for c in covered)
+    alike_seen = 0
+    for p in range(n):
+        alike = int(_devprog(arena, p)[56:60].view(np.uint32)[0]) and progs[p].blocks > 1
+        alike_seen += bool(alike)
+        B = progs[p].blocks
+        for x, (s, _) in enumerate(oracle.unroll(progs[p])):
+            for b in range(B):
+                need = not alike or progs[p].space[s] == 1 or b == 0
+                assert covered[p][x * B + b] == (1 if need else 0), (p, x, b)
+    assert alike_seen > 10
     assert sorted(order) == list(range(n))
     cost = [int(segbase[p + 1] - segbase[p]) * ((progs[p].threads + 7) // 8 * 8) for p in order]
     assert cost == sorted(cost, reverse=True)
