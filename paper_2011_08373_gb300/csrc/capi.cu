@@ -139,7 +139,34 @@ gr_status validate_loops(const gr_program *p, uint32_t idx) {
     return GR_OK;
 }
 
-gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
+// Whether the M entries of tbl are a permutation of 0..M-1 (M values below M
+// marking M distinct entries); dst (may be NULL) receives them as u16.
+bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst) {
+    uint8_t mark[GR_MAX_WORDS];
+    memset(mark, 0, M);
+    uint32_t bad = 0;
+    if (dst) {
+        for (uint32_t i = 0; i < M; ++i) {
+            const uint32_t v = tbl[i];
+            bad |= v >= M;
+            mark[v < M ? v : 0u] = 1;
+            dst[i] = (uint16_t)v;
+        }
+    } else {
+        for (uint32_t i = 0; i < M; ++i) {
+            const uint32_t v = tbl[i];
+            bad |= v >= M;
+            mark[v < M ? v : 0u] = 1;
+        }
+    }
+    uint32_t filled = 0;
+    for (uint32_t i = 0; i < M; ++i) filled += mark[i];
+    return !bad && filled == M;
+}
+
+// tables == false leaves the permutation-table check to pack_into, which
+// does it while converting the tables.
+gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx, bool tables) {
     if (!p) return fail(GR_EINVAL, "program %u: NULL", idx);
     if (p->n_stmts < 1 || p->n_stmts > GR_MAX_STMTS)
         return fail(GR_EINVAL, "program %u: n_stmts %u outside 1..%d", idx, p->n_stmts, GR_MAX_STMTS);
@@ -171,19 +198,8 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx) {
             if (!p->perm) return fail(GR_EINVAL, "program %u stmt %u: permutation map without perm", idx, s);
             if ((uint64_t)st.perm_off + M > p->perm_len)
                 return fail(GR_EINVAL, "program %u stmt %u: perm_off + M beyond perm_len", idx, s);
-            // a permutation: M values below M marking M distinct entries
-            uint8_t mark[GR_MAX_WORDS];
-            memset(mark, 0, M);
-            const uint32_t *tbl = p->perm + st.perm_off;
-            uint32_t bad = 0;
-            for (uint32_t i = 0; i < M; ++i) {
-                const uint32_t v = tbl[i];
-                bad |= v >= M;
-                mark[v < M ? v : 0u] = 1;
-            }
-            uint32_t filled = 0;
-            for (uint32_t i = 0; i < M; ++i) filled += mark[i];
-            if (bad || filled != M) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
+            if (tables && !table_to_u16(p->perm + st.perm_off, M, nullptr))
+                return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
         }
     }
     if (n > 0 && !p->slot_level) return fail(GR_EINVAL, "program %u: slot_level is NULL", idx);
@@ -331,7 +347,7 @@ void parallel_over(uint32_t n, F body) {
     HostPool::get().run(n, body);
 }
 
-gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n) {
+gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n, bool tables = true) {
     if (n == 0) return fail(GR_EINVAL, "no programs");
     if (!progs || !ls) return fail(GR_EINVAL, "progs or launches is NULL");
     // the first invalid program (lowest index) is reported, as in a serial scan
@@ -341,7 +357,7 @@ gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n)
     gr_status code = GR_OK;
     parallel_over(n, [&](uint32_t lo, uint32_t hi) {
         for (uint32_t p = lo; p < hi && p < first_bad.load(); ++p) {
-            gr_status s = validate_one(&progs[p], ls[p], p);
+            gr_status s = validate_one(&progs[p], ls[p], p, tables);
             if (s != GR_OK) {
                 std::lock_guard<std::mutex> g(mu);
                 if (p < first_bad.load()) {
@@ -358,7 +374,7 @@ gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n)
 }
 
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
-               uint8_t *arena) {
+               uint8_t *arena, uint32_t *table_bad) {
     // zero everything but the permutation area, which is fully overwritten
     memset(arena, 0, L.perm_off);
     ArenaHeader *H = reinterpret_cast<ArenaHeader *>(arena);
@@ -465,9 +481,34 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
                 }
             }
         }
-        if (P.perm && P.perm_len) {  // validated: every used entry is below its table's M <= 65,536
+        if (P.perm && P.perm_len) {
+            // each permutation statement's table as u16 (checked here when the
+            // caller left it unchecked); entries no statement uses are zeroed
             uint16_t *dst = perm + L.perm_base[p];
-            for (uint32_t i = 0; i < P.perm_len; ++i) dst[i] = (uint16_t)P.perm[i];
+            uint32_t lo[GR_MAX_STMTS], hi[GR_MAX_STMTS], ns = 0;
+            for (uint32_t s = 0; s < P.n_stmts; ++s) {
+                const gr_stmt &st = P.stmts[s];
+                if (st.kind != GR_PERM) continue;
+                const uint32_t M = st.space == GR_SHARED ? P.m_shared : P.m_global;
+                uint32_t at = ns++;
+                while (at > 0 && lo[at - 1] > st.perm_off) {
+                    lo[at] = lo[at - 1];
+                    hi[at] = hi[at - 1];
+                    --at;
+                }
+                lo[at] = st.perm_off;
+                hi[at] = st.perm_off + M;
+                if (!table_to_u16(P.perm + st.perm_off, M, dst + st.perm_off) && table_bad) {
+                    uint32_t cur = table_bad[p];
+                    if (s < cur) table_bad[p] = s;
+                }
+            }
+            uint32_t cur = 0;
+            for (uint32_t k = 0; k < ns; ++k) {
+                if (lo[k] > cur) memset(dst + cur, 0, (size_t)(lo[k] - cur) * 2);
+                cur = std::max(cur, hi[k]);
+            }
+            if (cur < P.perm_len) memset(dst + cur, 0, (size_t)(P.perm_len - cur) * 2);
         }
         segbase[p] = L.segmask_elem[p];
         cost[p] = (uint64_t)S * ls[p].blocks * t_pad_of(ls[p].threads);
@@ -700,7 +741,13 @@ gr_status upload_batch(Workspace &ws, const gr_program *progs, const gr_launch *
     }
     // the previous call on this workspace may still be reading the staging buffer
     GR_CUDA(cudaStreamSynchronize(st));
-    pack_into(progs, ls, modes, n, L, ws.host_arena);
+    // the callers validated everything but the permutation tables, which are
+    // checked while they are converted; the lowest bad program is reported
+    // before any device work, as a full validation would
+    std::vector<uint32_t> bad(n, 0xFFFFFFFFu);
+    pack_into(progs, ls, modes, n, L, ws.host_arena, bad.data());
+    for (uint32_t p = 0; p < n; ++p)
+        if (bad[p] != 0xFFFFFFFFu) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", p, bad[p]);
     gr_status s;
     if ((s = ws.arena.ensure(L.arena_bytes)) != GR_OK) return s;
     if ((s = ws.scratch.ensure(L.scratch_bytes)) != GR_OK) return s;
@@ -925,7 +972,7 @@ gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_mas
 gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, const int32_t *modes, uint32_t n,
                           const gr_options *opts, gr_repair_result *out, void *stream) {
     if (!out) return fail(GR_EINVAL, "out is NULL");
-    gr_status s = validate_all(progs, launches, n);
+    gr_status s = validate_all(progs, launches, n, false);
     if (s != GR_OK) return s;
     if ((s = validate_opts(opts)) != GR_OK) return s;
     if (modes)
@@ -964,7 +1011,7 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
 gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches, const uint32_t *masks, uint32_t n,
                          gr_witnesses *out, void *stream) {
     if (!out || !masks) return fail(GR_EINVAL, "out or masks is NULL");
-    gr_status s = validate_all(progs, launches, n);
+    gr_status s = validate_all(progs, launches, n, false);
     if (s != GR_OK) return s;
     for (uint32_t p = 0; p < n; ++p) {
         const uint32_t nsl = slots_of(progs[p]);
@@ -1005,7 +1052,7 @@ gr_status gr_repair(const gr_program *prog, gr_launch launch, int32_t mode, cons
 gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode, const gr_options *opts,
                           gr_repair_result *out) {
     if (!out) return fail(GR_EINVAL, "out is NULL");
-    gr_status s = validate_all(prog, &launch, 1);
+    gr_status s = validate_all(prog, &launch, 1, false);
     if (s != GR_OK) return s;
     if ((s = validate_opts(opts)) != GR_OK) return s;
     if (mode != GR_MODE_REPAIR && mode != GR_MODE_REMOVE) return fail(GR_EINVAL, "bad mode %d", mode);

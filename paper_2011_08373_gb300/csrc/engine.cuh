@@ -121,7 +121,7 @@ struct Layout {
     std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
 };
 gr_status fail(gr_status code, const char *fmt, ...);
-gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx);
+gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx, bool tables = true);
 // Statement instances in execution order (st: statement, ctr: counter of its
 // innermost loop); returns how many run, storing at most cap (counting stops
 // past cap).
@@ -136,8 +136,10 @@ inline uint32_t exec_count(const gr_program &p) {
 }
 size_t align_to(size_t x, size_t a);
 Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n);
+// table_bad (may be NULL): per program, the lowest statement whose permutation
+// table is not one (left as is when every table is)
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
-               uint8_t *arena);
+               uint8_t *arena, uint32_t *table_bad = nullptr);
 LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status);
 void set_last_error(const char *msg);
 

@@ -445,3 +445,30 @@ def test_blocks_that_differ(gb):
         _same_result(w, n)
     for p in progs[:8]:
         _same_result(gb.repair_plain(p), oracle.repair(p))
+
+
+def test_batch_rejects_bad_permutation_tables(gb):
+    """Host batch calls check permutation tables while packing them; the
+    lowest bad program is reported before any device work."""
+    good = synth.generate("batch1024_4x256_s24", 3)
+    bad = synth.generate("batch1024_4x256_s24", 3, start=10)
+    for p in bad:
+        assert (p.kind == 2).any()
+    import copy
+    progs = [good[0], copy.deepcopy(bad[0]), good[1], copy.deepcopy(bad[1])]
+    for p in (progs[1], progs[3]):
+        s = int(np.nonzero(p.kind == 2)[0][0])
+        off = int(p.perm_off[s])
+        p.perm = p.perm.copy()
+        p.perm[off + 1] = p.perm[off]  # a repeated entry
+    for fn in (lambda: gb.repair_batch(progs), lambda: gb.check_batch(progs, [0] * 4)):
+        with pytest.raises(gb.GrError) as e:
+            fn()
+        assert e.value.code == gb.EINVAL and "program 1 stmt" in str(e.value) and "permutation" in str(e.value)
+    with pytest.raises(gb.GrError) as e:
+        gb.repair_plain(progs[1])
+    assert e.value.code == gb.EINVAL
+    # the same batch without the bad tables goes through
+    got = gb.repair_batch([progs[0], progs[2]])
+    for p, g in zip([progs[0], progs[2]], got):
+        _same_result(g, oracle.repair(p))
