@@ -285,7 +285,7 @@ class HostPool {
     }
     template <typename F>
     void run(uint32_t n, F &body) {
-        const uint32_t parts = n >= 128 ? std::min<uint32_t>(n_workers_ + 1, (n + 63) / 64) : 1u;
+        const uint32_t parts = n >= 32 ? std::min<uint32_t>(n_workers_ + 1, (n + 15) / 16) : 1u;
         std::unique_lock<std::mutex> busy(use_, std::try_to_lock);
         if (parts <= 1 || !busy.owns_lock()) {
             body(0u, n);
@@ -984,27 +984,72 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     std::lock_guard<std::mutex> g(ws->mu);
     if ((s = ensure_configured(*ws)) != GR_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Layout L;
-    if ((s = upload_batch(*ws, progs, launches, modes, n, st, &L)) != GR_OK) return s;
-    if ((s = ws->out.ensure((size_t)n * sizeof(gr_repair_result))) != GR_OK) return s;
-    GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
-    GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
-    // the batch's size class picks the CTA shape; the first batch of a class tunes it
-    const SizeClass cls = size_class(progs, launches, n);
-    auto it = ws->class_shape.find(cls);
-    if (it == ws->class_shape.end()) {
-        uint32_t shape = 0;
-        gr_status ts = tune_shapes(*ws, ws->arena.p, n, opts_or_default(opts), ws->scratch.p,
-                                   static_cast<gr_repair_result *>(ws->out.p), st, cls.s_max, &shape);
-        if (ts != GR_OK) return ts;
-        it = ws->class_shape.emplace(cls, shape).first;
+    // Large batches go in chunks so that packing chunk c+1 on the host
+    // overlaps the device work of chunk c (H2D, expansion, repair, all on one
+    // stream: the device arena and scratch are reused in order).  Results
+    // gather in the device result buffer and reach `out` in one copy at the
+    // end, so `out` stays untouched when a later chunk holds a bad table.
+    const uint32_t K = n >= 512 ? 4u : (n >= 256 ? 2u : 1u);
+    std::vector<uint32_t> lo(K + 1);
+    for (uint32_t c = 0; c <= K; ++c) lo[c] = (uint32_t)((uint64_t)n * c / K);
+    std::vector<Layout> Ls(K);
+    std::vector<size_t> soff(K);
+    size_t stage = 0, arena_max = 0, scratch_max = 0;
+    for (uint32_t c = 0; c < K; ++c) {
+        Ls[c] = layout_of(progs + lo[c], launches + lo[c], lo[c + 1] - lo[c]);
+        soff[c] = stage;
+        stage += align_to(Ls[c].arena_bytes, 256);
+        arena_max = std::max(arena_max, Ls[c].arena_bytes);
+        scratch_max = std::max(scratch_max, Ls[c].scratch_bytes);
     }
-    LaunchCfg cfg = shape_cfg(*ws, n, it->second, cls.s_max);
-    if (!cfg.table_bytes) cfg = choose_cfg(*ws, n, cls.s_max);
-    GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
-    GR_CUDA(launch_repair(ws->arena.p, n, opts_or_default(opts), ws->scratch.p,
-                          static_cast<gr_repair_result *>(ws->out.p), cfg, st));
-    GR_CUDA(cudaMemcpyAsync(out, ws->out.p, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost, st));
+    // the previous call on this workspace may still be reading the staging buffer
+    GR_CUDA(cudaStreamSynchronize(st));
+    if (ws->host_arena_cap < stage) {
+        if (ws->host_arena) cudaFreeHost(ws->host_arena);
+        ws->host_arena = nullptr;
+        ws->host_arena_cap = 0;
+        const size_t want = std::max<size_t>(stage, (size_t)1 << 20);
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&ws->host_arena), want, cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(staging)");
+        ws->host_arena_cap = want;
+    }
+    if ((s = ws->arena.ensure(arena_max)) != GR_OK) return s;
+    if ((s = ws->scratch.ensure(scratch_max)) != GR_OK) return s;
+    if ((s = ws->out.ensure((size_t)n * sizeof(gr_repair_result))) != GR_OK) return s;
+    gr_repair_result *d_out = static_cast<gr_repair_result *>(ws->out.p);
+    std::vector<uint32_t> bad;
+    for (uint32_t c = 0; c < K; ++c) {
+        const uint32_t n_c = lo[c + 1] - lo[c];
+        uint8_t *staging = ws->host_arena + soff[c];
+        // permutation tables are checked while they are converted; the lowest
+        // bad program is reported (earlier chunks' device work is discarded)
+        bad.assign(n_c, 0xFFFFFFFFu);
+        pack_into(progs + lo[c], launches + lo[c], modes ? modes + lo[c] : nullptr, n_c, Ls[c], staging, bad.data());
+        for (uint32_t p = 0; p < n_c; ++p)
+            if (bad[p] != 0xFFFFFFFFu)
+                return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", lo[c] + p, bad[p]);
+        GR_CUDA(cudaMemcpyAsync(ws->arena.p, staging, Ls[c].arena_bytes, cudaMemcpyHostToDevice, st));
+        // queue counter (and, for the first chunk, the error word) cleared
+        GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, c == 0 ? 256 : 4, st));
+        GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
+        // the chunk's size class picks the CTA shape; the first batch of a class tunes it
+        const SizeClass cls = size_class(progs + lo[c], launches + lo[c], n_c);
+        auto it = ws->class_shape.find(cls);
+        if (it == ws->class_shape.end()) {
+            // tuning clears the scratch control words: report an earlier chunk's error first
+            if (c > 0 && (s = finish_sync(ws->scratch.p, st)) != GR_OK) return s;
+            uint32_t shape = 0;
+            gr_status ts = tune_shapes(*ws, ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, d_out + lo[c], st,
+                                       cls.s_max, &shape);
+            if (ts != GR_OK) return ts;
+            it = ws->class_shape.emplace(cls, shape).first;
+            GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 4, st));
+        }
+        LaunchCfg cfg = shape_cfg(*ws, n_c, it->second, cls.s_max);
+        if (!cfg.table_bytes) cfg = choose_cfg(*ws, n_c, cls.s_max);
+        GR_CUDA(launch_repair(ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, d_out + lo[c], cfg, st));
+    }
+    GR_CUDA(cudaMemcpyAsync(out, d_out, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost, st));
     return finish_sync(ws->scratch.p, st);
 }
 
