@@ -47,6 +47,7 @@ struct MhsSmem {
 struct Smem {
     DevProg prog;
     uint32_t act[GR_MAX_STMTS][32];  // active-thread bitmaps per statement
+    uint32_t nact[32];               // active threads per statement
     uint32_t rows_intra[32], rows_inter[32];
     uint32_t acc_intra[32], acc_inter[32];
     uint32_t ph_intra[32], ph_inter[32];
@@ -161,16 +162,24 @@ __device__ void load_program(Smem &sm, const DevProg *gp) {
     uint4 *dst = reinterpret_cast<uint4 *>(&sm.prog);
     for (uint32_t i = threadIdx.x; i < sizeof(DevProg) / 16; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    // active-thread bitmaps: one ballot per 32 threads of a statement
-    const uint32_t S = sm.prog.n_stmts, T = sm.prog.threads;
+    // active-thread bitmaps: one ballot per 32 threads of a statement (words
+    // past the launch's threads are zero), and the count of active threads
+    const uint32_t S = sm.prog.n_stmts, T = sm.prog.threads, nw = (T + 31u) >> 5;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (uint32_t w = warp; w < S * 32u; w += nwarps) {
-        const uint32_t s = w >> 5, word = w & 31u;
-        const uint32_t tid = word * 32u + lane;
+    for (uint32_t s = warp; s < S; s += nwarps) {
         const uint32_t k = sm.prog.stmts[s].gk, r = sm.prog.stmts[s].gr;
-        const bool on = tid < T && (k == 0 || tid % k == r);
-        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, on);
-        if (lane == 0) sm.act[s][word] = bits;
+        uint32_t n = 0;
+        for (uint32_t word = 0; word < 32u; ++word) {
+            uint32_t bits = 0;
+            if (word < nw) {
+                const uint32_t tid = word * 32u + lane;
+                const bool on = tid < T && (k == 0 || tid % k == r);
+                bits = __ballot_sync(0xFFFFFFFFu, on);
+                n += __popc(bits);
+            }
+            if (lane == 0) sm.act[s][word] = bits;
+        }
+        if (lane == 0) sm.nact[s] = n;
     }
     __syncthreads();
     pair_counts(sm);
@@ -509,11 +518,15 @@ __device__ void pair_counts(Smem &sm) {
         const DevStmt &a = P.stmts[i], &b = P.stmts[j];
         uint64_t same = 0, cross = 0;
         if (a.space == b.space && (a.op == GR_W || b.op == GR_W)) {
-            uint64_t ni = 0, nj = 0, nij = 0;
-            for (uint32_t w = 0; w < 32; ++w) {
-                ni += __popc(sm.act[i][w]);
-                nj += __popc(sm.act[j][w]);
-                nij += __popc(sm.act[i][w] & sm.act[j][w]);
+            const uint64_t ni = sm.nact[i], nj = sm.nact[j];
+            // threads active at both: one side unguarded, or one guard, needs no count
+            uint64_t nij;
+            if (a.gk == 0) nij = nj;
+            else if (b.gk == 0 || (a.gk == b.gk && a.gr == b.gr)) nij = ni;
+            else {
+                nij = 0;
+                const uint32_t nw = (P.threads + 31u) >> 5;
+                for (uint32_t w = 0; w < nw; ++w) nij += __popc(sm.act[i][w] & sm.act[j][w]);
             }
             const bool global = a.space == GR_GLOBAL;
             if (i < j) {
