@@ -1026,8 +1026,11 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
         bad.assign(n_c, 0xFFFFFFFFu);
         pack_into(progs + lo[c], launches + lo[c], modes ? modes + lo[c] : nullptr, n_c, Ls[c], staging, bad.data());
         for (uint32_t p = 0; p < n_c; ++p)
-            if (bad[p] != 0xFFFFFFFFu)
+            if (bad[p] != 0xFFFFFFFFu) {
+                // earlier chunks may still run: wait so that no later call reuses their buffers early
+                if (c > 0) cudaStreamSynchronize(st);
                 return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", lo[c] + p, bad[p]);
+            }
         GR_CUDA(cudaMemcpyAsync(ws->arena.p, staging, Ls[c].arena_bytes, cudaMemcpyHostToDevice, st));
         // queue counter (and, for the first chunk, the error word) cleared
         GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, c == 0 ? 256 : 4, st));
