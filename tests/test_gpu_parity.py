@@ -472,3 +472,20 @@ def test_batch_rejects_bad_permutation_tables(gb):
     got = gb.repair_batch([progs[0], progs[2]])
     for p, g in zip([progs[0], progs[2]], got):
         _same_result(g, oracle.repair(p))
+    # a large batch goes in chunks: a bad table in the last chunk is still
+    # reported (after earlier chunks ran), and the next call is unaffected
+    big = synth.generate("batch1024_4x256_s24", 600, blocks=2, threads=32, n_stmts=8, m_words=128)
+    k = next(i for i in range(590, 600) if (big[i].kind == 2).any())
+    s = int(np.nonzero(big[k].kind == 2)[0][0])
+    big[k] = copy.deepcopy(big[k])
+    big[k].perm = big[k].perm.copy()
+    big[k].perm[int(big[k].perm_off[s])] = big[k].perm[int(big[k].perm_off[s]) + 1]
+    out = np.zeros(600, dtype=gb.RESULT_DTYPE)
+    with pytest.raises(gb.GrError) as e:
+        gb.repair_batch_raw(big, out=out)
+    assert e.value.code == gb.EINVAL and f"program {k} stmt" in str(e.value)
+    assert not out.any()  # results untouched
+    good_big = big[:k] + big[k + 1:]
+    got = gb.repair_batch(good_big)
+    for i in (0, 150, 300, 450, len(good_big) - 1):
+        _same_result(got[i], oracle.repair(good_big[i]))
