@@ -1,0 +1,110 @@
+"""Edge cases of the CUDA path against the oracle (or, where the oracle's
+enumeration is too slow, against results fixed by reasoning): degenerate
+programs, the largest sizes the ABI allows."""
+import numpy as np
+import pytest
+
+import oracle
+from _tiny import random_program
+from paper_2011_08373_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("status", "mask", "weight", "added", "removed", "iters", "traj", "clauses", "forbidden",
+        "access_pairs")
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_08373_gb300.build import build
+    from paper_2011_08373_gb300 import binding
+
+    build()
+    binding.lib()
+    return binding
+
+
+def _same(g, w):
+    for k in KEYS:
+        assert g[k] == w[k], (k, g[k], w[k])
+
+
+def test_degenerate_programs(gb):
+    """One statement (no slot), one thread, one block, one-word arrays."""
+    progs = [
+        synth.make_program([{"op": "W"}], blocks=1, threads=1, m_shared=1),
+        synth.make_program([{"op": "W", "a": 0}], blocks=1, threads=5, m_shared=1),  # self race, no slot
+        synth.make_program([{"op": "R"}, {"op": "W"}], blocks=1, threads=1, m_shared=1),
+        synth.make_program([{"op": "W", "space": "global", "a": 0}, {"op": "R", "space": "global"}],
+                           blocks=3, threads=1, m_global=1),
+        synth.make_program([{"op": "R", "a": 0}, {"op": "R", "a": 0}], blocks=2, threads=7, m_shared=1),
+    ]
+    progs += [random_program(97000 + s, s_max=2, b_max=2, t_max=2, m_max=2) for s in range(60)]
+    for fn in (gb.repair_batch, lambda ps: [gb.repair(p) for p in ps], lambda ps: [gb.repair_plain(p) for p in ps]):
+        for p, g in zip(progs, fn(progs)):
+            _same(g, oracle.repair(p))
+    assert gb.repair(progs[1])["status"] == 1
+
+
+def test_largest_statement_count(gb):
+    """25 statements and 24 slots, 1,024 threads, 4,096-word shared array."""
+    progs = synth.generate("batch1024_4x256_s24", 3, n_stmts=25, blocks=1, threads=1024, m_words=4096)
+    assert all(p.n_stmts == 25 and p.n_slots == 24 for p in progs)
+    got = gb.repair_batch(progs)
+    want = oracle.repair_batch(progs, n_threads=8)
+    for g, w in zip(got, want):
+        _same(g, w)
+
+
+def test_largest_address_space(gb):
+    """65,536-word arrays: addresses up to 65,535 in the u16 traces."""
+    p = synth.make_program([{"op": "W", "space": "global", "a": 1, "b": 65535 - 63},
+                            {"op": "R", "space": "global", "a": 1, "b": 65535 - 62},
+                            {"op": "W", "a": 2, "b": 65534}, {"op": "R", "a": 2, "b": 0}],
+                           blocks=2, threads=64, m_global=65536, m_shared=65536)
+    for g, w in zip(gb.repair_batch([p]), [oracle.repair(p)]):
+        _same(g, w)
+    assert gb.check(p, 0) == oracle.check(p, 0)
+
+
+def test_most_blocks(gb):
+    """65,533 blocks of one thread (the owner tables hold block indices up to
+    65,532): block b writes word b and reads word b+1, which block b+1 writes,
+    so the one race is cross-block and only a grid barrier between the two
+    statements fixes it."""
+    B = 65533
+    p = synth.make_program([{"op": "R", "space": "global", "a": 0, "c": 1, "b": 1},
+                            {"op": "W", "space": "global", "a": 0, "c": 1, "b": 0}],
+                           blocks=B, threads=1, m_global=65536, slot_level=[1], slot_weight=[13])
+    w = gb.check(p, 0)
+    assert w["intra"] == [0, 0] and w["inter"] == [2, 0] and w["diverge"] == 0
+    # ordered pairs (read block b1, write block b2 != b1) plus unordered write pairs
+    assert w["access_pairs"] == B * (B - 1) + B * (B - 1) // 2
+    r = gb.repair(p)
+    assert (r["status"], r["mask"], r["weight"], r["traj"], r["clauses"]) == (0, 1, 13, [0, 1], [1])
+    assert gb.repair(p, grid_enabled=False)["status"] == 1
+
+
+def test_thirty_two_slots(gb):
+    """32 barrier variables (a block and a grid candidate at 16 sites): the
+    final repair is the lowest-key mask over the oracle's unconstrained
+    witnesses, found by integer programming (path independence)."""
+    pytest.importorskip("scipy.optimize")
+    from test_oracle_pins import milp_lowest_key
+
+    progs = synth.generate("sites128_16x256_s16", 6, n_stmts=17, blocks=2, threads=16, m_words=512)
+    assert all(p.n_slots == 32 for p in progs)
+    for p, g in zip(progs, gb.repair_batch(progs)):
+        w0 = oracle.check(p, 0)
+        assert gb.check(p, 0) == w0
+        cls = oracle.clauses(p, w0)
+        div = oracle.check(p, 0xFFFFFFFF)["diverge"]
+        want = milp_lowest_key(32, [int(x) for x in p.slot_weight], cls, (), 0, div)
+        if want is None:
+            assert g["status"] == 1
+        else:
+            assert g["status"] == 0 and (g["mask"], g["weight"]) == want
