@@ -1059,11 +1059,9 @@ __device__ void loop_step(Smem &sm, MhsSmem &mh) {
     __syncthreads();
 }
 
-// Bitonic sort of sm.cl padded to kClauseCap entries, then unique compaction
-// into out->clauses.
-__device__ void write_result(Smem &sm, gr_repair_result *out) {
-    const DevProg &P = sm.prog;
-    build_clauses(sm);
+// Bitonic sort of the clause list padded to a power of two, then unique
+// compaction into out->clauses; returns the number of distinct clauses.
+__device__ uint32_t sort_unique_clauses(Smem &sm, gr_repair_result *out) {
     const uint32_t n = sm.n_cl;
     uint32_t np2 = 32;
     while (np2 < n) np2 <<= 1;
@@ -1111,6 +1109,42 @@ __device__ void write_result(Smem &sm, gr_repair_result *out) {
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
         const uint32_t base = g ? sm.scan[g - 1] : 0u;
         if (first) out->clauses[base + __popc(bal & ((1u << lane) - 1u))] = mh_cl(sm)[i];
+    }
+    __syncthreads();
+    return n_unique;
+}
+
+// The program's result: status, mask, weight, the sorted unique clause list,
+// the trajectory and the counters.
+__device__ void write_result(Smem &sm, gr_repair_result *out) {
+    const DevProg &P = sm.prog;
+    if (threadIdx.x == 0) sm.scan[0] = 0;  // ordered by build_clauses' barriers
+    build_clauses(sm);
+    const uint32_t n = sm.n_cl;
+    uint32_t n_unique;
+    if (n <= 128) {
+        // few clauses: each first occurrence goes straight to its rank among
+        // the distinct clauses (two barriers instead of a sorting network)
+        MhsSmem &mh = *reinterpret_cast<MhsSmem *>(reinterpret_cast<uint8_t *>(&sm) + kFixedSmem);
+        const uint32_t *cl = mh.cl;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint32_t c = cl[i];
+            bool first = true;
+            for (uint32_t j = 0; j < i && first; ++j) first = cl[j] != c;
+            mh.pc[i] = first ? 1u : 0u;
+            if (first) atomicAdd(&sm.scan[0], 1u);
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            if (!mh.pc[i]) continue;
+            const uint32_t c = cl[i];
+            uint32_t pos = 0;
+            for (uint32_t j = 0; j < n; ++j) pos += (mh.pc[j] && cl[j] < c) ? 1u : 0u;
+            out->clauses[pos] = c;
+        }
+        n_unique = sm.scan[0];
+    } else {
+        n_unique = sort_unique_clauses(sm, out);
     }
     for (uint32_t i = threadIdx.x + n_unique; i < GR_MAX_CLAUSES; i += blockDim.x) out->clauses[i] = 0;
     for (uint32_t i = threadIdx.x; i < GR_MAX_ITERS; i += blockDim.x) out->traj[i] = i < sm.iters ? sm.traj[i] : 0u;
