@@ -35,6 +35,8 @@ WORKLOAD = "batch1024_4x256_s24"
 # DRAM bytes (read + write) of one k_repair launch, from the ncu capture summarised in
 # profiles/k_repair_batch1024_4x256_s24.md; reset to None whenever k_repair changes.
 NCU_TRAFFIC = {}  # k_repair changed (result write) after the last capture
+# the same for one k_check launch (profiles/k_check_batch1024_4x256_s24.md)
+NCU_CHECK_TRAFFIC = {}
 
 
 def _peaks():
@@ -319,6 +321,28 @@ def run_ours(args, rank, world, local):
             "same_final_mask": float(np.mean((gres["mask"] == res["mask"]) & (gres["status"] == res["status"]))),
         }
         del gb
+    check = None
+    if rank == 0 and args.check_steps > 0:
+        # the check kernel alone (gr_check_expanded): one check per program
+        # under the empty mask, where every statement pair is a candidate
+        batch.check([0] * n)
+        torch.cuda.synchronize()
+        c_ms = []
+        for _ in range(args.check_steps):
+            l2_flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch.check(None, expanded=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            c_ms.append(a.elapsed_time(b))
+        t_c = statistics.mean(c_ms) / 1000.0
+        c_bytes = (sum(check_bytes(batch.host_arena, i) for i in range(n)) + batch.arena_bytes
+                   + n * binding.WITNESS_DTYPE.itemsize)
+        check = {"checks_per_s": n / t_c, "check_kernel_ms": t_c * 1000, "mask": 0,
+                 "roofline": {"bound": "hbm", "achieved": c_bytes / t_c / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": c_bytes / t_c / 1e9 / peak, "kernel": "k_check",
+                              "algorithmic_bytes": c_bytes, "traffic": NCU_CHECK_TRAFFIC.get(args.workload)}}
     wide = None
     if rank == 0 and args.wide_steps > 0:
         # the wide lane on the same batch: one CTA per (program, block) per
@@ -365,7 +389,8 @@ def run_ours(args, rank, world, local):
             "expand_ms": statistics.mean(expand_ms), "repair_kernel_ms": statistics.mean(repair_ms),
             "latency_in_batch_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "status_counts": {"repaired": status[0], "unrepairable": status[1], "iter_cap": status[2]},
-            "checks_per_repair": checks / n, "strategies": strategies, "wide_lane": wide, "wall_s": wall,
+            "checks_per_repair": checks / n, "strategies": strategies, "wide_lane": wide,
+            "check_kernel": check, "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -443,6 +468,8 @@ def main():
     ap.add_argument("--programs", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--plain-programs", type=int, default=64)
+    ap.add_argument("--check-steps", type=int, default=5,
+                    help="timed launches of the check kernel alone on the same batch (0: skip)")
     ap.add_argument("--wide-steps", type=int, default=5,
                     help="calls of the wide lane on the same batch (0: skip)")
     ap.add_argument("--strategy-steps", type=int, default=5,

@@ -304,6 +304,12 @@ gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts
 gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_masks,
                           void *d_scratch, uint64_t scratch_bytes, gr_witnesses *d_out,
                           void *stream);
+/* gr_check_packed without the expansion: the checks alone, on traces a
+ * previous gr_expand_packed (or gr_check_packed / gr_repair_packed) of the same
+ * arena wrote into d_scratch.  For callers that time the check kernel. */
+gr_status gr_check_expanded(const void *d_arena, uint32_t n, const uint32_t *d_masks,
+                            void *d_scratch, uint64_t scratch_bytes, gr_witnesses *d_out,
+                            void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Repair server: continuous batching over a device-memory budget          */

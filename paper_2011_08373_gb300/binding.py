@@ -83,7 +83,7 @@ EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair"
            "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded",
            "gr_repair_packed_noalloc", "gr_server_create", "gr_server_submit", "gr_server_poll",
            "gr_server_drain", "gr_server_stats", "gr_server_destroy", "gr_tune_packed",
-           "gr_repair_packed_wide"]
+           "gr_repair_packed_wide", "gr_check_expanded"]
 
 
 def lib():
@@ -132,6 +132,7 @@ def lib():
                                          C.c_void_p, C.c_void_p, P(C.c_uint32)]
             L.gr_check_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint64,
                                           C.c_void_p, C.c_void_p]
+            L.gr_check_expanded.argtypes = L.gr_check_packed.argtypes
             for name in EXPORTS[2:]:
                 getattr(L, name).restype = C.c_int32
             _lib = L
@@ -508,19 +509,23 @@ class DeviceBatch:
                                         C.c_void_p(self._scratch_ptr), self.scratch_bytes,
                                         C.c_void_p(self._out_ptr), C.c_void_p(st)))
 
-    def check(self, masks, stream: Optional[int] = None):
+    def check(self, masks, stream: Optional[int] = None, expanded: bool = False):
+        """One check per program under masks[p] (gr_check_packed; with
+        expanded=True only the check kernel, gr_check_expanded, on traces a
+        previous call of this batch wrote)."""
         import torch
 
         if self.wit is None:
             self.wit = torch.empty(self.n * WITNESS_DTYPE.itemsize + 256, dtype=torch.uint8,
                                    device=self.arena.device)
             self.masks = torch.empty(self.n, dtype=torch.int32, device=self.arena.device)
-        self.masks.copy_(torch.as_tensor(np.asarray(masks, np.uint32).view(np.int32)))
+        if masks is not None:  # None: the masks of the previous call
+            self.masks.copy_(torch.as_tensor(np.asarray(masks, np.uint32).view(np.int32)))
         st = torch.cuda.current_stream().cuda_stream if stream is None else stream
-        _check(lib().gr_check_packed(C.c_void_p(self._arena_ptr), self.n,
-                                     C.c_void_p(self.masks.data_ptr()), C.c_void_p(self._scratch_ptr),
-                                     self.scratch_bytes, C.c_void_p(_aligned(self.wit.data_ptr())),
-                                     C.c_void_p(st)))
+        fn = lib().gr_check_expanded if expanded else lib().gr_check_packed
+        _check(fn(C.c_void_p(self._arena_ptr), self.n, C.c_void_p(self.masks.data_ptr()),
+                  C.c_void_p(self._scratch_ptr), self.scratch_bytes, C.c_void_p(_aligned(self.wit.data_ptr())),
+                  C.c_void_p(st)))
 
     def results_raw(self) -> np.ndarray:
         off = self._out_ptr - self.out.data_ptr()

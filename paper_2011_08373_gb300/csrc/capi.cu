@@ -969,6 +969,23 @@ gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_mas
     return GR_OK;
 }
 
+gr_status gr_check_expanded(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
+                            uint64_t scratch_bytes, gr_witnesses *d_out, void *stream) {
+    if (!d_arena || !d_scratch || !d_out || !d_masks || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    if (scratch_bytes < 256) return fail(GR_ECAPACITY, "scratch too small");
+    gr_status s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 4, st));  // the work-queue counter
+    GR_CUDA(launch_check(d_arena, n, d_masks, d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
+    return GR_OK;
+}
+
 gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, const int32_t *modes, uint32_t n,
                           const gr_options *opts, gr_repair_result *out, void *stream) {
     if (!out) return fail(GR_EINVAL, "out is NULL");
