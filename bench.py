@@ -36,7 +36,7 @@ WORKLOAD = "batch1024_4x256_s24"
 # profiles/k_repair_batch1024_4x256_s24.md; reset to None whenever k_repair changes.
 NCU_TRAFFIC = {}  # k_repair changed (result write) after the last capture
 # the same for one k_check launch (profiles/k_check_batch1024_4x256_s24.md)
-NCU_CHECK_TRAFFIC = {}
+NCU_CHECK_TRAFFIC = {"batch1024_4x256_s24": 14_136_576}
 
 
 def _peaks():
