@@ -61,16 +61,19 @@ class ClockSampler:
         self._stop = threading.Event()
         self._thr = None
 
+    def sample_now(self):
+        try:
+            out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                 timeout=5).stdout.strip()
+            if out:
+                self.samples.append([x.strip() for x in out.split(",")])
+        except Exception:
+            pass
+
     def _run(self):
         while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
+            self.sample_now()
             self._stop.wait(0.2)
 
     def __enter__(self):
@@ -243,6 +246,7 @@ def run_ours(args, rank, world, local):
             e1.record(stream)
             batch.repair_expanded()
             e2.record(stream)
+        clk.sample_now()  # the queued steps are still running on the device
         barrier()
         wall = time.perf_counter() - wall0
     step_ms = [a.elapsed_time(c) for a, b, c in ev]
@@ -461,8 +465,8 @@ def run_serve(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--programs", type=int, default=0)
@@ -475,7 +479,7 @@ def main():
     ap.add_argument("--strategy-steps", type=int, default=5,
                     help="timed launches of the mhs strategy on the same batch (0: skip)")
     ap.add_argument("--cpu-sample", type=int, default=32)
-    ap.add_argument("--ref-sample", type=int, default=32)
+    ap.add_argument("--ref-sample", type=int, default=16)
     ap.add_argument("--serve", action="store_true", help="Poisson request streams through the server")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 500.0, 2000.0])
     ap.add_argument("--serve-requests", type=int, default=1000)
