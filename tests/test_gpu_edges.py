@@ -108,3 +108,29 @@ def test_thirty_two_slots(gb):
             assert g["status"] == 1
         else:
             assert g["status"] == 0 and (g["mask"], g["weight"]) == want
+
+
+def test_many_blocks_that_differ(gb):
+    """More than 64 blocks whose access patterns differ (the check walks every
+    block and reads their chunk masks one block at a time), on the persistent
+    launch, the plain path and the wide lane."""
+    import torch
+
+    progs = []
+    for s in range(6):
+        p = random_program(98000 + s, s_min=3, s_max=5, b_min=1, b_max=1, t_min=3, t_max=4, m_max=3000,
+                           c_max=9, a_max=3, spaces=(1,))
+        p.blocks = 70 + s
+        p.c[0] = p.c[0] + 1  # blocks differ
+        progs.append(p)
+    want = oracle.repair_batch(progs, n_threads=4)
+    assert sum(w["status"] == 0 for w in want) >= 3
+    for p, g, w in zip(progs, gb.repair_batch(progs), want):
+        _same(g, w)
+        assert gb.check(p, 0) == oracle.check(p, 0)
+    _same(gb.repair_plain(progs[0]), want[0])
+    db = gb.DeviceBatch(progs)
+    db.run_wide()
+    torch.cuda.synchronize()
+    for g, w in zip(db.results(), want):
+        _same(g, w)
