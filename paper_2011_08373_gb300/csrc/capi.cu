@@ -143,16 +143,21 @@ gr_status validate_loops(const gr_program *p, uint32_t idx) {
 // marking M distinct entries); dst (may be NULL) receives them as u16.
 bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst) {
     uint8_t mark[GR_MAX_WORDS];
-    memset(mark, 0, M);
     uint32_t bad = 0;
     if (dst) {
+        // convert (a streaming loop the compiler vectorises) and check the
+        // range, then mark from the u16 copy
+        uint32_t mx = 0;
         for (uint32_t i = 0; i < M; ++i) {
             const uint32_t v = tbl[i];
-            bad |= v >= M;
-            mark[v < M ? v : 0u] = 1;
+            mx = v > mx ? v : mx;
             dst[i] = (uint16_t)v;
         }
+        if (mx >= M) return false;
+        memset(mark, 0, M);
+        for (uint32_t i = 0; i < M; ++i) mark[dst[i]] = 1;
     } else {
+        memset(mark, 0, M);
         for (uint32_t i = 0; i < M; ++i) {
             const uint32_t v = tbl[i];
             bad |= v >= M;
