@@ -198,7 +198,7 @@ class CProgram:
             self.coef = np.ascontiguousarray(coef, dtype=np.uint32)
             self.s.iter_coef = self.coef.ctypes.data_as(C.POINTER(C.c_uint32))
         pos = getattr(p, "slot_pos", None)
-        if pos is not None:
+        if pos is not None and len(pos):  # no slots: no places to give
             self.pos = np.ascontiguousarray(np.asarray(pos, dtype=np.uint8))
             self.s.n_slots = n
             self.s.slot_pos = self.pos.ctypes.data_as(C.POINTER(C.c_uint8))
@@ -286,7 +286,7 @@ class ProgramBatch:
                 [p.iter_coef if c else np.zeros(len(p.op), np.uint32) for p, c in zip(progs, has_coef)]
             ).astype(np.uint32))
             pa["iter_coef"] = np.where(has_coef, self.coef.ctypes.data + 4 * s_off[:-1], 0)
-        has_pos = np.array([getattr(p, "slot_pos", None) is not None for p in progs])
+        has_pos = np.array([getattr(p, "slot_pos", None) is not None and len(p.slot_pos) > 0 for p in progs])
         if has_pos.any():
             self.pos_arr = np.ascontiguousarray(np.concatenate(
                 [np.asarray(p.slot_pos, np.uint8) if h else np.zeros(0, np.uint8) for p, h in zip(progs, has_pos)]

@@ -22,6 +22,9 @@ constexpr uint32_t kItemSegs = 64;               // segments per trace-expansion
 constexpr uint16_t kEmpty = 0xFFFFu;           // owner-table sentinels
 constexpr uint16_t kMulti = 0xFFFEu;
 constexpr uint32_t kClauseCap = 1024;          // clause buffer (>= 2 * 25 * 26 / 2)
+constexpr uint32_t kClauseSetLog2 = 11;
+constexpr uint32_t kClauseSet = 1u << kClauseSetLog2;  // clause hash set (>= 2 x 650 entries)
+constexpr uint32_t kNoClause = 0xFFFFFFFFu;            // its empty marker
 constexpr uint32_t kMinTableBytes = 25u * 2u * kChunkWords;  // one chunk for 25 rows
 constexpr uint32_t kErrTableTooSmall = 1u;  // bits of the device error word (scratch control word 1)
 

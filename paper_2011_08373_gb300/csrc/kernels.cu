@@ -34,7 +34,7 @@ struct MhsSmem {
     uint32_t pc[kClauseCap];   // preprocessed positive clauses (0 = dropped)
     uint32_t khi[kClauseCap];  // kept clauses: compact high part
     uint32_t klo[kClauseCap];  // kept clauses: low-part hit pattern over 32 low assignments
-    uint32_t nraw[kClauseCap]; // negative clauses after preprocessing (0 = dropped)
+    uint32_t set[kClauseSet];  // open-addressing set of the clauses built so far
     uint32_t nhi[kClauseCap];
     uint32_t nlo[kClauseCap];
     uint32_t w8[4][256];       // weight of each byte of the high part
@@ -42,6 +42,7 @@ struct MhsSmem {
     uint32_t lb[GR_MAX_SLOTS + 2];  // sum of the k smallest high weights
     uint32_t wc[GR_MAX_SLOTS]; // compact weights
     uint32_t n_kept, n_negk, R, U, unsat;
+    uint32_t full_seen;  // the clause of all 32 slots (the set's empty marker) was built
 };
 
 struct Smem {
@@ -673,14 +674,17 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
         sm.best = ~0ull;
     }
     __syncthreads();
-    for (uint32_t i = tid; i < n_cl; i += nt) {
-        const uint32_t c = mh_cl(sm)[i];
+    const uint32_t n_cl4 = (n_cl + 3u) >> 2;
+    for (uint32_t i = tid; i < 4u * n_cl4; i += nt) {
         uint32_t pc = 0;
-        if (!(c & forced)) {
-            pc = c & ~forbidden;
-            if (!pc) mh.unsat = 1;
+        if (i < n_cl) {
+            const uint32_t c = mh_cl(sm)[i];
+            if (!(c & forced)) {
+                pc = c & ~forbidden;
+                if (!pc) mh.unsat = 1;
+            }
         }
-        mh.pc[i] = pc;
+        mh.pc[i] = pc;  // zero past the last clause: four at a time below
     }
     __syncthreads();
     if (mh.unsat) {
@@ -689,13 +693,17 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
         return;
     }
     // drop every clause that contains another one (equal clauses: keep the first)
+    const uint4 *pc4 = reinterpret_cast<const uint4 *>(mh.pc);
     for (uint32_t i = tid; i < n_cl; i += nt) {
         const uint32_t c = mh.pc[i];
         if (!c) continue;
+        // clause j drops clause i when it is a subset (equal: the earlier one)
+        auto drops = [&](uint32_t d, uint32_t j) { return d && j != i && (d & ~c) == 0 && (d != c || j < i); };
         bool keep = true;
-        for (uint32_t j = 0; j < n_cl && keep; ++j) {
-            const uint32_t d = mh.pc[j];
-            if (d && j != i && (d & ~c) == 0 && (d != c || j < i)) keep = false;
+        for (uint32_t q = 0; q < n_cl4 && keep; ++q) {
+            const uint4 d = pc4[q];
+            keep = !(drops(d.x, 4u * q) || drops(d.y, 4u * q + 1u) || drops(d.z, 4u * q + 2u) ||
+                     drops(d.w, 4u * q + 3u));
         }
         if (keep) {
             if ((c & (c - 1u)) == 0) {
@@ -937,21 +945,51 @@ __device__ void mhs_greedy(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_
 // Loop steps (Algorithm 1)
 // ---------------------------------------------------------------------------
 
+// Insert clause c into the clause set; a clause already there is not listed
+// again.  Linear probing over a table at least twice the largest clause count
+// (2 x 25 x 26 / 2 = 650 witness pairs), so every probe sequence meets an
+// empty entry; kNoClause, itself a clause (all 32 slots), is tracked apart.
+__device__ __forceinline__ void add_clause(Smem &sm, MhsSmem &mh, uint32_t c) {
+    bool fresh = true;
+    if (c == kNoClause) {
+        fresh = atomicExch(&mh.full_seen, 1u) == 0u;
+    } else {
+        uint32_t h = (c * 0x9E3779B1u) >> (32u - kClauseSetLog2);  // Fibonacci hashing
+        for (uint32_t q = 0; q < kClauseSet; ++q) {
+            const uint32_t prev = atomicCAS(&mh.set[h], kNoClause, c);
+            if (prev == kNoClause) break;
+            if (prev == c) {
+                fresh = false;
+                break;
+            }
+            h = (h + 1u) & (kClauseSet - 1u);
+        }
+    }
+    if (fresh) mh_cl(sm)[atomicAdd(&sm.n_cl, 1u)] = c;
+}
+
 // Clause list from the accumulated witnesses: same-block (i, j) -> the slots
 // whose barriers run in gaps i..j-1 (slots i..j-1 without loops); cross-block
-// (i, j) -> the grid slots among them (GenerateClause).
+// (i, j) -> the grid slots among them (GenerateClause).  The list holds each
+// distinct clause once: the clauses form a set, so the greedy strategy's hit
+// counts count distinct clauses.
 __device__ void build_clauses(Smem &sm) {
     const DevProg &P = sm.prog;
     const uint32_t S = P.n_stmts;
+    MhsSmem &mh = *reinterpret_cast<MhsSmem *>(reinterpret_cast<uint8_t *>(&sm) + kFixedSmem);
     __syncthreads();
-    if (threadIdx.x == 0) sm.n_cl = 0;
+    for (uint32_t i = threadIdx.x; i < kClauseSet; i += blockDim.x) mh.set[i] = kNoClause;
+    if (threadIdx.x == 0) {
+        sm.n_cl = 0;
+        mh.full_seen = 0;
+    }
     __syncthreads();
     for (uint32_t idx = threadIdx.x; idx < S * S; idx += blockDim.x) {
         const uint32_t i = idx / S, j = idx - i * S;
         if (j < i) continue;
         const uint32_t rg = slots_of_gaps(P, range_mask(i, j));
-        if ((sm.acc_intra[i] >> j) & 1u) mh_cl(sm)[atomicAdd(&sm.n_cl, 1u)] = rg;
-        if ((sm.acc_inter[i] >> j) & 1u) mh_cl(sm)[atomicAdd(&sm.n_cl, 1u)] = rg & P.grid_mask;
+        if ((sm.acc_intra[i] >> j) & 1u) add_clause(sm, mh, rg);
+        if ((sm.acc_inter[i] >> j) & 1u) add_clause(sm, mh, rg & P.grid_mask);
     }
     __syncthreads();
 }
@@ -1059,92 +1097,19 @@ __device__ void loop_step(Smem &sm, MhsSmem &mh) {
     __syncthreads();
 }
 
-// Bitonic sort of the clause list padded to a power of two, then unique
-// compaction into out->clauses; returns the number of distinct clauses.
-__device__ uint32_t sort_unique_clauses(Smem &sm, gr_repair_result *out) {
-    const uint32_t n = sm.n_cl;
-    uint32_t np2 = 32;
-    while (np2 < n) np2 <<= 1;
-    for (uint32_t i = threadIdx.x + n; i < kClauseCap; i += blockDim.x) mh_cl(sm)[i] = 0xFFFFFFFFu;
-    __syncthreads();
-    for (uint32_t k = 2; k <= np2; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = threadIdx.x; i < np2; i += blockDim.x) {
-                const uint32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const bool up = (i & k) == 0;
-                    const uint32_t a = mh_cl(sm)[i], b = mh_cl(sm)[ixj];
-                    if ((a > b) == up) {
-                        mh_cl(sm)[i] = b;
-                        mh_cl(sm)[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // unique: position of element i = number of first occurrences before it
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t groups = np2 / 32u;
-    for (uint32_t g = warp; g < groups; g += nw) {
-        const uint32_t i = g * 32u + lane;
-        const bool first = mh_cl(sm)[i] != 0xFFFFFFFFu && (i == 0 || mh_cl(sm)[i] != mh_cl(sm)[i - 1]);
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
-        if (lane == 0) sm.scan[g] = __popc(bal);
-    }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t v = lane < groups ? sm.scan[lane] : 0u;
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
-            if (lane >= o) v += t;
-        }
-        sm.scan[lane] = v;  // inclusive; lanes beyond the groups repeat the total
-    }
-    __syncthreads();
-    const uint32_t n_unique = sm.scan[groups - 1];
-    for (uint32_t g = warp; g < groups; g += nw) {
-        const uint32_t i = g * 32u + lane;
-        const bool first = mh_cl(sm)[i] != 0xFFFFFFFFu && (i == 0 || mh_cl(sm)[i] != mh_cl(sm)[i - 1]);
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, first);
-        const uint32_t base = g ? sm.scan[g - 1] : 0u;
-        if (first) out->clauses[base + __popc(bal & ((1u << lane) - 1u))] = mh_cl(sm)[i];
-    }
-    __syncthreads();
-    return n_unique;
-}
-
 // The program's result: status, mask, weight, the sorted unique clause list,
 // the trajectory and the counters.
 __device__ void write_result(Smem &sm, gr_repair_result *out) {
     const DevProg &P = sm.prog;
-    if (threadIdx.x == 0) sm.scan[0] = 0;  // ordered by build_clauses' barriers
     build_clauses(sm);
-    const uint32_t n = sm.n_cl;
-    uint32_t n_unique;
-    if (n <= 128) {
-        // few clauses: each first occurrence goes straight to its rank among
-        // the distinct clauses (two barriers instead of a sorting network)
-        MhsSmem &mh = *reinterpret_cast<MhsSmem *>(reinterpret_cast<uint8_t *>(&sm) + kFixedSmem);
-        const uint32_t *cl = mh.cl;
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint32_t c = cl[i];
-            bool first = true;
-            for (uint32_t j = 0; j < i && first; ++j) first = cl[j] != c;
-            mh.pc[i] = first ? 1u : 0u;
-            if (first) atomicAdd(&sm.scan[0], 1u);
-        }
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-            if (!mh.pc[i]) continue;
-            const uint32_t c = cl[i];
-            uint32_t pos = 0;
-            for (uint32_t j = 0; j < n; ++j) pos += (mh.pc[j] && cl[j] < c) ? 1u : 0u;
-            out->clauses[pos] = c;
-        }
-        n_unique = sm.scan[0];
-    } else {
-        n_unique = sort_unique_clauses(sm, out);
+    // the listed clauses are distinct: each goes straight to its rank
+    const uint32_t n_unique = sm.n_cl;
+    const uint32_t *cl = mh_cl(sm);
+    for (uint32_t i = threadIdx.x; i < n_unique; i += blockDim.x) {
+        const uint32_t c = cl[i];
+        uint32_t pos = 0;
+        for (uint32_t j = 0; j < n_unique; ++j) pos += cl[j] < c ? 1u : 0u;
+        out->clauses[pos] = c;
     }
     for (uint32_t i = threadIdx.x + n_unique; i < GR_MAX_CLAUSES; i += blockDim.x) out->clauses[i] = 0;
     for (uint32_t i = threadIdx.x; i < GR_MAX_ITERS; i += blockDim.x) out->traj[i] = i < sm.iters ? sm.traj[i] : 0u;

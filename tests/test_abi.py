@@ -294,6 +294,18 @@ def test_packer_places_slots(lib):
             assert int(d[GAPS0 + 4 * z:GAPS0 + 4 * z + 4].view(np.uint32)[0]) == want
 
 
+def test_program_without_slots_takes_empty_places(lib):
+    """A one-statement program laid out as sites has no slot and an empty
+    place list: the binding gives no places and the program validates and
+    packs."""
+    from _tiny import random_program, with_sites
+
+    p = with_sites(random_program(0, s_min=1, s_max=1), 0)
+    assert p.n_stmts == 1 and len(p.slot_pos) == 0
+    gb.validate(p)
+    gb.pack([p, _prog()])
+
+
 @pytest.mark.parametrize("pos,msg", [([0, 7], "place"), ([0] * 33, "more than 32 slots")])
 def test_validation_rejects_bad_places(lib, pos, msg):
     p = _prog()

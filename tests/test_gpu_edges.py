@@ -134,3 +134,23 @@ def test_many_blocks_that_differ(gb):
     torch.cuda.synchronize()
     for g, w in zip(db.results(), want):
         _same(g, w)
+
+
+def test_clause_of_all_slots(gb):
+    """A clause holding all 32 slots (every bit set) among more than 128
+    clauses: 25 statements that all write one shared word, so every pair of
+    statements races and pair (0, 24) is separated by every slot; the empty
+    clause of each statement's self race makes the program unrepairable after
+    the first check."""
+    pos = [g for g in range(24) for _ in range(2 if g < 8 else 1)]
+    level = [1 if (g < 8 and k == 1) else 0 for g in range(24) for k in range(2 if g < 8 else 1)]
+    p = synth.make_program([{"op": "W", "a": 0, "b": 0}] * 25, blocks=1, threads=4, m_shared=1,
+                           slot_pos=pos, slot_level=level, slot_weight=[1] * 32)
+    assert p.n_slots == 32
+    w0 = oracle.check(p, 0)
+    cls = oracle.clauses(p, w0)
+    assert len(cls) == 301 and cls[0] == 0 and cls[-1] == 0xFFFFFFFF
+    for strategy in (0, 1):
+        for g in (gb.repair_batch([p], strategy=strategy)[0], gb.repair_plain(p, strategy=strategy)):
+            assert (g["status"], g["iters"], g["traj"]) == (1, 1, [0])
+            assert g["clauses"] == cls

@@ -356,6 +356,23 @@ def test_site_cases(gb, case):
                 assert got[key] == exp[key], (fn.__name__, key)
 
 
+def test_greedy_counts_distinct_clauses(gb):
+    """The greedy strategy's hit counts are over the clause set: two witness
+    pairs with the same clause (a site's block and grid candidates make such
+    pairs) count once.  Seed 3048 of this family is a program whose greedy
+    trajectory changes if they count twice."""
+    from _tiny import with_sites
+
+    progs = [with_sites(random_program(s, s_max=7), s) for s in range(3000, 3100)]
+    want = oracle.repair_batch(progs, strategy=1)
+    for p, g, w in zip(progs, gb.repair_batch(progs, strategy=gb.STRATEGY_MHS), want):
+        _same_result(g, w, p.slot_pos)
+    _same_result(gb.repair_plain(progs[48], strategy=gb.STRATEGY_MHS), want[48], progs[48].slot_pos)
+    wide, _ = _wide(gb, progs, strategy=1)
+    for w, o in zip(wide, want):
+        _same_result(w, o, None)
+
+
 def test_site_programs_match_oracle(gb):
     from _tiny import random_loop_program, with_sites
 
