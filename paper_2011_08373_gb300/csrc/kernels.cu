@@ -169,17 +169,18 @@ __device__ void load_program(Smem &sm, const DevProg *gp) {
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (uint32_t s = warp; s < S; s += nwarps) {
         const uint32_t k = sm.prog.stmts[s].gk, r = sm.prog.stmts[s].gr;
-        uint32_t n = 0;
-        for (uint32_t word = 0; word < 32u; ++word) {
-            uint32_t bits = 0;
-            if (word < nw) {
-                const uint32_t tid = word * 32u + lane;
-                const bool on = tid < T && (k == 0 || tid % k == r);
-                bits = __ballot_sync(0xFFFFFFFFu, on);
-                n += __popc(bits);
-            }
-            if (lane == 0) sm.act[s][word] = bits;
+        // tid mod k for tid = 32 * word + lane, advanced one word at a time
+        const uint32_t kk = k ? k : 1u, step = 32u % kk;
+        uint32_t m = lane % kk, n = 0, mine = 0;
+        for (uint32_t word = 0; word < nw; ++word) {
+            const bool on = word * 32u + lane < T && (k == 0 || m == r);
+            const uint32_t bits = __ballot_sync(0xFFFFFFFFu, on);
+            n += __popc(bits);
+            if (lane == word) mine = bits;
+            m += step;
+            if (m >= kk) m -= kk;
         }
+        sm.act[s][lane] = mine;  // words past the launch's threads stay zero
         if (lane == 0) sm.nact[s] = n;
     }
     __syncthreads();
@@ -785,24 +786,26 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
         }
         mh.w8[q][byte] = v;
     }
-    if (tid == 0) {
-        uint32_t hw[GR_MAX_SLOTS];
-        for (uint32_t i = 0; i < rh; ++i) hw[i] = mh.wc[L + i];
-        for (uint32_t i = 1; i < rh; ++i) {
-            const uint32_t x = hw[i];
-            uint32_t j = i;
-            while (j > 0 && hw[j - 1] > x) {
-                hw[j] = hw[j - 1];
-                --j;
+    if (tid < 32) {
+        // lb[k] = the sum of the k lightest high weights: each lane puts its
+        // weight at its rank (ties by index), then an inclusive scan
+        const uint32_t v = tid < rh ? mh.wc[L + tid] : 0u;
+        if (tid < rh) {
+            uint32_t rank = 0;
+            for (uint32_t j = 0; j < rh; ++j) {
+                const uint32_t u = mh.wc[L + j];
+                rank += (u < v || (u == v && j < tid)) ? 1u : 0u;
             }
-            hw[j] = x;
+            mh.lb[rank + 1u] = v;
         }
-        uint32_t acc = 0;
-        mh.lb[0] = 0;
-        for (uint32_t i = 0; i < rh; ++i) {
-            acc += hw[i];
-            mh.lb[i + 1] = acc;
+        __syncwarp();
+        uint32_t acc = tid < rh ? mh.lb[tid + 1u] : 0u;
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, acc, o);
+            if (tid >= o) acc += t;
         }
+        if (tid < rh) mh.lb[tid + 1u] = acc;
+        if (tid == 0) mh.lb[0] = 0;
     }
     __syncthreads();
     const uint32_t VL = L == 5 ? 0xFFFFFFFFu : ((1u << (1u << L)) - 1u);
@@ -995,7 +998,7 @@ __device__ void build_clauses(Smem &sm) {
 }
 
 // Initial state: remove mode probes E; repair mode starts at MHS(empty) = E.
-__device__ void loop_init(Smem &sm, MhsSmem &mh, const gr_options &opts) {
+__device__ void loop_init(Smem &sm, const gr_options &opts) {
     const DevProg &P = sm.prog;
     if (threadIdx.x == 0) {
         sm.forced = P.mode == GR_MODE_REPAIR ? P.existing : 0u;
@@ -1016,17 +1019,20 @@ __device__ void loop_init(Smem &sm, MhsSmem &mh, const gr_options &opts) {
         sm.acc_inter[threadIdx.x] = 0;
     }
     __syncthreads();
-    if (P.mode != GR_MODE_REMOVE) {
-        mhs_solve(sm, mh, P.n_slots, P.weights, 0, P.neg, P.n_neg, sm.forced, sm.forbidden);
-        if (threadIdx.x == 0) {
-            if (sm.sol_found) {
-                sm.mask = sm.sol_mask;
-            } else {
-                sm.status = GR_UNREPAIRABLE;
-                sm.done = 1;
-            }
+    if (P.mode != GR_MODE_REMOVE && threadIdx.x == 0) {
+        // Solve over no positive clause: every admissible mask contains the
+        // forced set, so the forced set itself is the lowest key, unless it
+        // meets a forbidden slot or holds all slots of a negative clause (then
+        // so does every mask containing it)
+        bool ok = (sm.forced & sm.forbidden) == 0u;
+        for (uint32_t c = 0; c < P.n_neg && ok; ++c)
+            if ((sm.forced & P.neg[c]) == P.neg[c]) ok = false;
+        if (ok) {
+            sm.mask = sm.forced;
+        } else {
+            sm.status = GR_UNREPAIRABLE;
+            sm.done = 1;
         }
-        __syncthreads();
     }
     if (threadIdx.x == 0 && !sm.done && sm.iters >= sm.max_iters) {
         sm.status = GR_ITER_CAP;
@@ -1275,7 +1281,7 @@ __global__ void __launch_bounds__(NT, MINB)
         const uint16_t *trace = traces + sm.prog.trace_off;
         const uint64_t *sgm = segmask + sm.prog.segmask_off;
         const uint32_t *sgr = segrange + sm.prog.segmask_off;
-        loop_init(sm, *d.mh, opts);
+        loop_init(sm, opts);
         while (!sm.done) {
             const uint32_t mask = sm.mask;
             prepare_check(sm, mask);
@@ -1378,7 +1384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     Smem &sm = *d.sm;
     const ArenaView V = view(arena);
     load_program(sm, &V.progs[p]);
-    loop_init(sm, *d.mh, opts);
+    loop_init(sm, opts);
     state_from_smem(sm, st);
 }
 
@@ -1477,7 +1483,7 @@ __global__ void __launch_bounds__(kWideThreads, 2)
     const uint32_t p = blockIdx.x;
     if (p == 0 && threadIdx.x == 0) *W.ctl = WideCtl{0u, 0u, 0u, 0u};
     load_program(sm, &V.progs[p]);
-    loop_init(sm, *d.mh, opts);
+    loop_init(sm, opts);
     state_from_smem(sm, &W.st[p]);
     zero_witness(&W.wit[p]);
     if (sm.done) write_result(sm, &out[p]);
