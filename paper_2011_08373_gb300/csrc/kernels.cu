@@ -34,7 +34,8 @@ struct MhsSmem {
     uint32_t pc[kClauseCap];   // preprocessed positive clauses (0 = dropped)
     uint32_t khi[kClauseCap];  // kept clauses: compact high part
     uint32_t klo[kClauseCap];  // kept clauses: low-part hit pattern over 32 low assignments
-    uint32_t set[kClauseSet];  // open-addressing set of the clauses built so far
+    uint32_t set[kClauseSet];  // open-addressing set of the clauses built so far; the
+                               // solver's size-sorted clauses after that
     uint32_t nhi[kClauseCap];
     uint32_t nlo[kClauseCap];
     uint32_t w8[4][256];       // weight of each byte of the high part
@@ -43,6 +44,7 @@ struct MhsSmem {
     uint32_t wc[GR_MAX_SLOTS]; // compact weights
     uint32_t n_kept, n_negk, R, U, unsat;
     uint32_t full_seen;  // the clause of all 32 slots (the set's empty marker) was built
+    uint32_t size_at[33];  // counting sort of the positive clauses by size
 };
 
 struct Smem {
@@ -474,25 +476,21 @@ __device__ void prepare_check(Smem &sm, uint32_t mask) {
     const DevProg &P = sm.prog;
     const uint32_t S = P.n_stmts;
     if (threadIdx.x < 32) {
-        const uint32_t s = threadIdx.x;
-        const uint32_t gaps = gap_mask(P, mask);
+        const uint32_t s = threadIdx.x, bit = 1u << s;
         sm.rows_intra[s] = 0;
         sm.rows_inter[s] = 0;
+        uint32_t pi = 0, px = 0;
         if (s < S) {
-            sm.ph_intra[s] = phase_of(s, gaps, S);
-            sm.ph_inter[s] = phase_of(s, gap_mask(P, mask & P.grid_mask), S);
-        } else {
-            sm.ph_intra[s] = sm.ph_inter[s] = 0;
+            pi = phase_of(s, gap_mask(P, mask), S);
+            px = phase_of(s, gap_mask(P, mask & P.grid_mask), S);
         }
-        __syncwarp();
+        sm.ph_intra[s] = pi;
+        sm.ph_inter[s] = px;
+        // rows with a write in their phase (of their own array)
+        const uint32_t sh = __ballot_sync(0xFFFFFFFFu, (P.shared_rows & bit) && (pi & P.shared_rows & P.write_mask));
+        const uint32_t gi = __ballot_sync(0xFFFFFFFFu, (P.global_rows & bit) && (pi & P.global_rows & P.write_mask));
+        const uint32_t gx = __ballot_sync(0xFFFFFFFFu, (P.global_rows & bit) && (px & P.global_rows & P.write_mask));
         if (s == 0) {
-            uint32_t sh = 0, gi = 0, gx = 0;
-            for (uint32_t t = 0; t < S; ++t) {
-                const uint32_t bit = 1u << t;
-                if ((P.shared_rows & bit) && (sm.ph_intra[t] & P.shared_rows & P.write_mask)) sh |= bit;
-                if ((P.global_rows & bit) && (sm.ph_intra[t] & P.global_rows & P.write_mask)) gi |= bit;
-                if ((P.global_rows & bit) && (sm.ph_inter[t] & P.global_rows & P.write_mask)) gx |= bit;
-            }
             sm.rel_sh = sh;
             sm.rel_gi = gi;
             sm.rel_gx = (P.blocks > 1) ? gx : 0u;
@@ -550,15 +548,16 @@ __device__ void pair_counts(Smem &sm) {
 __device__ void check_misc(Smem &sm, uint32_t mask) {
     const DevProg &P = sm.prog;
     const uint32_t S = P.n_stmts, T = P.threads;
-    if (threadIdx.x == 0) {
-        uint32_t dv = 0;
-        for (uint32_t t = mask & P.guarded_slots; t; t &= t - 1u) {
-            const uint32_t k = __ffs(t) - 1u;
+    if (threadIdx.x < 32) {  // lane k: does enabled guarded slot k diverge?
+        const uint32_t k = threadIdx.x;
+        bool dv = false;
+        if (((mask & P.guarded_slots) >> k) & 1u) {
             const uint32_t gk = P.slot_gk[k], gr = P.slot_gr[k];
             const uint32_t cnt = T > gr ? (T - 1u - gr) / gk + 1u : 0u;
-            if (cnt > 0 && cnt < T) dv |= 1u << k;
+            dv = cnt > 0 && cnt < T;
         }
-        sm.diverge = dv;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, dv);
+        if (k == 0) sm.diverge = b;
     }
     unsigned long long local = 0;
     const uint32_t gaps = gap_mask(P, mask), grid_gaps = gap_mask(P, mask & P.grid_mask);
@@ -674,18 +673,17 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
         mh.unsat = (forced & forbidden) ? 1u : 0u;
         sm.best = ~0ull;
     }
+    if (tid < 33) mh.size_at[tid] = 0;
     __syncthreads();
-    const uint32_t n_cl4 = (n_cl + 3u) >> 2;
-    for (uint32_t i = tid; i < 4u * n_cl4; i += nt) {
+    for (uint32_t i = tid; i < n_cl; i += nt) {
+        const uint32_t c = mh_cl(sm)[i];
         uint32_t pc = 0;
-        if (i < n_cl) {
-            const uint32_t c = mh_cl(sm)[i];
-            if (!(c & forced)) {
-                pc = c & ~forbidden;
-                if (!pc) mh.unsat = 1;
-            }
+        if (!(c & forced)) {
+            pc = c & ~forbidden;
+            if (!pc) mh.unsat = 1;
+            else atomicAdd(&mh.size_at[__popc(pc)], 1u);
         }
-        mh.pc[i] = pc;  // zero past the last clause: four at a time below
+        mh.pc[i] = pc;
     }
     __syncthreads();
     if (mh.unsat) {
@@ -693,18 +691,36 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
         __syncthreads();
         return;
     }
-    // drop every clause that contains another one (equal clauses: keep the first)
-    const uint4 *pc4 = reinterpret_cast<const uint4 *>(mh.pc);
+    // the remaining clauses in order of size (counting sort): the first of
+    // each size by an exclusive scan, then each clause to its place
+    if (tid < 32) {
+        const uint32_t v = mh.size_at[tid + 1u];
+        uint32_t incl = v;
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (tid >= o) incl += t;
+        }
+        mh.size_at[tid + 1u] = incl - v;
+    }
+    __syncthreads();
     for (uint32_t i = tid; i < n_cl; i += nt) {
-        const uint32_t c = mh.pc[i];
-        if (!c) continue;
-        // clause j drops clause i when it is a subset (equal: the earlier one)
-        auto drops = [&](uint32_t d, uint32_t j) { return d && j != i && (d & ~c) == 0 && (d != c || j < i); };
+        const uint32_t pc = mh.pc[i];
+        if (pc) mh.set[atomicAdd(&mh.size_at[__popc(pc)], 1u)] = pc;
+    }
+    __syncthreads();
+    // drop every clause that contains another one.  In size order only an
+    // earlier clause can be a subset (of two equal clauses the later one is
+    // dropped), and the small clauses that drop most others come first.
+    const uint32_t n_sorted = mh.size_at[32];  // the end of the last size
+    const uint32_t *sorted = mh.set;
+    const uint4 *sorted4 = reinterpret_cast<const uint4 *>(mh.set);
+    for (uint32_t i = tid; i < n_sorted; i += nt) {
+        const uint32_t c = sorted[i];
         bool keep = true;
-        for (uint32_t q = 0; q < n_cl4 && keep; ++q) {
-            const uint4 d = pc4[q];
-            keep = !(drops(d.x, 4u * q) || drops(d.y, 4u * q + 1u) || drops(d.z, 4u * q + 2u) ||
-                     drops(d.w, 4u * q + 3u));
+        for (uint32_t j = 0; j < i && keep; j += 4u) {
+            const uint4 d = sorted4[j >> 2];
+            keep = (d.x & ~c) != 0 && (j + 1u >= i || (d.y & ~c) != 0) && (j + 2u >= i || (d.z & ~c) != 0) &&
+                   (j + 3u >= i || (d.w & ~c) != 0);
         }
         if (keep) {
             if ((c & (c - 1u)) == 0) {
@@ -779,6 +795,7 @@ __device__ void mhs_solve(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_t
     }
     for (uint32_t e = tid; e < 4 * 256; e += nt) {
         const uint32_t q = e >> 8, byte = e & 255u;
+        if (q * 8u >= rh && byte) continue;  // bytes past the high part are zero: only entry 0 is read
         uint32_t v = 0;
         for (uint32_t b = 0; b < 8; ++b) {
             const uint32_t hb = q * 8u + b;
@@ -1046,29 +1063,33 @@ __device__ void loop_init(Smem &sm, const gr_options &opts) {
 __device__ void loop_step(Smem &sm, MhsSmem &mh) {
     const DevProg &P = sm.prog;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        sm.traj[sm.iters] = sm.mask;
-        sm.iters += 1;
-        sm.access_pairs += sm.pairs;
-        uint32_t any = sm.diverge;
-        for (uint32_t i = 0; i < P.n_stmts; ++i) any |= sm.rows_intra[i] | sm.rows_inter[i];
-        sm.step = 0;  // a new proposal is needed
-        if (!any && !sm.probe) {
-            if (sm.greedy) {  // a clean greedy proposal: one exact query decides
-                sm.greedy = 0;
-                sm.step = 1;
+    if (threadIdx.x < 32) {  // lane i: witness row i (rows past the instances are zero)
+        const uint32_t i = threadIdx.x;
+        const uint32_t ra = sm.rows_intra[i], re = sm.rows_inter[i];
+        const bool clean = !__any_sync(0xFFFFFFFFu, (ra | re) != 0u) && !sm.diverge && !sm.probe;
+        if (!clean) {
+            sm.acc_intra[i] |= ra;
+            sm.acc_inter[i] |= re;
+        }
+        __syncwarp();  // every lane has read probe before lane 0 clears it
+        if (i == 0) {
+            sm.traj[sm.iters] = sm.mask;
+            sm.iters += 1;
+            sm.access_pairs += sm.pairs;
+            sm.step = 0;  // a new proposal is needed
+            if (clean) {
+                if (sm.greedy) {  // a clean greedy proposal: one exact query decides
+                    sm.greedy = 0;
+                    sm.step = 1;
+                } else {
+                    sm.status = GR_REPAIRED;
+                    sm.done = 1;
+                    sm.step = 2;
+                }
             } else {
-                sm.status = GR_REPAIRED;
-                sm.done = 1;
-                sm.step = 2;
+                sm.probe = 0;
+                sm.forbidden |= sm.diverge;
             }
-        } else {
-            sm.probe = 0;
-            for (uint32_t i = 0; i < P.n_stmts; ++i) {
-                sm.acc_intra[i] |= sm.rows_intra[i];
-                sm.acc_inter[i] |= sm.rows_inter[i];
-            }
-            sm.forbidden |= sm.diverge;
         }
     }
     __syncthreads();
