@@ -52,7 +52,7 @@ struct DevProg {
     uint32_t global_rows, guarded_slots;
     uint32_t blk_invariant;  // 1: every block has the same same-block witnesses (see the packer)
     uint32_t general;      // 1: counted loops or explicit slot places (gaps differ from slots)
-    uint64_t trace_off;    // u16 elements from the scratch trace base; layout [S][B][t_pad]
+    uint64_t trace_off;    // u16 elements from the scratch trace base; layout [S][B][t_pad], unit order
     uint64_t segmask_off;  // element index of the program's [S][B] segment masks and ranges
     uint32_t weights[GR_MAX_SLOTS];
     uint16_t slot_gk[GR_MAX_SLOTS];

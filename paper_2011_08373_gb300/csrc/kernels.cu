@@ -2,13 +2,17 @@
 // Section 2.4) over concrete access programs.
 //
 //   k_expand        : address traces, one u16 word address per (statement,
-//                     thread), layout [S][B][t_pad], plus per-(statement, block)
-//                     masks of the 1,024-word chunks touched.
+//                     thread), layout [S][B][t_pad] with a segment's threads in
+//                     unit order (8 per unit, spaced so that the 32 units of a
+//                     warp read 32 consecutive threads at a time), plus per
+//                     (statement, block) the 1,024-word chunks touched and the
+//                     address range.
 //   owner tables    : the check (Verify).  For each address of a chunk tile, a
 //                     shared-memory table holds per statement the one thread
 //                     (same-block pass) or block (cross-block pass) that touched
-//                     it, or MULTI.  Two plain-store passes build it without
-//                     atomics; a scan of the table emits the witness bitmaps.
+//                     it, or MULTI: a CAS installs each access.  A probe pass
+//                     then reads, at every access, the entries of the pending
+//                     partner statements and emits the witness bitmaps.
 //   mhs_solve       : exact minimum-weight hitting set (Solve), bit-sliced: the
 //                     low 5 compact variables ride in the bits of a 32-bit word,
 //                     the rest are enumerated by popcount level (Gosper order)
@@ -165,24 +169,35 @@ __device__ void load_program(Smem &sm, const DevProg *gp) {
     uint4 *dst = reinterpret_cast<uint4 *>(&sm.prog);
     for (uint32_t i = threadIdx.x; i < sizeof(DevProg) / 16; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    // active-thread bitmaps: one ballot per 32 threads of a statement (words
-    // past the launch's threads are zero), and the count of active threads
-    const uint32_t S = sm.prog.n_stmts, T = sm.prog.threads, nw = (T + 31u) >> 5;
+    // active-thread bitmaps in the traces' unit order: byte v of a row holds
+    // the 8 threads of unit v (unit v of group g: threads 256 g + (v mod 32) +
+    // U e, U = the group's units); bytes past the units are zero
+    const uint32_t S = sm.prog.n_stmts, T = sm.prog.threads, nv = sm.prog.t_pad >> 3;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (uint32_t s = warp; s < S; s += nwarps) {
-        const uint32_t k = sm.prog.stmts[s].gk, r = sm.prog.stmts[s].gr;
-        // tid mod k for tid = 32 * word + lane, advanced one word at a time
-        const uint32_t kk = k ? k : 1u, step = 32u % kk;
-        uint32_t m = lane % kk, n = 0, mine = 0;
-        for (uint32_t word = 0; word < nw; ++word) {
-            const bool on = word * 32u + lane < T && (k == 0 || m == r);
-            const uint32_t bits = __ballot_sync(0xFFFFFFFFu, on);
-            n += __popc(bits);
-            if (lane == word) mine = bits;
-            m += step;
-            if (m >= kk) m -= kk;
+        const uint32_t k = sm.prog.stmts[s].gk, r = sm.prog.stmts[s].gr, kk = k ? k : 1u;
+        uint32_t n = 0;
+        for (uint32_t g = 0; g < 4u; ++g) {  // unit v = 32 g + lane (at most 128 units)
+            const uint32_t v = 32u * g + lane;
+            uint32_t a8 = 0;
+            if (v < nv) {
+                const uint32_t U = min(32u, nv - 32u * g), t0 = 256u * g + lane;
+                // t mod k advanced by U threads at a time
+                const uint32_t du = U % kk;
+                uint32_t m = t0 % kk;
+                for (uint32_t e = 0; e < 8u; ++e) {
+                    if (t0 + U * e < T && (k == 0 || m == r)) a8 |= 1u << e;
+                    m += du;
+                    if (m >= kk) m -= kk;
+                }
+            }
+            n += __popc(a8);
+            uint32_t word = a8 << ((lane & 3u) * 8u);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+            word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+            if ((lane & 3u) == 0) sm.act[s][8u * g + (lane >> 2)] = word;
         }
-        sm.act[s][lane] = mine;  // words past the launch's threads stay zero
+        n = __reduce_add_sync(0xFFFFFFFFu, n);
         if (lane == 0) sm.nact[s] = n;
     }
     __syncthreads();
@@ -910,15 +925,25 @@ __device__ void mhs_greedy(Smem &sm, MhsSmem &mh, uint32_t n_vars, const uint32_
         __syncthreads();
         return;
     }
+    // every warp sweeps whole rounds of 32 clauses so that its ballots see full lanes
+    const uint32_t rounds = (n_cl + 31u) >> 5;
     for (;;) {
         const uint32_t x = *(volatile uint32_t *)&mh.R;
         if (tid < 32) cnt[tid] = 0;
         __syncthreads();
-        for (uint32_t i = tid; i < n_cl; i += nt) {
-            const uint32_t c = cl[i];
-            if (c & x) continue;
-            for (uint32_t t = c & ~forbidden; t; t &= t - 1u) atomicAdd(&cnt[__ffs(t) - 1u], 1u);
+        // lane v: the clauses not yet hit that slot v would hit, by one ballot
+        // per slot present in 32 clauses, then one atomic per lane and warp
+        uint32_t hits = 0;
+        for (uint32_t r = tid >> 5; r < rounds; r += nt >> 5) {
+            const uint32_t i = r * 32u + lane;
+            const uint32_t m = (i < n_cl && !(cl[i] & x)) ? (cl[i] & ~forbidden) : 0u;
+            for (uint32_t vs = __reduce_or_sync(0xFFFFFFFFu, m); vs; vs &= vs - 1u) {
+                const uint32_t v = __ffs(vs) - 1u;
+                const uint32_t n = __popc(__ballot_sync(0xFFFFFFFFu, (m >> v) & 1u));
+                if (lane == v) hits += n;
+            }
         }
+        if (hits) atomicAdd(&cnt[lane], hits);
         __syncthreads();
         if (tid < 32) {
             // lane k's candidate; reduce to the best by hits/weight, ties to the lower slot
@@ -1227,27 +1252,51 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
             uint16_t *out = traces + P.trace_off + (size_t)seg * tpad;
             uint64_t chunks = 0;
             uint32_t amin = 0xFFFFu, amax = 0;
-            for (uint32_t v = lane; v < (tpad >> 3); v += 32) {
-                const uint32_t t0 = v * 8u;
-                // x = (step * t + base) mod M, advanced by one thread at a time
-                uint32_t x = (uint32_t)(((uint64_t)step * t0 + base) % M);
+            const uint32_t nv = tpad >> 3;
+            // 32-bit arithmetic: step, base < M <= 65,536 and t < 1,024
+            const uint32_t gk = st.gk, gr = st.gr, dx32 = (step * 32u) % M, dg = (step * 256u) % M;
+            uint32_t xg = (step * lane + base) % M;  // the address at t = lane of group 0
+            for (uint32_t v = lane; v < nv; v += 32) {
+                // unit v of group g holds threads 256 g + (v mod 32) + U e, e = 0..7
+                // (U = the group's units), so that a warp's 32 units read 32
+                // consecutive threads at each e
+                const uint32_t g = v >> 5, U = min(32u, nv - 32u * g), t0 = 256u * g + lane;
+                // x = (step * t + base) mod M and t mod gk, advanced by U threads at a time
+                uint32_t x = xg;
+                const uint32_t dx = U == 32u ? dx32 : (step * U) % M;
+                uint32_t m = gk ? t0 % gk : 0u;
+                const uint32_t dm = gk ? U % gk : 0u;
+                // the 8 indices first, so that a permutation's 8 table loads
+                // (every index is below M, padding threads included) are in
+                // flight together
+                uint32_t av[8];
+                uint8_t on = 0;
+#pragma unroll
+                for (uint32_t e = 0; e < 8; ++e) {
+                    av[e] = x;
+                    if (t0 + U * e < T && (gk == 0 || m == gr)) on |= (uint8_t)(1u << e);
+                    x += dx;
+                    if (x >= M) x -= M;
+                    m += dm;
+                    if (m >= gk) m -= gk;
+                }
+                if (perm) {
+#pragma unroll
+                    for (uint32_t e = 0; e < 8; ++e) av[e] = V.perm[st.perm_off + av[e]];
+                }
                 uint32_t w4[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (uint32_t e = 0; e < 8; ++e) {
-                    const uint32_t t = t0 + e;
-                    uint32_t a = 0;
-                    if (t < T) {
-                        a = perm ? V.perm[st.perm_off + x] : x;
-                        if (st.gk == 0 || t % st.gk == st.gr) {
-                            chunks |= 1ull << (a >> kChunkShift);
-                            amin = min(amin, a);
-                            amax = max(amax, a);
-                        }
+                    const uint32_t a = t0 + U * e < T ? av[e] : 0u;
+                    if ((on >> e) & 1u) {
+                        chunks |= 1ull << (a >> kChunkShift);
+                        amin = min(amin, a);
+                        amax = max(amax, a);
                     }
                     w4[e >> 1] |= (a & 0xFFFFu) << ((e & 1u) * 16u);
-                    x += step;
-                    if (x >= M) x -= M;
                 }
+                xg += dg;
+                if (xg >= M) xg -= M;
                 reinterpret_cast<uint4 *>(out)[v] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
             }
             const uint32_t lo32 = __reduce_or_sync(0xFFFFFFFFu, (uint32_t)chunks);
