@@ -376,8 +376,8 @@ def run_ours(args, rank, world, local):
             "config": {"workload": args.workload, "programs": n, "blocks": wl.blocks, "threads": wl.threads,
                        "stmts": wl.n_stmts, "m_words": wl.m_words, "seed": wl.seed,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
-                       "cta_shape": {"threads": [512, 256, 256, 1024][shape & 15],
-                                     "ctas_per_sm": [2, 3, 4, 1][shape & 15],
+                       "cta_shape": {"threads": [512, 256, 256, 1024, 384][shape & 15],
+                                     "ctas_per_sm": [2, 3, 4, 1, 3][shape & 15],
                                      "balanced_grid": bool(shape & 16), "picked_by": "autotuner"},
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e,

@@ -108,7 +108,7 @@ struct LaunchCfg {
 struct LaunchShape {
     uint32_t threads, ctas_per_sm;
 };
-constexpr uint32_t kNumShapes = 4;
+constexpr uint32_t kNumShapes = 5;
 constexpr uint32_t kShapeMask = 15u;      // LaunchCfg::shape: index into kShapes ...
 constexpr uint32_t kShapeBalanced = 16u;  // ... plus: grid cut so every CTA gets the same number of programs
 extern const LaunchShape kShapes[kNumShapes];

@@ -1685,7 +1685,7 @@ size_t dyn_bytes(uint32_t table_bytes) {
 }
 
 // The CTA shapes of the persistent kernels: {threads, CTAs per SM}.
-const LaunchShape kShapes[kNumShapes] = {{512, 2}, {256, 3}, {256, 4}, {1024, 1}};
+const LaunchShape kShapes[kNumShapes] = {{512, 2}, {256, 3}, {256, 4}, {1024, 1}, {384, 3}};
 
 template <typename F>
 static cudaError_t set_smem(F *f, uint32_t max_dynamic_smem) {
@@ -1713,10 +1713,12 @@ cudaError_t configure_kernels(uint32_t max_dynamic_smem) {
     if ((e = set_smem(k_repair<256, 3>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_repair<256, 4>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_repair<1024, 1>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_repair<384, 3>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<512, 2>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<256, 3>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<256, 4>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<1024, 1>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = set_smem(k_check<384, 3>, max_dynamic_smem)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1734,6 +1736,7 @@ cudaError_t launch_repair(const void *d_arena, uint32_t n, const gr_options &opt
         case 1: k_repair<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
         case 2: k_repair<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
         case 3: k_repair<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
+        case 4: k_repair<384, 3><<<cfg.grid, 384, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
         default: k_repair<512, 2><<<cfg.grid, 512, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
     }
     return cudaGetLastError();
@@ -1748,6 +1751,7 @@ cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_mask
         case 1: k_check<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
         case 2: k_check<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
         case 3: k_check<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
+        case 4: k_check<384, 3><<<cfg.grid, 384, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
         default: k_check<512, 2><<<cfg.grid, 512, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
     }
     return cudaGetLastError();
