@@ -266,23 +266,37 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
         if (keep) sm.row_list[__popc(bal & ((1u << lane) - 1u))] = lane;
         if (lane == 0) sm.pass_rows = involved;
-        sm.rlo[lane] = 0xFFFFu;
-        sm.rhi[lane] = 0u;
+        // address range of each row over the blocks of the pass: here for a
+        // few blocks (each lane its own row), by the whole CTA below otherwise
+        uint32_t lo = 0xFFFFu, hi = 0u;
+        if (nb <= 32u && keep) {
+            for (uint32_t bi = 0; bi < nb; ++bi) {
+                const uint32_t r = segrange[(size_t)lane * B + blk_lo + bi];
+                if ((r & 0xFFFFu) <= (r >> 16)) {
+                    lo = min(lo, r & 0xFFFFu);
+                    hi = max(hi, r >> 16);
+                }
+            }
+        }
+        sm.rlo[lane] = lo;
+        sm.rhi[lane] = hi;
     }
     __syncthreads();
     rows = sm.pass_rows;
     const uint32_t n_rows = __popc(rows);
     if (n_rows == 0) return;  // every candidate pair already witnessed
-    // address range of each row over the blocks of the pass
-    for (uint32_t u = threadIdx.x; u < S * nb; u += blockDim.x) {
-        const uint32_t st = u / nb, bi = u - st * nb;
-        if (!((rows >> st) & 1u)) continue;
-        const uint32_t r = segrange[(size_t)st * B + blk_lo + bi];
-        const uint32_t lo = r & 0xFFFFu, hi = r >> 16;
-        if (lo <= hi) {
-            atomicMin(&sm.rlo[st], lo);
-            atomicMax(&sm.rhi[st], hi);
+    if (nb > 32u) {
+        for (uint32_t u = threadIdx.x; u < S * nb; u += blockDim.x) {
+            const uint32_t st = u / nb, bi = u - st * nb;
+            if (!((rows >> st) & 1u)) continue;
+            const uint32_t r = segrange[(size_t)st * B + blk_lo + bi];
+            const uint32_t lo = r & 0xFFFFu, hi = r >> 16;
+            if (lo <= hi) {
+                atomicMin(&sm.rlo[st], lo);
+                atomicMax(&sm.rhi[st], hi);
+            }
         }
+        __syncthreads();  // the ranges, before the column ranges of each tile
     }
     const uint32_t cap = min(table_bytes / (2u * S * kChunkWords), kMaxTileChunks);
     if (cap == 0) {  // the host sizes the table for at least one chunk; never loop without progress
@@ -302,11 +316,12 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
             ++k;
         }
         const uint32_t cols = k * kChunkWords;
-        if (threadIdx.x < 64) {
-            const uint32_t c = threadIdx.x;
-            sm.chunk_slot[c] = ((sel >> c) & 1ull) ? (uint8_t)__popcll(sel & ((1ull << c) - 1ull)) : 0xFF;
-        }
-        __syncthreads();
+        // tile slot of each chunk of the tile (0xFF: not in it); the column
+        // ranges below take it from sel directly, so one barrier serves both
+        auto slot_of = [sel](uint32_t ch) -> uint32_t {
+            return ((sel >> ch) & 1ull) ? (uint32_t)__popcll(sel & ((1ull << ch) - 1ull)) : 0xFFu;
+        };
+        if (threadIdx.x < 64) sm.chunk_slot[threadIdx.x] = (uint8_t)slot_of(threadIdx.x);
         // column range of each row within this tile (the tile keeps address order)
         if (threadIdx.x < 32) {
             const uint32_t st = threadIdx.x;
@@ -315,14 +330,16 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
             if (st < S && ((rows >> st) & 1u) && lo <= hi) {
                 const uint32_t k0 = lo >> kChunkShift, k1 = hi >> kChunkShift;
                 for (uint32_t ch = k0; ch <= k1; ++ch) {
-                    if (sm.chunk_slot[ch] != 0xFF) {
-                        c0 = sm.chunk_slot[ch] * kChunkWords + (ch == k0 ? (lo & (kChunkWords - 1u)) : 0u);
+                    const uint32_t slot = slot_of(ch);
+                    if (slot != 0xFFu) {
+                        c0 = slot * kChunkWords + (ch == k0 ? (lo & (kChunkWords - 1u)) : 0u);
                         break;
                     }
                 }
                 for (uint32_t ch = k1 + 1; ch-- > k0;) {
-                    if (sm.chunk_slot[ch] != 0xFF) {
-                        c1 = sm.chunk_slot[ch] * kChunkWords + (ch == k1 ? (hi & (kChunkWords - 1u)) : kChunkWords - 1u);
+                    const uint32_t slot = slot_of(ch);
+                    if (slot != 0xFFu) {
+                        c1 = slot * kChunkWords + (ch == k1 ? (hi & (kChunkWords - 1u)) : kChunkWords - 1u);
                         break;
                     }
                 }
@@ -380,7 +397,9 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                         if (keep) sm.seg_list[at + __popc(bal & ((1u << lane) - 1u))] = code;
                     }
                 }
-                __syncthreads();
+                // publishes the segment list, or orders pass 0's installs after
+                // the clear; pass 1 without a new list follows pass 0's barrier
+                if (pass == 0 || (!identity && !one_batch)) __syncthreads();
                 const uint32_t n_list = identity ? min(n_segs - base, kSegCap) : sm.n_seg_list;
                 const uint32_t units = n_list * nv;
                 const bool hold = one_batch && units <= 2u * blockDim.x;
