@@ -30,8 +30,11 @@
  * Ownership and errors (every entry point).  The caller owns every input and
  * output buffer.  Host-pointer entry points copy their inputs during the call
  * and return after the result is in the caller's memory.  Inputs are
- * validated before any device work; a rejected call returns GR_EINVAL and
- * leaves the outputs untouched (gr_last_error() says why).  CUDA failures
+ * validated before any device work (one exception: gr_repair_batch checks
+ * that each permutation table holds every index once on the device, next to
+ * the repair, and reads that back before it copies any result); a rejected
+ * call returns GR_EINVAL and leaves the outputs untouched (gr_last_error()
+ * says why).  CUDA failures
  * return GR_ECUDA; a failed allocation returns GR_ENOMEM.  The library keeps
  * one device workspace per device, grown on demand and guarded by a mutex:
  * host-pointer calls from several threads are serialised.
@@ -223,7 +226,7 @@ gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode
 
 /* Minimum-weight hitting set (Section 2.3 definitions, Section 2.4 weighted
  * MaxSAT form) on the GPU: the least (weight, mask) over masks x of n_vars
- * (1..24) bits with forced <= x, x & forbidden == 0, x & pos[i] != 0 for
+ * (1..32) bits with forced <= x, x & forbidden == 0, x & pos[i] != 0 for
  * every positive clause and (x & neg[i]) != neg[i] for every negative clause.
  * w: n_vars weights in 1..GR_MAX_WEIGHT.  n_pos + n_neg <= GR_MAX_CLAUSES.
  * Returns GR_OK (outputs set) or GR_UNSAT (outputs set to 0). */

@@ -140,8 +140,9 @@ gr_status validate_loops(const gr_program *p, uint32_t idx) {
 }
 
 // Whether the M entries of tbl are a permutation of 0..M-1 (M values below M
-// marking M distinct entries); dst (may be NULL) receives them as u16.
-bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst) {
+// marking M distinct entries); dst (may be NULL) receives them as u16.  With
+// range_only (dst given) only whether every entry is below M.
+bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst, bool range_only) {
     uint8_t mark[GR_MAX_WORDS];
     uint32_t bad = 0;
     if (dst) {
@@ -154,6 +155,7 @@ bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst) {
             dst[i] = (uint16_t)v;
         }
         if (mx >= M) return false;
+        if (range_only) return true;
         memset(mark, 0, M);
         for (uint32_t i = 0; i < M; ++i) mark[dst[i]] = 1;
     } else {
@@ -379,7 +381,7 @@ gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n,
 }
 
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
-               uint8_t *arena, uint32_t *table_bad) {
+               uint8_t *arena, uint32_t *table_bad, bool range_only) {
     // zero everything but the permutation area, which is fully overwritten
     memset(arena, 0, L.perm_off);
     ArenaHeader *H = reinterpret_cast<ArenaHeader *>(arena);
@@ -503,7 +505,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
                 }
                 lo[at] = st.perm_off;
                 hi[at] = st.perm_off + M;
-                if (!table_to_u16(P.perm + st.perm_off, M, dst + st.perm_off) && table_bad) {
+                if (!table_to_u16(P.perm + st.perm_off, M, dst + st.perm_off, range_only) && table_bad) {
                     uint32_t cur = table_bad[p];
                     if (s < cur) table_bad[p] = s;
                 }
@@ -1038,22 +1040,53 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     if ((s = ws->arena.ensure(arena_max)) != GR_OK) return s;
     if ((s = ws->scratch.ensure(scratch_max)) != GR_OK) return s;
     if ((s = ws->out.ensure((size_t)n * sizeof(gr_repair_result))) != GR_OK) return s;
+    if ((s = ws->aux.ensure(256)) != GR_OK) return s;
     gr_repair_result *d_out = static_cast<gr_repair_result *>(ws->out.p);
+    uint32_t *d_perm_bad = static_cast<uint32_t *>(ws->aux.p);
+    bool any_perm = false;
+    for (uint32_t p = 0; p < n && !any_perm; ++p) any_perm = progs[p].perm && progs[p].perm_len;
+    if (any_perm) GR_CUDA(cudaMemsetAsync(d_perm_bad, 0, 4, st));
+    // Permutation tables: the packer checks the range of every entry while
+    // converting; that each index occurs once is checked on the device
+    // (k_perm_check) and read back before the results are copied.  Either way
+    // the lowest bad program is reported and `out` stays untouched.
+    auto bad_stmt = [&](uint32_t p) -> uint32_t {  // the first table of p that is not a permutation, or ~0u
+        const gr_program &P = progs[p];
+        for (uint32_t q = 0; q < P.n_stmts; ++q) {
+            const gr_stmt &t = P.stmts[q];
+            const uint32_t M = t.space == GR_SHARED ? P.m_shared : P.m_global;
+            if (t.kind == GR_PERM && !table_to_u16(P.perm + t.perm_off, M, nullptr)) return q;
+        }
+        return 0xFFFFFFFFu;
+    };
+    auto device_bad = [&](uint32_t *p_out) -> gr_status {  // waits for the stream
+        uint32_t word = 0;
+        if (any_perm) GR_CUDA(cudaMemcpyAsync(&word, d_perm_bad, 4, cudaMemcpyDeviceToHost, st));
+        GR_CUDA(cudaStreamSynchronize(st));
+        *p_out = word ? ~word : 0xFFFFFFFFu;
+        return GR_OK;
+    };
     std::vector<uint32_t> bad;
     for (uint32_t c = 0; c < K; ++c) {
         const uint32_t n_c = lo[c + 1] - lo[c];
         uint8_t *staging = ws->host_arena + soff[c];
-        // permutation tables are checked while they are converted; the lowest
-        // bad program is reported (earlier chunks' device work is discarded)
         bad.assign(n_c, 0xFFFFFFFFu);
-        pack_into(progs + lo[c], launches + lo[c], modes ? modes + lo[c] : nullptr, n_c, Ls[c], staging, bad.data());
+        pack_into(progs + lo[c], launches + lo[c], modes ? modes + lo[c] : nullptr, n_c, Ls[c], staging, bad.data(),
+                  true);
         for (uint32_t p = 0; p < n_c; ++p)
             if (bad[p] != 0xFFFFFFFFu) {
-                // earlier chunks may still run: wait so that no later call reuses their buffers early
-                if (c > 0) cudaStreamSynchronize(st);
+                // an entry out of range: a lower program may hold a repeat, in
+                // an earlier chunk (the device check has run) or in this one
+                uint32_t low = 0xFFFFFFFFu;
+                if ((s = device_bad(&low)) != GR_OK) return s;
+                for (uint32_t q = lo[c]; q < lo[c] + p && low == 0xFFFFFFFFu; ++q)
+                    if (bad_stmt(q) != 0xFFFFFFFFu) low = q;
+                if (low < lo[c] + p)
+                    return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", low, bad_stmt(low));
                 return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", lo[c] + p, bad[p]);
             }
         GR_CUDA(cudaMemcpyAsync(ws->arena.p, staging, Ls[c].arena_bytes, cudaMemcpyHostToDevice, st));
+        if (any_perm) GR_CUDA(launch_perm_check(ws->arena.p, n_c, lo[c], d_perm_bad, (uint32_t)ws->sms, st));
         // queue counter (and, for the first chunk, the error word) cleared
         GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, c == 0 ? 256 : 4, st));
         GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
@@ -1073,6 +1106,12 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
         LaunchCfg cfg = shape_cfg(*ws, n_c, it->second, cls.s_max);
         if (!cfg.table_bytes) cfg = choose_cfg(*ws, n_c, cls.s_max);
         GR_CUDA(launch_repair(ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, d_out + lo[c], cfg, st));
+    }
+    if (any_perm) {
+        uint32_t low = 0xFFFFFFFFu;
+        if ((s = device_bad(&low)) != GR_OK) return s;
+        if (low != 0xFFFFFFFFu)
+            return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", low, bad_stmt(low));
     }
     GR_CUDA(cudaMemcpyAsync(out, d_out, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost, st));
     return finish_sync(ws->scratch.p, st);

@@ -140,14 +140,21 @@ inline uint32_t exec_count(const gr_program &p) {
 size_t align_to(size_t x, size_t a);
 Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n);
 // table_bad (may be NULL): per program, the lowest statement whose permutation
-// table is not one (left as is when every table is)
+// table is not one (left as is when every table is).  range_only: only entries
+// at or above M count as bad (repeats are left to the device check,
+// launch_perm_check).
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
-               uint8_t *arena, uint32_t *table_bad = nullptr);
+               uint8_t *arena, uint32_t *table_bad = nullptr, bool range_only = false);
+bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst, bool range_only = false);
 LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status);
 void set_last_error(const char *msg);
 
 // Host-callable launchers (kernels.cu).
 cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint32_t grid, cudaStream_t st);
+// Device check that the batch's permutation tables are permutations (the
+// lowest failing program + base, complemented, into *d_bad by atomicMax).
+cudaError_t launch_perm_check(const void *d_arena, uint32_t n, uint32_t base, uint32_t *d_bad, uint32_t sms,
+                              cudaStream_t st);
 cudaError_t launch_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
                           gr_repair_result *d_out, LaunchCfg cfg, cudaStream_t st);
 cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,

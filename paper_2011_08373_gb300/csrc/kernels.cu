@@ -1241,7 +1241,7 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
     uint16_t *traces = reinterpret_cast<uint16_t *>(scratch + V.h->scratch_trace_off);
     uint64_t *segmask = reinterpret_cast<uint64_t *>(scratch + V.h->scratch_segmask_off);
     uint32_t *segrange = reinterpret_cast<uint32_t *>(scratch + V.h->scratch_segrange_off);
-    __shared__ DevStmt st_sh[GR_MAX_STMTS];
+    __shared__ __align__(16) DevStmt st_sh[GR_MAX_STMTS];  // filled by 16-byte stores
     __shared__ uint32_t hdr[4];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (uint64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -1326,6 +1326,55 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
                 segmask[P.segmask_off + seg] = ((uint64_t)hi32 << 32) | lo32;
                 segrange[P.segmask_off + seg] = amin | (amax << 16);
             }
+        }
+    }
+}
+
+// Permutation tables of a packed batch: each table a permutation statement
+// reads must hold every index below M exactly once (the host checked the
+// range while converting the tables to u16).  CTAs take programs; per table
+// a 65,536-bit map in shared memory marks the entries and the marks are
+// counted.  The lowest failing program, plus `base`, is kept as its
+// complement in *bad (atomicMax; 0 = none).
+__global__ void __launch_bounds__(256) k_perm_check(const uint8_t *__restrict__ arena, uint32_t base,
+                                                    uint32_t *__restrict__ bad) {
+    const ArenaView V = view(arena);
+    const uint32_t n = V.h->n_progs, tid = threadIdx.x;
+    __shared__ uint32_t bits[GR_MAX_WORDS / 32];
+    __shared__ uint32_t total, n_stmts;
+    __shared__ __align__(16) DevStmt st_sh[GR_MAX_STMTS];  // filled by 16-byte stores
+    for (uint32_t p = blockIdx.x; p < n; p += gridDim.x) {
+        const DevProg &P = V.progs[p];
+        __syncthreads();  // the previous program's statements are no longer read
+        if (tid < GR_MAX_STMTS * sizeof(DevStmt) / 16)
+            reinterpret_cast<uint4 *>(st_sh)[tid] = reinterpret_cast<const uint4 *>(P.stmts)[tid];
+        if (tid == 0) n_stmts = P.n_stmts;
+        __syncthreads();
+        for (uint32_t s = 0; s < n_stmts; ++s) {
+            const DevStmt &st = st_sh[s];
+            if (st.kind != GR_PERM) continue;
+            // loop instances of one statement share its table
+            bool again = false;
+            for (uint32_t q = 0; q < s && !again; ++q)
+                again = st_sh[q].kind == GR_PERM && st_sh[q].perm_off == st.perm_off && st_sh[q].m == st.m;
+            if (again) continue;
+            const uint32_t M = st.m, words = (M + 31u) >> 5;
+            for (uint32_t i = tid; i < words; i += blockDim.x) bits[i] = 0;
+            if (tid == 0) total = 0;
+            __syncthreads();
+            const uint16_t *tbl = V.perm + st.perm_off;
+            for (uint32_t i = tid; i < M; i += blockDim.x) {
+                const uint32_t v = tbl[i];
+                if (v < M) atomicOr(&bits[v >> 5], 1u << (v & 31u));  // an entry past M marks nothing
+            }
+            __syncthreads();
+            uint32_t c = 0;
+            for (uint32_t i = tid; i < words; i += blockDim.x) c += __popc(bits[i]);
+            c = __reduce_add_sync(0xFFFFFFFFu, c);
+            if ((tid & 31u) == 0 && c) atomicAdd(&total, c);
+            __syncthreads();
+            if (tid == 0 && total != M) atomicMax(bad, ~(base + p));  // M distinct marks: a permutation
+            __syncthreads();  // the map and the count, before the next table clears them
         }
     }
 }
@@ -1739,6 +1788,13 @@ cudaError_t configure_kernels(uint32_t max_dynamic_smem) {
     if ((e = set_smem(k_check<1024, 1>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<384, 3>, max_dynamic_smem)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+cudaError_t launch_perm_check(const void *d_arena, uint32_t n, uint32_t base, uint32_t *d_bad, uint32_t sms,
+                              cudaStream_t st) {
+    const uint32_t grid = n < 4u * sms ? (n ? n : 1u) : 4u * sms;
+    k_perm_check<<<grid, 256, 0, st>>>(static_cast<const uint8_t *>(d_arena), base, d_bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint32_t grid, cudaStream_t st) {

@@ -465,8 +465,10 @@ def test_blocks_that_differ(gb):
 
 
 def test_batch_rejects_bad_permutation_tables(gb):
-    """Host batch calls check permutation tables while packing them; the
-    lowest bad program is reported before any device work."""
+    """Batch calls reject a permutation table with a repeated entry: the
+    host-pointer repair checks repeats on the device and the range on the
+    host, the check batch and the plain path on the host; the lowest bad
+    program is reported and the outputs stay untouched."""
     good = synth.generate("batch1024_4x256_s24", 3)
     bad = synth.generate("batch1024_4x256_s24", 3, start=10)
     for p in bad:
@@ -506,3 +508,52 @@ def test_batch_rejects_bad_permutation_tables(gb):
     got = gb.repair_batch(good_big)
     for i in (0, 150, 300, 450, len(good_big) - 1):
         _same_result(got[i], oracle.repair(good_big[i]))
+
+
+
+def _spoil(p, how):
+    """A copy of p whose first permutation table holds a repeated entry
+    ("repeat") or an entry past the array ("range")."""
+    import copy
+
+    q = copy.deepcopy(p)
+    s = int(np.nonzero(q.kind == 2)[0][0])
+    off = int(q.perm_off[s])
+    q.perm = q.perm.copy()
+    if how == "repeat":
+        q.perm[off + 1] = q.perm[off]
+    else:
+        q.perm[off] = (q.m_shared if q.space[s] == 0 else q.m_global) + 5
+    return q, s
+
+
+def test_batch_reports_lowest_bad_table(gb):
+    """A repeat (found on the device) below an out-of-range entry (found by
+    the packer) is still the one reported, in the same chunk and across
+    chunks; an out-of-range entry alone is reported too."""
+    small = synth.generate("batch1024_4x256_s24", 8, blocks=2, threads=32, n_stmts=8, m_words=128)
+    perm_idx = [i for i, p in enumerate(small) if (p.kind == 2).any()]
+    assert len(perm_idx) >= 3
+    a, b = perm_idx[0], perm_idx[2]
+    progs = list(small)
+    progs[a], sa = _spoil(small[a], "repeat")
+    progs[b], _ = _spoil(small[b], "range")
+    with pytest.raises(gb.GrError) as e:
+        gb.repair_batch(progs)
+    assert e.value.code == gb.EINVAL and f"program {a} stmt {sa}:" in str(e.value)
+    progs = list(small)
+    progs[b], sb = _spoil(small[b], "range")
+    with pytest.raises(gb.GrError) as e:
+        gb.repair_batch(progs)
+    assert f"program {b} stmt {sb}:" in str(e.value)
+    # 600 programs go in four chunks: a repeat in the first, a bad range in the third
+    big = synth.generate("batch1024_4x256_s24", 600, blocks=2, threads=32, n_stmts=8, m_words=128)
+    i = next(j for j in range(10, 100) if (big[j].kind == 2).any())
+    k = next(j for j in range(330, 440) if (big[j].kind == 2).any())
+    big[i], si = _spoil(big[i], "repeat")
+    big[k], _ = _spoil(big[k], "range")
+    out = np.zeros(600, dtype=gb.RESULT_DTYPE)
+    with pytest.raises(gb.GrError) as e:
+        gb.repair_batch_raw(big, out=out)
+    assert f"program {i} stmt {si}:" in str(e.value)
+    assert not out.view(np.uint8).any()
