@@ -1013,7 +1013,10 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     // stream: the device arena and scratch are reused in order).  Results
     // gather in the device result buffer and reach `out` in one copy at the
     // end, so `out` stays untouched when a later chunk holds a bad table.
-    const uint32_t K = n >= 512 ? 4u : (n >= 256 ? 2u : 1u);
+    // Chunks keep at least 128 programs, and below 2,048 programs at most two:
+    // a launch of a few hundred programs takes about one program's latency
+    // (one per CTA), so more, smaller chunks leave the device behind the host.
+    const uint32_t K = n >= 2048 ? 4u : (n >= 256 ? 2u : 1u);
     std::vector<uint32_t> lo(K + 1);
     for (uint32_t c = 0; c <= K; ++c) lo[c] = (uint32_t)((uint64_t)n * c / K);
     std::vector<Layout> Ls(K);

@@ -546,7 +546,7 @@ def test_batch_reports_lowest_bad_table(gb):
     with pytest.raises(gb.GrError) as e:
         gb.repair_batch(progs)
     assert f"program {b} stmt {sb}:" in str(e.value)
-    # 600 programs go in four chunks: a repeat in the first, a bad range in the third
+    # 600 programs go in two chunks: a repeat in the first, a bad range in the second
     big = synth.generate("batch1024_4x256_s24", 600, blocks=2, threads=32, n_stmts=8, m_words=128)
     i = next(j for j in range(10, 100) if (big[j].kind == 2).any())
     k = next(j for j in range(330, 440) if (big[j].kind == 2).any())
