@@ -58,6 +58,8 @@ MUTANTS = [
     ("head_slot_taken_after_statement", "if (orc_pos(p, k) == st[z] - 1u) m |= 1u << k;",
      "if (orc_pos(p, k) == st[z - 1]) m |= 1u << k;"),
     ("slot_position_ignored", "return p->slot_pos ? p->slot_pos[k] : k;", "return k;"),
+    ("clauses_kept_as_multiset", "if (u == 0 || clauses[u - 1] != clauses[t]) clauses[u++] = clauses[t];",
+     "clauses[u++] = clauses[t];"),
 ]
 
 
