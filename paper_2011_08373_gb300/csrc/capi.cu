@@ -292,7 +292,10 @@ class HostPool {
     }
     template <typename F>
     void run(uint32_t n, F &body) {
-        const uint32_t parts = n >= 32 ? std::min<uint32_t>(n_workers_ + 1, (n + 15) / 16) : 1u;
+        // more parts than threads, taken in turn by the caller and the
+        // workers, so that programs of uneven size balance
+        const uint32_t threads = n_workers_ + 1;
+        const uint32_t parts = n >= 32 ? std::min<uint32_t>(4u * threads, (n + 7) / 8) : 1u;
         std::unique_lock<std::mutex> busy(use_, std::try_to_lock);
         if (parts <= 1 || !busy.owns_lock()) {
             body(0u, n);
@@ -304,14 +307,22 @@ class HostPool {
             job_ = [&body](uint32_t lo, uint32_t hi) { body(lo, hi); };
             n_ = n;
             per_ = per;
-            next_.store(1);  // part 0 runs on the calling thread
+            next_.store(0);
             parts_ = parts;
-            pending_ = parts - 1;
+            pending_ = parts;
             ++gen_;
         }
         cv_.notify_all();
-        body(0u, std::min(n, per));
+        uint32_t mine = 0;
+        for (;;) {
+            const uint32_t k = next_.fetch_add(1);
+            if (k >= parts) break;
+            const uint32_t lo = k * per, hi = std::min(n, lo + per);
+            if (lo < hi) body(lo, hi);
+            ++mine;
+        }
         std::unique_lock<std::mutex> g(mu_);
+        pending_ -= mine;
         done_.wait(g, [&] { return pending_ == 0; });
     }
 
