@@ -62,7 +62,7 @@ struct Smem {
     uint32_t row_list[32];
     uint32_t pend_row[32];  // pending partners of each statement in the current pass
     uint32_t rep_pend[32], rep_conf[32];  // pending / witnessed pattern pairs (lower -> higher)
-    uint32_t n_seg_list, pass_rows;
+    uint32_t n_seg_list, pass_rows, pass_pend;
     uint32_t rlo[32], rhi[32], clo[32], chi[32];
     uint32_t seg_list[kSegCap];
     unsigned long long bchunk[2][64];
@@ -266,6 +266,8 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
         if (keep) sm.row_list[__popc(bal & ((1u << lane) - 1u))] = lane;
         if (lane == 0) sm.pass_rows = involved;
+        const uint32_t n_pend = __reduce_add_sync(0xFFFFFFFFu, __popc(rp));  // pending pattern pairs
+        if (lane == 0) sm.pass_pend = n_pend;
         // address range of each row over the blocks of the pass: here for a
         // few blocks (each lane its own row), by the whole CTA below otherwise
         uint32_t lo = 0xFFFFu, hi = 0u;
@@ -298,11 +300,24 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
         }
         __syncthreads();  // the ranges, before the column ranges of each tile
     }
-    const uint32_t cap = min(table_bytes / (2u * S * kChunkWords), kMaxTileChunks);
-    if (cap == 0) {  // the host sizes the table for at least one chunk; never loop without progress
+    const uint32_t cap_rows = min(table_bytes / (2u * S * kChunkWords), kMaxTileChunks);
+    if (cap_rows == 0) {  // the host sizes the table for at least one chunk; never loop without progress
         if (threadIdx.x == 0) atomicOr(sm.err, kErrTableTooSmall);
         return;
     }
+    // With room for a 32-bit mask per column (the rows that hold an entry
+    // there), the same-block probe pass reads only those rows' entries instead
+    // of every pending partner's; taken when the program's blocks are alike
+    // (one block pass probes every pending pair), rows have three or more
+    // pending partners on average (fewer cost less than the masks do) and the
+    // masks cost no extra tile.  (When blocks differ, or in the cross-block
+    // pass, many block passes each probe a few pairs, which the per-partner
+    // test below handles for less.)
+    const uint32_t cap_masks = min(table_bytes / ((2u * S + 4u) * kChunkWords), kMaxTileChunks);
+    const uint32_t n_chunks = __popcll(chunks);
+    const bool col_rows = !kInter && P.blk_invariant && sm.pass_pend >= 3u * n_rows && cap_masks > 0 &&
+                          (n_chunks + cap_masks - 1u) / cap_masks == (n_chunks + cap_rows - 1u) / cap_rows;
+    const uint32_t cap = col_rows ? cap_masks : cap_rows;
     const uint32_t n_segs = n_rows * nb;
     const bool one_batch = n_segs <= kSegCap;
     uint64_t pending = chunks;
@@ -360,6 +375,10 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
             uint32_t *row32 = reinterpret_cast<uint32_t *>(tab + (size_t)st * cols);
             for (uint32_t w = (c0 >> 1) + lane; w <= (c1 >> 1); w += 32) row32[w] = 0xFFFFFFFFu;
         }
+        // the column masks follow the S rows: (2 S + 4) bytes per column in all
+        uint32_t *colrows = reinterpret_cast<uint32_t *>(tab + (size_t)S * cols);
+        if (col_rows)
+            for (uint32_t w = threadIdx.x; w < cols; w += blockDim.x) colrows[w] = 0;
         // pass 0: each access installs its owner with a CAS on an empty entry;
         //         one that finds another owner stores MULTI (an entry only ever
         //         goes empty -> one owner -> MULTI, so the end state is exact);
@@ -447,7 +466,11 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                             }
                             const uint16_t owner = kInter ? (uint16_t)blk : (uint16_t)(v * 8u + e);
                             const uint16_t old = atomicCAS(row + idx, kEmpty, owner);
-                            if (old != kEmpty && old != owner) row[idx] = kMulti;
+                            if (old == kEmpty) {
+                                if (col_rows) atomicOr(&colrows[idx], 1u << st);  // the row's first entry here
+                            } else if (old != owner) {
+                                row[idx] = kMulti;
+                            }
                         }
                     } else {
                         uint32_t col[8];
@@ -461,6 +484,26 @@ __device__ void owner_pass(Smem &sm, uint16_t *tab, uint32_t table_bytes, const 
                                 col[e] = (((act8 >> e) & 1u) && slot != 0xFFu)
                                              ? slot * kChunkWords + (a & (kChunkWords - 1u)) : 0xFFFFFFFFu;
                             }
+                        }
+                        if (col_rows) {
+                            // at each access, the pending partners holding an
+                            // entry at its column; an entry not its own is a hit
+                            uint32_t hits = 0;
+#pragma unroll
+                            for (uint32_t e = 0; e < 8; ++e) {
+                                const uint32_t c = col[e];
+                                if (c == 0xFFFFFFFFu) continue;
+                                const uint32_t mine = kInter ? blk : (v * 8u + e);
+                                uint32_t t = colrows[c] & pend & ~hits;
+                                if (t) t &= ~*(volatile uint32_t *)&sm.rep_conf[st];  // found by another unit
+                                for (; t; t &= t - 1u) {
+                                    const uint32_t j = __ffs(t) - 1u;
+                                    const uint32_t o = tab[(size_t)j * cols + c];
+                                    if (o != kEmpty && o != mine) hits |= 1u << j;
+                                }
+                            }
+                            if (hits) atomicOr(&sm.rep_conf[st], hits);
+                            continue;
                         }
                         for (uint32_t jt = pend; jt; jt &= jt - 1u) {
                             const uint32_t j = __ffs(jt) - 1u;
