@@ -97,6 +97,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+# CTA shapes (threads, CTAs per SM) the kernels are built for, in the order
+# gr_tune_packed indexes them: the relation kernel's and the general check
+# kernel's
+REL_SHAPES = [(512, 3), (256, 4), (512, 2), (1024, 1), (256, 6), (128, 8)]
+GEN_SHAPES = [(512, 2), (256, 3), (256, 4), (1024, 1), (384, 3)]
+
+
+def shape_dict(shape):
+    rel, gen = shape & 0xFF, (shape >> 8) & 0xFF
+    return {"relation": {"threads": REL_SHAPES[rel][0], "ctas_per_sm": REL_SHAPES[rel][1]},
+            "general_check": {"threads": GEN_SHAPES[gen & 15][0], "ctas_per_sm": GEN_SHAPES[gen & 15][1],
+                              "balanced_grid": bool(gen & 16)},
+            "picked_by": "autotuner"}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -376,9 +391,7 @@ def run_ours(args, rank, world, local):
             "config": {"workload": args.workload, "programs": n, "blocks": wl.blocks, "threads": wl.threads,
                        "stmts": wl.n_stmts, "m_words": wl.m_words, "seed": wl.seed,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
-                       "cta_shape": {"threads": [512, 256, 256, 1024, 384][shape & 15],
-                                     "ctas_per_sm": [2, 3, 4, 1, 3][shape & 15],
-                                     "balanced_grid": bool(shape & 16), "picked_by": "autotuner"},
+                       "cta_shape": shape_dict(shape),
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,

@@ -59,6 +59,7 @@ extern "C" {
 #define GR_MAX_ITERS 64
 #define GR_MAX_LOOPS 4
 #define GR_MAX_NEG 32
+#define GR_MAX_DEADLINE_US (1ull << 40) /* about 12.7 days */
 
 typedef int32_t gr_status;
 enum {
@@ -84,8 +85,11 @@ enum { GR_BLOCK = 0, GR_GRID = 1 };
  *                 may drop barriers that no witness needs. */
 enum { GR_MODE_REPAIR = 0, GR_MODE_REMOVE = 1 };
 
-/* Per-program outcome (Algorithm 1's exits). */
-enum { GR_REPAIRED = 0, GR_UNREPAIRABLE = 1, GR_ITER_CAP = 2 };
+/* Per-program outcome (Algorithm 1's exits).  GR_ITER_CAP and GR_TIMEOUT are
+ * the two ways the loop gives up: more checks than gr_options.max_iters, or
+ * longer than gr_options.deadline_us (Section 5 runs every kernel under a
+ * time limit); both leave mask 0 and keep the trajectory so far. */
+enum { GR_REPAIRED = 0, GR_UNREPAIRABLE = 1, GR_ITER_CAP = 2, GR_TIMEOUT = 3 };
 
 typedef struct {
     uint8_t op;        /* GR_R / GR_W */
@@ -176,10 +180,16 @@ typedef struct {
     uint8_t strategy;     /* GR_STRATEGY_*; both end at the same minimum mask */
     uint8_t _pad[2];
     uint32_t max_iters;   /* checks allowed per program, 1..GR_MAX_ITERS; 0 = 64 */
+    uint64_t deadline_us; /* 0: none.  Else the time limit of each program's loop (Section 5
+                             runs the tool under a per-kernel timeout), on the device clock
+                             from the moment the program's loop starts: after a Solve, a
+                             program whose loop has run at least this long stops with
+                             GR_TIMEOUT instead of checking the next proposal.  At most
+                             GR_MAX_DEADLINE_US. */
 } gr_options;
 
 typedef struct {
-    int32_t status;               /* GR_REPAIRED / GR_UNREPAIRABLE / GR_ITER_CAP */
+    int32_t status;               /* GR_REPAIRED / GR_UNREPAIRABLE / GR_ITER_CAP / GR_TIMEOUT */
     uint32_t mask;                /* final mask (0 unless repaired) */
     uint32_t weight;              /* sum of the weights of mask's slots */
     uint32_t added, removed;      /* mask & ~E, E & ~mask (removed is 0 unless repaired) */
@@ -234,14 +244,19 @@ gr_status gr_solve(uint32_t n_vars, const uint32_t *w, const uint32_t *pos, uint
                    const uint32_t *neg, uint32_t n_neg, uint32_t forced, uint32_t forbidden,
                    uint32_t *mask_out, uint32_t *weight_out);
 
-/* Many independent programs (uneven sizes) in one persistent launch on
- * `stream` (a cudaStream_t, NULL = legacy default stream); returns once out
- * holds every result.  modes: one GR_MODE_* per program. */
+/* Algorithm 1 (Section 2.4) on each of many independent programs (uneven
+ * sizes), batched on the device: each program's conflict relation (Verify of
+ * Section 2.4 under the empty mask) in one check launch, then the loop of
+ * every program in one loop launch, on `stream` (a cudaStream_t, NULL =
+ * legacy default stream); returns once out holds every result.  Each result
+ * equals gr_repair's on the program alone.  modes: one GR_MODE_* per
+ * program (Section 5's configurations). */
 gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches,
                           const int32_t *modes, uint32_t n, const gr_options *opts,
                           gr_repair_result *out, void *stream);
 
-/* One check per (program, mask) in one persistent launch. */
+/* Verify (Algorithm 1, Section 2.4) of each (program, masks[i]) pair, all in
+ * one batched launch: out[i] equals gr_check(progs[i], launches[i], masks[i]). */
 gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches,
                          const uint32_t *masks, uint32_t n, gr_witnesses *out, void *stream);
 
@@ -260,11 +275,20 @@ gr_status gr_pack_size(const gr_program *progs, const gr_launch *launches, uint3
 gr_status gr_pack(const gr_program *progs, const gr_launch *launches, const int32_t *modes,
                   uint32_t n, void *host_arena, uint64_t arena_bytes);
 
-/* Algorithm 1 on every program of a packed arena already in device memory:
- * expands the address traces into d_scratch, then runs the persistent repair
- * launch.  d_out: n results in device memory.  Enqueued on stream; nothing is
- * allocated and nothing synchronises.  d_arena and d_scratch must be 256-byte
- * aligned; scratch_bytes must be at least gr_pack_size's figure. */
+/* Algorithm 1 on every program of a packed arena already in device memory.
+ * Programs on the shared array whose blocks see one access pattern (no
+ * address depends on the block, or every map shifts by the same offset per
+ * block) get their conflict relation from the relation kernel, which
+ * computes addresses from the maps; the others (a global array, or blocks
+ * that differ) have their address traces expanded into d_scratch and checked
+ * by the general check kernel; then the loop kernel runs Algorithm 1 per
+ * program on the relations.  d_out: n results in device memory.  Enqueued on
+ * stream; nothing is allocated and nothing synchronises.  d_arena and
+ * d_scratch must be 256-byte aligned; n must be the arena's program count and
+ * scratch_bytes at least gr_pack_size's figure.  The kernels compare both
+ * with the arena header: on a mismatch they do nothing (d_out untouched) and
+ * set bit 2 (value 4) of the device error word, the 32-bit word at byte 4 of
+ * d_scratch, which the host-pointer calls report as GR_ECUDA. */
 gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *opts,
                            void *d_scratch, uint64_t scratch_bytes, gr_repair_result *d_out,
                            void *stream);
@@ -284,22 +308,26 @@ gr_status gr_repair_packed_wide(const void *d_arena, uint32_t n, const gr_option
                                 void *stream);
 
 /* The two halves of gr_repair_packed, for callers that time or overlap them:
- * gr_expand_packed writes the address traces and chunk masks of every
- * program into d_scratch; gr_repair_expanded runs the persistent repair
- * launch on traces a previous gr_expand_packed of the same arena wrote. */
+ * gr_expand_packed writes the address traces and chunk masks of the programs
+ * the general check kernel reads (a global array, or blocks that differ) into
+ * d_scratch; gr_repair_expanded runs the relation, check and loop kernels on
+ * traces a previous gr_expand_packed of the same arena wrote. */
 gr_status gr_expand_packed(const void *d_arena, void *d_scratch, uint64_t scratch_bytes, void *stream);
 gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                              uint64_t scratch_bytes, gr_repair_result *d_out, void *stream);
 
-/* Autotuner: time every CTA shape the persistent repair is built for (threads
+/* Autotuner: time every CTA shape the check kernels are built for (threads
  * per CTA x CTAs per SM, with the owner-table budget that shape leaves) on
  * this arena, remember the fastest for later gr_repair_packed /
- * gr_repair_expanded / gr_check_packed calls on the same (d_arena, n), and
- * return it in shape_out (may be NULL): bits 0-3 index the CTA shape, bit 4
- * is set when the grid is cut so that every CTA gets the same number of
- * programs (fewer CTAs than fit, no partly filled last round).  Runs the repair several times
- * into d_out and synchronises the stream.  The host-pointer batch calls tune
- * the same way by themselves, once per batch size class. */
+ * gr_repair_expanded / gr_check_packed calls (and gr_repair_packed_noalloc)
+ * on the same (d_arena, n), and return them in shape_out (may be NULL): bits
+ * 0-7 index the relation kernel's shape, bits 8-11 the general check
+ * kernel's, bit 12 is set when that kernel's grid is cut so that every CTA
+ * gets the same number of programs (fewer CTAs than fit, no partly filled
+ * last round).  Runs the check kernels several times, then one repair with
+ * the shapes picked into d_out, and synchronises the stream.  The
+ * host-pointer batch calls tune the same way by themselves, once per batch
+ * size class. */
 gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                          uint64_t scratch_bytes, gr_repair_result *d_out, void *stream, uint32_t *shape_out);
 
@@ -319,7 +347,7 @@ gr_status gr_check_expanded(const void *d_arena, uint32_t n, const uint32_t *d_m
 /* ---------------------------------------------------------------------- */
 
 /* A server repairs single programs submitted at any time (the repair loop of
- * Algorithm 1 per request).  It owns n_slots (1..16) launch slots, each with
+ * Algorithm 1, Section 2.4, per request; each result equals gr_repair's).  It owns n_slots (1..16) launch slots, each with
  * its own stream and device buffers; together they take mem_budget_bytes of
  * device memory, allocated here, and nothing more is allocated while
  * serving.  A dispatcher thread admits queued requests in arrival order into

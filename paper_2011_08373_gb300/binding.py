@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libgpurepair.so")
 
 MAX_STMTS, MAX_SLOTS, MAX_ITERS, MAX_CLAUSES = 25, 32, 64, 656
 OK, UNSAT, EINVAL, ENOMEM, ECUDA, EBUSY, ECAPACITY = 0, 1, -1, -2, -4, -5, -6
-REPAIRED, UNREPAIRABLE, ITER_CAP = 0, 1, 2
+REPAIRED, UNREPAIRABLE, ITER_CAP, TIMEOUT = 0, 1, 2, 3
 
 
 class GrError(RuntimeError):
@@ -61,7 +61,7 @@ class gr_witnesses(C.Structure):
 
 class gr_options(C.Structure):
     _fields_ = [("grid_enabled", C.c_uint8), ("strategy", C.c_uint8), ("_pad", C.c_uint8 * 2),
-                ("max_iters", C.c_uint32)]
+                ("max_iters", C.c_uint32), ("deadline_us", C.c_uint64)]
 
 
 class gr_repair_result(C.Structure):
@@ -214,11 +214,13 @@ class CProgram:
 STRATEGY_MAXSAT, STRATEGY_MHS = 0, 1
 
 
-def _options(grid_enabled: bool = True, max_iters: int = 64, strategy: int = 0) -> gr_options:
+def _options(grid_enabled: bool = True, max_iters: int = 64, strategy: int = 0,
+             deadline_us: int = 0) -> gr_options:
     o = gr_options()
     o.grid_enabled = 1 if grid_enabled else 0
     o.strategy = strategy
     o.max_iters = max_iters
+    o.deadline_us = deadline_us
     return o
 
 
@@ -363,20 +365,20 @@ def check(p, mask: int) -> dict:
 
 
 def repair(p, mode: Optional[int] = None, grid_enabled: bool = True, max_iters: int = 64,
-           strategy: int = 0) -> dict:
+           strategy: int = 0, deadline_us: int = 0) -> dict:
     c = CProgram(p)
     r = gr_repair_result()
-    o = _options(grid_enabled, max_iters, strategy)
+    o = _options(grid_enabled, max_iters, strategy, deadline_us)
     _check(lib().gr_repair(C.byref(c.s), c.launch, c.mode if mode is None else mode, C.byref(o),
                            C.byref(r)))
     return result_dict(np.frombuffer(bytes(r), dtype=RESULT_DTYPE)[0])
 
 
 def repair_plain(p, mode: Optional[int] = None, grid_enabled: bool = True,
-                 max_iters: int = 64, strategy: int = 0) -> dict:
+                 max_iters: int = 64, strategy: int = 0, deadline_us: int = 0) -> dict:
     c = CProgram(p)
     r = gr_repair_result()
-    o = _options(grid_enabled, max_iters, strategy)
+    o = _options(grid_enabled, max_iters, strategy, deadline_us)
     _check(lib().gr_repair_plain(C.byref(c.s), c.launch, c.mode if mode is None else mode,
                                  C.byref(o), C.byref(r)))
     return result_dict(np.frombuffer(bytes(r), dtype=RESULT_DTYPE)[0])
@@ -394,21 +396,21 @@ def solve(n_vars: int, weights, pos, neg=(), forced: int = 0, forbidden: int = 0
 
 
 def repair_batch_raw(progs, grid_enabled: bool = True, max_iters: int = 64, stream: int = 0,
-                     out: Optional[np.ndarray] = None, strategy: int = 0) -> np.ndarray:
+                     out: Optional[np.ndarray] = None, strategy: int = 0, deadline_us: int = 0) -> np.ndarray:
     """gr_repair_batch.  ``progs`` is a list of programs or a ProgramBatch."""
     b = progs if isinstance(progs, ProgramBatch) else ProgramBatch(progs)
     if out is None:
         out = np.zeros(b.n, dtype=RESULT_DTYPE)
-    o = _options(grid_enabled, max_iters, strategy)
+    o = _options(grid_enabled, max_iters, strategy, deadline_us)
     _check(lib().gr_repair_batch(b.prog_ptr, b.launch_ptr, b.mode_ptr, b.n, C.byref(o), out.ctypes.data,
                                  C.c_void_p(stream)))
     return out
 
 
 def repair_batch(progs: Sequence, grid_enabled: bool = True, max_iters: int = 64,
-                 stream: int = 0, strategy: int = 0) -> List[dict]:
+                 stream: int = 0, strategy: int = 0, deadline_us: int = 0) -> List[dict]:
     return [result_dict(r) for r in repair_batch_raw(progs, grid_enabled, max_iters, stream,
-                                                      strategy=strategy)]
+                                                      strategy=strategy, deadline_us=deadline_us)]
 
 
 def check_batch(progs: Sequence, masks: Sequence[int], stream: int = 0) -> List[dict]:
@@ -443,7 +445,7 @@ class DeviceBatch:
     """
 
     def __init__(self, progs: Sequence, device: str = "cuda", grid_enabled: bool = True,
-                 max_iters: int = 64, strategy: int = 0):
+                 max_iters: int = 64, strategy: int = 0, deadline_us: int = 0):
         import torch
 
         self.n = len(progs)
@@ -459,7 +461,7 @@ class DeviceBatch:
         self._out_ptr = _aligned(self.out.data_ptr())
         a_off = self._arena_ptr - self.arena.data_ptr()
         self.arena[a_off:a_off + self.arena_bytes].copy_(torch.from_numpy(host))
-        self.opts = _options(grid_enabled, max_iters, strategy)
+        self.opts = _options(grid_enabled, max_iters, strategy, deadline_us)
         self.host_arena = host
 
     def run(self, stream: Optional[int] = None) -> None:
@@ -481,7 +483,8 @@ class DeviceBatch:
                                            C.c_void_p(self._out_ptr), C.c_void_p(st)))
 
     def tune(self, stream: Optional[int] = None) -> int:
-        """Pick the fastest CTA shape for this batch (gr_tune_packed)."""
+        """Pick the fastest CTA shapes for this batch (gr_tune_packed): bits 0-7
+        index the relation kernel's shape, bits 8-15 the general check kernel's."""
         import torch
 
         st = torch.cuda.current_stream().cuda_stream if stream is None else stream
@@ -553,9 +556,9 @@ class Server:
     """gr_server_*: submit single programs at any time; poll for results."""
 
     def __init__(self, mem_budget_bytes: int, n_slots: int = 4, max_inflight: int = 1 << 20,
-                 grid_enabled: bool = True, max_iters: int = 64, strategy: int = 0):
+                 grid_enabled: bool = True, max_iters: int = 64, strategy: int = 0, deadline_us: int = 0):
         self._h = C.c_void_p()
-        o = _options(grid_enabled, max_iters, strategy)
+        o = _options(grid_enabled, max_iters, strategy, deadline_us)
         _check(lib().gr_server_create(mem_budget_bytes, n_slots, max_inflight, C.byref(o),
                                       C.byref(self._h)))
         self._keep = {}

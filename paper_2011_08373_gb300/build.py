@@ -1,6 +1,6 @@
 """Build libgpurepair.so in-tree with nvcc for sm_103a (no cmake, no torch).
 
-Two translation units compile in parallel, then one link step.  Run
+The translation units compile in parallel, then one link step.  Run
 ``python -m paper_2011_08373_gb300.build`` or call ``build()``.
 """
 from __future__ import annotations
@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libgpurepair.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
            "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["kernels.cu", "capi.cu", "noalloc.cu", "server.cu"]
+SOURCES = ["kernels.cu", "relation.cu", "loop.cu", "capi.cu", "noalloc.cu", "server.cu"]
 
 
 def _nvcc() -> str:
@@ -42,7 +42,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link libgpurepair.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(INCLUDE, "gpurepair.h"), os.path.join(CSRC, "engine.cuh")]
+    headers = [os.path.join(INCLUDE, "gpurepair.h"), os.path.join(CSRC, "engine.cuh"),
+               os.path.join(CSRC, "device.cuh")]
     objs = []
     jobs = []
     for src in SOURCES:

@@ -233,7 +233,23 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx, bool tabl
 gr_status validate_opts(const gr_options *o) {
     if (o && o->max_iters > GR_MAX_ITERS) return fail(GR_EINVAL, "max_iters above %d", GR_MAX_ITERS);
     if (o && o->strategy > GR_STRATEGY_MHS) return fail(GR_EINVAL, "unknown strategy %u", o->strategy);
+    if (o && o->deadline_us > GR_MAX_DEADLINE_US)
+        return fail(GR_EINVAL, "deadline_us above %llu", (unsigned long long)GR_MAX_DEADLINE_US);
     return GR_OK;
+}
+
+gr_options opts_or_default(const gr_options *o) {
+    gr_options d;
+    memset(&d, 0, sizeof(d));
+    d.grid_enabled = 1;
+    d.max_iters = GR_MAX_ITERS;
+    if (o) {
+        d.grid_enabled = o->grid_enabled;
+        d.strategy = o->strategy;
+        d.max_iters = o->max_iters ? o->max_iters : GR_MAX_ITERS;
+        d.deadline_us = o->deadline_us;
+    }
+    return d;
 }
 
 // ---------------------------------------------------------------------------
@@ -275,7 +291,8 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     L.segrange_off = align_to(L.segmask_off + seg_total * 8, 256);
     L.trace_off = align_to(L.segrange_off + seg_total * 4, 256);
     L.wide_off = align_to(L.trace_off + trace_total * 2, 256);
-    L.scratch_bytes = align_to(L.wide_off + wide_bytes(n), 256);
+    L.rel_off = align_to(L.wide_off + wide_bytes(n), 256);
+    L.scratch_bytes = align_to(L.rel_off + (size_t)n * sizeof(gr_witnesses), 256);
     return L;
 }
 
@@ -391,6 +408,24 @@ gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n,
     return code;
 }
 
+// Whether no two threads of a block share the statement's address: an
+// affine or strided map a*tid + (the block's offset) mod M is injective on
+// tid in [0, T) iff T <= M / gcd(a, M); a permutation map is iff T <= M.
+// (A guard only removes threads.)  A false "no" costs only speed: the
+// relation kernel then installs that row with compare-and-swap.
+bool injective_on_threads(const gr_stmt &st, uint32_t M, uint32_t T) {
+    if (T <= 1) return true;
+    if (st.kind == GR_PERM) return T <= M;
+    uint32_t a = st.a % M, b = M;
+    if (a == 0) return false;
+    while (b) {
+        const uint32_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return T <= M / a;
+}
+
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
                uint8_t *arena, uint32_t *table_bad, bool range_only) {
     // zero everything but the permutation area, which is fully overwritten
@@ -413,6 +448,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     H->scratch_trace_off = L.trace_off;
     H->scratch_segrange_off = L.segrange_off;
     H->scratch_wide_off = L.wide_off;
+    H->scratch_rel_off = L.rel_off;
     H->scratch_bytes = L.scratch_bytes;
     DevProg *dp = reinterpret_cast<DevProg *>(arena + L.progs_off);
     uint32_t *order = reinterpret_cast<uint32_t *>(arena + L.order_off);
@@ -480,11 +516,16 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             ds.gk = st.guard_k;
             ds.gr = st.guard_r;
             ds.m = M;
+            ds.flags = injective_on_threads(st, M, ls[p].threads) ? kStmtInjective : 0u;
             if (st.op == GR_W) D.write_mask |= 1u << s;
             if (st.space == GR_SHARED) D.shared_rows |= 1u << s;
             else D.global_rows |= 1u << s;
         }
         D.blk_invariant = blocks_alike(P) ? 1u : 0u;
+        // the relation kernel takes programs on the shared array alone whose
+        // blocks are alike (or that have one block): block 0's owner table
+        // decides every pair
+        D.fast = (D.global_rows == 0 && (D.blk_invariant || D.blocks == 1)) ? 1u : 0u;
         // access-pattern classes: statements with the same array, map and
         // guard touch the same words from the same threads
         for (uint32_t s = 0; s < 32; ++s) D.rep[s] = (uint8_t)s;
@@ -539,8 +580,16 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
         if (tail < L.arena_bytes) memset(arena + tail, 0, L.arena_bytes - tail);
     }
     segbase[n] = L.n_segments;
+    // the relation kernel's programs first, then the general ones, each part
+    // largest first
     std::iota(order, order + n, 0u);
-    std::stable_sort(order, order + n, [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    std::stable_sort(order, order + n, [&](uint32_t a, uint32_t b) {
+        if (dp[a].fast != dp[b].fast) return dp[a].fast > dp[b].fast;
+        return cost[a] > cost[b];
+    });
+    uint32_t n_fast = 0;
+    while (n_fast < n && dp[order[n_fast]].fast) ++n_fast;
+    H->n_fast = n_fast;
     // expansion items, largest programs first: runs of up to kItemSegs
     // segments (kind 0); for a program whose blocks are alike the same-block
     // passes read block 0 only and only global statements have a cross-block
@@ -555,7 +604,10 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
         items[4 * k + 3] = kind;
         ++k;
     };
-    for (uint32_t i = 0; i < n; ++i) {
+    // the general programs' items first (the repair path expands only those)
+    for (uint32_t ii = 0; ii < n; ++ii) {
+        const uint32_t i = ii < n - n_fast ? n_fast + ii : ii - (n - n_fast);
+        if (ii == n - n_fast) H->n_items_gen = (uint32_t)k;
         const uint32_t p = order[i];
         const DevProg &D = dp[p];
         const uint32_t segs = (uint32_t)(segbase[p + 1] - segbase[p]);
@@ -570,6 +622,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             for (uint32_t lo = 0; lo < segs; lo += kItemSegs) emit(p, lo, std::min(segs, lo + kItemSegs), 0u);
         }
     }
+    if (n_fast == 0) H->n_items_gen = (uint32_t)k;
     H->n_items = k;
 }
 
@@ -596,6 +649,14 @@ uint32_t ceil_log2(uint64_t x) {
 }
 
 
+// The CTA shapes picked for a batch: the relation kernel's (kRelShapes), the
+// general check kernel's (kShapes, plus kShapeBalanced), the largest
+// program's statement instances (sizes the general check's table) and the
+// kSkip* bits of the batch.
+struct Tuned {
+    uint32_t rel_shape = 0, gen_shape = 0, s_max = GR_MAX_STMTS, skip = 0;
+};
+
 struct DeviceBuf {
     void *p = nullptr;
     size_t cap = 0;
@@ -619,8 +680,8 @@ struct Workspace {
     int smem_per_sm = 0;
     uint32_t max_dyn = 0;
     DeviceBuf arena, scratch, out, aux;
-    std::map<SizeClass, uint32_t> class_shape;                         // tuned host batches
-    std::map<std::pair<const void *, uint32_t>, std::pair<uint32_t, uint32_t>> arena_shape;  // (shape, s_max)
+    std::map<SizeClass, Tuned> class_shape;                             // tuned host batches
+    std::map<std::pair<const void *, uint32_t>, Tuned> arena_shape;     // gr_tune_packed
     uint8_t *host_arena = nullptr;  // pinned staging for the packed arena
     size_t host_arena_cap = 0;
 };
@@ -677,14 +738,61 @@ LaunchCfg shape_cfg(const Workspace &ws, uint32_t n, uint32_t shape, uint32_t s_
     return c;
 }
 
-// Default shape (512 threads, 2 CTAs per SM) unless it cannot hold the rows.
-LaunchCfg choose_cfg(const Workspace &ws, uint32_t n, uint32_t s_max = GR_MAX_STMTS) {
-    LaunchCfg c = shape_cfg(ws, n, 0, s_max);
-    if (!c.table_bytes) c = shape_cfg(ws, n, 3, s_max);
+// Launch of the relation kernel in CTA shape `shape` for n programs: the
+// owner table takes what is left of the SM's shared-memory share after the
+// fixed part (1 KB per CTA is reserved).  table_bytes is 0 when the shape
+// cannot hold one 32-column window of 27 rows.
+RelCfg rel_cfg(const Workspace &ws, uint32_t n, uint32_t shape) {
+    const LaunchShape sh = kRelShapes[shape];
+    RelCfg c{0, 0, shape};
+    const size_t per_cta = (size_t)ws.smem_per_sm / sh.ctas_per_sm;
+    const size_t fixed = rel_fixed_bytes() + 1024;
+    size_t table = per_cta > fixed ? (per_cta - fixed) / 256 * 256 : 0;
+    const size_t room = ws.max_dyn > rel_fixed_bytes() ? (ws.max_dyn - rel_fixed_bytes()) / 256 * 256 : 0;
+    table = std::min(table, room);
+    if (table < 2048) return c;
+    c.table_bytes = (uint32_t)table;
+    c.grid = std::max<uint32_t>(1u, std::min<uint32_t>(n, (uint32_t)ws.sms * sh.ctas_per_sm));
     return c;
 }
 
-// ---- autotuner: the fastest CTA shape per batch size class ---------------
+// CTAs of the loop kernel: as many as the SMs hold at once, at most one warp
+// per program.
+uint32_t loop_grid(const Workspace &ws, uint32_t n) {
+    const size_t per = loop_smem_bytes() + 1024;
+    const uint32_t by_smem = (uint32_t)std::max<size_t>(1, (size_t)ws.smem_per_sm / per);
+    const uint32_t by_threads = 2048u / kLoopThreads;
+    const uint32_t ctas = std::min(by_smem, by_threads);
+    const uint32_t need = (n + kLoopThreads / 32 - 1) / (kLoopThreads / 32);
+    return std::max<uint32_t>(1u, std::min<uint32_t>(need, (uint32_t)ws.sms * ctas));
+}
+
+// The whole launch configuration of a repair (or check) of n programs.
+LaunchCfg full_cfg(const Workspace &ws, uint32_t n, const Tuned &t) {
+    LaunchCfg c = shape_cfg(ws, n, t.gen_shape, t.s_max);
+    if (!c.table_bytes) c = shape_cfg(ws, n, 0, t.s_max);
+    if (!c.table_bytes) c = shape_cfg(ws, n, 3, t.s_max);
+    c.rel = rel_cfg(ws, n, t.rel_shape);
+    if (!c.rel.table_bytes) c.rel = rel_cfg(ws, n, 0);
+    c.loop_grid = loop_grid(ws, n);
+    c.skip = t.skip;
+    return c;
+}
+
+// Default shapes (the relation kernel's first, the general check's 512 x 2,
+// or 1024 x 1 when that cannot hold the rows).
+LaunchCfg choose_cfg(const Workspace &ws, uint32_t n, uint32_t s_max = GR_MAX_STMTS) {
+    Tuned t;
+    t.s_max = s_max;
+    return full_cfg(ws, n, t);
+}
+
+// The kSkip* bits of a packed batch from its header.
+uint32_t skip_bits(const ArenaHeader &h) {
+    return (h.n_fast == 0 ? kSkipFast : 0u) | (h.n_fast == h.n_progs ? kSkipGeneral : 0u);
+}
+
+// ---- autotuner: the fastest CTA shapes per batch size class ---------------
 
 SizeClass size_class(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     SizeClass k{0, 0, 0, 0, ceil_log2(n)};
@@ -699,47 +807,74 @@ SizeClass size_class(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     return k;
 }
 
-// Time every shape that can hold the batch (traces already expanded into
-// d_scratch) and return the fastest.  Synchronises the stream.
-gr_status tune_shapes(const Workspace &ws, const void *d_arena, uint32_t n, const gr_options &o, void *d_scratch,
-                      gr_repair_result *d_out, cudaStream_t st, uint32_t s_max, uint32_t *best_shape) {
-    float best = 1e30f;
-    *best_shape = choose_cfg(ws, n, s_max).shape;
+// Time every shape of the relation kernel on the batch's programs for it, and
+// every shape of the general check kernel (plain and with the balanced grid)
+// on the general programs' relations, and return the fastest of each.  The
+// general traces must be expanded into d_scratch.  Synchronises the stream;
+// leaves the scratch control words to be cleared by the next launch.
+gr_status tune_cfg(const Workspace &ws, const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                   cudaStream_t st, uint32_t s_max, uint32_t skip, Tuned *out) {
+    Tuned t;
+    t.s_max = s_max;
+    t.skip = skip;
     cudaEvent_t e0, e1;
     GR_CUDA(cudaEventCreate(&e0));
     GR_CUDA(cudaEventCreate(&e1));
-    for (uint32_t v = 0; v < 2 * kNumShapes; ++v) {
-        const uint32_t sh = v < kNumShapes ? v : ((v - kNumShapes) | kShapeBalanced);
-        const LaunchCfg cfg = shape_cfg(ws, n, sh, s_max);
-        if (!cfg.table_bytes) continue;
-        if ((sh & kShapeBalanced) && cfg.grid == shape_cfg(ws, n, sh & kShapeMask, s_max).grid) continue;
-        float ms = 0;
-        for (int rep = 0; rep < 2; ++rep) {  // the first run warms the shape
-            GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
-            GR_CUDA(cudaEventRecord(e0, st));
-            GR_CUDA(launch_repair(d_arena, n, o, d_scratch, d_out, cfg, st));
-            GR_CUDA(cudaEventRecord(e1, st));
-            GR_CUDA(cudaEventSynchronize(e1));
-            GR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    auto timed = [&](auto launch, float *ms) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms the shape
+            if ((e = cudaMemsetAsync(d_scratch, 0, 16, st)) != cudaSuccess) break;
+            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+            if ((e = launch()) != cudaSuccess) break;
+            if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            e = cudaEventElapsedTime(ms, e0, e1);
         }
-        if (ms < best) {
-            best = ms;
-            *best_shape = sh;
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (!(skip & kSkipFast)) {
+        float best = 1e30f;
+        for (uint32_t sh = 0; sh < kNumRelShapes && e == cudaSuccess; ++sh) {
+            const RelCfg rc = rel_cfg(ws, n, sh);
+            if (!rc.table_bytes) continue;
+            float ms = 0;
+            e = timed([&] { return launch_relation(d_arena, n, nullptr, d_scratch, scratch_bytes, nullptr, rc, st); },
+                      &ms);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                t.rel_shape = sh;
+            }
+        }
+    }
+    if (!(skip & kSkipGeneral) && e == cudaSuccess) {
+        float best = 1e30f;
+        for (uint32_t v = 0; v < 2 * kNumShapes && e == cudaSuccess; ++v) {
+            const uint32_t sh = v < kNumShapes ? v : ((v - kNumShapes) | kShapeBalanced);
+            const LaunchCfg cfg = shape_cfg(ws, n, sh, s_max);
+            if (!cfg.table_bytes) continue;
+            if ((sh & kShapeBalanced) && cfg.grid == shape_cfg(ws, n, sh & kShapeMask, s_max).grid) continue;
+            float ms = 0;
+            e = timed([&] { return launch_check(d_arena, n, nullptr, d_scratch, scratch_bytes, nullptr, cfg, st); },
+                      &ms);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                t.gen_shape = sh;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotuner");
+    *out = t;
     return GR_OK;
 }
 
-// Launch configuration for a device arena: its tuned shape if gr_tune_packed
-// ran on it, else the default.
+// Launch configuration for a device arena: its tuned shapes if gr_tune_packed
+// ran on it, else the defaults.
 LaunchCfg packed_cfg(const Workspace &ws, const void *d_arena, uint32_t n) {
     auto it = ws.arena_shape.find({d_arena, n});
-    if (it != ws.arena_shape.end()) {
-        const LaunchCfg c = shape_cfg(ws, n, it->second.first, it->second.second);
-        if (c.table_bytes) return c;
-    }
+    if (it != ws.arena_shape.end()) return full_cfg(ws, n, it->second);
     return choose_cfg(ws, n);
 }
 
@@ -788,20 +923,22 @@ gr_status finish_sync(void *d_scratch, cudaStream_t st) {
 namespace gr {
 // Launch shape of the persistent repair for n packed programs on the current
 // device (used by gr_repair_packed_noalloc in noalloc.cu).
-LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status) {
+LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, gr_status *status) {
     Workspace *ws;
-    LaunchCfg c{1, kMinTableBytes};
+    LaunchCfg c{};
     if ((*status = current_ws(&ws)) != GR_OK) return c;
     std::lock_guard<std::mutex> g(ws->mu);
     if ((*status = ensure_configured(*ws)) != GR_OK) return c;
-    return choose_cfg(*ws, n);
+    c = packed_cfg(*ws, d_arena, n);
+    c.skip |= skip;
+    return c;
 }
 
 // Owner-table budget of the wide lane's check CTAs (512 threads, two per SM)
 // for programs of up to s_max statement instances.
 LaunchCfg wide_launch_cfg(uint32_t n, uint32_t s_max, gr_status *status) {
     Workspace *ws;
-    LaunchCfg c{1, kMinTableBytes};
+    LaunchCfg c{};
     if ((*status = current_ws(&ws)) != GR_OK) return c;
     std::lock_guard<std::mutex> g(ws->mu);
     if ((*status = ensure_configured(*ws)) != GR_OK) return c;
@@ -851,19 +988,6 @@ gr_status gr_pack(const gr_program *progs, const gr_launch *launches, const int3
     return GR_OK;
 }
 
-static gr_options opts_or_default(const gr_options *o) {
-    gr_options d;
-    memset(&d, 0, sizeof(d));
-    d.grid_enabled = 1;
-    d.max_iters = GR_MAX_ITERS;
-    if (o) {
-        d.grid_enabled = o->grid_enabled;
-        d.strategy = o->strategy;
-        d.max_iters = o->max_iters ? o->max_iters : GR_MAX_ITERS;
-    }
-    return d;
-}
-
 gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                            uint64_t scratch_bytes, gr_repair_result *d_out, void *stream) {
     if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
@@ -876,10 +1000,9 @@ gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *op
     if ((s = current_ws(&ws)) != GR_OK) return s;
     std::lock_guard<std::mutex> g(ws->mu);
     if ((s = ensure_configured(*ws)) != GR_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
-    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
-    GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
+    GR_CUDA(enqueue_repair(d_arena, n, opts_or_default(opts), d_scratch, scratch_bytes, d_out,
+                           packed_cfg(*ws, d_arena, n), expand_grid(*ws), true, true,
+                           static_cast<cudaStream_t>(stream)));
     return GR_OK;
 }
 
@@ -905,7 +1028,7 @@ gr_status gr_repair_packed_wide(const void *d_arena, uint32_t n, const gr_option
     const LaunchCfg cfg = shape_cfg(*ws, n, 0, h.s_max);  // 512 threads, two CTAs per SM
     if (!cfg.table_bytes) return fail(GR_ECAPACITY, "no owner-table room for %u rows", h.s_max);
     GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
-    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
+    GR_CUDA(launch_expand(d_arena, d_scratch, scratch_bytes, false, expand_grid(*ws), st));
     GR_CUDA(launch_wide(d_arena, n, h.b_max, opts_or_default(opts), d_scratch, h.scratch_wide_off, d_out,
                         cfg.table_bytes, st));
     return GR_OK;
@@ -921,7 +1044,7 @@ gr_status gr_expand_packed(const void *d_arena, void *d_scratch, uint64_t scratc
     if ((s = current_ws(&ws)) != GR_OK) return s;
     std::lock_guard<std::mutex> g(ws->mu);
     if ((s = ensure_configured(*ws)) != GR_OK) return s;
-    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), static_cast<cudaStream_t>(stream)));
+    GR_CUDA(launch_expand(d_arena, d_scratch, scratch_bytes, true, expand_grid(*ws), static_cast<cudaStream_t>(stream)));
     return GR_OK;
 }
 
@@ -937,9 +1060,9 @@ gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *
     if ((s = current_ws(&ws)) != GR_OK) return s;
     std::lock_guard<std::mutex> g(ws->mu);
     if ((s = ensure_configured(*ws)) != GR_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
-    GR_CUDA(launch_repair(d_arena, n, opts_or_default(opts), d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
+    GR_CUDA(enqueue_repair(d_arena, n, opts_or_default(opts), d_scratch, scratch_bytes, d_out,
+                           packed_cfg(*ws, d_arena, n), expand_grid(*ws), false, true,
+                           static_cast<cudaStream_t>(stream)));
     return GR_OK;
 }
 
@@ -960,12 +1083,17 @@ gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts
     GR_CUDA(cudaStreamSynchronize(st));
     if (h.magic != kArenaMagic || h.n_progs != n) return fail(GR_EINVAL, "d_arena is not a packed arena of %u programs", n);
     if (scratch_bytes < h.scratch_bytes) return fail(GR_ECAPACITY, "scratch needs %llu bytes", (unsigned long long)h.scratch_bytes);
-    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
-    uint32_t shape = 0;
-    if ((s = tune_shapes(*ws, d_arena, n, opts_or_default(opts), d_scratch, d_out, st, h.s_max, &shape)) != GR_OK)
-        return s;
-    ws->arena_shape[{d_arena, n}] = {shape, h.s_max};
-    if (shape_out) *shape_out = shape;
+    const uint32_t skip = skip_bits(h);
+    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
+    if (!(skip & kSkipGeneral)) GR_CUDA(launch_expand(d_arena, d_scratch, scratch_bytes, true, expand_grid(*ws), st));
+    Tuned t;
+    if ((s = tune_cfg(*ws, d_arena, n, d_scratch, scratch_bytes, st, h.s_max, skip, &t)) != GR_OK) return s;
+    ws->arena_shape[{d_arena, n}] = t;
+    // one repair with the picked shapes leaves d_out filled, as documented
+    GR_CUDA(enqueue_repair(d_arena, n, opts_or_default(opts), d_scratch, scratch_bytes, d_out, full_cfg(*ws, n, t),
+                           expand_grid(*ws), false, true, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    if (shape_out) *shape_out = t.rel_shape | (t.gen_shape << 8);
     return GR_OK;
 }
 
@@ -980,10 +1108,8 @@ gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_mas
     if ((s = current_ws(&ws)) != GR_OK) return s;
     std::lock_guard<std::mutex> g(ws->mu);
     if ((s = ensure_configured(*ws)) != GR_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 256, st));
-    GR_CUDA(launch_expand(d_arena, d_scratch, expand_grid(*ws), st));
-    GR_CUDA(launch_check(d_arena, n, d_masks, d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
+    GR_CUDA(enqueue_check(d_arena, n, d_masks, d_scratch, scratch_bytes, d_out, packed_cfg(*ws, d_arena, n),
+                          expand_grid(*ws), true, static_cast<cudaStream_t>(stream)));
     return GR_OK;
 }
 
@@ -998,9 +1124,8 @@ gr_status gr_check_expanded(const void *d_arena, uint32_t n, const uint32_t *d_m
     if ((s = current_ws(&ws)) != GR_OK) return s;
     std::lock_guard<std::mutex> g(ws->mu);
     if ((s = ensure_configured(*ws)) != GR_OK) return s;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    GR_CUDA(cudaMemsetAsync(d_scratch, 0, 4, st));  // the work-queue counter
-    GR_CUDA(launch_check(d_arena, n, d_masks, d_scratch, d_out, packed_cfg(*ws, d_arena, n), st));
+    GR_CUDA(enqueue_check(d_arena, n, d_masks, d_scratch, scratch_bytes, d_out, packed_cfg(*ws, d_arena, n),
+                          expand_grid(*ws), false, static_cast<cudaStream_t>(stream)));
     return GR_OK;
 }
 
@@ -1101,25 +1226,28 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
             }
         GR_CUDA(cudaMemcpyAsync(ws->arena.p, staging, Ls[c].arena_bytes, cudaMemcpyHostToDevice, st));
         if (any_perm) GR_CUDA(launch_perm_check(ws->arena.p, n_c, lo[c], d_perm_bad, (uint32_t)ws->sms, st));
-        // queue counter (and, for the first chunk, the error word) cleared
-        GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, c == 0 ? 256 : 4, st));
-        GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
-        // the chunk's size class picks the CTA shape; the first batch of a class tunes it
+        const uint32_t skip = skip_bits(*reinterpret_cast<const ArenaHeader *>(staging));
+        const uint64_t sb = Ls[c].scratch_bytes;
+        // the chunk's size class picks the CTA shapes; the first batch of a class tunes them
         const SizeClass cls = size_class(progs + lo[c], launches + lo[c], n_c);
         auto it = ws->class_shape.find(cls);
         if (it == ws->class_shape.end()) {
             // tuning clears the scratch control words: report an earlier chunk's error first
             if (c > 0 && (s = finish_sync(ws->scratch.p, st)) != GR_OK) return s;
-            uint32_t shape = 0;
-            gr_status ts = tune_shapes(*ws, ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, d_out + lo[c], st,
-                                       cls.s_max, &shape);
+            GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
+            if (!(skip & kSkipGeneral))
+                GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, sb, true, expand_grid(*ws), st));
+            Tuned t;
+            gr_status ts = tune_cfg(*ws, ws->arena.p, n_c, ws->scratch.p, sb, st, cls.s_max, skip, &t);
             if (ts != GR_OK) return ts;
-            it = ws->class_shape.emplace(cls, shape).first;
-            GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 4, st));
+            t.skip = 0;  // per chunk below
+            it = ws->class_shape.emplace(cls, t).first;
         }
-        LaunchCfg cfg = shape_cfg(*ws, n_c, it->second, cls.s_max);
-        if (!cfg.table_bytes) cfg = choose_cfg(*ws, n_c, cls.s_max);
-        GR_CUDA(launch_repair(ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, d_out + lo[c], cfg, st));
+        LaunchCfg cfg = full_cfg(*ws, n_c, it->second);
+        cfg.skip = skip;
+        // the queue counters (and, for the first chunk, the error word) are cleared first
+        GR_CUDA(enqueue_repair(ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, sb, d_out + lo[c], cfg,
+                               expand_grid(*ws), true, c == 0, st));
     }
     if (any_perm) {
         uint32_t low = 0xFFFFFFFFu;
@@ -1151,14 +1279,12 @@ gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches, con
     if ((s = ws->out.ensure((size_t)n * sizeof(gr_witnesses))) != GR_OK) return s;
     if ((s = ws->aux.ensure(mask_bytes)) != GR_OK) return s;
     GR_CUDA(cudaMemcpyAsync(ws->aux.p, masks, (size_t)n * 4, cudaMemcpyHostToDevice, st));
-    GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
-    GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
     const SizeClass cls = size_class(progs, launches, n);
     auto it = ws->class_shape.find(cls);
-    LaunchCfg cfg = it == ws->class_shape.end() ? choose_cfg(*ws, n, cls.s_max) : shape_cfg(*ws, n, it->second, cls.s_max);
-    if (!cfg.table_bytes) cfg = choose_cfg(*ws, n, cls.s_max);
-    GR_CUDA(launch_check(ws->arena.p, n, static_cast<const uint32_t *>(ws->aux.p), ws->scratch.p,
-                         static_cast<gr_witnesses *>(ws->out.p), cfg, st));
+    LaunchCfg cfg = it == ws->class_shape.end() ? choose_cfg(*ws, n, cls.s_max) : full_cfg(*ws, n, it->second);
+    cfg.skip = skip_bits(*reinterpret_cast<const ArenaHeader *>(ws->host_arena));
+    GR_CUDA(enqueue_check(ws->arena.p, n, static_cast<const uint32_t *>(ws->aux.p), ws->scratch.p, L.scratch_bytes,
+                          static_cast<gr_witnesses *>(ws->out.p), cfg, expand_grid(*ws), true, st));
     GR_CUDA(cudaMemcpyAsync(out, ws->out.p, (size_t)n * sizeof(gr_witnesses), cudaMemcpyDeviceToHost, st));
     return finish_sync(ws->scratch.p, st);
 }
@@ -1193,7 +1319,8 @@ gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode
     gr_witnesses *d_wit = reinterpret_cast<gr_witnesses *>(static_cast<uint8_t *>(ws->aux.p) + state_bytes);
     gr_repair_result *d_out =
         reinterpret_cast<gr_repair_result *>(static_cast<uint8_t *>(ws->aux.p) + state_bytes + wit_bytes);
-    GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, expand_grid(*ws), st));
+    GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
+    GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, L.scratch_bytes, false, expand_grid(*ws), st));
     const gr_options o = opts_or_default(opts);
     GR_CUDA(launch_plain_init(ws->arena.p, 0, o, d_state, st));
     const LaunchCfg cfg = choose_cfg(*ws, 1);

@@ -27,10 +27,12 @@ constexpr uint32_t kClauseSet = 1u << kClauseSetLog2;  // clause hash set (>= 2 
 constexpr uint32_t kNoClause = 0xFFFFFFFFu;            // its empty marker
 constexpr uint32_t kMinTableBytes = 25u * 2u * kChunkWords;  // one chunk for 25 rows
 constexpr uint32_t kErrTableTooSmall = 1u;  // bits of the device error word (scratch control word 1)
+constexpr uint32_t kErrArgs = 4u;           // the launch's n or scratch size does not match the arena
+constexpr uint8_t kStmtInjective = 1u;      // DevStmt::flags: no two threads of a block share an address
 
 // One statement, with map coefficients reduced modulo its array's size.
 struct DevStmt {
-    uint8_t op, space, kind, _pad;
+    uint8_t op, space, kind, flags;  // flags: kStmtInjective
     uint32_t am, bm, cm;   // a, b, c mod M
     uint32_t perm_off;     // absolute index into the arena's permutation area
     uint16_t gk, gr;       // guard: active iff gk == 0 || tid % gk == gr
@@ -59,14 +61,19 @@ struct DevProg {
     uint16_t slot_gr[GR_MAX_SLOTS];
     uint8_t rep[32];       // lowest instance with the same array, map and guard
     uint32_t gapslots[32]; // slots whose barriers run between instances k and k+1
-    uint32_t n_neg, _r3[3];
+    uint32_t n_neg;
+    uint32_t fast;         // 1: checked by the relation kernel (shared array only, blocks alike)
+    uint32_t _r3[2];
     uint32_t neg[GR_MAX_NEG];  // negative clauses given with the program
     DevStmt stmts[GR_MAX_STMTS];  // one per executed statement instance
 };
 static_assert(sizeof(DevProg) % 16 == 0, "DevProg alignment");
 
 // Arena = ArenaHeader | DevProg[n] | order[n] | seg_base[n+1] | items[] | perm[]
-// Scratch = ctrl (256 B) | segmask u64[] | segrange u32[] | trace u16[]
+//   order: the n_fast programs the relation kernel checks, then the others,
+//   each part largest first; items: the expansion work items of the other
+//   programs (n_items_gen of them), then those of the n_fast programs.
+// Scratch = ctrl (256 B) | segmask u64[] | segrange u32[] | trace u16[] | wide | rel gr_witnesses[n]
 struct ArenaHeader {
     uint32_t magic, n_progs, s_max, b_max;  // most statement instances / blocks of any program
     uint64_t progs_off, order_off, segbase_off, perm_off;  // bytes from the arena start
@@ -76,7 +83,9 @@ struct ArenaHeader {
     uint64_t scratch_segrange_off;
     uint64_t scratch_wide_off;  // wide lane: LoopState[n] | gr_witnesses[n] | WideCtl
     uint64_t items_off, n_items;  // expansion work items (uint4: program, first, end segment)
-    uint64_t _r2[2];
+    uint64_t scratch_rel_off;     // each program's conflict relation (gr_witnesses rows)
+    uint32_t n_fast;              // programs checked by the relation kernel (first in order)
+    uint32_t n_items_gen;         // expansion items of the other programs (first in items)
 };
 static_assert(sizeof(ArenaHeader) == 128, "ArenaHeader layout");
 
@@ -86,6 +95,7 @@ struct LoopState {
     uint32_t mask, probe, done, status, iters, forced, forbidden, max_iters;
     uint32_t greedy, _pad0;
     uint64_t access_pairs, t_start;
+    uint64_t deadline_ns;  // 0: none
     uint32_t traj[GR_MAX_ITERS];
     uint32_t acc_intra[32], acc_inter[32];
 };
@@ -98,11 +108,25 @@ struct WideCtl {
     uint32_t _pad;
 };
 
-struct LaunchCfg {
-    uint32_t grid;         // CTAs of the persistent kernels
-    uint32_t table_bytes;  // shared-memory owner-table budget per CTA
-    uint32_t shape;        // index into kShapes
+// Launch of the relation kernel (relation.cu).
+struct RelCfg {
+    uint32_t grid;         // CTAs (persistent)
+    uint32_t table_bytes;  // owner-table budget per CTA
+    uint32_t shape;        // index into kRelShapes
 };
+
+// Launch of a repair: the general check kernel (k_check, one CTA per program
+// of the batch's general part), the relation kernel and the loop kernel.
+struct LaunchCfg {
+    uint32_t grid;         // CTAs of k_check
+    uint32_t table_bytes;  // its owner-table budget per CTA
+    uint32_t shape;        // index into kShapes
+    RelCfg rel;
+    uint32_t loop_grid;    // CTAs of the loop kernel
+    uint32_t skip;         // kSkip* bits: parts of the batch known to be empty
+};
+constexpr uint32_t kSkipGeneral = 1u;  // no general program: no expansion, no k_check
+constexpr uint32_t kSkipFast = 2u;     // no program for the relation kernel
 
 // CTA shapes the persistent kernels are instantiated for.
 struct LaunchShape {
@@ -114,12 +138,17 @@ constexpr uint32_t kShapeBalanced = 16u;  // ... plus: grid cut so every CTA get
 extern const LaunchShape kShapes[kNumShapes];
 size_t dyn_bytes(uint32_t table_bytes);
 size_t mhs_smem_bytes();
+constexpr uint32_t kNumRelShapes = 6;
+extern const LaunchShape kRelShapes[kNumRelShapes];
+size_t rel_fixed_bytes();   // the relation kernel's shared memory besides its table
+size_t loop_smem_bytes();   // the loop kernel's shared memory per CTA
+constexpr uint32_t kLoopThreads = 128;  // the loop kernel's CTA: four warps, a program each
 
 // Host-side helpers (capi.cu).
 struct Layout {
     size_t progs_off, order_off, segbase_off, items_off, perm_off, arena_bytes;
     uint64_t n_items;
-    size_t segmask_off, segrange_off, trace_off, wide_off, scratch_bytes;
+    size_t segmask_off, segrange_off, trace_off, wide_off, rel_off, scratch_bytes;
     uint64_t n_segments;
     std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
 };
@@ -146,19 +175,45 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n);
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
                uint8_t *arena, uint32_t *table_bad = nullptr, bool range_only = false);
 bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst, bool range_only = false);
-LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status);
+// The launch of a repair of n packed programs at d_arena on the current
+// device: the shapes gr_tune_packed recorded for (d_arena, n), else the
+// defaults, plus the kSkip* bits `skip`.
+LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, gr_status *status);
+// Options: GR_EINVAL for an unknown strategy or values out of range; the
+// defaults filled in (NULL: grid enabled, 64 iterations, no deadline).
+gr_status validate_opts(const gr_options *o);
+gr_options opts_or_default(const gr_options *o);
 void set_last_error(const char *msg);
 
 // Host-callable launchers (kernels.cu).
-cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint32_t grid, cudaStream_t st);
+// general_only: only the general programs' traces (the relation kernel
+// computes the other programs' addresses itself).
+cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint64_t scratch_bytes, bool general_only,
+                          uint32_t grid, cudaStream_t st);
 // Device check that the batch's permutation tables are permutations (the
 // lowest failing program + base, complemented, into *d_bad by atomicMax).
 cudaError_t launch_perm_check(const void *d_arena, uint32_t n, uint32_t base, uint32_t *d_bad, uint32_t sms,
                               cudaStream_t st);
-cudaError_t launch_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
-                          gr_repair_result *d_out, LaunchCfg cfg, cudaStream_t st);
+// One check per general program (d_masks NULL: the empty mask, rows into the
+// scratch's relation area when d_out is NULL).
 cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
-                         gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st);
+                         uint64_t scratch_bytes, gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st);
+// The same for the programs the relation kernel takes.
+cudaError_t launch_relation(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
+                            uint64_t scratch_bytes, gr_witnesses *d_out, RelCfg cfg, cudaStream_t st);
+// Algorithm 1 per program over the relations in the scratch.
+cudaError_t launch_loop(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
+                        uint64_t scratch_bytes, gr_repair_result *d_out, uint32_t grid, cudaStream_t st);
+// The whole repair of a packed batch on the device: the general programs'
+// traces (when `expand`), the relations, the loop.  Clears the work-queue
+// counters first, and the device error word too when clear_error.
+cudaError_t enqueue_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
+                           uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
+                           bool expand, bool clear_error, cudaStream_t st);
+// One check per program of a packed batch under d_masks.
+cudaError_t enqueue_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
+                          uint64_t scratch_bytes, gr_witnesses *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
+                          bool expand, cudaStream_t st);
 cudaError_t launch_plain_init(const void *d_arena, uint32_t p, const gr_options &opts,
                               LoopState *d_state, cudaStream_t st);
 cudaError_t launch_plain_check(const void *d_arena, uint32_t p, void *d_scratch, LoopState *d_state,
@@ -180,5 +235,7 @@ size_t wide_bytes(uint32_t n);
 LaunchCfg wide_launch_cfg(uint32_t n, uint32_t s_max, gr_status *status);
 size_t fixed_smem_bytes();
 cudaError_t configure_kernels(uint32_t max_dynamic_smem);
+cudaError_t configure_relation(uint32_t max_dynamic_smem);
+cudaError_t configure_loop(uint32_t max_dynamic_smem);
 
 }  // namespace gr

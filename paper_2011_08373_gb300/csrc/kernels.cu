@@ -17,15 +17,19 @@
 //                     low 5 compact variables ride in the bits of a 32-bit word,
 //                     the rest are enumerated by popcount level (Gosper order)
 //                     with a weight bound; ties go to the lowest mask.
-//   k_repair        : persistent work-queue kernel, one CTA per program, that
-//                     runs check -> clauses -> solve to the fixed point.
+//   k_check         : persistent work-queue kernel, one CTA per program, one
+//                     check per program of the batch's general part (a
+//                     global array, or blocks that differ); under the empty
+//                     mask it gives the conflict relation the loop kernel
+//                     (loop.cu) filters.  Programs on the shared array with
+//                     alike blocks go to the relation kernel (relation.cu).
 //   k_plain_*       : the same stages as separate launches, one check launch
 //                     per iteration (host-driven loop).
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
-#include "engine.cuh"
+#include "device.cuh"
 
 namespace gr {
 
@@ -77,6 +81,7 @@ struct Smem {
     // loop state
     uint32_t mask, probe, done, status, iters, forced, forbidden, max_iters;
     uint32_t greedy, step;  // mhs strategy: greedy proposals pending; kind of this step
+    unsigned long long deadline_ns;  // 0: none; else the loop's time limit (gr_options::deadline_us)
     uint32_t diverge, n_cl, n_rows, item;
     uint32_t rel_sh, rel_gi, rel_gx, sol_found, sol_mask, sol_weight;
     uint32_t *err;  // device error word (scratch control area)
@@ -92,71 +97,6 @@ __device__ __forceinline__ uint32_t *mh_cl(Smem &sm) {
 
 size_t fixed_smem_bytes() { return kFixedSmem; }
 size_t mhs_smem_bytes() { return align_up(sizeof(MhsSmem), 16); }
-
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ uint32_t range_mask(uint32_t i, uint32_t j) {  // bits [i, j)
-    const uint32_t hi = j >= 32 ? 0xFFFFFFFFu : ((1u << j) - 1u);
-    return hi & ~((1u << i) - 1u);
-}
-
-// Gaps between executed instances where an enabled barrier (of the slots in
-// `mask`) runs: gap k (between instances k and k+1) runs the barriers of the
-// slots gapslots[k].  Without loops or explicit places gap k is slot k.
-__device__ __forceinline__ uint32_t gap_mask(const DevProg &P, uint32_t mask) {
-    if (!P.general) return mask;
-    uint32_t g = 0;
-    for (uint32_t k = 0; k + 1 < P.n_stmts; ++k)
-        if (P.gapslots[k] & mask) g |= 1u << k;
-    return g;
-}
-
-// The slots whose barriers run in the gaps `gaps`.
-__device__ __forceinline__ uint32_t slots_of_gaps(const DevProg &P, uint32_t gaps) {
-    if (!P.general) return gaps;
-    uint32_t m = 0;
-    for (uint32_t t = gaps; t; t &= t - 1u) m |= P.gapslots[__ffs(t) - 1u];
-    return m;
-}
-
-// Instances in the same phase as s when the gaps in `cut` hold an enabled
-// barrier: gap k separates instances k and k+1.
-__device__ __forceinline__ uint32_t phase_of(uint32_t s, uint32_t cut, uint32_t S) {
-    const uint32_t below = cut & ((1u << s) - 1u);
-    const uint32_t start = below ? 32u - __clz(below) : 0u;
-    const uint32_t above = cut >> s;
-    const uint32_t end = above ? s + __ffs(above) - 1u : S - 1u;
-    return range_mask(start, end + 1u);
-}
-
-__device__ __forceinline__ uint32_t pext32(uint32_t x, uint32_t m) {
-    uint32_t out = 0, j = 0;
-    for (uint32_t t = m; t; t &= t - 1u, ++j)
-        if (x & (t & (0u - t))) out |= 1u << j;
-    return out;
-}
-
-__device__ __forceinline__ uint32_t pdep32(uint32_t x, uint32_t m) {
-    uint32_t out = 0, j = 0;
-    for (uint32_t t = m; t; t &= t - 1u, ++j)
-        if ((x >> j) & 1u) out |= t & (0u - t);
-    return out;
-}
-
-// Low assignments l in [0,32) with bit k set, k < 5.
-__device__ __forceinline__ uint32_t low_pattern(uint32_t k) {
-    const uint32_t p[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
-    return p[k];
-}
-
-__device__ __forceinline__ void or_row(uint32_t *rows, uint32_t i, uint32_t bits) {
-    volatile uint32_t *vr = rows;
-    if (bits & ~vr[i]) atomicOr(&rows[i], bits);
-}
 
 // ---------------------------------------------------------------------------
 // Program load
@@ -706,35 +646,6 @@ __device__ void check_blocks(Smem &sm, uint16_t *tab, uint32_t table_bytes, cons
 // Exact minimum-weight hitting set
 // ---------------------------------------------------------------------------
 
-struct BinomTable {
-    uint32_t v[GR_MAX_SLOTS + 1][GR_MAX_SLOTS + 1];  // C(n, k), n <= 32: at most C(32, 16) < 2^32
-    constexpr BinomTable() : v() {
-        for (int n = 0; n <= GR_MAX_SLOTS; ++n) {
-            v[n][0] = 1;
-            for (int k = 1; k <= n; ++k) v[n][k] = v[n - 1][k - 1] + (k <= n - 1 ? v[n - 1][k] : 0);
-        }
-    }
-};
-__constant__ BinomTable c_binom = BinomTable();
-
-__device__ __forceinline__ uint32_t unrank_colex(uint32_t rank, uint32_t k, uint32_t n) {
-    uint32_t h = 0;
-    int c = (int)n - 1;
-    for (uint32_t i = k; i >= 1; --i) {
-        while (c >= 0 && c_binom.v[c][i] > rank) --c;
-        h |= 1u << c;
-        rank -= c_binom.v[c][i];
-        --c;
-    }
-    return h;
-}
-
-__device__ __forceinline__ uint32_t gosper_next(uint32_t h) {
-    const uint32_t c = h & (0u - h);
-    const uint32_t r = h + c;
-    return (((r ^ h) >> 2) >> (__ffs(c) - 1u)) | r;
-}
-
 // Least (weight, mask) with forced <= mask, mask & forbidden == 0, hitting
 // every clause of mh_cl(sm)[0..n_cl) and containing no negative clause neg[0..n_neg).
 // Result in sm.sol_found / sol_mask / sol_weight.  All threads must call.
@@ -1114,6 +1025,7 @@ __device__ void loop_init(Smem &sm, const gr_options &opts) {
         sm.access_pairs = 0;
         sm.n_cl = 0;
         sm.t_start = globaltimer();
+        sm.deadline_ns = opts.deadline_us * 1000ull;
         sm.probe = P.mode == GR_MODE_REMOVE ? 1u : 0u;
         sm.greedy = opts.strategy == GR_STRATEGY_MHS ? 1u : 0u;
         sm.mask = P.existing;
@@ -1205,6 +1117,9 @@ __device__ void loop_step(Smem &sm, MhsSmem &mh) {
             if (sm.iters >= sm.max_iters) {
                 sm.status = GR_ITER_CAP;
                 sm.done = 1;
+            } else if (sm.deadline_ns && globaltimer() - sm.t_start >= sm.deadline_ns) {
+                sm.status = GR_TIMEOUT;
+                sm.done = 1;
             }
         }
     }
@@ -1252,24 +1167,6 @@ __device__ void write_result(Smem &sm, gr_repair_result *out) {
 // Kernels
 // ---------------------------------------------------------------------------
 
-struct ArenaView {
-    const ArenaHeader *h;
-    const DevProg *progs;
-    const uint32_t *order;
-    const uint64_t *segbase;
-    const uint16_t *perm;  // permutation tables, entries below 65,536
-};
-
-__device__ __forceinline__ ArenaView view(const uint8_t *arena) {
-    ArenaView v;
-    v.h = reinterpret_cast<const ArenaHeader *>(arena);
-    v.progs = reinterpret_cast<const DevProg *>(arena + v.h->progs_off);
-    v.order = reinterpret_cast<const uint32_t *>(arena + v.h->order_off);
-    v.segbase = reinterpret_cast<const uint64_t *>(arena + v.h->segbase_off);
-    v.perm = reinterpret_cast<const uint16_t *>(arena + v.h->perm_off);
-    return v;
-}
-
 // K0: CTAs take work items (runs of up to kItemSegs (statement, block)
 // segments of one program, largest programs first, so that a few large
 // programs spread over many CTAs and many small ones share them; or block 0
@@ -1277,9 +1174,16 @@ __device__ __forceinline__ ArenaView view(const uint8_t *arena) {
 // warp per segment of t_pad threads.  Writes the u16 address trace, and per
 // segment the mask of 1,024-word chunks and the [min, max] address of its
 // active accesses (min > max when none is active).
-__global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ arena, uint8_t *__restrict__ scratch) {
+__global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ arena, uint8_t *__restrict__ scratch,
+                                                uint64_t scratch_bytes, uint32_t general_only) {
     const ArenaView V = view(arena);
-    const uint64_t n_items = V.h->n_items;
+    if (V.h->magic != kArenaMagic || scratch_bytes < V.h->scratch_bytes) {
+        if (threadIdx.x == 0) atomicOr(reinterpret_cast<uint32_t *>(scratch) + 1, kErrArgs);
+        return;
+    }
+    // the general programs' items come first: the relation kernel computes
+    // the other programs' addresses itself
+    const uint64_t n_items = general_only ? V.h->n_items_gen : V.h->n_items;
     const uint4 *items = reinterpret_cast<const uint4 *>(arena + V.h->items_off);
     uint16_t *traces = reinterpret_cast<uint16_t *>(scratch + V.h->scratch_trace_off);
     uint64_t *segmask = reinterpret_cast<uint64_t *>(scratch + V.h->scratch_segmask_off);
@@ -1437,76 +1341,52 @@ __device__ __forceinline__ Dyn dyn_smem() {
     return d;
 }
 
-// K4: persistent repair.  CTAs take programs from a queue in the host's order
-// (largest first) and run Algorithm 1 on each.  Instantiated for several CTA
-// shapes (threads x CTAs per SM); the host picks one per batch.
-template <uint32_t NT, uint32_t MINB>
-__global__ void __launch_bounds__(NT, MINB)
-    k_repair(const uint8_t *__restrict__ arena, uint32_t n, gr_options opts, uint8_t *__restrict__ scratch,
-             gr_repair_result *__restrict__ out, uint32_t table_bytes) {
-    Dyn d = dyn_smem();
-    Smem &sm = *d.sm;
-    const ArenaView V = view(arena);
-    const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
-    const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
-    const uint32_t *segrange = reinterpret_cast<const uint32_t *>(scratch + V.h->scratch_segrange_off);
-    uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
-    if (threadIdx.x == 0) sm.err = &ctrl[1];
-    for (;;) {
-        if (threadIdx.x == 0) sm.item = atomicAdd(&ctrl[0], 1u);
-        __syncthreads();
-        const uint32_t item = sm.item;
-        if (item >= n) break;
-        const uint32_t p = V.order[item];
-        load_program(sm, &V.progs[p]);
-        const uint16_t *trace = traces + sm.prog.trace_off;
-        const uint64_t *sgm = segmask + sm.prog.segmask_off;
-        const uint32_t *sgr = segrange + sm.prog.segmask_off;
-        loop_init(sm, opts);
-        while (!sm.done) {
-            const uint32_t mask = sm.mask;
-            prepare_check(sm, mask);
-            check_misc(sm, mask);
-            check_blocks(sm, d.tab, table_bytes, trace, sgm, sgr, 0, sm.prog.blocks, true);
-            loop_step(sm, *d.mh);
-        }
-        write_result(sm, &out[p]);
-    }
-}
-
-// One check per program under masks[p] (persistent, same queue).
+// One check per program of the batch's general part (items n_fast..n-1 of
+// the order: a global array, or blocks that differ) under masks[p], or under
+// the empty mask when masks is NULL: then the witness rows are the
+// program's conflict relation, written to the scratch's relation area for
+// the loop kernel (out == NULL) or to out.  Persistent: CTAs take programs
+// from a queue, largest first.  Instantiated for several CTA shapes (threads
+// x CTAs per SM); the host picks one per batch.
 template <uint32_t NT, uint32_t MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_check(const uint8_t *__restrict__ arena, uint32_t n, const uint32_t *__restrict__ masks,
-            uint8_t *__restrict__ scratch, gr_witnesses *__restrict__ out, uint32_t table_bytes) {
+            uint8_t *__restrict__ scratch, uint64_t scratch_bytes, gr_witnesses *__restrict__ out,
+            uint32_t table_bytes) {
     Dyn d = dyn_smem();
     Smem &sm = *d.sm;
     const ArenaView V = view(arena);
+    uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
+    if (!launch_matches(V, n, scratch_bytes)) {
+        if (threadIdx.x == 0) atomicOr(&ctrl[1], kErrArgs);
+        return;
+    }
     const uint16_t *traces = reinterpret_cast<const uint16_t *>(scratch + V.h->scratch_trace_off);
     const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
     const uint32_t *segrange = reinterpret_cast<const uint32_t *>(scratch + V.h->scratch_segrange_off);
-    uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
+    gr_witnesses *dst = out ? out : reinterpret_cast<gr_witnesses *>(scratch + V.h->scratch_rel_off);
+    const uint32_t first = V.h->n_fast;
     if (threadIdx.x == 0) sm.err = &ctrl[1];
     for (;;) {
-        if (threadIdx.x == 0) sm.item = atomicAdd(&ctrl[0], 1u);
+        if (threadIdx.x == 0) sm.item = first + atomicAdd(&ctrl[0], 1u);
         __syncthreads();
         const uint32_t item = sm.item;
         if (item >= n) break;
         const uint32_t p = V.order[item];
         load_program(sm, &V.progs[p]);
-        const uint32_t mask = masks[p];
+        const uint32_t mask = masks ? masks[p] : 0u;
         prepare_check(sm, mask);
         check_misc(sm, mask);
         check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off,
                      segrange + sm.prog.segmask_off, 0, sm.prog.blocks, true);
         if (threadIdx.x < 32) {
-            out[p].race_intra[threadIdx.x] = sm.rows_intra[threadIdx.x];
-            out[p].race_inter[threadIdx.x] = sm.rows_inter[threadIdx.x];
+            dst[p].race_intra[threadIdx.x] = sm.rows_intra[threadIdx.x];
+            dst[p].race_inter[threadIdx.x] = sm.rows_inter[threadIdx.x];
         }
         if (threadIdx.x == 0) {
-            out[p].diverge = sm.diverge;
-            out[p].n_stmts = sm.prog.n_stmts;
-            out[p].access_pairs = sm.pairs;
+            dst[p].diverge = sm.diverge;
+            dst[p].n_stmts = sm.prog.n_stmts;
+            dst[p].access_pairs = sm.pairs;
         }
         __syncthreads();
     }
@@ -1524,6 +1404,7 @@ __device__ void state_to_smem(Smem &sm, const LoopState *st) {
         sm.forced = st->forced;
         sm.forbidden = st->forbidden;
         sm.max_iters = st->max_iters;
+        sm.deadline_ns = st->deadline_ns;
         sm.access_pairs = st->access_pairs;
         sm.t_start = st->t_start;
         sm.greedy = st->greedy;
@@ -1547,6 +1428,7 @@ __device__ void state_from_smem(const Smem &sm, LoopState *st) {
         st->forced = sm.forced;
         st->forbidden = sm.forbidden;
         st->max_iters = sm.max_iters;
+        st->deadline_ns = sm.deadline_ns;
         st->access_pairs = sm.access_pairs;
         st->t_start = sm.t_start;
         st->greedy = sm.greedy;
@@ -1820,16 +1702,13 @@ cudaError_t configure_kernels(uint32_t max_dynamic_smem) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
         if (e != cudaSuccess) return e;
     }
-    if ((e = set_smem(k_repair<512, 2>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = set_smem(k_repair<256, 3>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = set_smem(k_repair<256, 4>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = set_smem(k_repair<1024, 1>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = set_smem(k_repair<384, 3>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<512, 2>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<256, 3>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<256, 4>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<1024, 1>, max_dynamic_smem)) != cudaSuccess) return e;
     if ((e = set_smem(k_check<384, 3>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = configure_relation(max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = configure_loop(max_dynamic_smem)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1840,37 +1719,24 @@ cudaError_t launch_perm_check(const void *d_arena, uint32_t n, uint32_t base, ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint32_t grid, cudaStream_t st) {
-    k_expand<<<grid, 256, 0, st>>>(static_cast<const uint8_t *>(d_arena), static_cast<uint8_t *>(d_scratch));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
-                          gr_repair_result *d_out, LaunchCfg cfg, cudaStream_t st) {
-    const uint8_t *a = static_cast<const uint8_t *>(d_arena);
-    uint8_t *sc = static_cast<uint8_t *>(d_scratch);
-    const size_t smem = dyn_bytes(cfg.table_bytes);
-    switch (cfg.shape & kShapeMask) {
-        case 1: k_repair<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
-        case 2: k_repair<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
-        case 3: k_repair<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
-        case 4: k_repair<384, 3><<<cfg.grid, 384, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
-        default: k_repair<512, 2><<<cfg.grid, 512, smem, st>>>(a, n, opts, sc, d_out, cfg.table_bytes); break;
-    }
+cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint64_t scratch_bytes, bool general_only,
+                          uint32_t grid, cudaStream_t st) {
+    k_expand<<<grid, 256, 0, st>>>(static_cast<const uint8_t *>(d_arena), static_cast<uint8_t *>(d_scratch),
+                                   scratch_bytes, general_only ? 1u : 0u);
     return cudaGetLastError();
 }
 
 cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
-                         gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st) {
+                         uint64_t scratch_bytes, gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st) {
     const uint8_t *a = static_cast<const uint8_t *>(d_arena);
     uint8_t *sc = static_cast<uint8_t *>(d_scratch);
     const size_t smem = dyn_bytes(cfg.table_bytes);
     switch (cfg.shape & kShapeMask) {
-        case 1: k_check<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
-        case 2: k_check<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
-        case 3: k_check<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
-        case 4: k_check<384, 3><<<cfg.grid, 384, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
-        default: k_check<512, 2><<<cfg.grid, 512, smem, st>>>(a, n, d_masks, sc, d_out, cfg.table_bytes); break;
+        case 1: k_check<256, 3><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
+        case 2: k_check<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
+        case 3: k_check<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
+        case 4: k_check<384, 3><<<cfg.grid, 384, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
+        default: k_check<512, 2><<<cfg.grid, 512, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
     }
     return cudaGetLastError();
 }
@@ -1895,6 +1761,43 @@ cudaError_t launch_plain_solve(const void *d_arena, uint32_t p, LoopState *d_sta
     k_plain_solve<<<1, kThreads, dyn_bytes(kMinTableBytes), st>>>(static_cast<const uint8_t *>(d_arena), p,
                                                                    d_state, d_wit, out);
     return cudaGetLastError();
+}
+
+// Work-queue counters (scratch control words 0, 2, 3) and, when clear_error,
+// the device error word (word 1).
+static cudaError_t clear_ctrl(void *d_scratch, bool clear_error, cudaStream_t st) {
+    if (clear_error) return cudaMemsetAsync(d_scratch, 0, 256, st);
+    cudaError_t e = cudaMemsetAsync(d_scratch, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(static_cast<uint32_t *>(d_scratch) + 2, 0, 8, st);
+    return e;
+}
+
+cudaError_t enqueue_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
+                           uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
+                           bool expand, bool clear_error, cudaStream_t st) {
+    const bool general = !(cfg.skip & kSkipGeneral), fast = !(cfg.skip & kSkipFast);
+    cudaError_t e = clear_ctrl(d_scratch, clear_error, st);
+    if (e == cudaSuccess && general && expand)
+        e = launch_expand(d_arena, d_scratch, scratch_bytes, true, expand_grid, st);
+    if (e == cudaSuccess && fast)
+        e = launch_relation(d_arena, n, nullptr, d_scratch, scratch_bytes, nullptr, cfg.rel, st);
+    if (e == cudaSuccess && general)
+        e = launch_check(d_arena, n, nullptr, d_scratch, scratch_bytes, nullptr, cfg, st);
+    if (e == cudaSuccess) e = launch_loop(d_arena, n, opts, d_scratch, scratch_bytes, d_out, cfg.loop_grid, st);
+    return e;
+}
+
+cudaError_t enqueue_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
+                          uint64_t scratch_bytes, gr_witnesses *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
+                          bool expand, cudaStream_t st) {
+    const bool general = !(cfg.skip & kSkipGeneral), fast = !(cfg.skip & kSkipFast);
+    cudaError_t e = clear_ctrl(d_scratch, true, st);
+    if (e == cudaSuccess && general && expand)
+        e = launch_expand(d_arena, d_scratch, scratch_bytes, true, expand_grid, st);
+    if (e == cudaSuccess && fast)
+        e = launch_relation(d_arena, n, d_masks, d_scratch, scratch_bytes, d_out, cfg.rel, st);
+    if (e == cudaSuccess && general) e = launch_check(d_arena, n, d_masks, d_scratch, scratch_bytes, d_out, cfg, st);
+    return e;
 }
 
 size_t wide_bytes(uint32_t n) {

@@ -8,16 +8,21 @@
 // entry point lets them repair a batch with only their own input (the packed
 // arena) and output (the results) buffers.
 //
-// The scratch (address traces, per-segment masks and ranges, the work-queue
-// counter and the device error word) lives in `g_noalloc_scratch`, a file-scope
-// __device__ array of kNoAllocScratchBytes.  Every GPU that loads the library
-// holds it until the process exits.  Its device address is looked up once per
-// device, on the first call made with that device current; make that first
-// call before any stream capture.  Every call shares the one array and it
-// keeps the last call's contents: the control words are cleared on each call,
-// everything else is rewritten before it is read.  Calls that overlap on the
-// GPU (two streams, two host threads) race on the array and must not be
-// issued; the host-side lock below only orders the enqueueing.
+// The scratch (address traces, per-segment masks and ranges, the conflict
+// relations, the work-queue counters and the device error word) lives in
+// `g_noalloc_scratch`, a file-scope __device__ array of kNoAllocScratchBytes.
+// Every GPU that loads the library holds it until the process exits.  Its
+// device address is looked up once per device, on the first call made with
+// that device current; make that first call before any stream capture.  The
+// cached address belongs to the device's context: after cudaDeviceReset the
+// next call on that device must not be made (the context that the address
+// belongs to is gone).  Every call shares the one array and it keeps the last
+// call's contents: the control words are cleared on each call, everything
+// else is rewritten before it is read.  Calls that overlap on the GPU (two
+// streams, two host threads) race on the array and must not be issued; the
+// host-side lock below only orders the enqueueing.  The device error word
+// stays inside the array and is not read back: the library sizes every
+// launch from the arena header, which this call checks first.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -78,9 +83,6 @@ gr_status noalloc_setup(int *dev_out, void **ptr_out) {
 
 }  // namespace
 
-// Launch-shape helper shared with capi.cu (same choice as gr_repair_packed).
-LaunchCfg packed_launch_cfg(uint32_t n, gr_status *status);
-
 }  // namespace gr
 
 using namespace gr;
@@ -89,12 +91,12 @@ extern "C" gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, c
                                               gr_repair_result *d_out, void *stream) {
     if (!d_arena || !d_out || n == 0) return noalloc_fail(GR_EINVAL, "NULL buffer or n == 0");
     if (reinterpret_cast<uintptr_t>(d_arena) % 256) return noalloc_fail(GR_EINVAL, "d_arena must be 256-byte aligned");
-    if (opts && opts->max_iters > GR_MAX_ITERS) return noalloc_fail(GR_EINVAL, "max_iters above %d", GR_MAX_ITERS);
+    gr_status s = validate_opts(opts);  // the same options gr_repair_packed accepts
+    if (s != GR_OK) return s;
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     int dev = 0;
     void *scratch = nullptr;
-    gr_status s = noalloc_setup(&dev, &scratch);
-    if (s != GR_OK) return s;
+    if ((s = noalloc_setup(&dev, &scratch)) != GR_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the arena header says how much scratch the batch needs
     ArenaHeader h;
@@ -106,17 +108,14 @@ extern "C" gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, c
     if (h.scratch_bytes > kNoAllocScratchBytes)
         return noalloc_fail(GR_ECAPACITY, "batch needs %llu scratch bytes; the fixed array holds %llu",
                             (unsigned long long)h.scratch_bytes, (unsigned long long)kNoAllocScratchBytes);
-    LaunchCfg cfg = packed_launch_cfg(n, &s);
+    // the same launch as gr_repair_packed: the shapes gr_tune_packed recorded
+    // for this arena, else the defaults
+    const uint32_t skip = (h.n_fast == 0 ? kSkipFast : 0u) | (h.n_fast == h.n_progs ? kSkipGeneral : 0u);
+    const LaunchCfg cfg = packed_launch_cfg(d_arena, n, skip, &s);
     if (s != GR_OK) return noalloc_fail(s, "launch configuration failed");
-    gr_options o;
-    memset(&o, 0, sizeof(o));
-    o.grid_enabled = opts ? opts->grid_enabled : 1;
-    o.strategy = opts ? opts->strategy : 0;
-    o.max_iters = (opts && opts->max_iters) ? opts->max_iters : GR_MAX_ITERS;
-    // the queue counter and the error word must start at zero
-    e = cudaMemsetAsync(scratch, 0, 256, st);
-    if (e == cudaSuccess) e = launch_expand(d_arena, scratch, (uint32_t)g_noalloc_sms[dev] * 8u, st);
-    if (e == cudaSuccess) e = launch_repair(d_arena, n, o, scratch, d_out, cfg, st);
+    // the queue counters and the error word start at zero (cleared first)
+    e = enqueue_repair(d_arena, n, opts_or_default(opts), scratch, kNoAllocScratchBytes, d_out, cfg,
+                       (uint32_t)g_noalloc_sms[dev] * 8u, true, true, st);
     if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "launch: %s", cudaGetErrorString(e));
     return GR_OK;
 }

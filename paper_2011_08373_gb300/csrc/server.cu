@@ -196,16 +196,22 @@ bool dispatch(gr_server *s, Slot &sl, std::unique_lock<std::mutex> &lk) {
         s_max = std::max(s_max, exec_count(progs[i]));
         b_max = std::max(b_max, ls[i].blocks);
     }
-    const LaunchCfg cfg = wide ? wide_launch_cfg(n, s_max, &cs) : packed_launch_cfg(n, &cs);
+    const ArenaHeader &hd = *reinterpret_cast<const ArenaHeader *>(sl.h_arena);
+    const uint32_t skip = (hd.n_fast == 0 ? kSkipFast : 0u) | (hd.n_fast == n ? kSkipGeneral : 0u);
+    const LaunchCfg cfg = wide ? wide_launch_cfg(n, s_max, &cs) : packed_launch_cfg(sl.d_arena, n, skip, &cs);
     e = cudaMemcpyAsync(sl.d_arena, sl.h_arena, L.arena_bytes, cudaMemcpyHostToDevice, sl.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_scratch, 0, 256, sl.stream);
-    if (e == cudaSuccess) e = launch_expand(sl.d_arena, sl.d_scratch, s->expand_grid, sl.stream);
     if (e == cudaSuccess) {
-        if (wide)
-            e = launch_wide(sl.d_arena, n, b_max, s->opts, sl.d_scratch, L.wide_off, sl.d_out, cfg.table_bytes,
-                            sl.stream);
-        else
-            e = launch_repair(sl.d_arena, n, s->opts, sl.d_scratch, sl.d_out, cfg, sl.stream);
+        if (wide) {
+            e = cudaMemsetAsync(sl.d_scratch, 0, 256, sl.stream);
+            if (e == cudaSuccess)
+                e = launch_expand(sl.d_arena, sl.d_scratch, L.scratch_bytes, false, s->expand_grid, sl.stream);
+            if (e == cudaSuccess)
+                e = launch_wide(sl.d_arena, n, b_max, s->opts, sl.d_scratch, L.wide_off, sl.d_out, cfg.table_bytes,
+                                sl.stream);
+        } else {
+            e = enqueue_repair(sl.d_arena, n, s->opts, sl.d_scratch, L.scratch_bytes, sl.d_out, cfg, s->expand_grid,
+                               true, true, sl.stream);
+        }
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost,
@@ -284,21 +290,19 @@ gr_status gr_server_create(uint64_t mem_budget_bytes, uint32_t n_slots, uint32_t
     if (!out) return fail(GR_EINVAL, "out is NULL");
     if (n_slots < 1 || n_slots > 16) return fail(GR_EINVAL, "n_slots %u outside 1..16", n_slots);
     if (max_inflight < 1) return fail(GR_EINVAL, "max_inflight must be >= 1");
-    if (opts && opts->max_iters > GR_MAX_ITERS) return fail(GR_EINVAL, "max_iters above %d", GR_MAX_ITERS);
+    gr_status vs = validate_opts(opts);
+    if (vs != GR_OK) return vs;
     const uint64_t per_slot = mem_budget_bytes / n_slots;
     if (per_slot < (8ull << 20)) return fail(GR_EINVAL, "budget below 8 MiB per slot");
     gr_status cs = GR_OK;
-    packed_launch_cfg(1, &cs);  // configures the kernels on this device
+    packed_launch_cfg(nullptr, 1, 0, &cs);  // configures the kernels on this device
     if (cs != GR_OK) return cs;
     gr_server *s = new gr_server();
     cudaGetDevice(&s->device);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess && sms > 0)
         s->expand_grid = 8u * (uint32_t)sms;
-    memset(&s->opts, 0, sizeof(s->opts));
-    s->opts.grid_enabled = opts ? opts->grid_enabled : 1;
-    s->opts.strategy = opts ? opts->strategy : 0;
-    s->opts.max_iters = (opts && opts->max_iters) ? opts->max_iters : GR_MAX_ITERS;
+    s->opts = opts_or_default(opts);
     s->max_inflight = max_inflight;
     s->slots.resize(n_slots);
     // each slot: 1/16 of its share for the arena, 1/64 for results, the rest scratch

@@ -49,6 +49,18 @@ def test_struct_sizes_match_header(lib):
     assert C.sizeof(gb.gr_repair_result) == 2944
     assert C.sizeof(gb.gr_program) == 120
     assert C.sizeof(gb.gr_loop) == 12
+    assert C.sizeof(gb.gr_options) == 16 and gb.gr_options.deadline_us.offset == 8
+
+
+@pytest.mark.parametrize("over", [{"deadline_us": (1 << 40) + 1}, {"max_iters": 65}, {"strategy": 2}])
+def test_options_rejected_before_device_work(lib, over):
+    """Out-of-range options: GR_EINVAL before any CUDA call (this host has no GPU)."""
+    good = synth.generate("single_1x64_s8", 1)[0]
+    kw = {"max_iters": 64, "strategy": 0, "deadline_us": 0}
+    kw.update(over)
+    with pytest.raises(gb.GrError) as e:
+        gb.repair_batch([good], **kw)
+    assert e.value.code == gb.EINVAL
 
 
 def _prog(**over):
@@ -217,7 +229,10 @@ def test_expansion_items_cover_every_segment_once(lib):
     """The packer's trace-expansion work items: runs of at most 64 (statement,
     block) segments of one program (kind 0), or block 0 of a program's
     shared-array statements when its blocks are alike (kind 1), together
-    covering each segment a check reads exactly once, larger programs first."""
+    covering each segment a check reads exactly once; the general programs'
+    items first (the repair path expands only those), each part larger
+    programs first; the program order puts the relation kernel's programs
+    (shared array only, blocks alike or one block) first."""
     import oracle
     from _tiny import random_loop_program, random_program
 
@@ -253,8 +268,22 @@ def test_expansion_items_cover_every_segment_once(lib):
                 assert covered[p][x * B + b] == (1 if need else 0), (p, x, b)
     assert alike_seen > 10
     assert sorted(order) == list(range(n))
+    n_fast, n_items_gen = (int(x) for x in arena[120:128].view(np.uint32))
+    fast = [int(_devprog(arena, p)[NEG0 + 4:NEG0 + 8].view(np.uint32)[0]) for p in range(n)]
+    for p in range(n):
+        alike = int(_devprog(arena, p)[56:60].view(np.uint32)[0])
+        want = all(sp == 0 for sp in progs[p].space) and (alike or progs[p].blocks == 1)
+        assert fast[p] == int(want), p
+    assert n_fast == sum(fast) and 0 < n_fast < n
+    gen_items = {int(x) for x in items[:n_items_gen, 0]}
+    assert gen_items == {p for p in range(n) if not fast[p]}
+    assert {int(x) for x in items[n_items_gen:, 0]} == {p for p in range(n) if fast[p]}
     cost = [int(segbase[p + 1] - segbase[p]) * ((progs[p].threads + 7) // 8 * 8) for p in order]
-    assert cost == sorted(cost, reverse=True)
+    k = n - n_fast
+    assert all(not fast[p] for p in order[:k]) and all(fast[p] for p in order[k:])
+    assert cost[:k] == sorted(cost[:k], reverse=True) and cost[k:] == sorted(cost[k:], reverse=True)
+    prog_order = arena[int(h[3]):int(h[3]) + 4 * n].view(np.uint32).tolist()
+    assert [fast[p] for p in prog_order] == [1] * n_fast + [0] * (n - n_fast)
 
 
 @pytest.mark.parametrize("negs,msg", [([0], "empty"), ([1 << 7], "beyond slot"), ([1] * 33, "negative clauses")])
