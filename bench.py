@@ -1,10 +1,14 @@
 """Benchmark: repairs/s of the batched, device-resident repair loop.
 
 One step = the whole hot path over one batch of synthetic programs already
-resident in device memory: address-trace expansion, then the persistent
-repair launch (check -> clauses -> exact hitting set, to the fixed point for
-every program).  Default workload: 1,024 programs, 4 blocks x 256 threads,
-24 statements, 23 block slots, 1,024-word shared array.
+resident in device memory: the address traces of the programs the general
+check kernel reads (a global array, or blocks that differ; none in the
+default workload), every program's conflict relation (the check kernels:
+Verify of Algorithm 1 under the empty mask), then the loop kernel (check by
+the relation, clauses, exact hitting set, to the fixed point for every
+program).  Default workload: 4,096 uneven programs (threads log-uniform
+32-1024, blocks 1-16, statements 4-24, half repair / half removal mode),
+the largest single-GPU batch of the paper-shaped workloads.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -16,8 +20,10 @@ bounded sample of the same workload, on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -31,12 +37,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2011_08373_gb300 import synth  # noqa: E402
 
-WORKLOAD = "batch1024_4x256_s24"
-# DRAM bytes (read + write) of one k_repair launch, from the ncu capture summarised in
-# profiles/k_repair_batch1024_4x256_s24.md; reset to None whenever k_repair changes.
-NCU_TRAFFIC = {"batch1024_4x256_s24": 13_618_432}
-# the same for one k_check launch (profiles/k_check_batch1024_4x256_s24.md)
-NCU_CHECK_TRAFFIC = {"batch1024_4x256_s24": 13_586_432}
+WORKLOAD = "uneven4096_mixed"
+# further workloads timed on the device in the same run (extra keys)
+EXTRA_WORKLOADS = ("batch1024_4x256_s24", "interblock256_64x256_s16")
+CSRC = os.path.join(ROOT, "paper_2011_08373_gb300", "csrc")
 
 
 def _peaks():
@@ -185,20 +189,75 @@ def cpu_baseline_leg(workload, n_sample):
                       f"brute-force hitting set, {cores} threads, {dt:.1f} s"}
 
 
-# DevProg fields of a packed arena (bytes): n_stmts 0, blocks 8, threads 12,
-# shared_rows 44, global_rows 48, blocks alike 56; records of 1,440 bytes
+# Packed program records (DevProg, 1,440 bytes): n_stmts at byte 0, blocks
+# 8, threads 12, the statement instances (32 bytes each: op, space, kind,
+# flags, a, b, c, perm_off, guard k and r as u16 at 20 and 22) from byte 640;
+# the arena header's u64 at byte 16 is the records' offset, its u32 at byte
+# 120 the number of programs the relation kernel takes.
 DEVPROG_BYTES = 1440
+STMT0 = 640
+WITNESS_BYTES = 272
+RESULT_BYTES = 2944
 
 
-def check_bytes(arena, i):
-    """Trace bytes one check of packed program i reads."""
-    off = int(arena[16:24].view(np.uint64)[0]) + DEVPROG_BYTES * i
-    f = arena[off:off + 64].view(np.uint32)
-    n_inst, blocks, threads = int(f[0]), int(f[2]), int(f[3])
-    shared, glob, alike = int(f[11]), int(f[12]), int(f[14])
-    if alike and blocks > 1:
-        return (bin(shared).count("1") + bin(glob).count("1") * blocks) * threads * 2
-    return n_inst * blocks * threads * 2
+def _guard_count(T, k, r):
+    return T if k == 0 else ((T - 1 - r) // k + 1 if r < T else 0)
+
+
+def check_bytes(arena, n):
+    """Bytes one check of every program moves, two ways:
+
+    survey: the traces an expanded check reads, 4 bytes per active access
+      over every block, plus, since the maps are evaluated in the kernel, a
+      2-byte table entry per access of a permutation statement; plus the
+      program record and the relation rows written;
+    fused: what the relation kernel must move: the program record, the
+      permutation entries of block 0 (blocks alike: block 0 decides every
+      block), the relation rows.
+    """
+    off0 = int(arena[16:24].view(np.uint64)[0])
+    survey = fused = 0
+    for i in range(n):
+        off = off0 + DEVPROG_BYTES * i
+        f = arena[off:off + 16].view(np.uint32)
+        S, B, T = int(f[0]), int(f[2]), int(f[3])
+        st = arena[off + STMT0:off + STMT0 + 32 * S].reshape(S, 32)
+        for s in range(S):
+            k = int(st[s, 20:22].view(np.uint16)[0])
+            r = int(st[s, 22:24].view(np.uint16)[0])
+            act = _guard_count(T, k, r)
+            perm = int(st[s, 2]) == 2
+            survey += act * B * (4 + (2 if perm else 0))
+            fused += act * 2 if perm else 0
+        survey += DEVPROG_BYTES + WITNESS_BYTES
+        fused += DEVPROG_BYTES + WITNESS_BYTES
+    return survey, fused
+
+
+def kernel_source_sha(files=("relation.cu", "device.cuh", "engine.cuh")):
+    """Hash of the sources a kernel is built from (first 16 hex digits)."""
+    h = hashlib.sha256()
+    for name in files:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_counters(kernel, workload):
+    """Per-launch counters from the committed ncu summary of `kernel` on
+    `workload`, if its recorded source hash is this build's (else None).  The
+    summary carries one line `counters: source=<sha> wavefronts=<n>
+    dram_bytes=<n>`."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m = re.search(r"counters: source=(\w+) wavefronts=(\d+) dram_bytes=(\d+)", text)
+    if not m or m.group(1) != kernel_source_sha():
+        return None
+    return {"wavefronts": int(m.group(2)), "dram_bytes": int(m.group(3)), "source": m.group(1)}
 
 
 def shard(workload, n, rank):
@@ -221,6 +280,107 @@ def whole_job(n_per_rank, t_step_local, world, device="cuda"):
     return n_per_rank * world / t, t
 
 
+def _events(n):
+    import torch
+
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def time_steps(batch, steps, flush, stream):
+    """CUDA-event times (ms) of each part of `steps` device steps: expansion of
+    the general programs' traces, the relations, the loop.  The L2 is flushed
+    before each step, outside the events."""
+    import torch
+
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        e = _events(4)
+        e[0].record(stream)
+        if batch.has_general:
+            batch.expand()
+        e[1].record(stream)
+        batch.relation()
+        e[2].record(stream)
+        batch.loop()
+        e[3].record(stream)
+        evs.append(e)
+    torch.cuda.synchronize()
+    return [[a.elapsed_time(b) for a, b in zip(e[:-1], e[1:])] for e in evs]
+
+
+def launches_per_step(batch):
+    """Our kernels one step launches: the expansion (only with general
+    programs), the relation kernel and / or the general check kernel, the
+    loop kernel."""
+    return int(batch.has_general) + int(batch.n_fast > 0) + int(batch.has_general) + 1
+
+
+def device_workload(name, n, warmup, steps, flush, stream):
+    """repairs/s and kernel times of one workload's batch, device-timed."""
+    from paper_2011_08373_gb300 import binding
+
+    progs = synth.generate(name, n)
+    batch = binding.DeviceBatch(progs)
+    batch.tune()
+    for _ in range(warmup):
+        batch.run()
+    t = time_steps(batch, steps, flush, stream)
+    parts = [statistics.mean(x[i] for x in t) for i in range(3)]
+    res = batch.results_raw()
+    status = np.bincount(res["status"].astype(np.int64), minlength=4)[:4].tolist()
+    return {"repairs_per_s": n / (sum(parts) / 1000.0), "programs": n, "ms_per_step": sum(parts),
+            "expand_ms": parts[0], "relation_ms": parts[1], "loop_ms": parts[2],
+            "checks_per_repair": float(res["iters"].mean()),
+            "status_counts": {"repaired": status[0], "unrepairable": status[1], "iter_cap": status[2],
+                              "timeout": status[3]}}
+
+
+def serve_stream(rate, n, budget_gb, slots, local):
+    """A Poisson request stream through the repair server: p50/p99 latency
+    from submit to the poll that sees the result (host clock)."""
+    from paper_2011_08373_gb300 import binding
+
+    n_large = max(1, n // 20)
+    small = synth.generate("uneven4096_mixed", n - n_large, start=100000)
+    large = synth.generate("large_128x1024_s24", n_large)
+    rng = synth.SplitMix64(synth.program_seed(11, 0))
+    progs = list(small)
+    for p in large:  # 5% large programs at seeded positions
+        progs.insert(rng.randint(0, len(progs)), p)
+    with binding.Server(mem_budget_bytes=budget_gb << 30, n_slots=slots) as srv:
+        tk = [srv.submit(p) for p in progs[:64]]  # warm the server and the kernels
+        srv.drain(600000)
+        for t in tk:
+            srv.poll(t)
+        arrivals = synth.poisson_arrivals(rate, n, seed=int(rate))
+        tickets, lat = [], {}
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for p, at in zip(progs, arrivals):
+                while time.perf_counter() - t0 < at:
+                    pass
+                tickets.append(srv.submit(p))
+                if len(tickets) % 64 == 0:  # harvesting keeps the done map small
+                    for t in tickets[-128:-64]:
+                        if t not in lat:
+                            r = srv.poll(t)
+                            if r is not None:
+                                lat[t] = r[1]
+            srv.drain(600000)
+            t_end = time.perf_counter()
+        for t in tickets:
+            if t not in lat:
+                lat[t] = srv.poll(t)[1]
+        ls = np.array([lat[t] for t in tickets]) * 1e6
+        return {"rate_per_s": rate, "requests": n, "p50_us": float(np.percentile(ls, 50)),
+                "p99_us": float(np.percentile(ls, 99)), "repairs_per_s": n / (t_end - t0),
+                "offered_per_s": n / float(arrivals[-1]),
+                "config": {"workload": "uneven4096_mixed + 5% large_128x1024_s24", "budget_gb": budget_gb,
+                           "slots": slots},
+                "launches": srv.stats()["launches"], "clocks": clk.summary()}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -237,60 +397,74 @@ def run_ours(args, rank, world, local):
     progs = shard(args.workload, n, rank)
     batch = binding.DeviceBatch(progs)
     stream = torch.cuda.current_stream()
-    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # twice the 126 MB L2
+    props = torch.cuda.get_device_properties(local)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    shape = batch.tune()  # the autotuner picks the CTA shape for this batch
+    shape = batch.tune()  # the autotuner picks the CTA shapes for this batch
     for _ in range(args.warmup):
         batch.run()
     barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         barrier()
         wall0 = time.perf_counter()
-        for i in range(args.steps):
-            l2_flush.zero_()  # inputs fit in L2: flush it between steps (outside the events)
-            e0, e1, e2 = ev[i]
-            e0.record(stream)
-            batch.expand()
-            e1.record(stream)
-            batch.repair_expanded()
-            e2.record(stream)
-        clk.sample_now()  # the queued steps are still running on the device
+        t = time_steps(batch, args.steps, flush, stream)
+        clk.sample_now()
         barrier()
         wall = time.perf_counter() - wall0
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    repair_ms = [b.elapsed_time(c) for a, b, c in ev]
-    expand_ms = [a.elapsed_time(b) for a, b, c in ev]
-    t_step = sum(step_ms) / len(step_ms) / 1000.0
+    step_ms = [sum(x) for x in t]
+    expand_ms, rel_ms, loop_ms = ([x[i] for x in t] for i in range(3))
+    t_step = statistics.mean(step_ms) / 1000.0
     _, t_step = whole_job(n, t_step, world)
     res = batch.results_raw()
     checks = int(res["iters"].sum())
     pairs = int(res["access_pairs"].sum())
-    status = np.bincount(res["status"].astype(np.int64), minlength=3)[:3].tolist()
+    status = np.bincount(res["status"].astype(np.int64), minlength=4)[:4].tolist()
     lat = (res["t_end_ns"].astype(np.int64) - int(res["t_start_ns"].min())) / 1e3
-    value, _ = whole_job(n, t_step, 1)
-    value *= world
+    value = n * world / t_step
+    clocks = clk.summary()
+    hbm_peak, peak_kind = _peaks()
 
-    # algorithmic bytes of the repair kernel: each check reads the traces it
-    # needs once (u16 addresses of T threads per (statement instance, block):
-    # every block, or block 0 of the shared-array statements when the
-    # program's blocks are alike); the arena and results once per launch
-    trace_bytes = sum(check_bytes(batch.host_arena, i) * int(r["iters"]) for i, r in enumerate(res))
-    launch_bytes = trace_bytes + batch.arena_bytes + n * binding.RESULT_DTYPE.itemsize
-    t_rep = statistics.mean(repair_ms) / 1000.0
-    peak, peak_kind = _peaks()
-    achieved = launch_bytes / t_rep / 1e9
-    traffic = NCU_TRAFFIC.get(args.workload)
+    # rooflines.  The check kernel (relation) does one check per program, the
+    # empty-mask one; its bytes per check follow the survey's count (4-byte
+    # trace reads of every active access over every block), next to the bytes
+    # the fused kernel must move.  Its shared-memory fraction takes the
+    # wavefronts per launch from the committed ncu summary of this kernel
+    # build and workload over this run's kernel time and the SMs' 128 bytes
+    # per clock at the sampled SM clock.
+    t_rel = statistics.mean(rel_ms) / 1000.0
+    t_loop = statistics.mean(loop_ms) / 1000.0
+    survey_b, fused_b = check_bytes(batch.host_arena, n)
+    prof = profile_counters("k_relation", args.workload)
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    smem_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e9  # GB/s
+    check = {"kernel": "k_relation", "ms": t_rel * 1000, "checks_per_launch": n, "bound": "hbm",
+             "algorithmic_bytes": survey_b, "fused_bytes": fused_b,
+             "achieved": survey_b / t_rel / 1e9, "peak": hbm_peak, "unit": "GB/s",
+             "frac": survey_b / t_rel / 1e9 / hbm_peak, "peak_kind": peak_kind,
+             "fused_frac": fused_b / t_rel / 1e9 / hbm_peak,
+             "traffic": prof["dram_bytes"] if prof else None,
+             "smem": ({"achieved": prof["wavefronts"] * 128 / t_rel / 1e9, "peak": smem_peak, "unit": "GB/s",
+                       "frac": prof["wavefronts"] * 128 / t_rel / 1e9 / smem_peak,
+                       "wavefronts_per_launch": prof["wavefronts"], "source": prof["source"],
+                       "peak_def": f"{props.multi_processor_count} SMs x 128 B/clk x {sm_mhz:.0f} MHz"}
+                      if prof else None)}
+    loop_b = n * (DEVPROG_BYTES + WITNESS_BYTES + RESULT_BYTES)
+    loop_rf = {"kernel": "k_loop", "ms": t_loop * 1000, "bound": "hbm", "algorithmic_bytes": loop_b,
+               "achieved": loop_b / t_loop / 1e9, "peak": hbm_peak, "unit": "GB/s",
+               "frac": loop_b / t_loop / 1e9 / hbm_peak, "peak_kind": peak_kind, "traffic": None}
+    dominant = check if t_rel >= t_loop else loop_rf
+    roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                                         "algorithmic_bytes", "peak_kind")}
+
     e2e = None
     if rank == 0 and args.e2e_steps > 0:
         # the C-ABI call with host buffers: validate + pack into pinned staging
-        # + H2D + expansion + repair + D2H of the results (marshalling of the
+        # + H2D + relations + loop + D2H of the results (marshalling of the
         # Python objects into C structs happens once, outside the timed region)
         pb = binding.ProgramBatch(progs)
         host_out = np.zeros(n, dtype=binding.RESULT_DTYPE)
@@ -302,7 +476,9 @@ def run_ours(args, rank, world, local):
         e2e_t = (time.perf_counter() - t0) / args.e2e_steps
         e2e = {"value": n / e2e_t, "unit": "repairs/s", "h2d_bytes_per_step": int(batch.arena_bytes),
                "d2h_bytes_per_step": int(n * binding.RESULT_DTYPE.itemsize),
-               "note": "gr_repair_batch on host program structs: validate + pack + H2D + kernels + D2H"}
+               "note": "gr_repair_batch on host program structs: validate + pack + H2D + kernels + D2H",
+               "same_results": bool(np.array_equal(host_out["mask"], res["mask"])
+                                    and np.array_equal(host_out["iters"], res["iters"]))}
     plain = None
     if rank == 0 and args.plain_programs > 0:
         sub = progs[:args.plain_programs]
@@ -316,57 +492,40 @@ def run_ours(args, rank, world, local):
     if rank == 0 and args.strategy_steps > 0:
         # the paper's mhs strategy against the exact (MaxSAT) strategy on the
         # same batch: masks checked per repair (the verifier-call analogue) and
-        # the repair kernel's time; both must end at the same masks
+        # the loop kernel's time; both must end at the same masks
         gb = binding.DeviceBatch(progs, strategy=binding.STRATEGY_MHS)
         gb.tune()
-        gb.expand()
-        gb.repair_expanded()
-        torch.cuda.synchronize()
-        g_ms = []
-        for _ in range(args.strategy_steps):
-            l2_flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            gb.expand()
-            a.record(stream)
-            gb.repair_expanded()
-            b.record(stream)
-            torch.cuda.synchronize()
-            g_ms.append(a.elapsed_time(b))
+        gb.run()
+        tg = time_steps(gb, args.strategy_steps, flush, stream)
         gres = gb.results_raw()
         strategies = {
-            "maxsat": {"checks_per_repair": checks / n, "repair_kernel_ms": statistics.mean(repair_ms)},
+            "maxsat": {"checks_per_repair": checks / n, "loop_ms": statistics.mean(loop_ms)},
             "mhs": {"checks_per_repair": int(gres["iters"].sum()) / n,
-                    "repair_kernel_ms": statistics.mean(g_ms)},
+                    "loop_ms": statistics.mean(x[2] for x in tg)},
             "same_final_mask": float(np.mean((gres["mask"] == res["mask"]) & (gres["status"] == res["status"]))),
         }
         del gb
-    check = None
+    check_leg = None
     if rank == 0 and args.check_steps > 0:
-        # the check kernel alone (gr_check_expanded): one check per program
-        # under the empty mask, where every statement pair is a candidate
+        # gr_check_expanded: one check per program under the empty mask, with
+        # its divergence and pair count, on the relation kernel
         batch.check([0] * n)
         torch.cuda.synchronize()
         c_ms = []
         for _ in range(args.check_steps):
-            l2_flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a, b = _events(2)
             a.record(stream)
             batch.check(None, expanded=True)
             b.record(stream)
             torch.cuda.synchronize()
             c_ms.append(a.elapsed_time(b))
-        t_c = statistics.mean(c_ms) / 1000.0
-        c_bytes = (sum(check_bytes(batch.host_arena, i) for i in range(n)) + batch.arena_bytes
-                   + n * binding.WITNESS_DTYPE.itemsize)
-        check = {"checks_per_s": n / t_c, "check_kernel_ms": t_c * 1000, "mask": 0,
-                 "roofline": {"bound": "hbm", "achieved": c_bytes / t_c / 1e9, "peak": peak, "unit": "GB/s",
-                              "frac": c_bytes / t_c / 1e9 / peak, "kernel": "k_check",
-                              "algorithmic_bytes": c_bytes, "traffic": NCU_CHECK_TRAFFIC.get(args.workload)}}
+        check_leg = {"checks_per_s": n / (statistics.mean(c_ms) / 1000), "check_call_ms": statistics.mean(c_ms),
+                     "mask": 0}
     wide = None
     if rank == 0 and args.wide_steps > 0:
         # the wide lane on the same batch: one CTA per (program, block) per
         # check, the loop as a device-side graph; host wall time per call
-        # (header read, expansion, graph build and launch, completion)
         batch.run_wide()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -379,6 +538,14 @@ def run_ours(args, rank, world, local):
                 "same_results": bool(np.array_equal(wres["mask"], res["mask"])
                                      and np.array_equal(wres["iters"], res["iters"])),
                 "note": "gr_repair_packed_wide, host wall clock per call incl. synchronisation"}
+    extra = None
+    if rank == 0 and args.extra_steps > 0:
+        extra = {w: device_workload(w, synth.WORKLOADS[w].n_programs, 3, args.extra_steps, flush, stream)
+                 for w in EXTRA_WORKLOADS}
+    serving = None
+    if rank == 0 and args.serve_requests > 0 and args.serve_rate > 0:
+        serving = serve_stream(args.serve_rate, args.serve_requests, args.serve_budget_gb, args.serve_slots,
+                               local)
     cpu = None
     if rank == 0 and args.cpu_sample > 0:
         cpu = cpu_baseline_leg(args.workload, args.cpu_sample)
@@ -391,23 +558,23 @@ def run_ours(args, rank, world, local):
             "config": {"workload": args.workload, "programs": n, "blocks": wl.blocks, "threads": wl.threads,
                        "stmts": wl.n_stmts, "m_words": wl.m_words, "seed": wl.seed,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
-                       "cta_shape": shape_dict(shape),
-                       "parallelism": f"replicas x{world}"},
+                       "cta_shape": shape_dict(shape), "parallelism": f"replicas x{world}"},
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_repair",
-                         "algorithmic_bytes": launch_bytes, "peak_kind": peak_kind},
+            "gpu_launches": launches_per_step(batch) * args.steps,
+            "roofline": roofline,
+            "check_roofline": check,
+            "loop_roofline": loop_rf,
             "cpu_baseline": cpu,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "checks_per_s": checks * world / t_step,
             "access_pair_checks_per_s": pairs * world / t_step,
             "plain_repairs_per_s": plain,
-            "expand_ms": statistics.mean(expand_ms), "repair_kernel_ms": statistics.mean(repair_ms),
+            "expand_ms": statistics.mean(expand_ms), "relation_ms": t_rel * 1000, "loop_ms": t_loop * 1000,
             "latency_in_batch_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "status_counts": {"repaired": status[0], "unrepairable": status[1], "iter_cap": status[2]},
+            "status_counts": {"repaired": status[0], "unrepairable": status[1], "iter_cap": status[2],
+                              "timeout": status[3]},
             "checks_per_repair": checks / n, "strategies": strategies, "wide_lane": wide,
-            "check_kernel": check, "wall_s": wall,
+            "check_kernel": check_leg, "workloads": extra, "serving": serving, "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -418,67 +585,25 @@ def run_serve(args, rank, world, local):
     """Poisson request streams through the repair server (p50/p99 latency)."""
     import torch
 
-    from paper_2011_08373_gb300 import binding
     from paper_2011_08373_gb300.build import build
 
     if rank != 0:
         return
     torch.cuda.set_device(local)
     build()
-    n = args.serve_requests
-    n_large = max(1, n // 20)
-    small = synth.generate("uneven4096_mixed", n - n_large, start=100000)
-    large = synth.generate("large_128x1024_s24", n_large)
-    rng = synth.SplitMix64(synth.program_seed(11, 0))
-    progs = list(small)
-    for p in large:  # 5% large programs at seeded positions
-        progs.insert(rng.randint(0, len(progs)), p)
     lines = []
-    with binding.Server(mem_budget_bytes=args.serve_budget_gb << 30, n_slots=args.serve_slots) as srv:
-        # warm the server and the kernels
-        tk = [srv.submit(p) for p in progs[:64]]
-        srv.drain(600000)
-        for t in tk:
-            srv.poll(t)
-        for rate in args.serve_rates:
-            arrivals = synth.poisson_arrivals(rate, n, seed=int(rate))
-            tickets = []
-            lat = {}
-            with ClockSampler(local) as clk:
-                t0 = time.perf_counter()
-                for p, at in zip(progs, arrivals):
-                    while time.perf_counter() - t0 < at:
-                        pass
-                    tickets.append(srv.submit(p))
-                    # opportunistic harvesting keeps the done map small
-                    if len(tickets) % 64 == 0:
-                        for t in tickets[-128:-64]:
-                            if t not in lat:
-                                r = srv.poll(t)
-                                if r is not None:
-                                    lat[t] = r[1]
-                srv.drain(600000)
-                t_end = time.perf_counter()
-            for t in tickets:
-                if t not in lat:
-                    r = srv.poll(t)
-                    lat[t] = r[1]
-            ls = np.array([lat[t] for t in tickets]) * 1e6
-            line = {"metric": "p50/p99 repair latency (serving)", "rate_per_s": rate, "requests": n,
-                    "p50_us": float(np.percentile(ls, 50)), "p99_us": float(np.percentile(ls, 99)),
-                    "repairs_per_s": n / (t_end - t0), "offered_per_s": n / float(arrivals[-1]),
-                    "config": {"workload": "uneven4096_mixed + 5% large_128x1024_s24",
-                               "budget_gb": args.serve_budget_gb, "slots": args.serve_slots},
-                    "launches": srv.stats()["launches"], "clocks": clk.summary()}
-            lines.append(line)
-            print(json.dumps(line), flush=True)
+    for rate in args.serve_rates:
+        line = {"metric": "p50/p99 repair latency (serving)"}
+        line.update(serve_stream(rate, args.serve_requests, args.serve_budget_gb, args.serve_slots, local))
+        lines.append(line)
+        print(json.dumps(line), flush=True)
     return lines
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
@@ -487,15 +612,19 @@ def main():
     ap.add_argument("--plain-programs", type=int, default=64)
     ap.add_argument("--check-steps", type=int, default=5,
                     help="timed launches of the check kernel alone on the same batch (0: skip)")
-    ap.add_argument("--wide-steps", type=int, default=5,
+    ap.add_argument("--wide-steps", type=int, default=3,
                     help="calls of the wide lane on the same batch (0: skip)")
     ap.add_argument("--strategy-steps", type=int, default=5,
                     help="timed launches of the mhs strategy on the same batch (0: skip)")
-    ap.add_argument("--cpu-sample", type=int, default=32)
-    ap.add_argument("--ref-sample", type=int, default=16)
+    ap.add_argument("--extra-steps", type=int, default=10,
+                    help="timed steps of each further workload (batch of 1,024; inter-block), 0: skip")
+    ap.add_argument("--cpu-sample", type=int, default=64)
+    ap.add_argument("--ref-sample", type=int, default=64)
     ap.add_argument("--serve", action="store_true", help="Poisson request streams through the server")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 500.0, 2000.0])
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0,
+                    help="Poisson rate of the serving leg of the default run (0: skip)")
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()

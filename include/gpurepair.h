@@ -316,6 +316,23 @@ gr_status gr_expand_packed(const void *d_arena, void *d_scratch, uint64_t scratc
 gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                              uint64_t scratch_bytes, gr_repair_result *d_out, void *stream);
 
+/* The two stages of gr_repair_expanded, for callers that time them apart.
+ * gr_relation_packed: Verify (Algorithm 1, Section 2.4) of every program
+ * under the empty mask, i.e. each program's conflict relation (every
+ * instance pair with a write that conflicts on some word, same-block and
+ * cross-block), written into d_scratch: the relation kernel for programs on
+ * the shared array with alike blocks, the general check kernel on the traces
+ * a previous gr_expand_packed wrote for the others.  gr_loop_packed: the
+ * loop of Algorithm 1 for every program on the relations a previous
+ * gr_relation_packed of the same arena wrote (Verify of a proposal is the
+ * relation restricted to the proposal's phases, exact because a witness's
+ * clause is exactly the slots that order it), results into d_out.  The two
+ * calls in order on one stream equal gr_repair_expanded. */
+gr_status gr_relation_packed(const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                             void *stream);
+gr_status gr_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                         uint64_t scratch_bytes, gr_repair_result *d_out, void *stream);
+
 /* Autotuner: time every CTA shape the check kernels are built for (threads
  * per CTA x CTAs per SM, with the owner-table budget that shape leaves) on
  * this arena, remember the fastest for later gr_repair_packed /

@@ -83,7 +83,7 @@ EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair"
            "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded",
            "gr_repair_packed_noalloc", "gr_server_create", "gr_server_submit", "gr_server_poll",
            "gr_server_drain", "gr_server_stats", "gr_server_destroy", "gr_tune_packed",
-           "gr_repair_packed_wide", "gr_check_expanded"]
+           "gr_repair_packed_wide", "gr_check_expanded", "gr_relation_packed", "gr_loop_packed"]
 
 
 def lib():
@@ -133,6 +133,8 @@ def lib():
             L.gr_check_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_uint64,
                                           C.c_void_p, C.c_void_p]
             L.gr_check_expanded.argtypes = L.gr_check_packed.argtypes
+            L.gr_relation_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p]
+            L.gr_loop_packed.argtypes = L.gr_repair_packed.argtypes
             for name in EXPORTS[2:]:
                 getattr(L, name).restype = C.c_int32
             _lib = L
@@ -463,6 +465,10 @@ class DeviceBatch:
         self.arena[a_off:a_off + self.arena_bytes].copy_(torch.from_numpy(host))
         self.opts = _options(grid_enabled, max_iters, strategy, deadline_us)
         self.host_arena = host
+        # programs the relation kernel takes (header u32 at byte 120); the
+        # others need their traces expanded
+        self.n_fast = int(host[120:124].view(np.uint32)[0])
+        self.has_general = self.n_fast < self.n
 
     def run(self, stream: Optional[int] = None) -> None:
         import torch
@@ -511,6 +517,23 @@ class DeviceBatch:
         _check(lib().gr_repair_expanded(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
                                         C.c_void_p(self._scratch_ptr), self.scratch_bytes,
                                         C.c_void_p(self._out_ptr), C.c_void_p(st)))
+
+    def relation(self, stream: Optional[int] = None) -> None:
+        """Each program's conflict relation into the scratch (gr_relation_packed)."""
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_relation_packed(C.c_void_p(self._arena_ptr), self.n, C.c_void_p(self._scratch_ptr),
+                                        self.scratch_bytes, C.c_void_p(st)))
+
+    def loop(self, stream: Optional[int] = None) -> None:
+        """Algorithm 1 on the relations relation() wrote (gr_loop_packed)."""
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_loop_packed(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
+                                    C.c_void_p(self._scratch_ptr), self.scratch_bytes,
+                                    C.c_void_p(self._out_ptr), C.c_void_p(st)))
 
     def check(self, masks, stream: Optional[int] = None, expanded: bool = False):
         """One check per program under masks[p] (gr_check_packed; with

@@ -1066,6 +1066,39 @@ gr_status gr_repair_expanded(const void *d_arena, uint32_t n, const gr_options *
     return GR_OK;
 }
 
+gr_status gr_relation_packed(const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                             void *stream) {
+    if (!d_arena || !d_scratch || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    if (scratch_bytes < 256) return fail(GR_ECAPACITY, "scratch too small");
+    gr_status s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    GR_CUDA(enqueue_relation(d_arena, n, d_scratch, scratch_bytes, packed_cfg(*ws, d_arena, n), expand_grid(*ws),
+                             false, true, static_cast<cudaStream_t>(stream)));
+    return GR_OK;
+}
+
+gr_status gr_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                         uint64_t scratch_bytes, gr_repair_result *d_out, void *stream) {
+    if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    if (scratch_bytes < 256) return fail(GR_ECAPACITY, "scratch too small");
+    gr_status s = validate_opts(opts);
+    if (s != GR_OK) return s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    GR_CUDA(enqueue_loop(d_arena, n, opts_or_default(opts), d_scratch, scratch_bytes, d_out,
+                         packed_cfg(*ws, d_arena, n), static_cast<cudaStream_t>(stream)));
+    return GR_OK;
+}
+
 gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                          uint64_t scratch_bytes, gr_repair_result *d_out, void *stream, uint32_t *shape_out) {
     if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");

@@ -202,18 +202,23 @@ __device__ __forceinline__ uint32_t guard_both(uint32_t T, uint32_t k1, uint32_t
 // threads, B (n_i n_j - n_ij) in one block, B (B - 1) n_i n_j across blocks
 // (global array only); i == j: unordered pairs, B n_i (n_i - 1) / 2 and
 // B (B - 1) / 2 n_i^2.
-__device__ __forceinline__ void pair_count(const DevProg &P, uint32_t i, uint32_t j, uint64_t &same,
-                                           uint64_t &cross) {
+// nact: the active threads of each instance (guard_count).
+__device__ __forceinline__ void pair_count(const DevProg &P, const uint32_t *nact, uint32_t i, uint32_t j,
+                                           uint64_t &same, uint64_t &cross) {
     const DevStmt &a = P.stmts[i], &b = P.stmts[j];
     same = 0;
     cross = 0;
     if (a.space != b.space || (a.op != GR_W && b.op != GR_W)) return;
     const uint64_t T = P.threads, B = P.blocks;
-    const uint64_t ni = guard_count(P.threads, a.gk, a.gr);
+    const uint64_t ni = nact[i];
     const bool global = a.space == GR_GLOBAL;
     if (i < j) {
-        const uint64_t nj = guard_count(P.threads, b.gk, b.gr);
-        const uint64_t nij = guard_both(P.threads, a.gk, a.gr, b.gk, b.gr);
+        const uint64_t nj = nact[j];
+        // threads active at both: one side unguarded or both under one guard needs no count
+        const uint64_t nij = a.gk == 0 ? nj
+                             : (b.gk == 0 || (a.gk == b.gk && a.gr == b.gr))
+                                   ? ni
+                                   : guard_both(P.threads, a.gk, a.gr, b.gk, b.gr);
         same = B * (ni * nj - nij);
         cross = global ? B * (B - 1) * ni * nj : 0;
     } else {

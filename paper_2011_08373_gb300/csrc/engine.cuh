@@ -210,6 +210,13 @@ cudaError_t launch_loop(const void *d_arena, uint32_t n, const gr_options &opts,
 cudaError_t enqueue_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
                            uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
                            bool expand, bool clear_error, cudaStream_t st);
+// The two halves of enqueue_repair: the relations (the queue counters, and
+// the error word when clear_error, cleared first), then the loop (its queue
+// counter cleared first).
+cudaError_t enqueue_relation(const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                             const LaunchCfg &cfg, uint32_t expand_grid, bool expand, bool clear_error, cudaStream_t st);
+cudaError_t enqueue_loop(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
+                         uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, cudaStream_t st);
 // One check per program of a packed batch under d_masks.
 cudaError_t enqueue_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
                           uint64_t scratch_bytes, gr_witnesses *d_out, const LaunchCfg &cfg, uint32_t expand_grid,

@@ -1772,9 +1772,8 @@ static cudaError_t clear_ctrl(void *d_scratch, bool clear_error, cudaStream_t st
     return e;
 }
 
-cudaError_t enqueue_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
-                           uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
-                           bool expand, bool clear_error, cudaStream_t st) {
+cudaError_t enqueue_relation(const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                             const LaunchCfg &cfg, uint32_t expand_grid, bool expand, bool clear_error, cudaStream_t st) {
     const bool general = !(cfg.skip & kSkipGeneral), fast = !(cfg.skip & kSkipFast);
     cudaError_t e = clear_ctrl(d_scratch, clear_error, st);
     if (e == cudaSuccess && general && expand)
@@ -1783,6 +1782,20 @@ cudaError_t enqueue_repair(const void *d_arena, uint32_t n, const gr_options &op
         e = launch_relation(d_arena, n, nullptr, d_scratch, scratch_bytes, nullptr, cfg.rel, st);
     if (e == cudaSuccess && general)
         e = launch_check(d_arena, n, nullptr, d_scratch, scratch_bytes, nullptr, cfg, st);
+    return e;
+}
+
+cudaError_t enqueue_loop(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
+                         uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(static_cast<uint32_t *>(d_scratch) + 3, 0, 4, st);  // its queue counter
+    if (e == cudaSuccess) e = launch_loop(d_arena, n, opts, d_scratch, scratch_bytes, d_out, cfg.loop_grid, st);
+    return e;
+}
+
+cudaError_t enqueue_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
+                           uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
+                           bool expand, bool clear_error, cudaStream_t st) {
+    cudaError_t e = enqueue_relation(d_arena, n, d_scratch, scratch_bytes, cfg, expand_grid, expand, clear_error, st);
     if (e == cudaSuccess) e = launch_loop(d_arena, n, opts, d_scratch, scratch_bytes, d_out, cfg.loop_grid, st);
     return e;
 }

@@ -43,6 +43,7 @@ struct LoopWarp {
     uint32_t wc[32], wlo[32], lb[34];
     uint32_t w4[8][16];     // weight of each nibble of the high part
     uint32_t size_at[34];
+    uint32_t nact[32];      // active threads of each instance
 };
 
 constexpr size_t kLoopSmem = (sizeof(LoopWarp) + 15) / 16 * 16;
@@ -140,6 +141,24 @@ __device__ uint32_t build_clause_set(LoopWarp &lw, uint32_t acc_i, uint32_t acc_
     const DevProg &P = lw.prog;
     const uint32_t lane = lane_id();
     uint32_t m = 0;
+    if (!P.general && !__any_sync(0xFFFFFFFFu, acc_x != 0u)) {
+        // Without loops or explicit places and without cross-block witnesses
+        // the clause of (i, j) is the slot interval [i, j): 2^j - 2^i, all
+        // distinct, and in increasing order when sorted by j, then by
+        // decreasing i (the values for j lie in [2^(j-1), 2^j)); a
+        // same-statement witness gives the empty clause 0, first.
+        if (__any_sync(0xFFFFFFFFu, (acc_i >> lane) & 1u)) lw.cl[m++] = 0u;
+        const uint32_t rows = __reduce_or_sync(0xFFFFFFFFu, acc_i);
+        for (uint32_t t = rows & ~1u; t; t &= t - 1u) {
+            const uint32_t j = __ffs(t) - 1u;
+            const bool has = lane < j && ((acc_i >> j) & 1u);
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, has);
+            if (has) lw.cl[m + __popc(bal >> lane) - 1u] = (1u << j) - (1u << lane);
+            m += __popc(bal);
+        }
+        __syncwarp();
+        return m;
+    }
     // lane i emits its row's clauses one per round, in increasing j
     uint32_t ti = acc_i, tx = acc_x;
     while (__any_sync(0xFFFFFFFFu, (ti | tx) != 0u)) {
@@ -182,8 +201,8 @@ __device__ uint32_t build_clause_set(LoopWarp &lw, uint32_t acc_i, uint32_t acc_
 //      assignments that hit it — and the high slots are enumerated by size
 //      (Gosper's order), lanes taking contiguous ranges, stopping at the first
 //      size whose lightest member is heavier than the best key found.
-__device__ bool warp_solve(LoopWarp &lw, uint32_t n, uint32_t forced, uint32_t forbidden, uint32_t &mask_out,
-                           uint32_t &weight_out) {
+__device__ bool warp_solve(LoopWarp &lw, const uint32_t *cl, uint32_t n, uint32_t forced, uint32_t forbidden,
+                           uint32_t &mask_out, uint32_t &weight_out) {
     const DevProg &P = lw.prog;
     const uint32_t *w = P.weights;
     const uint32_t lane = lane_id();
@@ -193,7 +212,7 @@ __device__ bool warp_solve(LoopWarp &lw, uint32_t n, uint32_t forced, uint32_t f
     __syncwarp();
     bool bad = false;
     for (uint32_t i = lane; i < n; i += 32u) {
-        const uint32_t c = lw.cl[i];
+        const uint32_t c = cl[i];
         uint32_t pc = 0;
         if (!(c & forced)) {
             pc = c & ~forbidden;
@@ -448,6 +467,27 @@ __device__ bool warp_greedy(LoopWarp &lw, uint32_t n, uint32_t forced, uint32_t 
     return true;
 }
 
+// For the exact solve: one clause per witness row and kind, the one of the
+// row's nearest partner.  The clause of (i, j) only grows with j (it holds
+// the slots of gaps i..j-1), so it is contained in every other clause of row
+// i of its kind, and a mask hits all of them iff it hits this one: the
+// minimum-weight hitting sets of the whole clause set and of these (at most
+// 2 x 25) are the same.  Into lw.cl; returns how many.
+__device__ uint32_t build_row_minima(LoopWarp &lw, uint32_t acc_i, uint32_t acc_x) {
+    const DevProg &P = lw.prog;
+    const uint32_t lane = lane_id();
+    uint32_t ci = 0, cx = 0;
+    const bool hi = acc_i != 0u, hx = acc_x != 0u;
+    if (hi) ci = slots_of_gaps(P, range_mask(lane, __ffs(acc_i) - 1u));
+    if (hx) cx = slots_of_gaps(P, range_mask(lane, __ffs(acc_x) - 1u)) & P.grid_mask;
+    const uint32_t bi = __ballot_sync(0xFFFFFFFFu, hi), bx = __ballot_sync(0xFFFFFFFFu, hx);
+    const uint32_t below = (1u << lane) - 1u;
+    if (hi) lw.cl[__popc(bi & below)] = ci;
+    if (hx) lw.cl[__popc(bi) + __popc(bx & below)] = cx;
+    __syncwarp();
+    return __popc(bi) + __popc(bx);
+}
+
 // ---- the loop ---------------------------------------------------------------
 
 template <uint32_t WARPS>
@@ -525,16 +565,20 @@ __global__ void __launch_bounds__(WARPS * 32)
                 probe = false;
                 forbidden |= dv;
             }
-            n_cl = build_clause_set(lw, acc_i, acc_x);
             bool found = false, solved = false;
             uint32_t smask = 0, sweight = 0;
             if (step == 0 && greedy) {
+                // the greedy counts every distinct clause
+                n_cl = build_clause_set(lw, acc_i, acc_x);
                 found = warp_greedy(lw, n_cl, forced, forbidden, smask, sweight);
                 // a greedy set that holds a negative clause whole falls back to the MaxSAT solve
                 const bool viol = found && lane < P.n_neg && (smask & P.neg[lane]) == P.neg[lane];
                 solved = found && !__any_sync(0xFFFFFFFFu, viol);
             }
-            if (!solved) found = warp_solve(lw, n_cl, forced, forbidden, smask, sweight);
+            if (!solved) {
+                const uint32_t n_min = build_row_minima(lw, acc_i, acc_x);
+                found = warp_solve(lw, lw.cl, n_min, forced, forbidden, smask, sweight);
+            }
             if (step == 1 && (!found || smask == mask)) {
                 status = GR_REPAIRED;  // the greedy proposal is the minimum
                 done = true;
@@ -553,7 +597,8 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
         }
         __syncwarp();
-        // the result
+        // the result, with the sorted set of every clause built
+        n_cl = build_clause_set(lw, acc_i, acc_x);
         gr_repair_result &o = out[p];
         for (uint32_t k = lane; k < GR_MAX_ITERS; k += 32u) {
             const uint32_t m = k < iters ? lw.traj[k] : 0u;
@@ -566,12 +611,14 @@ __global__ void __launch_bounds__(WARPS * 32)
         for (uint32_t i = lane; i < GR_MAX_CLAUSES; i += 32u) o.clauses[i] = i < n_cl ? lw.cl[i] : 0u;
         __syncwarp();
         // thread pairs a pairwise checker examines, summed over the checks
+        lw.nact[lane] = lane < S ? guard_count(P.threads, P.stmts[lane].gk, P.stmts[lane].gr) : 0u;
+        __syncwarp();
         unsigned long long pairs = 0;
         for (uint32_t idx = lane; idx < S * S; idx += 32u) {
             const uint32_t i = idx / S, j = idx - i * S;
             if (j < i) continue;
             uint64_t same, cross;
-            pair_count(P, i, j, same, cross);
+            pair_count(P, lw.nact, i, j, same, cross);
             if (!same && !cross) continue;
             const uint32_t rg = range_mask(i, j);
             uint32_t cs = 0, cx = 0;

@@ -5,27 +5,32 @@
 // block 0 decides every candidate pair.
 //
 // Each CTA takes programs from a work queue and, per program:
-//   setup   — the candidate pairs: under a mask, the instance pairs (i <= j)
-//             with a write and no enabled barrier between them (one phase,
-//             Section 2.2); for the repair loop, every pair with a write (the
-//             empty mask), which gives the program's whole conflict
-//             relation.  Instances with the same map and guard touch the same
-//             words from the same threads and share one table row.
+//   setup   — (warp 0) the candidate pairs: under a mask, the instance pairs
+//             (i <= j) with a write and no enabled barrier between them (one
+//             phase, Section 2.2); for the repair loop, every pair with a
+//             write (the empty mask), which gives the program's whole
+//             conflict relation.  Instances with the same map and guard touch
+//             the same words from the same threads and share one table row.
 //   install — every access computes its word address from the map (affine
 //             or strided arithmetic, or one permutation-table load) and
-//             writes its thread into its row's owner entry; two threads of a
-//             row on one word leave MULTI (a compare-and-swap, only for rows
-//             whose map is not injective on the block's threads).  Per column
-//             a bit per row marks the rows holding an entry there.
-//   probe   — an access (thread t, word a) of row q and a pending partner row
-//             j conflict iff j's entry at a is not empty and is not t: an
-//             entry of another thread, or MULTI.  This is the race
-//             definition of Section 1 made concrete: two distinct threads,
-//             one word, at least one write, no barrier between them.
-//   reset   — every access puts its entries back to empty, so the table is
-//             clean for the next program without a clear of the whole array.
-// The table covers the array in windows when it does not fit; the addresses
-// of up to kRelCache accesses per thread stay in registers across the passes.
+//             writes its thread into its row's owner entry at that word; two
+//             threads of a row on one word leave MULTI (a compare-and-swap,
+//             only for rows whose map is not injective on the block's
+//             threads).  A bit per row and column marks the rows holding an
+//             entry there.
+//   scan    — each thread takes whole columns: the rows holding an entry at a
+//             column conflict pairwise unless both entries name the same
+//             single thread (an entry of another thread, or MULTI, is a
+//             second thread on the word: the race definition of Section 1
+//             made concrete — two distinct threads, one word, at least one
+//             write, no barrier between them).  The scan puts every entry it
+//             read back to empty, so the table is clean for the next program
+//             without a clear of the whole array.
+// Install works in units of one table row and 32 consecutive threads, a warp
+// per unit, so that a unit's map, guard and row are the same for the whole
+// warp: the per-unit arithmetic (a division or two) is done once and each
+// access costs a multiply and a reduction.  The table covers the array in
+// windows when it does not fit.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -34,17 +39,23 @@
 
 namespace gr {
 
-constexpr uint32_t kRelCache = 16;  // accesses a thread keeps in registers across the passes
 constexpr uint32_t kRelAllOnes = 0xFFFFFFFFu;
 
 struct RelSmem {
     DevProg prog;
-    uint32_t cand[32];      // table row q: partner rows (bit j, j >= q) still to decide
+    uint32_t cand[32];      // table row q: partner rows (bit j, j >= q) to decide
     uint32_t conf[32];      // table row q: partner rows found to conflict
     uint32_t pend[32];      // instance i: candidate partners (bit j, j >= i)
     uint32_t rep_conf[32];  // the conflicts by pattern representative
     uint32_t rep_list[32];  // representative of table row q
-    uint32_t involved, n_rows, use_col, W, n_win, inj_rows, item, bad;
+    // table row q's access map (its representative's statement, block 0):
+    uint32_t row_am[32];    // address of thread t: (am t + bm) mod M, or
+    uint32_t row_bm[32];    //   perm[po + (t + bm) mod M] when po != ~0
+    uint32_t row_po[32];
+    uint32_t row_gk[32], row_gr[32];  // guard (gk == 0: none)
+    uint32_t nact[32];      // active threads of each instance (for the pair count)
+    uint32_t involved, n_rows, W, pitch, n_win, inj_rows, bad, p;
+    uint32_t M, Mmagic;     // the shared array's words; floor((2^32 - 1) / M)
 };
 
 constexpr size_t kRelFixed = (sizeof(RelSmem) + 15) / 16 * 16;
@@ -52,14 +63,30 @@ size_t rel_fixed_bytes() { return kRelFixed; }
 
 // Column of word a within a window row: the low five bits are XOR-ed with
 // the next five, so that 32 words spaced 32 apart (stride-32 maps) fall on
-// 32 different banks; the window width is a multiple of 32, so a column
+// 32 different banks; the window width is a multiple of 64, so a column
 // stays within its row.
 __device__ __forceinline__ uint32_t swizzle(uint32_t c) { return c ^ ((c >> 5) & 31u); }
 
-// Per-program setup by warp 0: candidate pairs, table rows, window size.
-__device__ void rel_setup(RelSmem &sm, uint32_t mask, uint32_t table_bytes) {
+// x mod M for x < 2^31 by a reciprocal multiply: q = floor(x * magic / 2^32)
+// with magic = floor((2^32 - 1) / M) is floor(x / M) or one less, so one
+// correction gives the remainder (M = 1 included).
+__device__ __forceinline__ uint32_t mod_by(uint32_t x, uint32_t M, uint32_t magic) {
+    uint32_t r = x - __umulhi(x, magic) * M;
+    return r >= M ? r - M : r;
+}
+
+// Per-program setup by warp 0: the program record, candidate pairs, table
+// rows and their maps, window size.
+__device__ void rel_setup(RelSmem &sm, const DevProg *gp, uint32_t mask, uint32_t table_bytes) {
+    const uint32_t lane = threadIdx.x & 31u;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(gp);
+        uint4 *d4 = reinterpret_cast<uint4 *>(&sm.prog);
+        for (uint32_t i = lane; i < sizeof(DevProg) / 16; i += 32u) d4[i] = src[i];
+    }
+    __syncwarp();
     const DevProg &P = sm.prog;
-    const uint32_t lane = threadIdx.x & 31u, S = P.n_stmts;
+    const uint32_t S = P.n_stmts;
     const uint32_t gaps = gap_mask(P, mask);
     uint32_t pend = 0;
     if (lane < S) {
@@ -82,59 +109,144 @@ __device__ void rel_setup(RelSmem &sm, uint32_t mask, uint32_t table_bytes) {
     // rows in increasing representative order, so that a representative mask
     // compresses to a row mask by bit extraction
     if (keep) {
+        const DevStmt &st = P.stmts[lane];
         sm.rep_list[row] = lane;
         sm.cand[row] = pext32(rp, involved);
         sm.conf[row] = 0;
+        sm.row_am[row] = st.am;
+        sm.row_bm[row] = st.bm;
+        sm.row_po[row] = st.kind == GR_PERM ? st.perm_off : kRelAllOnes;
+        sm.row_gk[row] = st.gk;
+        sm.row_gr[row] = st.gr;
     }
     const uint32_t inj = __ballot_sync(0xFFFFFFFFu, keep && (P.stmts[lane].flags & kStmtInjective));
-    const uint32_t n_pairs = __reduce_add_sync(0xFFFFFFFFu, __popc(rp));
     if (lane == 0) {
         const uint32_t R = __popc(involved);
-        // a bit per row per column pays when rows have three or more pending
-        // partners on average (fewer are cheaper to probe one by one)
-        const uint32_t use_col = n_pairs >= 3u * R ? 1u : 0u;
-        const uint32_t per_col = R + 2u * use_col;  // u16 entries per column
         const uint32_t M = P.m_shared;
+        // R rows of W + 2 u16 entries (the extra word shifts each row by one
+        // bank) and W u32 column masks
         uint32_t W = 0, n_win = 0;
         if (R) {
-            const uint32_t wmax = (table_bytes / 2u / per_col) & ~31u;
-            const uint32_t mr = (M + 31u) & ~31u;
+            const uint32_t wmax = table_bytes > 4u * R ? ((table_bytes - 4u * R) / (2u * R + 4u)) & ~63u : 0u;
+            const uint32_t mr = (M + 63u) & ~63u;
             W = min(wmax, mr);
             n_win = W ? (M + W - 1u) / W : 0u;
         }
         sm.involved = involved;
+        sm.M = M;
+        sm.Mmagic = 0xFFFFFFFFu / M;
         sm.n_rows = R;
-        sm.use_col = use_col;
         sm.W = W;
+        sm.pitch = W + 2u;
         sm.n_win = n_win;
         sm.inj_rows = pext32(inj, involved);
         sm.bad = (R && W == 0) ? 1u : 0u;
     }
 }
 
-// The accesses of round `base` this thread takes: u = base + tid + k NT over
-// (table row q, thread t), q = u / T; key = word | t << 16 | q << 26, all ones
-// for no access (guard false, or past the end).
+// Install the accesses of the words [lo, lo + W) into the table: unit u (one
+// per warp at a time) covers table row q = u / cpr, threads 32 c .. 32 c + 31
+// with c = u mod cpr (cpr = chunks of 32 threads per row); lane l takes
+// thread 32 c + l.
 template <uint32_t NT>
-__device__ __forceinline__ void rel_keys(const RelSmem &sm, const uint16_t *__restrict__ perm, uint32_t base,
-                                         uint32_t total, uint32_t (&key)[kRelCache]) {
-    const DevProg &P = sm.prog;
-    const uint32_t T = P.threads;
+__device__ __forceinline__ void rel_install(const RelSmem &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
+                                            uint32_t *colrows, uint32_t lo) {
+    constexpr uint32_t NW = NT / 32;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W, pitch = sm.pitch;
+    const uint32_t cpr = (T + 31u) >> 5, n_units = sm.n_rows * cpr, inj = sm.inj_rows;
+    for (uint32_t u = warp; u < n_units; u += NW) {  // uniform over the warp
+        const uint32_t q = u / cpr, c = u - q * cpr;
+        const uint32_t tb = c << 5, t = tb + lane;
+        const uint32_t gk = sm.row_gk[q];
+        bool on = t < T;
+        if (gk) {
+            const uint32_t gr = sm.row_gr[q];
+            if ((gk & (gk - 1u)) == 0u) on = on && (t & (gk - 1u)) == gr;
+            else on = on && (tb % gk + lane) % gk == gr;
+        }
+        const uint32_t am = sm.row_am[q], bm = sm.row_bm[q], po = sm.row_po[q];
+        uint32_t a;
+        if (po != kRelAllOnes) {
+            // 32-bit: tb + bm < 2^10 + 2^16; ib + lane < 2^17
+            const uint32_t ib = (tb + bm) % M;
+            a = on ? (uint32_t)__ldg(perm + po + mod_by(ib + lane, M, magic)) : 0u;
+        } else {
+            // am, bm < M <= 2^16, tb < 2^10: am tb + bm < 2^27; xb + am lane < 2^22
+            const uint32_t xb = (am * tb + bm) % M;
+            a = mod_by(xb + am * lane, M, magic);
+        }
+        if (!on || a - lo >= W) continue;
+        const uint32_t col = swizzle(a - lo);
+        uint16_t *e = tab + (size_t)q * pitch + col;
+        if ((inj >> q) & 1u) {
+            *e = (uint16_t)t;
+        } else if (atomicCAS(e, kEmpty, (uint16_t)t) != kEmpty) {
+            *e = kMulti;  // a second thread of this row on the word
+        }
+        atomicAnd(&colrows[col], ~(1u << q));
+    }
+}
+
+// Scan the columns of the window: the rows holding an entry at a column
+// conflict pairwise unless both entries are the same single thread.  Up to 8
+// rows per column are compared in registers; more take the general loop.
+// Every entry read, and the column mask, go back to empty.
+template <uint32_t NT>
+__device__ __forceinline__ void rel_scan(RelSmem &sm, uint16_t *tab, uint32_t *colrows) {
+    const uint32_t W = sm.W, pitch = sm.pitch, inj = sm.inj_rows;
+    for (uint32_t c = threadIdx.x; c < W; c += NT) {
+        const uint32_t present = ~colrows[c];
+        if (!present) continue;
+        colrows[c] = kRelAllOnes;
+        if ((present & (present - 1u)) == 0u) {
+            // one row: only its own second thread (MULTI) can race with it
+            const uint32_t q = __ffs(present) - 1u;
+            uint16_t *e = tab + (size_t)q * pitch + c;
+            if (!((inj >> q) & 1u) && *e == kMulti && ((sm.cand[q] >> q) & 1u)) or_row(sm.conf, q, 1u << q);
+            *e = kEmpty;
+            continue;
+        }
+        uint32_t o[8], b[8], rest = present;
 #pragma unroll
-    for (uint32_t k = 0; k < kRelCache; ++k) {
-        const uint32_t u = base + threadIdx.x + k * NT;
-        key[k] = kRelAllOnes;
-        if (u < total) {
-            const uint32_t q = u / T, t = u - q * T;
-            const DevStmt &st = P.stmts[sm.rep_list[q]];
-            if (st.gk == 0 || t % st.gk == st.gr) {
-                const uint32_t M = st.m;
-                // 32-bit arithmetic: am, bm < M <= 65,536 and t < 1,024
-                const uint32_t a = st.kind == GR_PERM ? (uint32_t)__ldg(perm + st.perm_off + (t + st.bm) % M)
-                                                      : (st.am * t + st.bm) % M;
-                key[k] = a | (t << 16) | (q << 26);
+        for (uint32_t i = 0; i < 8; ++i) {
+            if (rest) {
+                const uint32_t q = __ffs(rest) - 1u;
+                rest &= rest - 1u;
+                o[i] = tab[(size_t)q * pitch + c];
+                b[i] = 1u << q;
+            } else {
+                o[i] = 0x10000u + i;  // distinct from every entry and from each other
+                b[i] = 0;
             }
         }
+        if (!rest) {
+#pragma unroll
+            for (uint32_t i = 0; i < 8; ++i) {
+                if (!b[i]) continue;
+                uint32_t same = 0;
+#pragma unroll
+                for (uint32_t j = 0; j < 8; ++j) same |= (o[j] == o[i]) ? b[j] : 0u;
+                const uint32_t partners = o[i] == kMulti ? present : (present & ~same);
+                const uint32_t q = __ffs(b[i]) - 1u;
+                const uint32_t bits = partners & sm.cand[q];
+                if (bits) or_row(sm.conf, q, bits);
+            }
+        } else {
+            for (uint32_t t = present; t; t &= t - 1u) {
+                const uint32_t q = __ffs(t) - 1u;
+                const uint32_t oq = tab[(size_t)q * pitch + c];
+                uint32_t same = 0;
+                for (uint32_t t2 = present; t2; t2 &= t2 - 1u) {
+                    const uint32_t r = __ffs(t2) - 1u;
+                    same |= (tab[(size_t)r * pitch + c] == oq) ? (1u << r) : 0u;
+                }
+                const uint32_t partners = oq == kMulti ? present : (present & ~same);
+                const uint32_t bits = partners & sm.cand[q];
+                if (bits) or_row(sm.conf, q, bits);
+            }
+        }
+        for (uint32_t t = present; t; t &= t - 1u) tab[(size_t)(__ffs(t) - 1u) * pitch + c] = kEmpty;
     }
 }
 
@@ -159,85 +271,28 @@ __global__ void __launch_bounds__(NT, MINB)
     for (uint32_t i = threadIdx.x; i < table_bytes / 16u; i += NT)
         reinterpret_cast<uint4 *>(tab)[i] = make_uint4(kRelAllOnes, kRelAllOnes, kRelAllOnes, kRelAllOnes);
     for (;;) {
-        if (threadIdx.x == 0) sm.item = atomicAdd(&ctrl[2], 1u);
-        __syncthreads();  // also: the previous program's reset is complete
-        const uint32_t item = sm.item;
-        if (item >= n_fast) break;
-        const uint32_t p = V.order[item];
-        {
-            const uint4 *src = reinterpret_cast<const uint4 *>(&V.progs[p]);
-            uint4 *d4 = reinterpret_cast<uint4 *>(&sm.prog);
-            for (uint32_t i = threadIdx.x; i < sizeof(DevProg) / 16; i += NT) d4[i] = src[i];
+        // warp 0 takes the next program and sets it up while the other warps
+        // wait at the barrier (the previous program's scan is complete)
+        if (warp == 0) {
+            uint32_t item = 0;
+            if (lane == 0) item = atomicAdd(&ctrl[2], 1u);
+            item = __shfl_sync(0xFFFFFFFFu, item, 0);
+            const uint32_t p = item < n_fast ? V.order[item] : kRelAllOnes;
+            if (lane == 0) sm.p = p;
+            if (p != kRelAllOnes) rel_setup(sm, &V.progs[p], masks ? masks[p] : 0u, table_bytes);
         }
         __syncthreads();
-        const uint32_t mask = masks ? masks[p] : 0u;
-        if (warp == 0) rel_setup(sm, mask, table_bytes);
-        __syncthreads();
-        const uint32_t R = sm.n_rows, W = sm.W, n_win = sm.n_win, use_col = sm.use_col, inj = sm.inj_rows;
+        const uint32_t p = sm.p;
+        if (p == kRelAllOnes) break;
+        const uint32_t R = sm.n_rows, W = sm.W, n_win = sm.n_win;
         if (sm.bad) {
             if (threadIdx.x == 0) atomicOr(&ctrl[1], kErrTableTooSmall);
         } else if (R) {
-            const uint32_t total = R * sm.prog.threads;
-            const uint32_t per_round = NT * kRelCache;
-            const uint32_t rounds = (total + per_round - 1u) / per_round;
-            uint32_t *colrows = reinterpret_cast<uint32_t *>(tab + (size_t)R * W);
-            uint32_t key[kRelCache];
-            if (rounds == 1) rel_keys<NT>(sm, V.perm, 0, total, key);
+            uint32_t *colrows = reinterpret_cast<uint32_t *>(tab + (size_t)R * sm.pitch);
             for (uint32_t w = 0; w < n_win; ++w) {
-                const uint32_t lo = w * W;
-                // install
-                for (uint32_t rd = 0; rd < rounds; ++rd) {
-                    if (rounds > 1) rel_keys<NT>(sm, V.perm, rd * per_round, total, key);
-#pragma unroll
-                    for (uint32_t k = 0; k < kRelCache; ++k) {
-                        const uint32_t x = key[k];
-                        if (x == kRelAllOnes || (x & 0xFFFFu) - lo >= W) continue;
-                        const uint32_t col = swizzle((x & 0xFFFFu) - lo), q = x >> 26;
-                        const uint16_t t = (uint16_t)((x >> 16) & 0x3FFu);
-                        uint16_t *e = tab + (size_t)q * W + col;
-                        if ((inj >> q) & 1u) {
-                            *e = t;
-                        } else if (atomicCAS(e, kEmpty, t) != kEmpty) {
-                            *e = kMulti;  // a second thread of this row on the word
-                        }
-                        if (use_col) atomicAnd(&colrows[col], ~(1u << q));
-                    }
-                }
+                rel_install<NT>(sm, V.perm, tab, colrows, w * W);
                 __syncthreads();
-                // probe
-                for (uint32_t rd = 0; rd < rounds; ++rd) {
-                    if (rounds > 1) rel_keys<NT>(sm, V.perm, rd * per_round, total, key);
-#pragma unroll
-                    for (uint32_t k = 0; k < kRelCache; ++k) {
-                        const uint32_t x = key[k];
-                        if (x == kRelAllOnes || (x & 0xFFFFu) - lo >= W) continue;
-                        const uint32_t col = swizzle((x & 0xFFFFu) - lo), q = x >> 26;
-                        const uint32_t t = (x >> 16) & 0x3FFu;
-                        uint32_t todo = sm.cand[q] & ~*(volatile uint32_t *)&sm.conf[q];
-                        if (!todo) continue;
-                        if (use_col) todo &= ~colrows[col];
-                        uint32_t hits = 0;
-                        for (; todo; todo &= todo - 1u) {
-                            const uint32_t j = __ffs(todo) - 1u;
-                            const uint32_t o = tab[(size_t)j * W + col];
-                            hits |= (o != kEmpty && o != t) ? (1u << j) : 0u;
-                        }
-                        if (hits) or_row(sm.conf, q, hits);
-                    }
-                }
-                __syncthreads();
-                // reset
-                for (uint32_t rd = 0; rd < rounds; ++rd) {
-                    if (rounds > 1) rel_keys<NT>(sm, V.perm, rd * per_round, total, key);
-#pragma unroll
-                    for (uint32_t k = 0; k < kRelCache; ++k) {
-                        const uint32_t x = key[k];
-                        if (x == kRelAllOnes || (x & 0xFFFFu) - lo >= W) continue;
-                        const uint32_t col = swizzle((x & 0xFFFFu) - lo), q = x >> 26;
-                        tab[(size_t)q * W + col] = kEmpty;
-                        if (use_col) colrows[col] = kRelAllOnes;
-                    }
-                }
+                rel_scan<NT>(sm, tab, colrows);
                 __syncthreads();
             }
         }
@@ -261,13 +316,16 @@ __global__ void __launch_bounds__(NT, MINB)
             uint32_t dv = 0;
             unsigned long long pairs = 0;
             if (masks) {
+                const uint32_t mask = masks[p];
                 dv = diverge_warp(P, mask, lane);
                 const uint32_t S = P.n_stmts, gaps = gap_mask(P, mask);
+                sm.nact[lane] = lane < S ? guard_count(P.threads, P.stmts[lane].gk, P.stmts[lane].gr) : 0u;
+                __syncwarp();
                 for (uint32_t idx = lane; idx < S * S; idx += 32u) {
                     const uint32_t i = idx / S, j = idx - i * S;
                     if (j < i || (gaps & range_mask(i, j))) continue;
                     uint64_t same, cross;
-                    pair_count(P, i, j, same, cross);
+                    pair_count(P, sm.nact, i, j, same, cross);
                     pairs += same;
                 }
                 pairs = warp_sum_u64(pairs);
@@ -277,6 +335,7 @@ __global__ void __launch_bounds__(NT, MINB)
                 wo.n_stmts = P.n_stmts;
                 wo.access_pairs = pairs;
             }
+            __syncwarp();
         }
     }
 }
