@@ -288,6 +288,35 @@ __device__ bool warp_solve(LoopWarp &lw, const uint32_t *cl, uint32_t n, uint32_
     const uint32_t r = __popc(R);
     const uint32_t L = r < 5 ? r : 5;
     const uint32_t rh = r - L;
+    if (r <= 5) {
+        // no high part: lane l tries the low assignment l itself (the slots
+        // of R in order; l < 2^r), every lane at once
+        const uint32_t l = lane;
+        bool ok = l < (1u << r);
+        uint32_t x = 0, wt = 0;
+        if (ok) {
+            uint32_t t = R;
+            for (uint32_t b = 0; b < r; ++b, t &= t - 1u) {
+                if ((l >> b) & 1u) {
+                    const uint32_t k = __ffs(t) - 1u;
+                    x |= 1u << k;
+                    wt += w[k];
+                }
+            }
+            for (uint32_t c = 0; c < n_kept && ok; ++c) ok = (lw.A[c] & x) != 0u;
+            for (uint32_t c = 0; c < n_negk && ok; ++c) ok = (lw.nhi[c] & ~x) != 0u;
+        }
+        // the key compares (weight, compact mask): the compact mask of x is l
+        const unsigned long long key = ok ? (((unsigned long long)wt << 32) | l) : ~0ull;
+        const unsigned long long best = warp_min_u64(key);
+        __syncwarp();
+        if (best == ~0ull) return false;
+        mask_out = pdep32((uint32_t)best, R) | forced;
+        uint32_t wf = (uint32_t)(best >> 32);
+        for (uint32_t t = forced; t; t &= t - 1u) wf += w[__ffs(t) - 1u];
+        weight_out = wf;
+        return true;
+    }
     {
         uint32_t v = 0;
         if (lane < r) {  // the weight of R's lane-th slot
@@ -614,19 +643,42 @@ __global__ void __launch_bounds__(WARPS * 32)
         lw.nact[lane] = lane < S ? guard_count(P.threads, P.stmts[lane].gk, P.stmts[lane].gr) : 0u;
         __syncwarp();
         unsigned long long pairs = 0;
+        // the gaps of up to four checked masks in registers (most programs)
+        uint32_t g[4], x[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            g[k] = k < iters ? lw.tg[k] : 0u;
+            x[k] = k < iters ? lw.tgg[k] : 0u;
+        }
+        // pair (i, j) = divmod(idx, S), stepped by 32 without a division
+        uint32_t i = lane / S, j = lane - i * S;
         for (uint32_t idx = lane; idx < S * S; idx += 32u) {
-            const uint32_t i = idx / S, j = idx - i * S;
-            if (j < i) continue;
-            uint64_t same, cross;
-            pair_count(P, lw.nact, i, j, same, cross);
-            if (!same && !cross) continue;
-            const uint32_t rg = range_mask(i, j);
-            uint32_t cs = 0, cx = 0;
-            for (uint32_t k = 0; k < iters; ++k) {
-                cs += (lw.tg[k] & rg) == 0u ? 1u : 0u;
-                cx += (lw.tgg[k] & rg) == 0u ? 1u : 0u;
+            if (j >= i) {
+                uint64_t same, cross;
+                pair_count(P, lw.nact, i, j, same, cross);
+                if (same || cross) {
+                    const uint32_t rg = range_mask(i, j);
+                    uint32_t cs = 0, cx = 0;
+                    if (iters <= 4) {
+#pragma unroll
+                        for (uint32_t k = 0; k < 4; ++k) {
+                            cs += (k < iters && (g[k] & rg) == 0u) ? 1u : 0u;
+                            cx += (k < iters && (x[k] & rg) == 0u) ? 1u : 0u;
+                        }
+                    } else {
+                        for (uint32_t k = 0; k < iters; ++k) {
+                            cs += (lw.tg[k] & rg) == 0u ? 1u : 0u;
+                            cx += (lw.tgg[k] & rg) == 0u ? 1u : 0u;
+                        }
+                    }
+                    pairs += same * cs + cross * cx;
+                }
             }
-            pairs += same * cs + cross * cx;
+            j += 32u;
+            while (j >= S) {
+                j -= S;
+                ++i;
+            }
         }
         pairs = warp_sum_u64(pairs);
         if (lane == 0) {

@@ -4,22 +4,26 @@
 // 0's, and no pair of blocks shares an array, so one owner-table pass over
 // block 0 decides every candidate pair.
 //
-// Each CTA takes programs from a work queue and, per program:
-//   setup   — (warp 0) the candidate pairs: under a mask, the instance pairs
+// Each CTA takes programs from a work queue.  Warp 0 is the control warp: it
+// runs one program ahead of the others (two program buffers), fetching and
+// setting up program k+1 and writing out program k-1 while warps 1.. (the
+// workers) check program k, so that the setup's loads and the output overlap
+// the table passes.  Per program:
+//   setup   — (control) the candidate pairs: under a mask, the instance pairs
 //             (i <= j) with a write and no enabled barrier between them (one
 //             phase, Section 2.2); for the repair loop, every pair with a
 //             write (the empty mask), which gives the program's whole
 //             conflict relation.  Instances with the same map and guard touch
 //             the same words from the same threads and share one table row.
-//   install — every access computes its word address from the map (affine
-//             or strided arithmetic, or one permutation-table load) and
-//             writes its thread into its row's owner entry at that word; two
-//             threads of a row on one word leave MULTI (a compare-and-swap,
-//             only for rows whose map is not injective on the block's
+//   install — (workers) every access computes its word address from the map
+//             (affine or strided arithmetic, or one permutation-table load)
+//             and writes its thread into its row's owner entry at that word;
+//             two threads of a row on one word leave MULTI (a compare-and-
+//             swap, only for rows whose map is not injective on the block's
 //             threads).  A bit per row and column marks the rows holding an
 //             entry there.
-//   scan    — each thread takes whole columns: the rows holding an entry at a
-//             column conflict pairwise unless both entries name the same
+//   scan    — (workers) each thread takes whole columns: two rows holding an
+//             entry at a column conflict unless both entries name the same
 //             single thread (an entry of another thread, or MULTI, is a
 //             second thread on the word: the race definition of Section 1
 //             made concrete — two distinct threads, one word, at least one
@@ -41,21 +45,26 @@ namespace gr {
 
 constexpr uint32_t kRelAllOnes = 0xFFFFFFFFu;
 
-struct RelSmem {
+// One program's state (the control warp fills one while the workers use the
+// other).
+struct RelProg {
     DevProg prog;
     uint32_t cand[32];      // table row q: partner rows (bit j, j >= q) to decide
     uint32_t conf[32];      // table row q: partner rows found to conflict
     uint32_t pend[32];      // instance i: candidate partners (bit j, j >= i)
     uint32_t rep_conf[32];  // the conflicts by pattern representative
-    uint32_t rep_list[32];  // representative of table row q
     // table row q's access map (its representative's statement, block 0):
     uint32_t row_am[32];    // address of thread t: (am t + bm) mod M, or
     uint32_t row_bm[32];    //   perm[po + (t + bm) mod M] when po != ~0
     uint32_t row_po[32];
     uint32_t row_gk[32], row_gr[32];  // guard (gk == 0: none)
     uint32_t nact[32];      // active threads of each instance (for the pair count)
-    uint32_t involved, n_rows, W, pitch, n_win, inj_rows, bad, p;
+    uint32_t involved, n_rows, W, pitch, n_win, inj_rows, bad, p, mask;
     uint32_t M, Mmagic;     // the shared array's words; floor((2^32 - 1) / M)
+};
+
+struct RelSmem {
+    RelProg buf[2];
 };
 
 constexpr size_t kRelFixed = (sizeof(RelSmem) + 15) / 16 * 16;
@@ -77,7 +86,7 @@ __device__ __forceinline__ uint32_t mod_by(uint32_t x, uint32_t M, uint32_t magi
 
 // Per-program setup by warp 0: the program record, candidate pairs, table
 // rows and their maps, window size.
-__device__ void rel_setup(RelSmem &sm, const DevProg *gp, uint32_t mask, uint32_t table_bytes) {
+__device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_t table_bytes) {
     const uint32_t lane = threadIdx.x & 31u;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(gp);
@@ -110,7 +119,6 @@ __device__ void rel_setup(RelSmem &sm, const DevProg *gp, uint32_t mask, uint32_
     // compresses to a row mask by bit extraction
     if (keep) {
         const DevStmt &st = P.stmts[lane];
-        sm.rep_list[row] = lane;
         sm.cand[row] = pext32(rp, involved);
         sm.conf[row] = 0;
         sm.row_am[row] = st.am;
@@ -141,21 +149,22 @@ __device__ void rel_setup(RelSmem &sm, const DevProg *gp, uint32_t mask, uint32_
         sm.n_win = n_win;
         sm.inj_rows = pext32(inj, involved);
         sm.bad = (R && W == 0) ? 1u : 0u;
+        sm.mask = mask;
     }
 }
 
 // Install the accesses of the words [lo, lo + W) into the table: unit u (one
-// per warp at a time) covers table row q = u / cpr, threads 32 c .. 32 c + 31
-// with c = u mod cpr (cpr = chunks of 32 threads per row); lane l takes
-// thread 32 c + l.
+// per worker warp at a time) covers table row q = u / cpr, threads
+// 32 c .. 32 c + 31 with c = u mod cpr (cpr = chunks of 32 threads per row);
+// lane l takes thread 32 c + l.
 template <uint32_t NT>
-__device__ __forceinline__ void rel_install(const RelSmem &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
+__device__ __forceinline__ void rel_install(const RelProg &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
                                             uint32_t *colrows, uint32_t lo) {
-    constexpr uint32_t NW = NT / 32;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    constexpr uint32_t NWK = NT / 32 - 1;  // worker warps
+    const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - 1u;
     const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W, pitch = sm.pitch;
     const uint32_t cpr = (T + 31u) >> 5, n_units = sm.n_rows * cpr, inj = sm.inj_rows;
-    for (uint32_t u = warp; u < n_units; u += NW) {  // uniform over the warp
+    for (uint32_t u = wk; u < n_units; u += NWK) {  // uniform over the warp
         const uint32_t q = u / cpr, c = u - q * cpr;
         const uint32_t tb = c << 5, t = tb + lane;
         const uint32_t gk = sm.row_gk[q];
@@ -188,66 +197,92 @@ __device__ __forceinline__ void rel_install(const RelSmem &sm, const uint16_t *_
     }
 }
 
-// Scan the columns of the window: the rows holding an entry at a column
-// conflict pairwise unless both entries are the same single thread.  Up to 8
-// rows per column are compared in registers; more take the general loop.
-// Every entry read, and the column mask, go back to empty.
+// Scan the window's columns (worker threads): two rows holding an entry at a
+// column conflict unless both entries are the same single thread; a row's
+// MULTI entry is its own race.  Each pair is compared once, from its lower
+// row (the candidates of a row are its pairs with higher rows).  Every
+// entry read, and the column mask, go back to empty.
 template <uint32_t NT>
-__device__ __forceinline__ void rel_scan(RelSmem &sm, uint16_t *tab, uint32_t *colrows) {
-    const uint32_t W = sm.W, pitch = sm.pitch, inj = sm.inj_rows;
-    for (uint32_t c = threadIdx.x; c < W; c += NT) {
+__device__ __forceinline__ void rel_scan(RelProg &sm, uint16_t *tab, uint32_t *colrows) {
+    const uint32_t W = sm.W, pitch = sm.pitch;
+    for (uint32_t c = threadIdx.x - 32u; c < W; c += NT - 32u) {
         const uint32_t present = ~colrows[c];
         if (!present) continue;
         colrows[c] = kRelAllOnes;
-        if ((present & (present - 1u)) == 0u) {
-            // one row: only its own second thread (MULTI) can race with it
-            const uint32_t q = __ffs(present) - 1u;
-            uint16_t *e = tab + (size_t)q * pitch + c;
-            if (!((inj >> q) & 1u) && *e == kMulti && ((sm.cand[q] >> q) & 1u)) or_row(sm.conf, q, 1u << q);
-            *e = kEmpty;
-            continue;
-        }
-        uint32_t o[8], b[8], rest = present;
-#pragma unroll
-        for (uint32_t i = 0; i < 8; ++i) {
-            if (rest) {
-                const uint32_t q = __ffs(rest) - 1u;
-                rest &= rest - 1u;
-                o[i] = tab[(size_t)q * pitch + c];
-                b[i] = 1u << q;
-            } else {
-                o[i] = 0x10000u + i;  // distinct from every entry and from each other
-                b[i] = 0;
+        for (uint32_t t = present; t; t &= t - 1u) {
+            const uint32_t qi = __ffs(t) - 1u;
+            uint16_t *ei = tab + (size_t)qi * pitch + c;
+            const uint32_t oi = *ei;
+            *ei = kEmpty;  // no later row of this column reads it again
+            uint32_t bits = oi == kMulti ? (1u << qi) : 0u;
+            for (uint32_t t2 = t & (t - 1u); t2; t2 &= t2 - 1u) {
+                const uint32_t qj = __ffs(t2) - 1u;
+                const uint32_t oj = tab[(size_t)qj * pitch + c];
+                bits |= (oi != oj || oi == kMulti) ? (1u << qj) : 0u;
             }
+            bits &= sm.cand[qi];
+            if (bits) or_row(sm.conf, qi, bits);
         }
-        if (!rest) {
-#pragma unroll
-            for (uint32_t i = 0; i < 8; ++i) {
-                if (!b[i]) continue;
-                uint32_t same = 0;
-#pragma unroll
-                for (uint32_t j = 0; j < 8; ++j) same |= (o[j] == o[i]) ? b[j] : 0u;
-                const uint32_t partners = o[i] == kMulti ? present : (present & ~same);
-                const uint32_t q = __ffs(b[i]) - 1u;
-                const uint32_t bits = partners & sm.cand[q];
-                if (bits) or_row(sm.conf, q, bits);
-            }
-        } else {
-            for (uint32_t t = present; t; t &= t - 1u) {
-                const uint32_t q = __ffs(t) - 1u;
-                const uint32_t oq = tab[(size_t)q * pitch + c];
-                uint32_t same = 0;
-                for (uint32_t t2 = present; t2; t2 &= t2 - 1u) {
-                    const uint32_t r = __ffs(t2) - 1u;
-                    same |= (tab[(size_t)r * pitch + c] == oq) ? (1u << r) : 0u;
-                }
-                const uint32_t partners = oq == kMulti ? present : (present & ~same);
-                const uint32_t bits = partners & sm.cand[q];
-                if (bits) or_row(sm.conf, q, bits);
-            }
-        }
-        for (uint32_t t = present; t; t &= t - 1u) tab[(size_t)(__ffs(t) - 1u) * pitch + c] = kEmpty;
     }
+}
+
+// The program's witness rows (race_intra; one array per block, so no
+// cross-block pairs) from the row conflicts, and under a mask its divergent
+// slots and pair count.  Warp 0.
+__device__ void rel_output(RelProg &sm, gr_witnesses *dst, bool with_mask) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const DevProg &P = sm.prog;
+    const uint32_t involved = sm.involved, p = sm.p;
+    uint32_t rc = 0;
+    if ((involved >> lane) & 1u) rc = pdep32(sm.conf[__popc(involved & ((1u << lane) - 1u))], involved);
+    sm.rep_conf[lane] = rc;
+    __syncwarp();
+    uint32_t rows = 0;
+    for (uint32_t t = sm.pend[lane]; t; t &= t - 1u) {
+        const uint32_t j = __ffs(t) - 1u;
+        const uint32_t ri = P.rep[lane], rj = P.rep[j];
+        if ((sm.rep_conf[min(ri, rj)] >> max(ri, rj)) & 1u) rows |= 1u << j;
+    }
+    gr_witnesses &wo = dst[p];
+    wo.race_intra[lane] = rows;
+    wo.race_inter[lane] = 0u;
+    uint32_t dv = 0;
+    unsigned long long pairs = 0;
+    if (with_mask) {
+        const uint32_t mask = sm.mask;
+        dv = diverge_warp(P, mask, lane);
+        const uint32_t S = P.n_stmts, gaps = gap_mask(P, mask);
+        sm.nact[lane] = lane < S ? guard_count(P.threads, P.stmts[lane].gk, P.stmts[lane].gr) : 0u;
+        __syncwarp();
+        for (uint32_t idx = lane; idx < S * S; idx += 32u) {
+            const uint32_t i = idx / S, j = idx - i * S;
+            if (j < i || (gaps & range_mask(i, j))) continue;
+            uint64_t same, cross;
+            pair_count(P, sm.nact, i, j, same, cross);
+            pairs += same;
+        }
+        pairs = warp_sum_u64(pairs);
+    }
+    if (lane == 0) {
+        wo.diverge = dv;
+        wo.n_stmts = P.n_stmts;
+        wo.access_pairs = pairs;
+    }
+    __syncwarp();
+}
+
+// The control warp: the next program from the queue into `b`, set up.
+__device__ __forceinline__ void rel_fetch(RelProg &b, const ArenaView &V, uint32_t *ctrl, uint32_t n_fast,
+                                          const uint32_t *masks, uint32_t table_bytes) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(&ctrl[2], 1u);
+    item = __shfl_sync(0xFFFFFFFFu, item, 0);
+    const uint32_t p = item < n_fast ? V.order[item] : kRelAllOnes;
+    if (p != kRelAllOnes) rel_setup(b, &V.progs[p], masks ? masks[p] : 0u, table_bytes);
+    __syncwarp();
+    if (lane == 0) b.p = p;
+    __syncwarp();
 }
 
 template <uint32_t NT, uint32_t MINB>
@@ -266,77 +301,43 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     gr_witnesses *dst = out ? out : reinterpret_cast<gr_witnesses *>(scratch + V.h->scratch_rel_off);
     const uint32_t n_fast = V.h->n_fast;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t warp = threadIdx.x >> 5;
+    constexpr uint32_t kWorkers = NT - 32u;
     // every table entry is empty (all ones) between programs
     for (uint32_t i = threadIdx.x; i < table_bytes / 16u; i += NT)
         reinterpret_cast<uint4 *>(tab)[i] = make_uint4(kRelAllOnes, kRelAllOnes, kRelAllOnes, kRelAllOnes);
-    for (;;) {
-        // warp 0 takes the next program and sets it up while the other warps
-        // wait at the barrier (the previous program's scan is complete)
+    if (warp == 0) {
+        rel_fetch(sm.buf[0], V, ctrl, n_fast, masks, table_bytes);
+        if ((threadIdx.x & 31u) == 0) sm.buf[1].p = kRelAllOnes;
+    }
+    __syncthreads();
+    for (uint32_t k = 0;; ++k) {
+        RelProg &cur = sm.buf[k & 1u], &prv = sm.buf[(k & 1u) ^ 1u];
+        const bool have_cur = cur.p != kRelAllOnes, have_prv = prv.p != kRelAllOnes;
+        if (!have_cur && !have_prv) break;  // uniform
         if (warp == 0) {
-            uint32_t item = 0;
-            if (lane == 0) item = atomicAdd(&ctrl[2], 1u);
-            item = __shfl_sync(0xFFFFFFFFu, item, 0);
-            const uint32_t p = item < n_fast ? V.order[item] : kRelAllOnes;
-            if (lane == 0) sm.p = p;
-            if (p != kRelAllOnes) rel_setup(sm, &V.progs[p], masks ? masks[p] : 0u, table_bytes);
+            // program k-1 out, then program k+1 into its buffer
+            if (have_prv) rel_output(prv, dst, masks != nullptr);
+            if (have_cur) {
+                rel_fetch(prv, V, ctrl, n_fast, masks, table_bytes);
+            } else if ((threadIdx.x & 31u) == 0) {
+                prv.p = kRelAllOnes;
+            }
+        } else if (have_cur) {
+            const uint32_t R = cur.n_rows, W = cur.W, n_win = cur.n_win;
+            if (cur.bad) {
+                if (threadIdx.x == 32) atomicOr(&ctrl[1], kErrTableTooSmall);
+            } else if (R) {
+                uint32_t *colrows = reinterpret_cast<uint32_t *>(tab + (size_t)R * cur.pitch);
+                for (uint32_t w = 0; w < n_win; ++w) {
+                    rel_install<NT>(cur, V.perm, tab, colrows, w * W);
+                    asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory");
+                    rel_scan<NT>(cur, tab, colrows);
+                    asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory");
+                }
+            }
         }
         __syncthreads();
-        const uint32_t p = sm.p;
-        if (p == kRelAllOnes) break;
-        const uint32_t R = sm.n_rows, W = sm.W, n_win = sm.n_win;
-        if (sm.bad) {
-            if (threadIdx.x == 0) atomicOr(&ctrl[1], kErrTableTooSmall);
-        } else if (R) {
-            uint32_t *colrows = reinterpret_cast<uint32_t *>(tab + (size_t)R * sm.pitch);
-            for (uint32_t w = 0; w < n_win; ++w) {
-                rel_install<NT>(sm, V.perm, tab, colrows, w * W);
-                __syncthreads();
-                rel_scan<NT>(sm, tab, colrows);
-                __syncthreads();
-            }
-        }
-        if (warp == 0) {
-            // row conflicts back to representatives, then to instance pairs
-            const DevProg &P = sm.prog;
-            const uint32_t involved = sm.involved;
-            uint32_t rc = 0;
-            if ((involved >> lane) & 1u) rc = pdep32(sm.conf[__popc(involved & ((1u << lane) - 1u))], involved);
-            sm.rep_conf[lane] = rc;
-            __syncwarp();
-            uint32_t rows = 0;
-            for (uint32_t t = sm.pend[lane]; t; t &= t - 1u) {
-                const uint32_t j = __ffs(t) - 1u;
-                const uint32_t ri = P.rep[lane], rj = P.rep[j];
-                if ((sm.rep_conf[min(ri, rj)] >> max(ri, rj)) & 1u) rows |= 1u << j;
-            }
-            gr_witnesses &wo = dst[p];
-            wo.race_intra[lane] = rows;
-            wo.race_inter[lane] = 0u;  // one array per block: no cross-block pairs
-            uint32_t dv = 0;
-            unsigned long long pairs = 0;
-            if (masks) {
-                const uint32_t mask = masks[p];
-                dv = diverge_warp(P, mask, lane);
-                const uint32_t S = P.n_stmts, gaps = gap_mask(P, mask);
-                sm.nact[lane] = lane < S ? guard_count(P.threads, P.stmts[lane].gk, P.stmts[lane].gr) : 0u;
-                __syncwarp();
-                for (uint32_t idx = lane; idx < S * S; idx += 32u) {
-                    const uint32_t i = idx / S, j = idx - i * S;
-                    if (j < i || (gaps & range_mask(i, j))) continue;
-                    uint64_t same, cross;
-                    pair_count(P, sm.nact, i, j, same, cross);
-                    pairs += same;
-                }
-                pairs = warp_sum_u64(pairs);
-            }
-            if (lane == 0) {
-                wo.diverge = dv;
-                wo.n_stmts = P.n_stmts;
-                wo.access_pairs = pairs;
-            }
-            __syncwarp();
-        }
     }
 }
 

@@ -102,9 +102,9 @@ def test_batch1024_full_size(gb):
     _, got = _run(gb, progs)
     for p, r in zip(progs, got):
         _properties(p, r)
-    sample = list(range(0, 1024, 43))
-    want = oracle.repair_batch([progs[i] for i in sample], n_threads=N_THREADS)
-    for i, w in zip(sample, want):
+    # every program, every field (about 30 s of oracle time on 16 cores)
+    want = oracle.repair_batch(progs, n_threads=N_THREADS)
+    for i, w in enumerate(want):
         for k in KEYS:
             assert got[i][k] == w[k], (i, k)
 
@@ -115,7 +115,9 @@ def test_uneven4096_full_size(gb):
     _, got = _run(gb, progs)
     for p, r in zip(progs, got):
         _properties(p, r)
-    sample = [i for i, p in enumerate(progs) if p.blocks * p.threads <= 1500][:48]
+    # every program of at most 4,096 threads in all, every field
+    sample = [i for i, p in enumerate(progs) if p.blocks * p.threads <= 4096]
+    assert len(sample) > 2000
     big = max(range(len(progs)), key=lambda i: progs[i].blocks * progs[i].threads * progs[i].n_stmts)
     want = oracle.repair_batch([progs[i] for i in sample], n_threads=N_THREADS)
     for i, w in zip(sample, want):
@@ -154,6 +156,19 @@ def test_interblock_full_size_sampled(gb, idx):
         assert r["status"] == 0 and (r["mask"], r["weight"]) == sol
     # repair mode with no existing barriers: the first check (mask 0) sees every race
     assert r["clauses"] == cls
+
+
+def test_interblock_full_size_every_field(gb):
+    """Eight programs of the inter-block batch (64 blocks x 256 threads over a
+    65,536-word global array) at full size, compared with the oracle's own
+    loop on every field: trajectory, iterations, clauses, access pairs."""
+    progs = synth.generate("interblock256_64x256_s16")
+    _, got = _run(gb, progs)
+    idx = list(range(5, 256, 32))
+    want = oracle.repair_batch([progs[i] for i in idx], n_threads=N_THREADS)
+    for i, w in zip(idx, want):
+        for k in KEYS:
+            assert got[i][k] == w[k], (i, k)
 
 
 def test_large_program_full_size(gb):
