@@ -174,7 +174,10 @@ __device__ __forceinline__ uint32_t mod_inverse(uint32_t a, uint32_t m) {
 __device__ __forceinline__ uint32_t guard_both(uint32_t T, uint32_t k1, uint32_t r1, uint32_t k2, uint32_t r2) {
     if (k1 == 0) return guard_count(T, k2, r2);
     if (k2 == 0) return guard_count(T, k1, r1);
-    if (k1 == k2) return r1 == r2 ? guard_count(T, k1, r1) : 0u;
+    // one modulus a multiple of the other (powers of two, equal moduli): the
+    // finer congruence decides, and it must agree with the coarser one
+    if (k2 % k1 == 0) return r2 % k1 == r1 ? guard_count(T, k2, r2) : 0u;
+    if (k1 % k2 == 0) return r1 % k2 == r2 ? guard_count(T, k1, r1) : 0u;
     uint32_t a = k1, b = k2;
     while (b) {
         const uint32_t t = a % b;

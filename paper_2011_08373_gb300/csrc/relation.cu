@@ -58,6 +58,7 @@ struct RelProg {
     uint32_t row_bm[32];    //   perm[po + (t + bm) mod M] when po != ~0
     uint32_t row_po[32];
     uint32_t row_gk[32], row_gr[32];  // guard (gk == 0: none)
+    uint32_t row_gmag[32];  // floor((2^32 - 1) / gk)
     uint32_t nact[32];      // active threads of each instance (for the pair count)
     uint32_t involved, n_rows, W, pitch, n_win, inj_rows, bad, p, mask;
     uint32_t M, Mmagic;     // the shared array's words; floor((2^32 - 1) / M)
@@ -126,6 +127,7 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
         sm.row_po[row] = st.kind == GR_PERM ? st.perm_off : kRelAllOnes;
         sm.row_gk[row] = st.gk;
         sm.row_gr[row] = st.gr;
+        sm.row_gmag[row] = st.gk ? 0xFFFFFFFFu / st.gk : 0u;
     }
     const uint32_t inj = __ballot_sync(0xFFFFFFFFu, keep && (P.stmts[lane].flags & kStmtInjective));
     if (lane == 0) {
@@ -156,7 +158,10 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
 // Install the accesses of the words [lo, lo + W) into the table: unit u (one
 // per worker warp at a time) covers table row q = u / cpr, threads
 // 32 c .. 32 c + 31 with c = u mod cpr (cpr = chunks of 32 threads per row);
-// lane l takes thread 32 c + l.
+// lane l takes thread 32 c + l.  (q, c) steps from unit to unit without a
+// division, and every reduction is a reciprocal multiply.  When the array
+// takes several windows, an affine unit whose 32 words (a run of 31 am + 1
+// positions, cyclically) miss the window is skipped whole.
 template <uint32_t NT>
 __device__ __forceinline__ void rel_install(const RelProg &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
                                             uint32_t *colrows, uint32_t lo) {
@@ -164,36 +169,48 @@ __device__ __forceinline__ void rel_install(const RelProg &sm, const uint16_t *_
     const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - 1u;
     const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W, pitch = sm.pitch;
     const uint32_t cpr = (T + 31u) >> 5, n_units = sm.n_rows * cpr, inj = sm.inj_rows;
+    const bool windows = sm.n_win > 1;
+    const uint32_t dq = NWK / cpr, dc = NWK - dq * cpr;
+    uint32_t q = wk / cpr, c = wk - q * cpr;
     for (uint32_t u = wk; u < n_units; u += NWK) {  // uniform over the warp
-        const uint32_t q = u / cpr, c = u - q * cpr;
         const uint32_t tb = c << 5, t = tb + lane;
-        const uint32_t gk = sm.row_gk[q];
+        const uint32_t gk = sm.row_gk[q], am = sm.row_am[q], bm = sm.row_bm[q], po = sm.row_po[q];
+        const uint32_t qq = q;
+        c += dc;
+        q += dq;
+        if (c >= cpr) {
+            c -= cpr;
+            ++q;
+        }
+        if (windows && po == kRelAllOnes && am * 31u + 1u < M) {
+            // am * tb + bm < 2^27: the unit's first word and the run to its last
+            const uint32_t start = mod_by(am * tb + bm, M, magic);
+            const uint32_t d = lo >= start ? lo - start : lo + M - start;  // (lo - start) mod M
+            const uint32_t e = start >= lo ? start - lo : start + M - lo;  // (start - lo) mod M
+            if (d > am * 31u && e >= W) continue;
+        }
         bool on = t < T;
         if (gk) {
-            const uint32_t gr = sm.row_gr[q];
-            if ((gk & (gk - 1u)) == 0u) on = on && (t & (gk - 1u)) == gr;
-            else on = on && (tb % gk + lane) % gk == gr;
+            const uint32_t gr = sm.row_gr[qq];
+            on = on && ((gk & (gk - 1u)) == 0u ? (t & (gk - 1u)) : mod_by(t, gk, sm.row_gmag[qq])) == gr;
         }
-        const uint32_t am = sm.row_am[q], bm = sm.row_bm[q], po = sm.row_po[q];
         uint32_t a;
         if (po != kRelAllOnes) {
-            // 32-bit: tb + bm < 2^10 + 2^16; ib + lane < 2^17
-            const uint32_t ib = (tb + bm) % M;
-            a = on ? (uint32_t)__ldg(perm + po + mod_by(ib + lane, M, magic)) : 0u;
+            // t + bm < 2^10 + 2^16
+            a = on ? (uint32_t)__ldg(perm + po + mod_by(t + bm, M, magic)) : 0u;
         } else {
-            // am, bm < M <= 2^16, tb < 2^10: am tb + bm < 2^27; xb + am lane < 2^22
-            const uint32_t xb = (am * tb + bm) % M;
-            a = mod_by(xb + am * lane, M, magic);
+            // am, bm < M <= 2^16, t < 2^10: am t + bm < 2^27
+            a = mod_by(am * t + bm, M, magic);
         }
         if (!on || a - lo >= W) continue;
         const uint32_t col = swizzle(a - lo);
-        uint16_t *e = tab + (size_t)q * pitch + col;
-        if ((inj >> q) & 1u) {
+        uint16_t *e = tab + (size_t)qq * pitch + col;
+        if ((inj >> qq) & 1u) {
             *e = (uint16_t)t;
         } else if (atomicCAS(e, kEmpty, (uint16_t)t) != kEmpty) {
             *e = kMulti;  // a second thread of this row on the word
         }
-        atomicAnd(&colrows[col], ~(1u << q));
+        atomicAnd(&colrows[col], ~(1u << qq));
     }
 }
 
