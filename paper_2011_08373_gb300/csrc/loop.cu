@@ -43,7 +43,7 @@ struct LoopWarp {
     uint32_t wc[32], wlo[32], lb[34];
     uint32_t w4[8][16];     // weight of each nibble of the high part
     uint32_t size_at[34];
-    uint32_t nact[32];      // active threads of each instance
+    unsigned long long pk[32];  // instance fields for the pair count: guard k, r, active threads, write, space
 };
 
 constexpr size_t kLoopSmem = (sizeof(LoopWarp) + 15) / 16 * 16;
@@ -207,6 +207,37 @@ __device__ bool warp_solve(LoopWarp &lw, const uint32_t *cl, uint32_t n, uint32_
     const uint32_t *w = P.weights;
     const uint32_t lane = lane_id();
     if (forced & forbidden) return false;
+    uint32_t n_kept = 0, U = 0, R = 0;
+    if (n <= 32u) {
+        // one clause per lane, in registers: drop a clause hit by a forced
+        // slot, remove forbidden slots (an emptied clause: unsatisfiable),
+        // then keep a clause unless another is a strict subset of it or an
+        // equal one sits on a lower lane (the same kept set as the size-ordered
+        // pass below)
+        uint32_t pc = 0;
+        bool bad = false;
+        if (lane < n) {
+            const uint32_t c = cl[lane];
+            if (!(c & forced)) {
+                pc = c & ~forbidden;
+                bad = pc == 0u;
+            }
+        }
+        if (__any_sync(0xFFFFFFFFu, bad)) return false;
+        bool keep = pc != 0u;
+        for (uint32_t j = 0; j < n; ++j) {
+            const uint32_t d = __shfl_sync(0xFFFFFFFFu, pc, j);
+            keep = keep && !(d != 0u && (d & ~pc) == 0u && (d != pc || j < lane));
+        }
+        const bool unit = keep && (pc & (pc - 1u)) == 0u;
+        U = __reduce_or_sync(0xFFFFFFFFu, unit ? pc : 0u);
+        const bool multi = keep && !unit;
+        R = __reduce_or_sync(0xFFFFFFFFu, multi ? pc : 0u);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, multi);
+        if (multi) lw.A[__popc(bal & ((1u << lane) - 1u))] = pc;
+        n_kept = __popc(bal);
+        __syncwarp();
+    } else {
     lw.size_at[lane] = 0;
     if (lane < 2) lw.size_at[32 + lane] = 0;
     __syncwarp();
@@ -244,7 +275,6 @@ __device__ bool warp_solve(LoopWarp &lw, const uint32_t *cl, uint32_t n, uint32_
     __syncwarp();
     // subsumption, in size order: keep a clause unless an earlier one is a
     // subset of it (of two equal clauses the later one goes)
-    uint32_t n_kept = 0, U = 0, R = 0;
     for (uint32_t base = 0; base < n_sorted; base += 32u) {
         const uint32_t i = base + lane;
         bool keep = false, unit = false;
@@ -263,6 +293,7 @@ __device__ bool warp_solve(LoopWarp &lw, const uint32_t *cl, uint32_t n, uint32_
         n_kept += __popc(bal);
     }
     __syncwarp();
+    }
     // a kept clause never contains a unit's slot (the unit subsumes it)
     forced |= U;
     // negative clauses: a forbidden slot in one keeps it satisfied; one inside
@@ -640,7 +671,18 @@ __global__ void __launch_bounds__(WARPS * 32)
         for (uint32_t i = lane; i < GR_MAX_CLAUSES; i += 32u) o.clauses[i] = i < n_cl ? lw.cl[i] : 0u;
         __syncwarp();
         // thread pairs a pairwise checker examines, summed over the checks
-        lw.nact[lane] = lane < S ? guard_count(P.threads, P.stmts[lane].gk, P.stmts[lane].gr) : 0u;
+        // lane i takes row i: the pairs (i, i + d), d = 0, 1, .. in step over
+        // the warp; each instance's fields packed in one shared word
+        {
+            uint64_t pk = 0;
+            if (lane < S) {
+                const DevStmt &st = P.stmts[lane];
+                const uint32_t na = guard_count(P.threads, st.gk, st.gr);
+                pk = (uint64_t)st.gk | ((uint64_t)st.gr << 16) | ((uint64_t)na << 32) |
+                     ((uint64_t)(st.op == GR_W) << 48) | ((uint64_t)st.space << 49);
+            }
+            lw.pk[lane] = pk;
+        }
         __syncwarp();
         unsigned long long pairs = 0;
         // the gaps of up to four checked masks in registers (most programs)
@@ -650,35 +692,48 @@ __global__ void __launch_bounds__(WARPS * 32)
             g[k] = k < iters ? lw.tg[k] : 0u;
             x[k] = k < iters ? lw.tgg[k] : 0u;
         }
-        // pair (i, j) = divmod(idx, S), stepped by 32 without a division
-        uint32_t i = lane / S, j = lane - i * S;
-        for (uint32_t idx = lane; idx < S * S; idx += 32u) {
-            if (j >= i) {
-                uint64_t same, cross;
-                pair_count(P, lw.nact, i, j, same, cross);
-                if (same || cross) {
-                    const uint32_t rg = range_mask(i, j);
-                    uint32_t cs = 0, cx = 0;
-                    if (iters <= 4) {
+        const uint64_t mi = lw.pk[lane];
+        const uint32_t gki = (uint32_t)(mi & 0xFFFFu), gri = (uint32_t)((mi >> 16) & 0xFFFFu);
+        const uint64_t ni = (mi >> 32) & 0xFFFFu, B = P.blocks;
+        const bool wi = (mi >> 48) & 1u;
+        const uint32_t spi = (uint32_t)((mi >> 49) & 1u);
+        for (uint32_t d = 0; d < S; ++d) {
+            const uint32_t j = lane + d;
+            if (lane >= S || j >= S) continue;
+            const uint64_t mj = lw.pk[j];
+            const bool wj = (mj >> 48) & 1u;
+            if (((mj >> 49) & 1u) != spi || (!wi && !wj)) continue;
+            const bool global = spi == GR_GLOBAL;
+            uint64_t same, cross;
+            if (d == 0) {
+                same = B * (ni * (ni - 1) / 2);
+                cross = global ? (B * (B - 1) / 2) * ni * ni : 0;
+            } else {
+                const uint32_t gkj = (uint32_t)(mj & 0xFFFFu), grj = (uint32_t)((mj >> 16) & 0xFFFFu);
+                const uint64_t nj = (mj >> 32) & 0xFFFFu;
+                // threads active at both: one side unguarded or both under one guard needs no count
+                const uint64_t nij = gki == 0 ? nj
+                                     : (gkj == 0 || (gki == gkj && gri == grj))
+                                           ? ni
+                                           : guard_both(P.threads, gki, gri, gkj, grj);
+                same = B * (ni * nj - nij);
+                cross = global ? B * (B - 1) * ni * nj : 0;
+            }
+            const uint32_t rg = range_mask(lane, j);
+            uint32_t cs = 0, cx = 0;
+            if (iters <= 4) {
 #pragma unroll
-                        for (uint32_t k = 0; k < 4; ++k) {
-                            cs += (k < iters && (g[k] & rg) == 0u) ? 1u : 0u;
-                            cx += (k < iters && (x[k] & rg) == 0u) ? 1u : 0u;
-                        }
-                    } else {
-                        for (uint32_t k = 0; k < iters; ++k) {
-                            cs += (lw.tg[k] & rg) == 0u ? 1u : 0u;
-                            cx += (lw.tgg[k] & rg) == 0u ? 1u : 0u;
-                        }
-                    }
-                    pairs += same * cs + cross * cx;
+                for (uint32_t k = 0; k < 4; ++k) {
+                    cs += (k < iters && (g[k] & rg) == 0u) ? 1u : 0u;
+                    cx += (k < iters && (x[k] & rg) == 0u) ? 1u : 0u;
+                }
+            } else {
+                for (uint32_t k = 0; k < iters; ++k) {
+                    cs += (lw.tg[k] & rg) == 0u ? 1u : 0u;
+                    cx += (lw.tgg[k] & rg) == 0u ? 1u : 0u;
                 }
             }
-            j += 32u;
-            while (j >= S) {
-                j -= S;
-                ++i;
-            }
+            pairs += same * cs + cross * cx;
         }
         pairs = warp_sum_u64(pairs);
         if (lane == 0) {
