@@ -428,8 +428,11 @@ bool injective_on_threads(const gr_stmt &st, uint32_t M, uint32_t T) {
 
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
                uint8_t *arena, uint32_t *table_bad, bool range_only) {
-    // zero everything but the permutation area, which is fully overwritten
-    memset(arena, 0, L.perm_off);
+    // zero everything but the permutation area, which is fully overwritten:
+    // the program records by their workers below, the rest here
+    const size_t progs_end = L.progs_off + (size_t)n * sizeof(DevProg);
+    memset(arena, 0, L.progs_off);
+    memset(arena + progs_end, 0, L.perm_off - progs_end);
     ArenaHeader *H = reinterpret_cast<ArenaHeader *>(arena);
     H->magic = kArenaMagic;
     H->n_progs = n;
@@ -441,7 +444,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     H->order_off = L.order_off;
     H->segbase_off = L.segbase_off;
     H->items_off = L.items_off;
-    H->n_items = L.n_items;
+    H->n_items = (uint32_t)L.n_items;
     H->perm_off = L.perm_off;
     H->n_segments = L.n_segments;
     H->scratch_segmask_off = L.segmask_off;
@@ -459,6 +462,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     for (uint32_t p = lo; p < hi; ++p) {
         const gr_program &P = progs[p];
         DevProg &D = dp[p];
+        memset(&D, 0, sizeof(DevProg));
         const uint32_t nsl = slots_of(P);
         // executed statement instances: identity without loops
         uint8_t st_of[GR_MAX_STMTS], ctr_of[GR_MAX_STMTS];
@@ -590,6 +594,9 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     uint32_t n_fast = 0;
     while (n_fast < n && dp[order[n_fast]].fast) ++n_fast;
     H->n_fast = n_fast;
+    bool simple = true;
+    for (uint32_t p = 0; p < n && simple; ++p) simple = !dp[p].general && dp[p].global_rows == 0;
+    H->flags = simple ? kArenaSimple : 0u;
     // expansion items, largest programs first: runs of up to kItemSegs
     // segments (kind 0); for a program whose blocks are alike the same-block
     // passes read block 0 only and only global statements have a cross-block
@@ -623,7 +630,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
         }
     }
     if (n_fast == 0) H->n_items_gen = (uint32_t)k;
-    H->n_items = k;
+    H->n_items = (uint32_t)k;
 }
 
 }  // namespace gr
@@ -654,7 +661,7 @@ uint32_t ceil_log2(uint64_t x) {
 // program's statement instances (sizes the general check's table) and the
 // kSkip* bits of the batch.
 struct Tuned {
-    uint32_t rel_shape = 0, gen_shape = 0, s_max = GR_MAX_STMTS, skip = 0;
+    uint32_t rel_shape = 0, gen_shape = 0, s_max = GR_MAX_STMTS, skip = 0, simple = 0;
 };
 
 struct DeviceBuf {
@@ -758,12 +765,13 @@ RelCfg rel_cfg(const Workspace &ws, uint32_t n, uint32_t shape) {
 
 // CTAs of the loop kernel: as many as the SMs hold at once, at most one warp
 // per program.
-uint32_t loop_grid(const Workspace &ws, uint32_t n) {
-    const size_t per = loop_smem_bytes() + 1024;
+uint32_t loop_grid(const Workspace &ws, uint32_t n, bool simple) {
+    const size_t per = loop_smem_bytes(simple) + 1024;
     const uint32_t by_smem = (uint32_t)std::max<size_t>(1, (size_t)ws.smem_per_sm / per);
-    const uint32_t by_threads = 2048u / kLoopThreads;
+    const uint32_t by_threads = 2048u / loop_threads(simple);
     const uint32_t ctas = std::min(by_smem, by_threads);
-    const uint32_t need = (n + kLoopThreads / 32 - 1) / (kLoopThreads / 32);
+    const uint32_t wpc = loop_threads(simple) / 32u;
+    const uint32_t need = (n + wpc - 1) / wpc;
     return std::max<uint32_t>(1u, std::min<uint32_t>(need, (uint32_t)ws.sms * ctas));
 }
 
@@ -774,8 +782,9 @@ LaunchCfg full_cfg(const Workspace &ws, uint32_t n, const Tuned &t) {
     if (!c.table_bytes) c = shape_cfg(ws, n, 3, t.s_max);
     c.rel = rel_cfg(ws, n, t.rel_shape);
     if (!c.rel.table_bytes) c.rel = rel_cfg(ws, n, 0);
-    c.loop_grid = loop_grid(ws, n);
+    c.loop_grid = loop_grid(ws, n, t.simple != 0);
     c.skip = t.skip;
+    c.simple = t.simple;
     return c;
 }
 
@@ -923,15 +932,17 @@ gr_status finish_sync(void *d_scratch, cudaStream_t st) {
 namespace gr {
 // Launch shape of the persistent repair for n packed programs on the current
 // device (used by gr_repair_packed_noalloc in noalloc.cu).
-LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, gr_status *status) {
+LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, bool simple, gr_status *status) {
     Workspace *ws;
     LaunchCfg c{};
     if ((*status = current_ws(&ws)) != GR_OK) return c;
     std::lock_guard<std::mutex> g(ws->mu);
     if ((*status = ensure_configured(*ws)) != GR_OK) return c;
-    c = packed_cfg(*ws, d_arena, n);
-    c.skip |= skip;
-    return c;
+    auto it = ws->arena_shape.find({d_arena, n});
+    Tuned t = it != ws->arena_shape.end() ? it->second : Tuned{};
+    t.skip |= skip;
+    t.simple = simple ? 1u : 0u;
+    return full_cfg(*ws, n, t);
 }
 
 // Owner-table budget of the wide lane's check CTAs (512 threads, two per SM)
@@ -1121,6 +1132,7 @@ gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts
     if (!(skip & kSkipGeneral)) GR_CUDA(launch_expand(d_arena, d_scratch, scratch_bytes, true, expand_grid(*ws), st));
     Tuned t;
     if ((s = tune_cfg(*ws, d_arena, n, d_scratch, scratch_bytes, st, h.s_max, skip, &t)) != GR_OK) return s;
+    t.simple = (h.flags & kArenaSimple) ? 1u : 0u;
     ws->arena_shape[{d_arena, n}] = t;
     // one repair with the picked shapes leaves d_out filled, as documented
     GR_CUDA(enqueue_repair(d_arena, n, opts_or_default(opts), d_scratch, scratch_bytes, d_out, full_cfg(*ws, n, t),
@@ -1276,8 +1288,10 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
             t.skip = 0;  // per chunk below
             it = ws->class_shape.emplace(cls, t).first;
         }
-        LaunchCfg cfg = full_cfg(*ws, n_c, it->second);
-        cfg.skip = skip;
+        Tuned tc = it->second;
+        tc.skip = skip;
+        tc.simple = (reinterpret_cast<const ArenaHeader *>(staging)->flags & kArenaSimple) ? 1u : 0u;
+        const LaunchCfg cfg = full_cfg(*ws, n_c, tc);
         // the queue counters (and, for the first chunk, the error word) are cleared first
         GR_CUDA(enqueue_repair(ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, sb, d_out + lo[c], cfg,
                                expand_grid(*ws), true, c == 0, st));

@@ -29,6 +29,8 @@ constexpr uint32_t kMinTableBytes = 25u * 2u * kChunkWords;  // one chunk for 25
 constexpr uint32_t kErrTableTooSmall = 1u;  // bits of the device error word (scratch control word 1)
 constexpr uint32_t kErrArgs = 4u;           // the launch's n or scratch size does not match the arena
 constexpr uint8_t kStmtInjective = 1u;      // DevStmt::flags: no two threads of a block share an address
+constexpr uint32_t kArenaSimple = 1u;       // ArenaHeader::flags: every program is straight-line (no loops or
+                                            // explicit slot places) on the shared array alone
 
 // One statement, with map coefficients reduced modulo its array's size.
 struct DevStmt {
@@ -82,7 +84,9 @@ struct ArenaHeader {
     uint64_t scratch_bytes;
     uint64_t scratch_segrange_off;
     uint64_t scratch_wide_off;  // wide lane: LoopState[n] | gr_witnesses[n] | WideCtl
-    uint64_t items_off, n_items;  // expansion work items (uint4: program, first, end segment)
+    uint64_t items_off;       // expansion work items (uint4: program, first, end segment)
+    uint32_t n_items;
+    uint32_t flags;           // kArena* bits
     uint64_t scratch_rel_off;     // each program's conflict relation (gr_witnesses rows)
     uint32_t n_fast;              // programs checked by the relation kernel (first in order)
     uint32_t n_items_gen;         // expansion items of the other programs (first in items)
@@ -124,6 +128,7 @@ struct LaunchCfg {
     RelCfg rel;
     uint32_t loop_grid;    // CTAs of the loop kernel
     uint32_t skip;         // kSkip* bits: parts of the batch known to be empty
+    uint32_t simple;       // 1: the loop kernel's small build (a batch the packer marked kArenaSimple)
 };
 constexpr uint32_t kSkipGeneral = 1u;  // no general program: no expansion, no k_check
 constexpr uint32_t kSkipFast = 2u;     // no program for the relation kernel
@@ -141,8 +146,9 @@ size_t mhs_smem_bytes();
 constexpr uint32_t kNumRelShapes = 6;
 extern const LaunchShape kRelShapes[kNumRelShapes];
 size_t rel_fixed_bytes();   // the relation kernel's shared memory besides its table
-size_t loop_smem_bytes();   // the loop kernel's shared memory per CTA
-constexpr uint32_t kLoopThreads = 128;  // the loop kernel's CTA: four warps, a program each
+size_t loop_smem_bytes(bool simple);  // the loop kernel's shared memory per CTA
+uint32_t loop_threads(bool simple);    // its threads per CTA (a warp per program)
+constexpr uint32_t kLoopThreads = 128;  // the general build's CTA: four warps
 
 // Host-side helpers (capi.cu).
 struct Layout {
@@ -177,8 +183,9 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
 bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst, bool range_only = false);
 // The launch of a repair of n packed programs at d_arena on the current
 // device: the shapes gr_tune_packed recorded for (d_arena, n), else the
-// defaults, plus the kSkip* bits `skip`.
-LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, gr_status *status);
+// defaults, plus the kSkip* bits `skip`; `simple`: the arena header's
+// kArenaSimple flag (the loop kernel's small build).
+LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, bool simple, gr_status *status);
 // Options: GR_EINVAL for an unknown strategy or values out of range; the
 // defaults filled in (NULL: grid enabled, 64 iterations, no deadline).
 gr_status validate_opts(const gr_options *o);
@@ -203,7 +210,7 @@ cudaError_t launch_relation(const void *d_arena, uint32_t n, const uint32_t *d_m
                             uint64_t scratch_bytes, gr_witnesses *d_out, RelCfg cfg, cudaStream_t st);
 // Algorithm 1 per program over the relations in the scratch.
 cudaError_t launch_loop(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
-                        uint64_t scratch_bytes, gr_repair_result *d_out, uint32_t grid, cudaStream_t st);
+                        uint64_t scratch_bytes, gr_repair_result *d_out, uint32_t grid, bool simple, cudaStream_t st);
 // The whole repair of a packed batch on the device: the general programs'
 // traces (when `expand`), the relations, the loop.  Clears the work-queue
 // counters first, and the device error word too when clear_error.

@@ -1788,7 +1788,7 @@ cudaError_t enqueue_relation(const void *d_arena, uint32_t n, void *d_scratch, u
 cudaError_t enqueue_loop(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
                          uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(static_cast<uint32_t *>(d_scratch) + 3, 0, 4, st);  // its queue counter
-    if (e == cudaSuccess) e = launch_loop(d_arena, n, opts, d_scratch, scratch_bytes, d_out, cfg.loop_grid, st);
+    if (e == cudaSuccess) e = launch_loop(d_arena, n, opts, d_scratch, scratch_bytes, d_out, cfg.loop_grid, cfg.simple != 0, st);
     return e;
 }
 
@@ -1796,7 +1796,7 @@ cudaError_t enqueue_repair(const void *d_arena, uint32_t n, const gr_options &op
                            uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
                            bool expand, bool clear_error, cudaStream_t st) {
     cudaError_t e = enqueue_relation(d_arena, n, d_scratch, scratch_bytes, cfg, expand_grid, expand, clear_error, st);
-    if (e == cudaSuccess) e = launch_loop(d_arena, n, opts, d_scratch, scratch_bytes, d_out, cfg.loop_grid, st);
+    if (e == cudaSuccess) e = launch_loop(d_arena, n, opts, d_scratch, scratch_bytes, d_out, cfg.loop_grid, cfg.simple != 0, st);
     return e;
 }
 

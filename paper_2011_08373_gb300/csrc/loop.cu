@@ -29,16 +29,26 @@
 
 namespace gr {
 
-constexpr uint32_t kLoopWarps = kLoopThreads / 32;  // programs in flight per CTA (one per warp)
-constexpr uint32_t kListCap = 704;   // >= GR_MAX_CLAUSES (656), a multiple of 32
+// Two builds of the kernel: the general one (four warps per CTA, clause
+// buffers for the largest clause sets) and, for batches of simple programs
+// (straight-line, shared array only: every clause an interval [i, j), at
+// most 25 * 24 / 2 + 1 of them, no sort, at most 25 row minima), one with
+// small buffers and twice the warps per CTA, so that more programs are in
+// flight per SM.
+constexpr uint32_t kListCap = 704;        // >= GR_MAX_CLAUSES (656), a multiple of 32
+constexpr uint32_t kSimpleListCap = 320;  // >= 301 interval clauses
+constexpr uint32_t kSimpleScratch = 64;   // >= 32 kept clauses (the register subsumption)
+constexpr uint32_t kSimpleWarps = 8;
 
-struct LoopWarp {
+template <uint32_t CAPC, uint32_t CAPA>
+struct LoopWarpT {
+    static constexpr uint32_t kCapC = CAPC, kCapA = CAPA;
     DevProg prog;
     uint32_t traj[GR_MAX_ITERS];
     uint32_t tg[GR_MAX_ITERS], tgg[GR_MAX_ITERS];  // gaps of each checked mask (all slots / grid slots)
-    uint32_t cl[kListCap];  // the clause set, sorted
-    uint32_t A[kListCap];   // scratch: candidate clauses, filtered clauses, kept high parts
-    uint32_t B[kListCap];   // scratch: sort buffer, size-ordered clauses, kept low patterns
+    uint32_t cl[CAPC];  // the clause set, sorted
+    uint32_t A[CAPA];   // scratch: candidate clauses, filtered clauses, kept high parts
+    uint32_t B[CAPA];   // scratch: sort buffer, size-ordered clauses, kept low patterns
     uint32_t nhi[32], nlo[32];
     uint32_t wc[32], wlo[32], lb[34];
     uint32_t w4[8][16];     // weight of each nibble of the high part
@@ -46,8 +56,16 @@ struct LoopWarp {
     unsigned long long pk[32];  // instance fields for the pair count: guard k, r, active threads, write, space
 };
 
-constexpr size_t kLoopSmem = (sizeof(LoopWarp) + 15) / 16 * 16;
-size_t loop_smem_bytes() { return kLoopSmem * kLoopWarps; }
+using LoopWarp = LoopWarpT<kListCap, kListCap>;
+using LoopWarpSimple = LoopWarpT<kSimpleListCap, kSimpleScratch>;
+constexpr uint32_t kLoopWarps = kLoopThreads / 32;  // programs in flight per CTA (one per warp)
+
+template <class LW>
+constexpr size_t warp_smem() { return (sizeof(LW) + 15) / 16 * 16; }
+size_t loop_smem_bytes(bool simple) {
+    return simple ? warp_smem<LoopWarpSimple>() * kSimpleWarps : warp_smem<LoopWarp>() * kLoopWarps;
+}
+uint32_t loop_threads(bool simple) { return simple ? kSimpleWarps * 32u : kLoopThreads; }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
@@ -137,7 +155,8 @@ __device__ uint32_t warp_unique(const uint32_t *src, uint32_t m, uint32_t *dst) 
 // witness (i, j) gives the slots whose barriers run in gaps i..j-1, a
 // cross-block witness the grid slots among them.  Lane i holds row i of both.
 // Returns the number of distinct clauses, sorted in lw.cl.
-__device__ uint32_t build_clause_set(LoopWarp &lw, uint32_t acc_i, uint32_t acc_x) {
+template <class LW>
+__device__ uint32_t build_clause_set(LW &lw, uint32_t acc_i, uint32_t acc_x) {
     const DevProg &P = lw.prog;
     const uint32_t lane = lane_id();
     uint32_t m = 0;
@@ -201,7 +220,8 @@ __device__ uint32_t build_clause_set(LoopWarp &lw, uint32_t acc_i, uint32_t acc_
 //      assignments that hit it — and the high slots are enumerated by size
 //      (Gosper's order), lanes taking contiguous ranges, stopping at the first
 //      size whose lightest member is heavier than the best key found.
-__device__ bool warp_solve(LoopWarp &lw, const uint32_t *cl, uint32_t n, uint32_t forced, uint32_t forbidden,
+template <class LW>
+__device__ bool warp_solve(LW &lw, const uint32_t *cl, uint32_t n, uint32_t forced, uint32_t forbidden,
                            uint32_t &mask_out, uint32_t &weight_out) {
     const DevProg &P = lw.prog;
     const uint32_t *w = P.weights;
@@ -470,7 +490,8 @@ __device__ bool warp_solve(LoopWarp &lw, const uint32_t *cl, uint32_t n, uint32_
 // the lower slot), then drop, from the highest slot down, every non-forced
 // slot whose removal leaves every clause hit.  Returns false when some
 // clause has no allowed slot (or a forced slot is forbidden).
-__device__ bool warp_greedy(LoopWarp &lw, uint32_t n, uint32_t forced, uint32_t forbidden, uint32_t &mask_out,
+template <class LW>
+__device__ bool warp_greedy(LW &lw, uint32_t n, uint32_t forced, uint32_t forbidden, uint32_t &mask_out,
                             uint32_t &weight_out) {
     const DevProg &P = lw.prog;
     const uint32_t *w = P.weights;
@@ -533,7 +554,8 @@ __device__ bool warp_greedy(LoopWarp &lw, uint32_t n, uint32_t forced, uint32_t 
 // i of its kind, and a mask hits all of them iff it hits this one: the
 // minimum-weight hitting sets of the whole clause set and of these (at most
 // 2 x 25) are the same.  Into lw.cl; returns how many.
-__device__ uint32_t build_row_minima(LoopWarp &lw, uint32_t acc_i, uint32_t acc_x) {
+template <class LW>
+__device__ uint32_t build_row_minima(LW &lw, uint32_t acc_i, uint32_t acc_x) {
     const DevProg &P = lw.prog;
     const uint32_t lane = lane_id();
     uint32_t ci = 0, cx = 0;
@@ -550,13 +572,13 @@ __device__ uint32_t build_row_minima(LoopWarp &lw, uint32_t acc_i, uint32_t acc_
 
 // ---- the loop ---------------------------------------------------------------
 
-template <uint32_t WARPS>
+template <uint32_t WARPS, class LW>
 __global__ void __launch_bounds__(WARPS * 32)
     k_loop(const uint8_t *__restrict__ arena, uint32_t n, gr_options opts, uint8_t *__restrict__ scratch,
            uint64_t scratch_bytes, gr_repair_result *__restrict__ out) {
     extern __shared__ uint4 loop_raw[];
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    LoopWarp &lw = *reinterpret_cast<LoopWarp *>(reinterpret_cast<uint8_t *>(loop_raw) + kLoopSmem * warp);
+    LW &lw = *reinterpret_cast<LW *>(reinterpret_cast<uint8_t *>(loop_raw) + warp_smem<LW>() * warp);
     const DevProg &P = lw.prog;
     const ArenaView V = view(arena);
     uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
@@ -580,6 +602,11 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         const uint32_t conf_i = rel[p].race_intra[lane], conf_x = rel[p].race_inter[lane];
         __syncwarp();
+        if (LW::kCapC < kListCap && (P.general || P.global_rows)) {
+            // the small build only takes batches the packer marked simple
+            if (lane == 0) atomicOr(&ctrl[1], kErrArgs);
+            continue;
+        }
         const uint32_t S = P.n_stmts, E = P.existing;
         const uint64_t t_start = globaltimer();
         uint32_t forced = P.mode == GR_MODE_REPAIR ? E : 0u;
@@ -670,9 +697,8 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         for (uint32_t i = lane; i < GR_MAX_CLAUSES; i += 32u) o.clauses[i] = i < n_cl ? lw.cl[i] : 0u;
         __syncwarp();
-        // thread pairs a pairwise checker examines, summed over the checks
-        // lane i takes row i: the pairs (i, i + d), d = 0, 1, .. in step over
-        // the warp; each instance's fields packed in one shared word
+        // thread pairs a pairwise checker examines, summed over the checks;
+        // each instance's fields packed in one shared word
         {
             uint64_t pk = 0;
             if (lane < S) {
@@ -684,7 +710,6 @@ __global__ void __launch_bounds__(WARPS * 32)
             lw.pk[lane] = pk;
         }
         __syncwarp();
-        unsigned long long pairs = 0;
         // the gaps of up to four checked masks in registers (most programs)
         uint32_t g[4], x[4];
 #pragma unroll
@@ -692,34 +717,27 @@ __global__ void __launch_bounds__(WARPS * 32)
             g[k] = k < iters ? lw.tg[k] : 0u;
             x[k] = k < iters ? lw.tgg[k] : 0u;
         }
-        const uint64_t mi = lw.pk[lane];
-        const uint32_t gki = (uint32_t)(mi & 0xFFFFu), gri = (uint32_t)((mi >> 16) & 0xFFFFu);
-        const uint64_t ni = (mi >> 32) & 0xFFFFu, B = P.blocks;
-        const bool wi = (mi >> 48) & 1u;
-        const uint32_t spi = (uint32_t)((mi >> 49) & 1u);
-        for (uint32_t d = 0; d < S; ++d) {
-            const uint32_t j = lane + d;
-            if (lane >= S || j >= S) continue;
-            const uint64_t mj = lw.pk[j];
-            const bool wj = (mj >> 48) & 1u;
+        // Pairs (i <= j) ordered by j, then i: pair idx = j (j + 1) / 2 + i, so
+        // the pairs of S instances are idx < S (S + 1) / 2, about ten per
+        // lane.  Per pair, thread counts without the block factors:
+        //   a1 += (n_i n_j - n_ij) c_s  (i < j),  n_i (n_i - 1) / 2 c_s  (i == j)
+        //   a2 += n_i n_j c_x  (i < j, global),  a3 += n_i^2 c_x  (i == j, global)
+        // with c_s / c_x the checks whose same-block / cross-block phase holds
+        // both; the block factors B, B (B - 1) and B (B - 1) / 2 at the end.
+        unsigned long long a1 = 0, a2 = 0, a3 = 0;
+        const uint32_t n_pairs = S * (S + 1u) / 2u;
+        for (uint32_t idx = lane; idx < n_pairs; idx += 32u) {
+            // j = floor((sqrt(8 idx + 1) - 1) / 2), corrected for rounding
+            uint32_t j = (uint32_t)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+            while (j * (j + 1u) / 2u > idx) --j;
+            while ((j + 1u) * (j + 2u) / 2u <= idx) ++j;
+            const uint32_t i = idx - j * (j + 1u) / 2u;
+            const uint64_t mi = lw.pk[i], mj = lw.pk[j];
+            const bool wi = (mi >> 48) & 1u, wj = (mj >> 48) & 1u;
+            const uint32_t spi = (uint32_t)((mi >> 49) & 1u);
             if (((mj >> 49) & 1u) != spi || (!wi && !wj)) continue;
-            const bool global = spi == GR_GLOBAL;
-            uint64_t same, cross;
-            if (d == 0) {
-                same = B * (ni * (ni - 1) / 2);
-                cross = global ? (B * (B - 1) / 2) * ni * ni : 0;
-            } else {
-                const uint32_t gkj = (uint32_t)(mj & 0xFFFFu), grj = (uint32_t)((mj >> 16) & 0xFFFFu);
-                const uint64_t nj = (mj >> 32) & 0xFFFFu;
-                // threads active at both: one side unguarded or both under one guard needs no count
-                const uint64_t nij = gki == 0 ? nj
-                                     : (gkj == 0 || (gki == gkj && gri == grj))
-                                           ? ni
-                                           : guard_both(P.threads, gki, gri, gkj, grj);
-                same = B * (ni * nj - nij);
-                cross = global ? B * (B - 1) * ni * nj : 0;
-            }
-            const uint32_t rg = range_mask(lane, j);
+            const uint32_t ni = (uint32_t)((mi >> 32) & 0xFFFFu), nj = (uint32_t)((mj >> 32) & 0xFFFFu);
+            const uint32_t rg = range_mask(i, j);
             uint32_t cs = 0, cx = 0;
             if (iters <= 4) {
 #pragma unroll
@@ -733,9 +751,27 @@ __global__ void __launch_bounds__(WARPS * 32)
                     cx += (lw.tgg[k] & rg) == 0u ? 1u : 0u;
                 }
             }
-            pairs += same * cs + cross * cx;
+            const bool global = spi == GR_GLOBAL;
+            if (i == j) {
+                a1 += (unsigned long long)(ni * (ni - 1u) / 2u) * cs;  // n_i <= 1,024: 32-bit products
+                if (global) a3 += (unsigned long long)(ni * ni) * cx;
+            } else {
+                const uint32_t gki = (uint32_t)(mi & 0xFFFFu), gri = (uint32_t)((mi >> 16) & 0xFFFFu);
+                const uint32_t gkj = (uint32_t)(mj & 0xFFFFu), grj = (uint32_t)((mj >> 16) & 0xFFFFu);
+                // threads active at both: one side unguarded or both under one guard needs no count
+                const uint32_t nij = gki == 0 ? nj
+                                     : (gkj == 0 || (gki == gkj && gri == grj))
+                                           ? ni
+                                           : guard_both(P.threads, gki, gri, gkj, grj);
+                a1 += (unsigned long long)(ni * nj - nij) * cs;
+                if (global) a2 += (unsigned long long)(ni * nj) * cx;
+            }
         }
-        pairs = warp_sum_u64(pairs);
+        a1 = warp_sum_u64(a1);
+        a2 = warp_sum_u64(a2);
+        a3 = warp_sum_u64(a3);
+        const unsigned long long Bq = P.blocks;
+        const unsigned long long pairs = Bq * a1 + Bq * (Bq - 1ull) * a2 + (Bq * (Bq - 1ull) / 2ull) * a3;
         if (lane == 0) {
             const bool ok = status == GR_REPAIRED;
             const uint32_t m = ok ? mask : 0u;
@@ -760,14 +796,23 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 cudaError_t configure_loop(uint32_t max_dynamic_smem) {
     (void)max_dynamic_smem;
-    return cudaFuncSetAttribute((const void *)k_loop<kLoopWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)loop_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_loop<kLoopWarps, LoopWarp>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem_bytes(false));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void *)k_loop<kSimpleWarps, LoopWarpSimple>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem_bytes(true));
 }
 
 cudaError_t launch_loop(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
-                        uint64_t scratch_bytes, gr_repair_result *d_out, uint32_t grid, cudaStream_t st) {
-    k_loop<kLoopWarps><<<grid, kLoopWarps * 32, loop_smem_bytes(), st>>>(
-        static_cast<const uint8_t *>(d_arena), n, opts, static_cast<uint8_t *>(d_scratch), scratch_bytes, d_out);
+                        uint64_t scratch_bytes, gr_repair_result *d_out, uint32_t grid, bool simple, cudaStream_t st) {
+    const uint8_t *a = static_cast<const uint8_t *>(d_arena);
+    uint8_t *sc = static_cast<uint8_t *>(d_scratch);
+    if (simple)
+        k_loop<kSimpleWarps, LoopWarpSimple>
+            <<<grid, kSimpleWarps * 32, loop_smem_bytes(true), st>>>(a, n, opts, sc, scratch_bytes, d_out);
+    else
+        k_loop<kLoopWarps, LoopWarp><<<grid, kLoopWarps * 32, loop_smem_bytes(false), st>>>(a, n, opts, sc,
+                                                                                          scratch_bytes, d_out);
     return cudaGetLastError();
 }
 

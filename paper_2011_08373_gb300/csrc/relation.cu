@@ -229,15 +229,23 @@ __device__ __forceinline__ void rel_scan(RelProg &sm, uint16_t *tab, uint32_t *c
         for (uint32_t t = present; t; t &= t - 1u) {
             const uint32_t qi = __ffs(t) - 1u;
             uint16_t *ei = tab + (size_t)qi * pitch + c;
+            // the partners of row qi at this column (itself and the higher rows
+            // present) whose pair is a candidate not found yet; none: skip
+            const uint32_t open =
+                sm.cand[qi] & ~*(volatile uint32_t *)&sm.conf[qi] & (t & ~((1u << qi) - 1u));
+            if (!open) {
+                *ei = kEmpty;
+                continue;
+            }
             const uint32_t oi = *ei;
             *ei = kEmpty;  // no later row of this column reads it again
             uint32_t bits = oi == kMulti ? (1u << qi) : 0u;
-            for (uint32_t t2 = t & (t - 1u); t2; t2 &= t2 - 1u) {
+            for (uint32_t t2 = open & ~(1u << qi); t2; t2 &= t2 - 1u) {
                 const uint32_t qj = __ffs(t2) - 1u;
                 const uint32_t oj = tab[(size_t)qj * pitch + c];
                 bits |= (oi != oj || oi == kMulti) ? (1u << qj) : 0u;
             }
-            bits &= sm.cand[qi];
+            bits &= open;
             if (bits) or_row(sm.conf, qi, bits);
         }
     }

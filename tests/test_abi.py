@@ -240,7 +240,7 @@ def test_expansion_items_cover_every_segment_once(lib):
     progs += [random_program(50 + s, s_min=2, s_max=6, b_min=2, b_max=5, c_max=3, shared_c=True) for s in range(20)]
     arena, _ = gb.pack(progs)
     h = arena[:128].view(np.uint64)
-    segbase_off, items_off, n_items = int(h[4]), int(h[12]), int(h[13])
+    segbase_off, items_off, n_items = int(h[4]), int(h[12]), int(h[13]) & 0xFFFFFFFF
     n = len(progs)
     segbase = arena[segbase_off:segbase_off + 8 * (n + 1)].view(np.uint64)
     items = arena[items_off:items_off + 16 * n_items].view(np.uint32).reshape(-1, 4)
