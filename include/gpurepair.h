@@ -234,6 +234,13 @@ gr_status gr_repair(const gr_program *prog, gr_launch launch, int32_t mode,
 gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode,
                           const gr_options *opts, gr_repair_result *out);
 
+/* gr_repair_plain, also writing to *loop_ms (when not NULL) the time, by CUDA
+ * events on the call's stream, from the first launch of the loop to its last:
+ * the per-iteration launches and the host's reads of the done flag, without
+ * validation, packing or the upload.  On an error *loop_ms is unchanged. */
+gr_status gr_repair_plain_timed(const gr_program *prog, gr_launch launch, int32_t mode,
+                                const gr_options *opts, gr_repair_result *out, float *loop_ms);
+
 /* Minimum-weight hitting set (Section 2.3 definitions, Section 2.4 weighted
  * MaxSAT form) on the GPU: the least (weight, mask) over masks x of n_vars
  * (1..32) bits with forced <= x, x & forbidden == 0, x & pos[i] != 0 for

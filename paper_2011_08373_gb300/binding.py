@@ -83,7 +83,8 @@ EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair"
            "gr_repair_packed", "gr_check_packed", "gr_expand_packed", "gr_repair_expanded",
            "gr_repair_packed_noalloc", "gr_server_create", "gr_server_submit", "gr_server_poll",
            "gr_server_drain", "gr_server_stats", "gr_server_destroy", "gr_tune_packed",
-           "gr_repair_packed_wide", "gr_check_expanded", "gr_relation_packed", "gr_loop_packed"]
+           "gr_repair_packed_wide", "gr_check_expanded", "gr_relation_packed", "gr_loop_packed",
+           "gr_repair_plain_timed"]
 
 
 def lib():
@@ -103,6 +104,7 @@ def lib():
             L.gr_repair.argtypes = [P(gr_program), gr_launch, C.c_int32, P(gr_options),
                                     P(gr_repair_result)]
             L.gr_repair_plain.argtypes = L.gr_repair.argtypes
+            L.gr_repair_plain_timed.argtypes = L.gr_repair.argtypes + [P(C.c_float)]
             L.gr_solve.argtypes = [C.c_uint32, P(C.c_uint32), P(C.c_uint32), C.c_uint32, P(C.c_uint32),
                                    C.c_uint32, C.c_uint32, C.c_uint32, P(C.c_uint32), P(C.c_uint32)]
             L.gr_repair_batch.argtypes = [P(gr_program), P(gr_launch), P(C.c_int32), C.c_uint32,
@@ -384,6 +386,18 @@ def repair_plain(p, mode: Optional[int] = None, grid_enabled: bool = True,
     _check(lib().gr_repair_plain(C.byref(c.s), c.launch, c.mode if mode is None else mode,
                                  C.byref(o), C.byref(r)))
     return result_dict(np.frombuffer(bytes(r), dtype=RESULT_DTYPE)[0])
+
+
+def repair_plain_timed(p, mode: Optional[int] = None, grid_enabled: bool = True,
+                       max_iters: int = 64, strategy: int = 0, deadline_us: int = 0):
+    """repair_plain, and the CUDA-event time (ms) of its launch loop alone."""
+    c = CProgram(p)
+    r = gr_repair_result()
+    o = _options(grid_enabled, max_iters, strategy, deadline_us)
+    ms = C.c_float(0.0)
+    _check(lib().gr_repair_plain_timed(C.byref(c.s), c.launch, c.mode if mode is None else mode,
+                                       C.byref(o), C.byref(r), C.byref(ms)))
+    return result_dict(np.frombuffer(bytes(r), dtype=RESULT_DTYPE)[0]), float(ms.value)
 
 
 def solve(n_vars: int, weights, pos, neg=(), forced: int = 0, forbidden: int = 0):

@@ -1347,6 +1347,11 @@ gr_status gr_repair(const gr_program *prog, gr_launch launch, int32_t mode, cons
 
 gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode, const gr_options *opts,
                           gr_repair_result *out) {
+    return gr_repair_plain_timed(prog, launch, mode, opts, out, nullptr);
+}
+
+gr_status gr_repair_plain_timed(const gr_program *prog, gr_launch launch, int32_t mode, const gr_options *opts,
+                                gr_repair_result *out, float *loop_ms) {
     if (!out) return fail(GR_EINVAL, "out is NULL");
     gr_status s = validate_all(prog, &launch, 1, false);
     if (s != GR_OK) return s;
@@ -1366,6 +1371,22 @@ gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode
     gr_witnesses *d_wit = reinterpret_cast<gr_witnesses *>(static_cast<uint8_t *>(ws->aux.p) + state_bytes);
     gr_repair_result *d_out =
         reinterpret_cast<gr_repair_result *>(static_cast<uint8_t *>(ws->aux.p) + state_bytes + wit_bytes);
+    // events bracket the launch loop alone: expansion, the per-iteration
+    // launches and the host's read of the done flag, not validation,
+    // packing or the upload
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } events;
+    cudaEvent_t *ev = events.e;
+    if (loop_ms) {
+        GR_CUDA(cudaEventCreate(&ev[0]));
+        GR_CUDA(cudaEventCreate(&ev[1]));
+        GR_CUDA(cudaEventRecord(ev[0], st));
+    }
     GR_CUDA(cudaMemsetAsync(ws->scratch.p, 0, 256, st));
     GR_CUDA(launch_expand(ws->arena.p, ws->scratch.p, L.scratch_bytes, false, expand_grid(*ws), st));
     const gr_options o = opts_or_default(opts);
@@ -1383,6 +1404,11 @@ gr_status gr_repair_plain(const gr_program *prog, gr_launch launch, int32_t mode
     if (L.n_segments == 0) return fail(GR_ECUDA, "empty layout");
     // a program that ended in the initial solve still needs its result written
     GR_CUDA(launch_plain_solve(ws->arena.p, 0, d_state, d_wit, d_out, st));
+    if (loop_ms) {
+        GR_CUDA(cudaEventRecord(ev[1], st));
+        GR_CUDA(cudaEventSynchronize(ev[1]));
+        GR_CUDA(cudaEventElapsedTime(loop_ms, ev[0], ev[1]));
+    }
     GR_CUDA(cudaMemcpy(out, d_out, sizeof(gr_repair_result), cudaMemcpyDeviceToHost));
     return GR_OK;
 }

@@ -8,7 +8,7 @@
 // runs one program ahead of the others (two program buffers), fetching and
 // setting up program k+1 and writing out program k-1 while warps 1.. (the
 // workers) check program k, so that the setup's loads and the output overlap
-// the table passes.  Per program:
+// the table pass.  Per program:
 //   setup   — (control) the candidate pairs: under a mask, the instance pairs
 //             (i <= j) with a write and no enabled barrier between them (one
 //             phase, Section 2.2); for the repair loop, every pair with a
@@ -16,25 +16,26 @@
 //             conflict relation.  Instances with the same map and guard touch
 //             the same words from the same threads and share one table row.
 //   install — (workers) every access computes its word address from the map
-//             (affine or strided arithmetic, or one permutation-table load)
-//             and writes its thread into its row's owner entry at that word;
-//             two threads of a row on one word leave MULTI (a compare-and-
-//             swap, only for rows whose map is not injective on the block's
-//             threads).  A bit per row and column marks the rows holding an
-//             entry there.
-//   scan    — (workers) each thread takes whole columns: two rows holding an
-//             entry at a column conflict unless both entries name the same
-//             single thread (an entry of another thread, or MULTI, is a
-//             second thread on the word: the race definition of Section 1
-//             made concrete — two distinct threads, one word, at least one
-//             write, no barrier between them).  The scan puts every entry it
-//             read back to empty, so the table is clean for the next program
-//             without a clear of the whole array.
+//             (affine or strided arithmetic, or one permutation-table load),
+//             writes its thread into its row's owner entry at that word (two
+//             threads of a row on one word leave MULTI: a compare-and-swap,
+//             only for rows whose map is not injective on the block's
+//             threads), then marks its row in the word's column mask with an
+//             acquire-release atomic that returns the rows already there, and
+//             compares its thread with their entries.  Two rows conflict at a
+//             word unless both hold the same single thread there (another
+//             thread, or MULTI, is a second thread on the word: the race
+//             definition of Section 1 made concrete — two distinct threads,
+//             one word, at least one write, no barrier between them).  Of the
+//             accesses of two rows to a word, the one whose atomic comes last
+//             sees the other row's final entry, so every conflicting pair is
+//             found; a row whose pairs are all decided stops installing.
+//   reset   — (workers) the rows and column masks used go back to empty.
 // Install works in units of one table row and 32 consecutive threads, a warp
 // per unit, so that a unit's map, guard and row are the same for the whole
-// warp: the per-unit arithmetic (a division or two) is done once and each
-// access costs a multiply and a reduction.  The table covers the array in
-// windows when it does not fit.
+// warp: the per-unit arithmetic is done once and each access costs a
+// multiply and a reduction.  The table covers the array in windows when it
+// does not fit.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -49,8 +50,8 @@ constexpr uint32_t kRelAllOnes = 0xFFFFFFFFu;
 // other).
 struct RelProg {
     DevProg prog;
-    uint32_t cand[32];      // table row q: partner rows (bit j, j >= q) to decide
-    uint32_t conf[32];      // table row q: partner rows found to conflict
+    uint32_t cand[32];      // table row q: candidate partner rows (bit j, j >= q)
+    uint32_t open[32];      // table row q: candidate partners in either direction not found yet
     uint32_t pend[32];      // instance i: candidate partners (bit j, j >= i)
     uint32_t rep_conf[32];  // the conflicts by pattern representative
     // table row q's access map (its representative's statement, block 0):
@@ -85,14 +86,33 @@ __device__ __forceinline__ uint32_t mod_by(uint32_t x, uint32_t M, uint32_t magi
     return r >= M ? r - M : r;
 }
 
+// *p &= v, returning the old value, with acquire-release order at CTA scope:
+// the caller's earlier shared-memory writes are visible to any thread whose
+// atomic on *p comes later, and its later reads see every write made before
+// the atomics that precede its own.
+__device__ __forceinline__ uint32_t and_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("atom.acq_rel.cta.shared::cta.and.b32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+    return old;
+}
+
 // Per-program setup by warp 0: the program record, candidate pairs, table
 // rows and their maps, window size.
 __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_t table_bytes) {
     const uint32_t lane = threadIdx.x & 31u;
     {
+        // every load in flight before the first store
+        constexpr uint32_t kN16 = sizeof(DevProg) / 16, kPer = (kN16 + 31u) / 32u;
         const uint4 *src = reinterpret_cast<const uint4 *>(gp);
         uint4 *d4 = reinterpret_cast<uint4 *>(&sm.prog);
-        for (uint32_t i = lane; i < sizeof(DevProg) / 16; i += 32u) d4[i] = src[i];
+        uint4 v[kPer];
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k)
+            if (lane + 32u * k < kN16) v[k] = src[lane + 32u * k];
+#pragma unroll
+        for (uint32_t k = 0; k < kPer; ++k)
+            if (lane + 32u * k < kN16) d4[lane + 32u * k] = v[k];
     }
     __syncwarp();
     const DevProg &P = sm.prog;
@@ -104,24 +124,39 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
         pend = range_mask(lane, S) & phase_of(lane, gaps, S) & (w ? kRelAllOnes : P.write_mask);
     }
     sm.pend[lane] = pend;
-    sm.rep_conf[lane] = 0;  // pattern pairs pending (lower representative -> higher)
-    __syncwarp();
-    for (uint32_t t = pend; t; t &= t - 1u) {
-        const uint32_t ri = P.rep[lane], rj = P.rep[__ffs(t) - 1u];
-        atomicOr(&sm.rep_conf[min(ri, rj)], 1u << max(ri, rj));
+    // pattern pairs pending (lower representative -> higher); when every
+    // instance is its own representative they are the pending pairs
+    uint32_t rp = pend;
+    if (!__all_sync(0xFFFFFFFFu, P.rep[lane] == lane)) {
+        sm.rep_conf[lane] = 0;
+        __syncwarp();
+        for (uint32_t t = pend; t; t &= t - 1u) {
+            const uint32_t ri = P.rep[lane], rj = P.rep[__ffs(t) - 1u];
+            atomicOr(&sm.rep_conf[min(ri, rj)], 1u << max(ri, rj));
+        }
+        __syncwarp();
+        rp = sm.rep_conf[lane];
     }
-    __syncwarp();
-    const uint32_t rp = sm.rep_conf[lane];
     uint32_t involved = rp | (rp ? (1u << lane) : 0u);
     involved = __reduce_or_sync(0xFFFFFFFFu, involved);
     const bool keep = (involved >> lane) & 1u;
     const uint32_t row = __popc(involved & ((1u << lane) - 1u));
+    const uint32_t R = __popc(involved);
+    // open pairs in both directions: the representative's candidates plus the
+    // representatives that have it as a candidate (the transpose, a ballot
+    // per representative), all in statement bits
+    uint32_t sym = rp;
+    for (uint32_t t = involved; t; t &= t - 1u) {
+        const uint32_t l = __ffs(t) - 1u;
+        const uint32_t col = __ballot_sync(0xFFFFFFFFu, (rp >> l) & 1u);
+        if (lane == l) sym |= col;
+    }
     // rows in increasing representative order, so that a representative mask
     // compresses to a row mask by bit extraction
     if (keep) {
         const DevStmt &st = P.stmts[lane];
         sm.cand[row] = pext32(rp, involved);
-        sm.conf[row] = 0;
+        sm.open[row] = pext32(sym, involved);
         sm.row_am[row] = st.am;
         sm.row_bm[row] = st.bm;
         sm.row_po[row] = st.kind == GR_PERM ? st.perm_off : kRelAllOnes;
@@ -129,9 +164,9 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
         sm.row_gr[row] = st.gr;
         sm.row_gmag[row] = st.gk ? 0xFFFFFFFFu / st.gk : 0u;
     }
-    const uint32_t inj = __ballot_sync(0xFFFFFFFFu, keep && (P.stmts[lane].flags & kStmtInjective));
+    const uint32_t inj =
+        __reduce_or_sync(0xFFFFFFFFu, keep && (P.stmts[lane].flags & kStmtInjective) ? 1u << row : 0u);
     if (lane == 0) {
-        const uint32_t R = __popc(involved);
         const uint32_t M = P.m_shared;
         // R rows of W + 2 u16 entries (the extra word shifts each row by one
         // bank) and W u32 column masks
@@ -149,21 +184,22 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
         sm.W = W;
         sm.pitch = W + 2u;
         sm.n_win = n_win;
-        sm.inj_rows = pext32(inj, involved);
+        sm.inj_rows = inj;
         sm.bad = (R && W == 0) ? 1u : 0u;
         sm.mask = mask;
     }
 }
 
-// Install the accesses of the words [lo, lo + W) into the table: unit u (one
-// per worker warp at a time) covers table row q = u / cpr, threads
+// Install and check the accesses of the words [lo, lo + W): unit u (one per
+// worker warp at a time) covers table row q = u / cpr, threads
 // 32 c .. 32 c + 31 with c = u mod cpr (cpr = chunks of 32 threads per row);
 // lane l takes thread 32 c + l.  (q, c) steps from unit to unit without a
 // division, and every reduction is a reciprocal multiply.  When the array
 // takes several windows, an affine unit whose 32 words (a run of 31 am + 1
-// positions, cyclically) miss the window is skipped whole.
+// positions, cyclically) miss the window is skipped whole.  A unit of a row
+// with no open pair is skipped too: no other row needs its entries.
 template <uint32_t NT>
-__device__ __forceinline__ void rel_install(const RelProg &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
+__device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
                                             uint32_t *colrows, uint32_t lo) {
     constexpr uint32_t NWK = NT / 32 - 1;  // worker warps
     const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - 1u;
@@ -173,15 +209,16 @@ __device__ __forceinline__ void rel_install(const RelProg &sm, const uint16_t *_
     const uint32_t dq = NWK / cpr, dc = NWK - dq * cpr;
     uint32_t q = wk / cpr, c = wk - q * cpr;
     for (uint32_t u = wk; u < n_units; u += NWK) {  // uniform over the warp
-        const uint32_t tb = c << 5, t = tb + lane;
-        const uint32_t gk = sm.row_gk[q], am = sm.row_am[q], bm = sm.row_bm[q], po = sm.row_po[q];
-        const uint32_t qq = q;
+        const uint32_t tb = c << 5, t = tb + lane, qq = q;
         c += dc;
         q += dq;
         if (c >= cpr) {
             c -= cpr;
             ++q;
         }
+        const uint32_t openq = *(volatile uint32_t *)&sm.open[qq];
+        if (!openq) continue;  // every pair of this row is decided
+        const uint32_t gk = sm.row_gk[qq], am = sm.row_am[qq], bm = sm.row_bm[qq], po = sm.row_po[qq];
         if (windows && po == kRelAllOnes && am * 31u + 1u < M) {
             // am * tb + bm < 2^27: the unit's first word and the run to its last
             const uint32_t start = mod_by(am * tb + bm, M, magic);
@@ -202,53 +239,48 @@ __device__ __forceinline__ void rel_install(const RelProg &sm, const uint16_t *_
             // am, bm < M <= 2^16, t < 2^10: am t + bm < 2^27
             a = mod_by(am * t + bm, M, magic);
         }
-        if (!on || a - lo >= W) continue;
-        const uint32_t col = swizzle(a - lo);
-        uint16_t *e = tab + (size_t)qq * pitch + col;
-        if ((inj >> qq) & 1u) {
-            *e = (uint16_t)t;
-        } else if (atomicCAS(e, kEmpty, (uint16_t)t) != kEmpty) {
-            *e = kMulti;  // a second thread of this row on the word
+        const uint32_t qbit = 1u << qq;
+        uint32_t found = 0;
+        if (on && a - lo < W) {
+            const uint32_t col = swizzle(a - lo);
+            uint16_t *e = tab + (size_t)qq * pitch + col;
+            bool multi = false;  // a second thread of this row on the word
+            if ((inj >> qq) & 1u) {
+                *e = (uint16_t)t;
+            } else if (atomicCAS(e, kEmpty, (uint16_t)t) != kEmpty) {
+                *e = kMulti;
+                multi = true;
+            }
+            // the rows present before this access (their bits are clear)
+            uint32_t part = ~and_acq_rel(&colrows[col], ~qbit) & openq & ~qbit;
+            if (multi) {
+                // two threads of this row here: the self pair, and a thread
+                // other than each partner's
+                found = (openq & qbit) | part;
+            } else {
+                for (; part; part &= part - 1u) {
+                    const uint32_t j = __ffs(part) - 1u;
+                    if (tab[(size_t)j * pitch + col] != (uint16_t)t) found |= 1u << j;  // another thread or MULTI
+                }
+            }
         }
-        atomicAnd(&colrows[col], ~(1u << qq));
+        found = __reduce_or_sync(0xFFFFFFFFu, found);
+        if (found) {  // uniform: close the pairs in both directions
+            if (lane == 0) atomicAnd(&sm.open[qq], ~found);
+            if (((found & ~qbit) >> lane) & 1u) atomicAnd(&sm.open[lane], ~qbit);
+        }
     }
 }
 
-// Scan the window's columns (worker threads): two rows holding an entry at a
-// column conflict unless both entries are the same single thread; a row's
-// MULTI entry is its own race.  Each pair is compared once, from its lower
-// row (the candidates of a row are its pairs with higher rows).  Every
-// entry read, and the column mask, go back to empty.
+// The rows and column masks of the window back to empty (all ones): R rows
+// of `pitch` u16 entries and W u32 masks from the table's start, in 16-byte
+// stores (the table is 16-byte aligned and sized in whole 256-byte units).
 template <uint32_t NT>
-__device__ __forceinline__ void rel_scan(RelProg &sm, uint16_t *tab, uint32_t *colrows) {
-    const uint32_t W = sm.W, pitch = sm.pitch;
-    for (uint32_t c = threadIdx.x - 32u; c < W; c += NT - 32u) {
-        const uint32_t present = ~colrows[c];
-        if (!present) continue;
-        colrows[c] = kRelAllOnes;
-        for (uint32_t t = present; t; t &= t - 1u) {
-            const uint32_t qi = __ffs(t) - 1u;
-            uint16_t *ei = tab + (size_t)qi * pitch + c;
-            // the partners of row qi at this column (itself and the higher rows
-            // present) whose pair is a candidate not found yet; none: skip
-            const uint32_t open =
-                sm.cand[qi] & ~*(volatile uint32_t *)&sm.conf[qi] & (t & ~((1u << qi) - 1u));
-            if (!open) {
-                *ei = kEmpty;
-                continue;
-            }
-            const uint32_t oi = *ei;
-            *ei = kEmpty;  // no later row of this column reads it again
-            uint32_t bits = oi == kMulti ? (1u << qi) : 0u;
-            for (uint32_t t2 = open & ~(1u << qi); t2; t2 &= t2 - 1u) {
-                const uint32_t qj = __ffs(t2) - 1u;
-                const uint32_t oj = tab[(size_t)qj * pitch + c];
-                bits |= (oi != oj || oi == kMulti) ? (1u << qj) : 0u;
-            }
-            bits &= open;
-            if (bits) or_row(sm.conf, qi, bits);
-        }
-    }
+__device__ __forceinline__ void rel_reset(const RelProg &sm, uint16_t *tab) {
+    const uint32_t n16 = (sm.n_rows * sm.pitch * 2u + sm.W * 4u + 15u) >> 4;
+    uint4 *t4 = reinterpret_cast<uint4 *>(tab);
+    for (uint32_t i = threadIdx.x - 32u; i < n16; i += NT - 32u)
+        t4[i] = make_uint4(kRelAllOnes, kRelAllOnes, kRelAllOnes, kRelAllOnes);
 }
 
 // The program's witness rows (race_intra; one array per block, so no
@@ -259,14 +291,22 @@ __device__ void rel_output(RelProg &sm, gr_witnesses *dst, bool with_mask) {
     const DevProg &P = sm.prog;
     const uint32_t involved = sm.involved, p = sm.p;
     uint32_t rc = 0;
-    if ((involved >> lane) & 1u) rc = pdep32(sm.conf[__popc(involved & ((1u << lane) - 1u))], involved);
-    sm.rep_conf[lane] = rc;
-    __syncwarp();
-    uint32_t rows = 0;
-    for (uint32_t t = sm.pend[lane]; t; t &= t - 1u) {
-        const uint32_t j = __ffs(t) - 1u;
-        const uint32_t ri = P.rep[lane], rj = P.rep[j];
-        if ((sm.rep_conf[min(ri, rj)] >> max(ri, rj)) & 1u) rows |= 1u << j;
+    if ((involved >> lane) & 1u) {
+        const uint32_t row = __popc(involved & ((1u << lane) - 1u));
+        rc = pdep32(sm.cand[row] & ~sm.open[row], involved);
+    }
+    uint32_t rows;
+    if (__all_sync(0xFFFFFFFFu, P.rep[lane] == lane)) {
+        rows = sm.pend[lane] & rc;  // every instance its own representative
+    } else {
+        sm.rep_conf[lane] = rc;
+        __syncwarp();
+        rows = 0;
+        for (uint32_t t = sm.pend[lane]; t; t &= t - 1u) {
+            const uint32_t j = __ffs(t) - 1u;
+            const uint32_t ri = P.rep[lane], rj = P.rep[j];
+            if ((sm.rep_conf[min(ri, rj)] >> max(ri, rj)) & 1u) rows |= 1u << j;
+        }
     }
     gr_witnesses &wo = dst[p];
     wo.race_intra[lane] = rows;
@@ -296,14 +336,35 @@ __device__ void rel_output(RelProg &sm, gr_witnesses *dst, bool with_mask) {
     __syncwarp();
 }
 
+// The control warp's place in the work queue, kept two programs ahead so
+// that neither the queue's atomic nor the order table's load is waited on:
+// `p_next` is the program of the next fetch (its order entry was loaded a
+// fetch ago), `item_next` the queue item after it (lane 0's atomic result,
+// read a fetch later).
+struct RelQueue {
+    uint32_t p_next, item_next;
+};
+
+__device__ __forceinline__ uint32_t rel_grab(uint32_t *ctrl) {
+    return (threadIdx.x & 31u) == 0 ? atomicAdd(&ctrl[2], 1u) : 0u;
+}
+
+__device__ __forceinline__ RelQueue rel_queue_start(const ArenaView &V, uint32_t *ctrl, uint32_t n_fast) {
+    RelQueue Q;
+    const uint32_t item = __shfl_sync(0xFFFFFFFFu, rel_grab(ctrl), 0);
+    Q.p_next = item < n_fast ? V.order[item] : kRelAllOnes;
+    Q.item_next = rel_grab(ctrl);
+    return Q;
+}
+
 // The control warp: the next program from the queue into `b`, set up.
-__device__ __forceinline__ void rel_fetch(RelProg &b, const ArenaView &V, uint32_t *ctrl, uint32_t n_fast,
-                                          const uint32_t *masks, uint32_t table_bytes) {
+__device__ __forceinline__ void rel_fetch(RelProg &b, RelQueue &Q, const ArenaView &V, uint32_t *ctrl,
+                                          uint32_t n_fast, const uint32_t *masks, uint32_t table_bytes) {
     const uint32_t lane = threadIdx.x & 31u;
-    uint32_t item = 0;
-    if (lane == 0) item = atomicAdd(&ctrl[2], 1u);
-    item = __shfl_sync(0xFFFFFFFFu, item, 0);
-    const uint32_t p = item < n_fast ? V.order[item] : kRelAllOnes;
+    const uint32_t p = Q.p_next;
+    const uint32_t item = __shfl_sync(0xFFFFFFFFu, Q.item_next, 0);
+    Q.p_next = item < n_fast ? V.order[item] : kRelAllOnes;
+    if (item < n_fast) Q.item_next = rel_grab(ctrl);  // once past the end, no further atomics
     if (p != kRelAllOnes) rel_setup(b, &V.progs[p], masks ? masks[p] : 0u, table_bytes);
     __syncwarp();
     if (lane == 0) b.p = p;
@@ -331,8 +392,10 @@ __global__ void __launch_bounds__(NT, MINB)
     // every table entry is empty (all ones) between programs
     for (uint32_t i = threadIdx.x; i < table_bytes / 16u; i += NT)
         reinterpret_cast<uint4 *>(tab)[i] = make_uint4(kRelAllOnes, kRelAllOnes, kRelAllOnes, kRelAllOnes);
+    RelQueue Q{kRelAllOnes, 0u};
     if (warp == 0) {
-        rel_fetch(sm.buf[0], V, ctrl, n_fast, masks, table_bytes);
+        Q = rel_queue_start(V, ctrl, n_fast);
+        rel_fetch(sm.buf[0], Q, V, ctrl, n_fast, masks, table_bytes);
         if ((threadIdx.x & 31u) == 0) sm.buf[1].p = kRelAllOnes;
     }
     __syncthreads();
@@ -344,7 +407,7 @@ __global__ void __launch_bounds__(NT, MINB)
             // program k-1 out, then program k+1 into its buffer
             if (have_prv) rel_output(prv, dst, masks != nullptr);
             if (have_cur) {
-                rel_fetch(prv, V, ctrl, n_fast, masks, table_bytes);
+                rel_fetch(prv, Q, V, ctrl, n_fast, masks, table_bytes);
             } else if ((threadIdx.x & 31u) == 0) {
                 prv.p = kRelAllOnes;
             }
@@ -357,8 +420,10 @@ __global__ void __launch_bounds__(NT, MINB)
                 for (uint32_t w = 0; w < n_win; ++w) {
                     rel_install<NT>(cur, V.perm, tab, colrows, w * W);
                     asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory");
-                    rel_scan<NT>(cur, tab, colrows);
-                    asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory");
+                    rel_reset<NT>(cur, tab);
+                    // the last window's reset is ordered before the next
+                    // program's install by the CTA barrier below
+                    if (w + 1u < n_win) asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory");
                 }
             }
         }

@@ -129,6 +129,9 @@ def test_many_blocks_that_differ(gb):
         _same(g, w)
         assert gb.check(p, 0) == oracle.check(p, 0)
     _same(gb.repair_plain(progs[0]), want[0])
+    timed, loop_ms = gb.repair_plain_timed(progs[1])
+    _same(timed, want[1])
+    assert loop_ms > 0.0
     db = gb.DeviceBatch(progs)
     db.run_wide()
     torch.cuda.synchronize()
