@@ -260,6 +260,18 @@ size_t align_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 uint32_t t_pad_of(uint32_t T) { return (T + 7u) & ~7u; }
 
+// A program on the shared array alone whose blocks are alike (or that has
+// one block) goes to the relation kernel; any other has one check item, or,
+// when its blocks differ, one per range of blocks (up to kMaxCheckSplit), so
+// that its same-block passes spread over several CTAs.
+uint32_t check_items_of(const gr_program &p, const gr_launch &l) {
+    bool global = false;
+    for (uint32_t s = 0; s < p.n_stmts; ++s) global |= p.stmts[s].space == GR_GLOBAL;
+    const bool alike = blocks_alike(p);
+    if (!global && (alike || l.blocks == 1)) return 0;
+    return alike ? 1u : std::min(l.blocks, kMaxCheckSplit);
+}
+
 Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     Layout L;
     L.progs_off = sizeof(ArenaHeader);
@@ -271,7 +283,10 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
         const uint64_t x = exec_count(progs[p]);
         L.n_items += (x * ls[p].blocks + kItemSegs - 1) / kItemSegs + x + 1;
     }
-    L.perm_off = align_to(L.items_off + (size_t)L.n_items * 16, 16);
+    L.citems_off = align_to(L.items_off + (size_t)L.n_items * 16, 16);
+    L.n_citems = 0;
+    for (uint32_t p = 0; p < n; ++p) L.n_citems += check_items_of(progs[p], ls[p]);
+    L.perm_off = align_to(L.citems_off + (size_t)L.n_citems * 16, 16);
     L.trace_elem.resize(n);
     L.segmask_elem.resize(n);
     L.perm_base.resize(n);
@@ -445,6 +460,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     H->segbase_off = L.segbase_off;
     H->items_off = L.items_off;
     H->n_items = (uint32_t)L.n_items;
+    H->citems_off = L.citems_off;
     H->perm_off = L.perm_off;
     H->n_segments = L.n_segments;
     H->scratch_segmask_off = L.segmask_off;
@@ -574,7 +590,15 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             if (cur < P.perm_len) memset(dst + cur, 0, (size_t)(P.perm_len - cur) * 2);
         }
         segbase[p] = L.segmask_elem[p];
-        cost[p] = (uint64_t)S * ls[p].blocks * t_pad_of(ls[p].threads);
+        // work estimate for the largest-first orders: block 0's accesses when
+        // the blocks are alike (the same-block passes read no other block),
+        // every block's otherwise, plus every block's global accesses (the
+        // cross-block pass)
+        {
+            const uint64_t tp = t_pad_of(ls[p].threads), B = ls[p].blocks;
+            const uint64_t G = (uint64_t)__builtin_popcount(D.global_rows);
+            cost[p] = (uint64_t)S * tp * (D.blk_invariant ? 1u : B) + (B > 1 ? G * B * tp : 0u);
+        }
     }
     });
     {
@@ -631,6 +655,25 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     }
     if (n_fast == 0) H->n_items_gen = (uint32_t)k;
     H->n_items = (uint32_t)k;
+    // check items of the general programs in their order (largest first); a
+    // program split by blocks lists its first range (which also does the
+    // cross-block pass) first
+    uint32_t *citems = reinterpret_cast<uint32_t *>(arena + L.citems_off);
+    uint32_t nc = 0, n_split = 0;
+    for (uint32_t i = n_fast; i < n; ++i) {
+        const uint32_t p = order[i];
+        const uint32_t K = check_items_of(progs[p], ls[p]), B = ls[p].blocks;
+        n_split += K > 1 ? 1u : 0u;
+        for (uint32_t c = 0; c < K; ++c) {
+            citems[4 * nc] = p;
+            citems[4 * nc + 1] = (uint32_t)((uint64_t)B * c / K);
+            citems[4 * nc + 2] = (uint32_t)((uint64_t)B * (c + 1) / K);
+            citems[4 * nc + 3] = (c == 0 ? kItemPrimary : 0u) | (K > 1 ? kItemSplit : 0u);
+            ++nc;
+        }
+    }
+    H->n_citems = nc;
+    H->n_split = n_split;
 }
 
 }  // namespace gr
@@ -737,7 +780,8 @@ LaunchCfg shape_cfg(const Workspace &ws, uint32_t n, uint32_t shape, uint32_t s_
     if (table < need) return c;
     c.table_bytes = (uint32_t)table;
     const uint32_t resident = (uint32_t)ws.sms * sh.ctas_per_sm;
-    c.grid = std::max<uint32_t>(1u, std::min<uint32_t>(n, resident));
+    // a program may take up to kMaxCheckSplit work items (blocks that differ)
+    c.grid = std::max<uint32_t>(1u, (uint32_t)std::min<uint64_t>((uint64_t)n * kMaxCheckSplit, resident));
     if (shape & kShapeBalanced) {  // as many CTAs as give every CTA the same number of programs
         const uint32_t waves = (n + resident - 1) / resident;
         c.grid = std::max<uint32_t>(1u, (n + waves - 1) / waves);
@@ -797,9 +841,6 @@ LaunchCfg choose_cfg(const Workspace &ws, uint32_t n, uint32_t s_max = GR_MAX_ST
 }
 
 // The kSkip* bits of a packed batch from its header.
-uint32_t skip_bits(const ArenaHeader &h) {
-    return (h.n_fast == 0 ? kSkipFast : 0u) | (h.n_fast == h.n_progs ? kSkipGeneral : 0u);
-}
 
 // ---- autotuner: the fastest CTA shapes per batch size class ---------------
 

@@ -31,6 +31,9 @@ constexpr uint32_t kErrArgs = 4u;           // the launch's n or scratch size do
 constexpr uint8_t kStmtInjective = 1u;      // DevStmt::flags: no two threads of a block share an address
 constexpr uint32_t kArenaSimple = 1u;       // ArenaHeader::flags: every program is straight-line (no loops or
                                             // explicit slot places) on the shared array alone
+constexpr uint32_t kMaxCheckSplit = 16u;    // most check items of one program (its blocks in ranges)
+constexpr uint32_t kItemPrimary = 1u;       // check item flags: the item with block 0, the divergence, the
+constexpr uint32_t kItemSplit = 2u;         //   pair count and the cross-block pass; one of several items
 
 // One statement, with map coefficients reduced modulo its array's size.
 struct DevStmt {
@@ -90,8 +93,15 @@ struct ArenaHeader {
     uint64_t scratch_rel_off;     // each program's conflict relation (gr_witnesses rows)
     uint32_t n_fast;              // programs checked by the relation kernel (first in order)
     uint32_t n_items_gen;         // expansion items of the other programs (first in items)
+    // the general check kernel's work items (uint4: program, first block,
+    // end block, kItem* flags), largest first: one per program, or, for a
+    // program whose blocks differ, one per range of its blocks
+    uint64_t citems_off;
+    uint32_t n_citems;
+    uint32_t n_split;             // programs with more than one check item
+    uint32_t _r[12];
 };
-static_assert(sizeof(ArenaHeader) == 128, "ArenaHeader layout");
+static_assert(sizeof(ArenaHeader) == 192, "ArenaHeader layout");
 
 // Loop state of one program between iterations (plain path keeps it in
 // device memory between launches).
@@ -132,6 +142,13 @@ struct LaunchCfg {
 };
 constexpr uint32_t kSkipGeneral = 1u;  // no general program: no expansion, no k_check
 constexpr uint32_t kSkipFast = 2u;     // no program for the relation kernel
+constexpr uint32_t kSkipSplit = 4u;    // no program with several check items (nothing to zero first)
+
+// The kSkip* bits of a packed batch.
+inline uint32_t skip_bits(const ArenaHeader &h) {
+    return (h.n_fast == 0 ? kSkipFast : 0u) | (h.n_fast == h.n_progs ? kSkipGeneral : 0u) |
+           (h.n_split == 0 ? kSkipSplit : 0u);
+}
 
 // CTA shapes the persistent kernels are instantiated for.
 struct LaunchShape {
@@ -152,13 +169,16 @@ constexpr uint32_t kLoopThreads = 128;  // the general build's CTA: four warps
 
 // Host-side helpers (capi.cu).
 struct Layout {
-    size_t progs_off, order_off, segbase_off, items_off, perm_off, arena_bytes;
-    uint64_t n_items;
+    size_t progs_off, order_off, segbase_off, items_off, citems_off, perm_off, arena_bytes;
+    uint64_t n_items, n_citems;
     size_t segmask_off, segrange_off, trace_off, wide_off, rel_off, scratch_bytes;
     uint64_t n_segments;
     std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
 };
 gr_status fail(gr_status code, const char *fmt, ...);
+// Check items of a program in the general check kernel's queue (see
+// ArenaHeader::citems_off): 0 for a program the relation kernel checks.
+uint32_t check_items_of(const gr_program &p, const gr_launch &l);
 gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx, bool tables = true);
 // Statement instances in execution order (st: statement, ctr: counter of its
 // innermost loop); returns how many run, storing at most cap (counting stops
@@ -203,6 +223,9 @@ cudaError_t launch_perm_check(const void *d_arena, uint32_t n, uint32_t base, ui
                               cudaStream_t st);
 // One check per general program (d_masks NULL: the empty mask, rows into the
 // scratch's relation area when d_out is NULL).
+// Clears the witness entries of programs split over several check items.
+cudaError_t launch_split_zero(const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                              gr_witnesses *d_out, cudaStream_t st);
 cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
                          uint64_t scratch_bytes, gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st);
 // The same for the programs the relation kernel takes.

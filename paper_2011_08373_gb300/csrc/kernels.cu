@@ -1341,13 +1341,18 @@ __device__ __forceinline__ Dyn dyn_smem() {
     return d;
 }
 
-// One check per program of the batch's general part (items n_fast..n-1 of
-// the order: a global array, or blocks that differ) under masks[p], or under
-// the empty mask when masks is NULL: then the witness rows are the
-// program's conflict relation, written to the scratch's relation area for
-// the loop kernel (out == NULL) or to out.  Persistent: CTAs take programs
-// from a queue, largest first.  Instantiated for several CTA shapes (threads
-// x CTAs per SM); the host picks one per batch.
+// The checks of the batch's general part (a global array, or blocks that
+// differ), one per work item of the arena's check list: a program, or a
+// range of a program's blocks when its blocks differ (then its items OR
+// their witness rows into the program's entry, which k_split_zero cleared,
+// and each item first reads the pairs the others found, to skip them).  The
+// item holding block 0 (primary) also takes the divergence, the pair count
+// and the cross-block pass.  Under masks[p], or under the empty mask when
+// masks is NULL: then the witness rows are the program's conflict relation,
+// written to the scratch's relation area for the loop kernel (out == NULL)
+// or to out.  Persistent: CTAs take items from a queue, largest first.
+// Instantiated for several CTA shapes (threads x CTAs per SM); the host
+// picks one per batch.
 template <uint32_t NT, uint32_t MINB>
 __global__ void __launch_bounds__(NT, MINB)
     k_check(const uint8_t *__restrict__ arena, uint32_t n, const uint32_t *__restrict__ masks,
@@ -1365,30 +1370,61 @@ __global__ void __launch_bounds__(NT, MINB)
     const uint64_t *segmask = reinterpret_cast<const uint64_t *>(scratch + V.h->scratch_segmask_off);
     const uint32_t *segrange = reinterpret_cast<const uint32_t *>(scratch + V.h->scratch_segrange_off);
     gr_witnesses *dst = out ? out : reinterpret_cast<gr_witnesses *>(scratch + V.h->scratch_rel_off);
-    const uint32_t first = V.h->n_fast;
+    const uint4 *citems = reinterpret_cast<const uint4 *>(arena + V.h->citems_off);
+    const uint32_t n_citems = V.h->n_citems;
     if (threadIdx.x == 0) sm.err = &ctrl[1];
     for (;;) {
-        if (threadIdx.x == 0) sm.item = first + atomicAdd(&ctrl[0], 1u);
+        if (threadIdx.x == 0) sm.item = atomicAdd(&ctrl[0], 1u);
         __syncthreads();
         const uint32_t item = sm.item;
-        if (item >= n) break;
-        const uint32_t p = V.order[item];
+        if (item >= n_citems) break;
+        const uint4 ci = citems[item];
+        const uint32_t p = ci.x;
+        const bool primary = (ci.w & kItemPrimary) != 0, split = (ci.w & kItemSplit) != 0;
         load_program(sm, &V.progs[p]);
         const uint32_t mask = masks ? masks[p] : 0u;
         prepare_check(sm, mask);
-        check_misc(sm, mask);
-        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off,
-                     segrange + sm.prog.segmask_off, 0, sm.prog.blocks, true);
-        if (threadIdx.x < 32) {
-            dst[p].race_intra[threadIdx.x] = sm.rows_intra[threadIdx.x];
-            dst[p].race_inter[threadIdx.x] = sm.rows_inter[threadIdx.x];
+        if (primary) check_misc(sm, mask);
+        if (split && threadIdx.x < 32) {
+            sm.rows_intra[threadIdx.x] = *(volatile uint32_t *)&dst[p].race_intra[threadIdx.x];
+            sm.rows_inter[threadIdx.x] = *(volatile uint32_t *)&dst[p].race_inter[threadIdx.x];
         }
-        if (threadIdx.x == 0) {
+        __syncthreads();
+        check_blocks(sm, d.tab, table_bytes, traces + sm.prog.trace_off, segmask + sm.prog.segmask_off,
+                     segrange + sm.prog.segmask_off, ci.y, ci.z, primary);
+        if (threadIdx.x < 32) {
+            const uint32_t ri = sm.rows_intra[threadIdx.x], rx = sm.rows_inter[threadIdx.x];
+            if (!split) {
+                dst[p].race_intra[threadIdx.x] = ri;
+                dst[p].race_inter[threadIdx.x] = rx;
+            } else {
+                if (ri) atomicOr(&dst[p].race_intra[threadIdx.x], ri);
+                if (rx) atomicOr(&dst[p].race_inter[threadIdx.x], rx);
+            }
+        }
+        if (primary && threadIdx.x == 0) {
             dst[p].diverge = sm.diverge;
             dst[p].n_stmts = sm.prog.n_stmts;
             dst[p].access_pairs = sm.pairs;
         }
         __syncthreads();
+    }
+}
+
+// Clears the witness entries of the programs split over several check items
+// (their items OR into them).  Runs before the check kernel on its stream.
+__global__ void __launch_bounds__(128) k_split_zero(const uint8_t *__restrict__ arena, uint32_t n,
+                                                    uint8_t *__restrict__ scratch, uint64_t scratch_bytes,
+                                                    gr_witnesses *__restrict__ out) {
+    const ArenaView V = view(arena);
+    if (!launch_matches(V, n, scratch_bytes)) return;  // the check kernel reports it
+    gr_witnesses *dst = out ? out : reinterpret_cast<gr_witnesses *>(scratch + V.h->scratch_rel_off);
+    const uint4 *citems = reinterpret_cast<const uint4 *>(arena + V.h->citems_off);
+    for (uint32_t i = blockIdx.x; i < V.h->n_citems; i += gridDim.x) {
+        const uint4 ci = citems[i];
+        if ((ci.w & (kItemPrimary | kItemSplit)) != (kItemPrimary | kItemSplit)) continue;
+        uint32_t *w = reinterpret_cast<uint32_t *>(&dst[ci.x]);
+        for (uint32_t j = threadIdx.x; j < sizeof(gr_witnesses) / 4; j += blockDim.x) w[j] = 0u;
     }
 }
 
@@ -1726,6 +1762,13 @@ cudaError_t launch_expand(const void *d_arena, void *d_scratch, uint64_t scratch
     return cudaGetLastError();
 }
 
+cudaError_t launch_split_zero(const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                              gr_witnesses *d_out, cudaStream_t st) {
+    k_split_zero<<<64, 128, 0, st>>>(static_cast<const uint8_t *>(d_arena), n, static_cast<uint8_t *>(d_scratch),
+                                     scratch_bytes, d_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
                          uint64_t scratch_bytes, gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st) {
     const uint8_t *a = static_cast<const uint8_t *>(d_arena);
@@ -1778,6 +1821,8 @@ cudaError_t enqueue_relation(const void *d_arena, uint32_t n, void *d_scratch, u
     cudaError_t e = clear_ctrl(d_scratch, clear_error, st);
     if (e == cudaSuccess && general && expand)
         e = launch_expand(d_arena, d_scratch, scratch_bytes, true, expand_grid, st);
+    if (e == cudaSuccess && general && !(cfg.skip & kSkipSplit))
+        e = launch_split_zero(d_arena, n, d_scratch, scratch_bytes, nullptr, st);
     if (e == cudaSuccess && fast)
         e = launch_relation(d_arena, n, nullptr, d_scratch, scratch_bytes, nullptr, cfg.rel, st);
     if (e == cudaSuccess && general)
@@ -1807,6 +1852,8 @@ cudaError_t enqueue_check(const void *d_arena, uint32_t n, const uint32_t *d_mas
     cudaError_t e = clear_ctrl(d_scratch, true, st);
     if (e == cudaSuccess && general && expand)
         e = launch_expand(d_arena, d_scratch, scratch_bytes, true, expand_grid, st);
+    if (e == cudaSuccess && general && !(cfg.skip & kSkipSplit))
+        e = launch_split_zero(d_arena, n, d_scratch, scratch_bytes, d_out, st);
     if (e == cudaSuccess && fast)
         e = launch_relation(d_arena, n, d_masks, d_scratch, scratch_bytes, d_out, cfg.rel, st);
     if (e == cudaSuccess && general) e = launch_check(d_arena, n, d_masks, d_scratch, scratch_bytes, d_out, cfg, st);

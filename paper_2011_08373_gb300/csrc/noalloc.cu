@@ -110,7 +110,7 @@ extern "C" gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, c
                             (unsigned long long)h.scratch_bytes, (unsigned long long)kNoAllocScratchBytes);
     // the same launch as gr_repair_packed: the shapes gr_tune_packed recorded
     // for this arena, else the defaults
-    const uint32_t skip = (h.n_fast == 0 ? kSkipFast : 0u) | (h.n_fast == h.n_progs ? kSkipGeneral : 0u);
+    const uint32_t skip = skip_bits(h);
     const LaunchCfg cfg = packed_launch_cfg(d_arena, n, skip, (h.flags & kArenaSimple) != 0, &s);
     if (s != GR_OK) return noalloc_fail(s, "launch configuration failed");
     // the queue counters and the error word start at zero (cleared first)

@@ -197,7 +197,7 @@ bool dispatch(gr_server *s, Slot &sl, std::unique_lock<std::mutex> &lk) {
         b_max = std::max(b_max, ls[i].blocks);
     }
     const ArenaHeader &hd = *reinterpret_cast<const ArenaHeader *>(sl.h_arena);
-    const uint32_t skip = (hd.n_fast == 0 ? kSkipFast : 0u) | (hd.n_fast == n ? kSkipGeneral : 0u);
+    const uint32_t skip = skip_bits(hd);
     const LaunchCfg cfg = wide ? wide_launch_cfg(n, s_max, &cs) : packed_launch_cfg(sl.d_arena, n, skip, (hd.flags & kArenaSimple) != 0, &cs);
     e = cudaMemcpyAsync(sl.d_arena, sl.h_arena, L.arena_bytes, cudaMemcpyHostToDevice, sl.stream);
     if (e == cudaSuccess) {

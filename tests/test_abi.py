@@ -278,12 +278,42 @@ def test_expansion_items_cover_every_segment_once(lib):
     gen_items = {int(x) for x in items[:n_items_gen, 0]}
     assert gen_items == {p for p in range(n) if not fast[p]}
     assert {int(x) for x in items[n_items_gen:, 0]} == {p for p in range(n) if fast[p]}
-    cost = [int(segbase[p + 1] - segbase[p]) * ((progs[p].threads + 7) // 8 * 8) for p in order]
-    k = n - n_fast
-    assert all(not fast[p] for p in order[:k]) and all(fast[p] for p in order[k:])
-    assert cost[:k] == sorted(cost[:k], reverse=True) and cost[k:] == sorted(cost[k:], reverse=True)
+    def cost(p):
+        # the packer's work estimate: block 0's accesses when the blocks are
+        # alike, every block's otherwise, plus every block's global accesses
+        B, tp = progs[p].blocks, (progs[p].threads + 7) // 8 * 8
+        inst = [s for s, _ in oracle.unroll(progs[p])]
+        alike = int(_devprog(arena, p)[56:60].view(np.uint32)[0])
+        G = sum(int(progs[p].space[s]) == 1 for s in inst)
+        return len(inst) * tp * (1 if alike else B) + (G * B * tp if B > 1 else 0)
+
     prog_order = arena[int(h[3]):int(h[3]) + 4 * n].view(np.uint32).tolist()
-    assert [fast[p] for p in prog_order] == [1] * n_fast + [0] * (n - n_fast)
+    k = n - n_fast
+    costs = [cost(p) for p in prog_order]
+    assert [fast[p] for p in prog_order] == [1] * n_fast + [0] * k
+    assert costs[:n_fast] == sorted(costs[:n_fast], reverse=True)
+    assert costs[n_fast:] == sorted(costs[n_fast:], reverse=True)
+    # the expansion items: the general programs first, each part in program order
+    assert order[:k] == prog_order[n_fast:] and order[k:] == prog_order[:n_fast]
+    # the check items: the general programs in program order, one item each,
+    # or one per range of blocks (at most 16, covering every block once) when
+    # the blocks differ; the first range is the primary item
+    ch = arena[128:192].view(np.uint32)
+    citems_off, n_citems, n_split = int(arena[128:136].view(np.uint64)[0]), int(ch[2]), int(ch[3])
+    citems = arena[citems_off:citems_off + 16 * n_citems].view(np.uint32).reshape(-1, 4).tolist()
+    seen, at = [], 0
+    for p in prog_order[n_fast:]:
+        alike = int(_devprog(arena, p)[56:60].view(np.uint32)[0])
+        B = progs[p].blocks
+        K = 1 if alike else min(B, 16)
+        mine = citems[at:at + K]
+        at += K
+        assert [c[0] for c in mine] == [p] * K
+        assert mine[0][1] == 0 and mine[-1][2] == B
+        assert all(a[2] == b[1] and a[1] < a[2] for a, b in zip(mine, mine[1:]))
+        assert [c[3] for c in mine] == [1 | (2 if K > 1 else 0)] + [2] * (K - 1)
+        seen.append(K > 1)
+    assert at == n_citems and sum(seen) == n_split > 0
 
 
 @pytest.mark.parametrize("negs,msg", [([0], "empty"), ([1 << 7], "beyond slot"), ([1] * 33, "negative clauses")])
