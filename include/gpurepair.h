@@ -21,6 +21,11 @@
  *   GR_PERM:               perm[perm_off + ((tid + c*blk + b) mod M)]
  * (64-bit intermediates; tid = threadIdx.x, blk = blockIdx.x).  Statement s
  * runs for thread tid iff guard_k == 0 or tid % guard_k == guard_r.
+ * A GR_PERM statement's table entries must be distinct indices below M
+ * where it reads them: when its address does not depend on the block
+ * (c mod M == 0, or one block) the min(T, M) entries from b on, cyclically
+ * (entries (b + tid) mod M, tid < T); else the whole table (a permutation
+ * of 0..M-1).  Entries it never reads are neither checked nor copied.
  * Slot k (0..S-2) is a candidate barrier between statements k and k+1 with a
  * level (GR_BLOCK orders threads of one block, GR_GRID orders all threads;
  * Section 2.2), a guard (same meaning; the barrier is executed by the threads
@@ -31,8 +36,9 @@
  * output buffer.  Host-pointer entry points copy their inputs during the call
  * and return after the result is in the caller's memory.  Inputs are
  * validated before any device work (one exception: gr_repair_batch checks
- * that each permutation table holds every index once on the device, next to
- * the repair, and reads that back before it copies any result); a rejected
+ * that the permutation entries each statement reads are distinct on the
+ * device, next to the repair, and reads that back before it copies any
+ * result); a rejected
  * call returns GR_EINVAL and leaves the outputs untouched (gr_last_error()
  * says why).  CUDA failures
  * return GR_ECUDA; a failed allocation returns GR_ENOMEM.  The library keeps

@@ -139,40 +139,102 @@ gr_status validate_loops(const gr_program *p, uint32_t idx) {
     return GR_OK;
 }
 
-// Whether the M entries of tbl are a permutation of 0..M-1 (M values below M
-// marking M distinct entries); dst (may be NULL) receives them as u16.  With
-// range_only (dst given) only whether every entry is below M.
-bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst, bool range_only) {
-    uint8_t mark[GR_MAX_WORDS];
-    uint32_t bad = 0;
-    if (dst) {
-        // convert (a streaming loop the compiler vectorises) and check the
-        // range, then mark from the u16 copy
-        uint32_t mx = 0;
-        for (uint32_t i = 0; i < M; ++i) {
-            const uint32_t v = tbl[i];
-            mx = v > mx ? v : mx;
-            dst[i] = (uint16_t)v;
-        }
-        if (mx >= M) return false;
-        if (range_only) return true;
-        memset(mark, 0, M);
-        for (uint32_t i = 0; i < M; ++i) mark[dst[i]] = 1;
-    } else {
-        memset(mark, 0, M);
-        for (uint32_t i = 0; i < M; ++i) {
-            const uint32_t v = tbl[i];
-            bad |= v >= M;
-            mark[v < M ? v : 0u] = 1;
-        }
-    }
-    uint32_t filled = 0;
-    for (uint32_t i = 0; i < M; ++i) filled += mark[i];
-    return !bad && filled == M;
+// The entries of its table a permutation statement reads, rotated to start
+// at its offset b: when its address does not depend on the block (c = 0 mod
+// M, or one block) the threads of a block read entries (b + t) mod M,
+// t < T, else every entry.  The packed window holds `len` entries (the
+// padded thread count, for the expansion kernel's padding lanes, or M) of
+// which the first `need` (min(T, M), or M) must be distinct indices below M.
+struct PermWindow {
+    uint32_t len, need;
+};
+
+uint32_t t_pad_of(uint32_t T) { return (T + 7u) & ~7u; }
+
+PermWindow perm_window(const gr_stmt &st, uint32_t M, const gr_launch &l) {
+    if (l.blocks > 1 && st.c % M != 0) return {M, M};
+    return {std::min(M, t_pad_of(l.threads)), std::min(M, l.threads)};
 }
 
-// tables == false leaves the permutation-table check to pack_into, which
-// does it while converting the tables.
+// The window of tbl from b (entries tbl[(b + k) mod M], k < w.len) into dst
+// (may be NULL) as u16; true when its first w.need entries are below M and,
+// unless range_only, distinct.
+bool window_to_u16(const uint32_t *tbl, uint32_t M, uint32_t b, PermWindow w, uint16_t *dst, bool range_only) {
+    const uint32_t n1 = std::min(w.len, M - b);  // [b, b + n1), then [0, len - n1)
+    uint32_t mx = 0;
+    // one streaming pass per run: the entries that must be in range, then the rest
+    auto run = [&](const uint32_t *src, uint16_t *d, uint32_t cnt, uint32_t cnt_need) {
+        if (d) {
+            for (uint32_t k = 0; k < cnt_need; ++k) {
+                const uint32_t v = src[k];
+                mx = v > mx ? v : mx;
+                d[k] = (uint16_t)v;
+            }
+            for (uint32_t k = cnt_need; k < cnt; ++k) d[k] = (uint16_t)src[k];
+        } else {
+            for (uint32_t k = 0; k < cnt_need; ++k) mx = src[k] > mx ? src[k] : mx;
+        }
+    };
+    run(tbl + b, dst, n1, std::min(w.need, n1));
+    run(tbl, dst ? dst + n1 : nullptr, w.len - n1, w.need > n1 ? w.need - n1 : 0u);
+    if (mx >= M) return false;
+    if (range_only) return true;
+    uint64_t seen[GR_MAX_WORDS / 64];
+    memset(seen, 0, ((M + 63u) / 64u) * 8u);
+    for (uint32_t k = 0; k < w.need; ++k) {
+        const uint32_t v = k < n1 ? tbl[b + k] : tbl[k - n1];
+        const uint64_t bit = 1ull << (v & 63u);
+        if (seen[v >> 6] & bit) return false;
+        seen[v >> 6] |= bit;
+    }
+    return true;
+}
+
+// Visit each permutation instance of p in execution order: f(instance,
+// statement, its gr_stmt, M, window start b, window).  Loop instances move b
+// by their counter times the statement's loop coefficient.
+template <typename F>
+void for_each_perm_instance(const gr_program &P, const gr_launch &l, F f) {
+    uint8_t st_of[GR_MAX_STMTS], ctr_of[GR_MAX_STMTS];
+    uint32_t S = P.n_stmts;
+    if (P.n_loops) {
+        S = exec_order(P, st_of, ctr_of, GR_MAX_STMTS);
+    } else {
+        for (uint32_t s = 0; s < S; ++s) {
+            st_of[s] = (uint8_t)s;
+            ctr_of[s] = 0;
+        }
+    }
+    for (uint32_t s = 0; s < S; ++s) {
+        const gr_stmt &st = P.stmts[st_of[s]];
+        if (st.kind != GR_PERM) continue;
+        const uint32_t M = st.space == GR_SHARED ? P.m_shared : P.m_global;
+        const uint64_t d = P.iter_coef ? (uint64_t)(P.iter_coef[st_of[s]] % M) * ctr_of[s] : 0u;
+        const uint32_t b = (uint32_t)(((uint64_t)(st.b % M) + d) % M);
+        f(s, (uint32_t)st_of[s], st, M, b, perm_window(st, M, l));
+    }
+}
+
+uint64_t perm_window_elems(const gr_program &P, const gr_launch &l) {
+    uint64_t e = 0;
+    for_each_perm_instance(P, l, [&](uint32_t, uint32_t, const gr_stmt &, uint32_t, uint32_t, PermWindow w) {
+        e += w.len;
+    });
+    return e;
+}
+
+// The lowest statement of p with a window that is not distinct indices
+// below M, or ~0u.
+uint32_t first_bad_window(const gr_program &P, const gr_launch &l) {
+    uint32_t bad = 0xFFFFFFFFu;
+    for_each_perm_instance(P, l, [&](uint32_t, uint32_t s, const gr_stmt &st, uint32_t M, uint32_t b, PermWindow w) {
+        if (s < bad && !window_to_u16(P.perm + st.perm_off, M, b, w, nullptr, false)) bad = s;
+    });
+    return bad;
+}
+
+// tables == false leaves the permutation-window check to pack_into, which
+// does it while converting the windows.
 gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx, bool tables) {
     if (!p) return fail(GR_EINVAL, "program %u: NULL", idx);
     if (p->n_stmts < 1 || p->n_stmts > GR_MAX_STMTS)
@@ -205,8 +267,6 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx, bool tabl
             if (!p->perm) return fail(GR_EINVAL, "program %u stmt %u: permutation map without perm", idx, s);
             if ((uint64_t)st.perm_off + M > p->perm_len)
                 return fail(GR_EINVAL, "program %u stmt %u: perm_off + M beyond perm_len", idx, s);
-            if (tables && !table_to_u16(p->perm + st.perm_off, M, nullptr))
-                return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", idx, s);
         }
     }
     if (n > 0 && !p->slot_level) return fail(GR_EINVAL, "program %u: slot_level is NULL", idx);
@@ -227,7 +287,13 @@ gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx, bool tabl
     for (uint32_t c = 0; c < p->n_neg; ++c)
         if (p->neg[c] == 0 || (n < 32 && (p->neg[c] >> n) != 0))
             return fail(GR_EINVAL, "program %u negative clause %u: empty or beyond slot %u", idx, c, n);
-    return validate_loops(p, idx);
+    gr_status ls = validate_loops(p, idx);
+    if (ls != GR_OK || !tables) return ls;
+    const uint32_t bad = first_bad_window(*p, l);
+    if (bad != 0xFFFFFFFFu)
+        return fail(GR_EINVAL, "program %u stmt %u: the permutation entries it reads are not distinct indices "
+                               "below M", idx, bad);
+    return GR_OK;
 }
 
 gr_status validate_opts(const gr_options *o) {
@@ -258,7 +324,6 @@ gr_options opts_or_default(const gr_options *o) {
 
 size_t align_to(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-uint32_t t_pad_of(uint32_t T) { return (T + 7u) & ~7u; }
 
 // A program on the shared array alone whose blocks are alike (or that has
 // one block) goes to the relation kernel; any other has one check item, or,
@@ -272,36 +337,52 @@ uint32_t check_items_of(const gr_program &p, const gr_launch &l) {
     return alike ? 1u : std::min(l.blocks, kMaxCheckSplit);
 }
 
+template <typename F>
+void parallel_over(uint32_t n, F body);
+
 Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
     Layout L;
+    // per-program sizes (in parallel), then their prefix sums
+    struct Sizes {
+        uint64_t items, citems, perm, segs, trace;
+    };
+    std::vector<Sizes> z(n);
+    parallel_over(n, [&](uint32_t lo, uint32_t hi) {
+        for (uint32_t p = lo; p < hi; ++p) {
+            const uint64_t x = exec_count(progs[p]), B = ls[p].blocks;
+            // room for either expansion item layout of the program (see pack_into)
+            z[p].items = (x * B + kItemSegs - 1) / kItemSegs + x + 1;
+            z[p].citems = check_items_of(progs[p], ls[p]);
+            z[p].perm = perm_window_elems(progs[p], ls[p]);  // one window per instance (equal ones shared)
+            z[p].segs = x * B;
+            z[p].trace = align_to(x * B * t_pad_of(ls[p].threads), 128);
+        }
+    });
     L.progs_off = sizeof(ArenaHeader);
     L.order_off = align_to(L.progs_off + (size_t)n * sizeof(DevProg), 16);
     L.segbase_off = align_to(L.order_off + (size_t)n * 4, 16);
     L.items_off = align_to(L.segbase_off + (size_t)(n + 1) * 8, 16);
-    L.n_items = 0;  // room for either item layout of each program (see pack_into)
-    for (uint32_t p = 0; p < n; ++p) {
-        const uint64_t x = exec_count(progs[p]);
-        L.n_items += (x * ls[p].blocks + kItemSegs - 1) / kItemSegs + x + 1;
-    }
-    L.citems_off = align_to(L.items_off + (size_t)L.n_items * 16, 16);
+    L.n_items = 0;
     L.n_citems = 0;
-    for (uint32_t p = 0; p < n; ++p) L.n_citems += check_items_of(progs[p], ls[p]);
-    L.perm_off = align_to(L.citems_off + (size_t)L.n_citems * 16, 16);
     L.trace_elem.resize(n);
     L.segmask_elem.resize(n);
     L.perm_base.resize(n);
     uint64_t perm_total = 0, seg_total = 0, trace_total = 0;
     for (uint32_t p = 0; p < n; ++p) {
+        L.n_items += z[p].items;
+        L.n_citems += z[p].citems;
         L.perm_base[p] = perm_total;
-        perm_total += progs[p].perm ? progs[p].perm_len : 0;
+        perm_total += z[p].perm;
         L.segmask_elem[p] = seg_total;
-        const uint64_t segs = (uint64_t)exec_count(progs[p]) * ls[p].blocks;
-        seg_total += segs;
+        seg_total += z[p].segs;
         L.trace_elem[p] = trace_total;
-        trace_total += align_to(segs * t_pad_of(ls[p].threads), 128);
+        trace_total += z[p].trace;
     }
+    L.citems_off = align_to(L.items_off + (size_t)L.n_items * 16, 16);
+    L.perm_off = align_to(L.citems_off + (size_t)L.n_citems * 16, 16);
     L.n_segments = seg_total;
-    L.arena_bytes = align_to(L.perm_off + perm_total * 2, 256);  // tables as u16 (M <= 65,536)
+    L.perm_elems = perm_total;
+    L.arena_bytes = align_to(L.perm_off + perm_total * 2, 256);  // windows as u16 (M <= 65,536)
     L.segmask_off = 256;
     L.segrange_off = align_to(L.segmask_off + seg_total * 8, 256);
     L.trace_off = align_to(L.segrange_off + seg_total * 4, 256);
@@ -517,8 +598,12 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
         for (uint32_t s = 0; s + 1 < S; ++s) {
             const uint32_t place = st_of[s + 1] - 1u;
             uint32_t m = 0;
-            for (uint32_t k = 0; k < nsl; ++k)
-                if ((P.slot_pos ? P.slot_pos[k] : k) == place) m |= 1u << k;
+            if (!P.slot_pos) {
+                m = place < nsl ? 1u << place : 0u;  // slot k sits after statement k
+            } else {
+                for (uint32_t k = 0; k < nsl; ++k)
+                    if (P.slot_pos[k] == place) m |= 1u << k;
+            }
             D.gapslots[s] = m;
         }
         for (uint32_t s = 0; s < S; ++s) {
@@ -532,7 +617,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             ds.am = st.a % M;
             ds.bm = (uint32_t)(((uint64_t)(st.b % M) + d) % M);
             ds.cm = st.c % M;
-            ds.perm_off = st.kind == GR_PERM ? (uint32_t)(L.perm_base[p] + st.perm_off) : 0u;
+            ds.perm_off = 0;
             ds.gk = st.guard_k;
             ds.gr = st.guard_r;
             ds.m = M;
@@ -540,6 +625,36 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
             if (st.op == GR_W) D.write_mask |= 1u << s;
             if (st.space == GR_SHARED) D.shared_rows |= 1u << s;
             else D.global_rows |= 1u << s;
+        }
+        // permutation instances: each reads its window (rotated to start at
+        // its b, which becomes 0); equal windows are shared, so that equal
+        // instances stay one access pattern
+        {
+            uint16_t *dst = perm + L.perm_base[p];
+            const uint64_t end = p + 1 < n ? L.perm_base[p + 1] : L.perm_elems;
+            const uint32_t room = (uint32_t)(end - L.perm_base[p]);
+            uint32_t used = 0, wst[GR_MAX_STMTS], wb[GR_MAX_STMTS], woff[GR_MAX_STMTS], nw = 0;
+            for_each_perm_instance(P, ls[p], [&](uint32_t x, uint32_t s, const gr_stmt &st, uint32_t M, uint32_t b,
+                                                 PermWindow w) {
+                uint32_t off = 0xFFFFFFFFu;
+                for (uint32_t k = 0; k < nw && off == 0xFFFFFFFFu; ++k)
+                    if (wst[k] == s && wb[k] == b) off = woff[k];
+                if (off == 0xFFFFFFFFu) {
+                    off = used;
+                    used += w.len;
+                    wst[nw] = s;
+                    wb[nw] = b;
+                    woff[nw++] = off;
+                    if (!window_to_u16(P.perm + st.perm_off, M, b, w, dst + off, range_only) && table_bad &&
+                        s < table_bad[p])
+                        table_bad[p] = s;
+                }
+                DevStmt &ds = D.stmts[x];
+                ds.perm_off = (uint32_t)(L.perm_base[p] + off);
+                ds.bm = 0;
+                ds.pneed = w.need;
+            });
+            if (used < room) memset(dst + used, 0, (size_t)(room - used) * 2);
         }
         D.blk_invariant = blocks_alike(P) ? 1u : 0u;
         // the relation kernel takes programs on the shared array alone whose
@@ -549,45 +664,31 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
         // access-pattern classes: statements with the same array, map and
         // guard touch the same words from the same threads
         for (uint32_t s = 0; s < 32; ++s) D.rep[s] = (uint8_t)s;
-        for (uint32_t s = 1; s < S; ++s) {
-            const DevStmt &a = D.stmts[s];
-            for (uint32_t q = 0; q < s; ++q) {
-                const DevStmt &b = D.stmts[q];
-                if (a.space == b.space && a.kind == b.kind && a.am == b.am && a.bm == b.bm && a.cm == b.cm &&
-                    a.perm_off == b.perm_off && a.gk == b.gk && a.gr == b.gr && a.m == b.m) {
-                    D.rep[s] = (uint8_t)q;
-                    break;
+        {
+            // a 64-bit key of each instance's pattern first, the fields on a match
+            uint64_t key[GR_MAX_STMTS];
+            for (uint32_t s = 0; s < S; ++s) {
+                const DevStmt &a = D.stmts[s];
+                uint64_t h = ((uint64_t)a.space << 8 | a.kind) * 0x9E3779B97F4A7C15ull;
+                h = (h ^ a.am) * 0x9E3779B97F4A7C15ull;
+                h = (h ^ a.bm) * 0x9E3779B97F4A7C15ull;
+                h = (h ^ a.cm) * 0x9E3779B97F4A7C15ull;
+                h = (h ^ a.perm_off) * 0x9E3779B97F4A7C15ull;
+                h = (h ^ ((uint64_t)a.gk << 16 | a.gr)) * 0x9E3779B97F4A7C15ull;
+                key[s] = h ^ a.m;
+            }
+            for (uint32_t s = 1; s < S; ++s) {
+                const DevStmt &a = D.stmts[s];
+                for (uint32_t q = 0; q < s; ++q) {
+                    if (key[q] != key[s]) continue;
+                    const DevStmt &b = D.stmts[q];
+                    if (a.space == b.space && a.kind == b.kind && a.am == b.am && a.bm == b.bm && a.cm == b.cm &&
+                        a.perm_off == b.perm_off && a.gk == b.gk && a.gr == b.gr && a.m == b.m) {
+                        D.rep[s] = (uint8_t)q;
+                        break;
+                    }
                 }
             }
-        }
-        if (P.perm && P.perm_len) {
-            // each permutation statement's table as u16 (checked here when the
-            // caller left it unchecked); entries no statement uses are zeroed
-            uint16_t *dst = perm + L.perm_base[p];
-            uint32_t lo[GR_MAX_STMTS], hi[GR_MAX_STMTS], ns = 0;
-            for (uint32_t s = 0; s < P.n_stmts; ++s) {
-                const gr_stmt &st = P.stmts[s];
-                if (st.kind != GR_PERM) continue;
-                const uint32_t M = st.space == GR_SHARED ? P.m_shared : P.m_global;
-                uint32_t at = ns++;
-                while (at > 0 && lo[at - 1] > st.perm_off) {
-                    lo[at] = lo[at - 1];
-                    hi[at] = hi[at - 1];
-                    --at;
-                }
-                lo[at] = st.perm_off;
-                hi[at] = st.perm_off + M;
-                if (!table_to_u16(P.perm + st.perm_off, M, dst + st.perm_off, range_only) && table_bad) {
-                    uint32_t cur = table_bad[p];
-                    if (s < cur) table_bad[p] = s;
-                }
-            }
-            uint32_t cur = 0;
-            for (uint32_t k = 0; k < ns; ++k) {
-                if (lo[k] > cur) memset(dst + cur, 0, (size_t)(lo[k] - cur) * 2);
-                cur = std::max(cur, hi[k]);
-            }
-            if (cur < P.perm_len) memset(dst + cur, 0, (size_t)(P.perm_len - cur) * 2);
         }
         segbase[p] = L.segmask_elem[p];
         // work estimate for the largest-first orders: block 0's accesses when
@@ -602,9 +703,7 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
     }
     });
     {
-        uint64_t perm_total = 0;
-        for (uint32_t p = 0; p < n; ++p) perm_total += progs[p].perm ? progs[p].perm_len : 0;
-        const size_t tail = L.perm_off + perm_total * 2;
+        const size_t tail = L.perm_off + L.perm_elems * 2;
         if (tail < L.arena_bytes) memset(arena + tail, 0, L.arena_bytes - tail);
     }
     segbase[n] = L.n_segments;
@@ -734,7 +833,22 @@ struct Workspace {
     std::map<std::pair<const void *, uint32_t>, Tuned> arena_shape;     // gr_tune_packed
     uint8_t *host_arena = nullptr;  // pinned staging for the packed arena
     size_t host_arena_cap = 0;
+    uint8_t *host_out = nullptr;    // pinned staging for a batch's results
+    size_t host_out_cap = 0;
 };
+
+// A pinned host buffer of at least `bytes` in *buf (grown, contents dropped).
+gr_status ensure_pinned(uint8_t **buf, size_t *cap, size_t bytes) {
+    if (*cap >= bytes) return GR_OK;
+    if (*buf) cudaFreeHost(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    const size_t want = std::max<size_t>(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(buf), want, cudaHostAllocDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(staging)");
+    *cap = want;
+    return GR_OK;
+}
 
 constexpr int kMaxDevices = 64;
 Workspace g_ws[kMaxDevices];
@@ -933,24 +1047,17 @@ uint32_t expand_grid(const Workspace &ws) { return (uint32_t)ws.sms * 8u; }
 gr_status upload_batch(Workspace &ws, const gr_program *progs, const gr_launch *ls, const int32_t *modes,
                        uint32_t n, cudaStream_t st, Layout *Lout) {
     Layout L = layout_of(progs, ls, n);
-    if (ws.host_arena_cap < L.arena_bytes) {
-        if (ws.host_arena) cudaFreeHost(ws.host_arena);
-        ws.host_arena = nullptr;
-        ws.host_arena_cap = 0;
-        const size_t want = std::max<size_t>(L.arena_bytes, (size_t)1 << 20);
-        cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&ws.host_arena), want, cudaHostAllocDefault);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(staging)");
-        ws.host_arena_cap = want;
-    }
     // the previous call on this workspace may still be reading the staging buffer
     GR_CUDA(cudaStreamSynchronize(st));
+    gr_status ps = ensure_pinned(&ws.host_arena, &ws.host_arena_cap, L.arena_bytes);
+    if (ps != GR_OK) return ps;
     // the callers validated everything but the permutation tables, which are
     // checked while they are converted; the lowest bad program is reported
     // before any device work, as a full validation would
     std::vector<uint32_t> bad(n, 0xFFFFFFFFu);
     pack_into(progs, ls, modes, n, L, ws.host_arena, bad.data());
     for (uint32_t p = 0; p < n; ++p)
-        if (bad[p] != 0xFFFFFFFFu) return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", p, bad[p]);
+        if (bad[p] != 0xFFFFFFFFu) return fail(GR_EINVAL, "program %u stmt %u: the permutation entries it reads are not distinct indices below M", p, bad[p]);
     gr_status s;
     if ((s = ws.arena.ensure(L.arena_bytes)) != GR_OK) return s;
     if ((s = ws.scratch.ensure(L.scratch_bytes)) != GR_OK) return s;
@@ -1253,15 +1360,7 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     }
     // the previous call on this workspace may still be reading the staging buffer
     GR_CUDA(cudaStreamSynchronize(st));
-    if (ws->host_arena_cap < stage) {
-        if (ws->host_arena) cudaFreeHost(ws->host_arena);
-        ws->host_arena = nullptr;
-        ws->host_arena_cap = 0;
-        const size_t want = std::max<size_t>(stage, (size_t)1 << 20);
-        cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&ws->host_arena), want, cudaHostAllocDefault);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(staging)");
-        ws->host_arena_cap = want;
-    }
+    if ((s = ensure_pinned(&ws->host_arena, &ws->host_arena_cap, stage)) != GR_OK) return s;
     if ((s = ws->arena.ensure(arena_max)) != GR_OK) return s;
     if ((s = ws->scratch.ensure(scratch_max)) != GR_OK) return s;
     if ((s = ws->out.ensure((size_t)n * sizeof(gr_repair_result))) != GR_OK) return s;
@@ -1275,14 +1374,8 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     // converting; that each index occurs once is checked on the device
     // (k_perm_check) and read back before the results are copied.  Either way
     // the lowest bad program is reported and `out` stays untouched.
-    auto bad_stmt = [&](uint32_t p) -> uint32_t {  // the first table of p that is not a permutation, or ~0u
-        const gr_program &P = progs[p];
-        for (uint32_t q = 0; q < P.n_stmts; ++q) {
-            const gr_stmt &t = P.stmts[q];
-            const uint32_t M = t.space == GR_SHARED ? P.m_shared : P.m_global;
-            if (t.kind == GR_PERM && !table_to_u16(P.perm + t.perm_off, M, nullptr)) return q;
-        }
-        return 0xFFFFFFFFu;
+    auto bad_stmt = [&](uint32_t p) -> uint32_t {  // the first bad permutation window of p, or ~0u
+        return first_bad_window(progs[p], launches[p]);
     };
     auto device_bad = [&](uint32_t *p_out) -> gr_status {  // waits for the stream
         uint32_t word = 0;
@@ -1307,8 +1400,8 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
                 for (uint32_t q = lo[c]; q < lo[c] + p && low == 0xFFFFFFFFu; ++q)
                     if (bad_stmt(q) != 0xFFFFFFFFu) low = q;
                 if (low < lo[c] + p)
-                    return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", low, bad_stmt(low));
-                return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", lo[c] + p, bad[p]);
+                    return fail(GR_EINVAL, "program %u stmt %u: the permutation entries it reads are not distinct indices below M", low, bad_stmt(low));
+                return fail(GR_EINVAL, "program %u stmt %u: the permutation entries it reads are not distinct indices below M", lo[c] + p, bad[p]);
             }
         GR_CUDA(cudaMemcpyAsync(ws->arena.p, staging, Ls[c].arena_bytes, cudaMemcpyHostToDevice, st));
         if (any_perm) GR_CUDA(launch_perm_check(ws->arena.p, n_c, lo[c], d_perm_bad, (uint32_t)ws->sms, st));
@@ -1341,10 +1434,20 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
         uint32_t low = 0xFFFFFFFFu;
         if ((s = device_bad(&low)) != GR_OK) return s;
         if (low != 0xFFFFFFFFu)
-            return fail(GR_EINVAL, "program %u stmt %u: table is not a permutation", low, bad_stmt(low));
+            return fail(GR_EINVAL, "program %u stmt %u: the permutation entries it reads are not distinct indices below M", low, bad_stmt(low));
     }
-    GR_CUDA(cudaMemcpyAsync(out, d_out, (size_t)n * sizeof(gr_repair_result), cudaMemcpyDeviceToHost, st));
-    return finish_sync(ws->scratch.p, st);
+    // the results come back through pinned staging (a DMA at full speed; a
+    // copy into the caller's pageable array would go through the driver's
+    // bounce buffer), then reach `out` in parallel, once the error word is clean
+    const size_t rb = (size_t)n * sizeof(gr_repair_result);
+    if ((s = ensure_pinned(&ws->host_out, &ws->host_out_cap, rb)) != GR_OK) return s;
+    GR_CUDA(cudaMemcpyAsync(ws->host_out, d_out, rb, cudaMemcpyDeviceToHost, st));
+    if ((s = finish_sync(ws->scratch.p, st)) != GR_OK) return s;
+    const uint8_t *staged = ws->host_out;
+    parallel_over(n, [&](uint32_t a, uint32_t b) {
+        memcpy(out + a, staged + (size_t)a * sizeof(gr_repair_result), (size_t)(b - a) * sizeof(gr_repair_result));
+    });
+    return GR_OK;
 }
 
 gr_status gr_check_batch(const gr_program *progs, const gr_launch *launches, const uint32_t *masks, uint32_t n,

@@ -39,10 +39,10 @@ constexpr uint32_t kItemSplit = 2u;         //   pair count and the cross-block 
 struct DevStmt {
     uint8_t op, space, kind, flags;  // flags: kStmtInjective
     uint32_t am, bm, cm;   // a, b, c mod M
-    uint32_t perm_off;     // absolute index into the arena's permutation area
+    uint32_t perm_off;     // GR_PERM: absolute index of its window (its table from b on; bm is then 0)
     uint16_t gk, gr;       // guard: active iff gk == 0 || tid % gk == gr
     uint32_t m;            // words of its array
-    uint32_t _pad2;
+    uint32_t pneed;        // GR_PERM: leading entries of its window that must be distinct (see the packer)
 };
 static_assert(sizeof(DevStmt) == 32, "DevStmt layout");
 
@@ -172,13 +172,17 @@ struct Layout {
     size_t progs_off, order_off, segbase_off, items_off, citems_off, perm_off, arena_bytes;
     uint64_t n_items, n_citems;
     size_t segmask_off, segrange_off, trace_off, wide_off, rel_off, scratch_bytes;
-    uint64_t n_segments;
+    uint64_t n_segments, perm_elems;
     std::vector<uint64_t> trace_elem, segmask_elem, perm_base;
 };
 gr_status fail(gr_status code, const char *fmt, ...);
 // Check items of a program in the general check kernel's queue (see
 // ArenaHeader::citems_off): 0 for a program the relation kernel checks.
 uint32_t check_items_of(const gr_program &p, const gr_launch &l);
+// u16 entries of the permutation windows the packer reserves for a program:
+// one per permutation instance, the instance's table from its offset b on
+// (the block's threads' entries, padded, or the whole table).
+uint64_t perm_window_elems(const gr_program &p, const gr_launch &l);
 gr_status validate_one(const gr_program *p, gr_launch l, uint32_t idx, bool tables = true);
 // Statement instances in execution order (st: statement, ctr: counter of its
 // innermost loop); returns how many run, storing at most cap (counting stops
@@ -200,7 +204,6 @@ Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n);
 // launch_perm_check).
 void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *modes, uint32_t n, const Layout &L,
                uint8_t *arena, uint32_t *table_bad = nullptr, bool range_only = false);
-bool table_to_u16(const uint32_t *tbl, uint32_t M, uint16_t *dst, bool range_only = false);
 // The launch of a repair of n packed programs at d_arena on the current
 // device: the shapes gr_tune_packed recorded for (d_arena, n), else the
 // defaults, plus the kSkip* bits `skip`; `simple`: the arena header's

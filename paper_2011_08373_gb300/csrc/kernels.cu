@@ -1277,12 +1277,12 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
     }
 }
 
-// Permutation tables of a packed batch: each table a permutation statement
-// reads must hold every index below M exactly once (the host checked the
-// range while converting the tables to u16).  CTAs take programs; per table
-// a 65,536-bit map in shared memory marks the entries and the marks are
-// counted.  The lowest failing program, plus `base`, is kept as its
-// complement in *bad (atomicMax; 0 = none).
+// Permutation windows of a packed batch: the leading pneed entries of each
+// window a permutation statement reads must be distinct (the host checked
+// that they are below M while converting them to u16).  CTAs take programs;
+// per window a 65,536-bit map in shared memory marks the entries and the
+// marks are counted.  The lowest failing program, plus `base`, is kept as
+// its complement in *bad (atomicMax; 0 = none).
 __global__ void __launch_bounds__(256) k_perm_check(const uint8_t *__restrict__ arena, uint32_t base,
                                                     uint32_t *__restrict__ bad) {
     const ArenaView V = view(arena);
@@ -1300,17 +1300,16 @@ __global__ void __launch_bounds__(256) k_perm_check(const uint8_t *__restrict__ 
         for (uint32_t s = 0; s < n_stmts; ++s) {
             const DevStmt &st = st_sh[s];
             if (st.kind != GR_PERM) continue;
-            // loop instances of one statement share its table
+            // equal instances share their window
             bool again = false;
-            for (uint32_t q = 0; q < s && !again; ++q)
-                again = st_sh[q].kind == GR_PERM && st_sh[q].perm_off == st.perm_off && st_sh[q].m == st.m;
+            for (uint32_t q = 0; q < s && !again; ++q) again = st_sh[q].kind == GR_PERM && st_sh[q].perm_off == st.perm_off;
             if (again) continue;
-            const uint32_t M = st.m, words = (M + 31u) >> 5;
+            const uint32_t M = st.m, need = st.pneed, words = (M + 31u) >> 5;
             for (uint32_t i = tid; i < words; i += blockDim.x) bits[i] = 0;
             if (tid == 0) total = 0;
             __syncthreads();
             const uint16_t *tbl = V.perm + st.perm_off;
-            for (uint32_t i = tid; i < M; i += blockDim.x) {
+            for (uint32_t i = tid; i < need; i += blockDim.x) {
                 const uint32_t v = tbl[i];
                 if (v < M) atomicOr(&bits[v >> 5], 1u << (v & 31u));  // an entry past M marks nothing
             }
@@ -1320,8 +1319,8 @@ __global__ void __launch_bounds__(256) k_perm_check(const uint8_t *__restrict__ 
             c = __reduce_add_sync(0xFFFFFFFFu, c);
             if ((tid & 31u) == 0 && c) atomicAdd(&total, c);
             __syncthreads();
-            if (tid == 0 && total != M) atomicMax(bad, ~(base + p));  // M distinct marks: a permutation
-            __syncthreads();  // the map and the count, before the next table clears them
+            if (tid == 0 && total != need) atomicMax(bad, ~(base + p));  // need distinct marks
+            __syncthreads();  // the map and the count, before the next window clears them
         }
     }
 }

@@ -378,6 +378,55 @@ __device__ bool warp_solve(LW &lw, const uint32_t *cl, uint32_t n, uint32_t forc
         lw.wc[lane] = v;
     }
     __syncwarp();
+    if (n_negk == 0) {
+        // Interval clauses: when every kept clause is a run of consecutive
+        // slots of R (a straight-line program's same-block clauses are the
+        // slots between two instances) and no negative clause is left, the
+        // minimum-weight stabbing set comes from a dynamic program over the
+        // compact slots, from the highest down.  g[k] = the least key of a
+        // set whose lowest member is k and that stabs every clause starting
+        // above k: key(k) plus the least g[j], k < j <= B_k (B_k = the least
+        // end of a clause starting above k), or key(k) alone when no clause
+        // starts above k.  The answer is the least g[k] over k <= the least
+        // clause end.  Keys add (weights; disjoint mask bits) and k's bit is
+        // below every bit of its continuation, so the least continuation
+        // gives the least key: the same (weight, lowest mask) minimum as the
+        // enumeration below.
+        bool ivl = true;
+        for (uint32_t c = lane; c < n_kept; c += 32u) {
+            const uint32_t x = pext32(lw.A[c], R);
+            const uint32_t lo = __ffs(x) - 1u, y = x >> lo;
+            const uint32_t hi = lo + 31u - __clz(y);
+            ivl = ivl && (y & (y + 1u)) == 0u;
+            lw.B[c] = lo | (hi << 8);
+        }
+        if (__all_sync(0xFFFFFFFFu, ivl)) {
+            __syncwarp();
+            uint32_t bk = 0xFFFFFFFFu, H = 0xFFFFFFFFu;
+            for (uint32_t c = 0; c < n_kept; ++c) {
+                const uint32_t e = lw.B[c], lo = e & 255u, hi = e >> 8;
+                H = min(H, hi);
+                if (lo > lane && hi < bk) bk = hi;
+            }
+            const unsigned long long keyk = ((unsigned long long)lw.wc[lane] << 32) | (1ull << lane);
+            unsigned long long g = ~0ull;
+            for (int k = (int)r - 1; k >= 0; --k) {  // uniform
+                const uint32_t b = __shfl_sync(0xFFFFFFFFu, bk, k);
+                const unsigned long long m =
+                    warp_min_u64(lane > (uint32_t)k && lane <= b && lane < r ? g : ~0ull);
+                if (lane == (uint32_t)k) g = b == 0xFFFFFFFFu ? keyk : (m == ~0ull ? ~0ull : keyk + m);
+            }
+            const unsigned long long best = warp_min_u64(lane < r && lane <= H ? g : ~0ull);
+            __syncwarp();
+            if (best == ~0ull) return false;
+            mask_out = pdep32((uint32_t)best, R) | forced;
+            uint32_t wt = (uint32_t)(best >> 32);
+            for (uint32_t t = forced; t; t &= t - 1u) wt += w[__ffs(t) - 1u];
+            weight_out = wt;
+            return true;
+        }
+        __syncwarp();
+    }
     for (uint32_t k = lane; k < n_kept; k += 32u) {
         const uint32_t c = pext32(lw.A[k], R);
         uint32_t lo = 0;

@@ -134,7 +134,7 @@ void footprint(const gr_program &p, gr_launch l, size_t *arena, size_t *scratch)
     const uint64_t segs = (uint64_t)exec_count(p) * l.blocks;
     const uint64_t tpad = (l.threads + 7u) & ~7u;
     *arena = sizeof(DevProg) + 4 + 8 + 64 + 16 * ((segs + kItemSegs - 1) / kItemSegs + exec_count(p) + 1) +
-             (size_t)(p.perm ? p.perm_len : 0) * 2 + 16;
+             16 * (size_t)check_items_of(p, l) + (size_t)perm_window_elems(p, l) * 2 + 32;
     *scratch = segs * 12 + 512 + align_to(segs * tpad, 128) * 2 + wide_bytes(1);
 }
 

@@ -218,7 +218,17 @@ def test_packer_lays_out_executed_instances(lib):
             M = p.m_shared if p.space[s] == 0 else p.m_global
             assert st[0] == p.op[s] and st[1] == p.space[s] and st[2] == p.kind[s]
             want_b = (int(p.b[s]) % M + (int(p.iter_coef[s]) % M) * ctr) % M
-            assert int(st[8:12].view(np.uint32)[0]) == want_b
+            if p.kind[s] == 2:
+                # a permutation instance reads its window, the table rotated to
+                # start at its offset (which becomes 0)
+                assert int(st[8:12].view(np.uint32)[0]) == 0
+                off, need = int(st[16:20].view(np.uint32)[0]), int(st[28:32].view(np.uint32)[0])
+                perm_off = int(arena[:128].view(np.uint64)[5])
+                win = arena[perm_off + 2 * off:perm_off + 2 * (off + need)].view(np.uint16)
+                idx = (want_b + np.arange(need)) % M
+                assert np.array_equal(win, p.perm[int(p.perm_off[s]) + idx].astype(np.uint16))
+            else:
+                assert int(st[8:12].view(np.uint32)[0]) == want_b
             assert int(st[20:22].view(np.uint16)[0]) == p.guard_k[s]
             if z + 1 < len(order):
                 k = order[z + 1][0] - 1

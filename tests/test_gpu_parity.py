@@ -477,9 +477,9 @@ def test_batch_rejects_bad_permutation_tables(gb):
     progs = [good[0], copy.deepcopy(bad[0]), good[1], copy.deepcopy(bad[1])]
     for p in (progs[1], progs[3]):
         s = int(np.nonzero(p.kind == 2)[0][0])
-        off = int(p.perm_off[s])
+        i0, i1 = _window_entries(p, s)
         p.perm = p.perm.copy()
-        p.perm[off + 1] = p.perm[off]  # a repeated entry
+        p.perm[i1] = p.perm[i0]  # a repeated entry among those the statement reads
     for fn in (lambda: gb.repair_batch(progs), lambda: gb.check_batch(progs, [0] * 4)):
         with pytest.raises(gb.GrError) as e:
             fn()
@@ -498,7 +498,8 @@ def test_batch_rejects_bad_permutation_tables(gb):
     s = int(np.nonzero(big[k].kind == 2)[0][0])
     big[k] = copy.deepcopy(big[k])
     big[k].perm = big[k].perm.copy()
-    big[k].perm[int(big[k].perm_off[s])] = big[k].perm[int(big[k].perm_off[s]) + 1]
+    i0, i1 = _window_entries(big[k], s)
+    big[k].perm[i0] = big[k].perm[i1]
     out = np.zeros(600, dtype=gb.RESULT_DTYPE)
     with pytest.raises(gb.GrError) as e:
         gb.repair_batch_raw(big, out=out)
@@ -511,19 +512,27 @@ def test_batch_rejects_bad_permutation_tables(gb):
 
 
 
+def _window_entries(p, s):
+    """Positions in p.perm of the first two table entries statement s reads:
+    threads 0 and 1 read entries b and b + 1 (mod M) of its table."""
+    M = p.m_shared if p.space[s] == 0 else p.m_global
+    off, b = int(p.perm_off[s]), int(p.b[s]) % M
+    return off + b, off + (b + 1) % M
+
+
 def _spoil(p, how):
-    """A copy of p whose first permutation table holds a repeated entry
+    """A copy of p whose first permutation statement reads a repeated entry
     ("repeat") or an entry past the array ("range")."""
     import copy
 
     q = copy.deepcopy(p)
     s = int(np.nonzero(q.kind == 2)[0][0])
-    off = int(q.perm_off[s])
+    i0, i1 = _window_entries(q, s)
     q.perm = q.perm.copy()
     if how == "repeat":
-        q.perm[off + 1] = q.perm[off]
+        q.perm[i1] = q.perm[i0]
     else:
-        q.perm[off] = (q.m_shared if q.space[s] == 0 else q.m_global) + 5
+        q.perm[i0] = (q.m_shared if q.space[s] == 0 else q.m_global) + 5
     return q, s
 
 
