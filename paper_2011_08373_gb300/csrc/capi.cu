@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <condition_variable>
 #include <functional>
@@ -340,24 +341,35 @@ uint32_t check_items_of(const gr_program &p, const gr_launch &l) {
 template <typename F>
 void parallel_over(uint32_t n, F body);
 
+// One program's share of a packed batch (entries of each part).
+struct ProgSizes {
+    uint64_t items, citems, perm, segs, trace;
+};
+Layout layout_from(const ProgSizes *z, uint32_t n);
+
+ProgSizes prog_sizes(const gr_program &p, const gr_launch &l) {
+    ProgSizes z;
+    const uint64_t x = exec_count(p), B = l.blocks;
+    // room for either expansion item layout of the program (see pack_into)
+    z.items = (x * B + kItemSegs - 1) / kItemSegs + x + 1;
+    z.citems = check_items_of(p, l);
+    z.perm = perm_window_elems(p, l);  // one window per instance (equal ones shared)
+    z.segs = x * B;
+    z.trace = align_to(x * B * t_pad_of(l.threads), 128);
+    return z;
+}
+
 Layout layout_of(const gr_program *progs, const gr_launch *ls, uint32_t n) {
-    Layout L;
-    // per-program sizes (in parallel), then their prefix sums
-    struct Sizes {
-        uint64_t items, citems, perm, segs, trace;
-    };
-    std::vector<Sizes> z(n);
+    std::vector<ProgSizes> z(n);
     parallel_over(n, [&](uint32_t lo, uint32_t hi) {
-        for (uint32_t p = lo; p < hi; ++p) {
-            const uint64_t x = exec_count(progs[p]), B = ls[p].blocks;
-            // room for either expansion item layout of the program (see pack_into)
-            z[p].items = (x * B + kItemSegs - 1) / kItemSegs + x + 1;
-            z[p].citems = check_items_of(progs[p], ls[p]);
-            z[p].perm = perm_window_elems(progs[p], ls[p]);  // one window per instance (equal ones shared)
-            z[p].segs = x * B;
-            z[p].trace = align_to(x * B * t_pad_of(ls[p].threads), 128);
-        }
+        for (uint32_t p = lo; p < hi; ++p) z[p] = prog_sizes(progs[p], ls[p]);
     });
+    return layout_from(z.data(), n);
+}
+
+// The layout of n programs from their sizes: the prefix sums.
+Layout layout_from(const ProgSizes *z, uint32_t n) {
+    Layout L;
     L.progs_off = sizeof(ArenaHeader);
     L.order_off = align_to(L.progs_off + (size_t)n * sizeof(DevProg), 16);
     L.segbase_off = align_to(L.order_off + (size_t)n * 4, 16);
@@ -423,7 +435,7 @@ class HostPool {
             next_.store(0);
             parts_ = parts;
             pending_ = parts;
-            ++gen_;
+            gen_.fetch_add(1, std::memory_order_release);
         }
         cv_.notify_all();
         uint32_t mine = 0;
@@ -449,9 +461,17 @@ class HostPool {
     void loop() {
         uint64_t seen = 0;
         for (;;) {
+            // spin a little before sleeping: the parallel steps of one batch
+            // call follow each other within microseconds, and a woken thread
+            // takes longer than that to start
+            {
+                const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(kSpinUs);
+                for (uint32_t i = 1; gen_.load(std::memory_order_acquire) == seen; ++i)
+                    if ((i & 255u) == 0 && std::chrono::steady_clock::now() > until) break;
+            }
             std::unique_lock<std::mutex> g(mu_);
-            cv_.wait(g, [&] { return gen_ != seen; });
-            seen = gen_;
+            cv_.wait(g, [&] { return gen_.load(std::memory_order_relaxed) != seen; });
+            seen = gen_.load(std::memory_order_relaxed);
             for (;;) {
                 const uint32_t k = next_.fetch_add(1);
                 if (k >= parts_) break;
@@ -468,8 +488,9 @@ class HostPool {
     std::vector<std::thread> threads_;
     std::function<void(uint32_t, uint32_t)> job_;
     std::atomic<uint32_t> next_{0};
+    static constexpr int kSpinUs = 200;
     uint32_t n_workers_ = 0, n_ = 0, per_ = 0, parts_ = 0, pending_ = 0;
-    uint64_t gen_ = 0;
+    std::atomic<uint64_t> gen_{0};  // written under mu_; read without it while spinning
 };
 
 // Run body(lo, hi) over [0, n) on the host pool (programs are independent).
@@ -478,7 +499,8 @@ void parallel_over(uint32_t n, F body) {
     HostPool::get().run(n, body);
 }
 
-gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n, bool tables = true) {
+gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n, bool tables = true,
+                       ProgSizes *sizes = nullptr) {
     if (n == 0) return fail(GR_EINVAL, "no programs");
     if (!progs || !ls) return fail(GR_EINVAL, "progs or launches is NULL");
     // the first invalid program (lowest index) is reported, as in a serial scan
@@ -489,6 +511,7 @@ gr_status validate_all(const gr_program *progs, const gr_launch *ls, uint32_t n,
     parallel_over(n, [&](uint32_t lo, uint32_t hi) {
         for (uint32_t p = lo; p < hi && p < first_bad.load(); ++p) {
             gr_status s = validate_one(&progs[p], ls[p], p, tables);
+            if (s == GR_OK && sizes) sizes[p] = prog_sizes(progs[p], ls[p]);
             if (s != GR_OK) {
                 std::lock_guard<std::mutex> g(mu);
                 if (p < first_bad.load()) {
@@ -1325,7 +1348,9 @@ gr_status gr_check_expanded(const void *d_arena, uint32_t n, const uint32_t *d_m
 gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, const int32_t *modes, uint32_t n,
                           const gr_options *opts, gr_repair_result *out, void *stream) {
     if (!out) return fail(GR_EINVAL, "out is NULL");
-    gr_status s = validate_all(progs, launches, n, false);
+    // validation and each program's share of the packed layout, in one pass
+    std::vector<ProgSizes> sizes(n);
+    gr_status s = validate_all(progs, launches, n, false, sizes.data());
     if (s != GR_OK) return s;
     if ((s = validate_opts(opts)) != GR_OK) return s;
     if (modes)
@@ -1345,14 +1370,17 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     // Chunks keep at least 128 programs, and below 2,048 programs at most two:
     // a launch of a few hundred programs takes about one program's latency
     // (one per CTA), so more, smaller chunks leave the device behind the host.
+    // The last chunk is half the size of the others: only its device work is
+    // not hidden behind packing.
     const uint32_t K = n >= 2048 ? 4u : (n >= 256 ? 2u : 1u);
     std::vector<uint32_t> lo(K + 1);
-    for (uint32_t c = 0; c <= K; ++c) lo[c] = (uint32_t)((uint64_t)n * c / K);
+    for (uint32_t c = 0; c < K; ++c) lo[c] = (uint32_t)((uint64_t)n * (2u * c) / (2u * K - 1u));
+    lo[K] = n;
     std::vector<Layout> Ls(K);
     std::vector<size_t> soff(K);
     size_t stage = 0, arena_max = 0, scratch_max = 0;
     for (uint32_t c = 0; c < K; ++c) {
-        Ls[c] = layout_of(progs + lo[c], launches + lo[c], lo[c + 1] - lo[c]);
+        Ls[c] = layout_from(sizes.data() + lo[c], lo[c + 1] - lo[c]);
         soff[c] = stage;
         stage += align_to(Ls[c].arena_bytes, 256);
         arena_max = std::max(arena_max, Ls[c].arena_bytes);
@@ -1430,19 +1458,24 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
         GR_CUDA(enqueue_repair(ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, sb, d_out + lo[c], cfg,
                                expand_grid(*ws), true, c == 0, st));
     }
-    if (any_perm) {
-        uint32_t low = 0xFFFFFFFFu;
-        if ((s = device_bad(&low)) != GR_OK) return s;
-        if (low != 0xFFFFFFFFu)
-            return fail(GR_EINVAL, "program %u stmt %u: the permutation entries it reads are not distinct indices below M", low, bad_stmt(low));
-    }
-    // the results come back through pinned staging (a DMA at full speed; a
-    // copy into the caller's pageable array would go through the driver's
-    // bounce buffer), then reach `out` in parallel, once the error word is clean
+    // The results, the permutation word and the device error word come back
+    // through pinned staging (DMAs at full speed, and no copy into pageable
+    // memory, which would block the host until the stream reaches it) with
+    // one synchronisation; `out` is written only if both words are clean.
     const size_t rb = (size_t)n * sizeof(gr_repair_result);
-    if ((s = ensure_pinned(&ws->host_out, &ws->host_out_cap, rb)) != GR_OK) return s;
+    if ((s = ensure_pinned(&ws->host_out, &ws->host_out_cap, rb + 16)) != GR_OK) return s;
+    uint32_t *words = reinterpret_cast<uint32_t *>(ws->host_out + rb);
+    words[0] = 0;
     GR_CUDA(cudaMemcpyAsync(ws->host_out, d_out, rb, cudaMemcpyDeviceToHost, st));
-    if ((s = finish_sync(ws->scratch.p, st)) != GR_OK) return s;
+    if (any_perm) GR_CUDA(cudaMemcpyAsync(&words[0], d_perm_bad, 4, cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaMemcpyAsync(&words[1], static_cast<uint32_t *>(ws->scratch.p) + 1, 4, cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    if (words[0]) {
+        const uint32_t low = ~words[0];
+        return fail(GR_EINVAL, "program %u stmt %u: the permutation entries it reads are not distinct indices below M",
+                    low, bad_stmt(low));
+    }
+    if (words[1]) return fail(GR_ECUDA, "device error word 0x%x (owner table too small)", words[1]);
     const uint8_t *staged = ws->host_out;
     parallel_over(n, [&](uint32_t a, uint32_t b) {
         memcpy(out + a, staged + (size_t)a * sizeof(gr_repair_result), (size_t)(b - a) * sizeof(gr_repair_result));

@@ -104,6 +104,32 @@ def test_validation_rejects_bad_permutation(lib):
         gb.validate(p)
 
 
+def test_permutation_check_covers_the_entries_read(lib):
+    """A permutation statement's table must hold distinct indices below M
+    where the statement reads it: from b on, one entry per thread, when its
+    address does not depend on the block; the whole table when it does.
+    Entries nobody reads are not checked."""
+    table = np.array([5, 5, 0, 1, 7, 7, 7, 7], np.uint32)  # distinct only at 2..3 (and 0 at 2)
+
+    def prog(b, c=0, blocks=1, threads=2):
+        return synth.make_program([{"op": "W", "kind": "perm", "perm": 0, "b": b, "c": c}, {"op": "R"}],
+                                  blocks=blocks, threads=threads, m_shared=8, perms=[table])
+
+    gb.validate(prog(b=2))  # reads entries 2, 3: distinct, below 8
+    for bad in (prog(b=0), prog(b=4), prog(b=3, threads=3)):  # a repeat, or 7 then 7, among those read
+        with pytest.raises(gb.GrError) as e:
+            gb.validate(bad)
+        assert e.value.code == gb.EINVAL and "permutation" in str(e.value)
+    # the block term moves the window across the table: all of it must be a permutation
+    with pytest.raises(gb.GrError):
+        gb.validate(prog(b=2, c=2, blocks=2))
+    gb.validate(prog(b=2, c=8, blocks=2))  # c = 0 mod M: every block reads entries 2, 3
+    # wrapping past the end: entries 7, 0 of a table whose others repeat
+    wrap = np.array([3, 9, 9, 9, 9, 9, 9, 4], np.uint32)
+    gb.validate(synth.make_program([{"op": "W", "kind": "perm", "perm": 0, "b": 7}, {"op": "R"}],
+                                   blocks=1, threads=2, m_shared=8, perms=[wrap]))
+
+
 def test_invalid_batch_rejected_before_device_work(lib):
     good = synth.generate("single_1x64_s8", 1)[0]
     bad = _prog(threads=5000)
