@@ -45,6 +45,17 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
+// x mod M for any 32-bit x by a reciprocal multiply: with magic =
+// floor((2^32 - 1) / M), q = floor(x magic / 2^32) is floor(x / M) or at most
+// two less (x magic / 2^32 > x / M - (1 + M) / M), so two corrections give
+// the remainder (M = 1 included).
+__device__ __forceinline__ uint32_t mod_u32(uint32_t x, uint32_t M, uint32_t magic) {
+    uint32_t r = x - __umulhi(x, magic) * M;
+    if (r >= M) r -= M;
+    if (r >= M) r -= M;
+    return r;
+}
+
 __device__ __forceinline__ uint32_t range_mask(uint32_t i, uint32_t j) {  // bits [i, j)
     const uint32_t hi = j >= 32 ? 0xFFFFFFFFu : ((1u << j) - 1u);
     return hi & ~((1u << i) - 1u);

@@ -1189,6 +1189,7 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
     uint64_t *segmask = reinterpret_cast<uint64_t *>(scratch + V.h->scratch_segmask_off);
     uint32_t *segrange = reinterpret_cast<uint32_t *>(scratch + V.h->scratch_segrange_off);
     __shared__ __align__(16) DevStmt st_sh[GR_MAX_STMTS];  // filled by 16-byte stores
+    __shared__ uint32_t mag_sh[GR_MAX_STMTS];               // floor((2^32 - 1) / M) of each statement
     __shared__ uint32_t hdr[4];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (uint64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -1203,6 +1204,8 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
             hdr[2] = P.t_pad;
         }
         __syncthreads();
+        if (threadIdx.x < GR_MAX_STMTS) mag_sh[threadIdx.x] = st_sh[threadIdx.x].m ? 0xFFFFFFFFu / st_sh[threadIdx.x].m : 0u;
+        __syncthreads();
         const uint32_t B = hdr[0], T = hdr[1], tpad = hdr[2];
         // kind 0: segments it.y..it.z-1; kind 1: block 0 of the shared-array
         // statements it.y..it.z-1 (blocks alike: no other block is read)
@@ -1211,8 +1214,9 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
             const uint32_t seg = it.w == 1u ? u * B : u;
             const uint32_t s = seg / B, blk = seg - s * B;
             const DevStmt &st = st_sh[s];
-            const uint32_t M = st.m;
-            const uint32_t base = (uint32_t)(((uint64_t)st.cm * blk + st.bm) % M);
+            const uint32_t M = st.m, mag = mag_sh[s];
+            // cm, blk < 2^16: cm blk < 2^32; then + bm < 2^17
+            const uint32_t base = mod_u32(mod_u32(st.cm * blk, M, mag) + st.bm, M, mag);
             const bool perm = st.kind == GR_PERM;
             const uint32_t step = perm ? 1u : st.am;
             uint16_t *out = traces + P.trace_off + (size_t)seg * tpad;
@@ -1220,8 +1224,8 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
             uint32_t amin = 0xFFFFu, amax = 0;
             const uint32_t nv = tpad >> 3;
             // 32-bit arithmetic: step, base < M <= 65,536 and t < 1,024
-            const uint32_t gk = st.gk, gr = st.gr, dx32 = (step * 32u) % M, dg = (step * 256u) % M;
-            uint32_t xg = (step * lane + base) % M;  // the address at t = lane of group 0
+            const uint32_t gk = st.gk, gr = st.gr, dx32 = mod_u32(step * 32u, M, mag), dg = mod_u32(step * 256u, M, mag);
+            uint32_t xg = mod_u32(step * lane + base, M, mag);  // the address at t = lane of group 0
             for (uint32_t v = lane; v < nv; v += 32) {
                 // unit v of group g holds threads 256 g + (v mod 32) + U e, e = 0..7
                 // (U = the group's units), so that a warp's 32 units read 32
@@ -1229,7 +1233,7 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
                 const uint32_t g = v >> 5, U = min(32u, nv - 32u * g), t0 = 256u * g + lane;
                 // x = (step * t + base) mod M and t mod gk, advanced by U threads at a time
                 uint32_t x = xg;
-                const uint32_t dx = U == 32u ? dx32 : (step * U) % M;
+                const uint32_t dx = U == 32u ? dx32 : mod_u32(step * U, M, mag);
                 uint32_t m = gk ? t0 % gk : 0u;
                 const uint32_t dm = gk ? U % gk : 0u;
                 // the 8 indices first, so that a permutation's 8 table loads

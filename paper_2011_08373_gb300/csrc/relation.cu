@@ -55,10 +55,10 @@ struct RelProg {
     uint32_t pend[32];      // instance i: candidate partners (bit j, j >= i)
     uint32_t rep_conf[32];  // the conflicts by pattern representative
     // table row q's access map (its representative's statement, block 0):
-    uint32_t row_am[32];    // address of thread t: (am t + bm) mod M, or
-    uint32_t row_bm[32];    //   perm[po + (t + bm) mod M] when po != ~0
-    uint32_t row_po[32];
-    uint32_t row_gk[32], row_gr[32];  // guard (gk == 0: none)
+    // {am, bm, po, gk | gr << 16}: the address of thread t is (am t + bm)
+    // mod M, or perm[po + (t + bm) mod M] when po != ~0; the guard holds iff
+    // gk == 0 or t mod gk == gr
+    uint4 row_map[32];
     uint32_t row_gmag[32];  // floor((2^32 - 1) / gk)
     uint32_t nact[32];      // active threads of each instance (for the pair count)
     uint32_t involved, n_rows, W, pitch, n_win, inj_rows, bad, p, mask;
@@ -157,11 +157,8 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
         const DevStmt &st = P.stmts[lane];
         sm.cand[row] = pext32(rp, involved);
         sm.open[row] = pext32(sym, involved);
-        sm.row_am[row] = st.am;
-        sm.row_bm[row] = st.bm;
-        sm.row_po[row] = st.kind == GR_PERM ? st.perm_off : kRelAllOnes;
-        sm.row_gk[row] = st.gk;
-        sm.row_gr[row] = st.gr;
+        sm.row_map[row] = make_uint4(st.am, st.bm, st.kind == GR_PERM ? st.perm_off : kRelAllOnes,
+                                     (uint32_t)st.gk | ((uint32_t)st.gr << 16));
         sm.row_gmag[row] = st.gk ? 0xFFFFFFFFu / st.gk : 0u;
     }
     const uint32_t inj =
@@ -218,7 +215,8 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
         }
         const uint32_t openq = *(volatile uint32_t *)&sm.open[qq];
         if (!openq) continue;  // every pair of this row is decided
-        const uint32_t gk = sm.row_gk[qq], am = sm.row_am[qq], bm = sm.row_bm[qq], po = sm.row_po[qq];
+        const uint4 mp = sm.row_map[qq];
+        const uint32_t am = mp.x, bm = mp.y, po = mp.z, gk = mp.w & 0xFFFFu;
         if (windows && po == kRelAllOnes && am * 31u + 1u < M) {
             // am * tb + bm < 2^27: the unit's first word and the run to its last
             const uint32_t start = mod_by(am * tb + bm, M, magic);
@@ -228,7 +226,7 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
         }
         bool on = t < T;
         if (gk) {
-            const uint32_t gr = sm.row_gr[qq];
+            const uint32_t gr = mp.w >> 16;
             on = on && ((gk & (gk - 1u)) == 0u ? (t & (gk - 1u)) : mod_by(t, gk, sm.row_gmag[qq])) == gr;
         }
         uint32_t a;
