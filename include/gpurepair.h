@@ -313,7 +313,7 @@ gr_status gr_repair_packed(const void *d_arena, uint32_t n, const gr_options *op
  * clause building and Solve).  The loop itself runs on the device as a CUDA
  * graph whose while-node repeats [check, step] until every program is decided
  * (bounded: GR_MAX_ITERS + 4 rounds; running past the bound sets the device
- * error word).  Results equal gr_repair_packed's.  Reads the 128-byte arena
+ * error word).  Results equal gr_repair_packed's.  Reads the 192-byte arena
  * header back to the host (a synchronising copy on stream), then enqueues the
  * expansion and the graph on stream.  n <= 65,535. */
 gr_status gr_repair_packed_wide(const void *d_arena, uint32_t n, const gr_options *opts,
@@ -414,11 +414,14 @@ gr_status gr_server_destroy(gr_server *s);
  * The scratch is a fixed 64 MiB device array inside the library, held by
  * every GPU that loads the library until the process exits; a batch whose
  * gr_pack_size scratch figure exceeds it is rejected with GR_ECAPACITY.  The
- * array's device address is looked up on the first call made on each device,
- * so make that first call before any stream capture.  The call reads the
- * 128-byte arena header back to the host (a synchronising copy on stream) and
- * allocates nothing.  All calls share the array: calls whose GPU work
- * overlaps (other streams, other threads) race and must not be issued.
+ * call reads the 192-byte arena header back to the host (a synchronising copy
+ * on stream), so it cannot be made inside a stream capture; it allocates
+ * nothing, validates opts as gr_repair_packed does and launches what
+ * gr_repair_packed launches (with the shapes gr_tune_packed recorded for
+ * (d_arena, n), else the defaults).  Device-side errors (the device error
+ * word) are not reported on this path: the word stays in the fixed array.
+ * All calls share the array: calls whose GPU work overlaps (other streams,
+ * other threads) race and must not be issued.
  * d_arena: a gr_pack arena in device memory, 256-byte aligned; d_out: n
  * results in device memory.  Enqueued on stream. */
 gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, const gr_options *opts,

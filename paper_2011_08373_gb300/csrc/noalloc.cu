@@ -12,17 +12,18 @@
 // relations, the work-queue counters and the device error word) lives in
 // `g_noalloc_scratch`, a file-scope __device__ array of kNoAllocScratchBytes.
 // Every GPU that loads the library holds it until the process exits.  Its
-// device address is looked up once per device, on the first call made with
-// that device current; make that first call before any stream capture.  The
-// cached address belongs to the device's context: after cudaDeviceReset the
-// next call on that device must not be made (the context that the address
-// belongs to is gone).  Every call shares the one array and it keeps the last
+// device address is looked up on every call (in the current context, so a
+// cudaDeviceReset between calls is harmless).  Every call reads the arena
+// header back and synchronises on it, so the call cannot be made inside a
+// stream capture.  Every call shares the one array and it keeps the last
 // call's contents: the control words are cleared on each call, everything
 // else is rewritten before it is read.  Calls that overlap on the GPU (two
 // streams, two host threads) race on the array and must not be issued; the
 // host-side lock below only orders the enqueueing.  The device error word
-// stays inside the array and is not read back: the library sizes every
-// launch from the arena header, which this call checks first.
+// stays inside the array and is not read back (the call does not wait for
+// its kernels): device-side errors are not reported on this path; the
+// library sizes every launch from the arena header, which this call checks
+// first.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -40,10 +41,7 @@ __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
 
-constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kNoAllocMaxDevices];
-int g_noalloc_sms[kNoAllocMaxDevices];
 
 }  // namespace
 void set_last_error(const char *msg);
@@ -59,25 +57,20 @@ gr_status noalloc_fail(gr_status code, const char *fmt, ...) {
     return code;
 }
 
-// Device address of the scratch array on the current device (set up once).
-gr_status noalloc_setup(int *dev_out, void **ptr_out) {
+// Device address of the scratch array and the SM count of the current device.
+gr_status noalloc_setup(int *sms_out, void **ptr_out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return noalloc_fail(GR_ECUDA, "device index %d unsupported", dev);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return noalloc_fail(GR_ECUDA, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
-        int sms = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
-        g_noalloc_sms[dev] = sms;
-        g_noalloc_ptr[dev] = p;
-    }
-    *dev_out = dev;
-    *ptr_out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return noalloc_fail(GR_ECUDA, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    *sms_out = sms;
+    *ptr_out = p;
     return GR_OK;
 }
 
@@ -94,9 +87,9 @@ extern "C" gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, c
     gr_status s = validate_opts(opts);  // the same options gr_repair_packed accepts
     if (s != GR_OK) return s;
     std::lock_guard<std::mutex> g(g_noalloc_mu);
-    int dev = 0;
+    int sms = 0;
     void *scratch = nullptr;
-    if ((s = noalloc_setup(&dev, &scratch)) != GR_OK) return s;
+    if ((s = noalloc_setup(&sms, &scratch)) != GR_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the arena header says how much scratch the batch needs
     ArenaHeader h;
@@ -115,7 +108,7 @@ extern "C" gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, c
     if (s != GR_OK) return noalloc_fail(s, "launch configuration failed");
     // the queue counters and the error word start at zero (cleared first)
     e = enqueue_repair(d_arena, n, opts_or_default(opts), scratch, kNoAllocScratchBytes, d_out, cfg,
-                       (uint32_t)g_noalloc_sms[dev] * 8u, true, true, st);
+                       (uint32_t)sms * 8u, true, true, st);
     if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "launch: %s", cudaGetErrorString(e));
     return GR_OK;
 }
