@@ -489,12 +489,12 @@ def run_ours(args, rank, world, local):
         binding.repair_plain(sub[0])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        loop_ms = 0.0
+        plain_ms = 0.0
         for p in sub:
             _, ms = binding.repair_plain_timed(p)
-            loop_ms += ms
+            plain_ms += ms
         plain = len(sub) / (time.perf_counter() - t0)
-        plain_device = len(sub) / (loop_ms * 1e-3)
+        plain_device = len(sub) / (plain_ms * 1e-3)
     strategies = None
     if rank == 0 and args.strategy_steps > 0:
         # the paper's mhs strategy against the exact (MaxSAT) strategy on the

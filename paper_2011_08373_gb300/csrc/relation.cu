@@ -30,7 +30,8 @@
 //             accesses of two rows to a word, the one whose atomic comes last
 //             sees the other row's final entry, so every conflicting pair is
 //             found; a row whose pairs are all decided stops installing.
-//   reset   — (workers) the rows and column masks used go back to empty.
+//   reset   — (workers) the column masks used go back to empty; entries
+//             carry the window's epoch, so stale ones read as empty.
 // Install works in units of one table row and 32 consecutive threads, a warp
 // per unit, so that a unit's map, guard and row are the same for the whole
 // warp: the per-unit arithmetic is done once and each access costs a
@@ -77,6 +78,22 @@ size_t rel_fixed_bytes() { return kRelFixed; }
 // 32 different banks; the window width is a multiple of 64, so a column
 // stays within its row.
 __device__ __forceinline__ uint32_t swizzle(uint32_t c) { return c ^ ((c >> 5) & 31u); }
+
+// The owner table: an entry area of u16 entries (rows of one program, W + 2
+// entries each) and, after it, a mask area of u32 column masks.  An entry
+// carries an epoch (bits 11-15; one per window, 1..31, 0 = cleared), the
+// MULTI flag (bit 10) and a thread (bits 0-9, T <= 1,024), so entries left by
+// earlier windows read as empty without being cleared; the mask area is
+// cleared after each window.  The areas never overlap, whatever the rows and
+// widths of consecutive programs.
+constexpr uint32_t kEntEpochShift = 11, kEntMulti = 1u << 10, kEntThread = kEntMulti - 1u, kMaxEpoch = 31;
+
+__device__ __forceinline__ uint32_t rel_col_cap(uint32_t table_bytes) {  // column masks (words)
+    return min(4096u, (table_bytes / 20u) & ~63u);
+}
+__device__ __forceinline__ uint32_t rel_entry_bytes(uint32_t table_bytes) {  // a multiple of 256
+    return table_bytes - 4u * rel_col_cap(table_bytes);
+}
 
 // x mod M for x < 2^31 by a reciprocal multiply: q = floor(x * magic / 2^32)
 // with magic = floor((2^32 - 1) / M) is floor(x / M) or one less, so one
@@ -137,6 +154,19 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
         __syncwarp();
         rp = sm.rep_conf[lane];
     }
+    {
+        // Pairs decided without the table: a map injective on the block's
+        // threads gives distinct threads distinct words, so two instances
+        // with that one map (whatever their guards; the self pair included)
+        // never race.  Dropping them lets a row retire once its other pairs
+        // are found.
+        const DevStmt &st = P.stmts[lane];
+        const unsigned long long key = st.kind == GR_PERM
+                                           ? (1ull << 63) | st.perm_off
+                                           : ((unsigned long long)st.am << 32) | st.bm;
+        const uint32_t same = __match_any_sync(0xFFFFFFFFu, key);
+        if (lane < S && (st.flags & kStmtInjective)) rp &= ~same;
+    }
     uint32_t involved = rp | (rp ? (1u << lane) : 0u);
     involved = __reduce_or_sync(0xFFFFFFFFu, involved);
     const bool keep = (involved >> lane) & 1u;
@@ -166,10 +196,12 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
     if (lane == 0) {
         const uint32_t M = P.m_shared;
         // R rows of W + 2 u16 entries (the extra word shifts each row by one
-        // bank) and W u32 column masks
+        // bank) in the entry area, W u32 column masks in the mask area
         uint32_t W = 0, n_win = 0;
         if (R) {
-            const uint32_t wmax = table_bytes > 4u * R ? ((table_bytes - 4u * R) / (2u * R + 4u)) & ~63u : 0u;
+            const uint32_t cap = rel_col_cap(table_bytes), ent = rel_entry_bytes(table_bytes);
+            const uint32_t per = ent / (2u * R);
+            const uint32_t wmax = per > 2u ? min(cap, (per - 2u) & ~63u) : 0u;
             const uint32_t mr = (M + 63u) & ~63u;
             W = min(wmax, mr);
             n_win = W ? (M + W - 1u) / W : 0u;
@@ -197,7 +229,8 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
 // with no open pair is skipped too: no other row needs its entries.
 template <uint32_t NT>
 __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
-                                            uint32_t *colrows, uint32_t lo) {
+                                            uint32_t *colrows, uint32_t lo, uint32_t epoch) {
+    const uint32_t tag = epoch << kEntEpochShift;
     constexpr uint32_t NWK = NT / 32 - 1;  // worker warps
     const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - 1u;
     const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W, pitch = sm.pitch;
@@ -244,10 +277,16 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
             uint16_t *e = tab + (size_t)qq * pitch + col;
             bool multi = false;  // a second thread of this row on the word
             if ((inj >> qq) & 1u) {
-                *e = (uint16_t)t;
-            } else if (atomicCAS(e, kEmpty, (uint16_t)t) != kEmpty) {
-                *e = kMulti;
-                multi = true;
+                *e = (uint16_t)(tag | t);
+            } else {
+                // the first thread of this window installs itself over the
+                // stale entry it read; any other finds this window's epoch
+                const uint16_t old = *(volatile uint16_t *)e;
+                if ((uint32_t)(old >> kEntEpochShift) == epoch ||
+                    atomicCAS(e, old, (uint16_t)(tag | t)) != old) {
+                    *e = (uint16_t)(tag | kEntMulti);
+                    multi = true;
+                }
             }
             // the rows present before this access (their bits are clear)
             uint32_t part = ~and_acq_rel(&colrows[col], ~qbit) & openq & ~qbit;
@@ -258,7 +297,8 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
             } else {
                 for (; part; part &= part - 1u) {
                     const uint32_t j = __ffs(part) - 1u;
-                    if (tab[(size_t)j * pitch + col] != (uint16_t)t) found |= 1u << j;  // another thread or MULTI
+                    // another thread, or MULTI (bit 10, above every thread)
+                    if ((tab[(size_t)j * pitch + col] & (kEntMulti | kEntThread)) != t) found |= 1u << j;
                 }
             }
         }
@@ -270,15 +310,21 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
     }
 }
 
-// The rows and column masks of the window back to empty (all ones): R rows
-// of `pitch` u16 entries and W u32 masks from the table's start, in 16-byte
-// stores (the table is 16-byte aligned and sized in whole 256-byte units).
+// The window's column masks back to empty (all ones), in 16-byte stores (W
+// is a multiple of 64 and the mask area 256-byte aligned).
 template <uint32_t NT>
-__device__ __forceinline__ void rel_reset(const RelProg &sm, uint16_t *tab) {
-    const uint32_t n16 = (sm.n_rows * sm.pitch * 2u + sm.W * 4u + 15u) >> 4;
+__device__ __forceinline__ void rel_reset(const RelProg &sm, uint32_t *colrows) {
+    uint4 *c4 = reinterpret_cast<uint4 *>(colrows);
+    for (uint32_t i = threadIdx.x - 32u; i < sm.W / 4u; i += NT - 32u)
+        c4[i] = make_uint4(kRelAllOnes, kRelAllOnes, kRelAllOnes, kRelAllOnes);
+}
+
+// The entry area back to epoch 0 (every entry empty), before the epochs wrap.
+template <uint32_t NT>
+__device__ __forceinline__ void rel_clear_entries(uint16_t *tab, uint32_t table_bytes) {
     uint4 *t4 = reinterpret_cast<uint4 *>(tab);
-    for (uint32_t i = threadIdx.x - 32u; i < n16; i += NT - 32u)
-        t4[i] = make_uint4(kRelAllOnes, kRelAllOnes, kRelAllOnes, kRelAllOnes);
+    for (uint32_t i = threadIdx.x - 32u; i < rel_entry_bytes(table_bytes) / 16u; i += NT - 32u)
+        t4[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // The program's witness rows (race_intra; one array per block, so no
@@ -387,9 +433,13 @@ __global__ void __launch_bounds__(NT, MINB)
     const uint32_t n_fast = V.h->n_fast;
     const uint32_t warp = threadIdx.x >> 5;
     constexpr uint32_t kWorkers = NT - 32u;
-    // every table entry is empty (all ones) between programs
-    for (uint32_t i = threadIdx.x; i < table_bytes / 16u; i += NT)
-        reinterpret_cast<uint4 *>(tab)[i] = make_uint4(kRelAllOnes, kRelAllOnes, kRelAllOnes, kRelAllOnes);
+    // entries at epoch 0 (empty), column masks empty (all ones)
+    uint32_t *colrows = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(tab) + rel_entry_bytes(table_bytes));
+    for (uint32_t i = threadIdx.x; i < table_bytes / 16u; i += NT) {
+        const uint32_t v = i < rel_entry_bytes(table_bytes) / 16u ? 0u : kRelAllOnes;
+        reinterpret_cast<uint4 *>(tab)[i] = make_uint4(v, v, v, v);
+    }
+    uint32_t epoch = 0;  // the workers' window count, modulo the epochs
     RelQueue Q{kRelAllOnes, 0u};
     if (warp == 0) {
         Q = rel_queue_start(V, ctrl, n_fast);
@@ -414,11 +464,15 @@ __global__ void __launch_bounds__(NT, MINB)
             if (cur.bad) {
                 if (threadIdx.x == 32) atomicOr(&ctrl[1], kErrTableTooSmall);
             } else if (R) {
-                uint32_t *colrows = reinterpret_cast<uint32_t *>(tab + (size_t)R * cur.pitch);
                 for (uint32_t w = 0; w < n_win; ++w) {
-                    rel_install<NT>(cur, V.perm, tab, colrows, w * W);
+                    if (++epoch > kMaxEpoch) {  // uniform over the workers
+                        rel_clear_entries<NT>(tab, table_bytes);
+                        asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory");
+                        epoch = 1;
+                    }
+                    rel_install<NT>(cur, V.perm, tab, colrows, w * W, epoch);
                     asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory");
-                    rel_reset<NT>(cur, tab);
+                    rel_reset<NT>(cur, colrows);
                     // the last window's reset is ordered before the next
                     // program's install by the CTA barrier below
                     if (w + 1u < n_win) asm volatile("bar.sync 1, %0;" ::"r"(kWorkers) : "memory");

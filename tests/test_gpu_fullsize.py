@@ -123,6 +123,12 @@ def test_uneven4096_full_size(gb):
     for i, w in zip(sample, want):
         for k in KEYS:
             assert got[i][k] == w[k], (i, k)
+    # the host-pointer call (chunks packed on the host, its own tuned shapes)
+    # agrees with the device-resident launch on every program and field
+    host = gb.repair_batch(progs)
+    for i in range(len(progs)):
+        for k in KEYS:
+            assert host[i][k] == got[i][k], (i, k)
     # the largest program of the batch: W(0) by sampled pairs, final mask by path independence
     p = progs[big]
     sol, _ = _expected_final(p, _w0_by_pairs(p))
