@@ -410,6 +410,12 @@ __device__ __forceinline__ void rel_fetch(RelProg &b, RelQueue &Q, const ArenaVi
     Q.p_next = item < n_fast ? V.order[item] : kRelAllOnes;
     if (item < n_fast) Q.item_next = rel_grab(ctrl);  // once past the end, no further atomics
     if (p != kRelAllOnes) rel_setup(b, &V.progs[p], masks ? masks[p] : 0u, table_bytes);
+    // the record of the program after it into L2 (its order entry has
+    // arrived by now), so that the next setup's loads do not wait on DRAM
+    if (Q.p_next != kRelAllOnes && lane < (sizeof(DevProg) + 127u) / 128u) {
+        const char *line = reinterpret_cast<const char *>(&V.progs[Q.p_next]) + 128u * lane;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+    }
     __syncwarp();
     if (lane == 0) b.p = p;
     __syncwarp();
