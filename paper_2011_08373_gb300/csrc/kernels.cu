@@ -1226,6 +1226,34 @@ __global__ void __launch_bounds__(256) k_expand(const uint8_t *__restrict__ aren
             // 32-bit arithmetic: step, base < M <= 65,536 and t < 1,024
             const uint32_t gk = st.gk, gr = st.gr, dx32 = mod_u32(step * 32u, M, mag), dg = mod_u32(step * 256u, M, mag);
             uint32_t xg = mod_u32(step * lane + base, M, mag);  // the address at t = lane of group 0
+            // An unguarded affine or strided segment whose addresses do not
+            // wrap (base + step (T - 1) < M) and step at most a chunk apart
+            // touches every chunk from base's to its last address's: its mask
+            // and range in closed form, and only the trace per unit.
+            if (!perm && gk == 0 && step <= kChunkWords && base + step * (T - 1u) < M) {
+                for (uint32_t v = lane; v < nv; v += 32) {
+                    const uint32_t g = v >> 5, U = min(32u, nv - 32u * g), t0 = 256u * g + lane;
+                    uint32_t x = xg;
+                    const uint32_t dx = U == 32u ? dx32 : mod_u32(step * U, M, mag);
+                    uint32_t w4[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (uint32_t e = 0; e < 8; ++e) {
+                        const uint32_t a = t0 + U * e < T ? x : 0u;
+                        w4[e >> 1] |= a << ((e & 1u) * 16u);
+                        x += dx;
+                        if (x >= M) x -= M;
+                    }
+                    xg += dg;
+                    if (xg >= M) xg -= M;
+                    reinterpret_cast<uint4 *>(out)[v] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                }
+                if (lane == 0) {
+                    const uint32_t hi = base + step * (T - 1u), c0 = base >> kChunkShift, c1 = hi >> kChunkShift;
+                    segmask[P.segmask_off + seg] = (c1 == 63u ? ~0ull : ((1ull << (c1 + 1u)) - 1ull)) & ~((1ull << c0) - 1ull);
+                    segrange[P.segmask_off + seg] = base | (hi << 16);
+                }
+                continue;
+            }
             for (uint32_t v = lane; v < nv; v += 32) {
                 // unit v of group g holds threads 256 g + (v mod 32) + U e, e = 0..7
                 // (U = the group's units), so that a warp's 32 units read 32
