@@ -1090,11 +1090,18 @@ gr_status upload_batch(Workspace &ws, const gr_program *progs, const gr_launch *
 }
 
 // Wait for the stream, then report the kernels' device error word.
+// The device error word's bits in words.
+const char *device_error_text(uint32_t err) {
+    if (err & kErrArgs) return "a launch's n or scratch size does not match the arena";
+    if (err & kErrTableTooSmall) return "owner table too small";
+    return "unknown";
+}
+
 gr_status finish_sync(void *d_scratch, cudaStream_t st) {
     uint32_t err = 0;
     GR_CUDA(cudaMemcpyAsync(&err, static_cast<uint32_t *>(d_scratch) + 1, 4, cudaMemcpyDeviceToHost, st));
     GR_CUDA(cudaStreamSynchronize(st));
-    if (err) return fail(GR_ECUDA, "device error word 0x%x (owner table too small)", err);
+    if (err) return fail(GR_ECUDA, "device error word 0x%x (%s)", err, device_error_text(err));
     return GR_OK;
 }
 
@@ -1475,7 +1482,7 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
         return fail(GR_EINVAL, "program %u stmt %u: the permutation entries it reads are not distinct indices below M",
                     low, bad_stmt(low));
     }
-    if (words[1]) return fail(GR_ECUDA, "device error word 0x%x (owner table too small)", words[1]);
+    if (words[1]) return fail(GR_ECUDA, "device error word 0x%x (%s)", words[1], device_error_text(words[1]));
     const uint8_t *staged = ws->host_out;
     parallel_over(n, [&](uint32_t a, uint32_t b) {
         memcpy(out + a, staged + (size_t)a * sizeof(gr_repair_result), (size_t)(b - a) * sizeof(gr_repair_result));
