@@ -221,25 +221,65 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
 
 // Install and check the accesses of the words [lo, lo + W): unit u (one per
 // worker warp at a time) covers table row q = u / cpr, threads
-// 32 c .. 32 c + 31 with c = u mod cpr (cpr = chunks of 32 threads per row);
-// lane l takes thread 32 c + l.  (q, c) steps from unit to unit without a
-// division, and every reduction is a reciprocal multiply.  When the array
-// takes several windows, an affine unit whose 32 words (a run of 31 am + 1
-// positions, cyclically) miss the window is skipped whole.  A unit of a row
-// with no open pair is skipped too: no other row needs its entries.
+// 64 c .. 64 c + 63 with c = u mod cpr (cpr = chunks of 64 threads per row);
+// lane l takes threads 64 c + l and 64 c + 32 + l.  (q, c) steps from unit
+// to unit without a division, and every reduction is a reciprocal multiply.
+// When the array takes several windows, an affine unit whose 64 words (a
+// run of 63 am + 1 positions, cyclically) miss the window is skipped whole.
+// A unit of a row with no open pair is skipped too: no other row needs its
+// entries.
+struct RelAccess {
+    uint32_t t, a;
+    bool on;  // thread active and its word in the window
+};
+
+// One access: the thread into its row's entry, then the rows already at the
+// word compared with it; returns the partners it conflicts with.
+__device__ __forceinline__ uint32_t rel_access(RelProg &sm, uint16_t *tab, uint32_t *colrows, uint32_t lo,
+                                               uint32_t qq, uint32_t openq, bool injective, RelAccess x,
+                                               uint32_t epoch) {
+    const uint32_t qbit = 1u << qq, pitch = sm.pitch, t = x.t;
+    const uint32_t tag = epoch << kEntEpochShift;
+    const uint32_t col = swizzle(x.a - lo);
+    uint16_t *e = tab + (size_t)qq * pitch + col;
+    bool multi = false;  // a second thread of this row on the word
+    if (injective) {
+        *e = (uint16_t)(tag | t);
+    } else {
+        // the first thread of this window installs itself over the stale
+        // entry it read; any other finds this window's epoch
+        const uint16_t old = *(volatile uint16_t *)e;
+        if ((uint32_t)(old >> kEntEpochShift) == epoch || atomicCAS(e, old, (uint16_t)(tag | t)) != old) {
+            *e = (uint16_t)(tag | kEntMulti);
+            multi = true;
+        }
+    }
+    // the rows present before this access (their bits are clear)
+    uint32_t part = ~and_acq_rel(&colrows[col], ~qbit) & openq & ~qbit;
+    // two threads of this row here: the self pair, and a thread other than
+    // each partner's
+    if (multi) return (openq & qbit) | part;
+    uint32_t found = 0;
+    for (; part; part &= part - 1u) {
+        const uint32_t j = __ffs(part) - 1u;
+        // another thread, or MULTI (bit 10, above every thread)
+        if ((tab[(size_t)j * pitch + col] & (kEntMulti | kEntThread)) != t) found |= 1u << j;
+    }
+    return found;
+}
+
 template <uint32_t NT>
 __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
                                             uint32_t *colrows, uint32_t lo, uint32_t epoch) {
-    const uint32_t tag = epoch << kEntEpochShift;
     constexpr uint32_t NWK = NT / 32 - 1;  // worker warps
     const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - 1u;
-    const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W, pitch = sm.pitch;
-    const uint32_t cpr = (T + 31u) >> 5, n_units = sm.n_rows * cpr, inj = sm.inj_rows;
+    const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W;
+    const uint32_t cpr = (T + 63u) >> 6, n_units = sm.n_rows * cpr, inj = sm.inj_rows;
     const bool windows = sm.n_win > 1;
     const uint32_t dq = NWK / cpr, dc = NWK - dq * cpr;
     uint32_t q = wk / cpr, c = wk - q * cpr;
     for (uint32_t u = wk; u < n_units; u += NWK) {  // uniform over the warp
-        const uint32_t tb = c << 5, t = tb + lane, qq = q;
+        const uint32_t tb = c << 6, qq = q;
         c += dc;
         q += dq;
         if (c >= cpr) {
@@ -250,60 +290,41 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
         if (!openq) continue;  // every pair of this row is decided
         const uint4 mp = sm.row_map[qq];
         const uint32_t am = mp.x, bm = mp.y, po = mp.z, gk = mp.w & 0xFFFFu;
-        if (windows && po == kRelAllOnes && am * 31u + 1u < M) {
+        if (windows && po == kRelAllOnes && am * 63u + 1u < M) {
             // am * tb + bm < 2^27: the unit's first word and the run to its last
             const uint32_t start = mod_by(am * tb + bm, M, magic);
             const uint32_t d = lo >= start ? lo - start : lo + M - start;  // (lo - start) mod M
             const uint32_t e = start >= lo ? start - lo : start + M - lo;  // (start - lo) mod M
-            if (d > am * 31u && e >= W) continue;
+            if (d > am * 63u && e >= W) continue;
         }
-        bool on = t < T;
-        if (gk) {
-            const uint32_t gr = mp.w >> 16;
-            on = on && ((gk & (gk - 1u)) == 0u ? (t & (gk - 1u)) : mod_by(t, gk, sm.row_gmag[qq])) == gr;
+        RelAccess x[2];
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t t = tb + 32u * h + lane;
+            bool on = t < T;
+            if (gk) {
+                const uint32_t gr = mp.w >> 16;
+                on = on && ((gk & (gk - 1u)) == 0u ? (t & (gk - 1u)) : mod_by(t, gk, sm.row_gmag[qq])) == gr;
+            }
+            uint32_t a;
+            if (po != kRelAllOnes) {
+                // t + bm < 2^10 + 2^16
+                a = on ? (uint32_t)__ldg(perm + po + mod_by(t + bm, M, magic)) : 0u;
+            } else {
+                // am, bm < M <= 2^16, t < 2^10: am t + bm < 2^27
+                a = mod_by(am * t + bm, M, magic);
+            }
+            x[h].t = t;
+            x[h].a = a;
+            x[h].on = on && a - lo < W;
         }
-        uint32_t a;
-        if (po != kRelAllOnes) {
-            // t + bm < 2^10 + 2^16
-            a = on ? (uint32_t)__ldg(perm + po + mod_by(t + bm, M, magic)) : 0u;
-        } else {
-            // am, bm < M <= 2^16, t < 2^10: am t + bm < 2^27
-            a = mod_by(am * t + bm, M, magic);
-        }
-        const uint32_t qbit = 1u << qq;
+        const bool injective = (inj >> qq) & 1u;
         uint32_t found = 0;
-        if (on && a - lo < W) {
-            const uint32_t col = swizzle(a - lo);
-            uint16_t *e = tab + (size_t)qq * pitch + col;
-            bool multi = false;  // a second thread of this row on the word
-            if ((inj >> qq) & 1u) {
-                *e = (uint16_t)(tag | t);
-            } else {
-                // the first thread of this window installs itself over the
-                // stale entry it read; any other finds this window's epoch
-                const uint16_t old = *(volatile uint16_t *)e;
-                if ((uint32_t)(old >> kEntEpochShift) == epoch ||
-                    atomicCAS(e, old, (uint16_t)(tag | t)) != old) {
-                    *e = (uint16_t)(tag | kEntMulti);
-                    multi = true;
-                }
-            }
-            // the rows present before this access (their bits are clear)
-            uint32_t part = ~and_acq_rel(&colrows[col], ~qbit) & openq & ~qbit;
-            if (multi) {
-                // two threads of this row here: the self pair, and a thread
-                // other than each partner's
-                found = (openq & qbit) | part;
-            } else {
-                for (; part; part &= part - 1u) {
-                    const uint32_t j = __ffs(part) - 1u;
-                    // another thread, or MULTI (bit 10, above every thread)
-                    if ((tab[(size_t)j * pitch + col] & (kEntMulti | kEntThread)) != t) found |= 1u << j;
-                }
-            }
-        }
+        if (x[0].on) found |= rel_access(sm, tab, colrows, lo, qq, openq, injective, x[0], epoch);
+        if (x[1].on) found |= rel_access(sm, tab, colrows, lo, qq, openq, injective, x[1], epoch);
         found = __reduce_or_sync(0xFFFFFFFFu, found);
         if (found) {  // uniform: close the pairs in both directions
+            const uint32_t qbit = 1u << qq;
             if (lane == 0) atomicAnd(&sm.open[qq], ~found);
             if (((found & ~qbit) >> lane) & 1u) atomicAnd(&sm.open[lane], ~qbit);
         }
