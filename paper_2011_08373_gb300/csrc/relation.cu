@@ -103,13 +103,13 @@ __device__ __forceinline__ uint32_t mod_by(uint32_t x, uint32_t M, uint32_t magi
     return r >= M ? r - M : r;
 }
 
-// *p &= v, returning the old value, with acquire-release order at CTA scope:
-// the caller's earlier shared-memory writes are visible to any thread whose
-// atomic on *p comes later, and its later reads see every write made before
-// the atomics that precede its own.
-__device__ __forceinline__ uint32_t and_acq_rel(uint32_t *p, uint32_t v) {
+// The word at shared-memory address a &= v, returning the old value, with
+// acquire-release order at CTA scope: the caller's earlier shared-memory
+// writes are visible to any thread whose atomic on the word comes later, and
+// its later reads see every write made before the atomics that precede its
+// own.
+__device__ __forceinline__ uint32_t and_acq_rel(uint32_t a, uint32_t v) {
     uint32_t old;
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
     asm volatile("atom.acq_rel.cta.shared::cta.and.b32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
     return old;
 }
@@ -228,6 +228,8 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
 // run of 63 am + 1 positions, cyclically) miss the window is skipped whole.
 // A unit of a row with no open pair is skipped too: no other row needs its
 // entries.
+constexpr uint32_t kRelTPL = 2;  // threads per lane of an install unit
+
 struct RelAccess {
     uint32_t t, a;
     bool on;  // thread active and its word in the window
@@ -235,7 +237,7 @@ struct RelAccess {
 
 // One access: the thread into its row's entry, then the rows already at the
 // word compared with it; returns the partners it conflicts with.
-__device__ __forceinline__ uint32_t rel_access(RelProg &sm, uint16_t *tab, uint32_t *colrows, uint32_t lo,
+__device__ __forceinline__ uint32_t rel_access(RelProg &sm, uint16_t *tab, uint32_t colrows_s, uint32_t lo,
                                                uint32_t qq, uint32_t openq, bool injective, RelAccess x,
                                                uint32_t epoch) {
     const uint32_t qbit = 1u << qq, pitch = sm.pitch, t = x.t;
@@ -255,7 +257,7 @@ __device__ __forceinline__ uint32_t rel_access(RelProg &sm, uint16_t *tab, uint3
         }
     }
     // the rows present before this access (their bits are clear)
-    uint32_t part = ~and_acq_rel(&colrows[col], ~qbit) & openq & ~qbit;
+    uint32_t part = ~and_acq_rel(colrows_s + 4u * col, ~qbit) & openq & ~qbit;
     // two threads of this row here: the self pair, and a thread other than
     // each partner's
     if (multi) return (openq & qbit) | part;
@@ -274,12 +276,12 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
     constexpr uint32_t NWK = NT / 32 - 1;  // worker warps
     const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - 1u;
     const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W;
-    const uint32_t cpr = (T + 63u) >> 6, n_units = sm.n_rows * cpr, inj = sm.inj_rows;
+    const uint32_t cpr = (T + 32u * kRelTPL - 1u) / (32u * kRelTPL), n_units = sm.n_rows * cpr, inj = sm.inj_rows;
     const bool windows = sm.n_win > 1;
     const uint32_t dq = NWK / cpr, dc = NWK - dq * cpr;
     uint32_t q = wk / cpr, c = wk - q * cpr;
     for (uint32_t u = wk; u < n_units; u += NWK) {  // uniform over the warp
-        const uint32_t tb = c << 6, qq = q;
+        const uint32_t tb = c * (32u * kRelTPL), qq = q;
         c += dc;
         q += dq;
         if (c >= cpr) {
@@ -290,16 +292,16 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
         if (!openq) continue;  // every pair of this row is decided
         const uint4 mp = sm.row_map[qq];
         const uint32_t am = mp.x, bm = mp.y, po = mp.z, gk = mp.w & 0xFFFFu;
-        if (windows && po == kRelAllOnes && am * 63u + 1u < M) {
+        if (windows && po == kRelAllOnes && am * (32u * kRelTPL - 1u) + 1u < M) {
             // am * tb + bm < 2^27: the unit's first word and the run to its last
             const uint32_t start = mod_by(am * tb + bm, M, magic);
             const uint32_t d = lo >= start ? lo - start : lo + M - start;  // (lo - start) mod M
             const uint32_t e = start >= lo ? start - lo : start + M - lo;  // (start - lo) mod M
-            if (d > am * 63u && e >= W) continue;
+            if (d > am * (32u * kRelTPL - 1u) && e >= W) continue;
         }
-        RelAccess x[2];
+        RelAccess x[kRelTPL];
 #pragma unroll
-        for (uint32_t h = 0; h < 2; ++h) {
+        for (uint32_t h = 0; h < kRelTPL; ++h) {
             const uint32_t t = tb + 32u * h + lane;
             bool on = t < T;
             if (gk) {
@@ -319,9 +321,11 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
             x[h].on = on && a - lo < W;
         }
         const bool injective = (inj >> qq) & 1u;
+        const uint32_t colrows_s = (uint32_t)__cvta_generic_to_shared(colrows);
         uint32_t found = 0;
-        if (x[0].on) found |= rel_access(sm, tab, colrows, lo, qq, openq, injective, x[0], epoch);
-        if (x[1].on) found |= rel_access(sm, tab, colrows, lo, qq, openq, injective, x[1], epoch);
+#pragma unroll
+        for (uint32_t h = 0; h < kRelTPL; ++h)
+            if (x[h].on) found |= rel_access(sm, tab, colrows_s, lo, qq, openq, injective, x[h], epoch);
         found = __reduce_or_sync(0xFFFFFFFFu, found);
         if (found) {  // uniform: close the pairs in both directions
             const uint32_t qbit = 1u << qq;
