@@ -377,8 +377,9 @@ gr_status gr_check_expanded(const void *d_arena, uint32_t n, const uint32_t *d_m
 /* ---------------------------------------------------------------------- */
 
 /* A server repairs single programs submitted at any time (the repair loop of
- * Algorithm 1, Section 2.4, per request; each result equals gr_repair's).  It owns n_slots (1..16) launch slots, each with
- * its own stream and device buffers; together they take mem_budget_bytes of
+ * Algorithm 1, Section 2.4, per request; each result equals gr_repair's).
+ * It owns n_slots (1..16) launch slots, each with its own stream and
+ * device buffers; together they take mem_budget_bytes of
  * device memory, allocated here, and nothing more is allocated while
  * serving.  A dispatcher thread admits queued requests in arrival order into
  * whichever slot is idle, as many as fit the slot's share of the budget and

@@ -1008,14 +1008,19 @@ gr_status tune_cfg(const Workspace &ws, const void *d_arena, uint32_t n, void *d
     GR_CUDA(cudaEventCreate(&e0));
     GR_CUDA(cudaEventCreate(&e1));
     auto timed = [&](auto launch, float *ms) -> cudaError_t {
+        // the first run warms the shape; the fastest of the next three counts
+        // (single runs vary by several percent, enough to pick the wrong shape)
         cudaError_t e = cudaSuccess;
-        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first run warms the shape
+        *ms = 1e30f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
             if ((e = cudaMemsetAsync(d_scratch, 0, 16, st)) != cudaSuccess) break;
             if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
             if ((e = launch()) != cudaSuccess) break;
             if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
             if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-            e = cudaEventElapsedTime(ms, e0, e1);
+            float t = 0;
+            if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+            if (rep > 0 && t < *ms) *ms = t;
         }
         return e;
     };
