@@ -157,3 +157,41 @@ def test_clause_of_all_slots(gb):
         for g in (gb.repair_batch([p], strategy=strategy)[0], gb.repair_plain(p, strategy=strategy)):
             assert (g["status"], g["iters"], g["traj"]) == (1, 1, [0])
             assert g["clauses"] == cls
+
+
+def test_launch_checks_n_and_scratch_against_the_arena(gb):
+    """A device-resident repair given a program count or a scratch size that
+    does not match its packed arena does no work: every kernel compares them
+    with the arena header first, leaves the results untouched and sets the
+    argument bit (4) of the device error word (scratch word 1).  A matching
+    call afterwards repairs the batch as usual."""
+    import ctypes as C
+
+    import torch
+
+    progs = synth.generate("batch1024_4x256_s24", 6, blocks=2, threads=32, n_stmts=8, m_words=128)
+    progs += [synth.generate("interblock256_64x256_s16", 1, blocks=3, threads=32, n_stmts=5, m_words=512)[0]]
+    db = gb.DeviceBatch(progs)
+    n = len(progs)
+    lib = gb.lib()
+    scratch_words = db.scratch.view(torch.uint8)
+    base = db._scratch_ptr - db.scratch.data_ptr()
+
+    def call(n_arg, scratch_bytes):
+        db.out.view(torch.uint8).fill_(0xA5)
+        scratch_words[base:base + 256].zero_()
+        gb._check(lib.gr_repair_packed(C.c_void_p(db._arena_ptr), n_arg, None, C.c_void_p(db._scratch_ptr),
+                                       C.c_uint64(scratch_bytes), C.c_void_p(db._out_ptr), None))
+        torch.cuda.synchronize()
+        err = int(scratch_words[base + 4:base + 8].cpu().numpy().view(np.uint32)[0])
+        untouched = bool((db.out.view(torch.uint8) == 0xA5).all())
+        return err, untouched
+
+    for n_arg, sb in ((n - 1, db.scratch_bytes), (n, db.scratch_bytes - 256)):
+        err, untouched = call(n_arg, sb)
+        assert err & 4 and untouched, (n_arg, sb, err)
+    err, untouched = call(n, db.scratch_bytes)
+    assert err == 0 and not untouched
+    want = oracle.repair_batch(progs, n_threads=4)
+    for g, w in zip(db.results(), want):
+        _same(g, w)
