@@ -220,8 +220,8 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
 }
 
 // Install and check the accesses of the words [lo, lo + W): unit u (one per
-// worker warp at a time) covers table row q = u / cpr, threads
-// 64 c .. 64 c + 63 with c = u mod cpr (cpr = chunks of 64 threads per row);
+// worker warp at a time) covers table row q = u mod R, threads
+// 64 c .. 64 c + 63 with c = u / R (R rows, cpr chunks of 64 threads each);
 // lane l takes threads 64 c + l and 64 c + 32 + l.  (q, c) steps from unit
 // to unit without a division, and every reduction is a reciprocal multiply.
 // When the array takes several windows, an affine unit whose 64 words (a
@@ -278,15 +278,18 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
     const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W;
     const uint32_t cpr = (T + 32u * kRelTPL - 1u) / (32u * kRelTPL), n_units = sm.n_rows * cpr, inj = sm.inj_rows;
     const bool windows = sm.n_win > 1;
-    const uint32_t dq = NWK / cpr, dc = NWK - dq * cpr;
-    uint32_t q = wk / cpr, c = wk - q * cpr;
+    // units chunk by chunk across the rows (u = c R + q): a pair that
+    // conflicts near the low threads is found early, its rows retire, and
+    // their later chunks are skipped
+    const uint32_t R = sm.n_rows, dc = NWK / R, dq = NWK - dc * R;
+    uint32_t c = wk / R, q = wk - c * R;
     for (uint32_t u = wk; u < n_units; u += NWK) {  // uniform over the warp
         const uint32_t tb = c * (32u * kRelTPL), qq = q;
-        c += dc;
         q += dq;
-        if (c >= cpr) {
-            c -= cpr;
-            ++q;
+        c += dc;
+        if (q >= R) {
+            q -= R;
+            ++c;
         }
         const uint32_t openq = *(volatile uint32_t *)&sm.open[qq];
         if (!openq) continue;  // every pair of this row is decided
