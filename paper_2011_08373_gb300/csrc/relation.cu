@@ -60,7 +60,7 @@ struct RelProg {
     // mod M, or perm[po + (t + bm) mod M] when po != ~0; the guard holds iff
     // gk == 0 or t mod gk == gr
     uint4 row_map[32];
-    uint32_t row_gmag[32];  // floor((2^32 - 1) / gk)
+    uint32_t row_nact[32];  // threads of a block the row's guard lets through
     uint32_t nact[32];      // active threads of each instance (for the pair count)
     uint32_t involved, n_rows, W, pitch, n_win, inj_rows, bad, p, mask;
     uint32_t M, Mmagic;     // the shared array's words; floor((2^32 - 1) / M)
@@ -189,7 +189,7 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
         sm.open[row] = pext32(sym, involved);
         sm.row_map[row] = make_uint4(st.am, st.bm, st.kind == GR_PERM ? st.perm_off : kRelAllOnes,
                                      (uint32_t)st.gk | ((uint32_t)st.gr << 16));
-        sm.row_gmag[row] = st.gk ? 0xFFFFFFFFu / st.gk : 0u;
+        sm.row_nact[row] = guard_count(P.threads, st.gk, st.gr);
     }
     const uint32_t inj =
         __reduce_or_sync(0xFFFFFFFFu, keep && (P.stmts[lane].flags & kStmtInjective) ? 1u << row : 0u);
@@ -220,9 +220,11 @@ __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_
 }
 
 // Install and check the accesses of the words [lo, lo + W): unit u (one per
-// worker warp at a time) covers table row q = u mod R, threads
-// 64 c .. 64 c + 63 with c = u / R (R rows, cpr chunks of 64 threads each);
-// lane l takes threads 64 c + l and 64 c + 32 + l.  (q, c) steps from unit
+// worker warp at a time) covers table row q = u mod R, active threads
+// 64 c .. 64 c + 63 of the row with c = u / R (R rows, cpr chunks of 64
+// threads each; a guarded row's active threads are its guard's residue
+// class, numbered in order); lane l takes active threads 64 c + l and
+// 64 c + 32 + l.  (q, c) steps from unit
 // to unit without a division, and every reduction is a reciprocal multiply.
 // When the array takes several windows, an affine unit whose 64 words (a
 // run of 63 am + 1 positions, cyclically) miss the window is skipped whole.
@@ -276,6 +278,8 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
     constexpr uint32_t NWK = NT / 32 - 1;  // worker warps
     const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - 1u;
     const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W;
+    // every row gets the chunks of the unguarded width; a guarded row's
+    // later chunks are empty and skipped at once
     const uint32_t cpr = (T + 32u * kRelTPL - 1u) / (32u * kRelTPL), n_units = sm.n_rows * cpr, inj = sm.inj_rows;
     const bool windows = sm.n_win > 1;
     // units chunk by chunk across the rows (u = c R + q): a pair that
@@ -291,26 +295,32 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
             q -= R;
             ++c;
         }
+        const uint32_t nq = sm.row_nact[qq];
+        if (tb >= nq) continue;  // past the row's active threads
         const uint32_t openq = *(volatile uint32_t *)&sm.open[qq];
         if (!openq) continue;  // every pair of this row is decided
         const uint4 mp = sm.row_map[qq];
         const uint32_t am = mp.x, bm = mp.y, po = mp.z, gk = mp.w & 0xFFFFu;
-        if (windows && po == kRelAllOnes && am * (32u * kRelTPL - 1u) + 1u < M) {
-            // am * tb + bm < 2^27: the unit's first word and the run to its last
-            const uint32_t start = mod_by(am * tb + bm, M, magic);
-            const uint32_t d = lo >= start ? lo - start : lo + M - start;  // (lo - start) mod M
-            const uint32_t e = start >= lo ? start - lo : start + M - lo;  // (start - lo) mod M
-            if (d > am * (32u * kRelTPL - 1u) && e >= W) continue;
+        // the unit's threads are the row's active ones: t = gr + g i, i in
+        // [tb, tb + 64) below nq (g = gk, or 1 with no guard)
+        const uint32_t g = gk ? gk : 1u, gr = mp.w >> 16;
+        if (windows && po == kRelAllOnes) {
+            // am (gr + g tb) < 2^16 2^10: the unit's first word; its words step
+            // by am g mod M, a run of 63 steps
+            const uint32_t start = mod_by(am * (gr + g * tb) + bm, M, magic);
+            const uint32_t step = mod_u32(am * g, M, magic);
+            if (step * (32u * kRelTPL - 1u) + 1u < M) {
+                const uint32_t d = lo >= start ? lo - start : lo + M - start;  // (lo - start) mod M
+                const uint32_t e = start >= lo ? start - lo : start + M - lo;  // (start - lo) mod M
+                if (d > step * (32u * kRelTPL - 1u) && e >= W) continue;
+            }
         }
         RelAccess x[kRelTPL];
 #pragma unroll
         for (uint32_t h = 0; h < kRelTPL; ++h) {
-            const uint32_t t = tb + 32u * h + lane;
-            bool on = t < T;
-            if (gk) {
-                const uint32_t gr = mp.w >> 16;
-                on = on && ((gk & (gk - 1u)) == 0u ? (t & (gk - 1u)) : mod_by(t, gk, sm.row_gmag[qq])) == gr;
-            }
+            const uint32_t i = tb + 32u * h + lane;
+            const bool on = i < nq;
+            const uint32_t t = on ? gr + g * i : 0u;  // < T
             uint32_t a;
             if (po != kRelAllOnes) {
                 // t + bm < 2^10 + 2^16
