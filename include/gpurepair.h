@@ -346,6 +346,21 @@ gr_status gr_relation_packed(const void *d_arena, uint32_t n, void *d_scratch, u
 gr_status gr_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                          uint64_t scratch_bytes, gr_repair_result *d_out, void *stream);
 
+/* The repair of gr_repair_packed as one launch, whatever the autotuner
+ * picked: the relation kernel computes each program's relation, then its
+ * warps run the loop of Algorithm 1 (Section 2.4) on the relations, each
+ * program's loop waiting for a flag its relation sets (a bounded wait:
+ * when it runs out, that program's result is not written, the warp takes
+ * no further program and bit 3, value 8, of the device error word at byte 4
+ * of d_scratch is set).  Only for a batch of straight-line
+ * programs on the shared array with no general program (the packer's simple
+ * flag, no program needing expanded traces); any other batch returns
+ * GR_EINVAL with nothing launched.  Reads the arena header back and
+ * synchronises on it (not capturable), then enqueues the launch on stream.
+ * Results into d_out as gr_repair_packed writes them. */
+gr_status gr_relation_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                                  uint64_t scratch_bytes, gr_repair_result *d_out, void *stream);
+
 /* Autotuner: time every CTA shape the check kernels are built for (threads
  * per CTA x CTAs per SM, with the owner-table budget that shape leaves) on
  * this arena, remember the fastest for later gr_repair_packed /
@@ -354,8 +369,11 @@ gr_status gr_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts
  * 0-7 index the relation kernel's shape, bits 8-11 the general check
  * kernel's, bit 12 is set when that kernel's grid is cut so that every CTA
  * gets the same number of programs (fewer CTAs than fit, no partly filled
- * last round).  Runs the check kernels several times, then one repair with
- * the shapes picked into d_out, and synchronises the stream.  The
+ * last round), bit 16 when a batch of straight-line programs (no general
+ * one) repairs faster with the relation kernel running the loop too, in one
+ * launch, than with the two kernels (both are timed).  Runs the kernels
+ * several times, then one repair with the choices picked into d_out, and
+ * synchronises the stream.  The
  * host-pointer batch calls tune the same way by themselves, once per batch
  * size class. */
 gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,

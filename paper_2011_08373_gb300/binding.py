@@ -84,7 +84,7 @@ EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair"
            "gr_repair_packed_noalloc", "gr_server_create", "gr_server_submit", "gr_server_poll",
            "gr_server_drain", "gr_server_stats", "gr_server_destroy", "gr_tune_packed",
            "gr_repair_packed_wide", "gr_check_expanded", "gr_relation_packed", "gr_loop_packed",
-           "gr_repair_plain_timed"]
+           "gr_repair_plain_timed", "gr_relation_loop_packed"]
 
 
 def lib():
@@ -137,6 +137,7 @@ def lib():
             L.gr_check_expanded.argtypes = L.gr_check_packed.argtypes
             L.gr_relation_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p]
             L.gr_loop_packed.argtypes = L.gr_repair_packed.argtypes
+            L.gr_relation_loop_packed.argtypes = L.gr_repair_packed.argtypes
             for name in EXPORTS[2:]:
                 getattr(L, name).restype = C.c_int32
             _lib = L
@@ -483,6 +484,9 @@ class DeviceBatch:
         # others need their traces expanded
         self.n_fast = int(host[120:124].view(np.uint32)[0])
         self.has_general = self.n_fast < self.n
+        # the packer's kArenaSimple flag: straight-line programs on the shared
+        # array only; with no general program, a tuned run() is one launch
+        self.simple = bool(int(host[108:112].view(np.uint32)[0]) & 1)
 
     def run(self, stream: Optional[int] = None) -> None:
         import torch
@@ -548,6 +552,16 @@ class DeviceBatch:
         _check(lib().gr_loop_packed(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
                                     C.c_void_p(self._scratch_ptr), self.scratch_bytes,
                                     C.c_void_p(self._out_ptr), C.c_void_p(st)))
+
+    def relation_loop(self, stream: Optional[int] = None) -> None:
+        """The whole repair as one launch (gr_relation_loop_packed); only for
+        straight-line programs on the shared array with no general one."""
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_relation_loop_packed(C.c_void_p(self._arena_ptr), self.n, C.byref(self.opts),
+                                             C.c_void_p(self._scratch_ptr), self.scratch_bytes,
+                                             C.c_void_p(self._out_ptr), C.c_void_p(st)))
 
     def check(self, masks, stream: Optional[int] = None, expanded: bool = False):
         """One check per program under masks[p] (gr_check_packed; with

@@ -43,7 +43,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(INCLUDE, "gpurepair.h"), os.path.join(CSRC, "engine.cuh"),
-               os.path.join(CSRC, "device.cuh")]
+               os.path.join(CSRC, "device.cuh"), os.path.join(CSRC, "loop.cuh")]
     objs = []
     jobs = []
     for src in SOURCES:

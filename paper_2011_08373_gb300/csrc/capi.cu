@@ -400,7 +400,7 @@ Layout layout_from(const ProgSizes *z, uint32_t n) {
     L.trace_off = align_to(L.segrange_off + seg_total * 4, 256);
     L.wide_off = align_to(L.trace_off + trace_total * 2, 256);
     L.rel_off = align_to(L.wide_off + wide_bytes(n), 256);
-    L.scratch_bytes = align_to(L.rel_off + (size_t)n * sizeof(gr_witnesses), 256);
+    L.scratch_bytes = align_to(rel_flags_off(L.rel_off, n) + (size_t)n * 4u, 256);
     return L;
 }
 
@@ -827,7 +827,13 @@ uint32_t ceil_log2(uint64_t x) {
 // kSkip* bits of the batch.
 struct Tuned {
     uint32_t rel_shape = 0, gen_shape = 0, s_max = GR_MAX_STMTS, skip = 0, simple = 0;
+    uint64_t rel_off = 0;  // the arena's scratch relation offset when known (0: no fused loop)
+    uint32_t fuse = 0;     // the relation kernel runs the loop too (one launch), when timed faster
 };
+
+// The relation kernel's CTA shape that also runs the loop (kRelShapes[2]: 512
+// threads, two per SM: 16 loop warps whose records fit its table).
+constexpr uint32_t kRelFusedShape = 2;
 
 struct DeviceBuf {
     void *p = nullptr;
@@ -966,6 +972,18 @@ LaunchCfg full_cfg(const Workspace &ws, uint32_t n, const Tuned &t) {
     c.loop_grid = loop_grid(ws, n, t.simple != 0);
     c.skip = t.skip;
     c.simple = t.simple;
+    // a batch of simple programs with no general one, where the autotuner
+    // timed it faster: the relation kernel runs the loop too, overlapping it
+    // with the relation tail
+    c.fused = RelCfg{0, 0, 0};
+    c.flags_off = 0;
+    if (t.fuse && t.rel_off && t.simple && (t.skip & kSkipGeneral) && !(t.skip & kSkipFast)) {
+        const RelCfg f = rel_cfg(ws, n, kRelFusedShape);
+        if (f.table_bytes && relation_loop_fits(f.table_bytes)) {
+            c.fused = f;
+            c.flags_off = rel_flags_off(t.rel_off, n);
+        }
+    }
     return c;
 }
 
@@ -999,6 +1017,26 @@ SizeClass size_class(const gr_program *progs, const gr_launch *ls, uint32_t n) {
 // on the general programs' relations, and return the fastest of each.  The
 // general traces must be expanded into d_scratch.  Synchronises the stream;
 // leaves the scratch control words to be cleared by the next launch.
+// The device time of launch(): the first run warms the shape, the fastest of
+// the next three counts (single runs vary by several percent, enough to pick
+// the wrong shape).  The scratch's control words are cleared before each run.
+template <class F>
+cudaError_t best_of_runs(F launch, void *d_scratch, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st, float *ms) {
+    cudaError_t e = cudaSuccess;
+    *ms = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        if ((e = cudaMemsetAsync(d_scratch, 0, 16, st)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+        if ((e = launch()) != cudaSuccess) break;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float t = 0;
+        if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+        if (rep > 0 && t < *ms) *ms = t;
+    }
+    return e;
+}
+
 gr_status tune_cfg(const Workspace &ws, const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
                    cudaStream_t st, uint32_t s_max, uint32_t skip, Tuned *out) {
     Tuned t;
@@ -1007,23 +1045,7 @@ gr_status tune_cfg(const Workspace &ws, const void *d_arena, uint32_t n, void *d
     cudaEvent_t e0, e1;
     GR_CUDA(cudaEventCreate(&e0));
     GR_CUDA(cudaEventCreate(&e1));
-    auto timed = [&](auto launch, float *ms) -> cudaError_t {
-        // the first run warms the shape; the fastest of the next three counts
-        // (single runs vary by several percent, enough to pick the wrong shape)
-        cudaError_t e = cudaSuccess;
-        *ms = 1e30f;
-        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-            if ((e = cudaMemsetAsync(d_scratch, 0, 16, st)) != cudaSuccess) break;
-            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-            if ((e = launch()) != cudaSuccess) break;
-            if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
-            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-            float t = 0;
-            if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
-            if (rep > 0 && t < *ms) *ms = t;
-        }
-        return e;
-    };
+    auto timed = [&](auto launch, float *ms) { return best_of_runs(launch, d_scratch, e0, e1, st, ms); };
     cudaError_t e = cudaSuccess;
     if (!(skip & kSkipFast)) {
         float best = 1e30f;
@@ -1098,6 +1120,7 @@ gr_status upload_batch(Workspace &ws, const gr_program *progs, const gr_launch *
 // The device error word's bits in words.
 const char *device_error_text(uint32_t err) {
     if (err & kErrArgs) return "a launch's n or scratch size does not match the arena";
+    if (err & kErrStall) return "a bounded wait for another CTA's result ran out";
     if (err & kErrTableTooSmall) return "owner table too small";
     return "unknown";
 }
@@ -1115,7 +1138,8 @@ gr_status finish_sync(void *d_scratch, cudaStream_t st) {
 namespace gr {
 // Launch shape of the persistent repair for n packed programs on the current
 // device (used by gr_repair_packed_noalloc in noalloc.cu).
-LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, bool simple, gr_status *status) {
+LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, bool simple, uint64_t rel_off,
+                            gr_status *status) {
     Workspace *ws;
     LaunchCfg c{};
     if ((*status = current_ws(&ws)) != GR_OK) return c;
@@ -1125,6 +1149,7 @@ LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, bool
     Tuned t = it != ws->arena_shape.end() ? it->second : Tuned{};
     t.skip |= skip;
     t.simple = simple ? 1u : 0u;
+    t.rel_off = rel_off;
     return full_cfg(*ws, n, t);
 }
 
@@ -1293,6 +1318,41 @@ gr_status gr_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts
     return GR_OK;
 }
 
+gr_status gr_relation_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
+                                  uint64_t scratch_bytes, gr_repair_result *d_out, void *stream) {
+    if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
+    if ((reinterpret_cast<uintptr_t>(d_arena) | reinterpret_cast<uintptr_t>(d_scratch)) % 256)
+        return fail(GR_EINVAL, "d_arena and d_scratch must be 256-byte aligned");
+    gr_status s = validate_opts(opts);
+    if (s != GR_OK) return s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ArenaHeader h;
+    GR_CUDA(cudaMemcpyAsync(&h, d_arena, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    if (h.magic != kArenaMagic || h.n_progs != n) return fail(GR_EINVAL, "d_arena is not a packed arena of %u programs", n);
+    if (scratch_bytes < h.scratch_bytes) return fail(GR_ECAPACITY, "scratch needs %llu bytes", (unsigned long long)h.scratch_bytes);
+    // the tuned relation shape when gr_tune_packed ran on this arena; the
+    // single launch itself always takes the 512 x 2 shape
+    auto it = ws->arena_shape.find({d_arena, n});
+    Tuned t = it != ws->arena_shape.end() ? it->second : Tuned{};
+    t.skip = skip_bits(h);
+    t.s_max = h.s_max;
+    t.simple = (h.flags & kArenaSimple) ? 1u : 0u;
+    t.rel_off = h.scratch_rel_off;
+    t.fuse = 1;
+    const LaunchCfg cfg = full_cfg(*ws, n, t);
+    if (!cfg.flags_off)
+        return fail(GR_EINVAL, "the batch cannot run in one launch: it needs straight-line programs on the "
+                               "shared array only, with no general program");
+    GR_CUDA(enqueue_repair(d_arena, n, opts_or_default(opts), d_scratch, scratch_bytes, d_out, cfg, expand_grid(*ws),
+                           false, true, st));
+    return GR_OK;
+}
+
 gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                          uint64_t scratch_bytes, gr_repair_result *d_out, void *stream, uint32_t *shape_out) {
     if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");
@@ -1316,12 +1376,36 @@ gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts
     Tuned t;
     if ((s = tune_cfg(*ws, d_arena, n, d_scratch, scratch_bytes, st, h.s_max, skip, &t)) != GR_OK) return s;
     t.simple = (h.flags & kArenaSimple) ? 1u : 0u;
+    t.rel_off = h.scratch_rel_off;
+    // one launch (the relation kernel runs the loop) or two: whichever
+    // repairs the batch faster.  The single launch saves a launch gap and
+    // overlaps the loop with the relation tail, but its loop warps share the
+    // SMs with up to 32 warps and have fewer registers than the loop kernel's.
+    Tuned tf = t;
+    tf.fuse = 1;
+    if (full_cfg(*ws, n, tf).flags_off) {
+        const gr_options o = opts_or_default(opts);
+        cudaEvent_t e0, e1;
+        GR_CUDA(cudaEventCreate(&e0));
+        GR_CUDA(cudaEventCreate(&e1));
+        float ms_two = 0, ms_one = 0;
+        auto repair_with = [&](const Tuned &x) {
+            return [&, x] { return enqueue_repair(d_arena, n, o, d_scratch, scratch_bytes, d_out,
+                                                  full_cfg(*ws, n, x), expand_grid(*ws), false, true, st); };
+        };
+        cudaError_t e = best_of_runs(repair_with(t), d_scratch, e0, e1, st, &ms_two);
+        if (e == cudaSuccess) e = best_of_runs(repair_with(tf), d_scratch, e0, e1, st, &ms_one);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess) return cuda_fail(e, "autotuner");
+        if (ms_one < ms_two) t.fuse = 1;
+    }
     ws->arena_shape[{d_arena, n}] = t;
     // one repair with the picked shapes leaves d_out filled, as documented
     GR_CUDA(enqueue_repair(d_arena, n, opts_or_default(opts), d_scratch, scratch_bytes, d_out, full_cfg(*ws, n, t),
                            expand_grid(*ws), false, true, st));
     GR_CUDA(cudaStreamSynchronize(st));
-    if (shape_out) *shape_out = t.rel_shape | (t.gen_shape << 8);
+    if (shape_out) *shape_out = t.rel_shape | (t.gen_shape << 8) | (t.fuse << 16);
     return GR_OK;
 }
 
@@ -1465,6 +1549,7 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
         Tuned tc = it->second;
         tc.skip = skip;
         tc.simple = (reinterpret_cast<const ArenaHeader *>(staging)->flags & kArenaSimple) ? 1u : 0u;
+        tc.rel_off = Ls[c].rel_off;
         const LaunchCfg cfg = full_cfg(*ws, n_c, tc);
         // the queue counters (and, for the first chunk, the error word) are cleared first
         GR_CUDA(enqueue_repair(ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, sb, d_out + lo[c], cfg,

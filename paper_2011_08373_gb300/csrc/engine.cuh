@@ -28,6 +28,7 @@ constexpr uint32_t kNoClause = 0xFFFFFFFFu;            // its empty marker
 constexpr uint32_t kMinTableBytes = 25u * 2u * kChunkWords;  // one chunk for 25 rows
 constexpr uint32_t kErrTableTooSmall = 1u;  // bits of the device error word (scratch control word 1)
 constexpr uint32_t kErrArgs = 4u;           // the launch's n or scratch size does not match the arena
+constexpr uint32_t kErrStall = 8u;          // a bounded wait for another CTA's result ran out
 constexpr uint8_t kStmtInjective = 1u;      // DevStmt::flags: no two threads of a block share an address
 constexpr uint32_t kArenaSimple = 1u;       // ArenaHeader::flags: every program is straight-line (no loops or
                                             // explicit slot places) on the shared array alone
@@ -139,7 +140,14 @@ struct LaunchCfg {
     uint32_t loop_grid;    // CTAs of the loop kernel
     uint32_t skip;         // kSkip* bits: parts of the batch known to be empty
     uint32_t simple;       // 1: the loop kernel's small build (a batch the packer marked kArenaSimple)
+    RelCfg fused;          // the relation kernel that also runs the loop (table_bytes 0: not used)
+    uint64_t flags_off;    // scratch bytes to its per-program done flags (see rel_flags_off)
 };
+
+// Scratch offset of the per-program done flags (u32[n]) after the relations.
+__host__ __device__ inline uint64_t rel_flags_off(uint64_t scratch_rel_off, uint32_t n) {
+    return (scratch_rel_off + (uint64_t)n * sizeof(gr_witnesses) + 255u) & ~(uint64_t)255u;
+}
 constexpr uint32_t kSkipGeneral = 1u;  // no general program: no expansion, no k_check
 constexpr uint32_t kSkipFast = 2u;     // no program for the relation kernel
 constexpr uint32_t kSkipSplit = 4u;    // no program with several check items (nothing to zero first)
@@ -208,7 +216,8 @@ void pack_into(const gr_program *progs, const gr_launch *ls, const int32_t *mode
 // device: the shapes gr_tune_packed recorded for (d_arena, n), else the
 // defaults, plus the kSkip* bits `skip`; `simple`: the arena header's
 // kArenaSimple flag (the loop kernel's small build).
-LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, bool simple, gr_status *status);
+LaunchCfg packed_launch_cfg(const void *d_arena, uint32_t n, uint32_t skip, bool simple, uint64_t rel_off,
+                            gr_status *status);
 // Options: GR_EINVAL for an unknown strategy or values out of range; the
 // defaults filled in (NULL: grid enabled, 64 iterations, no deadline).
 gr_status validate_opts(const gr_options *o);
@@ -232,6 +241,13 @@ cudaError_t launch_split_zero(const void *d_arena, uint32_t n, void *d_scratch, 
 cudaError_t launch_check(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
                          uint64_t scratch_bytes, gr_witnesses *d_out, LaunchCfg cfg, cudaStream_t st);
 // The same for the programs the relation kernel takes.
+// The relation kernel that, once the relation queue is empty, runs the loop
+// of every program (one warp each) in the same launch (batches the packer
+// marked simple with no general program; cfg.fused the CTA shape).
+cudaError_t launch_relation_loop(const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                                 const gr_options &opts, gr_repair_result *d_out, RelCfg cfg, cudaStream_t st);
+// Whether the fused kernel's loop records fit a CTA's table of table_bytes.
+bool relation_loop_fits(uint32_t table_bytes);
 cudaError_t launch_relation(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
                             uint64_t scratch_bytes, gr_witnesses *d_out, RelCfg cfg, cudaStream_t st);
 // Algorithm 1 per program over the relations in the scratch.

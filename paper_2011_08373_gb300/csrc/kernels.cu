@@ -1871,6 +1871,15 @@ cudaError_t enqueue_loop(const void *d_arena, uint32_t n, const gr_options &opts
 cudaError_t enqueue_repair(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
                            uint64_t scratch_bytes, gr_repair_result *d_out, const LaunchCfg &cfg, uint32_t expand_grid,
                            bool expand, bool clear_error, cudaStream_t st) {
+    if (cfg.flags_off && cfg.flags_off + (uint64_t)n * 4u <= scratch_bytes) {
+        // one launch: the relations, then each CTA runs the loop of programs
+        // whose relation is out (their done flags start cleared)
+        cudaError_t e = clear_ctrl(d_scratch, clear_error, st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(static_cast<uint8_t *>(d_scratch) + cfg.flags_off, 0, (size_t)n * 4u, st);
+        if (e == cudaSuccess) e = launch_relation_loop(d_arena, n, d_scratch, scratch_bytes, opts, d_out, cfg.fused, st);
+        return e;
+    }
     cudaError_t e = enqueue_relation(d_arena, n, d_scratch, scratch_bytes, cfg, expand_grid, expand, clear_error, st);
     if (e == cudaSuccess) e = launch_loop(d_arena, n, opts, d_scratch, scratch_bytes, d_out, cfg.loop_grid, cfg.simple != 0, st);
     return e;

@@ -104,7 +104,7 @@ extern "C" gr_status gr_repair_packed_noalloc(const void *d_arena, uint32_t n, c
     // the same launch as gr_repair_packed: the shapes gr_tune_packed recorded
     // for this arena, else the defaults
     const uint32_t skip = skip_bits(h);
-    const LaunchCfg cfg = packed_launch_cfg(d_arena, n, skip, (h.flags & kArenaSimple) != 0, &s);
+    const LaunchCfg cfg = packed_launch_cfg(d_arena, n, skip, (h.flags & kArenaSimple) != 0, h.scratch_rel_off, &s);
     if (s != GR_OK) return noalloc_fail(s, "launch configuration failed");
     // the queue counters and the error word start at zero (cleared first)
     e = enqueue_repair(d_arena, n, opts_or_default(opts), scratch, kNoAllocScratchBytes, d_out, cfg,

@@ -42,6 +42,7 @@
 #include <cstdint>
 
 #include "device.cuh"
+#include "loop.cuh"
 
 namespace gr {
 
@@ -368,7 +369,7 @@ __device__ __forceinline__ void rel_clear_entries(uint16_t *tab, uint32_t table_
 // The program's witness rows (race_intra; one array per block, so no
 // cross-block pairs) from the row conflicts, and under a mask its divergent
 // slots and pair count.  Warp 0.
-__device__ void rel_output(RelProg &sm, gr_witnesses *dst, bool with_mask) {
+__device__ void rel_output(RelProg &sm, gr_witnesses *dst, bool with_mask, uint32_t *done) {
     const uint32_t lane = threadIdx.x & 31u;
     const DevProg &P = sm.prog;
     const uint32_t involved = sm.involved, p = sm.p;
@@ -415,6 +416,12 @@ __device__ void rel_output(RelProg &sm, gr_witnesses *dst, bool with_mask) {
         wo.n_stmts = P.n_stmts;
         wo.access_pairs = pairs;
     }
+    if (done) {
+        // the rows before the flag, for the warps of other CTAs that wait on it
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) *(volatile uint32_t *)&done[p] = 1u;
+    }
     __syncwarp();
 }
 
@@ -459,11 +466,18 @@ __device__ __forceinline__ void rel_fetch(RelProg &b, RelQueue &Q, const ArenaVi
     __syncwarp();
 }
 
-template <uint32_t NT, uint32_t MINB>
+// The relation kernel.  FUSED: once the relation queue is empty and this
+// CTA's programs are written out, every warp runs Algorithm 1 for programs
+// from the loop queue (one warp each, as the loop kernel does), its record in
+// the freed table; a program's loop starts after its relation's done flag,
+// set by the CTA that took it (a CTA that is running: it took the item), so
+// the wait ends; it is bounded all the same, and running out sets the error
+// word.
+template <uint32_t NT, uint32_t MINB, bool FUSED>
 __global__ void __launch_bounds__(NT, MINB)
     k_relation(const uint8_t *__restrict__ arena, uint32_t n, const uint32_t *__restrict__ masks,
                uint8_t *__restrict__ scratch, uint64_t scratch_bytes, gr_witnesses *__restrict__ out,
-               uint32_t table_bytes) {
+               uint32_t table_bytes, gr_options opts, gr_repair_result *__restrict__ results) {
     extern __shared__ uint4 rel_raw[];
     RelSmem &sm = *reinterpret_cast<RelSmem *>(rel_raw);
     uint16_t *tab = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(rel_raw) + kRelFixed);
@@ -474,6 +488,7 @@ __global__ void __launch_bounds__(NT, MINB)
         return;
     }
     gr_witnesses *dst = out ? out : reinterpret_cast<gr_witnesses *>(scratch + V.h->scratch_rel_off);
+    uint32_t *done = FUSED ? reinterpret_cast<uint32_t *>(scratch + rel_flags_off(V.h->scratch_rel_off, n)) : nullptr;
     const uint32_t n_fast = V.h->n_fast;
     const uint32_t warp = threadIdx.x >> 5;
     constexpr uint32_t kWorkers = NT - 32u;
@@ -497,7 +512,7 @@ __global__ void __launch_bounds__(NT, MINB)
         if (!have_cur && !have_prv) break;  // uniform
         if (warp == 0) {
             // program k-1 out, then program k+1 into its buffer
-            if (have_prv) rel_output(prv, dst, masks != nullptr);
+            if (have_prv) rel_output(prv, dst, masks != nullptr, done);
             if (have_cur) {
                 rel_fetch(prv, Q, V, ctrl, n_fast, masks, table_bytes);
             } else if ((threadIdx.x & 31u) == 0) {
@@ -525,6 +540,37 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         __syncthreads();
     }
+    if constexpr (FUSED) {
+        // the pipeline has drained: the table area holds a loop record per warp
+        const uint32_t lane = threadIdx.x & 31u;
+        LoopWarpSimple &lw = *reinterpret_cast<LoopWarpSimple *>(reinterpret_cast<uint8_t *>(tab) +
+                                                                 warp_smem<LoopWarpSimple>() * warp);
+        const uint32_t max_iters =
+            opts.max_iters == 0 ? GR_MAX_ITERS : min(opts.max_iters, (uint32_t)GR_MAX_ITERS);
+        const uint64_t deadline_ns = opts.deadline_us * 1000ull;
+        constexpr uint32_t kWaitLimit = 1u << 23;  // about half a second of 64 ns sleeps
+        for (;;) {
+            uint32_t item = 0;
+            if (lane == 0) item = atomicAdd(&ctrl[3], 1u);
+            item = __shfl_sync(0xFFFFFFFFu, item, 0);
+            if (item >= n) break;
+            const uint32_t p = V.order[item];
+            uint32_t ok = 1;
+            if (lane == 0) {
+                for (uint32_t it = 0; *(volatile uint32_t *)&done[p] == 0u; ++it) {
+                    if (it >= kWaitLimit) {
+                        atomicOr(&ctrl[1], kErrStall);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                __threadfence();  // the relation rows after the flag
+            }
+            if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) return;
+            loop_program(lw, V, p, dst, opts, max_iters, deadline_ns, results, ctrl);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -545,13 +591,27 @@ static cudaError_t rel_set_smem(F *f, uint32_t max_dynamic_smem) {
 
 cudaError_t configure_relation(uint32_t max_dynamic_smem) {
     cudaError_t e;
-    if ((e = rel_set_smem(k_relation<512, 3>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = rel_set_smem(k_relation<256, 4>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = rel_set_smem(k_relation<512, 2>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = rel_set_smem(k_relation<1024, 1>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = rel_set_smem(k_relation<256, 6>, max_dynamic_smem)) != cudaSuccess) return e;
-    if ((e = rel_set_smem(k_relation<128, 8>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = rel_set_smem(k_relation<512, 3, false>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = rel_set_smem(k_relation<256, 4, false>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = rel_set_smem(k_relation<512, 2, false>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = rel_set_smem(k_relation<1024, 1, false>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = rel_set_smem(k_relation<256, 6, false>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = rel_set_smem(k_relation<128, 8, false>, max_dynamic_smem)) != cudaSuccess) return e;
+    if ((e = rel_set_smem(k_relation<512, 2, true>, max_dynamic_smem)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+bool relation_loop_fits(uint32_t table_bytes) {
+    return (size_t)table_bytes >= warp_smem<LoopWarpSimple>() * (512u / 32u);
+}
+
+cudaError_t launch_relation_loop(const void *d_arena, uint32_t n, void *d_scratch, uint64_t scratch_bytes,
+                                 const gr_options &opts, gr_repair_result *d_out, RelCfg cfg, cudaStream_t st) {
+    const size_t smem = kRelFixed + cfg.table_bytes;
+    k_relation<512, 2, true><<<cfg.grid, 512, smem, st>>>(static_cast<const uint8_t *>(d_arena), n, nullptr,
+                                                         static_cast<uint8_t *>(d_scratch), scratch_bytes, nullptr,
+                                                         cfg.table_bytes, opts, d_out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_relation(const void *d_arena, uint32_t n, const uint32_t *d_masks, void *d_scratch,
@@ -560,12 +620,12 @@ cudaError_t launch_relation(const void *d_arena, uint32_t n, const uint32_t *d_m
     uint8_t *sc = static_cast<uint8_t *>(d_scratch);
     const size_t smem = kRelFixed + cfg.table_bytes;
     switch (cfg.shape) {
-        case 1: k_relation<256, 4><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
-        case 2: k_relation<512, 2><<<cfg.grid, 512, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
-        case 3: k_relation<1024, 1><<<cfg.grid, 1024, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
-        case 4: k_relation<256, 6><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
-        case 5: k_relation<128, 8><<<cfg.grid, 128, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
-        default: k_relation<512, 3><<<cfg.grid, 512, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes); break;
+        case 1: k_relation<256, 4, false><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes, gr_options{}, nullptr); break;
+        case 2: k_relation<512, 2, false><<<cfg.grid, 512, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes, gr_options{}, nullptr); break;
+        case 3: k_relation<1024, 1, false><<<cfg.grid, 1024, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes, gr_options{}, nullptr); break;
+        case 4: k_relation<256, 6, false><<<cfg.grid, 256, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes, gr_options{}, nullptr); break;
+        case 5: k_relation<128, 8, false><<<cfg.grid, 128, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes, gr_options{}, nullptr); break;
+        default: k_relation<512, 3, false><<<cfg.grid, 512, smem, st>>>(a, n, d_masks, sc, scratch_bytes, d_out, cfg.table_bytes, gr_options{}, nullptr); break;
     }
     return cudaGetLastError();
 }

@@ -198,7 +198,7 @@ bool dispatch(gr_server *s, Slot &sl, std::unique_lock<std::mutex> &lk) {
     }
     const ArenaHeader &hd = *reinterpret_cast<const ArenaHeader *>(sl.h_arena);
     const uint32_t skip = skip_bits(hd);
-    const LaunchCfg cfg = wide ? wide_launch_cfg(n, s_max, &cs) : packed_launch_cfg(sl.d_arena, n, skip, (hd.flags & kArenaSimple) != 0, &cs);
+    const LaunchCfg cfg = wide ? wide_launch_cfg(n, s_max, &cs) : packed_launch_cfg(sl.d_arena, n, skip, (hd.flags & kArenaSimple) != 0, hd.scratch_rel_off, &cs);
     e = cudaMemcpyAsync(sl.d_arena, sl.h_arena, L.arena_bytes, cudaMemcpyHostToDevice, sl.stream);
     if (e == cudaSuccess) {
         if (wide) {
@@ -295,7 +295,7 @@ gr_status gr_server_create(uint64_t mem_budget_bytes, uint32_t n_slots, uint32_t
     const uint64_t per_slot = mem_budget_bytes / n_slots;
     if (per_slot < (8ull << 20)) return fail(GR_EINVAL, "budget below 8 MiB per slot");
     gr_status cs = GR_OK;
-    packed_launch_cfg(nullptr, 1, 0, false, &cs);  // configures the kernels on this device
+    packed_launch_cfg(nullptr, 1, 0, false, 0, &cs);  // configures the kernels on this device
     if (cs != GR_OK) return cs;
     gr_server *s = new gr_server();
     cudaGetDevice(&s->device);
