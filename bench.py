@@ -108,13 +108,13 @@ REL_SHAPES = [(512, 3), (256, 4), (512, 2), (1024, 1), (256, 6), (128, 8)]
 GEN_SHAPES = [(512, 2), (256, 3), (256, 4), (1024, 1), (384, 3)]
 
 
-def shape_dict(shape):
+def shape_dict(shape, picked_by="autotuner"):
     rel, gen = shape & 0xFF, (shape >> 8) & 0xFF
     return {"relation": {"threads": REL_SHAPES[rel][0], "ctas_per_sm": REL_SHAPES[rel][1]},
             "general_check": {"threads": GEN_SHAPES[gen & 15][0], "ctas_per_sm": GEN_SHAPES[gen & 15][1],
                               "balanced_grid": bool(gen & 16)},
             "relation_runs_loop": bool((shape >> 16) & 1),
-            "picked_by": "autotuner"}
+            "word": hex(shape), "picked_by": picked_by}
 
 
 def dist_env():
@@ -235,7 +235,7 @@ def check_bytes(arena, n):
     return survey, fused
 
 
-def kernel_source_sha(files=("relation.cu", "device.cuh", "engine.cuh")):
+def kernel_source_sha(files=("relation.cu", "loop.cuh", "device.cuh", "engine.cuh")):
     """Hash of the sources a kernel is built from (first 16 hex digits)."""
     h = hashlib.sha256()
     for name in files:
@@ -436,7 +436,10 @@ def run_ours(args, rank, world, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    shape = batch.tune()  # the autotuner picks the CTA shapes for this batch
+    if args.shape is None:
+        shape = batch.tune()  # the autotuner picks the CTA shapes for this batch
+    else:  # a word an earlier run's autotuner printed (its config.cta_shape.word)
+        shape = batch.set_shape(args.shape)
     for _ in range(args.warmup):
         batch.run()
     barrier()
@@ -599,7 +602,8 @@ def run_ours(args, rank, world, local):
             "config": {"workload": args.workload, "programs": n, "blocks": wl.blocks, "threads": wl.threads,
                        "stmts": wl.n_stmts, "m_words": wl.m_words, "seed": wl.seed,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
-                       "cta_shape": shape_dict(shape), "parallelism": f"replicas x{world}"},
+                       "cta_shape": shape_dict(shape, "autotuner" if args.shape is None else "--shape"),
+                       "parallelism": f"replicas x{world}"},
             "e2e": e2e,
             "gpu_launches": launches_per_step(batch) * args.steps,
             "roofline": roofline,
@@ -651,6 +655,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--programs", type=int, default=0)
+    ap.add_argument("--shape", type=lambda x: int(x, 0), default=None,
+                    help="CTA shape word to use instead of running the autotuner (config.cta_shape.word of "
+                         "an earlier run): profilers serialise launches, which changes the autotuner's pick")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--plain-programs", type=int, default=64)
     ap.add_argument("--check-steps", type=int, default=5,

@@ -379,6 +379,16 @@ gr_status gr_relation_loop_packed(const void *d_arena, uint32_t n, const gr_opti
 gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                          uint64_t scratch_bytes, gr_repair_result *d_out, void *stream, uint32_t *shape_out);
 
+/* Record a shape word for later calls on (d_arena, n) without timing
+ * anything, as if gr_tune_packed had picked it: a word gr_tune_packed
+ * returned earlier (for this batch or one like it, in this process or
+ * another), so a caller can tune once and reuse the choice.  The word's
+ * fields are gr_tune_packed's.  GR_EINVAL, with nothing recorded, for a
+ * field that names no built shape, a bit above 16, or bit 16 on a batch
+ * that cannot run in one launch.  Reads the arena header back on stream
+ * (synchronises); launches no kernel and writes no device memory. */
+gr_status gr_set_shape_packed(const void *d_arena, uint32_t n, uint32_t shape, void *stream);
+
 /* One check per program of a device-resident packed arena under d_masks[p]. */
 gr_status gr_check_packed(const void *d_arena, uint32_t n, const uint32_t *d_masks,
                           void *d_scratch, uint64_t scratch_bytes, gr_witnesses *d_out,

@@ -84,7 +84,7 @@ EXPORTS = ["gr_version", "gr_last_error", "gr_validate", "gr_check", "gr_repair"
            "gr_repair_packed_noalloc", "gr_server_create", "gr_server_submit", "gr_server_poll",
            "gr_server_drain", "gr_server_stats", "gr_server_destroy", "gr_tune_packed",
            "gr_repair_packed_wide", "gr_check_expanded", "gr_relation_packed", "gr_loop_packed",
-           "gr_repair_plain_timed", "gr_relation_loop_packed"]
+           "gr_repair_plain_timed", "gr_relation_loop_packed", "gr_set_shape_packed"]
 
 
 def lib():
@@ -138,6 +138,7 @@ def lib():
             L.gr_relation_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint64, C.c_void_p]
             L.gr_loop_packed.argtypes = L.gr_repair_packed.argtypes
             L.gr_relation_loop_packed.argtypes = L.gr_repair_packed.argtypes
+            L.gr_set_shape_packed.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p]
             for name in EXPORTS[2:]:
                 getattr(L, name).restype = C.c_int32
             _lib = L
@@ -518,6 +519,16 @@ class DeviceBatch:
                                     C.c_void_p(self._out_ptr), C.c_void_p(st), C.byref(shape)))
         self.shape = shape.value
         return shape.value
+
+    def set_shape(self, shape: int, stream: Optional[int] = None) -> int:
+        """Use a shape word tune() returned before (gr_set_shape_packed),
+        without timing anything."""
+        import torch
+
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib().gr_set_shape_packed(C.c_void_p(self._arena_ptr), self.n, shape, C.c_void_p(st)))
+        self.shape = shape
+        return shape
 
     def expand(self, stream: Optional[int] = None) -> None:
         """Only the trace expansion (first half of run())."""

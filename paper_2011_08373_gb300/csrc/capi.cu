@@ -1318,6 +1318,37 @@ gr_status gr_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts
     return GR_OK;
 }
 
+gr_status gr_set_shape_packed(const void *d_arena, uint32_t n, uint32_t shape, void *stream) {
+    if (!d_arena || n == 0) return fail(GR_EINVAL, "NULL arena or n == 0");
+    if (reinterpret_cast<uintptr_t>(d_arena) % 256) return fail(GR_EINVAL, "d_arena must be 256-byte aligned");
+    const uint32_t rel = shape & 0xFFu, gen = (shape >> 8) & 0xFFu;
+    if (rel >= kNumRelShapes || (gen & ~(kShapeMask | kShapeBalanced)) || (gen & kShapeMask) >= kNumShapes ||
+        (shape >> 17))
+        return fail(GR_EINVAL, "shape word 0x%x names no built shape", shape);
+    gr_status s;
+    Workspace *ws;
+    if ((s = current_ws(&ws)) != GR_OK) return s;
+    std::lock_guard<std::mutex> g(ws->mu);
+    if ((s = ensure_configured(*ws)) != GR_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ArenaHeader h;
+    GR_CUDA(cudaMemcpyAsync(&h, d_arena, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GR_CUDA(cudaStreamSynchronize(st));
+    if (h.magic != kArenaMagic || h.n_progs != n) return fail(GR_EINVAL, "d_arena is not a packed arena of %u programs", n);
+    Tuned t;
+    t.rel_shape = rel;
+    t.gen_shape = gen;
+    t.s_max = h.s_max;
+    t.skip = skip_bits(h);
+    t.simple = (h.flags & kArenaSimple) ? 1u : 0u;
+    t.rel_off = h.scratch_rel_off;
+    t.fuse = (shape >> 16) & 1u;
+    if (t.fuse && !full_cfg(*ws, n, t).flags_off)
+        return fail(GR_EINVAL, "bit 16 (one launch) is set, but the batch cannot run in one launch");
+    ws->arena_shape[{d_arena, n}] = t;
+    return GR_OK;
+}
+
 gr_status gr_relation_loop_packed(const void *d_arena, uint32_t n, const gr_options *opts, void *d_scratch,
                                   uint64_t scratch_bytes, gr_repair_result *d_out, void *stream) {
     if (!d_arena || !d_scratch || !d_out || n == 0) return fail(GR_EINVAL, "NULL buffer or n == 0");

@@ -246,3 +246,32 @@ def test_one_launch_equals_the_two_kernels(gb):
         db.relation_loop()
     torch.cuda.synchronize()
     assert bool((db.out.view(torch.uint8) == 0xA5).all())
+
+
+def test_a_recorded_shape_word_replaces_the_autotuner(gb):
+    """gr_set_shape_packed: the word gr_tune_packed returned, set on a fresh
+    arena of the same batch, gives the tuned batch's results; so does a word
+    with the one-launch bit on a batch that allows it.  Words that name no
+    built shape, and the one-launch bit on a batch with a general program,
+    are refused."""
+    import torch
+
+    progs = synth.generate("batch1024_4x256_s24", 24, blocks=2, threads=32, n_stmts=8, m_words=128)
+    want = oracle.repair_batch(progs, n_threads=4)
+    a = gb.DeviceBatch(progs)
+    word = a.tune()
+    for w in (word, (word & 0xFFFF) | (1 << 16)):
+        b = gb.DeviceBatch(progs)
+        assert b.set_shape(w) == w
+        b.run()
+        torch.cuda.synchronize()
+        for g, x in zip(b.results(), want):
+            _same(g, x)
+    b = gb.DeviceBatch(progs)
+    for bad in (6, 5 << 8, 0x20 << 8, 1 << 17):
+        with pytest.raises(gb.GrError):
+            b.set_shape(bad)
+    general = progs[:2] + synth.generate("interblock256_64x256_s16", 1, blocks=3, threads=32, n_stmts=5,
+                                         m_words=512)
+    with pytest.raises(gb.GrError):
+        gb.DeviceBatch(general).set_shape(1 << 16)
