@@ -1494,12 +1494,13 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
     // stream: the device arena and scratch are reused in order).  Results
     // gather in the device result buffer and reach `out` in one copy at the
     // end, so `out` stays untouched when a later chunk holds a bad table.
-    // Chunks keep at least 128 programs, and below 2,048 programs at most two:
-    // a launch of a few hundred programs takes about one program's latency
-    // (one per CTA), so more, smaller chunks leave the device behind the host.
+    // Below 2,048 programs the batch goes in one chunk: a launch of a few
+    // hundred programs takes about one program's latency (one per CTA), and
+    // packing 1,024 programs takes about as long, so a second chunk adds a
+    // latency to the device's chain without hiding more than it adds.
     // The last chunk is half the size of the others: only its device work is
     // not hidden behind packing.
-    const uint32_t K = n >= 2048 ? 4u : (n >= 256 ? 2u : 1u);
+    const uint32_t K = n >= 2048 ? 4u : 1u;
     std::vector<uint32_t> lo(K + 1);
     for (uint32_t c = 0; c < K; ++c) lo[c] = (uint32_t)((uint64_t)n * (2u * c) / (2u * K - 1u));
     lo[K] = n;
@@ -1539,6 +1540,8 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
         *p_out = word ? ~word : 0xFFFFFFFFu;
         return GR_OK;
     };
+    const size_t rb = (size_t)n * sizeof(gr_repair_result);
+    if ((s = ensure_pinned(&ws->host_out, &ws->host_out_cap, rb + 16)) != GR_OK) return s;
     std::vector<uint32_t> bad;
     for (uint32_t c = 0; c < K; ++c) {
         const uint32_t n_c = lo[c + 1] - lo[c];
@@ -1585,16 +1588,17 @@ gr_status gr_repair_batch(const gr_program *progs, const gr_launch *launches, co
         // the queue counters (and, for the first chunk, the error word) are cleared first
         GR_CUDA(enqueue_repair(ws->arena.p, n_c, opts_or_default(opts), ws->scratch.p, sb, d_out + lo[c], cfg,
                                expand_grid(*ws), true, c == 0, st));
+        // the chunk's results start back while the host packs the next one
+        GR_CUDA(cudaMemcpyAsync(ws->host_out + (size_t)lo[c] * sizeof(gr_repair_result), d_out + lo[c],
+                                (size_t)n_c * sizeof(gr_repair_result), cudaMemcpyDeviceToHost, st));
     }
-    // The results, the permutation word and the device error word come back
-    // through pinned staging (DMAs at full speed, and no copy into pageable
-    // memory, which would block the host until the stream reaches it) with
-    // one synchronisation; `out` is written only if both words are clean.
-    const size_t rb = (size_t)n * sizeof(gr_repair_result);
-    if ((s = ensure_pinned(&ws->host_out, &ws->host_out_cap, rb + 16)) != GR_OK) return s;
+    // The results (above, per chunk), the permutation word and the device
+    // error word come back through pinned staging (DMAs at full speed, and no
+    // copy into pageable memory, which would block the host until the stream
+    // reaches it) with one synchronisation; `out` is written only if both
+    // words are clean.
     uint32_t *words = reinterpret_cast<uint32_t *>(ws->host_out + rb);
     words[0] = 0;
-    GR_CUDA(cudaMemcpyAsync(ws->host_out, d_out, rb, cudaMemcpyDeviceToHost, st));
     if (any_perm) GR_CUDA(cudaMemcpyAsync(&words[0], d_perm_bad, 4, cudaMemcpyDeviceToHost, st));
     GR_CUDA(cudaMemcpyAsync(&words[1], static_cast<uint32_t *>(ws->scratch.p) + 1, 4, cudaMemcpyDeviceToHost, st));
     GR_CUDA(cudaStreamSynchronize(st));

@@ -493,21 +493,22 @@ def test_batch_rejects_bad_permutation_tables(gb):
         _same_result(g, oracle.repair(p))
     # a large batch goes in chunks: a bad table in the last chunk is still
     # reported (after earlier chunks ran), and the next call is unaffected
-    big = synth.generate("batch1024_4x256_s24", 600, blocks=2, threads=32, n_stmts=8, m_words=128)
-    k = next(i for i in range(590, 600) if (big[i].kind == 2).any())
+    # (2,100 programs: four chunks, the last from program 1,800)
+    big = synth.generate("batch1024_4x256_s24", 2100, blocks=2, threads=32, n_stmts=8, m_words=128)
+    k = next(i for i in range(2090, 2100) if (big[i].kind == 2).any())
     s = int(np.nonzero(big[k].kind == 2)[0][0])
     big[k] = copy.deepcopy(big[k])
     big[k].perm = big[k].perm.copy()
     i0, i1 = _window_entries(big[k], s)
     big[k].perm[i0] = big[k].perm[i1]
-    out = np.zeros(600, dtype=gb.RESULT_DTYPE)
+    out = np.zeros(2100, dtype=gb.RESULT_DTYPE)
     with pytest.raises(gb.GrError) as e:
         gb.repair_batch_raw(big, out=out)
     assert e.value.code == gb.EINVAL and f"program {k} stmt" in str(e.value)
     assert not out.view(np.uint8).any()  # results untouched
     good_big = big[:k] + big[k + 1:]
     got = gb.repair_batch(good_big)
-    for i in (0, 150, 300, 450, len(good_big) - 1):
+    for i in (0, 650, 1300, 1950, len(good_big) - 1):
         _same_result(got[i], oracle.repair(good_big[i]))
 
 
@@ -555,13 +556,14 @@ def test_batch_reports_lowest_bad_table(gb):
     with pytest.raises(gb.GrError) as e:
         gb.repair_batch(progs)
     assert f"program {b} stmt {sb}:" in str(e.value)
-    # 600 programs go in two chunks: a repeat in the first, a bad range in the second
-    big = synth.generate("batch1024_4x256_s24", 600, blocks=2, threads=32, n_stmts=8, m_words=128)
+    # 2,100 programs go in four chunks (from 0, 600, 1,200, 1,800): a repeat
+    # in the first, a bad range in the second
+    big = synth.generate("batch1024_4x256_s24", 2100, blocks=2, threads=32, n_stmts=8, m_words=128)
     i = next(j for j in range(10, 100) if (big[j].kind == 2).any())
-    k = next(j for j in range(330, 440) if (big[j].kind == 2).any())
+    k = next(j for j in range(700, 800) if (big[j].kind == 2).any())
     big[i], si = _spoil(big[i], "repeat")
     big[k], _ = _spoil(big[k], "range")
-    out = np.zeros(600, dtype=gb.RESULT_DTYPE)
+    out = np.zeros(2100, dtype=gb.RESULT_DTYPE)
     with pytest.raises(gb.GrError) as e:
         gb.repair_batch_raw(big, out=out)
     assert f"program {i} stmt {si}:" in str(e.value)
