@@ -4,12 +4,13 @@
 // 0's, and no pair of blocks shares an array, so one owner-table pass over
 // block 0 decides every candidate pair.
 //
-// Each CTA takes programs from a work queue.  Warp 0 is the control warp: it
-// runs one program ahead of the others (two program buffers), fetching and
-// setting up program k+1 and writing out program k-1 while warps 1.. (the
-// workers) check program k, so that the setup's loads and the output overlap
-// the table pass.  Per program:
-//   setup   — (control) the candidate pairs: under a mask, the instance pairs
+// Each CTA takes programs from a work queue, three at a time in three
+// program buffers: while warps 2.. (the workers) check program k, warp 1
+// fetches and sets up program k+1 and warp 0 writes out program k-1, so that
+// the setup's loads and arithmetic and the output overlap the table pass
+// (and each other: on one warp, setup and output took longer than a
+// program's install).  Per program:
+//   setup   — (warp 1) the candidate pairs: under a mask, the instance pairs
 //             (i <= j) with a write and no enabled barrier between them (one
 //             phase, Section 2.2); for the repair loop, every pair with a
 //             write (the empty mask), which gives the program's whole
@@ -32,10 +33,10 @@
 //             found; a row whose pairs are all decided stops installing.
 //   reset   — (workers) the column masks used go back to empty; entries
 //             carry the window's epoch, so stale ones read as empty.
-// Install works in units of one table row and 32 consecutive threads, a warp
-// per unit, so that a unit's map, guard and row are the same for the whole
-// warp: the per-unit arithmetic is done once and each access costs a
-// multiply and a reduction.  The table covers the array in windows when it
+// Install works in units of one table row and 64 consecutive active threads
+// (two per lane), a warp per unit, so that a unit's map, guard and row are
+// the same for the whole warp: the per-unit arithmetic is done once and each
+// access costs a multiply and a reduction.  The table covers the array in windows when it
 // does not fit.
 #include <cuda_runtime.h>
 
@@ -48,8 +49,8 @@ namespace gr {
 
 constexpr uint32_t kRelAllOnes = 0xFFFFFFFFu;
 
-// One program's state (the control warp fills one while the workers use the
-// other).
+// One program's state (warp 1 fills one, the workers use one, warp 0 writes
+// one out).
 struct RelProg {
     DevProg prog;
     uint32_t cand[32];      // table row q: candidate partner rows (bit j, j >= q)
@@ -67,8 +68,12 @@ struct RelProg {
     uint32_t M, Mmagic;     // the shared array's words; floor((2^32 - 1) / M)
 };
 
+// Warps 0 and 1 are the control warps (warp 0 writes programs out, warp 1
+// fetches and sets them up); the others are the workers.
+constexpr uint32_t kRelCtl = 2;
+
 struct RelSmem {
-    RelProg buf[2];
+    RelProg buf[3];  // program k - 1 (output), k (install), k + 1 (setup), by k mod 3
 };
 
 constexpr size_t kRelFixed = (sizeof(RelSmem) + 15) / 16 * 16;
@@ -115,7 +120,7 @@ __device__ __forceinline__ uint32_t and_acq_rel(uint32_t a, uint32_t v) {
     return old;
 }
 
-// Per-program setup by warp 0: the program record, candidate pairs, table
+// Per-program setup by warp 1: the program record, candidate pairs, table
 // rows and their maps, window size.
 __device__ void rel_setup(RelProg &sm, const DevProg *gp, uint32_t mask, uint32_t table_bytes) {
     const uint32_t lane = threadIdx.x & 31u;
@@ -276,8 +281,8 @@ __device__ __forceinline__ uint32_t rel_access(RelProg &sm, uint16_t *tab, uint3
 template <uint32_t NT>
 __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restrict__ perm, uint16_t *tab,
                                             uint32_t *colrows, uint32_t lo, uint32_t epoch) {
-    constexpr uint32_t NWK = NT / 32 - 1;  // worker warps
-    const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - 1u;
+    constexpr uint32_t NWK = NT / 32 - kRelCtl;  // worker warps
+    const uint32_t lane = threadIdx.x & 31u, wk = (threadIdx.x >> 5) - kRelCtl;
     const uint32_t T = sm.prog.threads, M = sm.M, magic = sm.Mmagic, W = sm.W;
     // every row gets the chunks of the unguarded width; a guarded row's
     // later chunks are empty and skipped at once
@@ -354,7 +359,7 @@ __device__ __forceinline__ void rel_install(RelProg &sm, const uint16_t *__restr
 template <uint32_t NT>
 __device__ __forceinline__ void rel_reset(const RelProg &sm, uint32_t *colrows) {
     uint4 *c4 = reinterpret_cast<uint4 *>(colrows);
-    for (uint32_t i = threadIdx.x - 32u; i < sm.W / 4u; i += NT - 32u)
+    for (uint32_t i = threadIdx.x - 32u * kRelCtl; i < sm.W / 4u; i += NT - 32u * kRelCtl)
         c4[i] = make_uint4(kRelAllOnes, kRelAllOnes, kRelAllOnes, kRelAllOnes);
 }
 
@@ -362,7 +367,7 @@ __device__ __forceinline__ void rel_reset(const RelProg &sm, uint32_t *colrows) 
 template <uint32_t NT>
 __device__ __forceinline__ void rel_clear_entries(uint16_t *tab, uint32_t table_bytes) {
     uint4 *t4 = reinterpret_cast<uint4 *>(tab);
-    for (uint32_t i = threadIdx.x - 32u; i < rel_entry_bytes(table_bytes) / 16u; i += NT - 32u)
+    for (uint32_t i = threadIdx.x - 32u * kRelCtl; i < rel_entry_bytes(table_bytes) / 16u; i += NT - 32u * kRelCtl)
         t4[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
@@ -425,7 +430,7 @@ __device__ void rel_output(RelProg &sm, gr_witnesses *dst, bool with_mask, uint3
     __syncwarp();
 }
 
-// The control warp's place in the work queue, kept two programs ahead so
+// Warp 1's place in the work queue, kept two programs ahead so
 // that neither the queue's atomic nor the order table's load is waited on:
 // `p_next` is the program of the next fetch (its order entry was loaded a
 // fetch ago), `item_next` the queue item after it (lane 0's atomic result,
@@ -446,7 +451,7 @@ __device__ __forceinline__ RelQueue rel_queue_start(const ArenaView &V, uint32_t
     return Q;
 }
 
-// The control warp: the next program from the queue into `b`, set up.
+// Warp 1: the next program from the queue into `b`, set up.
 __device__ __forceinline__ void rel_fetch(RelProg &b, RelQueue &Q, const ArenaView &V, uint32_t *ctrl,
                                           uint32_t n_fast, const uint32_t *masks, uint32_t table_bytes) {
     const uint32_t lane = threadIdx.x & 31u;
@@ -491,7 +496,8 @@ __global__ void __launch_bounds__(NT, MINB)
     uint32_t *done = FUSED ? reinterpret_cast<uint32_t *>(scratch + rel_flags_off(V.h->scratch_rel_off, n)) : nullptr;
     const uint32_t n_fast = V.h->n_fast;
     const uint32_t warp = threadIdx.x >> 5;
-    constexpr uint32_t kWorkers = NT - 32u;
+    constexpr uint32_t kWorkers = NT - 32u * kRelCtl;
+    static_assert(NT / 32 > kRelCtl, "the relation kernel needs a worker warp");
     // entries at epoch 0 (empty), column masks empty (all ones)
     uint32_t *colrows = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(tab) + rel_entry_bytes(table_bytes));
     for (uint32_t i = threadIdx.x; i < table_bytes / 16u; i += NT) {
@@ -500,28 +506,32 @@ __global__ void __launch_bounds__(NT, MINB)
     }
     uint32_t epoch = 0;  // the workers' window count, modulo the epochs
     RelQueue Q{kRelAllOnes, 0u};
-    if (warp == 0) {
+    if (warp == 1) {
         Q = rel_queue_start(V, ctrl, n_fast);
         rel_fetch(sm.buf[0], Q, V, ctrl, n_fast, masks, table_bytes);
-        if ((threadIdx.x & 31u) == 0) sm.buf[1].p = kRelAllOnes;
+    } else if (threadIdx.x == 0) {
+        sm.buf[1].p = kRelAllOnes;
+        sm.buf[2].p = kRelAllOnes;
     }
     __syncthreads();
-    for (uint32_t k = 0;; ++k) {
-        RelProg &cur = sm.buf[k & 1u], &prv = sm.buf[(k & 1u) ^ 1u];
+    for (uint32_t k = 0, ic = 0;; ++k, ic = ic == 2u ? 0u : ic + 1u) {  // ic = k mod 3
+        RelProg &cur = sm.buf[ic], &nxt = sm.buf[ic == 2u ? 0u : ic + 1u], &prv = sm.buf[ic == 0u ? 2u : ic - 1u];
         const bool have_cur = cur.p != kRelAllOnes, have_prv = prv.p != kRelAllOnes;
         if (!have_cur && !have_prv) break;  // uniform
         if (warp == 0) {
-            // program k-1 out, then program k+1 into its buffer
+            // program k-1 out (its buffer is set up again in the next round)
             if (have_prv) rel_output(prv, dst, masks != nullptr, done);
+        } else if (warp == 1) {
+            // program k+1 into the third buffer
             if (have_cur) {
-                rel_fetch(prv, Q, V, ctrl, n_fast, masks, table_bytes);
+                rel_fetch(nxt, Q, V, ctrl, n_fast, masks, table_bytes);
             } else if ((threadIdx.x & 31u) == 0) {
-                prv.p = kRelAllOnes;
+                nxt.p = kRelAllOnes;
             }
         } else if (have_cur) {
             const uint32_t R = cur.n_rows, W = cur.W, n_win = cur.n_win;
             if (cur.bad) {
-                if (threadIdx.x == 32) atomicOr(&ctrl[1], kErrTableTooSmall);
+                if (threadIdx.x == 32u * kRelCtl) atomicOr(&ctrl[1], kErrTableTooSmall);
             } else if (R) {
                 for (uint32_t w = 0; w < n_win; ++w) {
                     if (++epoch > kMaxEpoch) {  // uniform over the workers
