@@ -370,8 +370,8 @@ gr_status gr_relation_loop_packed(const void *d_arena, uint32_t n, const gr_opti
  * kernel's, bit 12 is set when that kernel's grid is cut so that every CTA
  * gets the same number of programs (fewer CTAs than fit, no partly filled
  * last round), bit 16 when a batch of straight-line programs (no general
- * one) repairs faster with the relation kernel running the loop too, in one
- * launch, than with the two kernels (both are timed).  Runs the kernels
+ * one) repairs at least 3% faster with the relation kernel running the loop
+ * too, in one launch, than with the two kernels (both are timed).  Runs the kernels
  * several times, then one repair with the choices picked into d_out, and
  * synchronises the stream.  The
  * host-pointer batch calls tune the same way by themselves, once per batch

@@ -1408,8 +1408,8 @@ gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts
     if ((s = tune_cfg(*ws, d_arena, n, d_scratch, scratch_bytes, st, h.s_max, skip, &t)) != GR_OK) return s;
     t.simple = (h.flags & kArenaSimple) ? 1u : 0u;
     t.rel_off = h.scratch_rel_off;
-    // one launch (the relation kernel runs the loop) or two: whichever
-    // repairs the batch faster.  The single launch saves a launch gap and
+    // one launch (the relation kernel runs the loop) or two: one launch
+    // when it repairs the batch at least 3% faster.  The single launch saves a launch gap and
     // overlaps the loop with the relation tail, but its loop warps share the
     // SMs with up to 32 warps and have fewer registers than the loop kernel's.
     Tuned tf = t;
@@ -1429,7 +1429,9 @@ gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (e != cudaSuccess) return cuda_fail(e, "autotuner");
-        if (ms_one < ms_two) t.fuse = 1;
+        // only a clear win: the two are often within the runs' noise, and
+        // two launches are the better-measured default
+        if (ms_one < 0.97f * ms_two) t.fuse = 1;
     }
     ws->arena_shape[{d_arena, n}] = t;
     // one repair with the picked shapes leaves d_out filled, as documented

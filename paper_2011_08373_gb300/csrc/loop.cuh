@@ -405,6 +405,30 @@ __device__ bool warp_solve(LW &lw, const uint32_t *cl, uint32_t n, uint32_t forc
                 H = min(H, hi);
                 if (lo > lane && hi < bk) bk = hi;
             }
+            // With the weights of R summing below 2^(32 - r), a key packs in
+            // 32 bits, (weight << r) | compact mask, in the same order, and
+            // each step's minimum is one warp reduction.  The clamp keeps the
+            // sum exact: a weight at or above the cap fails the test alone.
+            const uint32_t cap = 1u << (32u - r);  // 5 < r <= 32
+            const uint32_t sumw = __reduce_add_sync(0xFFFFFFFFu, min(lw.wc[lane], cap));
+            if (sumw + 1u < cap) {  // uniform; then r < 32 and no key reaches ~0u
+                const uint32_t key32 = lane < r ? (lw.wc[lane] << r) | (1u << lane) : 0u;
+                uint32_t g32 = 0xFFFFFFFFu;
+                for (int k = (int)r - 1; k >= 0; --k) {  // uniform
+                    const uint32_t b = __shfl_sync(0xFFFFFFFFu, bk, k);
+                    const uint32_t m = __reduce_min_sync(
+                        0xFFFFFFFFu, lane > (uint32_t)k && lane <= b && lane < r ? g32 : 0xFFFFFFFFu);
+                    if (lane == (uint32_t)k) g32 = b == 0xFFFFFFFFu ? key32 : (m == 0xFFFFFFFFu ? m : key32 + m);
+                }
+                const uint32_t best = __reduce_min_sync(0xFFFFFFFFu, lane < r && lane <= H ? g32 : 0xFFFFFFFFu);
+                __syncwarp();
+                if (best == 0xFFFFFFFFu) return false;
+                mask_out = pdep32(best & ((1u << r) - 1u), R) | forced;
+                uint32_t wt = best >> r;
+                for (uint32_t t = forced; t; t &= t - 1u) wt += w[__ffs(t) - 1u];
+                weight_out = wt;
+                return true;
+            }
             const unsigned long long keyk = ((unsigned long long)lw.wc[lane] << 32) | (1ull << lane);
             unsigned long long g = ~0ull;
             for (int k = (int)r - 1; k >= 0; --k) {  // uniform

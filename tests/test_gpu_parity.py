@@ -77,6 +77,27 @@ def test_solver_random_vs_oracle(gb):
         assert got == want, (seed, n)
 
 
+def test_interval_solve_key_widths(gb):
+    """The loop's interval stabbing program packs each (weight, mask) key in
+    32 bits, (weight << r) | compact mask, when the weights of the r compact
+    slots sum below 2^(32 - r), and keeps 64-bit keys otherwise.  Straight-line
+    programs on the shared array with small weights (packed keys) and with
+    weights near the 2^24 maximum (64-bit keys) give the oracle's results."""
+    progs = synth.generate("batch1024_4x256_s24", 40, start=5000, blocks=2, threads=32, n_stmts=14,
+                           m_words=128)
+    for k, p in enumerate(progs):
+        if k % 2:
+            rng = synth.SplitMix64(synth.program_seed(61, k))
+            p.slot_weight = np.array([(1 << 24) - rng.randint(0, 1000) for _ in range(p.n_slots)], np.uint32)
+    got = gb.repair_batch(progs)
+    wide = 0
+    for p, g in zip(progs, got):
+        want = oracle.repair(p)
+        _same_result(g, want)
+        wide += int(p.slot_weight[0]) > 1000 and g["status"] == 0 and bin(g["mask"]).count("1") > 1
+    assert wide >= 3  # repaired programs with several large-weight slots on
+
+
 def test_tiny_checks_all_masks(gb):
     progs, masks, refs = [], [], []
     for seed in range(150):
