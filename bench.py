@@ -244,6 +244,11 @@ def kernel_source_sha(files=("relation.cu", "loop.cuh", "device.cuh", "engine.cu
     return h.hexdigest()[:16]
 
 
+# the sources each profiled kernel is built from, in hash order
+KERNEL_SOURCES = {"k_relation": ("relation.cu", "loop.cuh", "device.cuh", "engine.cuh"),
+                  "k_check": ("kernels.cu", "device.cuh", "engine.cuh")}
+
+
 def profile_counters(kernel, workload):
     """Per-launch counters from the committed ncu summary of `kernel` on
     `workload`, if its recorded source hash is this build's (else None).  The
@@ -256,7 +261,7 @@ def profile_counters(kernel, workload):
     except OSError:
         return None
     m = re.search(r"counters: source=(\w+) wavefronts=(\d+) dram_bytes=(\d+)", text)
-    if not m or m.group(1) != kernel_source_sha():
+    if not m or kernel not in KERNEL_SOURCES or m.group(1) != kernel_source_sha(KERNEL_SOURCES[kernel]):
         return None
     return {"wavefronts": int(m.group(2)), "dram_bytes": int(m.group(3)), "source": m.group(1)}
 
@@ -476,10 +481,15 @@ def run_ours(args, rank, world, local):
     t_rel = statistics.mean(rel_ms) / 1000.0
     t_loop = statistics.mean(loop_ms) / 1000.0
     survey_b, fused_b = check_bytes(batch.host_arena, n)
-    prof = profile_counters("k_relation", args.workload)
+    # the check kernel: the relation kernel for programs on the shared array
+    # with alike blocks, the general check kernel (after the expansion) for
+    # the others
+    check_kernel = ("k_relation" if not batch.has_general else
+                    "k_check" if batch.n_fast == 0 else "k_relation + k_check")
+    prof = profile_counters(check_kernel, args.workload)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     smem_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e9  # GB/s
-    check = {"kernel": "k_relation", "ms": t_rel * 1000, "checks_per_launch": n, "bound": "hbm",
+    check = {"kernel": check_kernel, "ms": t_rel * 1000, "checks_per_launch": n, "bound": "hbm",
              "algorithmic_bytes": survey_b, "fused_bytes": fused_b,
              "achieved": survey_b / t_rel / 1e9, "peak": hbm_peak, "unit": "GB/s",
              "frac": survey_b / t_rel / 1e9 / hbm_peak, "peak_kind": peak_kind,
