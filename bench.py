@@ -317,9 +317,10 @@ def time_steps(batch, steps, flush, stream):
 
 def time_runs(batch, steps, flush, stream):
     """CUDA-event times (ms) of `steps` whole repairs of the batch, each one
-    gr_repair_packed call (after tune(): for a batch of simple programs with
-    no general one, a single launch that computes the relations and runs the
-    loop).  The L2 is flushed before each, outside the events."""
+    gr_repair_packed call (the relation and loop kernels, after the
+    expansion and general check when the batch has general programs; one
+    launch when the shape word has bit 16).  The L2 is flushed before each,
+    outside the events."""
     import torch
 
     evs = []
@@ -335,8 +336,8 @@ def time_runs(batch, steps, flush, stream):
 
 
 def fused(batch):
-    """Whether a tuned run() of the batch is the one-launch relation + loop
-    (the autotuner's bit 16: it timed that faster than the two kernels)."""
+    """Whether run() of the batch is the one-launch relation + loop (bit 16
+    of the shape word, given through --shape)."""
     return bool((getattr(batch, "shape", 0) >> 16) & 1)
 
 

@@ -369,9 +369,9 @@ gr_status gr_relation_loop_packed(const void *d_arena, uint32_t n, const gr_opti
  * 0-7 index the relation kernel's shape, bits 8-11 the general check
  * kernel's, bit 12 is set when that kernel's grid is cut so that every CTA
  * gets the same number of programs (fewer CTAs than fit, no partly filled
- * last round), bit 16 when a batch of straight-line programs (no general
- * one) repairs at least 3% faster with the relation kernel running the loop
- * too, in one launch, than with the two kernels (both are timed).  Runs the kernels
+ * last round); bit 16 (the relation kernel running the loop too, in one
+ * launch) is never set here: it is set through gr_set_shape_packed, and
+ * gr_relation_loop_packed runs that launch directly.  Runs the kernels
  * several times, then one repair with the choices picked into d_out, and
  * synchronises the stream.  The
  * host-pointer batch calls tune the same way by themselves, once per batch

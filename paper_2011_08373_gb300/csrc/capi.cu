@@ -1408,31 +1408,10 @@ gr_status gr_tune_packed(const void *d_arena, uint32_t n, const gr_options *opts
     if ((s = tune_cfg(*ws, d_arena, n, d_scratch, scratch_bytes, st, h.s_max, skip, &t)) != GR_OK) return s;
     t.simple = (h.flags & kArenaSimple) ? 1u : 0u;
     t.rel_off = h.scratch_rel_off;
-    // one launch (the relation kernel runs the loop) or two: one launch
-    // when it repairs the batch at least 3% faster.  The single launch saves a launch gap and
-    // overlaps the loop with the relation tail, but its loop warps share the
-    // SMs with up to 32 warps and have fewer registers than the loop kernel's.
-    Tuned tf = t;
-    tf.fuse = 1;
-    if (full_cfg(*ws, n, tf).flags_off) {
-        const gr_options o = opts_or_default(opts);
-        cudaEvent_t e0, e1;
-        GR_CUDA(cudaEventCreate(&e0));
-        GR_CUDA(cudaEventCreate(&e1));
-        float ms_two = 0, ms_one = 0;
-        auto repair_with = [&](const Tuned &x) {
-            return [&, x] { return enqueue_repair(d_arena, n, o, d_scratch, scratch_bytes, d_out,
-                                                  full_cfg(*ws, n, x), expand_grid(*ws), false, true, st); };
-        };
-        cudaError_t e = best_of_runs(repair_with(t), d_scratch, e0, e1, st, &ms_two);
-        if (e == cudaSuccess) e = best_of_runs(repair_with(tf), d_scratch, e0, e1, st, &ms_one);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        if (e != cudaSuccess) return cuda_fail(e, "autotuner");
-        // only a clear win: the two are often within the runs' noise, and
-        // two launches are the better-measured default
-        if (ms_one < 0.97f * ms_two) t.fuse = 1;
-    }
+    // two launches (relation, loop): the single launch (bit 16) is only
+    // taken when asked for (gr_set_shape_packed, gr_relation_loop_packed).
+    // Timed here on a warm L2 it sometimes came out ahead, then lost in
+    // steady runs that read their inputs from HBM.
     ws->arena_shape[{d_arena, n}] = t;
     // one repair with the picked shapes leaves d_out filled, as documented
     GR_CUDA(enqueue_repair(d_arena, n, opts_or_default(opts), d_scratch, scratch_bytes, d_out, full_cfg(*ws, n, t),
