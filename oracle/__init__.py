@@ -113,6 +113,8 @@ def _configure(path):
     lib = C.CDLL(path)
     lib.orc_check.argtypes = [C.POINTER(_Prog), C.c_uint32, C.POINTER(_Witness)]
     lib.orc_check.restype = None
+    lib.orc_check_words.argtypes = lib.orc_check.argtypes
+    lib.orc_check_words.restype = None
     lib.orc_clauses.argtypes = [C.POINTER(_Prog), C.POINTER(_Witness),
                                 C.POINTER(C.c_uint32), C.c_uint32]
     lib.orc_clauses.restype = C.c_uint32
@@ -129,6 +131,10 @@ def _configure(path):
     lib.orc_repair_batch.argtypes = [C.POINTER(_Prog), C.POINTER(C.c_int32), C.c_uint32,
                                      C.c_int, C.c_uint32, C.c_int, C.POINTER(_Result), C.c_uint32]
     lib.orc_repair_batch.restype = None
+    lib.orc_repair_words.argtypes = lib.orc_repair.argtypes
+    lib.orc_repair_words.restype = None
+    lib.orc_repair_batch_words.argtypes = lib.orc_repair_batch.argtypes
+    lib.orc_repair_batch_words.restype = None
     lib.orc_check_pair.argtypes = [C.POINTER(_Prog), C.c_uint32, C.c_uint32, C.c_uint32,
                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]
     lib.orc_check_pair.restype = None
@@ -211,13 +217,15 @@ class _Marshalled:
             raise ValueError(f"{self.n_exec} executed statement instances (at most {MAX_STMTS})")
 
 
-def check(p, mask: int) -> dict:
+def check(p, mask: int, words: bool = False) -> dict:
     """Witnesses of program ``p`` under barrier mask ``mask``; rows index the
-    executed statement instances (the statements themselves without loops)."""
+    executed statement instances (the statements themselves without loops).
+    words=True: the same definition grouped by word (orc_check_words), for
+    launches whose thread-pair enumeration is too slow."""
     lib = _load()
     m = _Marshalled(p)
     w = _Witness()
-    lib.orc_check(C.byref(m.s), mask, C.byref(w))
+    (lib.orc_check_words if words else lib.orc_check)(C.byref(m.s), mask, C.byref(w))
     S = m.n_exec
     return {"intra": [w.intra[i] for i in range(S)], "inter": [w.inter[i] for i in range(S)],
             "diverge": w.diverge, "access_pairs": w.access_pairs}
@@ -283,24 +291,28 @@ def greedy(n_vars: int, weights, pos, forced: int = 0, forbidden: int = 0):
     return mask.value
 
 
-def repair(p, mode=None, grid_enabled: bool = True, max_iters: int = 64, strategy: int = 0) -> dict:
+def repair(p, mode=None, grid_enabled: bool = True, max_iters: int = 64, strategy: int = 0,
+           words: bool = False) -> dict:
     """Algorithm 1 on one program (mode defaults to ``p.mode``); strategy 0 =
-    MaxSAT proposals, 1 = the mhs strategy."""
+    MaxSAT proposals, 1 = the mhs strategy; words=True verifies with the
+    word-grouped check."""
     lib = _load()
     m = _Marshalled(p)
     r = _Result()
-    lib.orc_repair(C.byref(m.s), int(p.mode if mode is None else mode), int(grid_enabled),
-                   max_iters, strategy, C.byref(r))
+    (lib.orc_repair_words if words else lib.orc_repair)(C.byref(m.s), int(p.mode if mode is None else mode),
+                                                        int(grid_enabled), max_iters, strategy, C.byref(r))
     return _result_dict(r)
 
 
 def repair_batch(progs, grid_enabled: bool = True, max_iters: int = 64,
-                 n_threads: int = 1, strategy: int = 0) -> list:
-    """Algorithm 1 on many programs, spread over ``n_threads`` CPU threads."""
+                 n_threads: int = 1, strategy: int = 0, words: bool = False) -> list:
+    """Algorithm 1 on many programs, spread over ``n_threads`` CPU threads
+    (words=True: Verify by the word-grouped check)."""
     lib = _load()
     ms = [_Marshalled(p) for p in progs]
     arr = (_Prog * len(progs))(*[m.s for m in ms])
     modes = (C.c_int32 * len(progs))(*[int(p.mode) for p in progs])
     out = (_Result * len(progs))()
-    lib.orc_repair_batch(arr, modes, len(progs), int(grid_enabled), max_iters, strategy, out, n_threads)
+    fn = lib.orc_repair_batch_words if words else lib.orc_repair_batch
+    fn(arr, modes, len(progs), int(grid_enabled), max_iters, strategy, out, n_threads)
     return [_result_dict(out[i]) for i in range(len(progs))]

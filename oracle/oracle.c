@@ -34,6 +34,9 @@
  *                 stabbing by dynamic programming, and scipy's MILP solver.
  *   orc_repair -- pinned by the listings and by the path-independence lemma
  *                 (final mask = lowest-key witness-free mask over all masks).
+ *   orc_check_words, orc_repair_words -- the same definitions grouped by
+ *                 word (for full-size launches), pinned by equality with
+ *                 orc_check / orc_repair on random programs.
  */
 #include <pthread.h>
 #include <stdint.h>
@@ -282,6 +285,117 @@ void orc_check_pair(const orc_prog *p, uint32_t mask, uint32_t x, uint32_t y, in
     free(aj);
 }
 
+/* orc_check's definition grouped by word, for full-size launches whose
+ * thread-pair enumeration is too slow.  Two accesses can only race at a word
+ * both touch, so each instance's active accesses are sorted by (word, block,
+ * thread) and, for an instance pair, only the accesses of each word the two
+ * share are paired; a pair races under the same conditions as in orc_check
+ * (distinct threads; same block for the same-block scope, different blocks
+ * for the cross-block one, the latter only on the global array; the scope
+ * not separated under m).  The thread pairs orc_check examines do not depend
+ * on the addresses, so their number is counted rather than enumerated: for
+ * x < y, B (n_x n_y - n_xy) same-block pairs (t1 != t2; n_xy threads run
+ * both) and B (B - 1) n_x n_y cross-block pairs; for x == y, each unordered
+ * pair once, B n_x (n_x - 1) / 2 and B (B - 1) / 2 n_x^2 (n_x: the threads of
+ * a block that run x).  Pinned against orc_check on random programs
+ * (tests/test_oracle_pins.py). */
+typedef struct {
+    uint32_t word, blk, tid;
+} orc_acc;
+
+static int orc_cmp_acc(const void *u, const void *v) {
+    const orc_acc *a = (const orc_acc *)u, *b = (const orc_acc *)v;
+    if (a->word != b->word) return a->word < b->word ? -1 : 1;
+    if (a->blk != b->blk) return a->blk < b->blk ? -1 : 1;
+    if (a->tid != b->tid) return a->tid < b->tid ? -1 : 1;
+    return 0;
+}
+
+void orc_check_words(const orc_prog *p, uint32_t mask, orc_witness *out) {
+    memset(out, 0, sizeof(*out));
+    uint32_t st[ORC_MAX_STMTS], it[ORC_MAX_STMTS];
+    const uint32_t X = orc_unroll(p, st, it);
+    if (X > ORC_MAX_STMTS) return;
+    const uint32_t B = p->blocks, T = p->threads;
+    const uint64_t G = (uint64_t)B * T;
+    orc_acc *acc = (orc_acc *)malloc(sizeof(orc_acc) * X * G);
+    uint8_t *act = (uint8_t *)malloc(X * (size_t)T);
+    uint64_t cnt[ORC_MAX_STMTS], nact[ORC_MAX_STMTS];
+    for (uint32_t x = 0; x < X; x++) {
+        const uint32_t s = st[x];
+        nact[x] = 0;
+        for (uint32_t t = 0; t < T; t++) {
+            act[(size_t)x * T + t] = (uint8_t)orc_active(p->guard_k[s], p->guard_r[s], t);
+            nact[x] += act[(size_t)x * T + t];
+        }
+        uint64_t n = 0;
+        for (uint32_t b = 0; b < B; b++)
+            for (uint32_t t = 0; t < T; t++)
+                if (act[(size_t)x * T + t]) acc[x * G + n++] = (orc_acc){orc_addr(p, s, b, t, it[x]), b, t};
+        cnt[x] = n;
+        qsort(acc + x * G, n, sizeof(orc_acc), orc_cmp_acc);
+    }
+    for (uint32_t x = 0; x < X; x++) {
+        for (uint32_t y = x; y < X; y++) {
+            const uint32_t i = st[x], j = st[y];
+            if (p->space[i] != p->space[j]) continue;
+            if (p->op[i] != 1 && p->op[j] != 1) continue;
+            const int shared = p->space[i] == 0;
+            const int open_same = !orc_separated(p, st, mask, x, y, 0);
+            const int open_cross = !shared && !orc_separated(p, st, mask, x, y, 1);
+            if (!open_same && !open_cross) continue;
+            const uint64_t nx = nact[x], ny = nact[y], bb = B;
+            if (x < y) {
+                uint64_t nxy = 0;
+                for (uint32_t t = 0; t < T; t++) nxy += act[(size_t)x * T + t] && act[(size_t)y * T + t];
+                if (open_same) out->access_pairs += bb * (nx * ny - nxy);
+                if (open_cross) out->access_pairs += bb * (bb - 1) * nx * ny;
+            } else {
+                if (open_same) out->access_pairs += bb * (nx * (nx - 1) / 2);
+                if (open_cross) out->access_pairs += bb * (bb - 1) / 2 * nx * nx;
+            }
+            /* the words both instances touch, in order */
+            const orc_acc *ax = acc + x * G, *ay = acc + y * G;
+            int found_same = 0, found_cross = 0;
+            uint64_t u = 0, v = 0;
+            while (u < cnt[x] && v < cnt[y] && (open_same > found_same || open_cross > found_cross)) {
+                if (ax[u].word < ay[v].word) {
+                    u++;
+                } else if (ax[u].word > ay[v].word) {
+                    v++;
+                } else {
+                    const uint32_t w = ax[u].word;
+                    uint64_t u1 = u, v1 = v;
+                    while (u1 < cnt[x] && ax[u1].word == w) u1++;
+                    while (v1 < cnt[y] && ay[v1].word == w) v1++;
+                    for (uint64_t a = u; a < u1; a++)
+                        for (uint64_t c = v; c < v1; c++) {
+                            const int same = ax[a].blk == ay[c].blk;
+                            if (same && ax[a].tid == ay[c].tid) continue; /* one thread */
+                            if (same && open_same) found_same = 1;
+                            if (!same && open_cross) found_cross = 1;
+                        }
+                    u = u1;
+                    v = v1;
+                }
+            }
+            if (found_same) out->intra[x] |= 1u << y;
+            if (found_cross) out->inter[x] |= 1u << y;
+        }
+    }
+    free(acc);
+    free(act);
+    for (uint32_t k = 0; k < orc_nslots(p); k++) {
+        if (!((mask >> k) & 1u) || p->slot_guard_k[k] == 0) continue;
+        int seen_true = 0, seen_false = 0;
+        for (uint32_t t = 0; t < T; t++) {
+            if (orc_active(p->slot_guard_k[k], p->slot_guard_r[k], t)) seen_true = 1;
+            else seen_false = 1;
+        }
+        if (seen_true && seen_false) out->diverge |= 1u << k;
+    }
+}
+
 /* GenerateClause (Section 2.4): a race witness (x, y) is avoided exactly when
  * some barrier able to order it is on: any slot whose barrier runs between
  * instances x and y for a same-block witness, such a grid slot for a
@@ -420,7 +534,10 @@ int orc_greedy(uint32_t n, const uint32_t *w, const uint32_t *pos, uint32_t n_po
  * proposed mask has no witness (repaired) or the clauses are unsatisfiable
  * (unrepairable); each race witness adds its clause, each divergent slot a
  * negative unit clause.  More than max_iters checks ends with status 2. */
-void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iters, int strategy, orc_result *r) {
+typedef void (*orc_check_fn)(const orc_prog *, uint32_t, orc_witness *);
+
+static void orc_repair_by(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iters, int strategy,
+                          orc_check_fn check, orc_result *r) {
     memset(r, 0, sizeof(*r));
     const uint32_t n = orc_nslots(p);
     uint32_t grid = 0;
@@ -450,7 +567,7 @@ void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iter
             break;
         }
         orc_witness w;
-        orc_check(p, m, &w);
+        check(p, m, &w);
         if (r->iters < ORC_MAX_TRAJ) r->traj[r->iters] = m;
         r->iters++;
         r->access_pairs += w.access_pairs;
@@ -502,12 +619,24 @@ done:
     r->forbidden = forbidden;
 }
 
+/* Algorithm 1 with Verify by the thread-pair enumeration (orc_check), or by
+ * its word-grouped form (orc_check_words) for full-size launches. */
+void orc_repair(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iters, int strategy, orc_result *r) {
+    orc_repair_by(p, mode, grid_enabled, max_iters, strategy, orc_check, r);
+}
+
+void orc_repair_words(const orc_prog *p, int mode, int grid_enabled, uint32_t max_iters, int strategy,
+                      orc_result *r) {
+    orc_repair_by(p, mode, grid_enabled, max_iters, strategy, orc_check_words, r);
+}
+
 /* Many independent programs on worker threads (programs are independent). */
 typedef struct {
     const orc_prog *progs;
     const int32_t *modes;
     int grid_enabled, strategy;
     uint32_t max_iters;
+    orc_check_fn check;
     orc_result *out;
     uint32_t n, stride, first;
 } orc_job;
@@ -515,21 +644,32 @@ typedef struct {
 static void *orc_worker(void *arg) {
     orc_job *j = (orc_job *)arg;
     for (uint32_t i = j->first; i < j->n; i += j->stride)
-        orc_repair(&j->progs[i], j->modes[i], j->grid_enabled, j->max_iters, j->strategy, &j->out[i]);
+        orc_repair_by(&j->progs[i], j->modes[i], j->grid_enabled, j->max_iters, j->strategy, j->check, &j->out[i]);
     return NULL;
 }
 
-void orc_repair_batch(const orc_prog *progs, const int32_t *modes, uint32_t n, int grid_enabled,
-                      uint32_t max_iters, int strategy, orc_result *out, uint32_t n_threads) {
+static void orc_repair_batch_by(const orc_prog *progs, const int32_t *modes, uint32_t n, int grid_enabled,
+                                uint32_t max_iters, int strategy, orc_check_fn check, orc_result *out,
+                                uint32_t n_threads) {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > 256) n_threads = 256;
     pthread_t th[256];
     orc_job jobs[256];
     for (uint32_t t = 0; t < n_threads; t++) {
-        jobs[t] = (orc_job){progs, modes, grid_enabled, strategy, max_iters, out, n, n_threads, t};
+        jobs[t] = (orc_job){progs, modes, grid_enabled, strategy, max_iters, check, out, n, n_threads, t};
         pthread_create(&th[t], NULL, orc_worker, &jobs[t]);
     }
     for (uint32_t t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+}
+
+void orc_repair_batch(const orc_prog *progs, const int32_t *modes, uint32_t n, int grid_enabled,
+                      uint32_t max_iters, int strategy, orc_result *out, uint32_t n_threads) {
+    orc_repair_batch_by(progs, modes, n, grid_enabled, max_iters, strategy, orc_check, out, n_threads);
+}
+
+void orc_repair_batch_words(const orc_prog *progs, const int32_t *modes, uint32_t n, int grid_enabled,
+                            uint32_t max_iters, int strategy, orc_result *out, uint32_t n_threads) {
+    orc_repair_batch_by(progs, modes, n, grid_enabled, max_iters, strategy, orc_check_words, out, n_threads);
 }
 
 uint32_t orc_sizeof_result(void) { return (uint32_t)sizeof(orc_result); }

@@ -1,13 +1,17 @@
 """Parity at the workloads' full sizes, in the launch configuration the
 benchmark times (the packed, device-resident batch, persistent launch).
 
-Where the oracle cannot enumerate a whole check (64 x 256 global arrays,
-128 x 1,024 launches) it is sampled: its one-pair check gives the
-unconstrained witness set W(0) pair by pair, its solver gives the expected
-final mask from W(0) (clauses are exact, so the loop ends at the lowest-key
-mask over all masks whose own check is clean, whatever the trajectory), and a
-launch-independent copy of the program (same threads and slot guards, no
-accesses) gives the divergent slots."""
+Every program of every batch is compared with the oracle's own loop on every
+field.  Where the oracle's thread-pair enumeration is too slow for a whole
+batch (64 x 256 global arrays, launches of up to 16 x 1,024 or 128 x 1,024
+threads) its loop verifies with the same definition grouped by word
+(orc_check_words, pinned against the enumeration on CPU).  Independently of
+that, the one-pair enumeration gives the unconstrained witness set W(0) pair
+by pair for sampled programs, its solver the expected final mask from W(0)
+(clauses are exact, so the loop ends at the lowest-key mask over all masks
+whose own check is clean, whatever the trajectory), and a launch-independent
+copy of the program (same threads and slot guards, no accesses) gives the
+divergent slots."""
 import concurrent.futures as cf
 import os
 
@@ -115,12 +119,18 @@ def test_uneven4096_full_size(gb):
     _, got = _run(gb, progs)
     for p, r in zip(progs, got):
         _properties(p, r)
-    # every program of at most 4,096 threads in all, every field
-    sample = [i for i, p in enumerate(progs) if p.blocks * p.threads <= 4096]
-    assert len(sample) > 2000
+    # every program, every field: the oracle's loop verifying by thread-pair
+    # enumeration on the programs of at most 1,024 threads in all, by the
+    # word-grouped check on all (about a minute of oracle time on 16 cores)
+    small = [i for i, p in enumerate(progs) if p.blocks * p.threads <= 1024]
+    assert len(small) > 1000
     big = max(range(len(progs)), key=lambda i: progs[i].blocks * progs[i].threads * progs[i].n_stmts)
-    want = oracle.repair_batch([progs[i] for i in sample], n_threads=N_THREADS)
-    for i, w in zip(sample, want):
+    want = oracle.repair_batch([progs[i] for i in small], n_threads=N_THREADS)
+    for i, w in zip(small, want):
+        for k in KEYS:
+            assert got[i][k] == w[k], (i, k)
+    want = oracle.repair_batch(progs, n_threads=N_THREADS, words=True)
+    for i, w in enumerate(want):
         for k in KEYS:
             assert got[i][k] == w[k], (i, k)
     # the host-pointer call (chunks packed on the host, its own tuned shapes)
@@ -165,11 +175,17 @@ def test_interblock_full_size_sampled(gb, idx):
 
 
 def test_interblock_full_size_every_field(gb):
-    """Eight programs of the inter-block batch (64 blocks x 256 threads over a
+    """Every program of the inter-block batch (64 blocks x 256 threads over a
     65,536-word global array) at full size, compared with the oracle's own
-    loop on every field: trajectory, iterations, clauses, access pairs."""
+    loop on every field: trajectory, iterations, clauses, access pairs (the
+    loop verifying with the word-grouped check; eight programs also with the
+    thread-pair enumeration)."""
     progs = synth.generate("interblock256_64x256_s16")
     _, got = _run(gb, progs)
+    want = oracle.repair_batch(progs, n_threads=N_THREADS, words=True)
+    for i, w in enumerate(want):
+        for k in KEYS:
+            assert got[i][k] == w[k], (i, k)
     idx = list(range(5, 256, 32))
     want = oracle.repair_batch([progs[i] for i in idx], n_threads=N_THREADS)
     for i, w in zip(idx, want):
@@ -187,6 +203,11 @@ def test_large_program_full_size(gb):
             assert r["status"] == 1
         else:
             assert r["status"] == 0 and (r["mask"], r["weight"]) == sol
+    # every field, the oracle's loop verifying with the word-grouped check
+    want = oracle.repair_batch(progs, n_threads=N_THREADS, words=True)
+    for i, w in enumerate(want):
+        for k in KEYS:
+            assert got[i][k] == w[k], (i, k)
 
 
 def test_loops512_full_size(gb):
@@ -198,6 +219,10 @@ def test_loops512_full_size(gb):
     sample = list(range(0, 512, 16))
     want = oracle.repair_batch([progs[i] for i in sample], n_threads=N_THREADS)
     for i, w in zip(sample, want):
+        for k in KEYS:
+            assert got[i][k] == w[k], (i, k)
+    want = oracle.repair_batch(progs, n_threads=N_THREADS, words=True)
+    for i, w in enumerate(want):
         for k in KEYS:
             assert got[i][k] == w[k], (i, k)
 

@@ -459,6 +459,44 @@ def test_check_pair_matches_check(seed):
         assert total == full["access_pairs"]
 
 
+@pytest.mark.parametrize("seed", range(40))
+def test_check_words_matches_check(seed):
+    """The word-grouped check (used at full size) gives every field of the
+    thread-pair enumeration: witnesses of both scopes, divergent slots and
+    the pairs examined, on random programs with guards, permutation maps,
+    both arrays, block-offset shared maps, counted loops and candidate
+    sites, under several masks."""
+    from _tiny import random_loop_program, with_sites
+
+    progs = [random_program(9100 + seed, s_max=6, b_max=3, t_max=9, m_max=12),
+             random_program(9200 + seed, s_max=5, b_max=4, t_max=12, m_max=20, shared_c=True),
+             random_loop_program(9300 + seed),
+             with_sites(random_program(9400 + seed, s_max=5, b_max=3, t_max=8, m_max=12), seed),
+             random_program(9500 + seed, s_min=4, s_max=8, b_min=2, b_max=6, t_min=16, t_max=48, m_max=200,
+                            a_max=3, c_max=60)]
+    for p in progs:
+        n = p.n_slots
+        for m in {0, (1 << n) - 1, (seed * 2654435761) % (1 << n) if n else 0, (seed * 40503) % (1 << n) if n else 0}:
+            assert oracle.check(p, m, words=True) == oracle.check(p, m), (seed, m)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_repair_words_matches_repair(seed):
+    """Algorithm 1 verified by the word-grouped check follows the same
+    trajectory to the same result, both strategies, one program at a time and
+    in a batch."""
+    from _tiny import random_loop_program
+
+    progs = [random_program(9600 + seed, s_max=7, b_max=3, t_max=10, m_max=16),
+             random_loop_program(9700 + seed),
+             random_program(9800 + seed, s_min=5, s_max=9, b_min=1, b_max=4, t_min=8, t_max=40, m_max=160,
+                            a_max=3, c_max=40, p_write=0.35)]
+    for strategy in (0, 1):
+        for p in progs:
+            assert oracle.repair(p, strategy=strategy, words=True) == oracle.repair(p, strategy=strategy)
+    assert oracle.repair_batch(progs, n_threads=2, words=True) == oracle.repair_batch(progs)
+
+
 # --------------------------------------------------------------------------
 # The mhs strategy (Section 2.4): greedy minimal hitting sets
 # --------------------------------------------------------------------------
