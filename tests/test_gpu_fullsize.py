@@ -227,6 +227,44 @@ def test_loops512_full_size(gb):
             assert got[i][k] == w[k], (i, k)
 
 
+def test_sites128_full_size(gb):
+    """The batch with 30 barrier variables per program (a block and a grid
+    candidate at 15 sites; 16 blocks x 256 threads over a global array) at
+    full size, every program.  The oracle's brute-force solve cannot reach 30
+    variables, so: the device's check under the empty mask equals the
+    oracle's (word-grouped) on every field; the repair ends at the lowest-key
+    mask over the clauses of those witnesses (path independence), found by
+    integer programming; its clauses are among those; and the check of its
+    final mask is equal on both sides."""
+    pytest.importorskip("scipy.optimize")
+    import torch
+    from test_oracle_pins import milp_lowest_key
+
+    progs = synth.generate("sites128_16x256_s16")
+    assert len(progs) == 128 and all(p.n_slots == 30 for p in progs)
+    db, got = _run(gb, progs)
+    db.check([0] * len(progs))
+    torch.cuda.synchronize()
+    w_dev = db.witnesses(progs)
+    db.check([r["mask"] for r in got])
+    torch.cuda.synchronize()
+    w_fin = db.witnesses(progs)
+    for i, (p, r) in enumerate(zip(progs, got)):
+        _properties(p, r)
+        w0 = oracle.check(p, 0, words=True)
+        assert w_dev[i] == w0, i
+        cls = oracle.clauses(p, w0)
+        div = oracle.check(p, (1 << p.n_slots) - 1, words=True)["diverge"]
+        forced = p.existing_mask if p.mode == MODE_REPAIR else 0
+        want = milp_lowest_key(p.n_slots, [int(x) for x in p.slot_weight], cls, p.neg_clauses, forced, div)
+        if want is None:
+            assert r["status"] == 1, i
+        else:
+            assert r["status"] == 0 and (r["mask"], r["weight"]) == want, i
+            assert set(r["clauses"]) <= set(cls), i
+            assert w_fin[i] == oracle.check(p, r["mask"], words=True), i
+
+
 def test_wide_lane_full_size(gb):
     """The wide lane at full size: the inter-block batch and large programs
     give the same results as the persistent launch (itself pinned above)."""
