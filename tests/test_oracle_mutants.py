@@ -60,6 +60,15 @@ MUTANTS = [
     ("slot_position_ignored", "return p->slot_pos ? p->slot_pos[k] : k;", "return k;"),
     ("clauses_kept_as_multiset", "if (u == 0 || clauses[u - 1] != clauses[t]) clauses[u++] = clauses[t];",
      "clauses[u++] = clauses[t];"),
+    # the word-grouped check
+    ("words_same_thread_races", "if (same && ax[a].tid == ay[c].tid) continue; /* one thread */", ""),
+    ("words_pairs_count_same_thread", "out->access_pairs += bb * (nx * ny - nxy);",
+     "out->access_pairs += bb * nx * ny;"),
+    ("words_unordered_cross_pairs_doubled", "out->access_pairs += bb * (bb - 1) / 2 * nx * nx;",
+     "out->access_pairs += bb * (bb - 1) * nx * nx;"),
+    ("words_merge_skips_a_word", "u = u1;\n                    v = v1;", "u = u1;\n                    v = v1 + 1;"),
+    ("words_stops_at_first_scope", "(open_same > found_same || open_cross > found_cross)",
+     "(open_same > found_same && open_cross > found_cross)"),
 ]
 
 
@@ -94,6 +103,8 @@ def _all_pins():
         yield lambda s=s: pins.test_repair_path_independence_with_negative_clauses(s)
         yield lambda s=s: pins.test_site_check_matches_interpreter(s)
         yield lambda s=s: pins.test_site_repair_path_independence(s)
+        yield lambda s=s: pins.test_check_words_matches_check(s)
+        yield lambda s=s: pins.test_repair_words_matches_repair(s)
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
