@@ -208,7 +208,7 @@ def _guard_count(T, k, r):
 def check_bytes(arena, n):
     """Bytes one check of every program moves, two ways:
 
-    survey: the traces an expanded check reads, 4 bytes per active access
+    expanded: the traces an expanded check reads, 4 bytes per active access
       over every block, plus, since the maps are evaluated in the kernel, a
       2-byte table entry per access of a permutation statement; plus the
       program record and the relation rows written;
@@ -217,7 +217,7 @@ def check_bytes(arena, n):
       block), the relation rows.
     """
     off0 = int(arena[16:24].view(np.uint64)[0])
-    survey = fused = 0
+    expanded = fused = 0
     for i in range(n):
         off = off0 + DEVPROG_BYTES * i
         f = arena[off:off + 16].view(np.uint32)
@@ -228,11 +228,11 @@ def check_bytes(arena, n):
             r = int(st[s, 22:24].view(np.uint16)[0])
             act = _guard_count(T, k, r)
             perm = int(st[s, 2]) == 2
-            survey += act * B * (4 + (2 if perm else 0))
+            expanded += act * B * (4 + (2 if perm else 0))
             fused += act * 2 if perm else 0
-        survey += DEVPROG_BYTES + WITNESS_BYTES
+        expanded += DEVPROG_BYTES + WITNESS_BYTES
         fused += DEVPROG_BYTES + WITNESS_BYTES
-    return survey, fused
+    return expanded, fused
 
 
 def kernel_source_sha(files=("relation.cu", "loop.cuh", "device.cuh", "engine.cuh")):
@@ -473,7 +473,7 @@ def run_ours(args, rank, world, local):
     hbm_peak, peak_kind = _peaks()
 
     # rooflines.  The check kernel (relation) does one check per program, the
-    # empty-mask one; its bytes per check follow the survey's count (4-byte
+    # empty-mask one; its bytes per check are those of an expanded check (4-byte
     # trace reads of every active access over every block), next to the bytes
     # the fused kernel must move.  Its shared-memory fraction takes the
     # wavefronts per launch from the committed ncu summary of this kernel
@@ -481,7 +481,7 @@ def run_ours(args, rank, world, local):
     # per clock at the sampled SM clock.
     t_rel = statistics.mean(rel_ms) / 1000.0
     t_loop = statistics.mean(loop_ms) / 1000.0
-    survey_b, fused_b = check_bytes(batch.host_arena, n)
+    expanded_b, fused_b = check_bytes(batch.host_arena, n)
     # the check kernel: the relation kernel for programs on the shared array
     # with alike blocks, the general check kernel (after the expansion) for
     # the others
@@ -491,9 +491,9 @@ def run_ours(args, rank, world, local):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     smem_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e9  # GB/s
     check = {"kernel": check_kernel, "ms": t_rel * 1000, "checks_per_launch": n, "bound": "hbm",
-             "algorithmic_bytes": survey_b, "fused_bytes": fused_b,
-             "achieved": survey_b / t_rel / 1e9, "peak": hbm_peak, "unit": "GB/s",
-             "frac": survey_b / t_rel / 1e9 / hbm_peak, "peak_kind": peak_kind,
+             "algorithmic_bytes": expanded_b, "fused_bytes": fused_b,
+             "achieved": expanded_b / t_rel / 1e9, "peak": hbm_peak, "unit": "GB/s",
+             "frac": expanded_b / t_rel / 1e9 / hbm_peak, "peak_kind": peak_kind,
              "fused_frac": fused_b / t_rel / 1e9 / hbm_peak,
              "traffic": prof["dram_bytes"] if prof else None,
              "smem": ({"achieved": prof["wavefronts"] * 128 / t_rel / 1e9, "peak": smem_peak, "unit": "GB/s",
