@@ -201,9 +201,9 @@ def test_one_launch_equals_the_two_kernels(gb):
     """gr_relation_loop_packed (the relation kernel running the loop too, each
     program's loop waiting on its relation's flag) writes the results the
     oracle gives on a small batch, and the two-kernel repair's results on the
-    1,024-program batch of 4 x 256 threads and 24 statements; the device
-    error word stays 0.  A batch with a program that needs expanded traces is
-    refused with nothing launched."""
+    1,024-program batch of 4 x 256 threads and 24 statements and on the
+    4,096-program uneven batch; the device error word stays 0.  A batch with
+    a program that needs expanded traces is refused with nothing launched."""
     import ctypes as C
 
     import torch
@@ -221,21 +221,22 @@ def test_one_launch_equals_the_two_kernels(gb):
     for g, w in zip(db.results(), oracle.repair_batch(small, n_threads=4)):
         _same(g, w)
 
-    full = synth.generate("batch1024_4x256_s24")
-    db = gb.DeviceBatch(full)
-    db.tune()
-    db.relation()
-    db.loop()
-    torch.cuda.synchronize()
-    two = db.results_raw().copy()
-    db.out.view(torch.uint8).fill_(0xA5)
-    db.relation_loop()
-    torch.cuda.synchronize()
-    assert err_word(db) == 0
-    one = db.results_raw()
-    for k in one.dtype.names:
-        if k not in ("_pad", "t_start_ns", "t_end_ns"):
-            assert np.array_equal(one[k], two[k]), k
+    for name in ("batch1024_4x256_s24", "uneven4096_mixed"):
+        full = synth.generate(name)
+        db = gb.DeviceBatch(full)
+        db.tune()
+        db.relation()
+        db.loop()
+        torch.cuda.synchronize()
+        two = db.results_raw().copy()
+        db.out.view(torch.uint8).fill_(0xA5)
+        db.relation_loop()
+        torch.cuda.synchronize()
+        assert err_word(db) == 0
+        one = db.results_raw()
+        for k in one.dtype.names:
+            if k not in ("_pad", "t_start_ns", "t_end_ns"):
+                assert np.array_equal(one[k], two[k]), (name, k)
 
     general = small[:3] + synth.generate("interblock256_64x256_s16", 1, blocks=3, threads=32, n_stmts=5,
                                          m_words=512)
