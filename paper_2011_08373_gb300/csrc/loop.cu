@@ -19,6 +19,11 @@ __global__ void __launch_bounds__(WARPS * 32)
     k_loop(const uint8_t *__restrict__ arena, uint32_t n, gr_options opts, uint8_t *__restrict__ scratch,
            uint64_t scratch_bytes, gr_repair_result *__restrict__ out) {
     extern __shared__ uint4 loop_raw[];
+    // launched as a programmatic dependent of the relation kernel: its CTAs
+    // may start while that kernel's last CTAs run, and wait here until it
+    // has completed and its relation rows are visible (no wait when the
+    // previous work in the stream was not a kernel that allows it)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     LW &lw = *reinterpret_cast<LW *>(reinterpret_cast<uint8_t *>(loop_raw) + warp_smem<LW>() * warp);
     const ArenaView V = view(arena);
@@ -48,17 +53,30 @@ cudaError_t configure_loop(uint32_t max_dynamic_smem) {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loop_smem_bytes(true));
 }
 
+// The loop kernel may launch before the kernel ahead of it in the stream
+// has finished (programmatic stream serialization): it waits for that
+// kernel's completion itself, at its first instruction, so its launch and
+// CTA placement overlap the relation kernel's tail.
 cudaError_t launch_loop(const void *d_arena, uint32_t n, const gr_options &opts, void *d_scratch,
                         uint64_t scratch_bytes, gr_repair_result *d_out, uint32_t grid, bool simple, cudaStream_t st) {
     const uint8_t *a = static_cast<const uint8_t *>(d_arena);
     uint8_t *sc = static_cast<uint8_t *>(d_scratch);
-    if (simple)
-        k_loop<kSimpleWarps, LoopWarpSimple>
-            <<<grid, kSimpleWarps * 32, loop_smem_bytes(true), st>>>(a, n, opts, sc, scratch_bytes, d_out);
-    else
-        k_loop<kLoopWarps, LoopWarp><<<grid, kLoopWarps * 32, loop_smem_bytes(false), st>>>(a, n, opts, sc,
-                                                                                          scratch_bytes, d_out);
-    return cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (simple) {
+        cfg.blockDim = dim3(kSimpleWarps * 32);
+        cfg.dynamicSmemBytes = loop_smem_bytes(true);
+        return cudaLaunchKernelEx(&cfg, k_loop<kSimpleWarps, LoopWarpSimple>, a, n, opts, sc, scratch_bytes, d_out);
+    }
+    cfg.blockDim = dim3(kLoopWarps * 32);
+    cfg.dynamicSmemBytes = loop_smem_bytes(false);
+    return cudaLaunchKernelEx(&cfg, k_loop<kLoopWarps, LoopWarp>, a, n, opts, sc, scratch_bytes, d_out);
 }
 
 }  // namespace gr

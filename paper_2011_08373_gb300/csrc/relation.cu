@@ -484,6 +484,11 @@ __global__ void __launch_bounds__(NT, MINB)
                uint8_t *__restrict__ scratch, uint64_t scratch_bytes, gr_witnesses *__restrict__ out,
                uint32_t table_bytes, gr_options opts, gr_repair_result *__restrict__ results) {
     extern __shared__ uint4 rel_raw[];
+    // a dependent launch (the loop kernel) may be placed as this kernel's
+    // CTAs exit; it waits for this kernel's completion before reading
+    // anything it writes.  Every CTA is resident from the start (the grid
+    // is at most the SMs' capacity), so nothing waits on the dependent.
+    asm volatile("griddepcontrol.launch_dependents;");
     RelSmem &sm = *reinterpret_cast<RelSmem *>(rel_raw);
     uint16_t *tab = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(rel_raw) + kRelFixed);
     const ArenaView V = view(arena);
