@@ -19,28 +19,36 @@ __global__ void __launch_bounds__(WARPS * 32)
     k_loop(const uint8_t *__restrict__ arena, uint32_t n, gr_options opts, uint8_t *__restrict__ scratch,
            uint64_t scratch_bytes, gr_repair_result *__restrict__ out) {
     extern __shared__ uint4 loop_raw[];
-    // launched as a programmatic dependent of the relation kernel: its CTAs
-    // may start while that kernel's last CTAs run, and wait here until it
-    // has completed and its relation rows are visible (no wait when the
-    // previous work in the stream was not a kernel that allows it)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     LW &lw = *reinterpret_cast<LW *>(reinterpret_cast<uint8_t *>(loop_raw) + warp_smem<LW>() * warp);
     const ArenaView V = view(arena);
     uint32_t *ctrl = reinterpret_cast<uint32_t *>(scratch);
-    if (!launch_matches(V, n, scratch_bytes)) {
+    const bool ok = launch_matches(V, n, scratch_bytes);
+    // The first program's queue item, order entry and record come from the
+    // queue counter (cleared before the relation kernel, which does not use
+    // it) and the arena, so they are fetched before the wait below.
+    uint32_t item = n;
+    if (ok) {
+        if (lane == 0) item = atomicAdd(&ctrl[3], 1u);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item < n) loop_load_record(lw, V, V.order[item]);
+    }
+    // Launched as a programmatic dependent of the relation kernel: its CTAs
+    // may start while that kernel's last CTAs run, and wait here until it
+    // has completed and its relation rows are visible (no wait when the
+    // previous work in the stream was not a kernel that allows it).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (!ok) {
         if (threadIdx.x == 0) atomicOr(&ctrl[1], kErrArgs);
         return;
     }
     const gr_witnesses *rel = reinterpret_cast<const gr_witnesses *>(scratch + V.h->scratch_rel_off);
     const uint32_t max_iters = opts.max_iters == 0 ? GR_MAX_ITERS : min(opts.max_iters, (uint32_t)GR_MAX_ITERS);
     const uint64_t deadline_ns = opts.deadline_us * 1000ull;
-    for (;;) {
-        uint32_t item = 0;
+    for (bool first = true; item < n; first = false) {
+        loop_program(lw, V, V.order[item], rel, opts, max_iters, deadline_ns, out, ctrl, first);
         if (lane == 0) item = atomicAdd(&ctrl[3], 1u);
         item = __shfl_sync(0xFFFFFFFFu, item, 0);
-        if (item >= n) break;
-        loop_program(lw, V, V.order[item], rel, opts, max_iters, deadline_ns, out, ctrl);
     }
 }
 

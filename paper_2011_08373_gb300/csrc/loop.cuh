@@ -644,17 +644,23 @@ __device__ uint32_t build_row_minima(LW &lw, uint32_t acc_i, uint32_t acc_x) {
 
 // Algorithm 1 for program p by the calling warp, over its conflict relation
 // rel[p]; writes out[p].  lw: the warp's record in shared memory.
+// Program p's record into the warp's shared copy (from the arena: it does
+// not depend on the relations).
+template <class LW>
+__device__ __forceinline__ void loop_load_record(LW &lw, const ArenaView &V, uint32_t p) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(&V.progs[p]);
+    uint4 *d4 = reinterpret_cast<uint4 *>(&lw.prog);
+    for (uint32_t i = lane_id(); i < sizeof(DevProg) / 16; i += 32u) d4[i] = src[i];
+}
+
+// have_record: loop_load_record(lw, V, p) has run already.
 template <class LW>
 __device__ __forceinline__ void loop_program(LW &lw, const ArenaView &V, uint32_t p, const gr_witnesses *rel,
                                              const gr_options &opts, uint32_t max_iters, uint64_t deadline_ns,
-                                             gr_repair_result *out, uint32_t *ctrl) {
+                                             gr_repair_result *out, uint32_t *ctrl, bool have_record = false) {
     const uint32_t lane = lane_id();
     const DevProg &P = lw.prog;
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(&V.progs[p]);
-        uint4 *d4 = reinterpret_cast<uint4 *>(&lw.prog);
-        for (uint32_t i = lane; i < sizeof(DevProg) / 16; i += 32u) d4[i] = src[i];
-    }
+    if (!have_record) loop_load_record(lw, V, p);
     // at L2 (not L1): in the relation kernel's own loop, another CTA wrote them
     const uint32_t conf_i = __ldcg(&rel[p].race_intra[lane]), conf_x = __ldcg(&rel[p].race_inter[lane]);
     __syncwarp();
