@@ -443,9 +443,13 @@ gr_status gr_server_destroy(gr_server *s);
  * The scratch is a fixed 64 MiB device array inside the library, held by
  * every GPU that loads the library until the process exits; a batch whose
  * gr_pack_size scratch figure exceeds it is rejected with GR_ECAPACITY.  The
- * call reads the 192-byte arena header back to the host (a synchronising copy
- * on stream), so it cannot be made inside a stream capture; it allocates
- * nothing, validates opts as gr_repair_packed does and launches what
+ * first call on a device sets that device up (it looks up the array's
+ * device address, with the device current), so that first call should come
+ * before any stream capture; a cudaDeviceReset of the device discards the
+ * array, and the entry point must not be called on that device again in
+ * the same process.  Each call reads the 192-byte arena header back to the
+ * host (a synchronising copy on stream); it allocates nothing, validates
+ * opts as gr_repair_packed does and launches what
  * gr_repair_packed launches (with the shapes gr_tune_packed recorded for
  * (d_arena, n), else the defaults).  Device-side errors (the device error
  * word) are not reported on this path: the word stays in the fixed array.

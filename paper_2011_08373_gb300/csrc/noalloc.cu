@@ -10,20 +10,25 @@
 //
 // The scratch (address traces, per-segment masks and ranges, the conflict
 // relations, the work-queue counters and the device error word) lives in
-// `g_noalloc_scratch`, a file-scope __device__ array of kNoAllocScratchBytes.
-// Every GPU that loads the library holds it until the process exits.  Its
-// device address is looked up on every call (in the current context, so a
-// cudaDeviceReset between calls is harmless).  Every call reads the arena
-// header back and synchronises on it, so the call cannot be made inside a
-// stream capture.  Every call shares the one array and it keeps the last
-// call's contents: the control words are cleared on each call, everything
-// else is rewritten before it is read.  Calls that overlap on the GPU (two
-// streams, two host threads) race on the array and must not be issued; the
-// host-side lock below only orders the enqueueing.  The device error word
-// stays inside the array and is not read back (the call does not wait for
-// its kernels): device-side errors are not reported on this path; the
-// library sizes every launch from the arena header, which this call checks
-// first.
+// `g_noalloc_scratch`, a file-scope static __device__ array of
+// kNoAllocScratchBytes.  Every GPU that loads the library holds it until the
+// process exits.  In host code that name is only a host-side stand-in for
+// the symbol, not a device address, so the first call on each device (with
+// that device current) looks the array's device address up with
+// cudaGetSymbolAddress, checks the result and keeps it for that device; the
+// kernels are given that address.  That first call should therefore come
+// before any stream capture.  A cudaDeviceReset of the device discards the
+// array with the context: do not call this entry point on that device again
+// in the same process afterwards.  Every call reads the arena header back
+// with a synchronising copy on its stream.  Every call shares the one array
+// and it keeps the last call's contents: the control words are cleared on
+// each call, everything else is rewritten before it is read.  Calls that
+// overlap on the GPU (two streams, two host threads) race on the array and
+// must not be issued; the host-side lock below only orders the enqueueing.
+// The device error word stays inside the array and is not read back (the
+// call does not wait for its kernels): device-side errors are not reported
+// on this path; the library sizes every launch from the arena header, which
+// this call checks first.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -37,11 +42,17 @@ namespace gr {
 
 constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB
 
-__device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
 
 std::mutex g_noalloc_mu;
+
+// Per device, set up by its first call: the array's device address and the
+// SM count (guarded by g_noalloc_mu).
+constexpr int kNoAllocDevices = 64;
+void *g_noalloc_ptr[kNoAllocDevices] = {};
+int g_noalloc_sms[kNoAllocDevices] = {};
 
 }  // namespace
 void set_last_error(const char *msg);
@@ -57,20 +68,27 @@ gr_status noalloc_fail(gr_status code, const char *fmt, ...) {
     return code;
 }
 
-// Device address of the scratch array and the SM count of the current device.
+// Device address of the scratch array and the SM count of the current
+// device: looked up by the first call on that device (which is current
+// here), then kept.  Called with g_noalloc_mu held.
 gr_status noalloc_setup(int *sms_out, void **ptr_out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-        return noalloc_fail(GR_ECUDA, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
-    *sms_out = sms;
-    *ptr_out = p;
+    if (dev < 0 || dev >= kNoAllocDevices) return noalloc_fail(GR_ECUDA, "device index %d unsupported", dev);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return noalloc_fail(GR_ECUDA, "cudaGetSymbolAddress(g_noalloc_scratch): %s", cudaGetErrorString(e));
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return noalloc_fail(GR_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+        g_noalloc_sms[dev] = sms;
+        g_noalloc_ptr[dev] = p;
+    }
+    *sms_out = g_noalloc_sms[dev];
+    *ptr_out = g_noalloc_ptr[dev];
     return GR_OK;
 }
 
